@@ -1,0 +1,312 @@
+#!/usr/bin/env python
+"""Benchmark of one CheFSI step on the 64^3 / 128-atom / Ns=512 / m=24 Gamma-point cell.
+
+A step is one pass of the whole hot path on one block of synthetic orbitals:
+10-step FP64 Lanczos bounds -> FP32 Chebyshev filter of degree 24 ->
+mixed-precision Rayleigh-Ritz (Grams, FP64 Cholesky + eigensolve, rotation).
+The metric is filter work per second, Nd * Ns * m point-orbital-degrees per
+step divided by the time of the whole step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 it runs under torchrun as independent replicas (one cell per GPU).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CheFSI filter throughput (G point-orbital-degrees/s)"
+UNIT = "Gpt-orb-deg/s"
+WORKLOAD = "64^3 grid h=0.4, 128 perturbed-FCC s+p atoms, Ns=512, m=24, Gamma point"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-cols", type=int, default=1)
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = tempfile.mktemp(suffix=".csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+_CPU_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from paper_1603_04339_gb300 import synth
+from oracle import sparc_oracle as O
+wl = synth.config2()
+H = O.OracleH(wl)
+X = synth.random_orbitals(wl.nd, wl.ns, 2002)[: {cols}].astype(np.float32).astype(np.float64)
+v0 = synth.lanczos_start(wl.nd, 2003)
+a0, b, _ = O.lanczos_bounds(H, v0, 10)
+a = a0 + (b - a0) * (wl.ns / wl.nd) ** (2.0 / 3.0)
+reps = []
+for _ in range({reps}):
+    t = time.perf_counter()
+    O.cheb_filter(H, X, wl.m, a, b, a0)
+    reps.append(time.perf_counter() - t)
+print(json.dumps({{"seconds": reps, "units": wl.nd * {cols} * wl.m}}))
+"""
+
+
+def cpu_oracle_sample(cols=1, reps=1):
+    """Time the oracle's filter on `cols` columns of the benchmark cell, single-threaded."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = _CPU_SNIPPET.format(root=ROOT, cols=cols, reps=reps)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d
+
+
+# ------------------------------------------------------------------ reference arm (the oracle)
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    # warm-up and timed steps, each a bounded sample (one column, all m degrees)
+    d = cpu_oracle_sample(cols=args.cpu_sample_cols, reps=args.steps + args.warmup)
+    secs = d["seconds"][args.warmup:]
+    units = d["units"]
+    t = sum(secs) / len(secs)
+    value = units / t / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD,
+                                            "sample": f"{args.cpu_sample_cols} of 512 orbitals, all 24 degrees"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"numpy FP64 oracle filter, {args.cpu_sample_cols} column(s) x 24 degrees"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    from paper_1603_04339_gb300 import build, synth
+    if world > 1:
+        if rank == 0:
+            build.build()
+        dist.barrier()
+    else:
+        build.build()
+    from paper_1603_04339_gb300 import sparc
+
+    wl = synth.config2()
+    nd, ns, m = wl.nd, wl.ns, wl.m
+    ctx = sparc.Context(local)
+    H = sparc.Hamiltonian.from_workload(ctx, wl)
+    X_host = synth.random_orbitals(nd, ns, 2002).astype(np.float32)
+    X = torch.from_numpy(X_host).cuda()
+    Y = torch.empty_like(X)
+    eig = torch.zeros(ns, dtype=torch.float64, device="cuda")
+    v0 = torch.from_numpy(synth.lanczos_start(nd, 2003)).cuda()
+    stream = torch.cuda.current_stream()
+    frac = (ns / nd) ** (2.0 / 3.0)
+
+    def step(Xin, Yout):
+        a0, b = sparc.sparc_lanczos_bounds(H, 10, v0, stream=stream)
+        a = a0 + (b - a0) * frac
+        sparc.sparc_cheb_filter(H, m, a, b, a0, Xin, Yout, stream=stream)
+        sparc.sparc_rayleigh_ritz(H, Yout, eig, sparc.RR_MIXED, stream=stream)
+
+    for _ in range(args.warmup):
+        step(X, Y)
+    torch.cuda.synchronize()
+
+    # ---- timed region (device events on the launching stream; inputs 537 MB > L2)
+    clocks = Clocks(torch.cuda.current_device())
+    ctx.timing(True)
+    l0 = ctx.launches()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(X, Y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    launches = (ctx.launches() - l0) // args.steps
+    ms = e0.elapsed_time(e1) / args.steps
+    hp_ms, hp_n = ctx.timing_read("hpass")
+    ga_ms, ga_n = ctx.timing_read("gather")
+    gr_ms, _ = ctx.timing_read("gram")
+    ei_ms, _ = ctx.timing_read("eig")
+    ro_ms, _ = ctx.timing_read("rotation")
+    ctx.timing(False)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    units = nd * ns * m
+    value = world * units / (ms * 1e-3) / 1e9
+
+    # ---- roofline of the dominant kernel (the H-pass of the filter)
+    s = 4
+    # algorithmic bytes of all H-pass launches in one step: filter degrees 2..m read
+    # Y_j, Y_{j-1} and write Y_{j+1} (3s); degree 1 and the Rayleigh-Ritz H U read one
+    # block and write one (2s); 10 Lanczos matvecs on one FP64 vector (2 x 8 B).
+    bytes_step = nd * ns * s * (3 * (m - 1) + 2 + 2) + 10 * 2 * 8 * nd
+    per_step_launches = hp_n / args.steps
+    hp_avg_ms = hp_ms / hp_n
+    achieved = bytes_step / (hp_ms / args.steps * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        Xp = torch.from_numpy(X_host).pin_memory()
+        Up = torch.empty_like(Xp).pin_memory()
+        eh = torch.empty(ns, dtype=torch.float64).pin_memory()
+        Xd = torch.empty_like(X)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.e2e_steps):
+            Xd.copy_(Xp, non_blocking=True)
+            step(Xd, Y)
+            Up.copy_(Y, non_blocking=True)
+            eh.copy_(eig, non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ems = f0.elapsed_time(f1) / args.e2e_steps
+        e2e = {"value": world * units / (ems * 1e-3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(X_host.nbytes),
+               "d2h_bytes_per_step": int(Y.numel() * 4 + ns * 8), "ms_per_step": ems}
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+        return 0
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        d = cpu_oracle_sample(cols=args.cpu_sample_cols, reps=1)
+        cpu = {"value": d["units"] / d["seconds"][0] / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"numpy FP64 oracle filter on {args.cpu_sample_cols} of 512 orbitals, "
+                         f"all {m} degrees ({d['seconds'][0]:.1f} s)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "path": "FP64 Lanczos k=10, FP32 filter, mixed Rayleigh-Ritz",
+                   "l2": "inputs larger than L2 (537 MB block)", "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "k_hpass", "launches_per_step": per_step_launches,
+                     "avg_launch_ms": hp_avg_ms},
+        "breakdown_ms_per_step": {"hpass": hp_ms / args.steps, "gather": ga_ms / args.steps,
+                                  "gram": gr_ms / args.steps, "chol_eig": ei_ms / args.steps,
+                                  "rotation": ro_ms / args.steps},
+        "filter_only": {"value": units / ((hp_ms + ga_ms) / args.steps * 1e-3) / 1e9, "unit": UNIT},
+        "clocks": ck, "e2e": e2e, "gpu_launches": int(launches), "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,164 @@
+/*
+ * sparc.h - C ABI of the GB300 CheFSI library (libsparc.so).
+ *
+ * The library computes the Chebyshev-filtered subspace iteration (CheFSI)
+ * step of real-space Kohn-Sham DFT as described in SPARC for extended systems
+ * (arXiv:1603.04339, Section 3.4 "Electron density calculation"):
+ *
+ *   H(k) = -1/2 nabla_h^2 + V_eff + V_nl                 (Eqn. EL, Eq. FD:Laplacian,
+ *                                                          Eq. NonlocalPS:FD)
+ *   U_f  = C_m((H - c)/e) U                              (Eq. ChebFilter)
+ *   H~ = U_f^H H U_f,  M~ = U_f^H U_f,  H~ y = lambda M~ y
+ *                                                        (Eq. SubspaceGeneralizedEigenproblem)
+ *   U    = U_f Y                                         (Eq. OrbitalTransformation)
+ *
+ * Conventions that hold for every entry point:
+ *   - Grid: n1 x n2 x n3 nodes, spacings h1,h2,h3 (bohr); node (i,j,k), 0-based,
+ *     sits at (-L1/2 + i h1, ...), L_s = n_s h_s; grid index g = i + n1 (j + n2 k).
+ *   - Orbitals: a column-major Nd x Ns matrix (Nd = n1 n2 n3) in DEVICE memory,
+ *     column n starts at X + n*ld elements, ld >= Nd.  Element type by
+ *     sparc_dtype; complex values are interleaved (re, im).
+ *   - Bloch-periodic boundary: psi(x + L_s e_s) = exp(i k_s L_s) psi(x).  A real
+ *     dtype (F64, F32) is only accepted at k = 0 (Gamma point).
+ *   - Energies in Hartree, lengths in bohr, k in bohr^-1 (Cartesian).
+ *   - Calls are asynchronous on `stream` (a cudaStream_t, NULL = legacy default
+ *     stream) unless stated otherwise.  Argument errors are returned at once;
+ *     errors found by kernels (non-positive-definite M~, bounded waits that
+ *     ran out) are latched in a device status word that sparc_sync() reads.
+ *   - The caller owns every buffer it passes.  The context owns its workspace,
+ *     which grows on demand and is reused across calls; calls on one context
+ *     must not overlap on different streams.
+ *   - Nothing throws or aborts across the ABI; every failure is a status code,
+ *     and sparc_last_error() gives a one-line reason.
+ */
+#ifndef SPARC_H
+#define SPARC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SPARC_OK = 0,
+  SPARC_ERR_INVALID_ARG = 1,   /* a size, pointer or bound is out of range          */
+  SPARC_ERR_OOM = 2,           /* device allocation of workspace failed             */
+  SPARC_ERR_CUDA = 3,          /* a CUDA runtime call failed (message has details)  */
+  SPARC_ERR_NOT_POSDEF = 4,    /* M~ is not numerically positive definite           */
+  SPARC_ERR_NO_CONVERGENCE = 5,/* the subspace eigensolver hit its sweep limit      */
+  SPARC_ERR_TIMEOUT = 6        /* a bounded device wait gave up                     */
+} sparc_status;
+
+typedef enum {
+  SPARC_F64 = 0,   /* double                          */
+  SPARC_F32 = 1,   /* float                           */
+  SPARC_C128 = 2,  /* complex double, (re, im) pairs  */
+  SPARC_C64 = 3    /* complex float,  (re, im) pairs  */
+} sparc_dtype;
+
+/* Rayleigh-Ritz precision modes. */
+typedef enum {
+  SPARC_RR_FP64 = 0,  /* Grams, eigensolve and rotation in FP64 (input must be F64/C128)   */
+  SPARC_RR_MIXED = 1  /* Grams and rotation from FP32 data with error-compensated products
+                         and FP32 accumulation, FP64 Cholesky + eigensolve (F32/C64 input)  */
+} sparc_rr_mode;
+
+/* Finite-difference grid at one Bloch wavevector (Section 3.1). */
+typedef struct {
+  int n[3];          /* nodes per axis, each >= 2*fd_radius + 1                          */
+  double h[3];       /* mesh spacing per axis (bohr), > 0                                 */
+  int fd_radius;     /* n_o of Eq. FD:Laplacian, 1..8 (paper: 6, twelfth order)           */
+  double k[3];       /* Bloch wavevector, Cartesian (bohr^-1)                             */
+} sparc_grid;
+
+/* Kleinman-Bylander projectors on cuboid boxes (Eq. NonlocalPS:FD, Section 3.4).
+ * Projector p has real values chi[chi_off[p] + a + nb0*(b + nb1*c)] at the
+ * unwrapped box node (box_lo[3p] + a, box_lo[3p+1] + b, box_lo[3p+2] + c);
+ * box_lo may be negative or >= n (the node maps to its periodic image, which
+ * carries the Bloch phase of the cell it lies in).  Each box_n[3p+s] <= n[s].
+ * All pointers are HOST pointers, read once by sparc_ham_create. */
+typedef struct {
+  int nproj;                 /* number of projectors (may be 0)          */
+  const int32_t* box_lo;     /* [3*nproj]                                 */
+  const int32_t* box_n;      /* [3*nproj]                                 */
+  const int64_t* chi_off;    /* [nproj]                                   */
+  const double* chi;         /* [chi_len] packed box values               */
+  int64_t chi_len;
+  const double* gamma;       /* [nproj] KB energies gamma_Jl (Ha)         */
+} sparc_nonlocal;
+
+typedef struct sparc_ctx sparc_ctx;   /* device, workspace, status word    */
+typedef struct sparc_ham sparc_ham;   /* H(k): grid, V_eff, projectors     */
+
+/* Create a context on CUDA device `device`.  *ctx is NULL on failure. */
+sparc_status sparc_create(sparc_ctx** ctx, int device);
+void sparc_destroy(sparc_ctx* ctx);
+/* One-line description of the last failure on this context ("" if none). */
+const char* sparc_last_error(const sparc_ctx* ctx);
+/* Synchronise `stream`, then read and clear the device status word. */
+sparc_status sparc_sync(sparc_ctx* ctx, void* stream);
+
+/* Build H(k) on the context's device: copies the grid, V_eff (host, Nd doubles)
+ * and the projector boxes; precomputes FD weights (Eq. weightsLap) and the
+ * projector-to-grid maps with their Bloch phases.  Synchronous. */
+sparc_status sparc_ham_create(sparc_ctx* ctx, const sparc_grid* grid, const double* veff_host,
+                              const sparc_nonlocal* nl, sparc_ham** H);
+/* Replace V_eff (Nd doubles).  `on_device` != 0: veff is a device pointer,
+ * copied asynchronously on `stream`; otherwise a host pointer (synchronous). */
+sparc_status sparc_ham_set_veff(sparc_ham* H, const double* veff, int on_device, void* stream);
+void sparc_ham_destroy(sparc_ham* H);
+
+/* Y = H X (Eqn. EL discretised by Eq. FD:Laplacian and Eq. NonlocalPS:FD).
+ * X, Y: device, column-major Nd x ns, leading dimension ld; must not overlap. */
+sparc_status sparc_apply_H(sparc_ham* H, sparc_dtype dtype, const void* X, void* Y, int ns,
+                           int64_t ld, void* stream);
+
+/* Scaled Chebyshev filter of degree m (Eq. ChebFilter with e = (b-a)/2, c = (b+a)/2):
+ *   Y = C_m((H - c)/e) X / C_m((a0 - c)/e),
+ * computed by the three-term recurrence.  a = filter cutoff lambda_c,
+ * b = upper bound of the spectrum, a0 = lower estimate; needs a0 < a < b, m >= 1.
+ * X, Y: device, column-major Nd x ns (ld); X is not modified; may not overlap. */
+sparc_status sparc_cheb_filter(sparc_ham* H, sparc_dtype dtype, int m, double a, double b,
+                               double a0, const void* X, void* Y, int ns, int64_t ld,
+                               void* stream);
+
+/* Extremal-eigenvalue estimates by `ksteps` Lanczos steps with full
+ * reorthogonalisation, in FP64 (Section 4: filter bounds by the Lanczos method).
+ * v0: device start vector, Nd elements of F64 (k = 0) or C128 (k != 0); it is
+ * normalised internally and not modified.  On return (the call synchronises
+ * `stream`) *a0 = smallest Ritz value, *b = largest Ritz value + |beta_k|.
+ * 2 <= ksteps <= 64. */
+sparc_status sparc_lanczos_bounds(sparc_ham* H, int ksteps, const void* v0, double* a0, double* b,
+                                  void* stream);
+
+/* Rayleigh-Ritz step (Eqs. SubspaceGeneralizedEigenproblem, OrbitalTransformation):
+ * H~ = U^H H U, M~ = U^H U, Cholesky M~ = L L^H, C = L^-1 H~ L^-H, C q = lambda q,
+ * U <- U L^-H Q.  U: device, column-major Nd x ns (ld), filtered on entry,
+ * rotated (orthonormal columns, U^H U = I) on exit.  eig: device, ns doubles,
+ * ascending Ritz values.  mode: sparc_rr_mode (FP64 for F64/C128 data, MIXED for
+ * F32/C64 data).  2 <= ns <= 1024.  Non-positive-definite M~ or a Jacobi sweep
+ * limit are reported by the return code (the call synchronises `stream`). */
+sparc_status sparc_rayleigh_ritz(sparc_ham* H, sparc_dtype dtype, void* U, int ns, int64_t ld,
+                                 double* eig, int mode, void* stream);
+
+/* Kernel timing (instrumentation, not part of the method).  While enabled, every
+ * launch of the kernels below is bracketed by CUDA events recorded on the
+ * stream it is launched on.  sparc_timing_read() synchronises those events and
+ * returns the summed device time (ms) and the launch count since the last
+ * enable; it is valid after the launches have completed.
+ *   which = 0: the H-apply / Chebyshev-recurrence pass (k_hpass)
+ *   which = 1: the nonlocal projection (k_nl_gather)
+ *   which = 2: the Gram products of Rayleigh-Ritz
+ *   which = 3: the Cholesky + subspace eigensolve of Rayleigh-Ritz
+ *   which = 4: the subspace rotation of Rayleigh-Ritz */
+sparc_status sparc_timing_enable(sparc_ctx* ctx, int on);
+sparc_status sparc_timing_read(sparc_ctx* ctx, int which, double* ms_total, int64_t* launches);
+/* Number of kernels this context has launched since it was created. */
+sparc_status sparc_launch_count(const sparc_ctx* ctx, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPARC_H */

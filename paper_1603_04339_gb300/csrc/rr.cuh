@@ -1,0 +1,25 @@
+// Internal interfaces shared by the API, Lanczos and Rayleigh-Ritz translation units.
+#pragma once
+
+#include "ham.cuh"
+
+namespace sparc {
+
+struct BlockWs {
+  void* b0;   // interleaved block buffer
+  void* b1;   // interleaved block buffer
+  void* gc;   // projector coefficients [nproj][nblk][32]
+};
+
+sparc_status ensure_vals(sparc_ham* H, sparc_dtype dt);
+sparc_status check_block_args(sparc_ham* H, sparc_dtype dt, const void* X, const void* Y, int ns,
+                              int64_t ld);
+// Carve the block workspace plus `extra` bytes (returned through *tail, 256-aligned).
+sparc_status block_ws(sparc_ham* H, sparc_dtype dt, int ns, size_t extra, BlockWs* w, char** tail);
+template <class T>
+sparc_status apply_block(sparc_ham* H, const T* X, T* Y, int ns, long long ld, cudaStream_t st,
+                         const BlockWs& w);
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace sparc

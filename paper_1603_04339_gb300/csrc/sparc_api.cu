@@ -1,0 +1,540 @@
+// C ABI of libsparc: contexts, H(k) construction, H-apply and the Chebyshev filter.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <new>
+
+#include "ham.cuh"
+#include "rr.cuh"
+
+namespace sparc {
+
+sparc_status fail(sparc_ctx* ctx, sparc_status st, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+  return st;
+}
+
+sparc_status cuda_fail(sparc_ctx* ctx, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(ctx, e == cudaErrorMemoryAllocation ? SPARC_ERR_OOM : SPARC_ERR_CUDA, m);
+}
+
+cudaEvent_t timing_begin(sparc_ctx* ctx, cudaStream_t st) {
+  if (!ctx->timing) return nullptr;
+  cudaEvent_t e = nullptr;
+  if (!ctx->ev_pool.empty()) {
+    e = ctx->ev_pool.back();
+    ctx->ev_pool.pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  cudaEventRecord(e, st);
+  return e;
+}
+
+void timing_end(sparc_ctx* ctx, int which, cudaEvent_t begin, cudaStream_t st) {
+  if (!ctx->timing || begin == nullptr) return;
+  cudaEvent_t e = nullptr;
+  if (!ctx->ev_pool.empty()) {
+    e = ctx->ev_pool.back();
+    ctx->ev_pool.pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->ev_pool.push_back(begin);
+    return;
+  }
+  cudaEventRecord(e, st);
+  ctx->ev[which].emplace_back(begin, e);
+}
+
+static void timing_reset(sparc_ctx* ctx) {
+  for (int w = 0; w < sparc_ctx::NTIMED; ++w) {
+    for (auto& pr : ctx->ev[w]) {
+      ctx->ev_pool.push_back(pr.first);
+      ctx->ev_pool.push_back(pr.second);
+    }
+    ctx->ev[w].clear();
+  }
+}
+
+bool ensure_ws(sparc_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->ws_bytes) return true;
+  if (ctx->ws) {
+    cudaDeviceSynchronize();
+    cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+  }
+  size_t want = std::max(bytes, (size_t)1 << 20);
+  if (cudaMalloc(&ctx->ws, want) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->ws = nullptr;
+    return false;
+  }
+  ctx->ws_bytes = want;
+  return true;
+}
+
+namespace {
+
+__global__ void k_d2f(const double* a, float* b, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+// Central FD weights of the second derivative, Eq. weightsLap.
+void fd_weights(int no, double h, double* w) {
+  double s = 0.0;
+  for (int q = 1; q <= no; ++q) s += 1.0 / ((double)q * q);
+  w[0] = -s / (h * h);
+  double fo = 1.0;
+  for (int q = 2; q <= no; ++q) fo *= q;
+  for (int p = 1; p <= no; ++p) {
+    double fm = 1.0, fp = 1.0;
+    for (int q = 2; q <= no - p; ++q) fm *= q;
+    for (int q = 2; q <= no + p; ++q) fp *= q;
+    double sign = (p % 2 == 1) ? 1.0 : -1.0;
+    w[p] = 2.0 * sign * fo * fo / (h * h * (double)p * p * fm * fp);
+  }
+}
+
+long long floordiv(long long a, long long b) {
+  long long q = a / b;
+  if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+  return q;
+}
+
+template <class T>
+T make_val(double re, double im);
+template <> double make_val<double>(double re, double) { return re; }
+template <> float make_val<float>(double re, double) { return (float)re; }
+template <> cf64 make_val<cf64>(double re, double im) { return {re, im}; }
+template <> cf32 make_val<cf32>(double re, double im) { return {(float)re, (float)im}; }
+
+template <class T>
+sparc_status upload_vals(sparc_ham* H, const std::vector<double>& re, const std::vector<double>& im,
+                         void** dst) {
+  std::vector<T> v(re.size());
+  for (size_t e = 0; e < re.size(); ++e) v[e] = make_val<T>(re[e], im.empty() ? 0.0 : im[e]);
+  SPARC_CUDA(H->ctx, cudaMalloc(dst, std::max<size_t>(1, v.size()) * sizeof(T)));
+  SPARC_CUDA(H->ctx, cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return SPARC_OK;
+}
+
+}  // namespace
+
+// Make the chi~ values of H available in the element type `dt` (first use only).
+sparc_status ensure_vals(sparc_ham* H, sparc_dtype dt) {
+  if (H->nproj == 0 || H->d_p_val[dt] != nullptr) return SPARC_OK;
+  sparc_status st = SPARC_OK;
+  switch (dt) {
+    case SPARC_F64:
+      st = upload_vals<double>(H, H->h_p_re, H->h_p_im, &H->d_p_val[dt]);
+      if (st == SPARC_OK) st = upload_vals<double>(H, H->h_pt_re, H->h_pt_im, &H->d_pt_val[dt]);
+      break;
+    case SPARC_F32:
+      st = upload_vals<float>(H, H->h_p_re, H->h_p_im, &H->d_p_val[dt]);
+      if (st == SPARC_OK) st = upload_vals<float>(H, H->h_pt_re, H->h_pt_im, &H->d_pt_val[dt]);
+      break;
+    case SPARC_C128:
+      st = upload_vals<cf64>(H, H->h_p_re, H->h_p_im, &H->d_p_val[dt]);
+      if (st == SPARC_OK) st = upload_vals<cf64>(H, H->h_pt_re, H->h_pt_im, &H->d_pt_val[dt]);
+      break;
+    case SPARC_C64:
+      st = upload_vals<cf32>(H, H->h_p_re, H->h_p_im, &H->d_p_val[dt]);
+      if (st == SPARC_OK) st = upload_vals<cf32>(H, H->h_pt_re, H->h_pt_im, &H->d_pt_val[dt]);
+      break;
+  }
+  return st;
+}
+
+sparc_status check_block_args(sparc_ham* H, sparc_dtype dt, const void* X, const void* Y, int ns,
+                              int64_t ld) {
+  sparc_ctx* ctx = H->ctx;
+  if ((int)dt < 0 || (int)dt > 3) return fail(ctx, SPARC_ERR_INVALID_ARG, "unknown dtype");
+  if (H->gd.cplx && (dt == SPARC_F64 || dt == SPARC_F32))
+    return fail(ctx, SPARC_ERR_INVALID_ARG, "real dtype needs k = 0 (Gamma point)");
+  if (ns < 1) return fail(ctx, SPARC_ERR_INVALID_ARG, "ns must be >= 1");
+  if (ld < H->gd.nd) return fail(ctx, SPARC_ERR_INVALID_ARG, "ld must be >= Nd");
+  if (X == nullptr || Y == nullptr) return fail(ctx, SPARC_ERR_INVALID_ARG, "null X or Y");
+  const size_t es = dtype_size(dt);
+  const char* x0 = (const char*)X;
+  const char* y0 = (const char*)Y;
+  const size_t span = ((size_t)(ns - 1) * (size_t)ld + (size_t)H->gd.nd) * es;
+  if (x0 < y0 + span && y0 < x0 + span) return fail(ctx, SPARC_ERR_INVALID_ARG, "X and Y overlap");
+  return ensure_vals(H, dt);
+}
+
+sparc_status block_ws(sparc_ham* H, sparc_dtype dt, int ns, size_t extra, BlockWs* w, char** tail) {
+  const size_t es = dtype_size(dt);
+  const int nblk = ceil_div(ns, NB);
+  const size_t bb = align256((size_t)nblk * H->gd.nd * NB * es);
+  const size_t gb = align256((size_t)std::max(1, H->nproj) * nblk * NB * es);
+  if (!ensure_ws(H->ctx, 2 * bb + gb + extra))
+    return fail(H->ctx, SPARC_ERR_OOM, "workspace allocation failed");
+  char* p = (char*)H->ctx->ws;
+  w->b0 = p;
+  w->b1 = p + bb;
+  w->gc = p + 2 * bb;
+  if (tail) *tail = p + 2 * bb + gb;
+  return SPARC_OK;
+}
+
+template <class T>
+sparc_status apply_block(sparc_ham* H, const T* X, T* Y, int ns, long long ld, cudaStream_t st,
+                         const BlockWs& w) {
+  const int nblk = ceil_div(ns, NB);
+  T* b0 = (T*)w.b0;
+  T* b1 = (T*)w.b1;
+  T* gc = (T*)w.gc;
+  SPARC_CUDA(H->ctx, launch_to_blocks<T>(X, ld, ns, b0, H->gd.nd, nblk, st));
+  ++H->ctx->launches;
+  SPARC_CUDA(H->ctx, launch_nl_gather<T>(H, b0, NB, nblk, gc, st));
+  SPARC_CUDA(H->ctx, launch_hpass<T>(H, b0, nullptr, b1, gc, NB, nblk, 1.0, 0.0, 0.0, st));
+  SPARC_CUDA(H->ctx, launch_from_blocks<T>(b1, H->gd.nd, nblk, Y, ld, ns, st));
+  ++H->ctx->launches;
+  return SPARC_OK;
+}
+
+// Scaled Chebyshev filter (Eq. ChebFilter), three-term recurrence in the
+// normalised form: sigma_1 = e/(a0-c), sigma_{j+1} = 1/(2/sigma_1 - sigma_j),
+// Y_1 = (sigma_1/e)(H-c)X, Y_{j+1} = (2 sigma_{j+1}/e)(H-c)Y_j - sigma_j sigma_{j+1} Y_{j-1}.
+template <class T>
+sparc_status filter_block(sparc_ham* H, int m, double a, double b, double a0, const T* X, T* Y,
+                          int ns, long long ld, cudaStream_t st, const BlockWs& w) {
+  const int nblk = ceil_div(ns, NB);
+  T* prev = (T*)w.b0;
+  T* cur = (T*)w.b1;
+  T* gc = (T*)w.gc;
+  const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+  const double sigma1 = e / (a0 - c);
+  double sigma = sigma1;
+  SPARC_CUDA(H->ctx, launch_to_blocks<T>(X, ld, ns, prev, H->gd.nd, nblk, st));
+  ++H->ctx->launches;
+  SPARC_CUDA(H->ctx, launch_nl_gather<T>(H, prev, NB, nblk, gc, st));
+  SPARC_CUDA(H->ctx, launch_hpass<T>(H, prev, nullptr, cur, gc, NB, nblk, sigma1 / e, c, 0.0, st));
+  for (int j = 1; j < m; ++j) {
+    const double sigma_new = 1.0 / (2.0 / sigma1 - sigma);
+    SPARC_CUDA(H->ctx, launch_nl_gather<T>(H, cur, NB, nblk, gc, st));
+    SPARC_CUDA(H->ctx, launch_hpass<T>(H, cur, prev, prev, gc, NB, nblk, 2.0 * sigma_new / e, c,
+                                       -sigma * sigma_new, st));
+    std::swap(cur, prev);
+    sigma = sigma_new;
+  }
+  SPARC_CUDA(H->ctx, launch_from_blocks<T>(cur, H->gd.nd, nblk, Y, ld, ns, st));
+  ++H->ctx->launches;
+  return SPARC_OK;
+}
+
+template sparc_status apply_block<double>(sparc_ham*, const double*, double*, int, long long,
+                                          cudaStream_t, const BlockWs&);
+template sparc_status apply_block<float>(sparc_ham*, const float*, float*, int, long long,
+                                         cudaStream_t, const BlockWs&);
+template sparc_status apply_block<cf64>(sparc_ham*, const cf64*, cf64*, int, long long,
+                                        cudaStream_t, const BlockWs&);
+template sparc_status apply_block<cf32>(sparc_ham*, const cf32*, cf32*, int, long long,
+                                        cudaStream_t, const BlockWs&);
+
+}  // namespace sparc
+
+using namespace sparc;
+
+extern "C" {
+
+sparc_status sparc_create(sparc_ctx** out, int device) {
+  if (!out) return SPARC_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return SPARC_ERR_INVALID_ARG;
+  }
+  sparc_ctx* ctx = new (std::nothrow) sparc_ctx();
+  if (!ctx) return SPARC_ERR_OOM;
+  ctx->device = device;
+  if (cudaSetDevice(device) != cudaSuccess || cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess ||
+      cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return SPARC_ERR_CUDA;
+  }
+  *out = ctx;
+  return SPARC_OK;
+}
+
+sparc_status sparc_timing_enable(sparc_ctx* ctx, int on) {
+  if (!ctx) return SPARC_ERR_INVALID_ARG;
+  SPARC_CUDA(ctx, cudaSetDevice(ctx->device));
+  SPARC_CUDA(ctx, cudaDeviceSynchronize());
+  timing_reset(ctx);
+  ctx->timing = (on != 0);
+  return SPARC_OK;
+}
+
+sparc_status sparc_launch_count(const sparc_ctx* ctx, int64_t* launches) {
+  if (!ctx || !launches) return SPARC_ERR_INVALID_ARG;
+  *launches = (int64_t)ctx->launches;
+  return SPARC_OK;
+}
+
+sparc_status sparc_timing_read(sparc_ctx* ctx, int which, double* ms_total, int64_t* launches) {
+  if (!ctx || which < 0 || which >= sparc_ctx::NTIMED || !ms_total || !launches)
+    return fail(ctx, SPARC_ERR_INVALID_ARG, "bad timing query");
+  double tot = 0.0;
+  for (auto& pr : ctx->ev[which]) {
+    SPARC_CUDA(ctx, cudaEventSynchronize(pr.second));
+    float ms = 0.f;
+    SPARC_CUDA(ctx, cudaEventElapsedTime(&ms, pr.first, pr.second));
+    tot += ms;
+  }
+  *ms_total = tot;
+  *launches = (int64_t)ctx->ev[which].size();
+  return SPARC_OK;
+}
+
+void sparc_destroy(sparc_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  timing_reset(ctx);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  delete ctx;
+}
+
+const char* sparc_last_error(const sparc_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+sparc_status sparc_sync(sparc_ctx* ctx, void* stream) {
+  if (!ctx) return SPARC_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  SPARC_CUDA(ctx, cudaStreamSynchronize(st));
+  int word = 0;
+  SPARC_CUDA(ctx, cudaMemcpy(&word, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  SPARC_CUDA(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)));
+  if (word & STATUS_TIMEOUT) return fail(ctx, SPARC_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (word & STATUS_NOT_POSDEF) return fail(ctx, SPARC_ERR_NOT_POSDEF, "M~ not positive definite");
+  if (word & STATUS_NO_CONVERGENCE)
+    return fail(ctx, SPARC_ERR_NO_CONVERGENCE, "subspace eigensolver did not converge");
+  return SPARC_OK;
+}
+
+sparc_status sparc_ham_create(sparc_ctx* ctx, const sparc_grid* grid, const double* veff,
+                              const sparc_nonlocal* nl, sparc_ham** out) {
+  if (!ctx || !grid || !veff || !out) return fail(ctx, SPARC_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  const sparc_grid& gr = *grid;
+  if (gr.fd_radius < 1 || gr.fd_radius > MAX_FD)
+    return fail(ctx, SPARC_ERR_INVALID_ARG, "fd_radius must be in 1..8");
+  for (int s = 0; s < 3; ++s) {
+    if (gr.n[s] < 2 * gr.fd_radius + 1)
+      return fail(ctx, SPARC_ERR_INVALID_ARG, "each n_s must be >= 2*fd_radius+1");
+    if (!(gr.h[s] > 0.0)) return fail(ctx, SPARC_ERR_INVALID_ARG, "h_s must be > 0");
+    if (!isfinite(gr.k[s])) return fail(ctx, SPARC_ERR_INVALID_ARG, "k must be finite");
+  }
+  const long long nd = (long long)gr.n[0] * gr.n[1] * gr.n[2];
+  if (nd > (1LL << 31) - 1) return fail(ctx, SPARC_ERR_INVALID_ARG, "grid too large");
+  SPARC_CUDA(ctx, cudaSetDevice(ctx->device));
+  sparc_ham* H = new (std::nothrow) sparc_ham();
+  if (!H) return fail(ctx, SPARC_ERR_OOM, "host allocation failed");
+  H->ctx = ctx;
+  H->grid = gr;
+  GridDev& gd = H->gd;
+  gd.n1 = gr.n[0];
+  gd.n2 = gr.n[1];
+  gd.n3 = gr.n[2];
+  gd.no = gr.fd_radius;
+  gd.nd = nd;
+  gd.cplx = (gr.k[0] != 0.0 || gr.k[1] != 0.0 || gr.k[2] != 0.0) ? 1 : 0;
+  for (int s = 0; s < 3; ++s) {
+    double w[MAX_FD + 1];
+    fd_weights(gr.fd_radius, gr.h[s], w);
+    for (int p = 0; p <= MAX_FD; ++p) gd.coef[s][p] = (p <= gr.fd_radius) ? -0.5 * w[p] : 0.0;
+    const double kL = gr.k[s] * gr.n[s] * gr.h[s];
+    gd.ph_re[s] = cos(kL);
+    gd.ph_im[s] = sin(kL);
+  }
+  auto bail = [&](sparc_status st) {
+    sparc_ham_destroy(H);
+    return st;
+  };
+  if (cudaMalloc(&H->d_veff, nd * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&H->d_veff32, nd * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(ctx, SPARC_ERR_OOM, "V_eff allocation failed"));
+  }
+  sparc_status st = sparc_ham_set_veff(H, veff, 0, nullptr);
+  if (st != SPARC_OK) return bail(st);
+
+  // ---- projectors: chi~_p[g] = exp(-i k.(t L)) chi_p[q], g = q mod n, t = floor(q/n)
+  const int np = nl ? nl->nproj : 0;
+  if (np < 0) return bail(fail(ctx, SPARC_ERR_INVALID_ARG, "nproj < 0"));
+  H->nproj = np;
+  if (np > 0) {
+    if (!nl->box_lo || !nl->box_n || !nl->chi_off || !nl->chi || !nl->gamma)
+      return bail(fail(ctx, SPARC_ERR_INVALID_ARG, "null projector array"));
+    std::vector<long long> p_off(np + 1, 0);
+    for (int p = 0; p < np; ++p) {
+      long long sz = 1;
+      for (int s = 0; s < 3; ++s) {
+        const int nb = nl->box_n[3 * p + s];
+        if (nb < 1 || nb > gr.n[s])
+          return bail(fail(ctx, SPARC_ERR_INVALID_ARG, "projector box size must be in 1..n_s"));
+        sz *= nb;
+      }
+      if (nl->chi_off[p] < 0 || nl->chi_off[p] + sz > nl->chi_len)
+        return bail(fail(ctx, SPARC_ERR_INVALID_ARG, "projector box outside chi"));
+      p_off[p + 1] = p_off[p] + sz;
+    }
+    const long long ne = p_off[np];
+    if (ne > (1LL << 31) - 1) return bail(fail(ctx, SPARC_ERR_INVALID_ARG, "too many box nodes"));
+    H->n_ent = ne;
+    std::vector<int> pg(ne);
+    H->h_p_re.resize(ne);
+    if (gd.cplx) H->h_p_im.resize(ne);
+    const double L[3] = {gr.n[0] * gr.h[0], gr.n[1] * gr.h[1], gr.n[2] * gr.h[2]};
+    for (int p = 0; p < np; ++p) {
+      const int* lo = nl->box_lo + 3 * p;
+      const int* nb = nl->box_n + 3 * p;
+      long long e = p_off[p];
+      for (int c = 0; c < nb[2]; ++c)
+        for (int b = 0; b < nb[1]; ++b)
+          for (int a = 0; a < nb[0]; ++a, ++e) {
+            const long long q[3] = {(long long)lo[0] + a, (long long)lo[1] + b, (long long)lo[2] + c};
+            long long gidx[3];
+            double kt = 0.0;
+            for (int s = 0; s < 3; ++s) {
+              const long long t = floordiv(q[s], gr.n[s]);
+              gidx[s] = q[s] - t * gr.n[s];
+              kt += gr.k[s] * L[s] * (double)t;
+            }
+            pg[e] = (int)(gidx[0] + gr.n[0] * (gidx[1] + (long long)gr.n[1] * gidx[2]));
+            const double v = nl->chi[nl->chi_off[p] + a + (long long)nb[0] * (b + (long long)nb[1] * c)];
+            if (gd.cplx) {
+              H->h_p_re[e] = v * cos(kt);
+              H->h_p_im[e] = -v * sin(kt);
+            } else {
+              H->h_p_re[e] = v;
+            }
+          }
+    }
+    // node-major copy for the scatter (stable in p)
+    std::vector<int> ptr(nd + 1, 0), pp(ne);
+    H->h_pt_re.resize(ne);
+    if (gd.cplx) H->h_pt_im.resize(ne);
+    for (long long e = 0; e < ne; ++e) ptr[pg[e] + 1]++;
+    for (long long g = 0; g < nd; ++g) ptr[g + 1] += ptr[g];
+    std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+    for (int p = 0; p < np; ++p)
+      for (long long e = p_off[p]; e < p_off[p + 1]; ++e) {
+        const int slot = fill[pg[e]]++;
+        pp[slot] = p;
+        H->h_pt_re[slot] = H->h_p_re[e];
+        if (gd.cplx) H->h_pt_im[slot] = H->h_p_im[e];
+      }
+    std::vector<float> g32(np);
+    for (int p = 0; p < np; ++p) g32[p] = (float)nl->gamma[p];
+    if (cudaMalloc(&H->d_gamma, np * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&H->d_gamma32, np * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&H->d_p_off, (np + 1) * sizeof(long long)) != cudaSuccess ||
+        cudaMalloc(&H->d_p_g, ne * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&H->d_pt_ptr, (nd + 1) * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&H->d_pt_p, ne * sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      return bail(fail(ctx, SPARC_ERR_OOM, "projector allocation failed"));
+    }
+    if (cudaMemcpy(H->d_gamma, nl->gamma, np * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(H->d_gamma32, g32.data(), np * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(H->d_p_off, p_off.data(), (np + 1) * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(H->d_p_g, pg.data(), ne * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(H->d_pt_ptr, ptr.data(), (nd + 1) * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(H->d_pt_p, pp.data(), ne * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
+      return bail(cuda_fail(ctx, cudaGetLastError(), "projector upload"));
+    }
+  }
+  *out = H;
+  return SPARC_OK;
+}
+
+sparc_status sparc_ham_set_veff(sparc_ham* H, const double* veff, int on_device, void* stream) {
+  if (!H || !veff) return SPARC_ERR_INVALID_ARG;
+  sparc_ctx* ctx = H->ctx;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long nd = H->gd.nd;
+  if (on_device) {
+    SPARC_CUDA(ctx, cudaMemcpyAsync(H->d_veff, veff, nd * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  } else {
+    SPARC_CUDA(ctx, cudaMemcpy(H->d_veff, veff, nd * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  k_d2f<<<ceil_div(nd, 256), 256, 0, st>>>(H->d_veff, H->d_veff32, nd);
+  ++ctx->launches;
+  SPARC_LAUNCH(ctx, "veff conversion");
+  if (!on_device) SPARC_CUDA(ctx, cudaStreamSynchronize(st));
+  return SPARC_OK;
+}
+
+void sparc_ham_destroy(sparc_ham* H) {
+  if (!H) return;
+  cudaSetDevice(H->ctx->device);
+  cudaDeviceSynchronize();
+  void* ptrs[] = {H->d_veff, H->d_veff32, H->d_gamma, H->d_gamma32, H->d_p_off, H->d_p_g,
+                  H->d_pt_ptr, H->d_pt_p};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (int i = 0; i < 4; ++i) {
+    if (H->d_p_val[i]) cudaFree(H->d_p_val[i]);
+    if (H->d_pt_val[i]) cudaFree(H->d_pt_val[i]);
+  }
+  delete H;
+}
+
+sparc_status sparc_apply_H(sparc_ham* H, sparc_dtype dtype, const void* X, void* Y, int ns,
+                           int64_t ld, void* stream) {
+  if (!H) return SPARC_ERR_INVALID_ARG;
+  sparc_status s = check_block_args(H, dtype, X, Y, ns, ld);
+  if (s != SPARC_OK) return s;
+  SPARC_CUDA(H->ctx, cudaSetDevice(H->ctx->device));
+  BlockWs w;
+  s = block_ws(H, dtype, ns, 0, &w, nullptr);
+  if (s != SPARC_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (dtype) {
+    case SPARC_F64: return apply_block<double>(H, (const double*)X, (double*)Y, ns, ld, st, w);
+    case SPARC_F32: return apply_block<float>(H, (const float*)X, (float*)Y, ns, ld, st, w);
+    case SPARC_C128: return apply_block<cf64>(H, (const cf64*)X, (cf64*)Y, ns, ld, st, w);
+    case SPARC_C64: return apply_block<cf32>(H, (const cf32*)X, (cf32*)Y, ns, ld, st, w);
+  }
+  return SPARC_ERR_INVALID_ARG;
+}
+
+sparc_status sparc_cheb_filter(sparc_ham* H, sparc_dtype dtype, int m, double a, double b,
+                               double a0, const void* X, void* Y, int ns, int64_t ld,
+                               void* stream) {
+  if (!H) return SPARC_ERR_INVALID_ARG;
+  if (m < 1) return fail(H->ctx, SPARC_ERR_INVALID_ARG, "m must be >= 1");
+  if (!(a0 < a && a < b) || !isfinite(a0) || !isfinite(b))
+    return fail(H->ctx, SPARC_ERR_INVALID_ARG, "filter bounds must satisfy a0 < a < b");
+  sparc_status s = check_block_args(H, dtype, X, Y, ns, ld);
+  if (s != SPARC_OK) return s;
+  SPARC_CUDA(H->ctx, cudaSetDevice(H->ctx->device));
+  BlockWs w;
+  s = block_ws(H, dtype, ns, 0, &w, nullptr);
+  if (s != SPARC_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (dtype) {
+    case SPARC_F64:
+      return filter_block<double>(H, m, a, b, a0, (const double*)X, (double*)Y, ns, ld, st, w);
+    case SPARC_F32:
+      return filter_block<float>(H, m, a, b, a0, (const float*)X, (float*)Y, ns, ld, st, w);
+    case SPARC_C128:
+      return filter_block<cf64>(H, m, a, b, a0, (const cf64*)X, (cf64*)Y, ns, ld, st, w);
+    case SPARC_C64:
+      return filter_block<cf32>(H, m, a, b, a0, (const cf32*)X, (cf32*)Y, ns, ld, st, w);
+  }
+  return SPARC_ERR_INVALID_ARG;
+}
+
+}  // extern "C"

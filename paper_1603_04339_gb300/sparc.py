@@ -1,0 +1,264 @@
+"""Thin ctypes binding of libsparc.so (include/sparc.h).
+
+Argument marshalling only: every step of the CheFSI path runs in the CUDA
+library.  Device buffers are passed as torch tensors (or raw device pointers),
+streams as torch.cuda.Stream (or raw handles).  Loading fails loudly when the
+library has not been built; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_int32, c_int64, c_void_p
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libsparc.so")
+
+F64, F32, C128, C64 = 0, 1, 2, 3
+RR_FP64, RR_MIXED = 0, 1
+STATUS = {0: "SPARC_OK", 1: "SPARC_ERR_INVALID_ARG", 2: "SPARC_ERR_OOM", 3: "SPARC_ERR_CUDA",
+          4: "SPARC_ERR_NOT_POSDEF", 5: "SPARC_ERR_NO_CONVERGENCE", 6: "SPARC_ERR_TIMEOUT"}
+
+EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_sync", "sparc_ham_create",
+           "sparc_ham_set_veff", "sparc_ham_destroy", "sparc_apply_H", "sparc_cheb_filter",
+           "sparc_lanczos_bounds", "sparc_rayleigh_ritz", "sparc_timing_enable", "sparc_timing_read",
+           "sparc_launch_count"]
+TIMED = {"hpass": 0, "gather": 1, "gram": 2, "eig": 3, "rotation": 4}
+
+
+class SparcGrid(ctypes.Structure):
+    _fields_ = [("n", c_int * 3), ("h", c_double * 3), ("fd_radius", c_int), ("k", c_double * 3)]
+
+
+class SparcNonlocal(ctypes.Structure):
+    _fields_ = [("nproj", c_int), ("box_lo", POINTER(c_int32)), ("box_n", POINTER(c_int32)),
+                ("chi_off", POINTER(c_int64)), ("chi", POINTER(c_double)), ("chi_len", c_int64),
+                ("gamma", POINTER(c_double))]
+
+
+class SparcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libsparc.so and declare its signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsparc.so not found at {path}; build it with "
+                           "paper_1603_04339_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    L.sparc_create.argtypes = [POINTER(c_void_p), c_int]
+    L.sparc_destroy.argtypes = [c_void_p]
+    L.sparc_destroy.restype = None
+    L.sparc_last_error.argtypes = [c_void_p]
+    L.sparc_last_error.restype = ctypes.c_char_p
+    L.sparc_sync.argtypes = [c_void_p, c_void_p]
+    L.sparc_ham_create.argtypes = [c_void_p, POINTER(SparcGrid), POINTER(c_double),
+                                   POINTER(SparcNonlocal), POINTER(c_void_p)]
+    L.sparc_ham_set_veff.argtypes = [c_void_p, c_void_p, c_int, c_void_p]
+    L.sparc_ham_destroy.argtypes = [c_void_p]
+    L.sparc_ham_destroy.restype = None
+    L.sparc_apply_H.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_int, c_int64, c_void_p]
+    L.sparc_cheb_filter.argtypes = [c_void_p, c_int, c_int, c_double, c_double, c_double, c_void_p,
+                                    c_void_p, c_int, c_int64, c_void_p]
+    L.sparc_lanczos_bounds.argtypes = [c_void_p, c_int, c_void_p, POINTER(c_double),
+                                       POINTER(c_double), c_void_p]
+    L.sparc_rayleigh_ritz.argtypes = [c_void_p, c_int, c_void_p, c_int, c_int64, c_void_p, c_int,
+                                      c_void_p]
+    L.sparc_timing_enable.argtypes = [c_void_p, c_int]
+    L.sparc_launch_count.argtypes = [c_void_p, POINTER(c_int64)]
+    L.sparc_launch_count.restype = c_int
+    L.sparc_timing_read.argtypes = [c_void_p, c_int, POINTER(c_double), POINTER(c_int64)]
+    for name in ("sparc_timing_enable", "sparc_timing_read", "sparc_create", "sparc_sync", "sparc_ham_create", "sparc_ham_set_veff",
+                 "sparc_apply_H", "sparc_cheb_filter", "sparc_lanczos_bounds", "sparc_rayleigh_ritz"):
+        getattr(L, name).restype = c_int
+    _lib = L
+    return L
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def dtype_code(t) -> int:
+    import torch
+    return {torch.float64: F64, torch.float32: F32, torch.complex128: C128,
+            torch.complex64: C64}[t.dtype]
+
+
+class Context:
+    """A libsparc context on one CUDA device (workspace + device status word)."""
+
+    def __init__(self, device: int = 0):
+        L = load()
+        h = c_void_p()
+        rc = L.sparc_create(ctypes.byref(h), int(device))
+        if rc != 0:
+            raise SparcError(rc, "sparc_create failed")
+        self.handle = h
+        self.device = device
+
+    def error(self) -> str:
+        return load().sparc_last_error(self.handle).decode()
+
+    def check(self, rc):
+        if rc != 0:
+            raise SparcError(rc, self.error())
+
+    def sync(self, stream=None):
+        self.check(load().sparc_sync(self.handle, _stream(stream)))
+
+    def timing(self, on: bool):
+        """Bracket the timed kernel classes with CUDA events (sparc_timing_enable)."""
+        self.check(load().sparc_timing_enable(self.handle, 1 if on else 0))
+
+    def timing_read(self, which: str):
+        """(total ms, launches) of a timed kernel class since timing was enabled."""
+        ms, n = c_double(), c_int64()
+        self.check(load().sparc_timing_read(self.handle, TIMED[which], ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def launches(self) -> int:
+        """Kernels launched by this context so far (sparc_launch_count)."""
+        n = c_int64()
+        self.check(load().sparc_launch_count(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def close(self):
+        if self.handle:
+            load().sparc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Hamiltonian:
+    """H(k) on the device: grid, V_eff and projector boxes (sparc_ham_create)."""
+
+    def __init__(self, ctx: Context, n, h, fd_radius, k, veff, proj=None):
+        L = load()
+        self.ctx = ctx
+        g = SparcGrid()
+        for s in range(3):
+            g.n[s] = int(n[s])
+            g.h[s] = float(h[s])
+            g.k[s] = float(k[s])
+        g.fd_radius = int(fd_radius)
+        self.grid = g
+        self.nd = int(n[0]) * int(n[1]) * int(n[2])
+        self.cplx = any(float(v) != 0.0 for v in k)
+        self._veff = np.ascontiguousarray(veff, dtype=np.float64)
+        nl = SparcNonlocal()
+        keep = []
+        if proj is not None and proj.nproj > 0:
+            arrs = [np.ascontiguousarray(proj.box_lo, np.int32).reshape(-1),
+                    np.ascontiguousarray(proj.box_n, np.int32).reshape(-1),
+                    np.ascontiguousarray(proj.chi_off, np.int64),
+                    np.ascontiguousarray(proj.chi, np.float64),
+                    np.ascontiguousarray(proj.gamma, np.float64)]
+            keep = arrs
+            nl.nproj = int(proj.nproj)
+            nl.box_lo = arrs[0].ctypes.data_as(POINTER(c_int32))
+            nl.box_n = arrs[1].ctypes.data_as(POINTER(c_int32))
+            nl.chi_off = arrs[2].ctypes.data_as(POINTER(c_int64))
+            nl.chi = arrs[3].ctypes.data_as(POINTER(c_double))
+            nl.chi_len = int(arrs[3].size)
+            nl.gamma = arrs[4].ctypes.data_as(POINTER(c_double))
+        else:
+            nl.nproj = 0
+        self._keep = keep
+        hh = c_void_p()
+        rc = L.sparc_ham_create(ctx.handle, ctypes.byref(g),
+                                self._veff.ctypes.data_as(POINTER(c_double)), ctypes.byref(nl),
+                                ctypes.byref(hh))
+        ctx.check(rc)
+        self.handle = hh
+
+    @classmethod
+    def from_workload(cls, ctx, wl, kidx=0):
+        return cls(ctx, wl.n, wl.h, wl.fd_radius, wl.kpts[kidx], wl.veff, wl.proj)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().sparc_ham_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- the C entry points
+
+def sparc_ham_set_veff(H: Hamiltonian, veff, stream=None):
+    """Replace V_eff: a torch CUDA float64 tensor (async) or a numpy array (sync)."""
+    if isinstance(veff, np.ndarray):
+        a = np.ascontiguousarray(veff, np.float64)
+        H.ctx.check(load().sparc_ham_set_veff(H.handle, a.ctypes.data, 0, None))
+    else:
+        H.ctx.check(load().sparc_ham_set_veff(H.handle, _ptr(veff), 1, _stream(stream)))
+
+
+def sparc_apply_H(H: Hamiltonian, X, Y, ns=None, ld=None, stream=None, dtype=None):
+    """Y = H X; X, Y are (ns, ld) CUDA tensors (column-major Nd x ns)."""
+    ns = X.shape[0] if ns is None else ns
+    ld = X.shape[-1] if ld is None else ld
+    dt = dtype_code(X) if dtype is None else dtype
+    H.ctx.check(load().sparc_apply_H(H.handle, dt, _ptr(X), _ptr(Y), int(ns), int(ld), _stream(stream)))
+
+
+def sparc_cheb_filter(H: Hamiltonian, m, a, b, a0, X, Y, ns=None, ld=None, stream=None, dtype=None):
+    """Y = C_m((H-c)/e) X / C_m((a0-c)/e), e=(b-a)/2, c=(b+a)/2."""
+    ns = X.shape[0] if ns is None else ns
+    ld = X.shape[-1] if ld is None else ld
+    dt = dtype_code(X) if dtype is None else dtype
+    H.ctx.check(load().sparc_cheb_filter(H.handle, dt, int(m), float(a), float(b), float(a0), _ptr(X),
+                                         _ptr(Y), int(ns), int(ld), _stream(stream)))
+
+
+def sparc_lanczos_bounds(H: Hamiltonian, ksteps, v0, stream=None):
+    """(a0, b) from `ksteps` Lanczos steps started at the device vector v0."""
+    a0 = c_double()
+    b = c_double()
+    H.ctx.check(load().sparc_lanczos_bounds(H.handle, int(ksteps), _ptr(v0), ctypes.byref(a0),
+                                            ctypes.byref(b), _stream(stream)))
+    return a0.value, b.value
+
+
+def sparc_rayleigh_ritz(H: Hamiltonian, U, eig, mode, ns=None, ld=None, stream=None, dtype=None):
+    """Rayleigh-Ritz in place on U (ns, ld); eig: CUDA float64 tensor of ns values."""
+    ns = U.shape[0] if ns is None else ns
+    ld = U.shape[-1] if ld is None else ld
+    dt = dtype_code(U) if dtype is None else dtype
+    H.ctx.check(load().sparc_rayleigh_ritz(H.handle, dt, _ptr(U), int(ns), int(ld), _ptr(eig), int(mode),
+                                           _stream(stream)))
