@@ -52,10 +52,11 @@ cudaError_t launch_from_blocks(const T* B, long long nd, int nblk, T* X, long lo
 template <class T>
 cudaError_t launch_nl_gather(const sparc_ham* H, const T* Y, int nbl, int nblk, T* gc,
                              cudaStream_t st);
-// Yout = alpha*((H - shift) Yin) + beta*Yprev   (Yprev may alias Yout, or be null)
+// Yout = alpha*((H - shift) Yin) + beta*Yprev   (Yprev may alias Yout, or be null);
+// diff: Laplacian in difference form (exact on constants; used for plain H-applies)
 template <class T>
 cudaError_t launch_hpass(const sparc_ham* H, const T* Yin, const T* Yprev, T* Yout, const T* gc,
-                         int nbl, int nblk, double alpha, double shift, double beta,
+                         int nbl, int nblk, double alpha, double shift, double beta, bool diff,
                          cudaStream_t st);
 
 }  // namespace sparc

@@ -33,7 +33,11 @@ __device__ __forceinline__ cf32 ldg(const cf32* p) {
 // One output element of  Yout = alpha * ((H - shift) Yin) + beta * Yprev.
 // H = -1/2 nabla_h^2 (Eq. FD:Laplacian, Bloch-periodic wrap) + V_eff
 //   + sum_p chi~_p gc_p (Eq. NonlocalPS:FD; gc = gamma h^3 chi~^H Yin from the gather).
-template <class T, int NBL>
+// DIFF selects the difference form sum_p c_p ((f_{+p} - f_0) + (f_{-p} - f_0)), which
+// uses sum_p w_p = -w_0 to drop the centre weight: constants are annihilated
+// exactly and rounding stays relative to the local variation of f, so FP32
+// weights do not shift the spectrum.  The filter passes use the direct form.
+template <class T, int NBL, bool DIFF>
 __global__ void __launch_bounds__(256)
 k_hpass(GridDev gd, const T* __restrict__ Yin, const T* Yprev, T* Yout,
         const typename Tr<T>::R* __restrict__ veff, const int* __restrict__ pt_ptr,
@@ -54,8 +58,10 @@ k_hpass(GridDev gd, const T* __restrict__ Yin, const T* Yprev, T* Yout,
   const int k = (int)(g / ((long long)n1 * n2));
   const long long sx = NBL, sy = (long long)n1 * NBL, sz = (long long)n1 * n2 * NBL;
   const T* yc = Y + g * NBL + lane;
-  R c0 = (R)(2.0 * (gd.coef[0][0] + gd.coef[1][0] + gd.coef[2][0])) + veff[g] - shift;
-  T acc = scale(c0, ldg(yc));
+  const T f0 = ldg(yc);
+  R c0 = veff[g] - shift;
+  if (!DIFF) c0 += (R)(2.0 * (gd.coef[0][0] + gd.coef[1][0] + gd.coef[2][0]));
+  T acc = scale(c0, f0);
   C phx{(R)gd.ph_re[0], (R)gd.ph_im[0]}, phy{(R)gd.ph_re[1], (R)gd.ph_im[1]},
       phz{(R)gd.ph_re[2], (R)gd.ph_im[2]};
   C phxm{phx.x, -phx.y}, phym{phy.x, -phy.y}, phzm{phz.x, -phz.y};
@@ -67,7 +73,8 @@ k_hpass(GridDev gd, const T* __restrict__ Yin, const T* Yprev, T* Yout,
     else { a = ldg(yc + (long long)(ip - n1 - i) * sx); if constexpr (Tr<T>::cplx) a = Tr<T>::mulc(a, phx); }
     if (im >= 0) b = ldg(yc - p * sx);
     else { b = ldg(yc + (long long)(im + n1 - i) * sx); if constexpr (Tr<T>::cplx) b = Tr<T>::mulc(b, phxm); }
-    acc = axpy(acc, (R)gd.coef[0][p], add(a, b));
+    if (DIFF) acc = axpy(acc, (R)gd.coef[0][p], add(a - f0, b - f0));
+    else acc = axpy(acc, (R)gd.coef[0][p], add(a, b));
   }
   // y
   for (int p = 1; p <= gd.no; ++p) {
@@ -77,7 +84,8 @@ k_hpass(GridDev gd, const T* __restrict__ Yin, const T* Yprev, T* Yout,
     else { a = ldg(yc + (long long)(jp - n2 - j) * sy); if constexpr (Tr<T>::cplx) a = Tr<T>::mulc(a, phy); }
     if (jm >= 0) b = ldg(yc - p * sy);
     else { b = ldg(yc + (long long)(jm + n2 - j) * sy); if constexpr (Tr<T>::cplx) b = Tr<T>::mulc(b, phym); }
-    acc = axpy(acc, (R)gd.coef[1][p], add(a, b));
+    if (DIFF) acc = axpy(acc, (R)gd.coef[1][p], add(a - f0, b - f0));
+    else acc = axpy(acc, (R)gd.coef[1][p], add(a, b));
   }
   // z
   for (int p = 1; p <= gd.no; ++p) {
@@ -87,7 +95,8 @@ k_hpass(GridDev gd, const T* __restrict__ Yin, const T* Yprev, T* Yout,
     else { a = ldg(yc + (long long)(kp - n3 - k) * sz); if constexpr (Tr<T>::cplx) a = Tr<T>::mulc(a, phz); }
     if (km >= 0) b = ldg(yc - p * sz);
     else { b = ldg(yc + (long long)(km + n3 - k) * sz); if constexpr (Tr<T>::cplx) b = Tr<T>::mulc(b, phzm); }
-    acc = axpy(acc, (R)gd.coef[2][p], add(a, b));
+    if (DIFF) acc = axpy(acc, (R)gd.coef[2][p], add(a - f0, b - f0));
+    else acc = axpy(acc, (R)gd.coef[2][p], add(a, b));
   }
   // nonlocal scatter: sum over the projectors whose box holds node g
   if (pt_ptr != nullptr) {
@@ -221,7 +230,7 @@ cudaError_t launch_nl_gather(const sparc_ham* H, const T* Y, int nbl, int nblk, 
 
 template <class T>
 cudaError_t launch_hpass(const sparc_ham* H, const T* Yin, const T* Yprev, T* Yout, const T* gc,
-                         int nbl, int nblk, double alpha, double shift, double beta,
+                         int nbl, int nblk, double alpha, double shift, double beta, bool diff,
                          cudaStream_t st) {
   using R = typename Tr<T>::R;
   const T* ptv = H->nproj ? reinterpret_cast<const T*>(H->d_pt_val[DtypeOf<T>::v]) : nullptr;
@@ -229,12 +238,16 @@ cudaError_t launch_hpass(const sparc_ham* H, const T* Yin, const T* Yprev, T* Yo
   long long threads = H->gd.nd * nbl;
   dim3 grid((unsigned)ceil_div(threads, 256), (unsigned)nblk);
   cudaEvent_t t0 = timing_begin(H->ctx, st);
-  if (nbl == NB)
-    k_hpass<T, NB><<<grid, 256, 0, st>>>(H->gd, Yin, Yprev, Yout, veff_of<T>(H), ptr, H->d_pt_p,
-                                         ptv, gc, nblk, (R)alpha, (R)shift, (R)beta);
-  else
-    k_hpass<T, 1><<<grid, 256, 0, st>>>(H->gd, Yin, Yprev, Yout, veff_of<T>(H), ptr, H->d_pt_p,
-                                        ptv, gc, nblk, (R)alpha, (R)shift, (R)beta);
+#define SPARC_HPASS(NBL_, D_)                                                                  \
+  k_hpass<T, NBL_, D_><<<grid, 256, 0, st>>>(H->gd, Yin, Yprev, Yout, veff_of<T>(H), ptr,      \
+                                             H->d_pt_p, ptv, gc, nblk, (R)alpha, (R)shift,    \
+                                             (R)beta)
+  if (nbl == NB) {
+    if (diff) SPARC_HPASS(NB, true); else SPARC_HPASS(NB, false);
+  } else {
+    if (diff) SPARC_HPASS(1, true); else SPARC_HPASS(1, false);
+  }
+#undef SPARC_HPASS
   ++H->ctx->launches;
   timing_end(H->ctx, TK_HPASS, t0, st);
   return cudaGetLastError();
@@ -248,7 +261,7 @@ cudaError_t launch_hpass(const sparc_ham* H, const T* Yin, const T* Yprev, T* Yo
   template cudaError_t launch_nl_gather<T>(const sparc_ham*, const T*, int, int, T*,           \
                                            cudaStream_t);                                      \
   template cudaError_t launch_hpass<T>(const sparc_ham*, const T*, const T*, T*, const T*, int,\
-                                       int, double, double, double, cudaStream_t);
+                                       int, double, double, double, bool, cudaStream_t);
 SPARC_INST(double)
 SPARC_INST(float)
 SPARC_INST(cf64)

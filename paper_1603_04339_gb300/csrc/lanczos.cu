@@ -182,7 +182,7 @@ sparc_status lanczos(sparc_ham* H, int ksteps, const T* v0, double* a0, double* 
   for (int j = 0; j < ksteps; ++j) {
     // w = H v_j  (single vector: interleaved width 1 equals plain layout)
     SPARC_CUDA(ctx, launch_nl_gather<T>(H, Vi(j), 1, 1, gc, st));
-    SPARC_CUDA(ctx, launch_hpass<T>(H, Vi(j), nullptr, w, gc, 1, 1, 1.0, 0.0, 0.0, st));
+    SPARC_CUDA(ctx, launch_hpass<T>(H, Vi(j), nullptr, w, gc, 1, 1, 1.0, 0.0, 0.0, true, st));
     // alpha_j = Re(v_j^H w); w -= alpha_j v_j + beta_{j-1} v_{j-1}
     k_multidot_part<T><<<RPARTS, RB, 0, st>>>(Vi(j), 1, 0, w, nd, part);
     ++ctx->launches;

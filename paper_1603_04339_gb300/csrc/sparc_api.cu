@@ -193,7 +193,7 @@ sparc_status apply_block(sparc_ham* H, const T* X, T* Y, int ns, long long ld, c
   SPARC_CUDA(H->ctx, launch_to_blocks<T>(X, ld, ns, b0, H->gd.nd, nblk, st));
   ++H->ctx->launches;
   SPARC_CUDA(H->ctx, launch_nl_gather<T>(H, b0, NB, nblk, gc, st));
-  SPARC_CUDA(H->ctx, launch_hpass<T>(H, b0, nullptr, b1, gc, NB, nblk, 1.0, 0.0, 0.0, st));
+  SPARC_CUDA(H->ctx, launch_hpass<T>(H, b0, nullptr, b1, gc, NB, nblk, 1.0, 0.0, 0.0, true, st));
   SPARC_CUDA(H->ctx, launch_from_blocks<T>(b1, H->gd.nd, nblk, Y, ld, ns, st));
   ++H->ctx->launches;
   return SPARC_OK;
@@ -215,12 +215,12 @@ sparc_status filter_block(sparc_ham* H, int m, double a, double b, double a0, co
   SPARC_CUDA(H->ctx, launch_to_blocks<T>(X, ld, ns, prev, H->gd.nd, nblk, st));
   ++H->ctx->launches;
   SPARC_CUDA(H->ctx, launch_nl_gather<T>(H, prev, NB, nblk, gc, st));
-  SPARC_CUDA(H->ctx, launch_hpass<T>(H, prev, nullptr, cur, gc, NB, nblk, sigma1 / e, c, 0.0, st));
+  SPARC_CUDA(H->ctx, launch_hpass<T>(H, prev, nullptr, cur, gc, NB, nblk, sigma1 / e, c, 0.0, false, st));
   for (int j = 1; j < m; ++j) {
     const double sigma_new = 1.0 / (2.0 / sigma1 - sigma);
     SPARC_CUDA(H->ctx, launch_nl_gather<T>(H, cur, NB, nblk, gc, st));
     SPARC_CUDA(H->ctx, launch_hpass<T>(H, cur, prev, prev, gc, NB, nblk, 2.0 * sigma_new / e, c,
-                                       -sigma * sigma_new, st));
+                                       -sigma * sigma_new, false, st));
     std::swap(cur, prev);
     sigma = sigma_new;
   }
