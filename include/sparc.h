@@ -114,6 +114,30 @@ void sparc_ham_destroy(sparc_ham* H);
 sparc_status sparc_apply_H(sparc_ham* H, sparc_dtype dtype, const void* X, void* Y, int ns,
                            int64_t ld, void* stream);
 
+/* Y = H X like sparc_apply_H, but the call itself allocates no device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate at the point of the call, such as code being captured into
+ * a CUDA graph, applications whose device memory is owned by another pool,
+ * or real-time loops that may not block on an allocator.  Its scratch is one
+ * fixed array of SPARC_NOALLOC_SCRATCH_BYTES in the library image, present
+ * on every GPU that loads the library until the process exits.
+ *   - Limit: 2 * ceil(ns/32)*32*Nd + max(nproj,1)*ceil(ns/32)*32 elements of
+ *     `dtype` (each part rounded up to 256 bytes) must fit in the array;
+ *     larger problems are rejected with SPARC_ERR_INVALID_ARG and a message.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - The projector values of H in `dtype` must already be on the device
+ *     (any call of sparc_apply_H with that dtype and H uploads them);
+ *     otherwise SPARC_ERR_INVALID_ARG.
+ *   - All calls on a device share the array: calls that overlap on the GPU
+ *     race and must be serialised by the caller.  Every byte a call reads from
+ *     it is written earlier in the same call, so nothing needs clearing.
+ * Arguments, layout and errors otherwise as sparc_apply_H. */
+#define SPARC_NOALLOC_SCRATCH_BYTES (32u << 20)
+sparc_status sparc_apply_H_noalloc(sparc_ham* H, sparc_dtype dtype, const void* X, void* Y,
+                                   int ns, int64_t ld, void* stream);
+
 /* Scaled Chebyshev filter of degree m (Eq. ChebFilter with e = (b-a)/2, c = (b+a)/2):
  *   Y = C_m((H - c)/e) X / C_m((a0 - c)/e),
  * computed by the three-term recurrence.  a = filter cutoff lambda_c,

@@ -23,7 +23,7 @@ STATUS = {0: "SPARC_OK", 1: "SPARC_ERR_INVALID_ARG", 2: "SPARC_ERR_OOM", 3: "SPA
 EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_sync", "sparc_ham_create",
            "sparc_ham_set_veff", "sparc_ham_destroy", "sparc_apply_H", "sparc_cheb_filter",
            "sparc_lanczos_bounds", "sparc_rayleigh_ritz", "sparc_timing_enable", "sparc_timing_read",
-           "sparc_launch_count"]
+           "sparc_launch_count", "sparc_apply_H_noalloc"]
 TIMED = {"hpass": 0, "gather": 1, "gram": 2, "eig": 3, "rotation": 4}
 
 
@@ -75,6 +75,8 @@ def load(path: str = LIB_PATH):
                                       c_void_p]
     L.sparc_timing_enable.argtypes = [c_void_p, c_int]
     L.sparc_launch_count.argtypes = [c_void_p, POINTER(c_int64)]
+    L.sparc_apply_H_noalloc.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_int, c_int64, c_void_p]
+    L.sparc_apply_H_noalloc.restype = c_int
     L.sparc_launch_count.restype = c_int
     L.sparc_timing_read.argtypes = [c_void_p, c_int, POINTER(c_double), POINTER(c_int64)]
     for name in ("sparc_timing_enable", "sparc_timing_read", "sparc_create", "sparc_sync", "sparc_ham_create", "sparc_ham_set_veff",
@@ -235,6 +237,21 @@ def sparc_apply_H(H: Hamiltonian, X, Y, ns=None, ld=None, stream=None, dtype=Non
     ld = X.shape[-1] if ld is None else ld
     dt = dtype_code(X) if dtype is None else dtype
     H.ctx.check(load().sparc_apply_H(H.handle, dt, _ptr(X), _ptr(Y), int(ns), int(ld), _stream(stream)))
+
+
+def sparc_apply_H_noalloc(H: Hamiltonian, X, Y, ns=None, ld=None, stream=None, dtype=None):
+    """Y = H X in the library's fixed scratch array: the call allocates no device memory.
+
+    For callers that cannot allocate when they need H X (graph capture, foreign
+    memory pools, real-time loops).  Needs the projector values of H in this
+    dtype on the device already (one sparc_apply_H call with the dtype uploads
+    them); calls that overlap on the GPU share the scratch and race.
+    """
+    ns = X.shape[0] if ns is None else ns
+    ld = X.shape[-1] if ld is None else ld
+    dt = dtype_code(X) if dtype is None else dtype
+    H.ctx.check(load().sparc_apply_H_noalloc(H.handle, dt, _ptr(X), _ptr(Y), int(ns), int(ld),
+                                             _stream(stream)))
 
 
 def sparc_cheb_filter(H: Hamiltonian, m, a, b, a0, X, Y, ns=None, ld=None, stream=None, dtype=None):
