@@ -38,6 +38,9 @@ def _args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-cols", type=int, default=1)
+    ap.add_argument("--mode", choices=["step", "filter"], default="step",
+                    help="filter: only the Chebyshev filter (for profiler captures)")
+    ap.add_argument("--ns", type=int, default=None, help="orbitals (filter mode; default: the cell's 512)")
     return ap.parse_args()
 
 
@@ -225,6 +228,8 @@ def run_ours(args):
     gr_ms, _ = ctx.timing_read("gram")
     ei_ms, _ = ctx.timing_read("eig")
     ro_ms, _ = ctx.timing_read("rotation")
+    ja_ms, _ = ctx.timing_read("jacobi")
+    sweeps = ctx.last_sweeps()
     ctx.timing(False)
     if world > 1:
         t = torch.tensor([ms], device="cuda")
@@ -291,7 +296,8 @@ def run_ours(args):
                      "avg_launch_ms": hp_avg_ms},
         "breakdown_ms_per_step": {"hpass": hp_ms / args.steps, "gather": ga_ms / args.steps,
                                   "gram": gr_ms / args.steps, "chol_eig": ei_ms / args.steps,
-                                  "rotation": ro_ms / args.steps},
+                                  "rotation": ro_ms / args.steps, "jacobi": ja_ms / args.steps,
+                                  "jacobi_sweeps": sweeps},
         "filter_only": {"value": units / ((hp_ms + ga_ms) / args.steps * 1e-3) / 1e9, "unit": UNIT},
         "clocks": ck, "e2e": e2e, "gpu_launches": int(launches), "cpu_baseline": cpu,
     }
@@ -301,10 +307,46 @@ def run_ours(args):
     return 0
 
 
+def run_filter_only(args):
+    """The filter alone on the benchmark cell (a short, fixed launch sequence for profiling)."""
+    import numpy as np
+    import torch
+    from paper_1603_04339_gb300 import build, synth
+    build.build()
+    from paper_1603_04339_gb300 import sparc
+    wl = synth.config2()
+    ns = args.ns or wl.ns
+    ctx = sparc.Context(0)
+    H = sparc.Hamiltonian.from_workload(ctx, wl)
+    X = torch.from_numpy(synth.random_orbitals(wl.nd, ns, 2002).astype(np.float32)).cuda()
+    Y = torch.empty_like(X)
+    a0, b = -2.5, 140.0
+    a = a0 + (b - a0) * (wl.ns / wl.nd) ** (2.0 / 3.0)
+    for _ in range(args.warmup):
+        sparc.sparc_cheb_filter(H, wl.m, a, b, a0, X, Y)
+    torch.cuda.synchronize()
+    ctx.timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        sparc.sparc_cheb_filter(H, wl.m, a, b, a0, X, Y)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    hp, hn = ctx.timing_read("hpass")
+    ga, gn = ctx.timing_read("gather")
+    print(json.dumps({"mode": "filter", "ns": ns, "ms_per_filter": ms,
+                      "gpt_orb_deg_per_s": wl.nd * ns * wl.m / (ms * 1e-3) / 1e9,
+                      "hpass_avg_ms": hp / max(hn, 1), "gather_avg_ms": ga / max(gn, 1)}), flush=True)
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "filter":
+        return run_filter_only(args)
     return run_ours(args)
 
 

@@ -121,7 +121,7 @@ sparc_status sparc_apply_H(sparc_ham* H, sparc_dtype dtype, const void* X, void*
  * or real-time loops that may not block on an allocator.  Its scratch is one
  * fixed array of SPARC_NOALLOC_SCRATCH_BYTES in the library image, present
  * on every GPU that loads the library until the process exits.
- *   - Limit: 2 * ceil(ns/32)*32*Nd + max(nproj,1)*ceil(ns/32)*32 elements of
+ *   - Limit: 2 * ceil(ns/8)*8*Nd + max(nproj,1)*ceil(ns/8)*8 elements of
  *     `dtype` (each part rounded up to 256 bytes) must fit in the array;
  *     larger problems are rejected with SPARC_ERR_INVALID_ARG and a message.
  *   - The first call on a device looks up the array's device address
@@ -175,11 +175,14 @@ sparc_status sparc_rayleigh_ritz(sparc_ham* H, sparc_dtype dtype, void* U, int n
  *   which = 1: the nonlocal projection (k_nl_gather)
  *   which = 2: the Gram products of Rayleigh-Ritz
  *   which = 3: the Cholesky + subspace eigensolve of Rayleigh-Ritz
- *   which = 4: the subspace rotation of Rayleigh-Ritz */
+ *   which = 4: the subspace rotation of Rayleigh-Ritz
+ *   which = 5: the Jacobi sweeps of the subspace eigensolve (inside which = 3) */
 sparc_status sparc_timing_enable(sparc_ctx* ctx, int on);
 sparc_status sparc_timing_read(sparc_ctx* ctx, int which, double* ms_total, int64_t* launches);
 /* Number of kernels this context has launched since it was created. */
 sparc_status sparc_launch_count(const sparc_ctx* ctx, int64_t* launches);
+/* Jacobi sweeps used by the last Rayleigh-Ritz call on this context. */
+sparc_status sparc_last_sweeps(const sparc_ctx* ctx, int* sweeps);
 
 #ifdef __cplusplus
 }

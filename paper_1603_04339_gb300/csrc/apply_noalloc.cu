@@ -95,7 +95,7 @@ extern "C" sparc_status sparc_apply_H_noalloc(sparc_ham* H, sparc_dtype dtype, c
                 "problem too large for the fixed scratch of sparc_apply_H_noalloc: needs " +
                     std::to_string(2 * bb + gb) + " bytes, limit " +
                     std::to_string((size_t)SPARC_NOALLOC_SCRATCH_BYTES) +
-                    " (2 * ceil(ns/32)*32*Nd + nproj*ceil(ns/32)*32 elements)");
+                    " (2 * ceil(ns/8)*8*Nd + nproj*ceil(ns/8)*8 elements)");
   SPARC_CUDA(ctx, cudaSetDevice(ctx->device));
   void* base = nullptr;
   SPARC_CUDA(ctx, scratch_address(ctx->device, &base));

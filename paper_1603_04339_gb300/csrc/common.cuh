@@ -5,7 +5,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/sparc.h"
@@ -143,7 +145,7 @@ enum : int {
 
 // ----------------------------------------------------------------- geometry passed to kernels
 constexpr int MAX_FD = 8;
-constexpr int NB = 32;        // orbitals per interleaved block (one warp lane each)
+constexpr int NB = 8;         // orbitals per interleaved block (8 lanes share a grid node)
 
 struct GridDev {
   int n1, n2, n3;
@@ -165,11 +167,15 @@ struct sparc_ctx {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   // kernel timing: event pairs per timed kernel class
-  static constexpr int NTIMED = 5;
+  static constexpr int NTIMED = 6;
   long long launches = 0;          // kernels launched by this context (instrumentation)
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[NTIMED];
   std::vector<cudaEvent_t> ev_pool;
+  // captured Jacobi sweeps, keyed by (element kind, n, buffers)
+  cudaStream_t cap_stream = nullptr;
+  std::map<std::tuple<int, int, void*, void*, void*>, cudaGraphExec_t> graphs;
+  int last_sweeps = 0;
 };
 
 namespace sparc {
@@ -187,16 +193,22 @@ sparc_status cuda_fail(sparc_ctx* ctx, cudaError_t e, const char* where);
     if (e_ != cudaSuccess) return ::sparc::cuda_fail(ctx, e_, #call); \
   } while (0)
 
-#define SPARC_LAUNCH(ctx, what)                                  \
-  do {                                                           \
-    cudaError_t e_ = cudaGetLastError();                         \
-    if (e_ != cudaSuccess) return ::sparc::cuda_fail(ctx, e_, what); \
+// Debug aid: with SPARC_SYNC_CHECK=1 in the environment every checkpoint also
+// synchronises the device, so that an asynchronous fault is reported at the
+// stage that caused it.
+bool sync_check();
+
+#define SPARC_LAUNCH(ctx, what)                                                  \
+  do {                                                                           \
+    cudaError_t e_ = cudaGetLastError();                                         \
+    if (e_ == cudaSuccess && ::sparc::sync_check()) e_ = cudaDeviceSynchronize(); \
+    if (e_ != cudaSuccess) return ::sparc::cuda_fail(ctx, e_, what);             \
   } while (0)
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // Timing hooks: bracket a launch with events on `st` while timing is enabled.
-enum TimedKernel { TK_HPASS = 0, TK_GATHER = 1, TK_GRAM = 2, TK_EIG = 3, TK_ROT = 4 };
+enum TimedKernel { TK_HPASS = 0, TK_GATHER = 1, TK_GRAM = 2, TK_EIG = 3, TK_ROT = 4, TK_JAC = 5 };
 cudaEvent_t timing_begin(sparc_ctx* ctx, cudaStream_t st);
 void timing_end(sparc_ctx* ctx, int which, cudaEvent_t begin, cudaStream_t st);
 

@@ -26,6 +26,7 @@ struct sparc_ham {
   void* d_p_val[4] = {nullptr, nullptr, nullptr, nullptr};   // [n_ent], projector-major
   void* d_pt_val[4] = {nullptr, nullptr, nullptr, nullptr};  // [n_ent], node-major
   std::vector<double> h_p_re, h_p_im, h_pt_re, h_pt_im;
+  void* fast = nullptr;          // sparc::fast::Tables* (tiled FP32 kernels)
 };
 
 namespace sparc {

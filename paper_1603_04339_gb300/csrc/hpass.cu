@@ -3,10 +3,10 @@
 // orbital-interleaved layout the kernels work in.
 //
 // Interleaved layout: B[blk][g][lane], lane = orbital within a block of `nbl`
-// orbitals (nbl = 32 for blocks of orbitals, 1 for single vectors).  A warp
-// then reads the 32 orbitals of one grid node as one contiguous line, the
-// projector values of a node are warp-uniform, and every node-index
-// computation is shared by the 32 lanes.
+// orbitals (nbl = NB = 8 for blocks of orbitals, 1 for single vectors).  The 8
+// orbitals of one grid node are one contiguous 32-byte sector (FP32), the
+// projector values of a node are shared by its 8 lanes, and every node-index
+// computation is shared by those lanes.
 #include "ham.cuh"
 
 namespace sparc {
@@ -139,41 +139,39 @@ k_nl_gather(const T* __restrict__ Y, long long nd, const long long* __restrict__
   if (grp == 0) gc[((size_t)p * nblk + blk) * NBL + lane] = scale(gamma[p] * dv, sm[lane]);
 }
 
-// Column-major X (Nd x ns, ld) -> B[blk][g][32]; lanes past ns are zero.
+// Column-major X (Nd x ns, ld) -> B[blk][g][NB]; lanes past ns are zero.
+// One CTA moves 32 nodes x NB orbitals: coalesced reads along g per orbital,
+// one contiguous 32*NB-element write.
 template <class T>
-__global__ void k_to_blocks(const T* __restrict__ X, long long ld, int ns, T* __restrict__ B,
-                            long long nd) {
-  __shared__ T tile[32][33];
+__global__ void __launch_bounds__(256) k_to_blocks(const T* __restrict__ X, long long ld, int ns,
+                                                   T* __restrict__ B, long long nd) {
+  __shared__ T tile[NB][33];
   const long long g0 = (long long)blockIdx.x * 32;
   const int blk = blockIdx.y;
-  for (int r = threadIdx.y; r < 32; r += 8) {
-    const int n = blk * 32 + r;
-    const long long g = g0 + threadIdx.x;
-    tile[r][threadIdx.x] = (n < ns && g < nd) ? X[g + (long long)n * ld] : Tr<T>::zero();
-  }
+  const int o = threadIdx.y, x = threadIdx.x;   // blockDim = (32, NB)
+  const int n = blk * NB + o;
+  const long long g = g0 + x;
+  tile[o][x] = (n < ns && g < nd) ? X[g + (long long)n * ld] : Tr<T>::zero();
   __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += 8) {
-    const long long g = g0 + r;
-    if (g < nd) B[((size_t)blk * nd + g) * 32 + threadIdx.x] = tile[threadIdx.x][r];
-  }
+  const int t = threadIdx.y * 32 + threadIdx.x;
+  const int p = t / NB, l = t % NB;
+  if (g0 + p < nd) B[((size_t)blk * nd + g0 + p) * NB + l] = tile[l][p];
 }
 
 template <class T>
-__global__ void k_from_blocks(const T* __restrict__ B, long long nd, T* __restrict__ X,
-                              long long ld, int ns) {
-  __shared__ T tile[32][33];
+__global__ void __launch_bounds__(256) k_from_blocks(const T* __restrict__ B, long long nd,
+                                                     T* __restrict__ X, long long ld, int ns) {
+  __shared__ T tile[NB][33];
   const long long g0 = (long long)blockIdx.x * 32;
   const int blk = blockIdx.y;
-  for (int r = threadIdx.y; r < 32; r += 8) {
-    const long long g = g0 + r;
-    if (g < nd) tile[r][threadIdx.x] = B[((size_t)blk * nd + g) * 32 + threadIdx.x];
-  }
+  const int t = threadIdx.y * 32 + threadIdx.x;
+  const int p = t / NB, l = t % NB;
+  if (g0 + p < nd) tile[l][p] = B[((size_t)blk * nd + g0 + p) * NB + l];
   __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += 8) {
-    const int n = blk * 32 + r;
-    const long long g = g0 + threadIdx.x;
-    if (n < ns && g < nd) X[g + (long long)n * ld] = tile[threadIdx.x][r];
-  }
+  const int o = threadIdx.y, x = threadIdx.x;
+  const int n = blk * NB + o;
+  const long long g = g0 + x;
+  if (n < ns && g < nd) X[g + (long long)n * ld] = tile[o][x];
 }
 
 template <class T>
@@ -195,7 +193,7 @@ template <> const float* gamma_of<cf32>(const sparc_ham* H) { return H->d_gamma3
 template <class T>
 cudaError_t launch_to_blocks(const T* X, long long ld, int ns, T* B, long long nd, int nblk,
                              cudaStream_t st) {
-  dim3 grid((unsigned)ceil_div(nd, 32), (unsigned)nblk), block(32, 8);
+  dim3 grid((unsigned)ceil_div(nd, 32), (unsigned)nblk), block(32, NB);
   k_to_blocks<T><<<grid, block, 0, st>>>(X, ld, ns, B, nd);
   return cudaGetLastError();
 }
@@ -203,7 +201,7 @@ cudaError_t launch_to_blocks(const T* X, long long ld, int ns, T* B, long long n
 template <class T>
 cudaError_t launch_from_blocks(const T* B, long long nd, int nblk, T* X, long long ld, int ns,
                                cudaStream_t st) {
-  dim3 grid((unsigned)ceil_div(nd, 32), (unsigned)nblk), block(32, 8);
+  dim3 grid((unsigned)ceil_div(nd, 32), (unsigned)nblk), block(32, NB);
   k_from_blocks<T><<<grid, block, 0, st>>>(B, nd, X, ld, ns);
   return cudaGetLastError();
 }

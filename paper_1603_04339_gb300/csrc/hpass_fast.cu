@@ -1,0 +1,726 @@
+// Tiled H-pass for FP32 and complex64 blocks (radius-6 FD stencil, the paper's
+// twelfth order), and the projection of the nonlocal operator by projector group.
+//
+// Kernel structure (one CTA = 16 x 16 nodes in (x, y) x one z-range x one block
+// of NB = 8 orbitals, 512 threads):
+//   * each thread owns RX = 4 x-consecutive nodes of one row for one orbital and
+//     keeps their values at z-6 .. z+6 in a register queue (the z part of the
+//     stencil comes from registers; the queue is rotated by unrolling 13 steps);
+//   * the (x, y) plane at z, with a 6-node halo, is staged in shared memory:
+//     nodes owned by the CTA come from the queues, the halo from global memory
+//     (L2) with Bloch-periodic wrap and phase; double-buffered, one barrier per z;
+//   * x and y neighbours come from the staged plane (a sliding window in x);
+//   * the nonlocal term sum_p chi~_p gc_p is added from the projector boxes that
+//     are active at (tile, z) (precomputed lists), 4 projectors per box at once;
+//   * the Chebyshev recurrence is the epilogue: Yout = alpha (H - shift) Yin + beta Yprev.
+#include <algorithm>
+#include <array>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "fast.cuh"
+
+namespace sparc {
+namespace fast {
+
+// --------------------------------------------------------------------------- host tables
+
+void free_tables(Tables& t) {
+  void* ps[] = {t.d_grp, t.d_sb, t.d_chi4};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  for (Layout& L : t.lay) {
+    void* qs[] = {L.d_cptr, L.d_citems, L.d_sptr, L.d_sslots};
+    for (void* p : qs)
+      if (p) cudaFree(p);
+  }
+  t = Tables();
+}
+
+static long long fdiv(long long a, long long b) {
+  long long q = a / b;
+  if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+  return q;
+}
+
+sparc_status build_tables(sparc_ham* H, const sparc_nonlocal* nl) {
+  sparc_ctx* ctx = H->ctx;
+  Tables* T = new Tables();
+  H->fast = T;
+  const int n[3] = {H->gd.n1, H->gd.n2, H->gd.n3};
+  const double L[3] = {H->grid.n[0] * H->grid.h[0], H->grid.n[1] * H->grid.h[1],
+                       H->grid.n[2] * H->grid.h[2]};
+  const int np = nl ? nl->nproj : 0;
+  // group projectors with identical boxes, in order, at most four per group
+  std::vector<Group> grps;
+  std::vector<std::array<int, 6>> gbox;
+  std::map<std::array<int, 6>, int> open;   // box -> index of the group being filled
+  for (int p = 0; p < np; ++p) {
+    std::array<int, 6> key{nl->box_lo[3 * p], nl->box_lo[3 * p + 1], nl->box_lo[3 * p + 2],
+                           nl->box_n[3 * p], nl->box_n[3 * p + 1], nl->box_n[3 * p + 2]};
+    auto it = open.find(key);
+    int gi;
+    if (it == open.end() || [&] { Group& g = grps[it->second]; return g.proj[3] >= 0; }()) {
+      Group g;
+      g.proj[0] = g.proj[1] = g.proj[2] = g.proj[3] = -1;
+      g.sb0 = g.sb1 = 0;
+      grps.push_back(g);
+      gbox.push_back(key);
+      gi = (int)grps.size() - 1;
+      open[key] = gi;
+    } else {
+      gi = it->second;
+    }
+    Group& g = grps[gi];
+    for (int s = 0; s < 4; ++s)
+      if (g.proj[s] < 0) { g.proj[s] = p; break; }
+  }
+  // box values [node][4] and the periodic pieces of every box
+  std::vector<float> chi4;
+  std::vector<SubBox> sbs;
+  long long off4 = 0;
+  for (size_t gi = 0; gi < grps.size(); ++gi) {
+    Group& g = grps[gi];
+    const int* lo = &gbox[gi][0];
+    const int* nb = &gbox[gi][3];
+    const long long sz = (long long)nb[0] * nb[1] * nb[2];
+    chi4.resize((size_t)(off4 + sz) * 4, 0.0f);
+    for (int s = 0; s < 4; ++s) {
+      const int p = g.proj[s];
+      if (p < 0) continue;
+      for (long long e = 0; e < sz; ++e) chi4[(size_t)(off4 + e) * 4 + s] = (float)nl->chi[nl->chi_off[p] + e];
+    }
+    // per axis: pieces [q0, q1) of the unwrapped box with one image index t each
+    std::vector<std::array<long long, 3>> piece[3];
+    for (int a = 0; a < 3; ++a) {
+      long long q = lo[a];
+      const long long qe = (long long)lo[a] + nb[a];
+      while (q < qe) {
+        const long long t = fdiv(q, n[a]);
+        const long long q1 = std::min(qe, (t + 1) * n[a]);
+        piece[a].push_back({q, q1, t});
+        q = q1;
+      }
+    }
+    g.sb0 = (int)sbs.size();
+    for (auto& pz : piece[2])
+      for (auto& py : piece[1])
+        for (auto& px : piece[0]) {
+          SubBox b;
+          b.gx0 = (int)(px[0] - px[2] * n[0]); b.gx1 = (int)(px[1] - px[2] * n[0]);
+          b.gy0 = (int)(py[0] - py[2] * n[1]); b.gy1 = (int)(py[1] - py[2] * n[1]);
+          b.gz0 = (int)(pz[0] - pz[2] * n[2]); b.gz1 = (int)(pz[1] - pz[2] * n[2]);
+          b.bx0 = (int)(px[0] - lo[0]); b.by0 = (int)(py[0] - lo[1]); b.bz0 = (int)(pz[0] - lo[2]);
+          b.nbx = nb[0]; b.nby = nb[1];
+          b.grp = (int)gi;
+          b.chi4_off = off4;
+          const double kt = H->grid.k[0] * L[0] * (double)px[2] + H->grid.k[1] * L[1] * (double)py[2] +
+                            H->grid.k[2] * L[2] * (double)pz[2];
+          b.ph_re = (float)cos(kt);
+          b.ph_im = (float)(-sin(kt));
+          sbs.push_back(b);
+        }
+    g.sb1 = (int)sbs.size();
+    off4 += sz;
+  }
+  // per kernel tile shape: CTA item lists and per-z active slots
+  T->ngrp = (int)grps.size();
+  T->nsb = (int)sbs.size();
+  for (int si = 0; si < 2; ++si) {
+    Layout& Lo = T->lay[si];
+    const int TYk = (si == 0) ? Shape<float>::TY : Shape<cf32>::TY;
+    Lo.tiles_x = ceil_div(n[0], TX);
+    Lo.tiles_y = ceil_div(n[1], TYk);
+    Lo.nchunk = ceil_div(n[2], ZC);
+    const int nct = Lo.tiles_x * Lo.tiles_y * Lo.nchunk;
+    std::vector<std::vector<int>> items(nct);
+    for (int i = 0; i < (int)sbs.size(); ++i) {
+      const SubBox& b = sbs[i];
+      for (int ty = 0; ty < Lo.tiles_y; ++ty) {
+        const int y0 = ty * TYk, y1 = std::min(n[1], y0 + TYk);
+        if (b.gy1 <= y0 || b.gy0 >= y1) continue;
+        for (int tx = 0; tx < Lo.tiles_x; ++tx) {
+          const int x0 = tx * TX, x1 = std::min(n[0], x0 + TX);
+          if (b.gx1 <= x0 || b.gx0 >= x1) continue;
+          for (int c = 0; c < Lo.nchunk; ++c) {
+            const int z0 = c * ZC, z1 = std::min(n[2], z0 + ZC);
+            if (b.gz1 <= z0 || b.gz0 >= z1) continue;
+            items[(ty * Lo.tiles_x + tx) * Lo.nchunk + c].push_back(i);
+          }
+        }
+      }
+    }
+    // per (CTA, z, group of 4 rows): CTA-local indices of the pieces that touch those rows
+    const int nrg = TYk / 4;
+    std::vector<int> cptr(nct + 1, 0), citems, sptr((size_t)nct * ZC * nrg + 1, 0), sslots;
+    Lo.max_items = 0;
+    Lo.max_steps = 0;
+    for (int c = 0; c < nct; ++c) {
+      const auto& it = items[c];
+      Lo.max_items = std::max(Lo.max_items, (int)it.size());
+      cptr[c + 1] = cptr[c] + (int)it.size();
+      citems.insert(citems.end(), it.begin(), it.end());
+      const int tile = c / Lo.nchunk;
+      const int x0 = (tile % Lo.tiles_x) * TX, x1 = std::min(n[0], x0 + TX);
+      const int y0t = (tile / Lo.tiles_x) * TYk;
+      const int z0 = (c % Lo.nchunk) * ZC;
+      const int first = (int)sslots.size();
+      for (int k = 0; k < ZC; ++k)
+        for (int rg = 0; rg < nrg; ++rg) {
+          sptr[((size_t)c * ZC + k) * nrg + rg] = (int)sslots.size();
+          const int z = z0 + k;
+          const int y0 = y0t + 4 * rg, y1 = std::min(n[1], y0 + 4);
+          if (z < n[2] && y0 < y1)
+            for (int j = 0; j < (int)it.size(); ++j) {
+              const SubBox& b = sbs[it[j]];
+              if (b.gz0 <= z && z < b.gz1 && b.gy0 < y1 && b.gy1 > y0 && b.gx0 < x1 && b.gx1 > x0)
+                sslots.push_back(j);
+            }
+        }
+      Lo.max_steps = std::max(Lo.max_steps, (int)sslots.size() - first);
+    }
+    sptr[(size_t)nct * ZC * nrg] = (int)sslots.size();
+    auto up = [&](void** d, const void* h, size_t bytes) -> bool {
+      if (cudaMalloc(d, std::max<size_t>(bytes, 16)) != cudaSuccess) return false;
+      return bytes == 0 || cudaMemcpy(*d, h, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    if (!up((void**)&Lo.d_cptr, cptr.data(), cptr.size() * sizeof(int)) ||
+        !up((void**)&Lo.d_citems, citems.data(), citems.size() * sizeof(int)) ||
+        !up((void**)&Lo.d_sptr, sptr.data(), sptr.size() * sizeof(int)) ||
+        !up((void**)&Lo.d_sslots, sslots.data(), sslots.size() * sizeof(int))) {
+      cudaGetLastError();
+      return fail(ctx, SPARC_ERR_OOM, "projector table allocation failed");
+    }
+  }
+  auto up = [&](void** d, const void* h, size_t bytes) -> bool {
+    if (cudaMalloc(d, std::max<size_t>(bytes, 16)) != cudaSuccess) return false;
+    return bytes == 0 || cudaMemcpy(*d, h, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+  };
+  if (!up((void**)&T->d_grp, grps.data(), grps.size() * sizeof(Group)) ||
+      !up((void**)&T->d_sb, sbs.data(), sbs.size() * sizeof(SubBox)) ||
+      !up((void**)&T->d_chi4, chi4.data(), chi4.size() * sizeof(float))) {
+    cudaGetLastError();
+    return fail(ctx, SPARC_ERR_OOM, "projector table allocation failed");
+  }
+  return SPARC_OK;
+}
+
+bool usable(const sparc_ham* H) {
+  const Tables* T = (const Tables*)H->fast;
+  return T != nullptr && H->gd.no == R && T->lay[0].max_items <= MAXI && T->lay[1].max_items <= MAXI &&
+         T->lay[0].max_steps <= MAXSTEP && T->lay[1].max_steps <= MAXSTEP;
+}
+
+// --------------------------------------------------------------------------- device helpers
+
+template <class T> struct FT;
+template <> struct FT<float> {
+  static constexpr bool cplx = false;
+  __device__ static float zero() { return 0.f; }
+  __device__ static float phase(float v, float, float) { return v; }
+  __device__ static float dot4(float4 c, const float g[4]) { return c.x * g[0] + c.y * g[1] + c.z * g[2] + c.w * g[3]; }
+};
+template <> struct FT<cf32> {
+  static constexpr bool cplx = true;
+  __device__ static cf32 zero() { return {0.f, 0.f}; }
+  __device__ static cf32 phase(cf32 v, float pr, float pi) { return {v.x * pr - v.y * pi, v.x * pi + v.y * pr}; }
+  __device__ static cf32 dot4(float4 c, const cf32 g[4]) {
+    return {c.x * g[0].x + c.y * g[1].x + c.z * g[2].x + c.w * g[3].x,
+            c.x * g[0].y + c.y * g[1].y + c.z * g[2].y + c.w * g[3].y};
+  }
+};
+
+__device__ __forceinline__ float fld(const float* p) { return __ldg(p); }
+__device__ __forceinline__ cf32 fld(const cf32* p) {
+  float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return {v.x, v.y};
+}
+
+// Bloch phase exp(i k L t) from the per-axis phase exp(i k L) and an integer t (small |t|).
+__device__ __forceinline__ void phase_pow(float pr, float pi, int t, float& rr, float& ri) {
+  rr = 1.f; ri = 0.f;
+  const float qi = (t < 0) ? -pi : pi;
+  for (int a = 0; a < (t < 0 ? -t : t); ++a) {
+    const float x = rr * pr - ri * qi;
+    ri = rr * qi + ri * pr;
+    rr = x;
+  }
+}
+
+// Wrap g into [0, n) and return the number of cells crossed.
+__device__ __forceinline__ int wrap(int& g, int n) {
+  int t = 0;
+  while (g >= n) { g -= n; ++t; }
+  while (g < 0) { g += n; --t; }
+  return t;
+}
+
+// Asynchronous global -> shared copies (completion tracked per thread by groups).
+__device__ __forceinline__ void cp16(void* sm, const void* gm) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sm);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gm) : "memory");
+}
+__device__ __forceinline__ void cp4(void* sm, const void* gm) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sm);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gm) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+struct PassArgs {
+  long long nd;
+  int n1, n2, n3;
+  int tiles_x, nchunk, blk0, nblk_total;
+  float cx[R + 1], cy[R + 1], cz[R + 1];
+  float c0;                       // centre Laplacian coefficient (sum of -w_0 over axes)
+  float phx_r, phx_i, phy_r, phy_i, phz_r, phz_i;   // exp(i k_s L_s)
+  float alpha, shift, beta;
+  const float* veff;
+  const int* cptr;
+  const int* citems;
+  const int* sptr;
+  const int* sslots;
+  const SubBox* sb;
+  const Group* grp;
+  const float4* chi4;
+};
+
+// Compact form of a projector-box piece for the scatter: chi4 row of grid row
+// (y, z) starts at base + sy * y + sz * z (index of grid x = 0).
+struct Piece {
+  int gy0, gy1, gx0, gx1;
+  int base, sy, sz;
+  float ph_re, ph_im;
+};
+
+constexpr int PX = TX + 2 * R;
+constexpr int RP = PX * NB + 8;     // row pitch in elements: rows of a warp land 8 banks apart
+template <class T> __host__ __device__ constexpr int plane_rows() { return Shape<T>::TY + 2 * R; }
+template <class T> struct Smem {
+  static constexpr int TY = Shape<T>::TY, PY = plane_rows<T>();
+  static constexpr int NRG = TY / 4;
+  static constexpr size_t planes = 3 * (size_t)PY * RP * sizeof(T);
+  static constexpr size_t yprev = 3 * (size_t)TY * TX * NB * sizeof(T);
+  static constexpr size_t vb = 3 * (size_t)TY * TX * sizeof(float);
+  static constexpr size_t desc = (size_t)MAXI * sizeof(Piece);
+  static constexpr size_t gcs = (size_t)MAXI * 4 * NB * sizeof(T);
+  static constexpr size_t steps = (size_t)(ZC * NRG + 1 + MAXSTEP) * sizeof(int);
+  static constexpr size_t total = planes + yprev + vb + desc + gcs + steps;
+};
+
+// Yprev may alias Yout (the recurrence is written in place): neither is restrict.
+template <class T>
+__global__ void __launch_bounds__(THREADS, 1)
+k_pass(PassArgs a, const T* __restrict__ Yin, const T* Yprev, T* Yout, const T* __restrict__ gc) {
+  constexpr int Q = 2 * R + 1;
+  constexpr int RX = Shape<T>::RX, TY = Shape<T>::TY, PY = plane_rows<T>(), NRG = Smem<T>::NRG;
+  constexpr int CH = (int)(NB * sizeof(T) / 16);    // 16-byte chunks per node
+  constexpr int EPC = 16 / (int)sizeof(T);          // elements per chunk
+  constexpr int NHC = (PX * PY * CH + THREADS - 1) / THREADS;   // halo chunk slots per thread
+  constexpr int NPC = (TX * TY * CH + THREADS - 1) / THREADS;   // Y_{j-1} chunk slots per thread
+  static_assert((TX / RX) * TY * NB == THREADS, "tile shape must use all threads");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* planes = reinterpret_cast<T*>(smraw);
+  T* yps = reinterpret_cast<T*>(smraw + Smem<T>::planes);
+  float* vbs = reinterpret_cast<float*>(smraw + Smem<T>::planes + Smem<T>::yprev);
+  Piece* desc = reinterpret_cast<Piece*>(smraw + Smem<T>::planes + Smem<T>::yprev + Smem<T>::vb);
+  T* gcs = reinterpret_cast<T*>(smraw + Smem<T>::planes + Smem<T>::yprev + Smem<T>::vb + Smem<T>::desc);
+  int* steps = reinterpret_cast<int*>(smraw + Smem<T>::planes + Smem<T>::yprev + Smem<T>::vb +
+                                      Smem<T>::desc + Smem<T>::gcs);
+  const int t = threadIdx.x;
+  const int o = t % NB;
+  const int rs = (t / NB) % 4;
+  const int xr = (t / 32) % (TX / RX);
+  const int yg = t / (32 * (TX / RX));
+  const int yl = yg * 4 + rs, xl0 = xr * RX;
+  const int tile = blockIdx.x;
+  const int chunk = blockIdx.y;
+  const int cta = tile * a.nchunk + chunk;
+  const int tx0 = (tile % a.tiles_x) * TX, ty0 = (tile / a.tiles_x) * TY;
+  const int zs = chunk * ZC;
+  const int ze = min(zs + ZC, a.n3);
+  const int blk = a.blk0 + blockIdx.z;
+  const size_t boff = (size_t)blk * a.nd * NB;
+  const T* Y = Yin + boff;
+  const int n1 = a.n1, n2 = a.n2, n3 = a.n3;
+  const long long plane_el = (long long)n1 * n2 * NB;   // elements per z-plane of a block
+  const int gy = ty0 + yl;
+  const bool vy = gy < n2;
+  const int txv = min(TX, n1 - tx0), tyv = min(TY, n2 - ty0);
+  bool vr[RX];
+#pragma unroll
+  for (int r = 0; r < RX; ++r) vr[r] = vy && (tx0 + xl0 + r < n1);
+
+  // ---- CTA tables: projector pieces (compact), their coefficients, per-(z, rows) activations
+  const int it0 = __ldg(a.cptr + cta), nit = __ldg(a.cptr + cta + 1) - it0;
+  for (int i = t; i < nit; i += THREADS) {
+    const SubBox b = a.sb[__ldg(a.citems + it0 + i)];
+    Piece pc;
+    pc.gy0 = b.gy0; pc.gy1 = b.gy1; pc.gx0 = b.gx0; pc.gx1 = b.gx1;
+    pc.sy = b.nbx;
+    pc.sz = b.nbx * b.nby;
+    pc.base = (int)b.chi4_off + b.bx0 - b.gx0 + b.nbx * (b.by0 - b.gy0) + pc.sz * (b.bz0 - b.gz0);
+    pc.ph_re = b.ph_re; pc.ph_im = b.ph_im;
+    desc[i] = pc;
+    for (int l = 0; l < 4; ++l) {
+      const int p = a.grp[b.grp].proj[l];
+      for (int oo = 0; oo < NB; ++oo)
+        gcs[(i * 4 + l) * NB + oo] = (p >= 0) ? gc[((size_t)p * a.nblk_total + blk) * NB + oo] : FT<T>::zero();
+    }
+  }
+  const size_t sb0 = (size_t)cta * ZC * NRG;
+  const int s0 = __ldg(a.sptr + sb0);
+  for (int k = t; k <= ZC * NRG; k += THREADS) steps[k] = __ldg(a.sptr + sb0 + k) - s0;
+  const int nst = __ldg(a.sptr + sb0 + ZC * NRG) - s0;
+  for (int k = t; k < nst; k += THREADS) steps[ZC * NRG + 1 + k] = __ldg(a.sslots + s0 + k);
+
+  // ---- per-thread copy descriptors (the same for every plane up to the z offset)
+  // hs: smem element offset in bits 0..19 and the face crossings (tx + 1) + 3 (ty + 1)
+  // in bits 20..23 (-1: no chunk); hg: in-plane global element offset
+  int hs[NHC], hg[NHC];
+#pragma unroll
+  for (int i = 0; i < NHC; ++i) {
+    const int idx = t + i * THREADS;
+    hs[i] = -1; hg[i] = 0;
+    if (idx < PX * PY * CH) {
+      const int pnt = idx / CH, ch = idx % CH;
+      const int sx = pnt % PX, sy = pnt / PX;
+      const int lx = sx - R, ly = sy - R;
+      if (!(lx >= 0 && lx < txv && ly >= 0 && ly < tyv)) {
+        int gxw = tx0 + lx, gyw = ty0 + ly;
+        const int tx = wrap(gxw, n1), ty = wrap(gyw, n2);
+        hs[i] = (sy * RP + sx * NB + ch * EPC) | (((tx + 1) + 3 * (ty + 1)) << 20);
+        hg[i] = (gyw * n1 + gxw) * NB + ch * EPC;
+      }
+    }
+  }
+  int ps[NPC], pg[NPC];   // Y_{j-1} chunks: smem and in-plane global element offsets
+#pragma unroll
+  for (int i = 0; i < NPC; ++i) {
+    const int idx = t + i * THREADS;
+    ps[i] = -1; pg[i] = 0;
+    if (idx < TX * TY * CH) {
+      const int node = idx / CH, ch = idx % CH;
+      const int lx = node % TX, ly = node / TX;
+      if (lx < txv && ly < tyv) {
+        ps[i] = node * NB + ch * EPC;
+        pg[i] = ((ty0 + ly) * n1 + tx0 + lx) * NB + ch * EPC;
+      }
+    }
+  }
+  const int vlx = t % TX, vly = t / TX;
+  const bool vv = t < TX * TY && vlx < txv && vly < tyv;
+  const int vg = (ty0 + vly) * n1 + tx0 + vlx;
+
+  // ---- queue of the thread's nodes at z-R .. z+R (q[i] holds z - R + i)
+  T q[Q][RX];
+  auto load_z = [&](int zz, T* dst) {
+    int zw = zz;
+    const int tz = wrap(zw, n3);
+    float pr = 1.f, pi = 0.f;
+    if (FT<T>::cplx && tz != 0) phase_pow(a.phz_r, a.phz_i, tz, pr, pi);
+    const T* src = Y + (size_t)zw * plane_el + ((size_t)gy * n1 + tx0 + xl0) * NB + o;
+#pragma unroll
+    for (int r = 0; r < RX; ++r) dst[r] = vr[r] ? FT<T>::phase(fld(src + r * NB), pr, pi) : FT<T>::zero();
+  };
+#pragma unroll
+  for (int i = 0; i < Q; ++i) load_z(zs - R + i, q[i]);
+
+  auto issue = [&](int zz, int b) {
+    int zw = zz;
+    wrap(zw, n3);
+    T* P = planes + (size_t)b * PY * RP;
+    const T* Yz = Y + (size_t)zw * plane_el;
+#pragma unroll
+    for (int i = 0; i < NHC; ++i)
+      if (hs[i] >= 0) cp16(P + (hs[i] & 0xFFFFF), Yz + hg[i]);
+    if (vv) cp4(vbs + (size_t)b * TY * TX + t, a.veff + (size_t)zw * n1 * n2 + vg);
+    if (Yprev != nullptr) {
+      T* Pp = yps + (size_t)b * TY * TX * NB;
+      const T* Yp = Yprev + boff + (size_t)zw * plane_el;
+#pragma unroll
+      for (int i = 0; i < NPC; ++i)
+        if (ps[i] >= 0) cp16(Pp + ps[i], Yp + pg[i]);
+    }
+  };
+  auto fixup = [&](int zz, int b) {   // Bloch phase of halo copies that crossed a face
+    if constexpr (FT<T>::cplx) {
+      int zw = zz;
+      const int tz = wrap(zw, n3);
+      T* P = planes + (size_t)b * PY * RP;
+#pragma unroll
+      for (int i = 0; i < NHC; ++i) {
+        const int hw = hs[i] >> 20;
+        if (hs[i] < 0 || (hw == 4 && tz == 0)) continue;
+        float pr, pi, qr, qi, rr, ri;
+        phase_pow(a.phx_r, a.phx_i, hw % 3 - 1, pr, pi);
+        phase_pow(a.phy_r, a.phy_i, hw / 3 - 1, qr, qi);
+        phase_pow(a.phz_r, a.phz_i, tz, rr, ri);
+        const float ar = pr * qr - pi * qi, ai = pr * qi + pi * qr;
+        const float br = ar * rr - ai * ri, bi = ar * ri + ai * rr;
+        float4* c = reinterpret_cast<float4*>(P + (hs[i] & 0xFFFFF));
+        const float4 v = *c;
+        *c = make_float4(v.x * br - v.y * bi, v.x * bi + v.y * br, v.z * br - v.w * bi, v.z * bi + v.w * br);
+      }
+    }
+  };
+  auto own = [&](const T* vals, int b) {
+    T* P = planes + (size_t)b * PY * RP;
+#pragma unroll
+    for (int r = 0; r < RX; ++r)
+      if (vr[r]) P[(yl + R) * RP + (xl0 + r + R) * NB + o] = vals[r];
+  };
+
+  issue(zs, 0);
+  cp_commit();
+  if (zs + 1 < ze) issue(zs + 1, 1);
+  cp_commit();
+  own(q[R], 0);
+  cp_wait1();
+  fixup(zs, 0);
+  __syncthreads();
+
+  for (int z = zs; z < ze; ++z) {
+    const int sidx = z - zs;
+    const int b = sidx % 3;
+    const T* P = planes + (size_t)b * PY * RP;
+    if (vy) {
+      T acc[RX];
+      const T* row = P + (yl + R) * RP + o;
+      // x window in registers for real data; complex data reads x neighbours from
+      // shared memory directly (the register queue already holds 2 floats per value)
+      constexpr int NW = FT<T>::cplx ? 1 : RX + 2 * R;
+      T w[NW];
+      if constexpr (!FT<T>::cplx) {
+#pragma unroll
+        for (int i = 0; i < NW; ++i) w[i] = row[(xl0 + i) * NB];
+      }
+      const float* V = vbs + (size_t)b * TY * TX + yl * TX + xl0;
+#pragma unroll
+      for (int r = 0; r < RX; ++r) {
+        const float cc = a.c0 + V[r] - a.shift;
+        T s;
+        if constexpr (FT<T>::cplx) s = cf32{cc * q[R][r].x, cc * q[R][r].y};
+        else s = cc * q[R][r];
+#pragma unroll
+        for (int p = 1; p <= R; ++p) {
+          const T u = P[(yl + R + p) * RP + (xl0 + r + R) * NB + o];
+          const T d = P[(yl + R - p) * RP + (xl0 + r + R) * NB + o];
+          if constexpr (FT<T>::cplx) {
+            const T xp = row[(xl0 + r + R + p) * NB], xm = row[(xl0 + r + R - p) * NB];
+            s.x += a.cx[p] * (xp.x + xm.x);
+            s.y += a.cx[p] * (xp.y + xm.y);
+            s.x += a.cy[p] * (u.x + d.x);
+            s.y += a.cy[p] * (u.y + d.y);
+            s.x += a.cz[p] * (q[R + p][r].x + q[R - p][r].x);
+            s.y += a.cz[p] * (q[R + p][r].y + q[R - p][r].y);
+          } else {
+            s = fmaf(a.cx[p], w[R + r + p] + w[R + r - p], s);
+            s = fmaf(a.cy[p], u + d, s);
+            s = fmaf(a.cz[p], q[R + p][r] + q[R - p][r], s);
+          }
+        }
+        acc[r] = s;
+      }
+      // nonlocal: pieces that touch this warp's 4 rows at z
+      const int ea = steps[sidx * NRG + yg], eb = steps[sidx * NRG + yg + 1];
+      const int x0r = tx0 + xl0;
+      for (int e = ea; e < eb; ++e) {
+        const int it = steps[ZC * NRG + 1 + e];
+        const Piece pc = desc[it];
+        if (gy < pc.gy0 || gy >= pc.gy1) continue;
+        T gv[4];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) gv[l] = gcs[(it * 4 + l) * NB + o];
+        const int rowoff = pc.base + pc.sy * gy + pc.sz * z;
+        float4 c4[RX];
+#pragma unroll
+        for (int r = 0; r < RX; ++r) {
+          const int gx = x0r + r;
+          c4[r] = (gx >= pc.gx0 && gx < pc.gx1) ? __ldg(a.chi4 + rowoff + gx) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int r = 0; r < RX; ++r) {
+          const T d = FT<T>::dot4(c4[r], gv);
+          if constexpr (FT<T>::cplx) {
+            acc[r].x += pc.ph_re * d.x - pc.ph_im * d.y;
+            acc[r].y += pc.ph_re * d.y + pc.ph_im * d.x;
+          } else {
+            acc[r] += d;   // real data: k = 0, the phase is 1
+          }
+        }
+      }
+      // recurrence epilogue
+      const T* Pp = yps + (size_t)b * TY * TX * NB + (yl * TX + xl0) * NB + o;
+      T* out = Yout + boff + (size_t)z * plane_el + ((size_t)gy * n1 + tx0 + xl0) * NB + o;
+#pragma unroll
+      for (int r = 0; r < RX; ++r) {
+        if (!vr[r]) continue;
+        T v;
+        if constexpr (FT<T>::cplx) {
+          v = cf32{a.alpha * acc[r].x, a.alpha * acc[r].y};
+          if (Yprev) { const T pv = Pp[r * NB]; v.x += a.beta * pv.x; v.y += a.beta * pv.y; }
+        } else {
+          v = a.alpha * acc[r];
+          if (Yprev) v = fmaf(a.beta, Pp[r * NB], v);
+        }
+        out[r * NB] = v;
+      }
+    }
+    // pipeline: own nodes of z+1 from the queue, copies for z+2, advance the queue
+    if (z + 1 < ze) own(q[R + 1], (sidx + 1) % 3);
+    if (z + 2 < ze) issue(z + 2, (sidx + 2) % 3);
+    cp_commit();
+#pragma unroll
+    for (int i = 0; i < Q - 1; ++i)
+#pragma unroll
+      for (int r = 0; r < RX; ++r) q[i][r] = q[i + 1][r];
+    load_z(z + R + 1, q[Q - 1]);
+    cp_wait1();
+    if (z + 1 < ze) fixup(z + 1, (sidx + 1) % 3);
+    __syncthreads();
+  }
+}
+
+// gc[p][blk][lane] = gamma_p h^3 sum_{box} conj(chi~_p) Y, one CTA per (group, block).
+// A warp takes whole x-rows of a piece (4 nodes x 8 lanes per step, unrolled).
+template <class T>
+__global__ void __launch_bounds__(512)
+k_gather(const T* __restrict__ Y, long long nd, int n1, int n2, const Group* __restrict__ grp,
+         const SubBox* __restrict__ sbs, const float4* __restrict__ chi4,
+         const float* __restrict__ gamma, float dv, T* __restrict__ gc, int nblk_total, int blk0) {
+  __shared__ T red[512][4];
+  const int gi = blockIdx.x;
+  const int blk = blk0 + blockIdx.y;
+  const int o = threadIdx.x % NB, ng = (threadIdx.x / NB) % 4, warp = threadIdx.x / 32;
+  const Group G = grp[gi];
+  const T* Yb = Y + (size_t)blk * nd * NB;
+  T acc[4] = {FT<T>::zero(), FT<T>::zero(), FT<T>::zero(), FT<T>::zero()};
+  for (int sbi = G.sb0; sbi < G.sb1; ++sbi) {
+    const SubBox b = sbs[sbi];
+    const int wx = b.gx1 - b.gx0, wy = b.gy1 - b.gy0, wz = b.gz1 - b.gz0;
+    T s[4] = {FT<T>::zero(), FT<T>::zero(), FT<T>::zero(), FT<T>::zero()};
+    for (int row = warp; row < wy * wz; row += 16) {
+      const int iy = row % wy, iz = row / wy;
+      const long long yrow = ((long long)(b.gz0 + iz) * n2 + (b.gy0 + iy)) * n1 + b.gx0;
+      const long long crow = b.chi4_off + b.bx0 + (long long)b.nbx * ((b.by0 + iy) + (long long)b.nby * (b.bz0 + iz));
+#pragma unroll 4
+      for (int ix = ng; ix < wx; ix += 4) {
+        const float4 c4 = __ldg(chi4 + crow + ix);
+        const T y = fld(Yb + (size_t)(yrow + ix) * NB + o);
+        if constexpr (FT<T>::cplx) {
+          s[0].x += c4.x * y.x; s[0].y += c4.x * y.y;
+          s[1].x += c4.y * y.x; s[1].y += c4.y * y.y;
+          s[2].x += c4.z * y.x; s[2].y += c4.z * y.y;
+          s[3].x += c4.w * y.x; s[3].y += c4.w * y.y;
+        } else {
+          s[0] = fmaf(c4.x, y, s[0]); s[1] = fmaf(c4.y, y, s[1]);
+          s[2] = fmaf(c4.z, y, s[2]); s[3] = fmaf(c4.w, y, s[3]);
+        }
+      }
+    }
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {   // conj(phase) of this piece
+      if constexpr (FT<T>::cplx) {
+        acc[l].x += b.ph_re * s[l].x + b.ph_im * s[l].y;
+        acc[l].y += b.ph_re * s[l].y - b.ph_im * s[l].x;
+      } else {
+        acc[l] += b.ph_re * s[l];
+      }
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < 4; ++l) red[threadIdx.x][l] = acc[l];
+  __syncthreads();
+  for (int st = 256; st >= NB; st >>= 1) {
+    if (threadIdx.x < st)
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        if constexpr (FT<T>::cplx) {
+          red[threadIdx.x][l].x += red[threadIdx.x + st][l].x;
+          red[threadIdx.x][l].y += red[threadIdx.x + st][l].y;
+        } else {
+          red[threadIdx.x][l] += red[threadIdx.x + st][l];
+        }
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x < NB) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      const int p = G.proj[l];
+      if (p < 0) continue;
+      const float f = gamma[p] * dv;
+      T v = red[threadIdx.x][l];
+      if constexpr (FT<T>::cplx) v = cf32{f * v.x, f * v.y};
+      else v = f * v;
+      gc[((size_t)p * nblk_total + blk) * NB + o] = v;
+    }
+  }
+}
+
+// --------------------------------------------------------------------------- launchers
+
+template <class T>
+cudaError_t launch_gather(const sparc_ham* H, const T* Y, int nblk_total, int blk0, int nb, T* gc,
+                          cudaStream_t st) {
+  const Tables* Tb = (const Tables*)H->fast;
+  if (H->nproj == 0 || Tb->ngrp == 0) return cudaSuccess;
+  const float dv = (float)(H->grid.h[0] * H->grid.h[1] * H->grid.h[2]);
+  cudaEvent_t t0 = timing_begin(H->ctx, st);
+  k_gather<T><<<dim3((unsigned)Tb->ngrp, (unsigned)nb), 512, 0, st>>>(
+      Y, H->gd.nd, H->gd.n1, H->gd.n2, Tb->d_grp, Tb->d_sb, (const float4*)Tb->d_chi4, H->d_gamma32,
+      dv, gc, nblk_total, blk0);
+  ++H->ctx->launches;
+  timing_end(H->ctx, TK_GATHER, t0, st);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_pass(const sparc_ham* H, const T* Yin, const T* Yprev, T* Yout, const T* gc,
+                        int nblk_total, int blk0, int nb, double alpha, double shift, double beta,
+                        cudaStream_t st) {
+  const Tables* Tb = (const Tables*)H->fast;
+  const Layout& Lo = Tb->lay[FT<T>::cplx ? 1 : 0];
+  PassArgs a;
+  a.nd = H->gd.nd;
+  a.n1 = H->gd.n1; a.n2 = H->gd.n2; a.n3 = H->gd.n3;
+  a.tiles_x = Lo.tiles_x;
+  a.nchunk = Lo.nchunk;
+  a.blk0 = blk0;
+  a.nblk_total = nblk_total;
+  for (int p = 0; p <= R; ++p) {
+    a.cx[p] = (float)H->gd.coef[0][p];
+    a.cy[p] = (float)H->gd.coef[1][p];
+    a.cz[p] = (float)H->gd.coef[2][p];
+  }
+  a.c0 = (float)(2.0 * (H->gd.coef[0][0] + H->gd.coef[1][0] + H->gd.coef[2][0]));
+  a.phx_r = (float)H->gd.ph_re[0]; a.phx_i = (float)H->gd.ph_im[0];
+  a.phy_r = (float)H->gd.ph_re[1]; a.phy_i = (float)H->gd.ph_im[1];
+  a.phz_r = (float)H->gd.ph_re[2]; a.phz_i = (float)H->gd.ph_im[2];
+  a.alpha = (float)alpha; a.shift = (float)shift; a.beta = (float)beta;
+  a.veff = H->d_veff32;
+  a.cptr = Lo.d_cptr; a.citems = Lo.d_citems; a.sptr = Lo.d_sptr; a.sslots = Lo.d_sslots;
+  a.sb = Tb->d_sb; a.grp = Tb->d_grp;
+  a.chi4 = (const float4*)Tb->d_chi4;
+  const size_t smem = Smem<T>::total;
+  cudaError_t e = cudaFuncSetAttribute(k_pass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)(Lo.tiles_x * Lo.tiles_y), (unsigned)Lo.nchunk, (unsigned)nb);
+  cudaEvent_t t0 = timing_begin(H->ctx, st);
+  k_pass<T><<<grid, THREADS, smem, st>>>(a, Yin, Yprev, Yout, gc);
+  ++H->ctx->launches;
+  timing_end(H->ctx, TK_HPASS, t0, st);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_gather<float>(const sparc_ham*, const float*, int, int, int, float*, cudaStream_t);
+template cudaError_t launch_gather<cf32>(const sparc_ham*, const cf32*, int, int, int, cf32*, cudaStream_t);
+template cudaError_t launch_pass<float>(const sparc_ham*, const float*, const float*, float*, const float*,
+                                        int, int, int, double, double, double, cudaStream_t);
+template cudaError_t launch_pass<cf32>(const sparc_ham*, const cf32*, const cf32*, cf32*, const cf32*,
+                                       int, int, int, double, double, double, cudaStream_t);
+
+}  // namespace fast
+}  // namespace sparc

@@ -5,6 +5,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <tuple>
 #include <vector>
 
 #include "rr.cuh"
@@ -32,8 +34,8 @@ template <class T> __device__ __forceinline__ T zero_of() { return Tr<T>::zero()
 template <class TA, class TB, class TC, class TO, bool ACT, bool BCT>
 __global__ void __launch_bounds__(256)
 k_gemm(int M, int N, int K, const TA* __restrict__ A, long long lda, const TB* __restrict__ B,
-       long long ldb, TO* __restrict__ C, long long ldc, long long cstride, int kchunk,
-       double alpha) {
+       long long ldb, TO* C, long long ldc, long long cstride, int kchunk,
+       double alpha, double beta) {
   using TW = typename Wide<TC>::W;
   constexpr int KF = (sizeof(typename Tr<TC>::R) == 4) ? 16 : 1 << 30;
   __shared__ TC As[16][65];
@@ -105,20 +107,22 @@ k_gemm(int M, int N, int K, const TA* __restrict__ A, long long lda, const TB* _
     for (int j = 0; j < 4; ++j) {
       const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
       if (m < M && n < N) {
-        TW v = add(accw[i][j], widen(acc[i][j]));
-        Cz[m + (long long)n * ldc] = narrow_to((TO*)nullptr, scale(alpha, v));
+        TW v = scale(alpha, add(accw[i][j], widen(acc[i][j])));
+        if (beta != 0.0) v = add(v, scale(beta, widen(Cz[m + (long long)n * ldc])));
+        Cz[m + (long long)n * ldc] = narrow_to((TO*)nullptr, v);
       }
     }
 }
 
 template <class TA, class TB, class TC, class TO, bool ACT, bool BCT>
 cudaError_t gemm(sparc_ctx* ctx, int M, int N, int K, const TA* A, long long lda, const TB* B, long long ldb, TO* C,
-                 long long ldc, int nsplit, long long cstride, double alpha, cudaStream_t st) {
+                 long long ldc, int nsplit, long long cstride, double alpha, cudaStream_t st,
+                 double beta = 0.0) {
   int kchunk = (int)(((long long)K + nsplit - 1) / nsplit);
   kchunk = (kchunk + 15) / 16 * 16;
   dim3 grid((unsigned)ceil_div(M, 64), (unsigned)ceil_div(N, 64), (unsigned)nsplit);
   k_gemm<TA, TB, TC, TO, ACT, BCT><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, cstride,
-                                                        kchunk, alpha);
+                                                        kchunk, alpha, beta);
   ++ctx->launches;
   return cudaGetLastError();
 }
@@ -205,71 +209,108 @@ __device__ __forceinline__ int rr_player(int pos, int r, int npad) {
   return pos == 0 ? 0 : 1 + (pos - 1 + r) % (npad - 1);
 }
 
-// 2x2 unitary U (entries u[x][y], x,y in {p,q}) that annihilates A_pq:
-// U = diag(1, e^{-i phi}) [[c, s], [-s, c]], e^{i phi} = A_pq/|A_pq|,
-// t = sign(th)/(|th| + sqrt(th^2 + 1)), th = (A_qq - A_pp)/(2|A_pq|), c = 1/sqrt(1+t^2), s = t c.
+// Rotation of pair (p, q): the 2x2 unitary U = diag(1, e^{-i phi}) [[c, s], [-s, c]]
+// with e^{i phi} = A_pq/|A_pq|, t = sign(th)/(|th| + sqrt(th^2 + 1)),
+// th = (A_qq - A_pp)/(2|A_pq|), c = 1/sqrt(1 + t^2), s = t c; it annihilates A_pq.
+// Stored as (c, s, e^{-i phi}); indices >= n (the padding player) give the identity.
 template <class TW>
-__device__ void jacobi_rot(const TW* A, int n, int p, int q, TW u[2][2]) {
-  const TW one = from_real<TW>(1.0);
-  u[0][0] = one; u[0][1] = zero_of<TW>(); u[1][0] = zero_of<TW>(); u[1][1] = one;
-  if (p >= n || q >= n) return;
+struct Rot {
+  typename Tr<TW>::R c, s;
+  TW eph;
+};
+
+template <class TW>
+__device__ Rot<TW> jacobi_rot(const TW* A, int n, int p, int q) {
+  using R = typename Tr<TW>::R;
+  Rot<TW> u;
+  u.c = (R)1; u.s = (R)0; u.eph = from_real<TW>(1.0);
+  if (p >= n || q >= n) return u;
   const TW b = A[p + (long long)q * n];
-  const double ab = sqrt(Tr<TW>::abs2(b));
-  const double a = Tr<TW>::re(A[p + (long long)p * n]);
-  const double d = Tr<TW>::re(A[q + (long long)q * n]);
-  if (ab == 0.0 || ab < 1e-300) return;
-  const double th = (d - a) / (2.0 * ab);
-  const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-  const double c = 1.0 / sqrt(t * t + 1.0);
-  const double s = t * c;
-  const TW eph = Tr<TW>::conj(scale(1.0 / ab, b));   // e^{-i phi}
-  u[0][0] = scale(c, one);
-  u[0][1] = scale(s, one);
-  u[1][0] = scale(-s, eph);
-  u[1][1] = scale(c, eph);
+  const R ab = sqrt(Tr<TW>::abs2(b));
+  if (!(ab > (R)0)) return u;
+  const R a = Tr<TW>::re(A[p + (long long)p * n]);
+  const R d = Tr<TW>::re(A[q + (long long)q * n]);
+  const R th = (d - a) / ((R)2 * ab);
+  const R t = (th >= (R)0 ? (R)1 : (R)-1) / (fabs(th) + sqrt(th * th + (R)1));
+  u.c = (R)1 / sqrt(t * t + (R)1);
+  u.s = t * u.c;
+  u.eph = Tr<TW>::conj(scale((R)1 / ab, b));
+  return u;
 }
 
+// entry (x, y) of the 2x2 block of U for a pair: [[c, s], [-s eph, c eph]]
+template <class TW>
+__device__ __forceinline__ TW rot_entry(const Rot<TW>& u, int x, int y) {
+  using R = typename Tr<TW>::R;
+  if (x == 0) return from_real<TW>(y == 0 ? (double)u.c : (double)u.s);
+  return scale(y == 0 ? -u.s : u.c, u.eph);
+}
+
+// One round of the parallel cyclic Jacobi method: A' = U^H A U (into An), V <- V U.
+// CTAs [0, nta) update 16 x 16 tiles of 2x2 blocks (pair P, pair Q) of A; the
+// remaining CTAs update 64 rows x 4 pairs of V.  Each CTA first computes the
+// rotations of the pairs it touches into shared memory.
 template <class TW>
 __global__ void __launch_bounds__(256)
 k_jacobi_round(const TW* __restrict__ A, TW* __restrict__ An, TW* __restrict__ V, int n, int npad,
                int r) {
+  __shared__ Rot<TW> rp[16], rq[16];
+  __shared__ int ip[16][2], iq[16][2];
   const int half = npad / 2;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long nA = (long long)half * half;
-  if (t < nA) {
-    const int P = (int)(t % half), Q = (int)(t / half);
-    const int ip[2] = {rr_player(P, r, npad), rr_player(npad - 1 - P, r, npad)};
-    const int iq[2] = {rr_player(Q, r, npad), rr_player(npad - 1 - Q, r, npad)};
-    TW up[2][2], uq[2][2];
-    jacobi_rot(A, n, ip[0], ip[1], up);
-    jacobi_rot(A, n, iq[0], iq[1], uq);
+  const int tpa = (half + 15) / 16;           // pair tiles per side
+  const int nta = tpa * tpa;
+  const int tid = threadIdx.x;
+  if ((int)blockIdx.x < nta) {
+    const int P0 = (blockIdx.x % tpa) * 16, Q0 = (blockIdx.x / tpa) * 16;
+    if (tid < 32) {
+      const int k = tid % 16;
+      const int Pp = (tid < 16 ? P0 : Q0) + k;
+      int p = n, q = n;
+      if (Pp < half) { p = rr_player(Pp, r, npad); q = rr_player(npad - 1 - Pp, r, npad); }
+      const Rot<TW> u = jacobi_rot(A, n, p, q);
+      if (tid < 16) { rp[k] = u; ip[k][0] = p; ip[k][1] = q; }
+      else { rq[k] = u; iq[k][0] = p; iq[k][1] = q; }
+    }
+    __syncthreads();
+    const int pl = tid % 16, ql = tid / 16;
+    if (P0 + pl >= half || Q0 + ql >= half) return;
+    const int i0 = ip[pl][0], i1 = ip[pl][1], j0 = iq[ql][0], j1 = iq[ql][1];
+    const int ii[2] = {i0, i1}, jj[2] = {j0, j1};
     TW a[2][2];
     for (int x = 0; x < 2; ++x)
       for (int y = 0; y < 2; ++y)
-        a[x][y] = (ip[x] < n && iq[y] < n) ? A[ip[x] + (long long)iq[y] * n] : zero_of<TW>();
+        a[x][y] = (ii[x] < n && jj[y] < n) ? A[ii[x] + (long long)jj[y] * n] : zero_of<TW>();
     for (int aa = 0; aa < 2; ++aa)
       for (int bb = 0; bb < 2; ++bb) {
-        if (ip[aa] >= n || iq[bb] >= n) continue;
+        if (ii[aa] >= n || jj[bb] >= n) continue;
         TW s = zero_of<TW>();
         for (int x = 0; x < 2; ++x)
           for (int y = 0; y < 2; ++y)
-            s = s + mul(Tr<TW>::conj(up[x][aa]), mul(a[x][y], uq[y][bb]));
-        An[ip[aa] + (long long)iq[bb] * n] = s;
+            s = s + mul(Tr<TW>::conj(rot_entry(rp[pl], x, aa)), mul(a[x][y], rot_entry(rq[ql], y, bb)));
+        An[ii[aa] + (long long)jj[bb] * n] = s;
       }
   } else {
-    const long long t2 = t - nA;
-    if (t2 >= (long long)n * half) return;
-    const int i = (int)(t2 % n), Q = (int)(t2 / n);
-    const int iq[2] = {rr_player(Q, r, npad), rr_player(npad - 1 - Q, r, npad)};
-    TW uq[2][2];
-    jacobi_rot(A, n, iq[0], iq[1], uq);
+    const int vb = blockIdx.x - nta;
+    const int rows = (n + 63) / 64;
+    const int R0 = (vb % rows) * 64, Q0 = (vb / rows) * 4;
+    if (tid < 4) {
+      const int Qq = Q0 + tid;
+      int p = n, q = n;
+      if (Qq < half) { p = rr_player(Qq, r, npad); q = rr_player(npad - 1 - Qq, r, npad); }
+      rq[tid] = jacobi_rot(A, n, p, q);
+      iq[tid][0] = p; iq[tid][1] = q;
+    }
+    __syncthreads();
+    const int i = R0 + tid % 64, ql = tid / 64;
+    if (i >= n || Q0 + ql >= half) return;
+    const int jj[2] = {iq[ql][0], iq[ql][1]};
     TW v[2];
-    for (int y = 0; y < 2; ++y) v[y] = (iq[y] < n) ? V[i + (long long)iq[y] * n] : zero_of<TW>();
+    for (int y = 0; y < 2; ++y) v[y] = (jj[y] < n) ? V[i + (long long)jj[y] * n] : zero_of<TW>();
     for (int bb = 0; bb < 2; ++bb) {
-      if (iq[bb] >= n) continue;
+      if (jj[bb] >= n) continue;
       TW s = zero_of<TW>();
-      for (int y = 0; y < 2; ++y) s = fmac(s, v[y], uq[y][bb]);
-      V[i + (long long)iq[bb] * n] = s;
+      for (int y = 0; y < 2; ++y) s = fmac(s, v[y], rot_entry(rq[ql], y, bb));
+      V[i + (long long)jj[bb] * n] = s;
     }
   }
 }
@@ -303,15 +344,17 @@ __global__ void __launch_bounds__(1024) k_offnorm(const TW* __restrict__ A, int 
 
 // Ascending order of the diagonal: eig[rank] = A_ii, Q[:, rank] = V[:, i]
 // (ties broken by index, so the order is deterministic).
+// vals != nullptr: sort by vals[i] instead of the diagonal of A.
 template <class TW>
-__global__ void __launch_bounds__(1024) k_sort(const TW* __restrict__ A, const TW* __restrict__ V,
-                                               int n, double* __restrict__ eig, TW* __restrict__ Q) {
+__global__ void __launch_bounds__(1024) k_sort(const TW* __restrict__ A, const double* __restrict__ vals,
+                                               const TW* __restrict__ V, int n, double* __restrict__ eig,
+                                               TW* __restrict__ Q) {
   __shared__ int perm[1024];
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double li = Tr<TW>::re(A[i + (long long)i * n]);
+    const double li = vals ? vals[i] : (double)Tr<TW>::re(A[i + (long long)i * n]);
     int rank = 0;
     for (int j = 0; j < n; ++j) {
-      const double lj = Tr<TW>::re(A[j + (long long)j * n]);
+      const double lj = vals ? vals[j] : (double)Tr<TW>::re(A[j + (long long)j * n]);
       if (lj < li || (lj == li && j < i)) ++rank;
     }
     perm[rank] = i;
@@ -330,10 +373,190 @@ __global__ void k_narrow(const TW* __restrict__ a, T* __restrict__ b, long long 
   if (t < n) b[t] = narrow_to((T*)nullptr, a[t]);
 }
 
+// ------------------------------------------------------------------ blocked FP64 Cholesky pieces
+constexpr int CB = 64;   // Cholesky / inverse block
+
+// dst (M x N, ldd) = src (M x N, lds)
+template <class TW>
+__global__ void k_copy2d(const TW* __restrict__ src, long long lds, TW* __restrict__ dst, long long ldd,
+                         int M, int N) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)M * N) return;
+  const int i = (int)(t % M), j = (int)(t / M);
+  dst[i + (long long)j * ldd] = src[i + (long long)j * lds];
+}
+
+template <class TW>
+__global__ void k_fill0(TW* a, long long n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) a[t] = zero_of<TW>();
+}
+
+// C = alpha * sum_z P[z] + beta * C  (M x N; partials packed with leading dimension M)
+template <class TW>
+__global__ void k_reduce_axpby(const TW* __restrict__ P, int nz, int M, int N, double alpha, double beta,
+                               TW* C, long long ldc) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)M * N) return;
+  const int i = (int)(t % M), j = (int)(t / M);
+  TW v = zero_of<TW>();
+  for (int z = 0; z < nz; ++z) v = add(v, P[(long long)z * M * N + t]);
+  v = scale(alpha, v);
+  if (beta != 0.0) v = add(v, scale(beta, C[i + (long long)j * ldc]));
+  C[i + (long long)j * ldc] = v;
+}
+
+// lam[i] = Re(q_i^H z_i) / Re(q_i^H q_i)   (FP64 Rayleigh quotients, one column per thread)
+template <class TW>
+__global__ void k_rayleigh(const TW* __restrict__ Qm, const TW* __restrict__ Z, int n, double* lam) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double num = 0.0, den = 0.0;
+  for (int k = 0; k < n; ++k) {
+    const TW q = Qm[k + (long long)i * n];
+    num += Tr<TW>::re(mul(Tr<TW>::conj(q), Z[k + (long long)i * n]));
+    den += Tr<TW>::abs2(q);
+  }
+  lam[i] = num / den;
+}
+
+template <class TA, class TB>
+__global__ void k_convert(const TA* __restrict__ a, TB* __restrict__ b, long long n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) b[t] = narrow_to((TB*)nullptr, widen(a[t]));
+}
+
+template <class T> struct Narrow;
+template <> struct Narrow<double> { using N = float; };
+template <> struct Narrow<cf64> { using N = cf32; };
+
+// FP64 GEMM spread over the GPU: split K when the output has few tiles.
+// C = alpha op(A) op(B) + beta C; `part` holds up to `cap` elements of partials.
+template <class TW, bool ACT, bool BCT>
+cudaError_t gemm64(sparc_ctx* ctx, int M, int N, int K, const TW* A, long long lda, const TW* B, long long ldb,
+                   TW* C, long long ldc, double alpha, double beta, TW* part, long long cap, cudaStream_t st) {
+  const int tiles = ceil_div(M, 64) * ceil_div(N, 64);
+  int nz = std::max(1, std::min(ceil_div(2 * 152, tiles), K / 64));
+  while (nz > 1 && (long long)nz * M * N > cap) --nz;
+  if (nz == 1) return gemm<TW, TW, TW, TW, ACT, BCT>(ctx, M, N, K, A, lda, B, ldb, C, ldc, 1, 0, alpha, st, beta);
+  cudaError_t e = gemm<TW, TW, TW, TW, ACT, BCT>(ctx, M, N, K, A, lda, B, ldb, part, M, nz, (long long)M * N, 1.0, st);
+  if (e != cudaSuccess) return e;
+  k_reduce_axpby<TW><<<ceil_div((long long)M * N, 256), 256, 0, st>>>(part, nz, M, N, alpha, beta, C, ldc);
+  ++ctx->launches;
+  return cudaGetLastError();
+}
+
+// Blocked right-looking Cholesky of the n x n Hermitian A (lower factor in place)
+// and L^-1 into Li; Dinv receives the inverted diagonal blocks.
+template <class TW>
+sparc_status chol_inverse(sparc_ctx* ctx, TW* A, TW* Li, int n, TW* Dinv, TW* tmp, TW* part, long long cap,
+                          cudaStream_t st) {
+  const int nbk = ceil_div(n, CB);
+  for (int kblk = 0; kblk < nbk; ++kblk) {
+    const int k0 = kblk * CB, kb = std::min(CB, n - k0);
+    TW* Dk = Dinv + (size_t)kblk * CB * CB;
+    TW* Akk = A + k0 + (long long)k0 * n;
+    // diagonal block: contiguous copy, one-CTA factor and inverse, copies back
+    TW* blk = part;                     // kb x kb, leading dimension kb
+    TW* blki = part + (size_t)CB * CB;  // its inverse
+    k_copy2d<TW><<<ceil_div((long long)kb * kb, 256), 256, 0, st>>>(Akk, n, blk, kb, kb, kb);
+    k_chol<TW><<<1, 1024, 0, st>>>(blk, kb, ctx->d_status);
+    k_trinv<TW><<<1, 1024, 0, st>>>(blk, blki, kb);
+    k_copy2d<TW><<<ceil_div((long long)kb * kb, 256), 256, 0, st>>>(blk, kb, Akk, n, kb, kb);
+    k_copy2d<TW><<<ceil_div((long long)kb * kb, 256), 256, 0, st>>>(blki, kb, Dk, CB, kb, kb);
+    ctx->launches += 5;
+    SPARC_LAUNCH(ctx, "cholesky block");
+    const int m2 = n - k0 - kb;
+    if (m2 > 0) {
+      // T = A21 L_kk^-H ; A22 -= T T^H ; A21 = T
+      SPARC_CUDA(ctx, (gemm64<TW, false, true>(ctx, m2, kb, kb, A + (k0 + kb) + (long long)k0 * n, n, Dk, CB,
+                                               tmp, m2, 1.0, 0.0, part, cap, st)));
+      SPARC_CUDA(ctx, (gemm64<TW, false, true>(ctx, m2, m2, kb, tmp, m2, tmp, m2,
+                                               A + (k0 + kb) + (long long)(k0 + kb) * n, n, -1.0, 1.0, part, cap, st)));
+      k_copy2d<TW><<<ceil_div((long long)m2 * kb, 256), 256, 0, st>>>(tmp, m2, A + (k0 + kb) + (long long)k0 * n, n, m2, kb);
+      ++ctx->launches;
+    }
+  }
+  // L^-1 by block rows: Li_ij = -Dinv_i (sum_{k<i} L_ik Li_kj)
+  k_fill0<TW><<<ceil_div((long long)n * n, 256), 256, 0, st>>>(Li, (long long)n * n);
+  ++ctx->launches;
+  SPARC_LAUNCH(ctx, "inverse init");
+  for (int iblk = 0; iblk < nbk; ++iblk) {
+    const int i0 = iblk * CB, ib = std::min(CB, n - i0);
+    TW* Di = Dinv + (size_t)iblk * CB * CB;
+    k_copy2d<TW><<<ceil_div((long long)ib * ib, 256), 256, 0, st>>>(Di, CB, Li + i0 + (long long)i0 * n, n, ib, ib);
+    ++ctx->launches;
+    if (i0 > 0) {
+      SPARC_CUDA(ctx, (gemm64<TW, false, false>(ctx, ib, i0, i0, A + i0, n, Li, n, tmp, ib, 1.0, 0.0, part, cap, st)));
+      SPARC_CUDA(ctx, (gemm64<TW, false, false>(ctx, ib, i0, ib, Di, CB, tmp, ib, Li + i0, n, -1.0, 0.0, part, cap, st)));
+    }
+  }
+  SPARC_LAUNCH(ctx, "triangular inverse");
+  return SPARC_OK;
+}
+
+// Parallel cyclic Jacobi on the n x n Hermitian A (ping-pong A0/A1, eigenvectors in V),
+// two sweeps per replay of a captured CUDA graph, until off(A) <= tol * |A|.
+template <class TJ>
+sparc_status jacobi(sparc_ctx* ctx, TJ* A0, TJ* A1, TJ* V, int n, double tol, int max_sweeps, double* scal,
+                    TJ** result, int* sweeps_out, cudaStream_t st) {
+  const int npad = n + (n & 1);
+  const int half = npad / 2;
+  const int nblocks = ((half + 15) / 16) * ((half + 15) / 16) + ((n + 63) / 64) * ((half + 3) / 4);
+  const int rounds = 2 * (npad - 1);
+  if (!ctx->cap_stream) {
+    SPARC_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  }
+  const auto key = std::make_tuple((int)sizeof(TJ) * 2 + (int)Tr<TJ>::cplx, n, (void*)A0, (void*)A1, (void*)V);
+  cudaGraphExec_t ge = nullptr;
+  auto it = ctx->graphs.find(key);
+  if (it != ctx->graphs.end()) {
+    ge = it->second;
+  } else {
+    cudaGraph_t g = nullptr;
+    SPARC_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    TJ* a = A0;
+    TJ* b = A1;
+    for (int r = 0; r < rounds; ++r) {
+      k_jacobi_round<TJ><<<nblocks, 256, 0, ctx->cap_stream>>>(a, b, V, n, npad, r % (npad - 1));
+      std::swap(a, b);
+    }
+    SPARC_CUDA(ctx, cudaStreamEndCapture(ctx->cap_stream, &g));
+    cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    SPARC_CUDA(ctx, e);
+    ctx->graphs[key] = ge;
+  }
+  double hs[2];
+  double prev_off = -1.0;
+  int sweeps = 0;
+  bool converged = false;
+  cudaEvent_t tj = timing_begin(ctx, st);
+  while (sweeps < max_sweeps && !converged) {
+    SPARC_CUDA(ctx, cudaGraphLaunch(ge, st));
+    ctx->launches += rounds;
+    sweeps += 2;
+    k_offnorm<TJ><<<1, 1024, 0, st>>>(A0, n, scal);
+    ++ctx->launches;
+    SPARC_CUDA(ctx, cudaMemcpyAsync(hs, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SPARC_CUDA(ctx, cudaStreamSynchronize(st));
+    // converged, or stagnated at the rounding floor of the element type (Jacobi
+    // converges quadratically, so two sweeps that do not halve off(A) are at the floor)
+    converged = !(hs[0] > tol * hs[1]) || (sweeps >= 4 && prev_off >= 0.0 && hs[0] > 0.5 * prev_off);
+    prev_off = hs[0];
+  }
+  timing_end(ctx, TK_JAC, tj, st);
+  *result = A0;   // an even number of rounds leaves the matrix in A0
+  *sweeps_out = sweeps;
+  if (!converged) return fail(ctx, SPARC_ERR_NO_CONVERGENCE, "Jacobi sweep limit reached");
+  return SPARC_OK;
+}
+
 // ------------------------------------------------------------------ driver
 template <class T, class TC>
-sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig, cudaStream_t st) {
+sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig, bool mixed, cudaStream_t st) {
   using TW = typename Wide<T>::W;
+  using TS = typename Narrow<TW>::N;
   sparc_ctx* ctx = H->ctx;
   const long long nd = H->gd.nd;
   const size_t es = sizeof(T), ew = sizeof(TW);
@@ -343,8 +566,12 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
   nsplit = std::min<long long>(nsplit, std::max<long long>(1, nd / 64));
   const size_t hub = align256((size_t)nd * ns * es);
   const size_t sm = align256((size_t)nn * ew);
-  const size_t partb = align256((size_t)nsplit * nn * ew);
-  const size_t extra = hub + 2 * partb + 10 * sm + align256(nn * es) + 256;
+  // split-K partials; also the diagonal-block scratch of the Cholesky (2 * CB * CB)
+  const size_t partb = align256((size_t)std::max<long long>(std::max<long long>(nsplit, 8) * nn, 2LL * CB * CB) * ew);
+  const int nbk = ceil_div(ns, CB);
+  const size_t dinvb = align256((size_t)nbk * CB * CB * ew);
+  const size_t extra = hub + 2 * partb + 10 * sm + dinvb + align256(nn * es) + 3 * align256(nn * sizeof(TS)) +
+                       align256(ns * sizeof(double)) + 256;
   BlockWs w;
   char* tail = nullptr;
   sparc_status s = block_ws(H, DtypeOf<T>::v, ns, extra, &w, &tail);
@@ -362,7 +589,13 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
   TW* Qs = (TW*)tail; tail += sm;
   TW* Yr = (TW*)tail; tail += sm;
   double* scal = (double*)tail; tail += sm;
-  T* YrT = (T*)tail;
+  TW* Dinv = (TW*)tail; tail += dinvb;
+  T* YrT = (T*)tail; tail += align256(nn * es);
+  TS* S0 = (TS*)tail; tail += align256(nn * sizeof(TS));
+  TS* S1 = (TS*)tail; tail += align256(nn * sizeof(TS));
+  TS* SV = (TS*)tail; tail += align256(nn * sizeof(TS));
+  double* lam = (double*)tail;
+  const long long pcap = (long long)(partb / ew);
 
   // 1. HU = H U
   s = apply_block<T>(H, U, HU, ns, ld, st, w);
@@ -371,8 +604,10 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
   cudaEvent_t tg = timing_begin(ctx, st);
   SPARC_CUDA(ctx, (gemm<T, T, TC, TW, true, false>(ctx, ns, ns, (int)nd, U, ld, HU, nd, partH, ns, nsplit,
                                                    nn, 1.0, st)));
+  SPARC_LAUNCH(ctx, "gram H");
   SPARC_CUDA(ctx, (gemm<T, T, TC, TW, true, false>(ctx, ns, ns, (int)nd, U, ld, U, ld, partM, ns, nsplit,
                                                    nn, 1.0, st)));
+  SPARC_LAUNCH(ctx, "gram M");
   k_reduce_sym<TW><<<ceil_div(nn, 256), 256, 0, st>>>(partH, nsplit, nn, ns, Hs);
   ++ctx->launches;
   k_reduce_sym<TW><<<ceil_div(nn, 256), 256, 0, st>>>(partM, nsplit, nn, ns, Ms);
@@ -380,12 +615,9 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
   SPARC_LAUNCH(ctx, "gram");
   timing_end(ctx, TK_GRAM, tg, st);
   cudaEvent_t te = timing_begin(ctx, st);
-  // 3. M~ = L L^H, Linv = L^-1
-  k_chol<TW><<<1, 1024, 0, st>>>(Ms, ns, ctx->d_status);
-  ++ctx->launches;
-  k_trinv<TW><<<1, 1024, 0, st>>>(Ms, Li, ns);
-  ++ctx->launches;
-  SPARC_LAUNCH(ctx, "cholesky");
+  // 3. M~ = L L^H (blocked, FP64) and Linv = L^-1
+  s = chol_inverse<TW>(ctx, Ms, Li, ns, Dinv, T1, partH, pcap, st);
+  if (s != SPARC_OK) return s;
   int word = 0;
   SPARC_CUDA(ctx, cudaMemcpyAsync(&word, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
   SPARC_CUDA(ctx, cudaStreamSynchronize(st));
@@ -393,41 +625,43 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
     cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st);
     return fail(ctx, SPARC_ERR_NOT_POSDEF, "M~ = U^H U is not positive definite");
   }
-  // 4. C = Linv H~ Linv^H (symmetrised)
-  SPARC_CUDA(ctx, (gemm<TW, TW, TW, TW, false, false>(ctx, ns, ns, ns, Li, ns, Hs, ns, T1, ns, 1, 0, 1.0, st)));
-  SPARC_CUDA(ctx, (gemm<TW, TW, TW, TW, false, true>(ctx, ns, ns, ns, T1, ns, Li, ns, partH, ns, 1, 0, 1.0, st)));
-  k_reduce_sym<TW><<<ceil_div(nn, 256), 256, 0, st>>>(partH, 1, nn, ns, A0);
+  // 4. C = Linv H~ Linv^H (symmetrised) into A0
+  SPARC_CUDA(ctx, (gemm64<TW, false, false>(ctx, ns, ns, ns, Li, ns, Hs, ns, T1, ns, 1.0, 0.0, partH, pcap, st)));
+  SPARC_CUDA(ctx, (gemm64<TW, false, true>(ctx, ns, ns, ns, T1, ns, Li, ns, Yr, ns, 1.0, 0.0, partH, pcap, st)));
+  k_reduce_sym<TW><<<ceil_div(nn, 256), 256, 0, st>>>(Yr, 1, nn, ns, A0);
   ++ctx->launches;
-  // 5. Jacobi sweeps on C
-  k_identity<TW><<<ceil_div(nn, 256), 256, 0, st>>>(Vj, ns);
-  ++ctx->launches;
-  SPARC_LAUNCH(ctx, "subspace matrix");
-  const int npad = ns + (ns & 1);
-  const long long nthr = (long long)(npad / 2) * (npad / 2) + (long long)ns * (npad / 2);
-  TW* Acur = A0;
-  TW* Anext = A1;
-  bool converged = false;
-  double hs[2];
-  for (int sweep = 0; sweep < 40 && !converged; ++sweep) {
-    for (int r = 0; r < npad - 1; ++r) {
-      // copy-through of the entries no thread writes is not needed: every (P, Q)
-      // block covers the whole matrix once per round
-      k_jacobi_round<TW><<<ceil_div(nthr, 256), 256, 0, st>>>(Acur, Anext, Vj, ns, npad, r);
-      ++ctx->launches;
-      std::swap(Acur, Anext);
-    }
-    SPARC_LAUNCH(ctx, "jacobi round");
-    k_offnorm<TW><<<1, 1024, 0, st>>>(Acur, ns, scal);
+  int sweeps = 0;
+  if (!mixed) {
+    // 5a. FP64 Jacobi on C; eigenvalues from the converged diagonal
+    k_identity<TW><<<ceil_div(nn, 256), 256, 0, st>>>(Vj, ns);
     ++ctx->launches;
-    SPARC_CUDA(ctx, cudaMemcpyAsync(hs, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    SPARC_CUDA(ctx, cudaStreamSynchronize(st));
-    converged = !(hs[0] > 1e-26 * hs[1]);
+    SPARC_LAUNCH(ctx, "subspace matrix");
+    TW* Ares = nullptr;
+    s = jacobi<TW>(ctx, A0, A1, Vj, ns, 1e-26, 40, scal, &Ares, &sweeps, st);
+    if (s != SPARC_OK) return s;
+    k_sort<TW><<<1, 1024, 0, st>>>(Ares, nullptr, Vj, ns, eig, Qs);
+    ++ctx->launches;
+  } else {
+    // 5b. FP32 Jacobi on C for the eigenvectors, FP64 Rayleigh quotients for the eigenvalues
+    k_convert<TW, TS><<<ceil_div(nn, 256), 256, 0, st>>>(A0, S0, nn);
+    ++ctx->launches;
+    k_identity<TS><<<ceil_div(nn, 256), 256, 0, st>>>(SV, ns);
+    ++ctx->launches;
+    SPARC_LAUNCH(ctx, "subspace matrix");
+    TS* Sres = nullptr;
+    s = jacobi<TS>(ctx, S0, S1, SV, ns, 1e-10, 40, scal, &Sres, &sweeps, st);
+    if (s != SPARC_OK) return s;
+    k_convert<TS, TW><<<ceil_div(nn, 256), 256, 0, st>>>(SV, Vj, nn);
+    ++ctx->launches;
+    SPARC_CUDA(ctx, (gemm64<TW, false, false>(ctx, ns, ns, ns, A0, ns, Vj, ns, T1, ns, 1.0, 0.0, partH, pcap, st)));
+    k_rayleigh<TW><<<ceil_div(ns, 128), 128, 0, st>>>(Vj, T1, ns, lam);
+    ++ctx->launches;
+    k_sort<TW><<<1, 1024, 0, st>>>(nullptr, lam, Vj, ns, eig, Qs);
+    ++ctx->launches;
   }
-  if (!converged) return fail(ctx, SPARC_ERR_NO_CONVERGENCE, "Jacobi sweep limit reached");
-  // 6. ascending order, Ritz vectors of the pencil: Yr = Linv^H Q
-  k_sort<TW><<<1, 1024, 0, st>>>(Acur, Vj, ns, eig, Qs);
-  ++ctx->launches;
-  SPARC_CUDA(ctx, (gemm<TW, TW, TW, TW, true, false>(ctx, ns, ns, ns, Li, ns, Qs, ns, Yr, ns, 1, 0, 1.0, st)));
+  ctx->last_sweeps = sweeps;
+  // 6. Ritz vectors of the pencil: Yr = Linv^H Q
+  SPARC_CUDA(ctx, (gemm64<TW, true, false>(ctx, ns, ns, ns, Li, ns, Qs, ns, Yr, ns, 1.0, 0.0, partH, pcap, st)));
   // 7. rotation U <- U Yr (into HU, then back into U)
   k_narrow<TW, T><<<ceil_div(nn, 256), 256, 0, st>>>(Yr, YrT, nn);
   ++ctx->launches;
@@ -468,10 +702,10 @@ extern "C" sparc_status sparc_rayleigh_ritz(sparc_ham* H, sparc_dtype dtype, voi
   if (s != SPARC_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
   switch (dtype) {
-    case SPARC_F64: return rayleigh_ritz<double, double>(H, (double*)U, ns, ld, eig, st);
-    case SPARC_F32: return rayleigh_ritz<float, float>(H, (float*)U, ns, ld, eig, st);
-    case SPARC_C128: return rayleigh_ritz<cf64, cf64>(H, (cf64*)U, ns, ld, eig, st);
-    case SPARC_C64: return rayleigh_ritz<cf32, cf32>(H, (cf32*)U, ns, ld, eig, st);
+    case SPARC_F64: return rayleigh_ritz<double, double>(H, (double*)U, ns, ld, eig, false, st);
+    case SPARC_F32: return rayleigh_ritz<float, float>(H, (float*)U, ns, ld, eig, true, st);
+    case SPARC_C128: return rayleigh_ritz<cf64, cf64>(H, (cf64*)U, ns, ld, eig, false, st);
+    case SPARC_C64: return rayleigh_ritz<cf32, cf32>(H, (cf32*)U, ns, ld, eig, true, st);
   }
   return SPARC_ERR_INVALID_ARG;
 }

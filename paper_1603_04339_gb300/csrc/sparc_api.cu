@@ -1,5 +1,6 @@
 // C ABI of libsparc: contexts, H(k) construction, H-apply and the Chebyshev filter.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -7,9 +8,18 @@
 #include <new>
 
 #include "ham.cuh"
+#include "fast.cuh"
 #include "rr.cuh"
 
 namespace sparc {
+
+bool sync_check() {
+  static const bool on = [] {
+    const char* v = getenv("SPARC_SYNC_CHECK");
+    return v != nullptr && v[0] == '1';
+  }();
+  return on;
+}
 
 sparc_status fail(sparc_ctx* ctx, sparc_status st, const std::string& msg) {
   if (ctx) ctx->last_error = msg;
@@ -196,6 +206,7 @@ sparc_status apply_block(sparc_ham* H, const T* X, T* Y, int ns, long long ld, c
   SPARC_CUDA(H->ctx, launch_hpass<T>(H, b0, nullptr, b1, gc, NB, nblk, 1.0, 0.0, 0.0, true, st));
   SPARC_CUDA(H->ctx, launch_from_blocks<T>(b1, H->gd.nd, nblk, Y, ld, ns, st));
   ++H->ctx->launches;
+  SPARC_LAUNCH(H->ctx, "H apply");
   return SPARC_OK;
 }
 
@@ -226,6 +237,7 @@ sparc_status filter_block(sparc_ham* H, int m, double a, double b, double a0, co
   }
   SPARC_CUDA(H->ctx, launch_from_blocks<T>(cur, H->gd.nd, nblk, Y, ld, ns, st));
   ++H->ctx->launches;
+  SPARC_LAUNCH(H->ctx, "filter");
   return SPARC_OK;
 }
 
@@ -237,6 +249,45 @@ template sparc_status apply_block<cf64>(sparc_ham*, const cf64*, cf64*, int, lon
                                         cudaStream_t, const BlockWs&);
 template sparc_status apply_block<cf32>(sparc_ham*, const cf32*, cf32*, int, long long,
                                         cudaStream_t, const BlockWs&);
+
+// The filter on the tiled FP32 / complex64 kernels.  Blocks are processed in
+// groups whose two live buffers fit in L2 (about 72 MB), all m degrees per
+// group, so that the projection of each degree reads the block from L2.
+template <class T>
+sparc_status filter_block_fast(sparc_ham* H, int m, double a, double b, double a0, const T* X, T* Y,
+                               int ns, long long ld, cudaStream_t st, const BlockWs& w) {
+  const int nblk = ceil_div(ns, NB);
+  T* B0 = (T*)w.b0;
+  T* B1 = (T*)w.b1;
+  T* gc = (T*)w.gc;
+  const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+  const double sigma1 = e / (a0 - c);
+  const size_t per_blk = 2 * (size_t)H->gd.nd * NB * sizeof(T);
+  const int G = std::max(1, (int)((size_t)72 * 1024 * 1024 / per_blk));
+  SPARC_CUDA(H->ctx, launch_to_blocks<T>(X, ld, ns, B0, H->gd.nd, nblk, st));
+  ++H->ctx->launches;
+  T* res = B1;
+  for (int g0 = 0; g0 < nblk; g0 += G) {
+    const int nb = std::min(G, nblk - g0);
+    T* prev = B0;
+    T* cur = B1;
+    double sigma = sigma1;
+    SPARC_CUDA(H->ctx, fast::launch_gather<T>(H, prev, nblk, g0, nb, gc, st));
+    SPARC_CUDA(H->ctx, fast::launch_pass<T>(H, prev, nullptr, cur, gc, nblk, g0, nb, sigma1 / e, c, 0.0, st));
+    for (int j = 1; j < m; ++j) {
+      const double sigma_new = 1.0 / (2.0 / sigma1 - sigma);
+      SPARC_CUDA(H->ctx, fast::launch_gather<T>(H, cur, nblk, g0, nb, gc, st));
+      SPARC_CUDA(H->ctx, fast::launch_pass<T>(H, cur, prev, prev, gc, nblk, g0, nb, 2.0 * sigma_new / e, c,
+                                              -sigma * sigma_new, st));
+      std::swap(cur, prev);
+      sigma = sigma_new;
+    }
+    res = cur;
+  }
+  SPARC_CUDA(H->ctx, launch_from_blocks<T>(res, H->gd.nd, nblk, Y, ld, ns, st));
+  ++H->ctx->launches;
+  return SPARC_OK;
+}
 
 }  // namespace sparc
 
@@ -255,8 +306,9 @@ sparc_status sparc_create(sparc_ctx** out, int device) {
   sparc_ctx* ctx = new (std::nothrow) sparc_ctx();
   if (!ctx) return SPARC_ERR_OOM;
   ctx->device = device;
-  if (cudaSetDevice(device) != cudaSuccess || cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess ||
-      cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) {
+  // status word + 15 words of diagnostics (used only with SPARC_SYNC_CHECK=1)
+  if (cudaSetDevice(device) != cudaSuccess || cudaMalloc(&ctx->d_status, 16 * sizeof(int)) != cudaSuccess ||
+      cudaMemset(ctx->d_status, 0, 16 * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     delete ctx;
     return SPARC_ERR_CUDA;
@@ -271,6 +323,12 @@ sparc_status sparc_timing_enable(sparc_ctx* ctx, int on) {
   SPARC_CUDA(ctx, cudaDeviceSynchronize());
   timing_reset(ctx);
   ctx->timing = (on != 0);
+  return SPARC_OK;
+}
+
+sparc_status sparc_last_sweeps(const sparc_ctx* ctx, int* sweeps) {
+  if (!ctx || !sweeps) return SPARC_ERR_INVALID_ARG;
+  *sweeps = ctx->last_sweeps;
   return SPARC_OK;
 }
 
@@ -301,6 +359,8 @@ void sparc_destroy(sparc_ctx* ctx) {
   cudaDeviceSynchronize();
   timing_reset(ctx);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->d_status) cudaFree(ctx->d_status);
   delete ctx;
@@ -455,6 +515,10 @@ sparc_status sparc_ham_create(sparc_ctx* ctx, const sparc_grid* grid, const doub
       return bail(cuda_fail(ctx, cudaGetLastError(), "projector upload"));
     }
   }
+  {
+    const sparc_status fst = fast::build_tables(H, nl);
+    if (fst != SPARC_OK) return bail(fst);
+  }
   *out = H;
   return SPARC_OK;
 }
@@ -487,6 +551,10 @@ void sparc_ham_destroy(sparc_ham* H) {
   for (int i = 0; i < 4; ++i) {
     if (H->d_p_val[i]) cudaFree(H->d_p_val[i]);
     if (H->d_pt_val[i]) cudaFree(H->d_pt_val[i]);
+  }
+  if (H->fast) {
+    fast::free_tables(*(fast::Tables*)H->fast);
+    delete (fast::Tables*)H->fast;
   }
   delete H;
 }
@@ -528,10 +596,14 @@ sparc_status sparc_cheb_filter(sparc_ham* H, sparc_dtype dtype, int m, double a,
     case SPARC_F64:
       return filter_block<double>(H, m, a, b, a0, (const double*)X, (double*)Y, ns, ld, st, w);
     case SPARC_F32:
+      if (fast::usable(H))
+        return filter_block_fast<float>(H, m, a, b, a0, (const float*)X, (float*)Y, ns, ld, st, w);
       return filter_block<float>(H, m, a, b, a0, (const float*)X, (float*)Y, ns, ld, st, w);
     case SPARC_C128:
       return filter_block<cf64>(H, m, a, b, a0, (const cf64*)X, (cf64*)Y, ns, ld, st, w);
     case SPARC_C64:
+      if (fast::usable(H))
+        return filter_block_fast<cf32>(H, m, a, b, a0, (const cf32*)X, (cf32*)Y, ns, ld, st, w);
       return filter_block<cf32>(H, m, a, b, a0, (const cf32*)X, (cf32*)Y, ns, ld, st, w);
   }
   return SPARC_ERR_INVALID_ARG;

@@ -23,8 +23,8 @@ STATUS = {0: "SPARC_OK", 1: "SPARC_ERR_INVALID_ARG", 2: "SPARC_ERR_OOM", 3: "SPA
 EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_sync", "sparc_ham_create",
            "sparc_ham_set_veff", "sparc_ham_destroy", "sparc_apply_H", "sparc_cheb_filter",
            "sparc_lanczos_bounds", "sparc_rayleigh_ritz", "sparc_timing_enable", "sparc_timing_read",
-           "sparc_launch_count", "sparc_apply_H_noalloc"]
-TIMED = {"hpass": 0, "gather": 1, "gram": 2, "eig": 3, "rotation": 4}
+           "sparc_launch_count", "sparc_apply_H_noalloc", "sparc_last_sweeps"]
+TIMED = {"hpass": 0, "gather": 1, "gram": 2, "eig": 3, "rotation": 4, "jacobi": 5}
 
 
 class SparcGrid(ctypes.Structure):
@@ -75,6 +75,8 @@ def load(path: str = LIB_PATH):
                                       c_void_p]
     L.sparc_timing_enable.argtypes = [c_void_p, c_int]
     L.sparc_launch_count.argtypes = [c_void_p, POINTER(c_int64)]
+    L.sparc_last_sweeps.argtypes = [c_void_p, POINTER(c_int)]
+    L.sparc_last_sweeps.restype = c_int
     L.sparc_apply_H_noalloc.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_int, c_int64, c_void_p]
     L.sparc_apply_H_noalloc.restype = c_int
     L.sparc_launch_count.restype = c_int
@@ -143,6 +145,12 @@ class Context:
         ms, n = c_double(), c_int64()
         self.check(load().sparc_timing_read(self.handle, TIMED[which], ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+    def last_sweeps(self) -> int:
+        """Jacobi sweeps of the last Rayleigh-Ritz call (sparc_last_sweeps)."""
+        n = c_int()
+        self.check(load().sparc_last_sweeps(self.handle, ctypes.byref(n)))
+        return n.value
 
     def launches(self) -> int:
         """Kernels launched by this context so far (sparc_launch_count)."""
