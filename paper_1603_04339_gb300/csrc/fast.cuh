@@ -64,10 +64,12 @@ void free_tables(Tables& t);
 // Whether the tiled kernel handles this Hamiltonian (radius 6, FP32 element types).
 bool usable(const sparc_ham* H);
 
-// gc[p][blk][lane] for the blocks [blk0, blk0 + nb) (gamma_p h^3 chi~_p^H Y).
+// gc[p][blk][lane] for the blocks [blk0, blk0 + nb) (gamma_p h^3 chi~_p^H Y);
+// `scratch` holds gather_scratch_bytes(H, nb, sizeof(T)) bytes of per-slab partial sums.
+size_t gather_scratch_bytes(const sparc_ham* H, int nb, size_t esize);
 template <class T>
 cudaError_t launch_gather(const sparc_ham* H, const T* Y, int nblk_total, int blk0, int nb, T* gc,
-                          cudaStream_t st);
+                          T* scratch, cudaStream_t st);
 // Yout = alpha (H - shift) Yin + beta Yprev for blocks [blk0, blk0 + nb).
 template <class T>
 cudaError_t launch_pass(const sparc_ham* H, const T* Yin, const T* Yprev, T* Yout, const T* gc,

@@ -151,8 +151,10 @@ sparc_status build_tables(sparc_ham* H, const sparc_nonlocal* nl) {
         }
       }
     }
-    // per (CTA, z, group of 4 rows): CTA-local indices of the pieces that touch those rows
-    const int nrg = TYk / 4;
+    // per (CTA, z, row group): CTA-local indices of the pieces that touch those rows;
+    // a row group is the rows one warp covers (8 for FP32, 4 for complex64)
+    const int rgh = (si == 0) ? 8 : 4;
+    const int nrg = TYk / rgh;
     std::vector<int> cptr(nct + 1, 0), citems, sptr((size_t)nct * ZC * nrg + 1, 0), sslots;
     Lo.max_items = 0;
     Lo.max_steps = 0;
@@ -170,7 +172,7 @@ sparc_status build_tables(sparc_ham* H, const sparc_nonlocal* nl) {
         for (int rg = 0; rg < nrg; ++rg) {
           sptr[((size_t)c * ZC + k) * nrg + rg] = (int)sslots.size();
           const int z = z0 + k;
-          const int y0 = y0t + 4 * rg, y1 = std::min(n[1], y0 + 4);
+          const int y0 = y0t + rgh * rg, y1 = std::min(n[1], y0 + rgh);
           if (z < n[2] && y0 < y1)
             for (int j = 0; j < (int)it.size(); ++j) {
               const SubBox& b = sbs[it[j]];
@@ -299,7 +301,7 @@ constexpr int RP = PX * NB + 8;     // row pitch in elements: rows of a warp lan
 template <class T> __host__ __device__ constexpr int plane_rows() { return Shape<T>::TY + 2 * R; }
 template <class T> struct Smem {
   static constexpr int TY = Shape<T>::TY, PY = plane_rows<T>();
-  static constexpr int NRG = TY / 4;
+  static constexpr int NRG = TY / (sizeof(T) == 4 ? 8 : 4);   // row groups of the z lists
   static constexpr size_t planes = 3 * (size_t)PY * RP * sizeof(T);
   static constexpr size_t yprev = 3 * (size_t)TY * TX * NB * sizeof(T);
   static constexpr size_t vb = 3 * (size_t)TY * TX * sizeof(float);
@@ -583,6 +585,243 @@ k_pass(PassArgs a, const T* __restrict__ Yin, const T* Yprev, T* Yout, const T* 
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 pass with orbital pairs: each thread owns 2 x-consecutive nodes x 2
+// orbitals (a float2), so every stencil term is one packed FFMA2/FADD2 and every
+// shared-memory neighbour read is one 64-bit load.  A warp covers 8 rows x 4
+// orbital pairs at one x-run.  CTAs are persistent: they loop over (tile,
+// z-chunk, block) items, so the last wave is not partly empty.
+constexpr int RX2 = 2, TY2 = 16;
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 lds2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+
+__global__ void __launch_bounds__(THREADS, 1)
+k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* Yout,
+          const float* __restrict__ gc, int nitems) {
+  constexpr int Q = 2 * R + 1;
+  constexpr int PY = TY2 + 2 * R;
+  constexpr int CH = 2;                                  // 16-byte chunks per node (8 floats)
+  constexpr int NHC = (PX * PY * CH + THREADS - 1) / THREADS;
+  constexpr int NPC = (TX * TY2 * CH + THREADS - 1) / THREADS;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* planes = reinterpret_cast<float*>(smraw);
+  float* yps = reinterpret_cast<float*>(smraw + Smem<float>::planes);
+  float* vbs = reinterpret_cast<float*>(smraw + Smem<float>::planes + Smem<float>::yprev);
+  Piece* desc = reinterpret_cast<Piece*>(smraw + Smem<float>::planes + Smem<float>::yprev + Smem<float>::vb);
+  float* gcs = reinterpret_cast<float*>(smraw + Smem<float>::planes + Smem<float>::yprev + Smem<float>::vb +
+                                        Smem<float>::desc);
+  int* steps = reinterpret_cast<int*>(smraw + Smem<float>::planes + Smem<float>::yprev + Smem<float>::vb +
+                                      Smem<float>::desc + Smem<float>::gcs);
+  const int t = threadIdx.x;
+  const int op = t % 4;                  // orbital pair
+  const int r8 = (t / 4) % 8;            // row within the warp
+  const int xr = (t / 32) % (TX / RX2);  // x-run
+  const int yg = t / 256;                // row group (0, 1)
+  const int yl = yg * 8 + r8, xl0 = xr * RX2;
+  const int o2 = 2 * op;
+  const int n1 = a.n1, n2 = a.n2, n3 = a.n3;
+  const long long plane_el = (long long)n1 * n2 * NB;
+  const int ntiles = a.tiles_x * ((n2 + TY2 - 1) / TY2);
+  constexpr int NRG = TY2 / 8;   // list row groups (8 rows: one per warp)
+
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int tile = item % ntiles;
+    const int chunk = (item / ntiles) % a.nchunk;
+    const int bi = item / (ntiles * a.nchunk);
+    const int cta = tile * a.nchunk + chunk;
+    const int tx0 = (tile % a.tiles_x) * TX, ty0 = (tile / a.tiles_x) * TY2;
+    const int zs = chunk * ZC;
+    const int ze = min(zs + ZC, n3);
+    const int blk = a.blk0 + bi;
+    const size_t boff = (size_t)blk * a.nd * NB;
+    const float* Y = Yin + boff;
+    const int gy = ty0 + yl;
+    const bool vy = gy < n2;
+    const int txv = min(TX, n1 - tx0), tyv = min(TY2, n2 - ty0);
+    bool vr[RX2];
+#pragma unroll
+    for (int r = 0; r < RX2; ++r) vr[r] = vy && (tx0 + xl0 + r < n1);
+
+    // ---- item tables
+    const int it0 = __ldg(a.cptr + cta), nit = __ldg(a.cptr + cta + 1) - it0;
+    for (int i = t; i < nit; i += THREADS) {
+      const SubBox b = a.sb[__ldg(a.citems + it0 + i)];
+      Piece pc;
+      pc.gy0 = b.gy0; pc.gy1 = b.gy1; pc.gx0 = b.gx0; pc.gx1 = b.gx1;
+      pc.sy = b.nbx;
+      pc.sz = b.nbx * b.nby;
+      pc.base = (int)b.chi4_off + b.bx0 - b.gx0 + b.nbx * (b.by0 - b.gy0) + pc.sz * (b.bz0 - b.gz0);
+      pc.ph_re = b.ph_re; pc.ph_im = b.ph_im;
+      desc[i] = pc;
+      for (int l = 0; l < 4; ++l) {
+        const int p = a.grp[b.grp].proj[l];
+        for (int oo = 0; oo < NB; ++oo)
+          gcs[(i * 4 + l) * NB + oo] = (p >= 0) ? gc[((size_t)p * a.nblk_total + blk) * NB + oo] : 0.f;
+      }
+    }
+    const size_t sb0 = (size_t)cta * ZC * NRG;
+    const int s0 = __ldg(a.sptr + sb0);
+    for (int k = t; k <= ZC * NRG; k += THREADS) steps[k] = __ldg(a.sptr + sb0 + k) - s0;
+    const int nst = __ldg(a.sptr + sb0 + ZC * NRG) - s0;
+    for (int k = t; k < nst; k += THREADS) steps[ZC * NRG + 1 + k] = __ldg(a.sslots + s0 + k);
+
+    // ---- copy descriptors
+    int hs[NHC], hg[NHC];
+#pragma unroll
+    for (int i = 0; i < NHC; ++i) {
+      const int idx = t + i * THREADS;
+      hs[i] = -1; hg[i] = 0;
+      if (idx < PX * PY * CH) {
+        const int pnt = idx / CH, ch = idx % CH;
+        const int sx = pnt % PX, sy = pnt / PX;
+        const int lx = sx - R, ly = sy - R;
+        if (!(lx >= 0 && lx < txv && ly >= 0 && ly < tyv)) {
+          int gxw = tx0 + lx, gyw = ty0 + ly;
+          wrap(gxw, n1);
+          wrap(gyw, n2);
+          hs[i] = sy * RP + sx * NB + ch * 4;
+          hg[i] = (gyw * n1 + gxw) * NB + ch * 4;
+        }
+      }
+    }
+    int ps[NPC], pg[NPC];
+#pragma unroll
+    for (int i = 0; i < NPC; ++i) {
+      const int idx = t + i * THREADS;
+      ps[i] = -1; pg[i] = 0;
+      if (idx < TX * TY2 * CH) {
+        const int node = idx / CH, ch = idx % CH;
+        const int lx = node % TX, ly = node / TX;
+        if (lx < txv && ly < tyv) {
+          ps[i] = node * NB + ch * 4;
+          pg[i] = ((ty0 + ly) * n1 + tx0 + lx) * NB + ch * 4;
+        }
+      }
+    }
+    const int vlx = t % TX, vly = t / TX;
+    const bool vv = t < TX * TY2 && vlx < txv && vly < tyv;
+    const int vgo = (ty0 + vly) * n1 + tx0 + vlx;
+
+    float2 q[Q][RX2];
+    auto load_z = [&](int zz, float2* dst) {
+      int zw = zz;
+      wrap(zw, n3);
+      const float* src = Y + (size_t)zw * plane_el + ((size_t)gy * n1 + tx0 + xl0) * NB + o2;
+#pragma unroll
+      for (int r = 0; r < RX2; ++r)
+        dst[r] = vr[r] ? __ldg(reinterpret_cast<const float2*>(src + r * NB)) : make_float2(0.f, 0.f);
+    };
+#pragma unroll
+    for (int i = 0; i < Q; ++i) load_z(zs - R + i, q[i]);
+
+    auto issue = [&](int zz, int b) {
+      int zw = zz;
+      wrap(zw, n3);
+      float* P = planes + (size_t)b * PY * RP;
+      const float* Yz = Y + (size_t)zw * plane_el;
+#pragma unroll
+      for (int i = 0; i < NHC; ++i)
+        if (hs[i] >= 0) cp16(P + hs[i], Yz + hg[i]);
+      if (vv) cp4(vbs + (size_t)b * TY2 * TX + t, a.veff + (size_t)zw * n1 * n2 + vgo);
+      if (Yprev != nullptr) {
+        float* Pp = yps + (size_t)b * TY2 * TX * NB;
+        const float* Yp = Yprev + boff + (size_t)zw * plane_el;
+#pragma unroll
+        for (int i = 0; i < NPC; ++i)
+          if (ps[i] >= 0) cp16(Pp + ps[i], Yp + pg[i]);
+      }
+    };
+    auto own = [&](const float2* vals, int b) {
+      float* P = planes + (size_t)b * PY * RP;
+#pragma unroll
+      for (int r = 0; r < RX2; ++r)
+        if (vr[r]) *reinterpret_cast<float2*>(P + (yl + R) * RP + (xl0 + r + R) * NB + o2) = vals[r];
+    };
+
+    issue(zs, 0);
+    cp_commit();
+    if (zs + 1 < ze) issue(zs + 1, 1);
+    cp_commit();
+    own(q[R], 0);
+    cp_wait1();
+    __syncthreads();
+
+    for (int z = zs; z < ze; ++z) {
+      const int sidx = z - zs;
+      const int b = sidx % 3;
+      const float* P = planes + (size_t)b * PY * RP;
+      if (vy) {
+        float2 acc[RX2];
+        const float* row = P + (yl + R) * RP + o2;
+        float2 w[RX2 + 2 * R];
+#pragma unroll
+        for (int i = 0; i < RX2 + 2 * R; ++i) w[i] = lds2(row + (xl0 + i) * NB);
+        const float* V = vbs + (size_t)b * TY2 * TX + yl * TX + xl0;
+#pragma unroll
+        for (int r = 0; r < RX2; ++r) {
+          float2 s = __fmul2_rn(f2(a.c0 + V[r] - a.shift), q[R][r]);
+          const float* col = P + (xl0 + r + R) * NB + o2;
+#pragma unroll
+          for (int p = 1; p <= R; ++p) {
+            const float2 u = lds2(col + (yl + R + p) * RP);
+            const float2 d = lds2(col + (yl + R - p) * RP);
+            s = __ffma2_rn(f2(a.cx[p]), __fadd2_rn(w[R + r + p], w[R + r - p]), s);
+            s = __ffma2_rn(f2(a.cy[p]), __fadd2_rn(u, d), s);
+            s = __ffma2_rn(f2(a.cz[p]), __fadd2_rn(q[R + p][r], q[R - p][r]), s);
+          }
+          acc[r] = s;
+        }
+        // nonlocal scatter: pieces that touch this warp's 8 rows at z
+        const int rg = yg;
+        const int ea = steps[sidx * NRG + rg], eb = steps[sidx * NRG + rg + 1];
+        const int x0r = tx0 + xl0;
+        for (int e = ea; e < eb; ++e) {
+          const int it = steps[ZC * NRG + 1 + e];
+          const Piece pc = desc[it];
+          if (gy < pc.gy0 || gy >= pc.gy1) continue;
+          float2 gv[4];
+#pragma unroll
+          for (int l = 0; l < 4; ++l) gv[l] = lds2(gcs + (it * 4 + l) * NB + o2);
+          const int rowoff = pc.base + pc.sy * gy + pc.sz * z;
+#pragma unroll
+          for (int r = 0; r < RX2; ++r) {
+            const int gx = x0r + r;
+            if (gx >= pc.gx0 && gx < pc.gx1) {
+              const float4 c4 = __ldg(a.chi4 + rowoff + gx);
+              float2 d = __fmul2_rn(f2(c4.x), gv[0]);
+              d = __ffma2_rn(f2(c4.y), gv[1], d);
+              d = __ffma2_rn(f2(c4.z), gv[2], d);
+              d = __ffma2_rn(f2(c4.w), gv[3], d);
+              acc[r] = __fadd2_rn(acc[r], d);
+            }
+          }
+        }
+        // recurrence epilogue
+        const float* Pp = yps + (size_t)b * TY2 * TX * NB + (yl * TX + xl0) * NB + o2;
+        float* out = Yout + boff + (size_t)z * plane_el + ((size_t)gy * n1 + tx0 + xl0) * NB + o2;
+#pragma unroll
+        for (int r = 0; r < RX2; ++r) {
+          if (!vr[r]) continue;
+          float2 v = __fmul2_rn(f2(a.alpha), acc[r]);
+          if (Yprev) v = __ffma2_rn(f2(a.beta), lds2(Pp + r * NB), v);
+          *reinterpret_cast<float2*>(out + r * NB) = v;
+        }
+      }
+      if (z + 1 < ze) own(q[R + 1], (sidx + 1) % 3);
+      if (z + 2 < ze) issue(z + 2, (sidx + 2) % 3);
+      cp_commit();
+#pragma unroll
+      for (int i = 0; i < Q - 1; ++i)
+#pragma unroll
+        for (int r = 0; r < RX2; ++r) q[i][r] = q[i + 1][r];
+      load_z(z + R + 1, q[Q - 1]);
+      cp_wait1();
+      __syncthreads();
+    }
+  }
+}
+
 // gc[p][blk][lane] = gamma_p h^3 sum_{box} conj(chi~_p) Y, one CTA per (group, block).
 // A warp takes whole x-rows of a piece (4 nodes x 8 lanes per step, unrolled).
 template <class T>
@@ -660,19 +899,123 @@ k_gather(const T* __restrict__ Y, long long nd, int n1, int n2, const Group* __r
   }
 }
 
+// Projection by row slabs: CTA (group g, slab s) sums conj(chi~) Y over the box
+// rows r of group g with r % nslab == s, for up to 4 blocks at once (a warp is
+// 4 blocks x 8 lanes, one grid node per step, chi values shared by the warp).
+// part[((g * nslab + s) * 4 + l) * (nb * NB) + bi * NB + lane] gets the CTA sum.
+template <class T>
+__global__ void __launch_bounds__(256)
+k_gather_slab(const T* __restrict__ Y, long long nd, int n1, int n2, const Group* __restrict__ grp,
+              const SubBox* __restrict__ sbs, const float4* __restrict__ chi4, T* __restrict__ part,
+              int blk0, int nb, int nslab) {
+  __shared__ T red[8][4][32];
+  const int gi = blockIdx.x, sl = blockIdx.y, quad = blockIdx.z;
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  const int o = lane % NB, bq = lane / NB;            // block within the quad
+  const int bi = quad * 4 + bq;
+  const bool vb = bi < nb;
+  const T* Yb = Y + (size_t)(blk0 + (vb ? bi : 0)) * nd * NB;
+  const Group G = grp[gi];
+  T acc[4] = {FT<T>::zero(), FT<T>::zero(), FT<T>::zero(), FT<T>::zero()};
+  int rbase = 0;
+  for (int sbi = G.sb0; sbi < G.sb1; ++sbi) {
+    const SubBox b = sbs[sbi];
+    const int wx = b.gx1 - b.gx0, wy = b.gy1 - b.gy0, wz = b.gz1 - b.gz0;
+    const int rows = wy * wz;
+    // rows of this piece handled by this CTA: global row index (rbase + row) % nslab == sl
+    int first = (sl - rbase % nslab + nslab) % nslab;
+    for (int row = first + warp * nslab; row < rows; row += 8 * nslab) {
+      const int iy = row % wy, iz = row / wy;
+      const long long yrow = ((long long)(b.gz0 + iz) * n2 + (b.gy0 + iy)) * n1 + b.gx0;
+      const long long crow = b.chi4_off + b.bx0 + (long long)b.nbx * ((b.by0 + iy) + (long long)b.nby * (b.bz0 + iz));
+      T s[4] = {FT<T>::zero(), FT<T>::zero(), FT<T>::zero(), FT<T>::zero()};
+#pragma unroll 4
+      for (int ix = 0; ix < wx; ++ix) {
+        const float4 c4 = __ldg(chi4 + crow + ix);
+        const T y = vb ? fld(Yb + (size_t)(yrow + ix) * NB + o) : FT<T>::zero();
+        if constexpr (FT<T>::cplx) {
+          s[0].x += c4.x * y.x; s[0].y += c4.x * y.y;
+          s[1].x += c4.y * y.x; s[1].y += c4.y * y.y;
+          s[2].x += c4.z * y.x; s[2].y += c4.z * y.y;
+          s[3].x += c4.w * y.x; s[3].y += c4.w * y.y;
+        } else {
+          s[0] = fmaf(c4.x, y, s[0]); s[1] = fmaf(c4.y, y, s[1]);
+          s[2] = fmaf(c4.z, y, s[2]); s[3] = fmaf(c4.w, y, s[3]);
+        }
+      }
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {   // conj(phase) of this piece
+        if constexpr (FT<T>::cplx) {
+          acc[l].x += b.ph_re * s[l].x + b.ph_im * s[l].y;
+          acc[l].y += b.ph_re * s[l].y - b.ph_im * s[l].x;
+        } else {
+          acc[l] += s[l];   // real data: k = 0, the phase is 1
+        }
+      }
+    }
+    rbase += rows;
+  }
+#pragma unroll
+  for (int l = 0; l < 4; ++l) red[warp][l][lane] = acc[l];
+  __syncthreads();
+  if (warp < 4) {   // warp w reduces projector slot l = w over the 8 warps, fixed order
+    const int l = warp;
+    T v = red[0][l][lane];
+    for (int w2 = 1; w2 < 8; ++w2) {
+      if constexpr (FT<T>::cplx) { v.x += red[w2][l][lane].x; v.y += red[w2][l][lane].y; }
+      else v += red[w2][l][lane];
+    }
+    if (vb) part[((size_t)(gi * nslab + sl) * 4 + l) * ((size_t)nb * NB) + bi * NB + o] = v;
+  }
+}
+
+// gc[p][blk][lane] = gamma_p h^3 sum_s part[g][s][l][bi][lane] (fixed order over slabs)
+template <class T>
+__global__ void k_gather_sum(const T* __restrict__ part, const Group* __restrict__ grp,
+                             const float* __restrict__ gamma, float dv, T* __restrict__ gc, int ngrp,
+                             int nslab, int nblk_total, int blk0, int nb) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long per = 4LL * nb * NB;
+  if (t >= (long long)ngrp * per) return;
+  const int gi = (int)(t / per);
+  const int rem = (int)(t % per);
+  const int l = rem / (nb * NB), bi = (rem / NB) % nb, o = rem % NB;
+  const int p = grp[gi].proj[l];
+  if (p < 0) return;
+  T v = FT<T>::zero();
+  for (int s = 0; s < nslab; ++s) {
+    const T x = part[((size_t)(gi * nslab + s) * 4 + l) * ((size_t)nb * NB) + bi * NB + o];
+    if constexpr (FT<T>::cplx) { v.x += x.x; v.y += x.y; }
+    else v += x;
+  }
+  const float f = gamma[p] * dv;
+  if constexpr (FT<T>::cplx) v = cf32{f * v.x, f * v.y};
+  else v = f * v;
+  gc[((size_t)p * nblk_total + blk0 + bi) * NB + o] = v;
+}
+
 // --------------------------------------------------------------------------- launchers
+
+constexpr int NSLAB = 8;
+
+size_t gather_scratch_bytes(const sparc_ham* H, int nb, size_t esize) {
+  const Tables* Tb = (const Tables*)H->fast;
+  return (size_t)std::max(1, Tb->ngrp) * NSLAB * 4 * nb * NB * esize;
+}
 
 template <class T>
 cudaError_t launch_gather(const sparc_ham* H, const T* Y, int nblk_total, int blk0, int nb, T* gc,
-                          cudaStream_t st) {
+                          T* scratch, cudaStream_t st) {
   const Tables* Tb = (const Tables*)H->fast;
   if (H->nproj == 0 || Tb->ngrp == 0) return cudaSuccess;
   const float dv = (float)(H->grid.h[0] * H->grid.h[1] * H->grid.h[2]);
   cudaEvent_t t0 = timing_begin(H->ctx, st);
-  k_gather<T><<<dim3((unsigned)Tb->ngrp, (unsigned)nb), 512, 0, st>>>(
-      Y, H->gd.nd, H->gd.n1, H->gd.n2, Tb->d_grp, Tb->d_sb, (const float4*)Tb->d_chi4, H->d_gamma32,
-      dv, gc, nblk_total, blk0);
-  ++H->ctx->launches;
+  k_gather_slab<T><<<dim3((unsigned)Tb->ngrp, NSLAB, (unsigned)ceil_div(nb, 4)), 256, 0, st>>>(
+      Y, H->gd.nd, H->gd.n1, H->gd.n2, Tb->d_grp, Tb->d_sb, (const float4*)Tb->d_chi4, scratch, blk0, nb, NSLAB);
+  const long long tot = (long long)Tb->ngrp * 4 * nb * NB;
+  k_gather_sum<T><<<ceil_div(tot, 256), 256, 0, st>>>(scratch, Tb->d_grp, H->d_gamma32, dv, gc, Tb->ngrp,
+                                                      NSLAB, nblk_total, blk0, nb);
+  H->ctx->launches += 2;
   timing_end(H->ctx, TK_GATHER, t0, st);
   return cudaGetLastError();
 }
@@ -705,18 +1048,30 @@ cudaError_t launch_pass(const sparc_ham* H, const T* Yin, const T* Yprev, T* You
   a.sb = Tb->d_sb; a.grp = Tb->d_grp;
   a.chi4 = (const float4*)Tb->d_chi4;
   const size_t smem = Smem<T>::total;
-  cudaError_t e = cudaFuncSetAttribute(k_pass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)(Lo.tiles_x * Lo.tiles_y), (unsigned)Lo.nchunk, (unsigned)nb);
-  cudaEvent_t t0 = timing_begin(H->ctx, st);
-  k_pass<T><<<grid, THREADS, smem, st>>>(a, Yin, Yprev, Yout, gc);
+  cudaEvent_t t0 = nullptr;
+  if constexpr (!FT<T>::cplx) {
+    // persistent CTAs over (tile, chunk, block) items
+    cudaError_t e = cudaFuncSetAttribute(k_pass_f2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int nitems = Lo.tiles_x * Lo.tiles_y * Lo.nchunk * nb;
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, H->ctx->device);
+    t0 = timing_begin(H->ctx, st);
+    k_pass_f2<<<std::min(nitems, std::max(nsm, 1)), THREADS, smem, st>>>(a, Yin, Yprev, Yout, gc, nitems);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(k_pass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)(Lo.tiles_x * Lo.tiles_y), (unsigned)Lo.nchunk, (unsigned)nb);
+    t0 = timing_begin(H->ctx, st);
+    k_pass<T><<<grid, THREADS, smem, st>>>(a, Yin, Yprev, Yout, gc);
+  }
   ++H->ctx->launches;
   timing_end(H->ctx, TK_HPASS, t0, st);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_gather<float>(const sparc_ham*, const float*, int, int, int, float*, cudaStream_t);
-template cudaError_t launch_gather<cf32>(const sparc_ham*, const cf32*, int, int, int, cf32*, cudaStream_t);
+template cudaError_t launch_gather<float>(const sparc_ham*, const float*, int, int, int, float*, float*, cudaStream_t);
+template cudaError_t launch_gather<cf32>(const sparc_ham*, const cf32*, int, int, int, cf32*, cf32*, cudaStream_t);
 template cudaError_t launch_pass<float>(const sparc_ham*, const float*, const float*, float*, const float*,
                                         int, int, int, double, double, double, cudaStream_t);
 template cudaError_t launch_pass<cf32>(const sparc_ham*, const cf32*, const cf32*, cf32*, const cf32*,

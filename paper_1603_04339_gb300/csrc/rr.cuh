@@ -8,7 +8,8 @@ namespace sparc {
 struct BlockWs {
   void* b0;   // interleaved block buffer
   void* b1;   // interleaved block buffer
-  void* gc;   // projector coefficients [nproj][nblk][32]
+  void* gc;   // projector coefficients [nproj][nblk][NB]
+  char* tail; // first byte after the block workspace (start of the caller's extra bytes)
 };
 
 sparc_status ensure_vals(sparc_ham* H, sparc_dtype dt);

@@ -189,6 +189,7 @@ sparc_status block_ws(sparc_ham* H, sparc_dtype dt, int ns, size_t extra, BlockW
   w->b0 = p;
   w->b1 = p + bb;
   w->gc = p + 2 * bb;
+  w->tail = p + 2 * bb + gb;
   if (tail) *tail = p + 2 * bb + gb;
   return SPARC_OK;
 }
@@ -264,6 +265,7 @@ sparc_status filter_block_fast(sparc_ham* H, int m, double a, double b, double a
   const double sigma1 = e / (a0 - c);
   const size_t per_blk = 2 * (size_t)H->gd.nd * NB * sizeof(T);
   const int G = std::max(1, (int)((size_t)72 * 1024 * 1024 / per_blk));
+  T* scratch = (T*)w.tail;
   SPARC_CUDA(H->ctx, launch_to_blocks<T>(X, ld, ns, B0, H->gd.nd, nblk, st));
   ++H->ctx->launches;
   T* res = B1;
@@ -272,11 +274,11 @@ sparc_status filter_block_fast(sparc_ham* H, int m, double a, double b, double a
     T* prev = B0;
     T* cur = B1;
     double sigma = sigma1;
-    SPARC_CUDA(H->ctx, fast::launch_gather<T>(H, prev, nblk, g0, nb, gc, st));
+    SPARC_CUDA(H->ctx, fast::launch_gather<T>(H, prev, nblk, g0, nb, gc, scratch, st));
     SPARC_CUDA(H->ctx, fast::launch_pass<T>(H, prev, nullptr, cur, gc, nblk, g0, nb, sigma1 / e, c, 0.0, st));
     for (int j = 1; j < m; ++j) {
       const double sigma_new = 1.0 / (2.0 / sigma1 - sigma);
-      SPARC_CUDA(H->ctx, fast::launch_gather<T>(H, cur, nblk, g0, nb, gc, st));
+      SPARC_CUDA(H->ctx, fast::launch_gather<T>(H, cur, nblk, g0, nb, gc, scratch, st));
       SPARC_CUDA(H->ctx, fast::launch_pass<T>(H, cur, prev, prev, gc, nblk, g0, nb, 2.0 * sigma_new / e, c,
                                               -sigma * sigma_new, st));
       std::swap(cur, prev);
@@ -596,14 +598,20 @@ sparc_status sparc_cheb_filter(sparc_ham* H, sparc_dtype dtype, int m, double a,
     case SPARC_F64:
       return filter_block<double>(H, m, a, b, a0, (const double*)X, (double*)Y, ns, ld, st, w);
     case SPARC_F32:
-      if (fast::usable(H))
+      if (fast::usable(H)) {
+        s = block_ws(H, dtype, ns, fast::gather_scratch_bytes(H, ceil_div(ns, NB), sizeof(float)), &w, nullptr);
+        if (s != SPARC_OK) return s;
         return filter_block_fast<float>(H, m, a, b, a0, (const float*)X, (float*)Y, ns, ld, st, w);
+      }
       return filter_block<float>(H, m, a, b, a0, (const float*)X, (float*)Y, ns, ld, st, w);
     case SPARC_C128:
       return filter_block<cf64>(H, m, a, b, a0, (const cf64*)X, (cf64*)Y, ns, ld, st, w);
     case SPARC_C64:
-      if (fast::usable(H))
+      if (fast::usable(H)) {
+        s = block_ws(H, dtype, ns, fast::gather_scratch_bytes(H, ceil_div(ns, NB), sizeof(cf32)), &w, nullptr);
+        if (s != SPARC_OK) return s;
         return filter_block_fast<cf32>(H, m, a, b, a0, (const cf32*)X, (cf32*)Y, ns, ld, st, w);
+      }
       return filter_block<cf32>(H, m, a, b, a0, (const cf32*)X, (cf32*)Y, ns, ld, st, w);
   }
   return SPARC_ERR_INVALID_ARG;
