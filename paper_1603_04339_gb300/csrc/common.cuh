@@ -167,7 +167,7 @@ struct sparc_ctx {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   // kernel timing: event pairs per timed kernel class
-  static constexpr int NTIMED = 6;
+  static constexpr int NTIMED = 7;
   long long launches = 0;          // kernels launched by this context (instrumentation)
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[NTIMED];
@@ -208,7 +208,7 @@ bool sync_check();
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // Timing hooks: bracket a launch with events on `st` while timing is enabled.
-enum TimedKernel { TK_HPASS = 0, TK_GATHER = 1, TK_GRAM = 2, TK_EIG = 3, TK_ROT = 4, TK_JAC = 5 };
+enum TimedKernel { TK_HPASS = 0, TK_GATHER = 1, TK_GRAM = 2, TK_EIG = 3, TK_ROT = 4, TK_JAC = 5, TK_FPASS = 6 };
 cudaEvent_t timing_begin(sparc_ctx* ctx, cudaStream_t st);
 void timing_end(sparc_ctx* ctx, int which, cudaEvent_t begin, cudaStream_t st);
 

@@ -11,7 +11,7 @@ constexpr int TX = 16;                // x extent of a CTA tile
 constexpr int ZC = 13;                // z-range of a CTA (one turn of the 13-deep queue)
 constexpr int THREADS = 512;
 constexpr int MAXI = 96;              // projector-box pieces a CTA can hold in shared memory
-constexpr int MAXSTEP = 640;          // (z, piece) activations a CTA can hold
+constexpr int MAXSTEP = 2048;         // (z, rows, x-run, piece) activations a CTA can hold
 // per element type: x-consecutive nodes per thread and y extent of a CTA tile
 // (the register queue holds 13 * RX values, which bounds RX for complex data)
 template <class T> struct Shape;
@@ -45,8 +45,8 @@ struct Layout {
   int max_items = 0, max_steps = 0;
   int* d_cptr = nullptr;      // [cta + 1] into d_citems
   int* d_citems = nullptr;    // sub-box ids
-  int* d_sptr = nullptr;      // [cta * (ZC + 1) + k] into d_sslots
-  int* d_sslots = nullptr;    // CTA-local piece indices active at z = chunk start + k
+  int* d_sptr = nullptr;      // [((cta * ZC + k) * row groups + rg) * x-runs + xr] into d_sslots
+  int* d_sslots = nullptr;    // CTA-local indices of the pieces touching those nodes at z
 };
 
 struct Tables {
@@ -63,6 +63,9 @@ void free_tables(Tables& t);
 
 // Whether the tiled kernel handles this Hamiltonian (radius 6, FP32 element types).
 bool usable(const sparc_ham* H);
+// Work items (tile x z-chunk) of one block of orbitals for the element type T.
+template <class T>
+int items_per_block(const sparc_ham* H);
 
 // gc[p][blk][lane] for the blocks [blk0, blk0 + nb) (gamma_p h^3 chi~_p^H Y);
 // `scratch` holds gather_scratch_bytes(H, nb, sizeof(T)) bytes of per-slab partial sums.

@@ -155,7 +155,9 @@ sparc_status build_tables(sparc_ham* H, const sparc_nonlocal* nl) {
     // a row group is the rows one warp covers (8 for FP32, 4 for complex64)
     const int rgh = (si == 0) ? 8 : 4;
     const int nrg = TYk / rgh;
-    std::vector<int> cptr(nct + 1, 0), citems, sptr((size_t)nct * ZC * nrg + 1, 0), sslots;
+    const int xrw = (si == 0) ? 2 : TX;          // x extent of a list (FP32: one warp's x-run)
+    const int nxr = TX / xrw;
+    std::vector<int> cptr(nct + 1, 0), citems, sptr((size_t)nct * ZC * nrg * nxr + 1, 0), sslots;
     Lo.max_items = 0;
     Lo.max_steps = 0;
     for (int c = 0; c < nct; ++c) {
@@ -169,20 +171,22 @@ sparc_status build_tables(sparc_ham* H, const sparc_nonlocal* nl) {
       const int z0 = (c % Lo.nchunk) * ZC;
       const int first = (int)sslots.size();
       for (int k = 0; k < ZC; ++k)
-        for (int rg = 0; rg < nrg; ++rg) {
-          sptr[((size_t)c * ZC + k) * nrg + rg] = (int)sslots.size();
-          const int z = z0 + k;
-          const int y0 = y0t + rgh * rg, y1 = std::min(n[1], y0 + rgh);
-          if (z < n[2] && y0 < y1)
-            for (int j = 0; j < (int)it.size(); ++j) {
-              const SubBox& b = sbs[it[j]];
-              if (b.gz0 <= z && z < b.gz1 && b.gy0 < y1 && b.gy1 > y0 && b.gx0 < x1 && b.gx1 > x0)
-                sslots.push_back(j);
-            }
-        }
+        for (int rg = 0; rg < nrg; ++rg)
+          for (int xq = 0; xq < nxr; ++xq) {
+            sptr[(((size_t)c * ZC + k) * nrg + rg) * nxr + xq] = (int)sslots.size();
+            const int z = z0 + k;
+            const int y0 = y0t + rgh * rg, y1 = std::min(n[1], y0 + rgh);
+            const int xa = x0 + xq * xrw, xb = std::min(x1, xa + xrw);
+            if (z < n[2] && y0 < y1 && xa < xb)
+              for (int j = 0; j < (int)it.size(); ++j) {
+                const SubBox& b = sbs[it[j]];
+                if (b.gz0 <= z && z < b.gz1 && b.gy0 < y1 && b.gy1 > y0 && b.gx0 < xb && b.gx1 > xa)
+                  sslots.push_back(j);
+              }
+          }
       Lo.max_steps = std::max(Lo.max_steps, (int)sslots.size() - first);
     }
-    sptr[(size_t)nct * ZC * nrg] = (int)sslots.size();
+    sptr[(size_t)nct * ZC * nrg * nxr] = (int)sslots.size();
     auto up = [&](void** d, const void* h, size_t bytes) -> bool {
       if (cudaMalloc(d, std::max<size_t>(bytes, 16)) != cudaSuccess) return false;
       return bytes == 0 || cudaMemcpy(*d, h, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
@@ -278,6 +282,7 @@ struct PassArgs {
   float c0;                       // centre Laplacian coefficient (sum of -w_0 over axes)
   float phx_r, phx_i, phy_r, phy_i, phz_r, phz_i;   // exp(i k_s L_s)
   float alpha, shift, beta;
+  float2 cx2[R + 1], cy2[R + 1], cz2[R + 1], alpha2, beta2;   // the same, as packed pairs
   const float* veff;
   const int* cptr;
   const int* citems;
@@ -290,10 +295,10 @@ struct PassArgs {
 
 // Compact form of a projector-box piece for the scatter: chi4 row of grid row
 // (y, z) starts at base + sy * y + sz * z (index of grid x = 0).
-struct Piece {
+struct __align__(16) Piece {
   int gy0, gy1, gx0, gx1;
-  int base, sy, sz;
-  float ph_re, ph_im;
+  int base, sy, sz, pad0;
+  float ph_re, ph_im, pad1, pad2;
 };
 
 constexpr int PX = TX + 2 * R;
@@ -302,12 +307,14 @@ template <class T> __host__ __device__ constexpr int plane_rows() { return Shape
 template <class T> struct Smem {
   static constexpr int TY = Shape<T>::TY, PY = plane_rows<T>();
   static constexpr int NRG = TY / (sizeof(T) == 4 ? 8 : 4);   // row groups of the z lists
+  static constexpr int NXR = (sizeof(T) == 4) ? 8 : 1;         // x-runs of the z lists
+  static constexpr int NL = ZC * NRG * NXR;                    // lists per CTA
   static constexpr size_t planes = 3 * (size_t)PY * RP * sizeof(T);
   static constexpr size_t yprev = 3 * (size_t)TY * TX * NB * sizeof(T);
   static constexpr size_t vb = 3 * (size_t)TY * TX * sizeof(float);
   static constexpr size_t desc = (size_t)MAXI * sizeof(Piece);
   static constexpr size_t gcs = (size_t)MAXI * 4 * NB * sizeof(T);
-  static constexpr size_t steps = (size_t)(ZC * NRG + 1 + MAXSTEP) * sizeof(int);
+  static constexpr size_t steps = (size_t)(NL + 1 + MAXSTEP) * sizeof(int);
   static constexpr size_t total = planes + yprev + vb + desc + gcs + steps;
 };
 
@@ -371,11 +378,12 @@ k_pass(PassArgs a, const T* __restrict__ Yin, const T* Yprev, T* Yout, const T* 
         gcs[(i * 4 + l) * NB + oo] = (p >= 0) ? gc[((size_t)p * a.nblk_total + blk) * NB + oo] : FT<T>::zero();
     }
   }
-  const size_t sb0 = (size_t)cta * ZC * NRG;
+  constexpr int NL = Smem<T>::NL;
+  const size_t sb0 = (size_t)cta * NL;
   const int s0 = __ldg(a.sptr + sb0);
-  for (int k = t; k <= ZC * NRG; k += THREADS) steps[k] = __ldg(a.sptr + sb0 + k) - s0;
-  const int nst = __ldg(a.sptr + sb0 + ZC * NRG) - s0;
-  for (int k = t; k < nst; k += THREADS) steps[ZC * NRG + 1 + k] = __ldg(a.sslots + s0 + k);
+  for (int k = t; k <= NL; k += THREADS) steps[k] = __ldg(a.sptr + sb0 + k) - s0;
+  const int nst = __ldg(a.sptr + sb0 + NL) - s0;
+  for (int k = t; k < nst; k += THREADS) steps[NL + 1 + k] = __ldg(a.sslots + s0 + k);
 
   // ---- per-thread copy descriptors (the same for every plane up to the z offset)
   // hs: smem element offset in bits 0..19 and the face crossings (tx + 1) + 3 (ty + 1)
@@ -529,7 +537,7 @@ k_pass(PassArgs a, const T* __restrict__ Yin, const T* Yprev, T* Yout, const T* 
       const int ea = steps[sidx * NRG + yg], eb = steps[sidx * NRG + yg + 1];
       const int x0r = tx0 + xl0;
       for (int e = ea; e < eb; ++e) {
-        const int it = steps[ZC * NRG + 1 + e];
+        const int it = steps[NL + 1 + e];
         const Piece pc = desc[it];
         if (gy < pc.gy0 || gy >= pc.gy1) continue;
         T gv[4];
@@ -623,7 +631,8 @@ k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* 
   const int n1 = a.n1, n2 = a.n2, n3 = a.n3;
   const long long plane_el = (long long)n1 * n2 * NB;
   const int ntiles = a.tiles_x * ((n2 + TY2 - 1) / TY2);
-  constexpr int NRG = TY2 / 8;   // list row groups (8 rows: one per warp)
+  constexpr int NRG = Smem<float>::NRG, NXR = Smem<float>::NXR, NL = Smem<float>::NL;
+  static_assert(NRG == TY2 / 8 && NXR == TX / RX2, "one list per warp");
 
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
     const int tile = item % ntiles;
@@ -660,11 +669,11 @@ k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* 
           gcs[(i * 4 + l) * NB + oo] = (p >= 0) ? gc[((size_t)p * a.nblk_total + blk) * NB + oo] : 0.f;
       }
     }
-    const size_t sb0 = (size_t)cta * ZC * NRG;
+    const size_t sb0 = (size_t)cta * NL;
     const int s0 = __ldg(a.sptr + sb0);
-    for (int k = t; k <= ZC * NRG; k += THREADS) steps[k] = __ldg(a.sptr + sb0 + k) - s0;
-    const int nst = __ldg(a.sptr + sb0 + ZC * NRG) - s0;
-    for (int k = t; k < nst; k += THREADS) steps[ZC * NRG + 1 + k] = __ldg(a.sslots + s0 + k);
+    for (int k = t; k <= NL; k += THREADS) steps[k] = __ldg(a.sptr + sb0 + k) - s0;
+    const int nst = __ldg(a.sptr + sb0 + NL) - s0;
+    for (int k = t; k < nst; k += THREADS) steps[NL + 1 + k] = __ldg(a.sslots + s0 + k);
 
     // ---- copy descriptors
     int hs[NHC], hg[NHC];
@@ -766,28 +775,29 @@ k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* 
           for (int p = 1; p <= R; ++p) {
             const float2 u = lds2(col + (yl + R + p) * RP);
             const float2 d = lds2(col + (yl + R - p) * RP);
-            s = __ffma2_rn(f2(a.cx[p]), __fadd2_rn(w[R + r + p], w[R + r - p]), s);
-            s = __ffma2_rn(f2(a.cy[p]), __fadd2_rn(u, d), s);
-            s = __ffma2_rn(f2(a.cz[p]), __fadd2_rn(q[R + p][r], q[R - p][r]), s);
+            s = __ffma2_rn(a.cx2[p], __fadd2_rn(w[R + r + p], w[R + r - p]), s);
+            s = __ffma2_rn(a.cy2[p], __fadd2_rn(u, d), s);
+            s = __ffma2_rn(a.cz2[p], __fadd2_rn(q[R + p][r], q[R - p][r]), s);
           }
           acc[r] = s;
         }
-        // nonlocal scatter: pieces that touch this warp's 8 rows at z
-        const int rg = yg;
-        const int ea = steps[sidx * NRG + rg], eb = steps[sidx * NRG + rg + 1];
+        // nonlocal scatter: the pieces that touch this warp's 8 rows x 2 columns at z
+        const int li = (sidx * NRG + yg) * NXR + xr;
+        const int ea = steps[li], eb = steps[li + 1];
         const int x0r = tx0 + xl0;
         for (int e = ea; e < eb; ++e) {
-          const int it = steps[ZC * NRG + 1 + e];
-          const Piece pc = desc[it];
-          if (gy < pc.gy0 || gy >= pc.gy1) continue;
+          const int it = steps[NL + 1 + e];
+          const int4 pa = *reinterpret_cast<const int4*>(&desc[it].gy0);   // gy0 gy1 gx0 gx1
+          if (gy < pa.x || gy >= pa.y) continue;
+          const int4 pb = *reinterpret_cast<const int4*>(&desc[it].base);  // base sy sz -
           float2 gv[4];
 #pragma unroll
           for (int l = 0; l < 4; ++l) gv[l] = lds2(gcs + (it * 4 + l) * NB + o2);
-          const int rowoff = pc.base + pc.sy * gy + pc.sz * z;
+          const int rowoff = pb.x + pb.y * gy + pb.z * z;
 #pragma unroll
           for (int r = 0; r < RX2; ++r) {
             const int gx = x0r + r;
-            if (gx >= pc.gx0 && gx < pc.gx1) {
+            if (gx >= pa.z && gx < pa.w) {
               const float4 c4 = __ldg(a.chi4 + rowoff + gx);
               float2 d = __fmul2_rn(f2(c4.x), gv[0]);
               d = __ffma2_rn(f2(c4.y), gv[1], d);
@@ -803,8 +813,8 @@ k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* 
 #pragma unroll
         for (int r = 0; r < RX2; ++r) {
           if (!vr[r]) continue;
-          float2 v = __fmul2_rn(f2(a.alpha), acc[r]);
-          if (Yprev) v = __ffma2_rn(f2(a.beta), lds2(Pp + r * NB), v);
+          float2 v = __fmul2_rn(a.alpha2, acc[r]);
+          if (Yprev) v = __ffma2_rn(a.beta2, lds2(Pp + r * NB), v);
           *reinterpret_cast<float2*>(out + r * NB) = v;
         }
       }
@@ -1043,6 +1053,13 @@ cudaError_t launch_pass(const sparc_ham* H, const T* Yin, const T* Yprev, T* You
   a.phy_r = (float)H->gd.ph_re[1]; a.phy_i = (float)H->gd.ph_im[1];
   a.phz_r = (float)H->gd.ph_re[2]; a.phz_i = (float)H->gd.ph_im[2];
   a.alpha = (float)alpha; a.shift = (float)shift; a.beta = (float)beta;
+  for (int p = 0; p <= R; ++p) {
+    a.cx2[p] = make_float2(a.cx[p], a.cx[p]);
+    a.cy2[p] = make_float2(a.cy[p], a.cy[p]);
+    a.cz2[p] = make_float2(a.cz[p], a.cz[p]);
+  }
+  a.alpha2 = make_float2(a.alpha, a.alpha);
+  a.beta2 = make_float2(a.beta, a.beta);
   a.veff = H->d_veff32;
   a.cptr = Lo.d_cptr; a.citems = Lo.d_citems; a.sptr = Lo.d_sptr; a.sslots = Lo.d_sslots;
   a.sb = Tb->d_sb; a.grp = Tb->d_grp;
@@ -1066,9 +1083,17 @@ cudaError_t launch_pass(const sparc_ham* H, const T* Yin, const T* Yprev, T* You
     k_pass<T><<<grid, THREADS, smem, st>>>(a, Yin, Yprev, Yout, gc);
   }
   ++H->ctx->launches;
-  timing_end(H->ctx, TK_HPASS, t0, st);
+  timing_end(H->ctx, TK_FPASS, t0, st);
   return cudaGetLastError();
 }
+
+template <class T>
+int items_per_block(const sparc_ham* H) {
+  const Layout& Lo = ((const Tables*)H->fast)->lay[FT<T>::cplx ? 1 : 0];
+  return Lo.tiles_x * Lo.tiles_y * Lo.nchunk;
+}
+template int items_per_block<float>(const sparc_ham*);
+template int items_per_block<cf32>(const sparc_ham*);
 
 template cudaError_t launch_gather<float>(const sparc_ham*, const float*, int, int, int, float*, float*, cudaStream_t);
 template cudaError_t launch_gather<cf32>(const sparc_ham*, const cf32*, int, int, int, cf32*, cf32*, cudaStream_t);

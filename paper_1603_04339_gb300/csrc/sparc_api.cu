@@ -263,8 +263,20 @@ sparc_status filter_block_fast(sparc_ham* H, int m, double a, double b, double a
   T* gc = (T*)w.gc;
   const double e = 0.5 * (b - a), c = 0.5 * (b + a);
   const double sigma1 = e / (a0 - c);
+  // blocks per group: the two live buffers of a group stay in L2 (<= 90 MB), and among
+  // those sizes take the one whose work items fill the SMs most evenly
   const size_t per_blk = 2 * (size_t)H->gd.nd * NB * sizeof(T);
-  const int G = std::max(1, (int)((size_t)72 * 1024 * 1024 / per_blk));
+  const int gmax = std::max(1, std::min(nblk, (int)((size_t)90 * 1024 * 1024 / per_blk)));
+  const int items_per_blk = fast::items_per_block<T>(H);
+  int nsm = 152;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, H->ctx->device);
+  int G = gmax;
+  double best = -1.0;
+  for (int g = std::max(1, gmax / 2); g <= gmax; ++g) {
+    const long long it = (long long)items_per_blk * g;
+    const double eff = (double)it / ((double)nsm * (double)((it + nsm - 1) / nsm));
+    if (eff > best + 1e-9 || (std::abs(eff - best) <= 1e-9 && g > G)) { best = eff; G = g; }
+  }
   T* scratch = (T*)w.tail;
   SPARC_CUDA(H->ctx, launch_to_blocks<T>(X, ld, ns, B0, H->gd.nd, nblk, st));
   ++H->ctx->launches;
