@@ -357,3 +357,50 @@ def test_free_electron_shell_closure():
         lam, X = O.chefsi_step(H, X, 16, a, b, a0)
     assert abs(lam[0]) < 1e-9
     assert np.allclose(lam[1:], t1 + 2 * O.fd_symbol(np.array([0.0]), 6, 0.5)[0], atol=1e-9)
+
+
+def test_fd_weights_match_textbook_table():
+    """Eq. weightsLap with the centre counted twice reproduces the tabulated central
+    second-derivative coefficients (tests/golden/fd_second_derivative_central.txt)."""
+    from fractions import Fraction
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "fd_second_derivative_central.txt")
+    rows = 0
+    for line in open(path):
+        line = line.split("#")[0].split()
+        if not line:
+            continue
+        n_o = int(line[0])
+        ref = [float(Fraction(t)) for t in line[1:]]
+        assert len(ref) == n_o + 1
+        w = O.fd_weights(n_o, 1.0)
+        got = [2.0 * w[0]] + list(w[1:])
+        assert np.allclose(got, ref, rtol=1e-14, atol=0), (n_o, got, ref)
+        rows += 1
+    assert rows == 4
+
+
+def test_fd_weights_order12_solve_moment_equations_exactly():
+    """n_o = 6 (the paper's twelfth order): the weights are the unique solution of the
+    moment equations sum_p c_p (p^(2j) + (-p)^(2j)) = 2 [j == 1], j = 0..n_o (c_0 counted
+    once at p = 0), solved here in exact rational arithmetic by Gaussian elimination."""
+    from fractions import Fraction
+    n_o = 6
+    # unknowns c_0 .. c_6; equation j: c_0 [j == 0] + sum_p 2 p^(2j) c_p = 2 [j == 1]
+    A = [[Fraction(1 if j == 0 else 0)] + [Fraction(2 * p ** (2 * j)) for p in range(1, n_o + 1)]
+         for j in range(n_o + 1)]
+    rhs = [Fraction(2 if j == 1 else 0) for j in range(n_o + 1)]
+    n = n_o + 1
+    for c in range(n):
+        r = next(i for i in range(c, n) if A[i][c] != 0)
+        A[c], A[r] = A[r], A[c]
+        rhs[c], rhs[r] = rhs[r], rhs[c]
+        for i in range(n):
+            if i != c and A[i][c] != 0:
+                f = A[i][c] / A[c][c]
+                A[i] = [a - f * b for a, b in zip(A[i], A[c])]
+                rhs[i] -= f * rhs[c]
+    c = [float(rhs[i] / A[i][i]) for i in range(n)]
+    w = O.fd_weights(n_o, 1.0)
+    got = [2.0 * w[0]] + list(w[1:])
+    assert np.allclose(got, c, rtol=1e-13, atol=0), (got, c)
