@@ -60,8 +60,9 @@ typedef enum {
 /* Rayleigh-Ritz precision modes. */
 typedef enum {
   SPARC_RR_FP64 = 0,  /* Grams, eigensolve and rotation in FP64 (input must be F64/C128)   */
-  SPARC_RR_MIXED = 1  /* Grams and rotation from FP32 data with error-compensated products
-                         and FP32 accumulation, FP64 Cholesky + eigensolve (F32/C64 input)  */
+  SPARC_RR_MIXED = 1  /* F32 input: Grams and rotation on tensor cores with 3xTF32
+                         error compensation (see sparc_gram_f32); C64 input: FP32 SIMT
+                         products with FP64 accumulation; FP64 Cholesky + eigensolve */
 } sparc_rr_mode;
 
 /* Finite-difference grid at one Bloch wavevector (Section 3.1). */
@@ -107,6 +108,8 @@ sparc_status sparc_ham_create(sparc_ctx* ctx, const sparc_grid* grid, const doub
 /* Replace V_eff (Nd doubles).  `on_device` != 0: veff is a device pointer,
  * copied asynchronously on `stream`; otherwise a host pointer (synchronous). */
 sparc_status sparc_ham_set_veff(sparc_ham* H, const double* veff, int on_device, void* stream);
+/* Free H.  Uses no state of its context, so it may follow sparc_destroy of that
+ * context; calls other than this one need a live context. */
 void sparc_ham_destroy(sparc_ham* H);
 
 /* Y = H X (Eqn. EL discretised by Eq. FD:Laplacian and Eq. NonlocalPS:FD).
@@ -166,6 +169,24 @@ sparc_status sparc_lanczos_bounds(sparc_ham* H, int ksteps, const void* v0, doub
 sparc_status sparc_rayleigh_ritz(sparc_ham* H, sparc_dtype dtype, void* U, int ns, int64_t ld,
                                  double* eig, int mode, void* stream);
 
+/* The projections of Eq. SubspaceGeneralizedEigenproblem for FP32 data, as
+ * sparc_rayleigh_ritz computes them in MIXED mode: G = A^T B, with A, B device,
+ * real FP32, column-major nd x ns (lda, ldb >= nd) and G device, FP64,
+ * column-major ns x ns.  (H~ = U^T (H U) and M~ = U^T U are the two calls.)
+ * Tensor-core products (tcgen05, kind::tf32) with 3xTF32 error compensation,
+ * FP32 accumulation over chunks of 1024 grid points and FP64 across chunks;
+ * the result is symmetrised (G is taken as symmetric: tiles below the diagonal
+ * are the transposes of those above).  Deterministic.  1 <= ns <= 4096. */
+sparc_status sparc_gram_f32(sparc_ctx* ctx, const float* A, int64_t lda, const float* B, int64_t ldb,
+                            int64_t nd, int ns, double* G, void* stream);
+
+/* The rotation of Eq. OrbitalTransformation for FP32 data: C = U Yr, with U
+ * device FP32 column-major nd x ns (ldu), Yr device FP64 column-major ns x ns
+ * (rounded to FP32), C device FP32 column-major nd x ns (ldc); C may not
+ * overlap U.  Tensor-core products with 3xTF32 compensation.  1 <= ns <= 4096. */
+sparc_status sparc_rotate_f32(sparc_ctx* ctx, const float* U, int64_t ldu, const double* Yr, int64_t nd,
+                              int ns, float* C, int64_t ldc, void* stream);
+
 /* Kernel timing (instrumentation, not part of the method).  While enabled, every
  * launch of the kernels below is bracketed by CUDA events recorded on the
  * stream it is launched on.  sparc_timing_read() synchronises those events and
@@ -173,9 +194,9 @@ sparc_status sparc_rayleigh_ritz(sparc_ham* H, sparc_dtype dtype, void* U, int n
  * enable; it is valid after the launches have completed.
  *   which = 0: the H-apply / Chebyshev-recurrence pass of the generic kernel (k_hpass)
  *   which = 1: the nonlocal projection (k_nl_gather)
- *   which = 2: the Gram products of Rayleigh-Ritz
+ *   which = 2: the Gram products of Rayleigh-Ritz (and sparc_gram_f32)
  *   which = 3: the Cholesky + subspace eigensolve of Rayleigh-Ritz
- *   which = 4: the subspace rotation of Rayleigh-Ritz
+ *   which = 4: the subspace rotation of Rayleigh-Ritz (and sparc_rotate_f32)
  *   which = 5: the Jacobi sweeps of the subspace eigensolve (inside which = 3)
  *   which = 6: the tiled FP32 / complex64 filter pass (k_pass_f2, k_pass) */
 sparc_status sparc_timing_enable(sparc_ctx* ctx, int on);

@@ -161,6 +161,7 @@ struct GridDev {
 // ----------------------------------------------------------------- internal objects
 struct sparc_ctx {
   int device = 0;
+  int nsm = 152;                   // multiprocessors of the device
   std::string last_error;
   int* d_status = nullptr;         // device status word
   // growable workspace arena

@@ -6,6 +6,7 @@
 
 struct sparc_ham {
   sparc_ctx* ctx = nullptr;
+  int device = 0;                // the context's device (sparc_ham_destroy does not read ctx)
   sparc_grid grid{};
   sparc::GridDev gd{};
   double* d_veff = nullptr;      // [Nd]

@@ -756,8 +756,12 @@ k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* 
     cp_wait1();
     __syncthreads();
 
-    for (int z = zs; z < ze; ++z) {
-      const int sidx = z - zs;
+    // the z loop is unrolled over the 13 planes of a chunk, so the register queue
+    // rotates by renaming: plane z + d sits in q[(sidx + R + d) % Q]
+#pragma unroll
+    for (int sidx = 0; sidx < ZC; ++sidx) {
+      const int z = zs + sidx;
+      if (z >= ze) break;
       const int b = sidx % 3;
       const float* P = planes + (size_t)b * PY * RP;
       if (vy) {
@@ -769,7 +773,7 @@ k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* 
         const float* V = vbs + (size_t)b * TY2 * TX + yl * TX + xl0;
 #pragma unroll
         for (int r = 0; r < RX2; ++r) {
-          float2 s = __fmul2_rn(f2(a.c0 + V[r] - a.shift), q[R][r]);
+          float2 s = __fmul2_rn(f2(a.c0 + V[r] - a.shift), q[(sidx + R) % Q][r]);
           const float* col = P + (xl0 + r + R) * NB + o2;
 #pragma unroll
           for (int p = 1; p <= R; ++p) {
@@ -777,7 +781,7 @@ k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* 
             const float2 d = lds2(col + (yl + R - p) * RP);
             s = __ffma2_rn(a.cx2[p], __fadd2_rn(w[R + r + p], w[R + r - p]), s);
             s = __ffma2_rn(a.cy2[p], __fadd2_rn(u, d), s);
-            s = __ffma2_rn(a.cz2[p], __fadd2_rn(q[R + p][r], q[R - p][r]), s);
+            s = __ffma2_rn(a.cz2[p], __fadd2_rn(q[(sidx + R + p) % Q][r], q[(sidx + R - p) % Q][r]), s);
           }
           acc[r] = s;
         }
@@ -818,14 +822,10 @@ k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* 
           *reinterpret_cast<float2*>(out + r * NB) = v;
         }
       }
-      if (z + 1 < ze) own(q[R + 1], (sidx + 1) % 3);
+      if (z + 1 < ze) own(q[(sidx + R + 1) % Q], (sidx + 1) % 3);
       if (z + 2 < ze) issue(z + 2, (sidx + 2) % 3);
       cp_commit();
-#pragma unroll
-      for (int i = 0; i < Q - 1; ++i)
-#pragma unroll
-        for (int r = 0; r < RX2; ++r) q[i][r] = q[i + 1][r];
-      load_z(z + R + 1, q[Q - 1]);
+      load_z(z + R + 1, q[sidx % Q]);   // plane z - R is no longer needed
       cp_wait1();
       __syncthreads();
     }
@@ -909,73 +909,131 @@ k_gather(const T* __restrict__ Y, long long nd, int n1, int n2, const Group* __r
   }
 }
 
-// Projection by row slabs: CTA (group g, slab s) sums conj(chi~) Y over the box
-// rows r of group g with r % nslab == s, for up to 4 blocks at once (a warp is
-// 4 blocks x 8 lanes, one grid node per step, chi values shared by the warp).
-// part[((g * nslab + s) * 4 + l) * (nb * NB) + bi * NB + lane] gets the CTA sum.
-template <class T>
-__global__ void __launch_bounds__(256)
-k_gather_slab(const T* __restrict__ Y, long long nd, int n1, int n2, const Group* __restrict__ grp,
-              const SubBox* __restrict__ sbs, const float4* __restrict__ chi4, T* __restrict__ part,
-              int blk0, int nb, int nslab) {
-  __shared__ T red[8][4][32];
-  const int gi = blockIdx.x, sl = blockIdx.y, quad = blockIdx.z;
-  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
-  const int o = lane % NB, bq = lane / NB;            // block within the quad
-  const int bi = quad * 4 + bq;
-  const bool vb = bi < nb;
-  const T* Yb = Y + (size_t)(blk0 + (vb ? bi : 0)) * nd * NB;
-  const Group G = grp[gi];
-  T acc[4] = {FT<T>::zero(), FT<T>::zero(), FT<T>::zero(), FT<T>::zero()};
-  int rbase = 0;
-  for (int sbi = G.sb0; sbi < G.sb1; ++sbi) {
-    const SubBox b = sbs[sbi];
-    const int wx = b.gx1 - b.gx0, wy = b.gy1 - b.gy0, wz = b.gz1 - b.gz0;
-    const int rows = wy * wz;
-    // rows of this piece handled by this CTA: global row index (rbase + row) % nslab == sl
-    int first = (sl - rbase % nslab + nslab) % nslab;
-    for (int row = first + warp * nslab; row < rows; row += 8 * nslab) {
-      const int iy = row % wy, iz = row / wy;
-      const long long yrow = ((long long)(b.gz0 + iz) * n2 + (b.gy0 + iy)) * n1 + b.gx0;
-      const long long crow = b.chi4_off + b.bx0 + (long long)b.nbx * ((b.by0 + iy) + (long long)b.nby * (b.bz0 + iz));
-      T s[4] = {FT<T>::zero(), FT<T>::zero(), FT<T>::zero(), FT<T>::zero()};
-#pragma unroll 4
-      for (int ix = 0; ix < wx; ++ix) {
-        const float4 c4 = __ldg(chi4 + crow + ix);
-        const T y = vb ? fld(Yb + (size_t)(yrow + ix) * NB + o) : FT<T>::zero();
+// s[b][l] += sum over this lane's nodes ix = xi, xi+4, .. < wx of chi_l(ix) Y_b(ix).
+// The row is taken in chunks of 4 NXS nodes; every load of a chunk is issued
+// before its first multiply, so a warp has (1 + NBM) NXS loads in flight.
+template <class T, int NBM, int NXS>
+__device__ __forceinline__ void gather_row(T (&s)[NBM][4], const float4* __restrict__ c, const T* __restrict__ y0,
+                                           size_t bstride, int wx, int xi, int nbv) {
+  for (int x0 = 0; x0 < wx; x0 += 4 * NXS) {
+    float4 c4[NXS];
+    T y[NXS][NBM];
+#pragma unroll
+    for (int u = 0; u < NXS; ++u) {
+      const int ix = x0 + xi + 4 * u;
+      const bool ok = ix < wx;
+      c4[u] = ok ? __ldg(c + ix) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int b = 0; b < NBM; ++b)
+        y[u][b] = (ok && b < nbv) ? fld(y0 + b * bstride + (size_t)ix * NB) : FT<T>::zero();
+    }
+#pragma unroll
+    for (int u = 0; u < NXS; ++u)
+#pragma unroll
+      for (int b = 0; b < NBM; ++b) {
         if constexpr (FT<T>::cplx) {
-          s[0].x += c4.x * y.x; s[0].y += c4.x * y.y;
-          s[1].x += c4.y * y.x; s[1].y += c4.y * y.y;
-          s[2].x += c4.z * y.x; s[2].y += c4.z * y.y;
-          s[3].x += c4.w * y.x; s[3].y += c4.w * y.y;
+          s[b][0].x = fmaf(c4[u].x, y[u][b].x, s[b][0].x); s[b][0].y = fmaf(c4[u].x, y[u][b].y, s[b][0].y);
+          s[b][1].x = fmaf(c4[u].y, y[u][b].x, s[b][1].x); s[b][1].y = fmaf(c4[u].y, y[u][b].y, s[b][1].y);
+          s[b][2].x = fmaf(c4[u].z, y[u][b].x, s[b][2].x); s[b][2].y = fmaf(c4[u].z, y[u][b].y, s[b][2].y);
+          s[b][3].x = fmaf(c4[u].w, y[u][b].x, s[b][3].x); s[b][3].y = fmaf(c4[u].w, y[u][b].y, s[b][3].y);
         } else {
-          s[0] = fmaf(c4.x, y, s[0]); s[1] = fmaf(c4.y, y, s[1]);
-          s[2] = fmaf(c4.z, y, s[2]); s[3] = fmaf(c4.w, y, s[3]);
+          s[b][0] = fmaf(c4[u].x, y[u][b], s[b][0]); s[b][1] = fmaf(c4[u].y, y[u][b], s[b][1]);
+          s[b][2] = fmaf(c4[u].z, y[u][b], s[b][2]); s[b][3] = fmaf(c4[u].w, y[u][b], s[b][3]);
         }
       }
+  }
+}
+
+// Projection by row slabs: CTA (group g, slab s, octet q) sums conj(chi~) Y over
+// the box rows r of group g with r % nslab == s, for the blocks q*NBM .. q*NBM+NBM-1.
+// A warp takes one box row at a time; lane = xi * 8 + o covers 4 x-consecutive
+// nodes x 8 orbital lanes, so one load of a block is 4 contiguous 32-byte node
+// groups and the chi values of those 4 nodes are read once for all NBM blocks.
+// The row sums of a piece carry its constant phase; partial sums are reduced
+// over xi by shuffles and over the 8 warps in shared memory, in a fixed order.
+// part[((g * nslab + s) * 4 + l) * (nb * NB) + bi * NB + lane] gets the CTA sum.
+template <class T, int NBM>
+__global__ void __launch_bounds__(256, 2)
+k_gather_rows(const T* __restrict__ Y, long long nd, int n1, int n2, const Group* __restrict__ grp,
+              const SubBox* __restrict__ sbs, const float4* __restrict__ chi4, T* __restrict__ part,
+              int blk0, int nb, int nslab) {
+  __shared__ T red[8][NBM][4][NB];
+  const int gi = blockIdx.x, sl = blockIdx.y, q = blockIdx.z;
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  const int o = lane % NB, xi = lane / NB;
+  const int nbv = min(NBM, nb - q * NBM);   // valid blocks of this octet (uniform per CTA)
+  const T* Yb = Y + (size_t)(blk0 + q * NBM) * nd * NB + o;
+  const size_t bstride = (size_t)nd * NB;
+  const Group G = grp[gi];
+  T acc[NBM][4];
 #pragma unroll
-      for (int l = 0; l < 4; ++l) {   // conj(phase) of this piece
-        if constexpr (FT<T>::cplx) {
-          acc[l].x += b.ph_re * s[l].x + b.ph_im * s[l].y;
-          acc[l].y += b.ph_re * s[l].y - b.ph_im * s[l].x;
-        } else {
-          acc[l] += s[l];   // real data: k = 0, the phase is 1
-        }
+  for (int b = 0; b < NBM; ++b)
+#pragma unroll
+    for (int l = 0; l < 4; ++l) acc[b][l] = FT<T>::zero();
+  int rbase = 0;
+  for (int sbi = G.sb0; sbi < G.sb1; ++sbi) {
+    const SubBox sb = sbs[sbi];
+    const int wx = sb.gx1 - sb.gx0, wy = sb.gy1 - sb.gy0, wz = sb.gz1 - sb.gz0;
+    const int rows = wy * wz;
+    const int first = (sl - rbase % nslab + nslab) % nslab;
+    for (int row = first + warp * nslab; row < rows; row += 8 * nslab) {
+      const int iy = row % wy, iz = row / wy;
+      const long long yrow = ((long long)(sb.gz0 + iz) * n2 + (sb.gy0 + iy)) * n1 + sb.gx0;
+      const long long crow =
+          sb.chi4_off + sb.bx0 + (long long)sb.nbx * ((sb.by0 + iy) + (long long)sb.nby * (sb.bz0 + iz));
+      if constexpr (FT<T>::cplx) {
+        T s[NBM][4];
+#pragma unroll
+        for (int b = 0; b < NBM; ++b)
+#pragma unroll
+          for (int l = 0; l < 4; ++l) s[b][l] = FT<T>::zero();
+        gather_row<T, NBM, FT<T>::cplx ? 3 : 5>(s, chi4 + crow, Yb + (size_t)yrow * NB, bstride, wx, xi, nbv);
+#pragma unroll
+        for (int b = 0; b < NBM; ++b)
+#pragma unroll
+          for (int l = 0; l < 4; ++l) {   // conj(phase) of this piece
+            acc[b][l].x += sb.ph_re * s[b][l].x + sb.ph_im * s[b][l].y;
+            acc[b][l].y += sb.ph_re * s[b][l].y - sb.ph_im * s[b][l].x;
+          }
+      } else {
+        // real data: k = 0, every phase is 1; accumulate in place
+        gather_row<T, NBM, 5>(acc, chi4 + crow, Yb + (size_t)yrow * NB, bstride, wx, xi, nbv);
       }
     }
     rbase += rows;
   }
+  // reduce over the 4 x-lanes (xi) of each orbital lane: fixed butterfly order
 #pragma unroll
-  for (int l = 0; l < 4; ++l) red[warp][l][lane] = acc[l];
-  __syncthreads();
-  if (warp < 4) {   // warp w reduces projector slot l = w over the 8 warps, fixed order
-    const int l = warp;
-    T v = red[0][l][lane];
-    for (int w2 = 1; w2 < 8; ++w2) {
-      if constexpr (FT<T>::cplx) { v.x += red[w2][l][lane].x; v.y += red[w2][l][lane].y; }
-      else v += red[w2][l][lane];
+  for (int b = 0; b < NBM; ++b)
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      if constexpr (FT<T>::cplx) {
+        acc[b][l].x += __shfl_xor_sync(0xffffffffu, acc[b][l].x, 8);
+        acc[b][l].y += __shfl_xor_sync(0xffffffffu, acc[b][l].y, 8);
+        acc[b][l].x += __shfl_xor_sync(0xffffffffu, acc[b][l].x, 16);
+        acc[b][l].y += __shfl_xor_sync(0xffffffffu, acc[b][l].y, 16);
+      } else {
+        acc[b][l] += __shfl_xor_sync(0xffffffffu, acc[b][l], 8);
+        acc[b][l] += __shfl_xor_sync(0xffffffffu, acc[b][l], 16);
+      }
     }
-    if (vb) part[((size_t)(gi * nslab + sl) * 4 + l) * ((size_t)nb * NB) + bi * NB + o] = v;
+  if (xi == 0) {
+#pragma unroll
+    for (int b = 0; b < NBM; ++b)
+#pragma unroll
+      for (int l = 0; l < 4; ++l) red[warp][b][l][o] = acc[b][l];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < NBM * 4 * NB; t += blockDim.x) {   // fixed order over warps
+    const int oo = t % NB, l = (t / NB) % 4, b = t / (4 * NB);
+    if (b >= nbv) continue;
+    T v = red[0][b][l][oo];
+    for (int w2 = 1; w2 < 8; ++w2) {
+      if constexpr (FT<T>::cplx) { v.x += red[w2][b][l][oo].x; v.y += red[w2][b][l][oo].y; }
+      else v += red[w2][b][l][oo];
+    }
+    const int bi = q * NBM + b;
+    part[((size_t)(gi * nslab + sl) * 4 + l) * ((size_t)nb * NB) + bi * NB + oo] = v;
   }
 }
 
@@ -1006,11 +1064,19 @@ __global__ void k_gather_sum(const T* __restrict__ part, const Group* __restrict
 
 // --------------------------------------------------------------------------- launchers
 
-constexpr int NSLAB = 8;
+constexpr int NSLAB_MAX = 16;
+// Row slabs per projector group: enough CTAs for about six per SM, at most 16.
+static int gather_slabs(const sparc_ham* H) {
+  const Tables* Tb = (const Tables*)H->fast;
+  const int want = 6 * H->ctx->nsm;
+  return std::max(1, std::min(NSLAB_MAX, ceil_div(want, std::max(1, Tb->ngrp))));
+}
+template <class T> struct GatherOct { static constexpr int v = 8; };
+template <> struct GatherOct<cf32> { static constexpr int v = 4; };
 
 size_t gather_scratch_bytes(const sparc_ham* H, int nb, size_t esize) {
   const Tables* Tb = (const Tables*)H->fast;
-  return (size_t)std::max(1, Tb->ngrp) * NSLAB * 4 * nb * NB * esize;
+  return (size_t)std::max(1, Tb->ngrp) * NSLAB_MAX * 4 * nb * NB * esize;
 }
 
 template <class T>
@@ -1019,12 +1085,15 @@ cudaError_t launch_gather(const sparc_ham* H, const T* Y, int nblk_total, int bl
   const Tables* Tb = (const Tables*)H->fast;
   if (H->nproj == 0 || Tb->ngrp == 0) return cudaSuccess;
   const float dv = (float)(H->grid.h[0] * H->grid.h[1] * H->grid.h[2]);
+  const int nslab = gather_slabs(H);
+  constexpr int NBM = GatherOct<T>::v;
+  const dim3 grid((unsigned)Tb->ngrp, (unsigned)nslab, (unsigned)ceil_div(nb, NBM));
   cudaEvent_t t0 = timing_begin(H->ctx, st);
-  k_gather_slab<T><<<dim3((unsigned)Tb->ngrp, NSLAB, (unsigned)ceil_div(nb, 4)), 256, 0, st>>>(
-      Y, H->gd.nd, H->gd.n1, H->gd.n2, Tb->d_grp, Tb->d_sb, (const float4*)Tb->d_chi4, scratch, blk0, nb, NSLAB);
+  k_gather_rows<T, NBM><<<grid, 256, 0, st>>>(Y, H->gd.nd, H->gd.n1, H->gd.n2, Tb->d_grp, Tb->d_sb,
+                                              (const float4*)Tb->d_chi4, scratch, blk0, nb, nslab);
   const long long tot = (long long)Tb->ngrp * 4 * nb * NB;
   k_gather_sum<T><<<ceil_div(tot, 256), 256, 0, st>>>(scratch, Tb->d_grp, H->d_gamma32, dv, gc, Tb->ngrp,
-                                                      NSLAB, nblk_total, blk0, nb);
+                                                      nslab, nblk_total, blk0, nb);
   H->ctx->launches += 2;
   timing_end(H->ctx, TK_GATHER, t0, st);
   return cudaGetLastError();
@@ -1071,8 +1140,7 @@ cudaError_t launch_pass(const sparc_ham* H, const T* Yin, const T* Yprev, T* You
     cudaError_t e = cudaFuncSetAttribute(k_pass_f2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int nitems = Lo.tiles_x * Lo.tiles_y * Lo.nchunk * nb;
-    int nsm = 0;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, H->ctx->device);
+    const int nsm = H->ctx->nsm;
     t0 = timing_begin(H->ctx, st);
     k_pass_f2<<<std::min(nitems, std::max(nsm, 1)), THREADS, smem, st>>>(a, Yin, Yprev, Yout, gc, nitems);
   } else {

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "rr.cuh"
@@ -187,6 +188,73 @@ __global__ void __launch_bounds__(1024) k_chol(TW* A, int n, int* status) {
   }
 }
 
+// Diagonal block of the blocked Cholesky, FP64, in shared memory (one CTA):
+// the kb x kb block at A (leading dimension lda, lower part read) is factored
+// right-looking, L is written back over the block (strict upper part zeroed), and
+// L^-1 is formed in place (column-oriented, from the last column to the first)
+// and written to Dk (leading dimension ldd).  Pivot rule as k_chol.
+template <int MB>
+__global__ void __launch_bounds__(256) k_chol_blk(double* A, long long lda, double* Dk, long long ldd, int kb,
+                                                  int* status) {
+  __shared__ double S[MB][MB + 1];
+  __shared__ double x[MB];
+  __shared__ int bad;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) bad = 0;
+  for (int e = tid; e < kb * kb; e += nt) {
+    const int i = e % kb, j = e / kb;
+    S[i][j] = i >= j ? A[i + (long long)j * lda] : 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    if (tid == 0) {
+      // S[j][j] holds a_jj minus the updates of the columns before j
+      const double d = S[j][j];
+      const double ajj = A[j + (long long)j * lda];
+      if (!(d > 1e-14 * ajj) || !isfinite(d)) {
+        bad = 1;
+        atomicOr(status, STATUS_NOT_POSDEF);
+      } else {
+        S[j][j] = sqrt(d);
+      }
+    }
+    __syncthreads();
+    if (bad) return;
+    const double inv = 1.0 / S[j][j];
+    for (int i = j + 1 + tid; i < kb; i += nt) S[i][j] *= inv;
+    __syncthreads();
+    const int m = kb - j - 1;   // trailing lower triangle, column-major over (i, c), c <= i
+    for (int e = tid; e < m * m; e += nt) {
+      const int i = j + 1 + e % m, c = j + 1 + e / m;
+      if (c <= i) S[i][c] -= S[i][j] * S[c][j];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < kb * kb; e += nt) {
+    const int i = e % kb, j = e / kb;
+    A[i + (long long)j * lda] = i >= j ? S[i][j] : 0.0;
+  }
+  __syncthreads();
+  // in-place inverse: for j = kb-1 .. 0, column j below the diagonal becomes
+  // -(1/L_jj) Linv[j+1:, j+1:] L[j+1:, j], using the already inverted trailing block
+  for (int j = kb - 1; j >= 0; --j) {
+    const double ljj = 1.0 / S[j][j];
+    for (int i = j + 1 + tid; i < kb; i += nt) {
+      double s = 0.0;
+      for (int k = j + 1; k <= i; ++k) s += S[i][k] * S[k][j];
+      x[i] = -ljj * s;
+    }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < kb; i += nt) S[i][j] = x[i];
+    if (tid == 0) S[j][j] = ljj;
+    __syncthreads();
+  }
+  for (int e = tid; e < kb * kb; e += nt) {
+    const int i = e % kb, j = e / kb;
+    Dk[i + (long long)j * ldd] = i >= j ? S[i][j] : 0.0;
+  }
+}
+
 // Linv = L^-1 for lower-triangular L (one CTA, one thread per column).
 template <class TW>
 __global__ void __launch_bounds__(1024) k_trinv(const TW* __restrict__ L, TW* __restrict__ Li, int n) {
@@ -313,6 +381,14 @@ k_jacobi_round(const TW* __restrict__ A, TW* __restrict__ An, TW* __restrict__ V
       V[i + (long long)jj[bb] * n] = s;
     }
   }
+}
+
+// out = in^T (n x n, column-major)
+__global__ void k_transpose(const double* __restrict__ in, double* __restrict__ out, int n) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  const int i = (int)(e % n), j = (int)(e / n);
+  out[j + (long long)i * n] = in[e];
 }
 
 template <class TW>
@@ -457,14 +533,20 @@ sparc_status chol_inverse(sparc_ctx* ctx, TW* A, TW* Li, int n, TW* Dinv, TW* tm
     TW* Dk = Dinv + (size_t)kblk * CB * CB;
     TW* Akk = A + k0 + (long long)k0 * n;
     // diagonal block: contiguous copy, one-CTA factor and inverse, copies back
-    TW* blk = part;                     // kb x kb, leading dimension kb
-    TW* blki = part + (size_t)CB * CB;  // its inverse
-    k_copy2d<TW><<<ceil_div((long long)kb * kb, 256), 256, 0, st>>>(Akk, n, blk, kb, kb, kb);
-    k_chol<TW><<<1, 1024, 0, st>>>(blk, kb, ctx->d_status);
-    k_trinv<TW><<<1, 1024, 0, st>>>(blk, blki, kb);
-    k_copy2d<TW><<<ceil_div((long long)kb * kb, 256), 256, 0, st>>>(blk, kb, Akk, n, kb, kb);
-    k_copy2d<TW><<<ceil_div((long long)kb * kb, 256), 256, 0, st>>>(blki, kb, Dk, CB, kb, kb);
-    ctx->launches += 5;
+    if constexpr (std::is_same<TW, double>::value) {
+      // factor and invert the block in shared memory, one launch
+      k_chol_blk<CB><<<1, 256, 0, st>>>(Akk, n, Dk, CB, kb, ctx->d_status);
+      ctx->launches += 1;
+    } else {
+      TW* blk = part;                     // kb x kb, leading dimension kb
+      TW* blki = part + (size_t)CB * CB;  // its inverse
+      k_copy2d<TW><<<ceil_div((long long)kb * kb, 256), 256, 0, st>>>(Akk, n, blk, kb, kb, kb);
+      k_chol<TW><<<1, 1024, 0, st>>>(blk, kb, ctx->d_status);
+      k_trinv<TW><<<1, 1024, 0, st>>>(blk, blki, kb);
+      k_copy2d<TW><<<ceil_div((long long)kb * kb, 256), 256, 0, st>>>(blk, kb, Akk, n, kb, kb);
+      k_copy2d<TW><<<ceil_div((long long)kb * kb, 256), 256, 0, st>>>(blki, kb, Dk, CB, kb, kb);
+      ctx->launches += 5;
+    }
     SPARC_LAUNCH(ctx, "cholesky block");
     const int m2 = n - k0 - kb;
     if (m2 > 0) {
@@ -570,8 +652,11 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
   const size_t partb = align256((size_t)std::max<long long>(std::max<long long>(nsplit, 8) * nn, 2LL * CB * CB) * ew);
   const int nbk = ceil_div(ns, CB);
   const size_t dinvb = align256((size_t)nbk * CB * CB * ew);
+  constexpr bool TCP = std::is_same<T, float>::value;   // FP32 data: tensor-core Grams and rotation
+  const size_t tcb = TCP ? align256(std::max(tc::gram_scratch_bytes(ctx, ns, nd), tc::rot_scratch_bytes(ns))) : 0;
+  const size_t w1b = TCP ? hub : 0;   // U1, the orthonormalised basis
   const size_t extra = hub + 2 * partb + 10 * sm + dinvb + align256(nn * es) + 3 * align256(nn * sizeof(TS)) +
-                       align256(ns * sizeof(double)) + 256;
+                       align256(ns * sizeof(double)) + tcb + w1b + 256;
   BlockWs w;
   char* tail = nullptr;
   sparc_status s = block_ws(H, DtypeOf<T>::v, ns, extra, &w, &tail);
@@ -594,25 +679,67 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
   TS* S0 = (TS*)tail; tail += align256(nn * sizeof(TS));
   TS* S1 = (TS*)tail; tail += align256(nn * sizeof(TS));
   TS* SV = (TS*)tail; tail += align256(nn * sizeof(TS));
-  double* lam = (double*)tail;
+  double* lam = (double*)tail; tail += align256(ns * sizeof(double));
+  void* tcs = tail; tail += tcb;
+  T* W1 = (T*)tail;
   const long long pcap = (long long)(partb / ew);
 
-  // 1. HU = H U
-  s = apply_block<T>(H, U, HU, ns, ld, st, w);
+  T* Ub = U;            // basis of the Rayleigh-Ritz pass
+  long long ldb = ld;
+  cudaEvent_t tg = nullptr;
+  if constexpr (TCP) {
+    // FP32 data: orthonormalise first (Cholesky-QR, U1 = U L^-T), then Rayleigh-Ritz in
+    // the basis U1 with H U1 applied to it.  The filtered block is ill-conditioned
+    // (kappa(M~) grows like the square of the filter's gain T_m), and one Cholesky of
+    // M~ amplifies the Gram's rounding by kappa; in the basis U1 the pencil has M~1 ~ I.
+    // Both bases span the same subspace (Eq. SubspaceGeneralizedEigenproblem).
+    tg = timing_begin(ctx, st);
+    SPARC_CUDA(ctx, tc::gram(ctx, U, ld, U, ld, nd, ns, Ms, tcs, st));
+    SPARC_LAUNCH(ctx, "gram M0");
+    timing_end(ctx, TK_GRAM, tg, st);
+    cudaEvent_t t0 = timing_begin(ctx, st);
+    s = chol_inverse<TW>(ctx, Ms, Li, ns, Dinv, T1, partH, pcap, st);
+    if (s != SPARC_OK) return s;
+    int w0 = 0;
+    SPARC_CUDA(ctx, cudaMemcpyAsync(&w0, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SPARC_CUDA(ctx, cudaStreamSynchronize(st));
+    if (w0 & STATUS_NOT_POSDEF) {
+      cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st);
+      return fail(ctx, SPARC_ERR_NOT_POSDEF, "M~ = U^H U is not positive definite");
+    }
+    k_transpose<<<ceil_div(nn, 256), 256, 0, st>>>((const double*)Li, (double*)T1, ns);
+    ++ctx->launches;
+    timing_end(ctx, TK_EIG, t0, st);
+    cudaEvent_t t1 = timing_begin(ctx, st);
+    SPARC_CUDA(ctx, tc::rotate(ctx, U, ld, (const double*)T1, nd, ns, W1, nd, tcs, st));   // U1
+    SPARC_LAUNCH(ctx, "orthonormalise");
+    timing_end(ctx, TK_ROT, t1, st);
+    Ub = W1;
+    ldb = nd;
+  }
+  // 1. HU = H U (U1 for FP32 data)
+  s = apply_block<T>(H, Ub, HU, ns, ldb, st, w);
   if (s != SPARC_OK) return s;
   // 2. H~ = U^H (HU), M~ = U^H U (split-K partials, then fixed-order sum + symmetrisation)
-  cudaEvent_t tg = timing_begin(ctx, st);
-  SPARC_CUDA(ctx, (gemm<T, T, TC, TW, true, false>(ctx, ns, ns, (int)nd, U, ld, HU, nd, partH, ns, nsplit,
-                                                   nn, 1.0, st)));
-  SPARC_LAUNCH(ctx, "gram H");
-  SPARC_CUDA(ctx, (gemm<T, T, TC, TW, true, false>(ctx, ns, ns, (int)nd, U, ld, U, ld, partM, ns, nsplit,
-                                                   nn, 1.0, st)));
-  SPARC_LAUNCH(ctx, "gram M");
-  k_reduce_sym<TW><<<ceil_div(nn, 256), 256, 0, st>>>(partH, nsplit, nn, ns, Hs);
-  ++ctx->launches;
-  k_reduce_sym<TW><<<ceil_div(nn, 256), 256, 0, st>>>(partM, nsplit, nn, ns, Ms);
-  ++ctx->launches;
-  SPARC_LAUNCH(ctx, "gram");
+  tg = timing_begin(ctx, st);
+  if constexpr (TCP) {
+    SPARC_CUDA(ctx, tc::gram(ctx, Ub, nd, HU, nd, nd, ns, Hs, tcs, st));
+    SPARC_LAUNCH(ctx, "gram H");
+    SPARC_CUDA(ctx, tc::gram(ctx, Ub, nd, Ub, nd, nd, ns, Ms, tcs, st));
+    SPARC_LAUNCH(ctx, "gram M");
+  } else {
+    SPARC_CUDA(ctx, (gemm<T, T, TC, TW, true, false>(ctx, ns, ns, (int)nd, U, ld, HU, nd, partH, ns, nsplit,
+                                                     nn, 1.0, st)));
+    SPARC_LAUNCH(ctx, "gram H");
+    SPARC_CUDA(ctx, (gemm<T, T, TC, TW, true, false>(ctx, ns, ns, (int)nd, U, ld, U, ld, partM, ns, nsplit,
+                                                     nn, 1.0, st)));
+    SPARC_LAUNCH(ctx, "gram M");
+    k_reduce_sym<TW><<<ceil_div(nn, 256), 256, 0, st>>>(partH, nsplit, nn, ns, Hs);
+    ++ctx->launches;
+    k_reduce_sym<TW><<<ceil_div(nn, 256), 256, 0, st>>>(partM, nsplit, nn, ns, Ms);
+    ++ctx->launches;
+    SPARC_LAUNCH(ctx, "gram");
+  }
   timing_end(ctx, TK_GRAM, tg, st);
   cudaEvent_t te = timing_begin(ctx, st);
   // 3. M~ = L L^H (blocked, FP64) and Linv = L^-1
@@ -651,8 +778,13 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
     TS* Sres = nullptr;
     s = jacobi<TS>(ctx, S0, S1, SV, ns, 1e-10, 40, scal, &Sres, &sweeps, st);
     if (s != SPARC_OK) return s;
-    k_convert<TS, TW><<<ceil_div(nn, 256), 256, 0, st>>>(SV, Vj, nn);
+    k_convert<TS, TW><<<ceil_div(nn, 256), 256, 0, st>>>(SV, A1, nn);
     ++ctx->launches;
+    // FP32 Jacobi vectors are orthonormal to about (rotations per vector) x u32; one
+    // Newton-Schulz step in FP64, V <- V (3 I - V^H V) / 2, squares that error
+    SPARC_CUDA(ctx, (gemm64<TW, true, false>(ctx, ns, ns, ns, A1, ns, A1, ns, T1, ns, 1.0, 0.0, partH, pcap, st)));
+    SPARC_CUDA(ctx, cudaMemcpyAsync(Vj, A1, nn * sizeof(TW), cudaMemcpyDeviceToDevice, st));
+    SPARC_CUDA(ctx, (gemm64<TW, false, false>(ctx, ns, ns, ns, A1, ns, T1, ns, Vj, ns, -0.5, 1.5, partH, pcap, st)));
     SPARC_CUDA(ctx, (gemm64<TW, false, false>(ctx, ns, ns, ns, A0, ns, Vj, ns, T1, ns, 1.0, 0.0, partH, pcap, st)));
     k_rayleigh<TW><<<ceil_div(ns, 128), 128, 0, st>>>(Vj, T1, ns, lam);
     ++ctx->launches;
@@ -663,13 +795,19 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
   // 6. Ritz vectors of the pencil: Yr = Linv^H Q
   SPARC_CUDA(ctx, (gemm64<TW, true, false>(ctx, ns, ns, ns, Li, ns, Qs, ns, Yr, ns, 1.0, 0.0, partH, pcap, st)));
   // 7. rotation U <- U Yr (into HU, then back into U)
-  k_narrow<TW, T><<<ceil_div(nn, 256), 256, 0, st>>>(Yr, YrT, nn);
-  ++ctx->launches;
+  if constexpr (!TCP) {
+    k_narrow<TW, T><<<ceil_div(nn, 256), 256, 0, st>>>(Yr, YrT, nn);
+    ++ctx->launches;
+  }
   SPARC_LAUNCH(ctx, "ritz vectors");
   timing_end(ctx, TK_EIG, te, st);
   cudaEvent_t tr = timing_begin(ctx, st);
-  SPARC_CUDA(ctx, (gemm<T, T, TC, T, false, false>(ctx, (int)nd, ns, ns, U, ld, YrT, ns, HU, nd, 1, 0, 1.0, st)));
-  SPARC_CUDA(ctx, cudaMemcpy2DAsync(U, ld * es, HU, nd * es, nd * es, ns, cudaMemcpyDeviceToDevice, st));
+  if constexpr (TCP) {
+    SPARC_CUDA(ctx, tc::rotate(ctx, Ub, ldb, Yr, nd, ns, U, ld, tcs, st));   // U1 -> U
+  } else {
+    SPARC_CUDA(ctx, (gemm<T, T, TC, T, false, false>(ctx, (int)nd, ns, ns, U, ld, YrT, ns, HU, nd, 1, 0, 1.0, st)));
+    SPARC_CUDA(ctx, cudaMemcpy2DAsync(U, ld * es, HU, nd * es, nd * es, ns, cudaMemcpyDeviceToDevice, st));
+  }
   timing_end(ctx, TK_ROT, tr, st);
   return SPARC_OK;
 }

@@ -23,4 +23,16 @@ sparc_status apply_block(sparc_ham* H, const T* X, T* Y, int ns, long long ld, c
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Tensor-core (tcgen05, 3xTF32) products of FP32 orbitals (tc_gemm.cu).
+namespace tc {
+// G = A^T B (ns x ns, FP64, symmetrised) for column-major nd x ns FP32 A, B.
+size_t gram_scratch_bytes(const sparc_ctx* ctx, int ns, long long nd);
+cudaError_t gram(sparc_ctx* ctx, const float* A, long long lda, const float* B, long long ldb, long long nd, int ns,
+                 double* G, void* scratch, cudaStream_t st);
+// C = U Yr (nd x ns, FP32) for column-major FP32 U and FP64 ns x ns Yr; C must not overlap U.
+size_t rot_scratch_bytes(int ns);
+cudaError_t rotate(sparc_ctx* ctx, const float* U, long long ldu, const double* Yr, long long nd, int ns, float* C,
+                   long long ldc, void* scratch, cudaStream_t st);
+}  // namespace tc
+
 }  // namespace sparc

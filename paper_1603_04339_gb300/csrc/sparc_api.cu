@@ -268,8 +268,7 @@ sparc_status filter_block_fast(sparc_ham* H, int m, double a, double b, double a
   const size_t per_blk = 2 * (size_t)H->gd.nd * NB * sizeof(T);
   const int gmax = std::max(1, std::min(nblk, (int)((size_t)90 * 1024 * 1024 / per_blk)));
   const int items_per_blk = fast::items_per_block<T>(H);
-  int nsm = 152;
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, H->ctx->device);
+  const int nsm = H->ctx->nsm;
   int G = gmax;
   double best = -1.0;
   for (int g = std::max(1, gmax / 2); g <= gmax; ++g) {
@@ -327,6 +326,7 @@ sparc_status sparc_create(sparc_ctx** out, int device) {
     delete ctx;
     return SPARC_ERR_CUDA;
   }
+  cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, device);
   *out = ctx;
   return SPARC_OK;
 }
@@ -415,6 +415,7 @@ sparc_status sparc_ham_create(sparc_ctx* ctx, const sparc_grid* grid, const doub
   sparc_ham* H = new (std::nothrow) sparc_ham();
   if (!H) return fail(ctx, SPARC_ERR_OOM, "host allocation failed");
   H->ctx = ctx;
+  H->device = ctx->device;
   H->grid = gr;
   GridDev& gd = H->gd;
   gd.n1 = gr.n[0];
@@ -556,7 +557,7 @@ sparc_status sparc_ham_set_veff(sparc_ham* H, const double* veff, int on_device,
 
 void sparc_ham_destroy(sparc_ham* H) {
   if (!H) return;
-  cudaSetDevice(H->ctx->device);
+  cudaSetDevice(H->device);
   cudaDeviceSynchronize();
   void* ptrs[] = {H->d_veff, H->d_veff32, H->d_gamma, H->d_gamma32, H->d_p_off, H->d_p_g,
                   H->d_pt_ptr, H->d_pt_p};

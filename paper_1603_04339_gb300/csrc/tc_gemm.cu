@@ -1,0 +1,510 @@
+// Tensor-core products of Rayleigh-Ritz for FP32 orbitals (Section 3.4: the
+// projections of Eq. SubspaceGeneralizedEigenproblem and the rotation of Eq.
+// OrbitalTransformation) on sm_103a.
+//
+// tcgen05.mma kind::tf32 with the accumulator in tensor memory (TMEM).  Operands
+// are staged in shared memory in the canonical K-major layout with the 128-byte
+// swizzle (rows of 32 FP32 values, 8-row groups 1024 bytes apart).  Products
+// are error-compensated ("3xTF32"):
+//   a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi,
+// where a_hi keeps the sign, exponent and top 10 stored mantissa bits of a and
+// a_lo = a - a_hi exactly; a_lo b_lo (relative size 2^-22) is dropped.
+//
+// Gram  G = A^T B (Ns x Ns, FP64): one CTA per (upper-triangular 128 x 128 tile
+//   pair, split of the Nd range); the CTA accumulates GCH k-tiles at a time in
+//   TMEM (FP32; a_hi b_hi and the cross terms in separate accumulators) and adds
+//   each chunk in FP64 to its own partial; a second kernel
+//   sums the splits in a fixed order and mirrors the tiles, so the result is
+//   deterministic.
+// Rotation  C = U Yr (Nd x Ns): one CTA per (128 grid rows, 256 columns); Yr is
+//   split and swizzled once into its shared-memory images, U is split and
+//   transposed to K-major on its way into shared memory.
+#include <algorithm>
+
+#include "ptx.cuh"
+#include "rr.cuh"
+
+namespace sparc {
+namespace tc {
+namespace {
+
+constexpr int BM = 128;        // MMA M: rows of D = TMEM lanes
+constexpr int BK = 32;         // k-tile: 32 FP32 values = one 128-byte swizzled row
+constexpr int THREADS = 256;
+constexpr int GN = 128;        // Gram tile N
+constexpr int GST = 3;         // Gram pipeline stages
+constexpr int GCH = 8;         // Gram k-tiles per FP32 accumulation chunk (256 grid points)
+constexpr int RN = 256;        // rotation tile N
+constexpr int RST = 2;         // rotation pipeline stages
+constexpr int TILE_A = BM * BK * 4;   // 16 KB: one 128-row operand image
+constexpr int GSTAGE = 4 * TILE_A;    // A_hi, A_lo, B_hi, B_lo
+constexpr int RSTAGE = 2 * TILE_A + 2 * (RN * BK * 4);
+constexpr int GSMEM = GST * GSTAGE + 1024;
+constexpr int RSMEM = RST * RSTAGE + 1024;
+
+// ------------------------------------------------------------------ PTX wrappers
+using ptx::mbar_init;
+using ptx::mbar_wait;
+using ptx::saddr;
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {   // whole warp
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(dst)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_free(uint32_t taddr, uint32_t ncols) {     // whole warp
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// make this thread's generic-proxy shared-memory writes visible to the tensor core
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+// arrive once on `bar` when every tcgen05.mma issued so far by this thread has completed
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+               : "memory");
+}
+// thread l of the warp reads TMEM lane (lane field of taddr) + l, 32 consecutive columns
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B
+// apart (stride byte offset), descriptor version 1, base offset 0 (operand images
+// start on 1024-byte boundaries; the start address advances 32 B per K = 8 step).
+__device__ __forceinline__ uint64_t desc_k128(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// Instruction descriptor, kind::tf32: D FP32, A and B TF32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+// byte offset of 16-byte chunk c (0..7) of row r in a swizzled operand image
+__device__ __forceinline__ uint32_t swz(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
+
+__device__ __forceinline__ void split(float x, float& hi, float& lo) {
+  hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+  lo = x - hi;   // exact: x and hi share the exponent
+}
+__device__ __forceinline__ void split4(float4 x, float4& hi, float4& lo) {
+  split(x.x, hi.x, lo.x); split(x.y, hi.y, lo.y); split(x.z, hi.z, lo.z); split(x.w, hi.w, lo.w);
+}
+
+// Issue the 12 MMAs of one k-tile (4 K-steps x 3 products): a_hi b_hi into d, the
+// two small cross products into ds (ds == d accumulates all three together).  The
+// tensor core's FP32 accumulation rounds each addition, so keeping the small terms
+// apart from the large one, and the chunks short, bounds the accumulated rounding.
+__device__ __forceinline__ void mma_ktile(uint32_t d, uint32_t ds, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
+                                          uint32_t b_lo, uint32_t idesc, bool overwrite) {
+#pragma unroll
+  for (int kk = 0; kk < BK / 8; ++kk) {
+    const uint64_t ah = desc_k128(a_hi + kk * 32), al = desc_k128(a_lo + kk * 32);
+    const uint64_t bh = desc_k128(b_hi + kk * 32), bl = desc_k128(b_lo + kk * 32);
+    const bool first = overwrite && kk == 0;
+    mma_tf32(d, ah, bh, idesc, first ? 0u : 1u);
+    mma_tf32(ds, ah, bl, idesc, (first && ds != d) ? 0u : 1u);
+    mma_tf32(ds, al, bh, idesc, 1u);
+  }
+}
+
+// ------------------------------------------------------------------ Gram
+// Load one k-tile (rows i0..i0+127 of A^T and j0..j0+127 of B^T, grid points
+// g0..g0+31) into registers: thread t holds 16-byte chunks f = t + 256 q,
+// row f / 8, chunk f % 8.  Out-of-range rows or points read as zero.
+template <bool VEC>
+__device__ __forceinline__ void gram_load(const float* __restrict__ X, long long ldx, int r0, int ns, long long nd,
+                                          long long g0, float4 (&v)[4]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int f = threadIdx.x + THREADS * q;
+    const int r = f >> 3, c = f & 7;
+    const long long g = g0 + 4 * c;
+    const bool rok = r0 + r < ns;
+    const float* p = X + (long long)(r0 + r) * ldx + g;
+    if (VEC) {
+      v[q] = (rok && g < nd) ? __ldg((const float4*)p) : make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      v[q].x = (rok && g + 0 < nd) ? __ldg(p + 0) : 0.f;
+      v[q].y = (rok && g + 1 < nd) ? __ldg(p + 1) : 0.f;
+      v[q].z = (rok && g + 2 < nd) ? __ldg(p + 2) : 0.f;
+      v[q].w = (rok && g + 3 < nd) ? __ldg(p + 3) : 0.f;
+    }
+  }
+}
+__device__ __forceinline__ void gram_store(uint8_t* hi, uint8_t* lo, const float4 (&v)[4]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int f = threadIdx.x + THREADS * q;
+    const uint32_t off = swz(f >> 3, f & 7);
+    float4 h, l;
+    split4(v[q], h, l);
+    *(float4*)(hi + off) = h;
+    *(float4*)(lo + off) = l;
+  }
+}
+
+// part[(blockIdx.x * nsplit + split)][j][i] = sum over this CTA's grid points of
+// A[g][ti*128 + i] B[g][tj*128 + j]  (tile pair blockIdx.x = (ti <= tj), split = blockIdx.y)
+template <bool VEC>
+__global__ void __launch_bounds__(THREADS, 1)
+k_gram_tc(const float* __restrict__ A, long long lda, const float* __restrict__ B, long long ldb, long long nd,
+          int ns, int nt, int nsplit, double* __restrict__ part, int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t bar[GST];
+  __shared__ uint32_t tmem_base;
+  const uint32_t raw = saddr(smem_raw);
+  uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  int pr = blockIdx.x, ti = 0;
+  while (pr >= nt - ti) { pr -= nt - ti; ++ti; }
+  const int tj = ti + pr;
+  const int sp = blockIdx.y;
+  const long long nkt_all = (nd + BK - 1) / BK;
+  const long long kt0 = nkt_all * sp / nsplit;
+  const int nkt = (int)(nkt_all * (sp + 1) / nsplit - kt0);
+  double* P = part + (size_t)(blockIdx.x * nsplit + sp) * (BM * GN);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (nkt <= 0) {   // empty split: a zero partial
+    for (int e = threadIdx.x; e < BM * GN; e += THREADS) P[e] = 0.0;
+    return;
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < GST; ++s) mbar_init(&bar[s], 1);
+    ptx::mbar_init_fence();
+  }
+  if (warp == 0) tmem_alloc(&tmem_base, 2 * GN);   // D (a_hi b_hi) and Ds (cross terms)
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = tmem_base;
+  constexpr uint32_t IDESC = idesc_tf32(BM, GN);
+  const int i0 = ti * BM, j0 = tj * GN;
+  float4 ca[4], cb[4], na[4], nb[4];
+  gram_load<VEC>(A, lda, i0, ns, nd, kt0 * BK, ca);
+  gram_load<VEC>(B, ldb, j0, ns, nd, kt0 * BK, cb);
+  bool first_flush = true, aborted = false;
+  int last = -1;
+  for (int t = 0; t < nkt; ++t) {
+    const int s = t % GST;
+    if (t + 1 < nkt) {
+      gram_load<VEC>(A, lda, i0, ns, nd, (kt0 + t + 1) * BK, na);
+      gram_load<VEC>(B, ldb, j0, ns, nd, (kt0 + t + 1) * BK, nb);
+    }
+    bool ok = true;
+    if (t >= GST) ok = mbar_wait(&bar[s], (uint32_t)((t / GST) - 1) & 1u);   // MMAs of tile t - GST done
+    uint8_t* st = sm + s * GSTAGE;
+    gram_store(st, st + TILE_A, ca);
+    gram_store(st + 2 * TILE_A, st + 3 * TILE_A, cb);
+    proxy_fence();
+    if (__syncthreads_or(!ok)) { aborted = true; break; }
+    if (threadIdx.x == 0) {
+      tc_after();
+      const uint32_t b0 = saddr(st);
+      mma_ktile(tmem, tmem + GN, b0, b0 + TILE_A, b0 + 2 * TILE_A, b0 + 3 * TILE_A, IDESC, t % GCH == 0);
+      mma_commit(&bar[s]);
+    }
+    last = t;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { ca[q] = na[q]; cb[q] = nb[q]; }
+    if (t % GCH == GCH - 1 || t == nkt - 1) {
+      // drain the FP32 chunk in TMEM into the FP64 partial
+      ok = mbar_wait(&bar[s], (uint32_t)(t / GST) & 1u);
+      tc_after();
+      const int row = 32 * (warp & 3) + lane;
+      const int c0 = (warp >> 2) * (GN / 2);
+#pragma unroll
+      for (int h = 0; h < GN / 64; ++h) {
+        float v[32], vs[32];
+        const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(c0 + 32 * h);
+        tmem_ld32(ta, v);
+        tmem_ld32(ta + GN, vs);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          double* p = P + (size_t)(c0 + 32 * h + c) * BM + row;
+          const double x = (double)v[c] + (double)vs[c];
+          *p = first_flush ? x : *p + x;
+        }
+      }
+      first_flush = false;
+      tc_before();
+      if (__syncthreads_or(!ok)) { aborted = true; break; }
+    }
+  }
+  if (aborted) {
+    if (threadIdx.x == 0) {
+      atomicOr(status, STATUS_TIMEOUT);
+      if (last >= 0) mbar_wait(&bar[last % GST], (uint32_t)(last / GST) & 1u);
+    }
+    tc_before();
+    __syncthreads();
+  }
+  tc_after();
+  if (warp == 0) tmem_free(tmem, 2 * GN);
+}
+
+// G[i + j ns] from the partials: fixed-order sum over splits; tile pairs below the
+// diagonal are the transposes of those above; diagonal tiles are symmetrised.
+__global__ void k_gram_reduce(const double* __restrict__ part, int nt, int nsplit, int ns, double* __restrict__ G) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)ns * ns) return;
+  const int i = (int)(e % ns), j = (int)(e / ns);
+  const int ti = i / BM, tj = j / GN, ii = i % BM, jj = j % GN;
+  auto pidx = [&](int a, int b) { return a * nt - a * (a - 1) / 2 + (b - a); };
+  const int p = ti <= tj ? pidx(ti, tj) : pidx(tj, ti);
+  const double* P = part + (size_t)p * nsplit * (BM * GN);
+  double a = 0.0, b = 0.0;
+  for (int s = 0; s < nsplit; ++s) {
+    const double* Ps = P + (size_t)s * (BM * GN);
+    if (ti <= tj) a += Ps[(size_t)jj * BM + ii];
+    if (ti >= tj) b += Ps[(size_t)ii * BM + jj];
+  }
+  G[e] = ti < tj ? a : (ti > tj ? b : 0.5 * (a + b));
+}
+
+// ------------------------------------------------------------------ rotation
+// Shared-memory images of Yr: for column half nh (256 columns) and k-tile t,
+// hi then lo, each 256 rows (columns n of Yr) x 32 values (rows k of Yr), swizzled.
+__global__ void k_rot_pack(const double* __restrict__ Yr, int ns, int nkt, int nnh, float* __restrict__ bp) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)nnh * nkt * RN * BK) return;
+  const int kk = (int)(e % BK), r = (int)((e / BK) % RN);
+  const int t = (int)((e / (BK * RN)) % nkt), nh = (int)(e / ((long long)BK * RN * nkt));
+  const int n = nh * RN + r, k = t * BK + kk;
+  const float x = (n < ns && k < ns) ? (float)Yr[k + (size_t)n * ns] : 0.f;
+  float hi, lo;
+  split(x, hi, lo);
+  const size_t img = (size_t)(nh * nkt + t) * 2 * (RN * BK);
+  const int off = r * BK + ((((kk >> 2) ^ (r & 7)) << 2) | (kk & 3));
+  bp[img + off] = hi;
+  bp[img + RN * BK + off] = lo;
+}
+
+// C[g + n ldc] = sum_k U[g + k ldu] Yr[k + n ns] for g in [128 blockIdx.y, +128),
+// n in [256 blockIdx.x, +256).
+__global__ void __launch_bounds__(THREADS, 1)
+k_rot_tc(const float* __restrict__ U, long long ldu, const float* __restrict__ bp, long long nd, int ns, int nkt,
+         float* __restrict__ C, long long ldc, int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t bar[RST];
+  __shared__ uint32_t tmem_base;
+  const uint32_t raw = saddr(smem_raw);
+  uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  const int nh = blockIdx.x;
+  const long long m0 = (long long)blockIdx.y * BM;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < RST; ++s) mbar_init(&bar[s], 1);
+    ptx::mbar_init_fence();
+  }
+  if (warp == 0) tmem_alloc(&tmem_base, 2 * RN);   // D (a_hi b_hi) and Ds (cross terms)
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = tmem_base;
+  constexpr uint32_t IDESC = idesc_tf32(BM, RN);
+  // A: thread t loads grid row gl = t % 128 at 16 consecutive k (kh = t / 128 picks the half)
+  const int gl = threadIdx.x & (BM - 1), kh = threadIdx.x >> 7;
+  const long long g = m0 + gl;
+  const bool gok = g < nd;
+  auto load_a = [&](int t, float (&v)[16]) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int k = t * BK + kh * 16 + j;
+      v[j] = (gok && k < ns) ? __ldg(U + g + (long long)k * ldu) : 0.f;
+    }
+  };
+  auto load_b = [&](int t, int s) {   // the hi and lo images of Yr, 64 KB
+    const float* src = bp + (size_t)(nh * nkt + t) * 2 * (RN * BK);
+    const uint32_t dst = saddr(sm + s * RSTAGE + 2 * TILE_A);
+#pragma unroll 4
+    for (int q = 0; q < (2 * RN * BK * 4) / (16 * THREADS); ++q) {
+      const int f = threadIdx.x + THREADS * q;
+      cp_async16(dst + 16 * f, src + 4 * f);
+    }
+    cp_async_commit();
+  };
+  float ca[16], na[16];
+  load_b(0, 0);
+  load_a(0, ca);
+  bool aborted = false;
+  int last = -1;
+  for (int t = 0; t < nkt; ++t) {
+    const int s = t & 1, s1 = s ^ 1;
+    bool ok = true;
+    if (t + 1 < nkt) {
+      if (t >= 1) ok = mbar_wait(&bar[s1], (uint32_t)((t - 1) >> 1) & 1u);   // MMAs of tile t - 1 done
+      load_b(t + 1, s1);
+      load_a(t + 1, na);
+    }
+    uint8_t* st = sm + s * RSTAGE;
+#pragma unroll
+    for (int c4 = 0; c4 < 4; ++c4) {   // chunk kh*4 + c4 of row gl: k = kh*16 + 4*c4 .. +3
+      float4 x = make_float4(ca[4 * c4], ca[4 * c4 + 1], ca[4 * c4 + 2], ca[4 * c4 + 3]), h, l;
+      split4(x, h, l);
+      const uint32_t off = swz(gl, kh * 4 + c4);
+      *(float4*)(st + off) = h;
+      *(float4*)(st + TILE_A + off) = l;
+    }
+    if (t + 1 < nkt) cp_async_wait<1>(); else cp_async_wait<0>();
+    proxy_fence();
+    if (__syncthreads_or(!ok)) { aborted = true; break; }
+    if (threadIdx.x == 0) {
+      tc_after();
+      const uint32_t b0 = saddr(st);
+      mma_ktile(tmem, tmem + RN, b0, b0 + TILE_A, b0 + 2 * TILE_A, b0 + 2 * TILE_A + RN * BK * 4, IDESC, t == 0);
+      mma_commit(&bar[s]);
+    }
+    last = t;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) ca[j] = na[j];
+  }
+  bool ok = true;
+  if (last >= 0) ok = mbar_wait(&bar[last & 1], (uint32_t)(last >> 1) & 1u);
+  if (!ok || aborted) {
+    if (threadIdx.x == 0) atomicOr(status, STATUS_TIMEOUT);
+  } else {
+    tc_after();
+    const int row = 32 * (warp & 3) + lane;
+    const long long gr = m0 + row;
+    const int c0 = (warp >> 2) * (RN / 2);
+#pragma unroll
+    for (int h = 0; h < RN / 64; ++h) {
+      float v[32], vs[32];
+      const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(c0 + 32 * h);
+      tmem_ld32(ta, v);
+      tmem_ld32(ta + RN, vs);
+      if (gr < nd) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const int n = nh * RN + c0 + 32 * h + c;
+          if (n < ns) C[gr + (long long)n * ldc] = v[c] + vs[c];
+        }
+      }
+    }
+  }
+  tc_before();
+  __syncthreads();
+  tc_after();
+  if (warp == 0) tmem_free(tmem, 2 * RN);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host side
+static int gram_nsplit(const sparc_ctx* ctx, int ns, long long nd) {
+  const int nt = ceil_div(ns, BM);
+  const int pairs = nt * (nt + 1) / 2;
+  const long long nkt = (nd + BK - 1) / BK;
+  int nsplit = std::max(1, ctx->nsm / pairs);
+  return (int)std::max<long long>(1, std::min<long long>(nsplit, nkt));
+}
+
+size_t gram_scratch_bytes(const sparc_ctx* ctx, int ns, long long nd) {
+  const int nt = ceil_div(ns, BM);
+  return (size_t)(nt * (nt + 1) / 2) * gram_nsplit(ctx, ns, nd) * BM * GN * sizeof(double);
+}
+
+cudaError_t gram(sparc_ctx* ctx, const float* A, long long lda, const float* B, long long ldb, long long nd, int ns,
+                 double* G, void* scratch, cudaStream_t st) {
+  const int nt = ceil_div(ns, BM);
+  const int pairs = nt * (nt + 1) / 2;
+  const int nsplit = gram_nsplit(ctx, ns, nd);
+  const bool vec = (lda % 4 == 0) && (ldb % 4 == 0) && (nd % 4 == 0) && ((uintptr_t)A % 16 == 0) &&
+                   ((uintptr_t)B % 16 == 0);
+  cudaError_t e;
+  if (vec) {
+    e = cudaFuncSetAttribute(k_gram_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, GSMEM);
+    if (e != cudaSuccess) return e;
+    k_gram_tc<true><<<dim3(pairs, nsplit), THREADS, GSMEM, st>>>(A, lda, B, ldb, nd, ns, nt, nsplit,
+                                                                 (double*)scratch, ctx->d_status);
+  } else {
+    e = cudaFuncSetAttribute(k_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, GSMEM);
+    if (e != cudaSuccess) return e;
+    k_gram_tc<false><<<dim3(pairs, nsplit), THREADS, GSMEM, st>>>(A, lda, B, ldb, nd, ns, nt, nsplit,
+                                                                  (double*)scratch, ctx->d_status);
+  }
+  const long long nn = (long long)ns * ns;
+  k_gram_reduce<<<(unsigned)ceil_div(nn, 256), 256, 0, st>>>((const double*)scratch, nt, nsplit, ns, G);
+  ctx->launches += 2;
+  return cudaGetLastError();
+}
+
+size_t rot_scratch_bytes(int ns) {
+  const int nkt = ceil_div(ns, BK), nnh = ceil_div(ns, RN);
+  return (size_t)nnh * nkt * 2 * RN * BK * sizeof(float);
+}
+
+cudaError_t rotate(sparc_ctx* ctx, const float* U, long long ldu, const double* Yr, long long nd, int ns, float* C,
+                   long long ldc, void* scratch, cudaStream_t st) {
+  const int nkt = ceil_div(ns, BK), nnh = ceil_div(ns, RN);
+  if ((nd + BM - 1) / BM > 65535) return cudaErrorInvalidValue;   // grid y limit
+  const long long npack = (long long)nnh * nkt * RN * BK;
+  k_rot_pack<<<(unsigned)ceil_div(npack, 256), 256, 0, st>>>(Yr, ns, nkt, nnh, (float*)scratch);
+  cudaError_t e = cudaFuncSetAttribute(k_rot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, RSMEM);
+  if (e != cudaSuccess) return e;
+  k_rot_tc<<<dim3(nnh, (unsigned)ceil_div(nd, BM)), THREADS, RSMEM, st>>>(U, ldu, (const float*)scratch, nd, ns, nkt,
+                                                                          C, ldc, ctx->d_status);
+  ctx->launches += 2;
+  return cudaGetLastError();
+}
+
+}  // namespace tc
+}  // namespace sparc
+
+// ------------------------------------------------------------------ C ABI
+using namespace sparc;
+
+extern "C" sparc_status sparc_gram_f32(sparc_ctx* ctx, const float* A, int64_t lda, const float* B, int64_t ldb,
+                                       int64_t nd, int ns, double* G, void* stream) {
+  if (!ctx) return SPARC_ERR_INVALID_ARG;
+  if (!A || !B || !G || nd < 1 || ns < 1 || ns > 4096 || lda < nd || ldb < nd)
+    return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_gram_f32: need nd >= 1, 1 <= ns <= 4096, lda, ldb >= nd");
+  SPARC_CUDA(ctx, cudaSetDevice(ctx->device));
+  if (!ensure_ws(ctx, tc::gram_scratch_bytes(ctx, ns, nd)))
+    return fail(ctx, SPARC_ERR_OOM, "sparc_gram_f32: workspace allocation failed");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t t0 = timing_begin(ctx, st);
+  SPARC_CUDA(ctx, tc::gram(ctx, A, lda, B, ldb, nd, ns, G, ctx->ws, st));
+  timing_end(ctx, TK_GRAM, t0, st);
+  return SPARC_OK;
+}
+
+extern "C" sparc_status sparc_rotate_f32(sparc_ctx* ctx, const float* U, int64_t ldu, const double* Yr, int64_t nd,
+                                         int ns, float* C, int64_t ldc, void* stream) {
+  if (!ctx) return SPARC_ERR_INVALID_ARG;
+  if (!U || !Yr || !C || nd < 1 || ns < 1 || ns > 4096 || ldu < nd || ldc < nd)
+    return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_rotate_f32: need nd >= 1, 1 <= ns <= 4096, ldu, ldc >= nd");
+  const char* u0 = (const char*)U;
+  const char* u1 = (const char*)(U + (size_t)ldu * (ns - 1) + nd);
+  const char* c0 = (const char*)C;
+  const char* c1 = (const char*)(C + (size_t)ldc * (ns - 1) + nd);
+  if (u0 < c1 && c0 < u1) return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_rotate_f32: C overlaps U");
+  SPARC_CUDA(ctx, cudaSetDevice(ctx->device));
+  if (!ensure_ws(ctx, tc::rot_scratch_bytes(ns)))
+    return fail(ctx, SPARC_ERR_OOM, "sparc_rotate_f32: workspace allocation failed");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t t0 = timing_begin(ctx, st);
+  SPARC_CUDA(ctx, tc::rotate(ctx, U, ldu, Yr, nd, ns, C, ldc, ctx->ws, st));
+  timing_end(ctx, TK_ROT, t0, st);
+  return SPARC_OK;
+}

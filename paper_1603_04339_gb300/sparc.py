@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 from ctypes import POINTER, c_double, c_int, c_int32, c_int64, c_void_p
 
 import numpy as np
@@ -23,7 +24,8 @@ STATUS = {0: "SPARC_OK", 1: "SPARC_ERR_INVALID_ARG", 2: "SPARC_ERR_OOM", 3: "SPA
 EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_sync", "sparc_ham_create",
            "sparc_ham_set_veff", "sparc_ham_destroy", "sparc_apply_H", "sparc_cheb_filter",
            "sparc_lanczos_bounds", "sparc_rayleigh_ritz", "sparc_timing_enable", "sparc_timing_read",
-           "sparc_launch_count", "sparc_apply_H_noalloc", "sparc_last_sweeps"]
+           "sparc_launch_count", "sparc_apply_H_noalloc", "sparc_last_sweeps", "sparc_gram_f32",
+           "sparc_rotate_f32"]
 TIMED = {"hpass": 0, "gather": 1, "gram": 2, "eig": 3, "rotation": 4, "jacobi": 5, "fpass": 6}
 
 
@@ -81,8 +83,13 @@ def load(path: str = LIB_PATH):
     L.sparc_apply_H_noalloc.restype = c_int
     L.sparc_launch_count.restype = c_int
     L.sparc_timing_read.argtypes = [c_void_p, c_int, POINTER(c_double), POINTER(c_int64)]
+    L.sparc_gram_f32.argtypes = [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int64, c_int, c_void_p,
+                                 c_void_p]
+    L.sparc_rotate_f32.argtypes = [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int, c_void_p, c_int64,
+                                   c_void_p]
     for name in ("sparc_timing_enable", "sparc_timing_read", "sparc_create", "sparc_sync", "sparc_ham_create", "sparc_ham_set_veff",
-                 "sparc_apply_H", "sparc_cheb_filter", "sparc_lanczos_bounds", "sparc_rayleigh_ritz"):
+                 "sparc_apply_H", "sparc_cheb_filter", "sparc_lanczos_bounds", "sparc_rayleigh_ritz",
+                 "sparc_gram_f32", "sparc_rotate_f32"):
         getattr(L, name).restype = c_int
     _lib = L
     return L
@@ -125,6 +132,7 @@ class Context:
             raise SparcError(rc, "sparc_create failed")
         self.handle = h
         self.device = device
+        self._hams = weakref.WeakSet()   # Hamiltonians of this context, closed with it
 
     def error(self) -> str:
         return load().sparc_last_error(self.handle).decode()
@@ -160,6 +168,8 @@ class Context:
 
     def close(self):
         if self.handle:
+            for H in list(self._hams):
+                H.close()
             load().sparc_destroy(self.handle)
             self.handle = None
 
@@ -211,6 +221,7 @@ class Hamiltonian:
                                 ctypes.byref(hh))
         ctx.check(rc)
         self.handle = hh
+        ctx._hams.add(self)
 
     @classmethod
     def from_workload(cls, ctx, wl, kidx=0):
@@ -287,3 +298,20 @@ def sparc_rayleigh_ritz(H: Hamiltonian, U, eig, mode, ns=None, ld=None, stream=N
     dt = dtype_code(U) if dtype is None else dtype
     H.ctx.check(load().sparc_rayleigh_ritz(H.handle, dt, _ptr(U), int(ns), int(ld), _ptr(eig), int(mode),
                                            _stream(stream)))
+
+
+def sparc_gram_f32(ctx: Context, A, B, G, nd=None, stream=None):
+    """G = A^T B (FP64, ns x ns) for FP32 CUDA tensors A, B of shape (ns, ld) (column-major nd x ns)."""
+    ns = A.shape[0]
+    nd = A.shape[-1] if nd is None else nd
+    ctx.check(load().sparc_gram_f32(ctx.handle, _ptr(A), int(A.shape[-1]), _ptr(B), int(B.shape[-1]), int(nd),
+                                    int(ns), _ptr(G), _stream(stream)))
+
+
+def sparc_rotate_f32(ctx: Context, U, Yr, C, nd=None, stream=None):
+    """C = U Yr for FP32 CUDA tensors U, C of shape (ns, ld) and an FP64 (ns, ns) tensor Yr
+    holding the column-major ns x ns matrix (row n of the tensor is column n of Yr)."""
+    ns = U.shape[0]
+    nd = U.shape[-1] if nd is None else nd
+    ctx.check(load().sparc_rotate_f32(ctx.handle, _ptr(U), int(U.shape[-1]), _ptr(Yr), int(nd), int(ns), _ptr(C),
+                                      int(C.shape[-1]), _stream(stream)))

@@ -121,11 +121,15 @@ def test_benchmark_cell_mixed_rayleigh_ritz_properties(ctx, cell64):
     assert lam[-1] <= b, (lam[-1], b)
     U64 = Yd.to(torch.float64)
     G = (U64 @ U64.T).cpu().numpy()
-    # one Cholesky orthonormalisation of FP32 data: |U^T U - I| ~ kappa(M~) * u_32
-    assert np.max(np.abs(G - np.eye(wl.ns))) < 5e-4, np.max(np.abs(G - np.eye(wl.ns)))
+    # Cholesky-QR pass, Rayleigh-Ritz in the orthonormal basis and an FP64 Newton-Schulz
+    # step on the eigenvectors: |U^T U - I| is set by the FP32 rounding of U and the
+    # 3xTF32 rotation (measured 6e-6 on this cell)
+    print(f"mixed orthonormality {np.max(np.abs(G - np.eye(wl.ns))):.3e}")
+    assert np.max(np.abs(G - np.eye(wl.ns))) < 5e-5, np.max(np.abs(G - np.eye(wl.ns)))
     HU = torch.empty_like(U64)
     sparc.sparc_apply_H(H, U64, HU)
     rq = (U64 * HU).sum(dim=1).cpu().numpy() / np.diag(G)
+    print(f"mixed RQ consistency {np.max(np.abs(rq - lam)):.3e}")
     assert np.max(np.abs(rq - lam)) < 1e-5 * max(1.0, np.max(np.abs(lam))), np.max(np.abs(rq - lam))
 
 
@@ -145,3 +149,36 @@ def test_si_cell_one_kpoint_complex64_filter_sampled_columns(ctx):
     cols = [3, 191]
     Yref = O.cheb_filter(Hor, X[cols].astype(np.complex128), wl.m, a, b, a0)
     assert _colerr(Yd[cols].cpu().numpy().astype(np.complex128), Yref) < 2e-4
+
+
+def test_benchmark_cell_mixed_vs_fp64_rayleigh_ritz(ctx, cell64):
+    """The mixed Rayleigh-Ritz (FP32 data, tensor-core Grams and rotation, FP64
+    Cholesky and eigensolve) against the FP64 Rayleigh-Ritz of the same filtered
+    block (the FP32 values widened exactly): both compute the Ritz values of one
+    subspace, so they differ only by the mixed path's own rounding."""
+    from paper_1603_04339_gb300 import sparc
+    wl, _ = cell64
+    H = sparc.Hamiltonian.from_workload(ctx, wl)
+    X32 = synth.random_orbitals(wl.nd, wl.ns, 2004).astype(np.float32)
+    Xd = torch.from_numpy(X32).cuda()
+    Yd = torch.empty_like(Xd)
+    a0, b = sparc.sparc_lanczos_bounds(H, 10, torch.from_numpy(synth.lanczos_start(wl.nd, 2005)).cuda())
+    a = a0 + (b - a0) * (wl.ns / wl.nd) ** (2.0 / 3.0)
+    sparc.sparc_cheb_filter(H, wl.m, a, b, a0, Xd, Yd)
+    Y64 = Yd.to(torch.float64)
+    e32 = torch.zeros(wl.ns, dtype=torch.float64, device="cuda")
+    e64 = torch.zeros_like(e32)
+    sparc.sparc_rayleigh_ritz(H, Yd, e32, sparc.RR_MIXED)
+    sparc.sparc_rayleigh_ritz(H, Y64, e64, sparc.RR_FP64)
+    torch.cuda.synchronize()
+    d = np.abs(e32.cpu().numpy() - e64.cpu().numpy())
+    lam = e64.cpu().numpy()
+    print(f"mixed vs FP64 Ritz values: max {d.max():.3e} Ha, lowest 256: {d[:256].max():.3e} Ha, "
+          f"range [{lam[0]:.4f}, {lam[-1]:.4f}]")
+    U64 = Yd.to(torch.float64)
+    G = (U64 @ U64.T).cpu().numpy()
+    print(f"mixed orthonormality: {np.max(np.abs(G - np.eye(wl.ns))):.3e}")
+    # the mixed path's eigenvalue target is 1e-6 Ha (measured 7.6e-7 Ha on this cell);
+    # 2e-6 leaves room for other seeds, and a single-TF32 product path misses it by 100x
+    assert d.max() < 2e-6, d.max()
+    assert np.max(np.abs(G - np.eye(wl.ns))) < 5e-5
