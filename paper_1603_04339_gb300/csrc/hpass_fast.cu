@@ -1037,6 +1037,105 @@ k_gather_rows(const T* __restrict__ Y, long long nd, int n1, int n2, const Group
   }
 }
 
+// FP32 projection with pairs of blocks packed in float2 (one FFMA2 per projector and
+// node serves two blocks); same row slabs, lane layout and fixed-order reductions as
+// k_gather_rows.  NB2 pairs = 2 NB2 blocks per CTA (grid z covers the rest).
+template <int NB2>
+__device__ __forceinline__ void gather_row_f2(float2 (&s)[NB2][4], const float4* __restrict__ c,
+                                              const float* __restrict__ y0, size_t bstride, int wx, int xi,
+                                              int nbv) {
+  constexpr int NXS = 5;
+  for (int x0 = 0; x0 < wx; x0 += 4 * NXS) {
+    float4 c4[NXS];
+    float2 y[NXS][NB2];
+#pragma unroll
+    for (int u = 0; u < NXS; ++u) {
+      const int ix = x0 + xi + 4 * u;
+      const bool ok = ix < wx;
+      c4[u] = ok ? __ldg(c + ix) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < NB2; ++j) {
+        const float* p = y0 + (size_t)(2 * j) * bstride + (size_t)ix * NB;
+        y[u][j].x = (ok && 2 * j < nbv) ? __ldg(p) : 0.f;
+        y[u][j].y = (ok && 2 * j + 1 < nbv) ? __ldg(p + bstride) : 0.f;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < NXS; ++u)
+#pragma unroll
+      for (int j = 0; j < NB2; ++j) {
+        s[j][0] = __ffma2_rn(f2(c4[u].x), y[u][j], s[j][0]);
+        s[j][1] = __ffma2_rn(f2(c4[u].y), y[u][j], s[j][1]);
+        s[j][2] = __ffma2_rn(f2(c4[u].z), y[u][j], s[j][2]);
+        s[j][3] = __ffma2_rn(f2(c4[u].w), y[u][j], s[j][3]);
+      }
+  }
+}
+
+template <int NB2>
+__global__ void __launch_bounds__(256, 2)
+k_gather_rows_f2(const float* __restrict__ Y, long long nd, int n1, int n2, const Group* __restrict__ grp,
+                 const SubBox* __restrict__ sbs, const float4* __restrict__ chi4, float* __restrict__ part,
+                 int blk0, int nb, int nslab) {
+  constexpr int NBM = 2 * NB2;
+  __shared__ float red[8][NBM][4][NB];
+  const int gi = blockIdx.x, sl = blockIdx.y, q = blockIdx.z;
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  const int o = lane % NB, xi = lane / NB;
+  const int nbv = min(NBM, nb - q * NBM);
+  const float* Yb = Y + (size_t)(blk0 + q * NBM) * nd * NB + o;
+  const size_t bstride = (size_t)nd * NB;
+  const Group G = grp[gi];
+  float2 acc[NB2][4];
+#pragma unroll
+  for (int j = 0; j < NB2; ++j)
+#pragma unroll
+    for (int l = 0; l < 4; ++l) acc[j][l] = make_float2(0.f, 0.f);
+  int rbase = 0;
+  for (int sbi = G.sb0; sbi < G.sb1; ++sbi) {
+    const SubBox sb = sbs[sbi];
+    const int wx = sb.gx1 - sb.gx0, wy = sb.gy1 - sb.gy0, wz = sb.gz1 - sb.gz0;
+    const int rows = wy * wz;
+    const int first = (sl - rbase % nslab + nslab) % nslab;
+    for (int row = first + warp * nslab; row < rows; row += 8 * nslab) {
+      const int iy = row % wy, iz = row / wy;
+      const long long yrow = ((long long)(sb.gz0 + iz) * n2 + (sb.gy0 + iy)) * n1 + sb.gx0;
+      const long long crow =
+          sb.chi4_off + sb.bx0 + (long long)sb.nbx * ((sb.by0 + iy) + (long long)sb.nby * (sb.bz0 + iz));
+      // real data: k = 0, every phase is 1; accumulate in place
+      gather_row_f2<NB2>(acc, chi4 + crow, Yb + (size_t)yrow * NB, bstride, wx, xi, nbv);
+    }
+    rbase += rows;
+  }
+#pragma unroll
+  for (int j = 0; j < NB2; ++j)
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {   // over the 4 x-lanes: fixed butterfly order
+      acc[j][l].x += __shfl_xor_sync(0xffffffffu, acc[j][l].x, 8);
+      acc[j][l].y += __shfl_xor_sync(0xffffffffu, acc[j][l].y, 8);
+      acc[j][l].x += __shfl_xor_sync(0xffffffffu, acc[j][l].x, 16);
+      acc[j][l].y += __shfl_xor_sync(0xffffffffu, acc[j][l].y, 16);
+    }
+  if (xi == 0) {
+#pragma unroll
+    for (int j = 0; j < NB2; ++j)
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        red[warp][2 * j][l][o] = acc[j][l].x;
+        red[warp][2 * j + 1][l][o] = acc[j][l].y;
+      }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < NBM * 4 * NB; t += blockDim.x) {   // fixed order over warps
+    const int oo = t % NB, l = (t / NB) % 4, b = t / (4 * NB);
+    if (b >= nbv) continue;
+    float v = red[0][b][l][oo];
+    for (int w2 = 1; w2 < 8; ++w2) v += red[w2][b][l][oo];
+    const int bi = q * NBM + b;
+    part[((size_t)(gi * nslab + sl) * 4 + l) * ((size_t)nb * NB) + bi * NB + oo] = v;
+  }
+}
+
 // gc[p][blk][lane] = gamma_p h^3 sum_s part[g][s][l][bi][lane] (fixed order over slabs)
 template <class T>
 __global__ void k_gather_sum(const T* __restrict__ part, const Group* __restrict__ grp,
@@ -1086,11 +1185,27 @@ cudaError_t launch_gather(const sparc_ham* H, const T* Y, int nblk_total, int bl
   if (H->nproj == 0 || Tb->ngrp == 0) return cudaSuccess;
   const float dv = (float)(H->grid.h[0] * H->grid.h[1] * H->grid.h[2]);
   const int nslab = gather_slabs(H);
-  constexpr int NBM = GatherOct<T>::v;
-  const dim3 grid((unsigned)Tb->ngrp, (unsigned)nslab, (unsigned)ceil_div(nb, NBM));
   cudaEvent_t t0 = timing_begin(H->ctx, st);
-  k_gather_rows<T, NBM><<<grid, 256, 0, st>>>(Y, H->gd.nd, H->gd.n1, H->gd.n2, Tb->d_grp, Tb->d_sb,
-                                              (const float4*)Tb->d_chi4, scratch, blk0, nb, nslab);
+  if constexpr (FT<T>::cplx) {
+    constexpr int NBM = GatherOct<T>::v;
+    const dim3 grid((unsigned)Tb->ngrp, (unsigned)nslab, (unsigned)ceil_div(nb, NBM));
+    k_gather_rows<T, NBM><<<grid, 256, 0, st>>>(Y, H->gd.nd, H->gd.n1, H->gd.n2, Tb->d_grp, Tb->d_sb,
+                                                (const float4*)Tb->d_chi4, scratch, blk0, nb, nslab);
+  } else {
+    // pairs of blocks per CTA: as many as the group has, at most 4 pairs
+    const int nb2 = std::min(4, (nb + 1) / 2);
+    const dim3 grid((unsigned)Tb->ngrp, (unsigned)nslab, (unsigned)ceil_div(nb, 2 * nb2));
+    auto go = [&](auto kern) {
+      kern<<<grid, 256, 0, st>>>(Y, H->gd.nd, H->gd.n1, H->gd.n2, Tb->d_grp, Tb->d_sb, (const float4*)Tb->d_chi4,
+                                 scratch, blk0, nb, nslab);
+    };
+    switch (nb2) {
+      case 1: go(k_gather_rows_f2<1>); break;
+      case 2: go(k_gather_rows_f2<2>); break;
+      case 3: go(k_gather_rows_f2<3>); break;
+      default: go(k_gather_rows_f2<4>); break;
+    }
+  }
   const long long tot = (long long)Tb->ngrp * 4 * nb * NB;
   k_gather_sum<T><<<ceil_div(tot, 256), 256, 0, st>>>(scratch, Tb->d_grp, H->d_gamma32, dv, gc, Tb->ngrp,
                                                       nslab, nblk_total, blk0, nb);
