@@ -187,6 +187,60 @@ sparc_status sparc_gram_f32(sparc_ctx* ctx, const float* A, int64_t lda, const f
 sparc_status sparc_rotate_f32(sparc_ctx* ctx, const float* U, int64_t ldu, const double* Yr, int64_t nd,
                               int ns, float* C, int64_t ldc, void* stream);
 
+/* ---------------------------------------------------------------- SCF iteration
+ * One self-consistent-field iteration around the CheFSI step (Section 3.4, Eq. EL;
+ * Section 5 names the solvers), for one Bloch wavevector of weight 1:
+ *   filter bounds (Lanczos, 10 steps from the start vector v0; the cutoff and lower end
+ *   are the largest and smallest Ritz values of the previous iteration, or a Weyl
+ *   estimate at the first), scaled Chebyshev filter of degree m, Rayleigh-Ritz (mixed
+ *   for FP32 data), Fermi level by Brent's method, density
+ *   rho = 2 sum g_n |u_n|^2 / (h1h2h3), Poisson -(1/4pi) lap_h phi = rho + b by
+ *   conjugate gradients (periodic, zero-mean phi, warm start), LDA (Slater exchange,
+ *   Perdew-Wang 1992 correlation), V_out = phi + V_xc, Anderson extrapolation of V_eff
+ *   (relaxation mix_beta, history mix_history), and the free energy of
+ *   Eq. FreeEnergy:GroundState:DFT:discrete (E_c = 0).  The next V_eff is written into
+ *   H.  All grid arithmetic is FP64 and deterministic.
+ * Local pseudopotential of atom I: V_I(r) = -Z_I erf(r/rc_I)/r; its pseudocharge
+ * b_I = -(1/4pi) lap_h V_I (Eq. PseudochargeDiscrete) on a cube of half-width
+ * ceil(6 rc_I / h_s) nodes (charge error below 1e-8), self energy by Eq. DiscreteEself.  sparc_scf_create sets
+ * H's V_eff to V_xc of the starting density rho0 = -b (a superposition of Gaussian
+ * atomic densities, neutral with the pseudocharges). */
+typedef struct {
+  int natom;
+  const double* R;       /* [3*natom] positions (bohr), frame of the grid (origin at the centre) */
+  const double* Z;       /* [natom] valence charges, > 0; N_e = sum Z */
+  const double* rc;      /* [natom] widths of the local pseudopotentials (bohr), > 0 */
+  double kT;             /* smearing k_B T (Ha), > 0 (the paper: 0.01) */
+  double mix_beta;       /* Anderson relaxation, > 0 (the paper: 0.3) */
+  int mix_history;       /* Anderson history, 0..8 (the paper: 7) */
+  double poisson_tol;    /* relative residual of the Poisson solve, > 0 */
+  const double* v0;      /* Lanczos start vector, host: Nd doubles (k = 0) or Nd (re, im) pairs */
+} sparc_scf_desc;
+
+typedef struct {
+  double free_energy;    /* Ha */
+  double fermi;          /* lambda_f (Ha) */
+  double vresid;         /* |V_out - V_in| / |V_out| of this iteration */
+  double nelec;          /* 2 sum g_n (= N_e) */
+  double e_band, e_xc, e_el, e_self, e_entropy;   /* the terms of the free energy */
+  int poisson_iters;
+  double a0, a, b;       /* filter bounds used */
+} sparc_scf_info;
+
+typedef struct sparc_scf sparc_scf;
+/* Pseudocharges, self energy and the starting V_eff of H.  S uses H in every call but
+ * sparc_scf_destroy, so H must outlive the calls on S. */
+sparc_status sparc_scf_create(sparc_ham* H, const sparc_scf_desc* d, sparc_scf** S);
+/* One iteration on the orbitals U (device, column-major Nd x ns, ld >= Nd, dtype F64, F32,
+ * C128 or C64; updated in place to the rotated orbitals); eig: device, ns Ritz values.
+ * 2 ns must exceed N_e.  Synchronises `stream`. */
+sparc_status sparc_scf_step(sparc_scf* S, sparc_dtype dtype, int m, void* U, int ns, int64_t ld, double* eig,
+                            sparc_scf_info* info, void* stream);
+/* Copy one grid field (Nd doubles) to the device buffer dst: which = 0 b, 1 rho (last
+ * iteration), 2 phi, 3 V_xc, 4 V_out, 5 the current V_eff of H (the next V_in). */
+sparc_status sparc_scf_read(const sparc_scf* S, int which, double* dst, void* stream);
+void sparc_scf_destroy(sparc_scf* S);
+
 /* Kernel timing (instrumentation, not part of the method).  While enabled, every
  * launch of the kernels below is bracketed by CUDA events recorded on the
  * stream it is launched on.  sparc_timing_read() synchronises those events and

@@ -1,0 +1,245 @@
+"""FP64 CPU oracle for one SCF iteration around the CheFSI step (SPARC, arXiv:1603.04339).
+
+TEST INFRASTRUCTURE ONLY, like sparc_oracle.py: only the tests, the smoke check and
+the benchmark's CPU baseline may import it, and it shares no code with the CUDA
+library.  Each function restates one passage of the paper (cited in its docstring),
+in the paper's order, with numpy (and scipy's Brent root finder as the library step
+the paper names).
+
+Readings where the paper is silent or leaves a choice (also in the design notes):
+  * the local pseudopotential of atom I is V_I(r) = -Z_I erf(r/rc_I)/r (a stand-in
+    for the Troullier-Martins tables); its discrete pseudocharge
+    b_I = -(1/4pi) lap_h V_I (Eq. PseudochargeDiscrete) is kept on a cube of
+    half-width ceil(6 rc_I / h) nodes around the atom's nearest node, which meets the
+    paper's charge tolerance eps_b = 1e-8 (Eq. PseudochargeRadiusChoice), and it
+    integrates to -Z_I (the sign that makes the cell neutral, int b = -N_e,
+    Eq. IntegralPseudocharges);
+  * E_c (overlapping pseudocharges) is zero: the Gaussian pseudocharges of the
+    synthetic atoms do not overlap to 1e-12;
+  * the Poisson problem -lap_h phi = 4 pi (rho + b) is periodic; phi has zero mean
+    and the mean of the right-hand side (the truncation error of b) is removed;
+  * LDA: Slater exchange and the Perdew-Wang 1992 parametrisation of the
+    correlation energy of the unpolarised electron gas (Section 5);
+  * Anderson extrapolation on V_eff with relaxation beta and history m (Section 5):
+    with f = V_out - V_in, gamma solves the normal equations of min |f_k - dF gamma|
+    over the last m differences (dF^T dF regularised by 1e-12 of its trace, so that a
+    converged history stays solvable), V_next = (V_k - dX gamma) + beta (f_k - dF gamma);
+  * the free energy (Eq. FreeEnergy:GroundState:DFT:discrete) is evaluated with the
+    band energy of H[V_in] and the grid terms of the output density rho_out (its own
+    phi and V_xc), which is the paper's expression at self-consistency;
+  * the Fermi level is bracketed by [lambda_min - 1, lambda_max + 1] Ha and found to
+    1e-12 Ha.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.optimize
+from scipy.special import erf
+
+from . import sparc_oracle as O
+
+__all__ = ["local_potential", "pseudocharge", "occupations", "fermi_level", "density",
+           "poisson", "lda", "anderson", "free_energy", "entropy_term", "PW92"]
+
+# Perdew-Wang 1992 parameters of the correlation energy of the unpolarised gas
+# (A, alpha1, beta1..beta4; p = 1).  A equals (1 - ln 2)/pi^2, the exact high-density
+# coefficient of ln(rs), which the pins check.
+PW92 = (0.031091, 0.21370, 7.5957, 3.5876, 1.6382, 0.49294)
+
+
+def _coords(n, h):
+    """Node coordinates x_i = -L/2 + i h per axis (Section 3.1)."""
+    return [(-0.5 * n[s] * h[s] + h[s] * np.arange(n[s])) for s in range(3)]
+
+
+def local_potential(r: np.ndarray, Z: float, rc: float) -> np.ndarray:
+    """V_I(r) = -Z erf(r/rc)/r, with its limit -2Z/(sqrt(pi) rc) at r = 0."""
+    r = np.asarray(r, dtype=np.float64)
+    out = np.empty_like(r)
+    small = r < 1e-12
+    out[~small] = -Z * erf(r[~small] / rc) / r[~small]
+    out[small] = -2.0 * Z / (math.sqrt(math.pi) * rc)
+    return out
+
+
+def pseudocharge(n, h, n_o, R, Z, rc):
+    """Discrete pseudocharge b and self energy E_self^h (Eqs. PseudochargeDiscrete and
+    DiscreteEself; the loop over atoms of Algorithm "Pseudocharge density generation").
+
+    For each atom: V_I on its cube plus an n_o halo (unwrapped node coordinates),
+    b_I = -(1/4pi) lap_h V_I on the cube, added into b with periodic wrap, and
+    E_self += 1/2 h1h2h3 sum_cube b_I V_I.  Returns (b[Nd], E_self, per-atom charges)."""
+    n = tuple(int(v) for v in n)
+    h = tuple(float(v) for v in h)
+    L = [n[s] * h[s] for s in range(3)]
+    w = [O.fd_weights(n_o, h[s]) for s in range(3)]
+    dv = h[0] * h[1] * h[2]
+    b = np.zeros(n[::-1], dtype=np.float64)          # [k][j][i]
+    e_self = 0.0
+    charges = []
+    for I in range(len(Z)):
+        nb = [int(math.ceil(6.0 * rc[I] / h[s])) for s in range(3)]
+        c = [int(round((R[I][s] + 0.5 * L[s]) / h[s])) for s in range(3)]   # nearest node
+        lo = [c[s] - nb[s] - n_o for s in range(3)]
+        m = [2 * nb[s] + 1 + 2 * n_o for s in range(3)]
+        xs = [(-0.5 * L[s] + h[s] * (lo[s] + np.arange(m[s]))) - R[I][s] for s in range(3)]
+        X, Y, Zc = np.meshgrid(xs[0], xs[1], xs[2], indexing="ij")
+        V = local_potential(np.sqrt(X * X + Y * Y + Zc * Zc), Z[I], rc[I])   # [i][j][k]
+        inner = tuple(slice(n_o, n_o + 2 * nb[s] + 1) for s in range(3))
+        lap = np.zeros([2 * nb[s] + 1 for s in range(3)])
+        for s in range(3):
+            acc = 2.0 * w[s][0] * V[inner]
+            for p in range(1, n_o + 1):
+                sl_p = list(inner)
+                sl_m = list(inner)
+                sl_p[s] = slice(n_o + p, n_o + p + 2 * nb[s] + 1)
+                sl_m[s] = slice(n_o - p, n_o - p + 2 * nb[s] + 1)
+                acc = acc + w[s][p] * (V[tuple(sl_p)] + V[tuple(sl_m)])
+            lap = lap + acc
+        bI = -lap / (4.0 * math.pi)
+        e_self += 0.5 * dv * float(np.sum(bI * V[inner]))
+        charges.append(dv * float(np.sum(bI)))
+        ii = [np.mod(lo[s] + n_o + np.arange(2 * nb[s] + 1), n[s]) for s in range(3)]
+        np.add.at(b, np.ix_(ii[2], ii[1], ii[0]), np.transpose(bI, (2, 1, 0)))
+    return b.reshape(-1), e_self, np.array(charges)
+
+
+def occupations(lam: np.ndarray, mu: float, kT: float) -> np.ndarray:
+    """g_n = (1 + exp((lambda_n - lambda_f)/kT))^-1 (Eq. EL), written without overflow."""
+    x = (np.asarray(lam, dtype=np.float64) - mu) / kT
+    out = np.empty_like(x)
+    pos = x > 0
+    e = np.exp(-x[pos])
+    out[pos] = e / (1.0 + e)
+    out[~pos] = 1.0 / (1.0 + np.exp(x[~pos]))
+    return out
+
+
+def fermi_level(lam: np.ndarray, Ne: float, kT: float, wk: float = 1.0) -> float:
+    """lambda_f such that 2 sum_n w g_n = N_e, by Brent's method (Section 5)."""
+    lam = np.asarray(lam, dtype=np.float64)
+    f = lambda mu: 2.0 * wk * float(np.sum(occupations(lam, mu, kT))) - Ne
+    return scipy.optimize.brentq(f, lam.min() - 1.0, lam.max() + 1.0, xtol=1e-14, maxiter=500)
+
+
+def density(U: np.ndarray, g: np.ndarray, h, wk: float = 1.0) -> np.ndarray:
+    """rho = 2 sum_n w g_n |u_n|^2 (Section 3.4, "Electron density calculation"), with the
+    orbitals U (rows) orthonormal in the Euclidean sense, so u_n = U_n / sqrt(h1h2h3)."""
+    dv = h[0] * h[1] * h[2]
+    return 2.0 * wk * np.einsum("n,ng->g", np.asarray(g, dtype=np.float64), np.abs(U) ** 2) / dv
+
+
+def poisson(rhs_density: np.ndarray, n, h, n_o: int) -> np.ndarray:
+    """phi with -(1/4pi) lap_h phi = rhs_density (Eq. EL's Poisson equation, FD Laplacian
+    of Eq. FD:Laplacian), periodic, zero mean.  The FD Laplacian is circulant on the
+    periodic grid, so it is diagonal in the discrete Fourier basis with eigenvalues
+    -2 fd_symbol (the oracle's own closed form), and the solve is exact up to rounding."""
+    n = tuple(int(v) for v in n)
+    f = np.asarray(rhs_density, dtype=np.float64).reshape(n[::-1])
+    f = f - f.mean()
+    F = np.fft.fftn(f)
+    lam = np.zeros(n[::-1])
+    for s, ax in ((0, 2), (1, 1), (2, 0)):
+        theta_h = 2.0 * math.pi * np.fft.fftfreq(n[s])          # theta * h
+        sym = 2.0 * O.fd_symbol(theta_h, n_o, h[s])              # -lap symbol along axis s
+        shape = [1, 1, 1]
+        shape[ax] = n[s]
+        lam = lam + sym.reshape(shape)
+    lam.flat[0] = 1.0
+    P = 4.0 * math.pi * F / lam
+    P.flat[0] = 0.0
+    return np.real(np.fft.ifftn(P)).reshape(-1)
+
+
+def lda(rho: np.ndarray):
+    """(eps_xc, V_xc) of the LDA (Section 2, Exchange-correlation energy; Section 5: Slater
+    exchange, Perdew-Wang 1992 correlation), for the unpolarised density rho."""
+    rho = np.asarray(rho, dtype=np.float64)
+    eps = np.zeros_like(rho)
+    v = np.zeros_like(rho)
+    ok = rho > 1e-30
+    r = rho[ok]
+    ex = -0.75 * (3.0 / math.pi) ** (1.0 / 3.0) * r ** (1.0 / 3.0)
+    vx = (4.0 / 3.0) * ex
+    A, a1, b1, b2, b3, b4 = PW92
+    rs = (3.0 / (4.0 * math.pi * r)) ** (1.0 / 3.0)
+    srs = np.sqrt(rs)
+    Q0 = -2.0 * A * (1.0 + a1 * rs)
+    Q1 = 2.0 * A * (b1 * srs + b2 * rs + b3 * rs * srs + b4 * rs * rs)
+    Q1p = A * (b1 / srs + 2.0 * b2 + 3.0 * b3 * srs + 4.0 * b4 * rs)
+    L = np.log1p(1.0 / Q1)
+    ec = Q0 * L
+    dec = -2.0 * A * a1 * L - Q0 * Q1p / (Q1 * Q1 + Q1)
+    vc = ec - rs / 3.0 * dec
+    eps[ok] = ex + ec
+    v[ok] = vx + vc
+    return eps, v
+
+
+def entropy_term(g: np.ndarray, kT: float, wk: float = 1.0) -> float:
+    """2 kT sum_n w (g ln g + (1-g) ln(1-g)), with 0 ln 0 = 0."""
+    g = np.asarray(g, dtype=np.float64)
+    t = np.zeros_like(g)
+    m = (g > 0) & (g < 1)
+    t[m] = g[m] * np.log(g[m]) + (1.0 - g[m]) * np.log(1.0 - g[m])
+    return 2.0 * kT * wk * float(np.sum(t))
+
+
+def free_energy(lam, g, rho, b, phi, eps_xc, v_xc, h, e_self, kT, e_c=0.0, wk=1.0):
+    """Eq. FreeEnergy:GroundState:DFT:discrete.  Returns (F, parts)."""
+    dv = h[0] * h[1] * h[2]
+    e_band = 2.0 * wk * float(np.sum(np.asarray(g) * np.asarray(lam)))
+    e_xc = dv * float(np.sum(eps_xc * rho - v_xc * rho))
+    e_el = dv * float(np.sum(0.5 * (b - rho) * phi))
+    e_ent = entropy_term(g, kT, wk)
+    F = e_band + e_xc + e_el - e_self + e_c + e_ent
+    return F, {"band": e_band, "xc": e_xc, "el": e_el, "self": e_self, "entropy": e_ent}
+
+
+def anderson(x_hist, f_hist, beta: float, m: int) -> np.ndarray:
+    """Anderson extrapolation (Section 5): x_hist, f_hist are the lists of the inputs
+    x_j = V_in and residuals f_j = V_out - V_in so far (last entry = current).  With
+    dX, dF the differences of the last min(k, m) pairs, gamma minimises |f_k - dF gamma|
+    (normal equations, regularised by 1e-12 of the trace of dF^T dF), and the next
+    input is (x_k - dX gamma) + beta (f_k - dF gamma)."""
+    xk, fk = x_hist[-1], f_hist[-1]
+    k = len(x_hist) - 1
+    mm = min(k, m)
+    if mm == 0:
+        return xk + beta * fk
+    dX = np.stack([x_hist[-1 - j] - x_hist[-2 - j] for j in range(mm)], axis=1)
+    dF = np.stack([f_hist[-1 - j] - f_hist[-2 - j] for j in range(mm)], axis=1)
+    Gm = dF.T @ dF
+    Gm = Gm + 1e-12 * np.trace(Gm) * np.eye(mm)   # keeps the normal equations solvable at convergence
+    gamma = np.linalg.solve(Gm, dF.T @ fk)
+    return (xk - dX @ gamma) + beta * (fk - dF @ gamma)
+
+
+def scf_iteration(H: "O.OracleH", U, lam_prev, v0, b, e_self, Ne, kT, m, lanczos_k=10):
+    """One SCF iteration at fixed V_in = H.veff (Section 3.4 and Eq. EL), in the order
+    the CUDA path takes it: filter bounds by Lanczos (Section 5; the cutoff is the
+    largest previous Ritz value, or the Weyl estimate a0 + (b - a0)(Ns/Nd)^(2/3) at
+    the first iteration, and a0 the smallest), scaled Chebyshev filter, Rayleigh-Ritz,
+    Fermi level, density, Poisson, LDA, V_out = phi + V_xc and the free energy.
+    Returns a dict of every intermediate."""
+    U = np.atleast_2d(U)
+    ns = U.shape[0]
+    a0, bb, _ = O.lanczos_bounds(H, v0, lanczos_k)
+    if lam_prev is None:
+        a = a0 + (bb - a0) * (ns / H.nd) ** (2.0 / 3.0)
+    else:
+        a0 = float(lam_prev[0])
+        a = float(lam_prev[-1])
+    Yf = O.cheb_filter(H, U, m, a, bb, a0)
+    lam, Uo, _, _ = O.rayleigh_ritz(H, Yf)
+    mu = fermi_level(lam, Ne, kT)
+    g = occupations(lam, mu, kT)
+    rho = density(Uo, g, H.h)
+    phi = poisson(rho + b, H.n, H.h, H.n_o)
+    eps, vxc = lda(rho)
+    v_out = phi + vxc
+    F, parts = free_energy(lam, g, rho, b, phi, eps, vxc, H.h, e_self, kT)
+    return {"a0": a0, "a": a, "b": bb, "lam": lam, "U": Uo, "mu": mu, "g": g, "rho": rho,
+            "phi": phi, "eps": eps, "vxc": vxc, "v_out": v_out, "F": F, "parts": parts}

@@ -604,6 +604,35 @@ constexpr int RX2 = 2, TY2 = 16;
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 lds2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 
+__device__ __forceinline__ void mma_tf32_16x8x8(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// d += A B for one m16n8k8 TF32 tile in three products (a_hi b_hi + a_hi b_lo +
+// a_lo b_hi, hi = the value with its low 13 mantissa bits cleared): about 21 bits,
+// close to an FP32 product.  a: the thread's 4 A-fragment values, b: its 2 B values.
+__device__ __forceinline__ void mma_tf32x3(float (&d)[4], const float (&a)[4], const float (&b)[2]) {
+  uint32_t ah[4], al[4], bh[2], bl[2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float hi = __uint_as_float(__float_as_uint(a[i]) & 0xFFFFE000u);
+    ah[i] = __float_as_uint(hi);
+    al[i] = __float_as_uint(a[i] - hi);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float hi = __uint_as_float(__float_as_uint(b[i]) & 0xFFFFE000u);
+    bh[i] = __float_as_uint(hi);
+    bl[i] = __float_as_uint(b[i] - hi);
+  }
+  mma_tf32_16x8x8(d, al, bh);
+  mma_tf32_16x8x8(d, ah, bl);
+  mma_tf32_16x8x8(d, ah, bh);
+}
+
 __global__ void __launch_bounds__(THREADS, 1)
 k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* Yout,
           const float* __restrict__ gc, int nitems) {
@@ -761,11 +790,11 @@ k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* 
 #pragma unroll
     for (int sidx = 0; sidx < ZC; ++sidx) {
       const int z = zs + sidx;
-      if (z >= ze) break;
+      if (z < ze) {   // uniform over the CTA; no break, so the loop unrolls completely
       const int b = sidx % 3;
       const float* P = planes + (size_t)b * PY * RP;
+      float2 acc[RX2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
       if (vy) {
-        float2 acc[RX2];
         const float* row = P + (yl + R) * RP + o2;
         float2 w[RX2 + 2 * R];
 #pragma unroll
@@ -785,32 +814,45 @@ k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* 
           }
           acc[r] = s;
         }
-        // nonlocal scatter: the pieces that touch this warp's 8 rows x 2 columns at z
+      }
+      // nonlocal scatter on the tensor cores: for the warp's 16 nodes (8 rows x 2
+      // columns) x 8 orbitals, sum_p chi_p(node) gc_p(orbital) over the pieces active at
+      // z is a 16 x 8 x (4 per piece) product.  The m16n8k8 fragments match the thread
+      // layout (row groupID = the thread's row, threadID_in_group = its orbital pair),
+      // so two pieces (K = 8) per mma.sync, in 3xTF32 for FP32 accuracy, accumulate
+      // into nl, which is added to the stencil sum in FP32.
+      {
         const int li = (sidx * NRG + yg) * NXR + xr;
         const int ea = steps[li], eb = steps[li + 1];
         const int x0r = tx0 + xl0;
-        for (int e = ea; e < eb; ++e) {
-          const int it = steps[NL + 1 + e];
-          const int4 pa = *reinterpret_cast<const int4*>(&desc[it].gy0);   // gy0 gy1 gx0 gx1
-          if (gy < pa.x || gy >= pa.y) continue;
-          const int4 pb = *reinterpret_cast<const int4*>(&desc[it].base);  // base sy sz -
-          float2 gv[4];
+        const int cq = op, gq = r8;   // threadID_in_group, groupID
+        float nl[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int e = ea; e < eb; e += 2) {
+          float av[4], bv[2];
 #pragma unroll
-          for (int l = 0; l < 4; ++l) gv[l] = lds2(gcs + (it * 4 + l) * NB + o2);
-          const int rowoff = pb.x + pb.y * gy + pb.z * z;
+          for (int h = 0; h < 2; ++h) {
+            av[2 * h] = av[2 * h + 1] = 0.f;
+            bv[h] = 0.f;
+            if (e + h < eb) {
+              const int it = steps[NL + 1 + e + h];
+              const int4 pa = *reinterpret_cast<const int4*>(&desc[it].gy0);   // gy0 gy1 gx0 gx1
+              const int4 pb = *reinterpret_cast<const int4*>(&desc[it].base);  // base sy sz -
+              const bool rok = vy && gy >= pa.x && gy < pa.y;
+              const int rowoff = pb.x + pb.y * gy + pb.z * z;
 #pragma unroll
-          for (int r = 0; r < RX2; ++r) {
-            const int gx = x0r + r;
-            if (gx >= pa.z && gx < pa.w) {
-              const float4 c4 = __ldg(a.chi4 + rowoff + gx);
-              float2 d = __fmul2_rn(f2(c4.x), gv[0]);
-              d = __ffma2_rn(f2(c4.y), gv[1], d);
-              d = __ffma2_rn(f2(c4.z), gv[2], d);
-              d = __ffma2_rn(f2(c4.w), gv[3], d);
-              acc[r] = __fadd2_rn(acc[r], d);
+              for (int r = 0; r < RX2; ++r) {
+                const int gx = x0r + r;
+                if (rok && gx >= pa.z && gx < pa.w) av[2 * h + r] = __ldg(reinterpret_cast<const float*>(a.chi4) + (size_t)(rowoff + gx) * 4 + cq);
+              }
+              bv[h] = gcs[(it * 4 + cq) * NB + gq];
             }
           }
+          mma_tf32x3(nl, av, bv);
         }
+        acc[0] = __fadd2_rn(acc[0], make_float2(nl[0], nl[1]));
+        acc[1] = __fadd2_rn(acc[1], make_float2(nl[2], nl[3]));
+      }
+      if (vy) {
         // recurrence epilogue
         const float* Pp = yps + (size_t)b * TY2 * TX * NB + (yl * TX + xl0) * NB + o2;
         float* out = Yout + boff + (size_t)z * plane_el + ((size_t)gy * n1 + tx0 + xl0) * NB + o2;
@@ -828,6 +870,7 @@ k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* 
       load_z(z + R + 1, q[sidx % Q]);   // plane z - R is no longer needed
       cp_wait1();
       __syncthreads();
+      }
     }
   }
 }

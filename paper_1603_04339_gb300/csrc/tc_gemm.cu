@@ -30,7 +30,8 @@ namespace {
 
 constexpr int BM = 128;        // MMA M: rows of D = TMEM lanes
 constexpr int BK = 32;         // k-tile: 32 FP32 values = one 128-byte swizzled row
-constexpr int THREADS = 256;
+constexpr int THREADS = 256;   // rotation CTA
+constexpr int GTHREADS = 512;  // Gram CTA: 16 warps split, swizzle and stage the operands
 constexpr int GN = 128;        // Gram tile N
 constexpr int GST = 3;         // Gram pipeline stages
 constexpr int GCH = 8;         // Gram k-tiles per FP32 accumulation chunk (256 grid points)
@@ -130,14 +131,15 @@ __device__ __forceinline__ void mma_ktile(uint32_t d, uint32_t ds, uint32_t a_hi
 
 // ------------------------------------------------------------------ Gram
 // Load one k-tile (rows i0..i0+127 of A^T and j0..j0+127 of B^T, grid points
-// g0..g0+31) into registers: thread t holds 16-byte chunks f = t + 256 q,
+// g0..g0+31) into registers: thread t holds 16-byte chunks f = t + GTHREADS q,
 // row f / 8, chunk f % 8.  Out-of-range rows or points read as zero.
+constexpr int GQ = BM * 8 / GTHREADS;   // chunks per thread and operand
 template <bool VEC>
 __device__ __forceinline__ void gram_load(const float* __restrict__ X, long long ldx, int r0, int ns, long long nd,
-                                          long long g0, float4 (&v)[4]) {
+                                          long long g0, float4 (&v)[GQ]) {
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int f = threadIdx.x + THREADS * q;
+  for (int q = 0; q < GQ; ++q) {
+    const int f = threadIdx.x + GTHREADS * q;
     const int r = f >> 3, c = f & 7;
     const long long g = g0 + 4 * c;
     const bool rok = r0 + r < ns;
@@ -152,10 +154,10 @@ __device__ __forceinline__ void gram_load(const float* __restrict__ X, long long
     }
   }
 }
-__device__ __forceinline__ void gram_store(uint8_t* hi, uint8_t* lo, const float4 (&v)[4]) {
+__device__ __forceinline__ void gram_store(uint8_t* hi, uint8_t* lo, const float4 (&v)[GQ]) {
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int f = threadIdx.x + THREADS * q;
+  for (int q = 0; q < GQ; ++q) {
+    const int f = threadIdx.x + GTHREADS * q;
     const uint32_t off = swz(f >> 3, f & 7);
     float4 h, l;
     split4(v[q], h, l);
@@ -167,7 +169,7 @@ __device__ __forceinline__ void gram_store(uint8_t* hi, uint8_t* lo, const float
 // part[(blockIdx.x * nsplit + split)][j][i] = sum over this CTA's grid points of
 // A[g][ti*128 + i] B[g][tj*128 + j]  (tile pair blockIdx.x = (ti <= tj), split = blockIdx.y)
 template <bool VEC>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(GTHREADS, 1)
 k_gram_tc(const float* __restrict__ A, long long lda, const float* __restrict__ B, long long ldb, long long nd,
           int ns, int nt, int nsplit, double* __restrict__ part, int* status) {
   extern __shared__ uint8_t smem_raw[];
@@ -185,7 +187,7 @@ k_gram_tc(const float* __restrict__ A, long long lda, const float* __restrict__ 
   double* P = part + (size_t)(blockIdx.x * nsplit + sp) * (BM * GN);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (nkt <= 0) {   // empty split: a zero partial
-    for (int e = threadIdx.x; e < BM * GN; e += THREADS) P[e] = 0.0;
+    for (int e = threadIdx.x; e < BM * GN; e += GTHREADS) P[e] = 0.0;
     return;
   }
   if (threadIdx.x == 0) {
@@ -199,7 +201,7 @@ k_gram_tc(const float* __restrict__ A, long long lda, const float* __restrict__ 
   const uint32_t tmem = tmem_base;
   constexpr uint32_t IDESC = idesc_tf32(BM, GN);
   const int i0 = ti * BM, j0 = tj * GN;
-  float4 ca[4], cb[4], na[4], nb[4];
+  float4 ca[GQ], cb[GQ], na[GQ], nb[GQ];
   gram_load<VEC>(A, lda, i0, ns, nd, kt0 * BK, ca);
   gram_load<VEC>(B, ldb, j0, ns, nd, kt0 * BK, cb);
   bool first_flush = true, aborted = false;
@@ -225,15 +227,15 @@ k_gram_tc(const float* __restrict__ A, long long lda, const float* __restrict__ 
     }
     last = t;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) { ca[q] = na[q]; cb[q] = nb[q]; }
+    for (int q = 0; q < GQ; ++q) { ca[q] = na[q]; cb[q] = nb[q]; }
     if (t % GCH == GCH - 1 || t == nkt - 1) {
       // drain the FP32 chunk in TMEM into the FP64 partial
       ok = mbar_wait(&bar[s], (uint32_t)(t / GST) & 1u);
       tc_after();
       const int row = 32 * (warp & 3) + lane;
-      const int c0 = (warp >> 2) * (GN / 2);
+      const int c0 = (warp >> 2) * (GN * 4 / (GTHREADS / 32));   // warps 4q..4q+3 drain columns 32q..
 #pragma unroll
-      for (int h = 0; h < GN / 64; ++h) {
+      for (int h = 0; h < GN * 4 / GTHREADS; ++h) {
         float v[32], vs[32];
         const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(c0 + 32 * h);
         tmem_ld32(ta, v);
@@ -435,12 +437,12 @@ cudaError_t gram(sparc_ctx* ctx, const float* A, long long lda, const float* B, 
   if (vec) {
     e = cudaFuncSetAttribute(k_gram_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, GSMEM);
     if (e != cudaSuccess) return e;
-    k_gram_tc<true><<<dim3(pairs, nsplit), THREADS, GSMEM, st>>>(A, lda, B, ldb, nd, ns, nt, nsplit,
+    k_gram_tc<true><<<dim3(pairs, nsplit), GTHREADS, GSMEM, st>>>(A, lda, B, ldb, nd, ns, nt, nsplit,
                                                                  (double*)scratch, ctx->d_status);
   } else {
     e = cudaFuncSetAttribute(k_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, GSMEM);
     if (e != cudaSuccess) return e;
-    k_gram_tc<false><<<dim3(pairs, nsplit), THREADS, GSMEM, st>>>(A, lda, B, ldb, nd, ns, nt, nsplit,
+    k_gram_tc<false><<<dim3(pairs, nsplit), GTHREADS, GSMEM, st>>>(A, lda, B, ldb, nd, ns, nt, nsplit,
                                                                   (double*)scratch, ctx->d_status);
   }
   const long long nn = (long long)ns * ns;

@@ -25,7 +25,7 @@ EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_sync", "s
            "sparc_ham_set_veff", "sparc_ham_destroy", "sparc_apply_H", "sparc_cheb_filter",
            "sparc_lanczos_bounds", "sparc_rayleigh_ritz", "sparc_timing_enable", "sparc_timing_read",
            "sparc_launch_count", "sparc_apply_H_noalloc", "sparc_last_sweeps", "sparc_gram_f32",
-           "sparc_rotate_f32"]
+           "sparc_rotate_f32", "sparc_scf_create", "sparc_scf_step", "sparc_scf_read", "sparc_scf_destroy"]
 TIMED = {"hpass": 0, "gather": 1, "gram": 2, "eig": 3, "rotation": 4, "jacobi": 5, "fpass": 6}
 
 
@@ -37,6 +37,22 @@ class SparcNonlocal(ctypes.Structure):
     _fields_ = [("nproj", c_int), ("box_lo", POINTER(c_int32)), ("box_n", POINTER(c_int32)),
                 ("chi_off", POINTER(c_int64)), ("chi", POINTER(c_double)), ("chi_len", c_int64),
                 ("gamma", POINTER(c_double))]
+
+
+class SparcScfDesc(ctypes.Structure):
+    _fields_ = [("natom", c_int), ("R", POINTER(c_double)), ("Z", POINTER(c_double)), ("rc", POINTER(c_double)),
+                ("kT", c_double), ("mix_beta", c_double), ("mix_history", c_int), ("poisson_tol", c_double),
+                ("v0", POINTER(c_double))]
+
+
+class SparcScfInfo(ctypes.Structure):
+    _fields_ = [("free_energy", c_double), ("fermi", c_double), ("vresid", c_double), ("nelec", c_double),
+                ("e_band", c_double), ("e_xc", c_double), ("e_el", c_double), ("e_self", c_double),
+                ("e_entropy", c_double), ("poisson_iters", c_int), ("a0", c_double), ("a", c_double),
+                ("b", c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class SparcError(RuntimeError):
@@ -87,9 +103,15 @@ def load(path: str = LIB_PATH):
                                  c_void_p]
     L.sparc_rotate_f32.argtypes = [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int, c_void_p, c_int64,
                                    c_void_p]
+    L.sparc_scf_create.argtypes = [c_void_p, POINTER(SparcScfDesc), POINTER(c_void_p)]
+    L.sparc_scf_step.argtypes = [c_void_p, c_int, c_int, c_void_p, c_int, c_int64, c_void_p,
+                                 POINTER(SparcScfInfo), c_void_p]
+    L.sparc_scf_read.argtypes = [c_void_p, c_int, c_void_p, c_void_p]
+    L.sparc_scf_destroy.argtypes = [c_void_p]
+    L.sparc_scf_destroy.restype = None
     for name in ("sparc_timing_enable", "sparc_timing_read", "sparc_create", "sparc_sync", "sparc_ham_create", "sparc_ham_set_veff",
                  "sparc_apply_H", "sparc_cheb_filter", "sparc_lanczos_bounds", "sparc_rayleigh_ritz",
-                 "sparc_gram_f32", "sparc_rotate_f32"):
+                 "sparc_gram_f32", "sparc_rotate_f32", "sparc_scf_create", "sparc_scf_step", "sparc_scf_read"):
         getattr(L, name).restype = c_int
     _lib = L
     return L
@@ -133,6 +155,7 @@ class Context:
         self.handle = h
         self.device = device
         self._hams = weakref.WeakSet()   # Hamiltonians of this context, closed with it
+        self._scfs = weakref.WeakSet()   # SCF states, closed before the Hamiltonians
 
     def error(self) -> str:
         return load().sparc_last_error(self.handle).decode()
@@ -168,6 +191,8 @@ class Context:
 
     def close(self):
         if self.handle:
+            for S in list(self._scfs):
+                S.close()
             for H in list(self._hams):
                 H.close()
             load().sparc_destroy(self.handle)
@@ -315,3 +340,63 @@ def sparc_rotate_f32(ctx: Context, U, Yr, C, nd=None, stream=None):
     nd = U.shape[-1] if nd is None else nd
     ctx.check(load().sparc_rotate_f32(ctx.handle, _ptr(U), int(U.shape[-1]), _ptr(Yr), int(nd), int(ns), _ptr(C),
                                       int(C.shape[-1]), _stream(stream)))
+
+
+class Scf:
+    """SCF state on a Hamiltonian (sparc_scf_create): pseudocharges, history, fields."""
+
+    FIELDS = {"b": 0, "rho": 1, "phi": 2, "vxc": 3, "vout": 4, "veff": 5}
+
+    def __init__(self, H: Hamiltonian, R, Z, rc, v0, kT=0.01, mix_beta=0.3, mix_history=7, poisson_tol=1e-10):
+        self.H = H
+        self._R = np.ascontiguousarray(R, dtype=np.float64).reshape(-1)
+        self._Z = np.ascontiguousarray(Z, dtype=np.float64)
+        self._rc = np.ascontiguousarray(rc, dtype=np.float64)
+        v = np.asarray(v0)
+        if np.iscomplexobj(v):
+            v = np.ascontiguousarray(v.astype(np.complex128)).view(np.float64)
+        self._v0 = np.ascontiguousarray(v, dtype=np.float64)
+        d = SparcScfDesc()
+        d.natom = int(self._Z.size)
+        d.R = self._R.ctypes.data_as(POINTER(c_double))
+        d.Z = self._Z.ctypes.data_as(POINTER(c_double))
+        d.rc = self._rc.ctypes.data_as(POINTER(c_double))
+        d.kT = float(kT)
+        d.mix_beta = float(mix_beta)
+        d.mix_history = int(mix_history)
+        d.poisson_tol = float(poisson_tol)
+        d.v0 = self._v0.ctypes.data_as(POINTER(c_double))
+        h = c_void_p()
+        H.ctx.check(load().sparc_scf_create(H.handle, ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+        H.ctx._scfs.add(self)
+
+    @classmethod
+    def from_system(cls, H: Hamiltonian, sysd, **kw):
+        return cls(H, sysd.wl.atoms, sysd.Z, sysd.rc, sysd.v0, **kw)
+
+    def read(self, name: str, out, stream=None):
+        """Copy a grid field (b, rho, phi, vxc, vout, veff) into the float64 CUDA tensor `out`."""
+        self.H.ctx.check(load().sparc_scf_read(self.handle, self.FIELDS[name], _ptr(out), _stream(stream)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().sparc_scf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sparc_scf_step(S: Scf, U, eig, m, ns=None, ld=None, stream=None, dtype=None) -> dict:
+    """One SCF iteration on the orbitals U (ns, ld) in place; returns the sparc_scf_info fields."""
+    ns = U.shape[0] if ns is None else ns
+    ld = U.shape[-1] if ld is None else ld
+    dt = dtype_code(U) if dtype is None else dtype
+    info = SparcScfInfo()
+    S.H.ctx.check(load().sparc_scf_step(S.handle, dt, int(m), _ptr(U), int(ns), int(ld), _ptr(eig),
+                                        ctypes.byref(info), _stream(stream)))
+    return info.as_dict()

@@ -31,7 +31,7 @@ import numpy as np
 __all__ = [
     "Workload", "Projectors", "make_projectors", "gaussian_veff", "fcc_sites",
     "diamond_sites", "monkhorst_pack", "config1", "config2", "config3",
-    "small_case", "random_orbitals", "lanczos_start",
+    "small_case", "random_orbitals", "lanczos_start", "ScfSystem", "scf_small", "scf_fcc32",
 ]
 
 
@@ -272,3 +272,62 @@ def small_case(n=(14, 12, 13), h=(0.55, 0.6, 0.5), fd_radius=6, natom=2, k=(0.0,
                            with_p=with_p) if natom else Projectors.empty()
     return Workload(f"small_{n[0]}x{n[1]}x{n[2]}", tuple(n), tuple(h), fd_radius,
                     np.asarray([k], np.float64), np.ones(1), veff, atoms, proj, ns, m, seed)
+
+
+@dataclass
+class ScfSystem:
+    """Inputs of an SCF run: the workload (grid, projectors; its veff is unused, the SCF
+    sets V_eff), valence charges Z and widths rc of the local pseudopotentials
+    -Z erf(r/rc)/r, the Lanczos start vector and the start orbitals."""
+    wl: Workload
+    Z: np.ndarray
+    rc: np.ndarray
+    v0: np.ndarray
+    U0: np.ndarray
+
+    @property
+    def nelec(self) -> float:
+        return float(np.sum(self.Z))
+
+
+def scf_small(n=(20, 20, 20), h=(0.5, 0.5, 0.5), natom=4, ns=12, m=12, seed=41, Z=1.0, rc_loc=0.7,
+              rc_proj=0.9, gamma=0.3) -> ScfSystem:
+    """A small cell for SCF parity against the oracle: atoms at random sites at least
+    3.5 bohr apart (periodic images included), s+p projectors with energies U[-gamma, gamma]."""
+    rng = np.random.default_rng(seed)
+    L = np.array([n[s] * h[s] for s in range(3)])
+    atoms = []
+    while len(atoms) < natom:
+        x = rng.uniform(-0.5, 0.5, 3) * L
+        ok = True
+        for y in atoms:
+            d = x - y
+            d -= L * np.round(d / L)
+            ok = ok and float(np.linalg.norm(d)) > 3.5
+        if ok:
+            atoms.append(x)
+    atoms = np.array(atoms)
+    proj = make_projectors(n, h, atoms, rc_proj, rng.uniform(-gamma, gamma, natom),
+                           rng.uniform(-gamma, gamma, natom))
+    nd = n[0] * n[1] * n[2]
+    wl = Workload(f"scf_{n[0]}x{n[1]}x{n[2]}", tuple(n), tuple(h), 6, np.zeros((1, 3)), np.ones(1),
+                  np.zeros(nd), atoms, proj, ns, m, seed)
+    return ScfSystem(wl, np.full(natom, float(Z)), np.full(natom, float(rc_loc)), lanczos_start(nd, seed + 1),
+                     random_orbitals(nd, ns, seed + 2))
+
+
+def scf_fcc32(seed=1005, a=8.1, h=0.45, sigma=0.05, Z=3.0, rc_loc=0.8, rc_proj=1.2, ns=58, m=20) -> ScfSystem:
+    """32 atoms on 2x2x2 perturbed FCC cells (a = 8.1 bohr, 36^3 grid at h = 0.45),
+    Z = 3 (N_e = 96), local pseudopotential width 0.8 bohr, s+p projectors with
+    energies U[-0.5, 0.5] Ha, Ns = 58, m = 20 (the SCF cell of the learned-density study)."""
+    rng = np.random.default_rng(seed)
+    n = int(round(2 * a / h))
+    sites = fcc_sites((2, 2, 2), a, rng, sigma)
+    hh = (2 * a / n,) * 3
+    proj = make_projectors((n, n, n), hh, sites, rc_proj, rng.uniform(-0.5, 0.5, len(sites)),
+                           rng.uniform(-0.5, 0.5, len(sites)))
+    nd = n ** 3
+    wl = Workload("fcc32_scf", (n, n, n), hh, 6, np.zeros((1, 3)), np.ones(1), np.zeros(nd), sites, proj, ns, m,
+                  seed)
+    return ScfSystem(wl, np.full(len(sites), Z), np.full(len(sites), rc_loc), lanczos_start(nd, seed + 1),
+                     random_orbitals(nd, ns, seed + 2))

@@ -1,0 +1,128 @@
+"""SCF iteration (sparc_scf_step) through the C ABI against the SCF oracle.
+
+* pseudocharges and the starting potential element by element;
+* three FP64 iterations from the same orbitals, start vector and potential: Ritz
+  values, Fermi level, density, electrostatic potential, V_out, free energy and the
+  Anderson-extrapolated next V_eff, per iteration;
+* convergence of the FP64 iteration, and the mixed path (FP32 orbitals) reaching the
+  same free energy within 1e-5 Ha per atom.
+"""
+import numpy as np
+import pytest
+
+from oracle import scf_oracle as SO
+from oracle import sparc_oracle as O
+from paper_1603_04339_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+KT, BETA, HIST = 0.01, 0.3, 7
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1603_04339_gb300 import build, sparc
+    build.build()
+    c = sparc.Context(0)
+    yield c
+    c.close()
+
+
+def _field(S, name, nd):
+    out = torch.zeros(nd, dtype=torch.float64, device="cuda")
+    S.read(name, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def test_pseudocharge_and_starting_potential(ctx):
+    from paper_1603_04339_gb300 import sparc
+    sysd = synth.scf_small()
+    wl = sysd.wl
+    H = sparc.Hamiltonian.from_workload(ctx, wl)
+    S = sparc.Scf.from_system(H, sysd, kT=KT)
+    b_ref, e_self, q = SO.pseudocharge(wl.n, wl.h, 6, wl.atoms, sysd.Z, sysd.rc)
+    assert np.allclose(q, -sysd.Z, atol=1e-8)
+    b = _field(S, "b", wl.nd)
+    assert np.max(np.abs(b - b_ref)) < 1e-12 * np.max(np.abs(b_ref))
+    v0 = _field(S, "veff", wl.nd)
+    assert np.max(np.abs(v0 - SO.lda(-b_ref)[1])) < 1e-12 * np.max(np.abs(v0))
+
+
+def test_three_fp64_iterations_match_the_oracle(ctx):
+    from paper_1603_04339_gb300 import sparc
+    sysd = synth.scf_small()
+    wl = sysd.wl
+    H = sparc.Hamiltonian.from_workload(ctx, wl)
+    S = sparc.Scf.from_system(H, sysd, kT=KT, mix_beta=BETA, mix_history=HIST, poisson_tol=1e-13)
+    U = torch.from_numpy(sysd.U0.copy()).cuda()
+    eig = torch.zeros(wl.ns, dtype=torch.float64, device="cuda")
+    b, e_self, _ = SO.pseudocharge(wl.n, wl.h, 6, wl.atoms, sysd.Z, sysd.rc)
+    v_in = SO.lda(-b)[1]
+    xh, fh = [], []
+    U_or, lam_prev = sysd.U0.copy(), None
+    for it in range(3):
+        info = sparc.sparc_scf_step(S, U, eig, wl.m)
+        Hor = O.OracleH(wl, veff=v_in)
+        out = SO.scf_iteration(Hor, U_or, lam_prev, sysd.v0, b, e_self, sysd.nelec, KT, wl.m)
+        lam = eig.cpu().numpy()
+        assert np.max(np.abs(lam - out["lam"])) < 1e-9 * np.max(np.abs(out["lam"])), it
+        assert abs(info["fermi"] - out["mu"]) < 1e-9, it
+        assert abs(info["nelec"] - sysd.nelec) < 1e-9
+        assert abs(info["e_self"] - e_self) < 1e-10 * e_self
+        rho = _field(S, "rho", wl.nd)
+        assert np.max(np.abs(rho - out["rho"])) < 1e-9 * np.max(out["rho"]), it
+        phi = _field(S, "phi", wl.nd)
+        assert np.max(np.abs(phi - out["phi"])) < 1e-8 * np.max(np.abs(out["phi"])), it
+        vout = _field(S, "vout", wl.nd)
+        assert np.max(np.abs(vout - out["v_out"])) < 1e-8 * np.max(np.abs(out["v_out"])), it
+        assert abs(info["free_energy"] - out["F"]) < 1e-9 * abs(out["F"]), (it, info["free_energy"], out["F"])
+        xh.append(v_in)
+        fh.append(out["v_out"] - v_in)
+        v_next = SO.anderson(xh, fh, BETA, HIST)
+        veff = _field(S, "veff", wl.nd)
+        assert np.max(np.abs(veff - v_next)) < 1e-8 * np.max(np.abs(v_next)), it
+        v_in, U_or, lam_prev = v_next, out["U"], out["lam"]
+
+
+def _run(ctx, dtype, iters):
+    from paper_1603_04339_gb300 import sparc
+    sysd = synth.scf_small()
+    wl = sysd.wl
+    H = sparc.Hamiltonian.from_workload(ctx, wl)
+    S = sparc.Scf.from_system(H, sysd, kT=KT, mix_beta=BETA, mix_history=HIST, poisson_tol=1e-11)
+    U = torch.from_numpy(sysd.U0.copy()).to(dtype).cuda()
+    eig = torch.zeros(wl.ns, dtype=torch.float64, device="cuda")
+    hist = [sparc.sparc_scf_step(S, U, eig, wl.m) for _ in range(iters)]
+    S.close()
+    H.close()
+    return hist, len(sysd.Z)
+
+
+def test_fp64_iteration_converges_and_mixed_reaches_the_same_energy(ctx):
+    h64, natom = _run(ctx, torch.float64, 30)
+    res = [h["vresid"] for h in h64]
+    print("FP64 V residuals:", " ".join(f"{r:.1e}" for r in res))
+    assert res[-1] < 1e-6, res
+    F = [h["free_energy"] for h in h64]
+    assert abs(F[-1] - F[-2]) < 1e-8 * natom
+    h32, _ = _run(ctx, torch.float32, 30)
+    res32 = [h["vresid"] for h in h32]
+    print("mixed V residuals:", " ".join(f"{r:.1e}" for r in res32))
+    dF = abs(h32[-1]["free_energy"] - F[-1]) / natom
+    print(f"free energy FP64 {F[-1]:.10f} Ha, mixed {h32[-1]['free_energy']:.10f} Ha, |dF|/atom {dF:.2e}")
+    assert dF < 1e-5
+
+
+def test_scf_rejects_bad_arguments(ctx):
+    from paper_1603_04339_gb300 import sparc
+    sysd = synth.scf_small()
+    H = sparc.Hamiltonian.from_workload(ctx, sysd.wl)
+    with pytest.raises(sparc.SparcError):
+        sparc.Scf(H, sysd.wl.atoms, sysd.Z, sysd.rc, sysd.v0, kT=0.0)
+    S = sparc.Scf.from_system(H, sysd)
+    U = torch.zeros((1, sysd.wl.nd), dtype=torch.float64, device="cuda")   # 2 ns < N_e = 4
+    eig = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(sparc.SparcError):
+        sparc.sparc_scf_step(S, U, eig, 6)

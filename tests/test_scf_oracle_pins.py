@@ -1,0 +1,160 @@
+"""Pins of the SCF oracle (oracle/scf_oracle.py) to facts outside itself: closed forms,
+limits, exact solutions of the discrete problems and a jellium fixed point."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import scf_oracle as S
+from oracle import sparc_oracle as O
+
+
+def test_local_potential_limits():
+    Z, rc = 3.0, 0.8
+    assert abs(S.local_potential(np.array([0.0]), Z, rc)[0] - S.local_potential(np.array([1e-7]), Z, rc)[0]) < 1e-9
+    r = np.array([12.0])
+    assert abs(S.local_potential(r, Z, rc)[0] + Z / 12.0) < 1e-14   # erf(15) = 1
+
+
+def test_pseudocharge_is_the_gaussian_of_charge_minus_z_and_its_self_energy():
+    """-(1/4pi) lap V_I of V_I = -Z erf(r/rc)/r is -Z (pi^3/2 rc^3)^-1 exp(-r^2/rc^2) in the
+    continuum; on a fine grid the discrete b_I matches it, integrates to -Z, and
+    E_self = 1/2 int b V = Z^2 / (sqrt(2 pi) rc)."""
+    n, h = (40, 40, 40), (0.2, 0.2, 0.2)
+    Z, rc = 3.0, 0.8
+    R = [[0.013, -0.021, 0.007]]
+    b, e_self, q = S.pseudocharge(n, h, 6, R, [Z], [rc])
+    assert abs(q[0] + Z) < 1e-8 * Z
+    assert abs(b.sum() * 0.008 + Z) < 1e-8 * Z
+    xs = [-0.5 * n[s] * h[s] + h[s] * np.arange(n[s]) - R[0][s] for s in range(3)]
+    Zc, Y, X = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+    r2 = X * X + Y * Y + Zc * Zc
+    ref = -Z / (math.pi ** 1.5 * rc ** 3) * np.exp(-r2 / rc ** 2)
+    assert np.max(np.abs(b - ref.reshape(-1))) < 1e-5 * np.max(np.abs(ref))
+    assert abs(e_self - Z * Z / (math.sqrt(2 * math.pi) * rc)) < 1e-6 * e_self
+
+
+def test_pseudocharge_wraps_periodically():
+    """An atom near a face: the same charge, b equal to that of the centred atom shifted."""
+    n, h = (24, 24, 24), (0.5, 0.5, 0.5)
+    b1, e1, _ = S.pseudocharge(n, h, 6, [[0.0, 0.0, 0.0]], [2.0], [0.7])
+    b2, e2, _ = S.pseudocharge(n, h, 6, [[-6.0, 0.0, 0.0]], [2.0], [0.7])   # 12 nodes to the left
+    assert abs(e1 - e2) < 1e-12 * e1
+    assert np.allclose(np.roll(b1.reshape(24, 24, 24), -12, axis=2).reshape(-1), b2, atol=1e-14)
+
+
+def test_poisson_plane_wave_closed_form():
+    n, h, n_o = (12, 10, 8), (0.4, 0.5, 0.45), 6
+    j = (2, 1, 3)
+    xs = [h[s] * np.arange(n[s]) for s in range(3)]
+    Zc, Y, X = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+    th = [2 * math.pi * j[s] / (n[s] * h[s]) for s in range(3)]
+    f = np.cos(th[0] * X + th[1] * Y + th[2] * Zc).reshape(-1)
+    lam = sum(2.0 * O.fd_symbol(np.array([th[s] * h[s]]), n_o, h[s])[0] for s in range(3))
+    phi = S.poisson(f, n, h, n_o)
+    assert np.allclose(phi, 4 * math.pi * f / lam, atol=1e-12 * np.max(np.abs(phi)))
+
+
+def test_poisson_matches_dense_solve():
+    n, h, n_o = (6, 5, 7), (0.5, 0.6, 0.4), 2
+    nd = 210
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal(nd)
+    f -= f.mean()
+    Lm = np.zeros((nd, nd))
+    for c in range(nd):
+        e = np.zeros(nd); e[c] = 1.0
+        Lm[:, c] = O.laplacian(e.reshape(1, n[2], n[1], n[0]), n, h, n_o).reshape(-1).real
+    phi_d = np.linalg.lstsq(-Lm / (4 * math.pi), f, rcond=None)[0]
+    phi_d -= phi_d.mean()
+    phi = S.poisson(f, n, h, n_o)
+    assert np.allclose(phi, phi_d, atol=1e-10 * np.max(np.abs(phi_d)))
+
+
+def test_lda_exchange_closed_form_and_potential_derivative():
+    rs = np.array([0.5, 1.0, 2.0, 5.0])
+    rho = 3.0 / (4.0 * math.pi * rs ** 3)
+    eps, v = S.lda(rho)
+    # exchange alone, the textbook form in rs: -(3/4pi)(9pi/4)^(1/3)/rs
+    ex = -(3.0 / (4.0 * math.pi)) * (9.0 * math.pi / 4.0) ** (1.0 / 3.0) / rs
+    A, a1, b1, b2, b3, b4 = S.PW92
+    ec = eps - ex
+    assert np.all(ec < 0) and np.all(np.diff(ec) > 0)      # negative, weaker at lower density
+    # V_xc = d(rho eps_xc)/d rho, by central differences
+    for r0 in rho:
+        d = 1e-6 * r0
+        e_p, _ = S.lda(np.array([r0 + d]))
+        e_m, _ = S.lda(np.array([r0 - d]))
+        num = ((r0 + d) * e_p[0] - (r0 - d) * e_m[0]) / (2 * d)
+        _, v0 = S.lda(np.array([r0]))
+        assert abs(num - v0[0]) < 1e-7 * abs(v0[0])
+
+
+def test_pw92_high_density_limit_is_gell_mann_brueckner():
+    """d eps_c / d ln rs -> (1 - ln 2)/pi^2 as rs -> 0 (exact high-density coefficient)."""
+    A = (1.0 - math.log(2.0)) / math.pi ** 2
+    assert abs(S.PW92[0] - A) < 2e-6
+    rs1, rs2 = 1e-7, 2e-7
+    rho = 3.0 / (4.0 * math.pi * np.array([rs1, rs2]) ** 3)
+    eps, _ = S.lda(rho)
+    ex = -(3.0 / (4.0 * math.pi)) * (9.0 * math.pi / 4.0) ** (1.0 / 3.0) / np.array([rs1, rs2])
+    ec = eps - ex
+    slope = (ec[1] - ec[0]) / math.log(2.0)
+    assert abs(slope - A) < 1e-3 * A
+
+
+def test_fermi_level_symmetric_spectrum():
+    lam = 0.1 * np.arange(20)
+    mu = S.fermi_level(lam, 20.0, 0.01)        # 10 of 20 levels filled: midway by symmetry
+    assert abs(mu - 0.95) < 1e-12
+    g = S.occupations(lam, mu, 0.01)
+    assert abs(2 * g.sum() - 20.0) < 1e-12
+    assert abs(S.entropy_term(np.array([0.5]), 0.01) - 2 * 0.01 * math.log(0.5)) < 1e-15
+
+
+def test_anderson_solves_a_linear_fixed_point_exactly():
+    rng = np.random.default_rng(5)
+    dim = 5
+    G = 0.5 * rng.standard_normal((dim, dim)) / math.sqrt(dim)
+    c = rng.standard_normal(dim)
+    x_star = np.linalg.solve(np.eye(dim) - G, c)
+    xs, fs = [np.zeros(dim)], []
+    for it in range(dim + 2):
+        fs.append(G @ xs[-1] + c - xs[-1])
+        xs.append(S.anderson(xs, fs, 0.3, 7))
+    assert np.linalg.norm(xs[-1] - x_star) < 1e-10 * np.linalg.norm(x_star)
+
+
+def test_jellium_is_a_fixed_point_with_closed_form_energy():
+    """Uniform background b = -N_e/Omega, no projectors, 14 electrons in the 7 lowest
+    plane waves (a closed shell at the Gamma point; 3 more orbitals from the next shell
+    keep the filter cutoff above it and stay empty): the density is uniform, phi = 0,
+    V_xc is constant, so V_in = V_xc(N_e/Omega) is self-consistent and the free
+    energy is 2 sum g lambda + Omega (eps_xc - V_xc) rho + entropy, with lambda the FD
+    free-electron values (Eq. FD:Laplacian symbol) shifted by V_xc."""
+    n, h, n_o = (8, 8, 8), (0.5, 0.5, 0.5), 6
+    nd = 512
+    vol = nd * 0.125
+    Ne, kT = 14.0, 1e-3
+    rho0 = Ne / vol
+    eps0, v0 = S.lda(np.array([rho0]))
+    H = O.OracleH(n=n, h=h, fd_radius=n_o, k=(0, 0, 0), veff=np.full(nd, v0[0]),
+                  proj=type("P", (), {"nproj": 0})())
+    b = np.full(nd, -rho0)
+    rng = np.random.default_rng(7)
+    U = rng.standard_normal((10, nd))
+    lam_prev = None
+    for it in range(12):     # converge the subspace at fixed V_in
+        out = S.scf_iteration(H, U, lam_prev, rng.standard_normal(nd), b, 0.0, Ne, kT, 12)
+        U, lam_prev = out["U"], out["lam"]
+    sym = lambda j: 2 * O.fd_symbol(np.array([2 * math.pi * j / 8]), n_o, 0.5)[0] / 2.0
+    lam_ref = np.sort([v0[0]] + [v0[0] + sym(1)] * 6)
+    assert np.allclose(out["lam"][:7], lam_ref, atol=1e-9)
+    assert out["lam"][7] > lam_ref[-1] + 1.0
+    assert np.allclose(out["rho"], rho0, atol=1e-9 * rho0)
+    assert np.max(np.abs(out["phi"])) < 1e-9
+    assert np.max(np.abs(out["v_out"] - v0[0])) < 1e-9
+    g = out["g"]
+    assert np.all(g[7:] < 1e-100)
+    F_ref = 2 * np.sum(g[:7] * lam_ref) + vol * (eps0[0] - v0[0]) * rho0 + S.entropy_term(g, kT)
+    assert abs(out["F"] - F_ref) < 1e-9 * abs(F_ref)
