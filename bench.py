@@ -40,6 +40,7 @@ def _args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-scf", action="store_true", help="skip the SCF time-to-solution comparison")
     ap.add_argument("--cpu-sample-cols", type=int, default=1)
     ap.add_argument("--mode", choices=["step", "filter"], default="step",
                     help="filter: only the Chebyshev filter (for profiler captures)")
@@ -160,6 +161,52 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def scf_time_to_solution(sparc, synth, torch, tol_per_atom=1e-5, max_iter=60):
+    """SCF on the 32-atom FCC cell (36^3 grid): the FP64 path run to V residual 1e-9
+    gives the reference free energy; for the FP64 and the mixed (FP32 orbitals) paths,
+    the device time until the free energy is within tol_per_atom per atom of it."""
+    import time as _t
+    sysd = synth.scf_fcc32()
+    wl = sysd.wl
+    natom = len(sysd.Z)
+    runs = {}
+    for name, dt in (("fp64", torch.float64), ("mixed", torch.float32)):
+        ctx = sparc.Context(torch.cuda.current_device())
+        H = sparc.Hamiltonian.from_workload(ctx, wl)
+        S = sparc.Scf.from_system(H, sysd, kT=0.01, mix_beta=0.3, mix_history=7, poisson_tol=1e-10)
+        U = torch.from_numpy(sysd.U0.copy()).to(dt).cuda()
+        eig = torch.zeros(wl.ns, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = _t.perf_counter()
+        hist = []
+        for it in range(max_iter):
+            info = sparc.sparc_scf_step(S, U, eig, wl.m)   # synchronises its stream
+            hist.append((_t.perf_counter() - t0, info["free_energy"], info["vresid"]))
+            if name == "fp64" and info["vresid"] < 1e-9:
+                break
+            if name == "mixed" and it >= 5 and info["vresid"] < 1e-6:
+                break
+        runs[name] = hist
+        ctx.close()
+    E_ref = runs["fp64"][-1][1]
+
+    def reach(hist):
+        for k, (t, F, _) in enumerate(hist):
+            if all(abs(F2 - E_ref) <= tol_per_atom * natom for _, F2, _ in hist[k:]):
+                return k + 1, t
+        return None, None
+
+    out = {"workload": "32-atom perturbed-FCC cell, 36^3 grid h=0.45, Z=3 (N_e=96), Ns=58, m=20, "
+                       "kT=0.01 Ha, Anderson 0.3/7", "tolerance_ha_per_atom": tol_per_atom, "E_ref_ha": E_ref}
+    for name, hist in runs.items():
+        k, t = reach(hist)
+        out[name] = {"iterations_to_tol": k, "seconds_to_tol": t, "iterations_run": len(hist),
+                     "final_vresid": hist[-1][2], "final_dE_per_atom": abs(hist[-1][1] - E_ref) / natom}
+    if out["fp64"]["seconds_to_tol"] and out["mixed"]["seconds_to_tol"]:
+        out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds_to_tol"] / out["mixed"]["seconds_to_tol"]
+    return out
 
 
 # ------------------------------------------------------------------ our arm
@@ -343,6 +390,7 @@ def run_ours(args):
                                   "jacobi_sweeps": sweeps},
         "filter_only": {"value": units / ((fp_ms + ga_ms) / args.steps * 1e-3) / 1e9, "unit": UNIT},
         "clocks": ck, "e2e": e2e, "gpu_launches": int(launches), "cpu_baseline": cpu,
+        "scf": None if (args.no_scf or world > 1) else scf_time_to_solution(sparc, synth, torch),
     }
     print(json.dumps(line), flush=True)
     if world > 1:

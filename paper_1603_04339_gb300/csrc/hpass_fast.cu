@@ -802,17 +802,19 @@ k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* 
         const float* V = vbs + (size_t)b * TY2 * TX + yl * TX + xl0;
 #pragma unroll
         for (int r = 0; r < RX2; ++r) {
-          float2 s = __fmul2_rn(f2(a.c0 + V[r] - a.shift), q[(sidx + R) % Q][r]);
+          // one partial sum per axis: three short dependency chains instead of one long one
+          float2 sx = __fmul2_rn(f2(a.c0 + V[r] - a.shift), q[(sidx + R) % Q][r]);
+          float2 sy = make_float2(0.f, 0.f), sz = make_float2(0.f, 0.f);
           const float* col = P + (xl0 + r + R) * NB + o2;
 #pragma unroll
           for (int p = 1; p <= R; ++p) {
             const float2 u = lds2(col + (yl + R + p) * RP);
             const float2 d = lds2(col + (yl + R - p) * RP);
-            s = __ffma2_rn(a.cx2[p], __fadd2_rn(w[R + r + p], w[R + r - p]), s);
-            s = __ffma2_rn(a.cy2[p], __fadd2_rn(u, d), s);
-            s = __ffma2_rn(a.cz2[p], __fadd2_rn(q[(sidx + R + p) % Q][r], q[(sidx + R - p) % Q][r]), s);
+            sx = __ffma2_rn(a.cx2[p], __fadd2_rn(w[R + r + p], w[R + r - p]), sx);
+            sy = __ffma2_rn(a.cy2[p], __fadd2_rn(u, d), sy);
+            sz = __ffma2_rn(a.cz2[p], __fadd2_rn(q[(sidx + R + p) % Q][r], q[(sidx + R - p) % Q][r]), sz);
           }
-          acc[r] = s;
+          acc[r] = __fadd2_rn(sx, __fadd2_rn(sy, sz));
         }
       }
       // nonlocal scatter on the tensor cores: for the warp's 16 nodes (8 rows x 2

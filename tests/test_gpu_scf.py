@@ -47,7 +47,12 @@ def test_pseudocharge_and_starting_potential(ctx):
     b = _field(S, "b", wl.nd)
     assert np.max(np.abs(b - b_ref)) < 1e-12 * np.max(np.abs(b_ref))
     v0 = _field(S, "veff", wl.nd)
-    assert np.max(np.abs(v0 - SO.lda(-b_ref)[1])) < 1e-12 * np.max(np.abs(v0))
+    # V_xc ~ rho^(1/3) has an unbounded derivative at rho -> 0, where rho0 = -b is ~1e-10:
+    # the 1e-12 agreement of b becomes ~1e-9 there; where rho0 is not tiny it stays ~1e-13
+    v_ref = SO.lda(-b_ref)[1]
+    big = -b_ref > 1e-4 * np.max(-b_ref)
+    assert np.max(np.abs(v0 - v_ref)[big]) < 1e-12 * np.max(np.abs(v0))
+    assert np.max(np.abs(v0 - v_ref)) < 1e-8 * np.max(np.abs(v0))
 
 
 def test_three_fp64_iterations_match_the_oracle(ctx):
