@@ -28,8 +28,8 @@ METRIC = "CheFSI filter throughput (G point-orbital-degrees/s)"
 UNIT = "Gpt-orb-deg/s"
 WORKLOAD = "64^3 grid h=0.4, 128 perturbed-FCC s+p atoms, Ns=512, m=24, Gamma point"
 # DRAM bytes of k_pass_f2 per block of 8 orbitals per degree on this cell, from the ncu
-# capture summarised in profiles/k_pass_f2_64cube_4blocks.md ((66.03 + 1.87) MB / 4 blocks)
-PASS_DRAM_BYTES_PER_BLOCK = (66.034688e6 + 1.869824e6) / 4
+# capture summarised in profiles/k_pass_f2_64cube_4blocks.md ((66.18 + 1.93) MB / 4 blocks)
+PASS_DRAM_BYTES_PER_BLOCK = (66.179328e6 + 1.934336e6) / 4
 
 
 def _args():
@@ -163,6 +163,19 @@ def run_reference(args):
     return 0
 
 
+def job_rate(ms_local, units_per_rank, world, dist=None, device="cpu"):
+    """Whole-job rate of weakly scaled replicas: every rank processed units_per_rank in
+    ms_local; the job time is the slowest rank's (all-reduce MAX), the job rate
+    world * units / time in G units/s.  Returns (job ms, rate)."""
+    ms = float(ms_local)
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * units_per_rank / (ms * 1e-3) / 1e9
+
+
 def scf_time_to_solution(sparc, synth, torch, tol_per_atom=1e-5, max_iter=60):
     """SCF on the 32-atom FCC cell (36^3 grid): the FP64 path run to V residual 1e-9
     gives the reference free energy; for the FP64 and the mixed (FP32 orbitals) paths,
@@ -282,12 +295,8 @@ def run_ours(args):
     fp_ms, fp_n = ctx.timing_read("fpass")
     sweeps = ctx.last_sweeps()
     ctx.timing(False)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     units = nd * ns * m
-    value = world * units / (ms * 1e-3) / 1e9
+    ms, value = job_rate(ms, units, world, dist if world > 1 else None, "cuda")
 
     # ---- roofline of the dominant kernel: the tiled filter pass k_pass_f2
     # algorithmic bytes per step: degrees 2..m read Y_j and Y_{j-1} and write Y_{j+1}
@@ -298,7 +307,7 @@ def run_ours(args):
     achieved = bytes_step / (fp_ms / args.steps * 1e-3) / 1e9
     peak, peak_kind = _peaks()
     # DRAM traffic: one ncu capture of a 4-block launch of this cell (profiles/
-    # k_pass_f2_64cube_4blocks.md: 66.03 MB read + 1.87 MB written), scaled by blocks
+    # k_pass_f2_64cube_4blocks.md: 66.18 MB read + 1.93 MB written), scaled by blocks
     traffic = PASS_DRAM_BYTES_PER_BLOCK * (ns // 8) * m / fp_launches if fp_launches else None
 
     # ---- end to end through the C ABI with host buffers: every step copies its input from

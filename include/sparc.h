@@ -215,6 +215,7 @@ typedef struct {
   int mix_history;       /* Anderson history, 0..8 (the paper: 7) */
   double poisson_tol;    /* relative residual of the Poisson solve, > 0 */
   const double* v0;      /* Lanczos start vector, host: Nd doubles (k = 0) or Nd (re, im) pairs */
+  const int32_t* proj_atom; /* [nproj of H] atom of each projector, for sparc_scf_forces; may be NULL */
 } sparc_scf_desc;
 
 typedef struct {
@@ -240,6 +241,15 @@ sparc_status sparc_scf_step(sparc_scf* S, sparc_dtype dtype, int m, void* U, int
  * iteration), 2 phi, 3 V_xc, 4 V_out, 5 the current V_eff of H (the next V_in). */
 sparc_status sparc_scf_read(const sparc_scf* S, int which, double* dst, void* stream);
 void sparc_scf_destroy(sparc_scf* S);
+/* Atomic forces at the state of the last sparc_scf_step (Section 3.6): U are its
+ * rotated orbitals (F64 or F32, Gamma point), with its occupations and electrostatic
+ * potential.  f_host (host, 9*natom doubles): [0, 3 natom) the forces, then the local
+ * (Eq. LocalForce:Discrete) and the nonlocal (Eq. NonlocForce:Discrete, the projector
+ * derivative moved onto nabla_h psi) parts, 3 per atom, Ha/bohr; the overlap
+ * correction f_c is zero (E_c = 0).  Needs sparc_scf_desc.proj_atom when H has
+ * projectors.  Synchronises `stream`. */
+sparc_status sparc_scf_forces(sparc_scf* S, sparc_dtype dtype, const void* U, int ns, int64_t ld, double* f_host,
+                              void* stream);
 
 /* Kernel timing (instrumentation, not part of the method).  While enabled, every
  * launch of the kernels below is bracketed by CUDA events recorded on the

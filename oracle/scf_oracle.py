@@ -243,3 +243,98 @@ def scf_iteration(H: "O.OracleH", U, lam_prev, v0, b, e_self, Ne, kT, m, lanczos
     F, parts = free_energy(lam, g, rho, b, phi, eps, vxc, H.h, e_self, kT)
     return {"a0": a0, "a": a, "b": bb, "lam": lam, "U": Uo, "mu": mu, "g": g, "rho": rho,
             "phi": phi, "eps": eps, "vxc": vxc, "v_out": v_out, "F": F, "parts": parts}
+
+
+def grad_weights(n_o: int, h: float) -> np.ndarray:
+    """Central first-derivative weights w~_p, p = 1..n_o (the gradient formula of
+    Section 3.1): w~_p = (-1)^(p+1) (n_o!)^2 / (h p (n_o-p)! (n_o+p)!)."""
+    fo = math.factorial(n_o)
+    return np.array([0.0] + [(-1) ** (p + 1) * fo * fo / (h * p * math.factorial(n_o - p) * math.factorial(n_o + p))
+                             for p in range(1, n_o + 1)])
+
+
+def grad_h(F: np.ndarray, n, h, n_o: int) -> np.ndarray:
+    """nabla_h F for F of shape (..., n3, n2, n1), periodic (Eq. gradient:approximate).
+    Returns shape (3, ...)."""
+    out = []
+    for s in range(3):
+        ax = F.ndim - 1 - s
+        w = grad_weights(n_o, h[s])
+        g = np.zeros_like(F)
+        for p in range(1, n_o + 1):
+            g = g + w[p] * (np.roll(F, -p, axis=ax) - np.roll(F, p, axis=ax))
+        out.append(g)
+    return np.stack(out)
+
+
+def forces(n, h, n_o, R, Z, rc, phi, proj, U, g, gamma_atoms=None):
+    """Atomic forces at the Gamma point (Section 3.6): f = f_loc + f_c + f_nloc, with
+    f_c = 0 (no overlapping pseudocharges, see the readings).
+
+    f_loc (Eq. LocalForce:Discrete): h1h2h3 sum over the atom's cube nodes of
+      nabla_h b_J (phi - V_J), b_J = -(1/4pi) lap_h V_J evaluated at any node from the
+      analytic V_J (the cube is the pseudocharge cube of the atom, images included).
+    f_nloc (Eq. NonlocForce:Discrete): -4 sum_n g_n sum_lm gamma_Jl Y_Jnlm W_Jnlm with
+      Y = h1h2h3 sum psi chi, W = h1h2h3 sum nabla_h psi chi over the projector box
+      (psi = U / sqrt(h1h2h3), real at the Gamma point).
+    Returns (f [natom, 3], f_loc, f_nloc)."""
+    n = tuple(int(v) for v in n)
+    h = tuple(float(v) for v in h)
+    L = [n[s] * h[s] for s in range(3)]
+    dv = h[0] * h[1] * h[2]
+    wl = [O.fd_weights(n_o, h[s]) for s in range(3)]
+    wg = [grad_weights(n_o, h[s]) for s in range(3)]
+    phi3 = np.asarray(phi, dtype=np.float64).reshape(n[::-1])
+    natom = len(Z)
+    f_loc = np.zeros((natom, 3))
+    for I in range(natom):
+        nb = [int(math.ceil(6.0 * rc[I] / h[s])) for s in range(3)]
+        c = [int(round((R[I][s] + 0.5 * L[s]) / h[s])) for s in range(3)]
+        # V_I on the cube plus a 2 n_o halo; b_I on the cube plus an n_o halo
+        H2 = 2 * n_o
+        lo = [c[s] - nb[s] - H2 for s in range(3)]
+        m = [2 * nb[s] + 1 + 2 * H2 for s in range(3)]
+        xs = [(-0.5 * L[s] + h[s] * (lo[s] + np.arange(m[s]))) - R[I][s] for s in range(3)]
+        X, Y, Zc = np.meshgrid(xs[0], xs[1], xs[2], indexing="ij")
+        V = local_potential(np.sqrt(X * X + Y * Y + Zc * Zc), Z[I], rc[I])    # [i][j][k]
+        mb = [2 * nb[s] + 1 + 2 * n_o for s in range(3)]
+        inner_b = tuple(slice(n_o, n_o + mb[s]) for s in range(3))
+        lap = np.zeros(mb)
+        for s in range(3):
+            acc = 2.0 * wl[s][0] * V[inner_b]
+            for p in range(1, n_o + 1):
+                sp, sm = list(inner_b), list(inner_b)
+                sp[s] = slice(n_o + p, n_o + p + mb[s])
+                sm[s] = slice(n_o - p, n_o - p + mb[s])
+                acc = acc + wl[s][p] * (V[tuple(sp)] + V[tuple(sm)])
+            lap = lap + acc
+        bI = -lap / (4.0 * math.pi)                                             # cube + n_o halo
+        cube = tuple(slice(n_o, n_o + 2 * nb[s] + 1) for s in range(3))
+        ii = [np.mod(c[s] - nb[s] + np.arange(2 * nb[s] + 1), n[s]) for s in range(3)]
+        phic = np.transpose(phi3[np.ix_(ii[2], ii[1], ii[0])], (2, 1, 0))      # [i][j][k]
+        Vc = V[tuple(slice(H2, H2 + 2 * nb[s] + 1) for s in range(3))]
+        for s in range(3):
+            gb = np.zeros([2 * nb[t] + 1 for t in range(3)])
+            for p in range(1, n_o + 1):
+                sp, sm = list(cube), list(cube)
+                sp[s] = slice(n_o + p, n_o + p + 2 * nb[s] + 1)
+                sm[s] = slice(n_o - p, n_o - p + 2 * nb[s] + 1)
+                gb = gb + wg[s][p] * (bI[tuple(sp)] - bI[tuple(sm)])
+            f_loc[I, s] = dv * float(np.sum(gb * (phic - Vc)))
+    # nonlocal
+    f_nl = np.zeros((natom, 3))
+    U3 = np.asarray(U, dtype=np.float64).reshape((-1,) + n[::-1])
+    G = grad_h(U3, n, h, n_o)                                                  # (3, ns, n3, n2, n1)
+    for p in range(proj.nproj):
+        J = int(proj.atom[p])
+        lo = proj.box_lo[p]
+        bn = proj.box_n[p]
+        chi = proj.chi[proj.chi_off[p]: proj.chi_off[p] + int(np.prod(bn))].reshape(bn[2], bn[1], bn[0])
+        idx = [np.mod(lo[s] + np.arange(bn[s]), n[s]) for s in range(3)]
+        Ub = U3[:, idx[2]][:, :, idx[1]][:, :, :, idx[0]]                       # (ns, bz, by, bx)
+        Yp = math.sqrt(dv) * np.einsum("nzyx,zyx->n", Ub, chi)
+        for s in range(3):
+            Gb = G[s][:, idx[2]][:, :, idx[1]][:, :, :, idx[0]]
+            Wp = math.sqrt(dv) * np.einsum("nzyx,zyx->n", Gb, chi)
+            f_nl[J, s] += -4.0 * float(proj.gamma[p]) * float(np.sum(np.asarray(g) * Yp * Wp))
+    return f_loc + f_nl, f_loc, f_nl

@@ -223,10 +223,11 @@ __global__ void __launch_bounds__(256) k_chol_blk(double* A, long long lda, doub
     const double inv = 1.0 / S[j][j];
     for (int i = j + 1 + tid; i < kb; i += nt) S[i][j] *= inv;
     __syncthreads();
-    const int m = kb - j - 1;   // trailing lower triangle, column-major over (i, c), c <= i
-    for (int e = tid; e < m * m; e += nt) {
-      const int i = j + 1 + e % m, c = j + 1 + e / m;
-      if (c <= i) S[i][c] -= S[i][j] * S[c][j];
+    // trailing lower triangle (i, c), j < c <= i: 16 x 16 thread tiles, no index division
+    const int tx = tid & 15, ty = tid >> 4;
+    for (int i = j + 1 + ty; i < kb; i += 16) {
+      const double lij = S[i][j];
+      for (int c = j + 1 + tx; c <= i; c += 16) S[i][c] -= lij * S[c][j];
     }
     __syncthreads();
   }
@@ -237,11 +238,20 @@ __global__ void __launch_bounds__(256) k_chol_blk(double* A, long long lda, doub
   __syncthreads();
   // in-place inverse: for j = kb-1 .. 0, column j below the diagonal becomes
   // -(1/L_jj) Linv[j+1:, j+1:] L[j+1:, j], using the already inverted trailing block
+  __shared__ double part[16][MB];
   for (int j = kb - 1; j >= 0; --j) {
     const double ljj = 1.0 / S[j][j];
+    // x_i = sum_{k=j+1..i} Linv[i][k] L[k][j]: 16 partial sums per row over k, then a fixed-order sum
+    const int tx = tid & 15, ty = tid >> 4;
+    for (int i = j + 1 + ty; i < kb; i += 16) {
+      double s = 0.0;
+      for (int k = j + 1 + tx; k <= i; k += 16) s += S[i][k] * S[k][j];
+      part[tx][i] = s;
+    }
+    __syncthreads();
     for (int i = j + 1 + tid; i < kb; i += nt) {
       double s = 0.0;
-      for (int k = j + 1; k <= i; ++k) s += S[i][k] * S[k][j];
+      for (int q = 0; q < 16; ++q) s += (j + 1 + q <= i) ? part[q][i] : 0.0;
       x[i] = -ljj * s;
     }
     __syncthreads();
@@ -398,15 +408,21 @@ __global__ void k_identity(TW* V, int n) {
   V[t] = from_real<TW>((t % n == t / n) ? 1.0 : 0.0);
 }
 
-// out[0] = sum_{i != j} |A_ij|^2, out[1] = sum |A_ij|^2   (one CTA, fixed order)
+// part[2 b], part[2 b + 1] = sums over column block b of the off-diagonal and all |A_ij|^2
+// (one CTA per 8 columns, fixed order); k_offnorm_sum adds the blocks in order.
 template <class TW>
-__global__ void __launch_bounds__(1024) k_offnorm(const TW* __restrict__ A, int n, double* out) {
-  __shared__ double s0[1024], s1[1024];
+__global__ void __launch_bounds__(256) k_offnorm(const TW* __restrict__ A, int n, double* part) {
+  __shared__ double s0[256], s1[256];
   double off = 0.0, tot = 0.0;
-  for (long long t = threadIdx.x; t < (long long)n * n; t += blockDim.x) {
-    const double v = Tr<TW>::abs2(A[t]);
-    tot += v;
-    if (t % n != t / n) off += v;
+  const int c0 = blockIdx.x * 8;
+  for (int jj = 0; jj < 8; ++jj) {
+    const int j = c0 + jj;
+    if (j >= n) break;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double v = Tr<TW>::abs2(A[i + (long long)j * n]);
+      tot += v;
+      if (i != j) off += v;
+    }
   }
   s0[threadIdx.x] = off;
   s1[threadIdx.x] = tot;
@@ -415,7 +431,15 @@ __global__ void __launch_bounds__(1024) k_offnorm(const TW* __restrict__ A, int 
     if (threadIdx.x < s) { s0[threadIdx.x] += s0[threadIdx.x + s]; s1[threadIdx.x] += s1[threadIdx.x + s]; }
     __syncthreads();
   }
-  if (threadIdx.x == 0) { out[0] = s0[0]; out[1] = s1[0]; }
+  if (threadIdx.x == 0) { part[2 * blockIdx.x] = s0[0]; part[2 * blockIdx.x + 1] = s1[0]; }
+}
+
+__global__ void k_offnorm_sum(const double* part, int nb, double* out) {
+  if (threadIdx.x != 0) return;
+  double a = 0.0, b = 0.0;
+  for (int i = 0; i < nb; ++i) { a += part[2 * i]; b += part[2 * i + 1]; }
+  out[0] = a;
+  out[1] = b;
 }
 
 // Ascending order of the diagonal: eig[rank] = A_ii, Q[:, rank] = V[:, i]
@@ -618,8 +642,10 @@ sparc_status jacobi(sparc_ctx* ctx, TJ* A0, TJ* A1, TJ* V, int n, double tol, in
     SPARC_CUDA(ctx, cudaGraphLaunch(ge, st));
     ctx->launches += rounds;
     sweeps += 2;
-    k_offnorm<TJ><<<1, 1024, 0, st>>>(A0, n, scal);
-    ++ctx->launches;
+    const int nbo = ceil_div(n, 8);
+    k_offnorm<TJ><<<nbo, 256, 0, st>>>(A0, n, scal + 2);
+    k_offnorm_sum<<<1, 32, 0, st>>>(scal + 2, nbo, scal);
+    ctx->launches += 2;
     SPARC_CUDA(ctx, cudaMemcpyAsync(hs, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     SPARC_CUDA(ctx, cudaStreamSynchronize(st));
     // converged, or stagnated at the rounding floor of the element type (Jacobi

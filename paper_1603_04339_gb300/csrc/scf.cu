@@ -483,6 +483,134 @@ __global__ void k_anderson_next(const double* __restrict__ X, const double* __re
   vnext[g] = x + beta * f;
 }
 
+
+// ------------------------------------------------------------------ forces (Section 3.6)
+struct GWeights {
+  double w[3][MAX_FD + 1];   // central first-derivative weights w~_{p,s} (gradient formula)
+};
+
+// lap_h V_I at the point y (relative to the atom), node spacing h
+__device__ double lap_vloc(const double y[3], const double h[3], int no, const Weights& W, double Z, double rc) {
+  double lap = 0.0;
+  const double v0 = vloc(sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]), Z, rc);
+  for (int s = 0; s < 3; ++s) {
+    double acc = 2.0 * W.w[s][0] * v0;
+    for (int p = 1; p <= no; ++p) {
+      double a[3] = {y[0], y[1], y[2]};
+      a[s] = y[s] + p * h[s];
+      const double vp = vloc(sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]), Z, rc);
+      a[s] = y[s] - p * h[s];
+      const double vm = vloc(sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]), Z, rc);
+      acc += W.w[s][p] * (vp + vm);
+    }
+    lap += acc;
+  }
+  return lap;
+}
+
+// Local force (Eq. LocalForce:Discrete): h1h2h3 sum over the atom's cube nodes of
+// nabla_h b_I (phi - V_I), b_I = -(1/4pi) lap_h V_I evaluated at any node.
+// Grid: (atom, blocks over the cube); part[(atom * gridDim.y + block) * 3 + s].
+__global__ void __launch_bounds__(TPB) k_force_local(int n1, int n2, int n3, double h1, double h2, double h3, int no,
+                                                     Weights W, GWeights G, const Atom* __restrict__ atoms,
+                                                     const double* __restrict__ phi, double* part) {
+  __shared__ double sh[32];
+  const Atom A = atoms[blockIdx.x];
+  const int m0 = 2 * A.nb[0] + 1, m1 = 2 * A.nb[1] + 1, m2 = 2 * A.nb[2] + 1;
+  const long long ncube = (long long)m0 * m1 * m2;
+  const long long e = (long long)blockIdx.y * blockDim.x + threadIdx.x;
+  const int n[3] = {n1, n2, n3};
+  const double h[3] = {h1, h2, h3};
+  double f[3] = {0.0, 0.0, 0.0};
+  if (e < ncube) {
+    const int u[3] = {A.c[0] - A.nb[0] + (int)(e % m0), A.c[1] - A.nb[1] + (int)((e / m0) % m1),
+                      A.c[2] - A.nb[2] + (int)(e / ((long long)m0 * m1))};
+    double x[3];
+    int gi[3];
+    for (int s = 0; s < 3; ++s) {
+      x[s] = -0.5 * n[s] * h[s] + (double)u[s] * h[s] - A.R[s];
+      gi[s] = (int)(((long long)u[s] % n[s] + n[s]) % n[s]);
+    }
+    const double pv = phi[((long long)gi[2] * n2 + gi[1]) * n1 + gi[0]] -
+                      vloc(sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]), A.Z, A.rc);
+    for (int s = 0; s < 3; ++s) {
+      double gb = 0.0;
+      for (int p = 1; p <= no; ++p) {
+        double y[3] = {x[0], x[1], x[2]};
+        y[s] = x[s] + p * h[s];
+        const double lp = lap_vloc(y, h, no, W, A.Z, A.rc);
+        y[s] = x[s] - p * h[s];
+        const double lm = lap_vloc(y, h, no, W, A.Z, A.rc);
+        gb += G.w[s][p] * (lp - lm);
+      }
+      f[s] = h1 * h2 * h3 * (-gb / (4.0 * M_PI)) * pv;
+    }
+  }
+  for (int s = 0; s < 3; ++s) {
+    const double t = block_sum(f[s], sh);
+    if (threadIdx.x == 0) part[((long long)blockIdx.x * gridDim.y + blockIdx.y) * 3 + s] = t;
+  }
+}
+
+// Nonlocal projections for the force: for projector p = blockIdx.x and orbital
+// n = blockIdx.y, out[(p * ns + n) * 4 + {0, 1, 2, 3}] = sum over the box of chi U and of
+// chi nabla_h U (Y and W without the h1h2h3 and normalisation factors).
+template <class T>
+__global__ void __launch_bounds__(TPB) k_force_proj(const T* __restrict__ U, long long ld, int n1, int n2, int n3, int no,
+                                                    GWeights G, const long long* __restrict__ p_off,
+                                                    const int* __restrict__ p_g, const double* __restrict__ p_val,
+                                                    int ns, double* out) {
+  __shared__ double sh[32];
+  const int p = blockIdx.x, nn = blockIdx.y;
+  const T* u = U + (long long)nn * ld;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (long long e = p_off[p] + threadIdx.x; e < p_off[p + 1]; e += blockDim.x) {
+    const int g = p_g[e];
+    const double c = p_val[e];
+    const int i = g % n1, j = (g / n1) % n2, k = g / (n1 * n2);
+    acc[0] += c * (double)u[g];
+    double gr[3] = {0.0, 0.0, 0.0};
+    for (int q = 1; q <= no; ++q) {
+      int ip = i + q; if (ip >= n1) ip -= n1;
+      int im = i - q; if (im < 0) im += n1;
+      int jp = j + q; if (jp >= n2) jp -= n2;
+      int jm = j - q; if (jm < 0) jm += n2;
+      int kp = k + q; if (kp >= n3) kp -= n3;
+      int km = k - q; if (km < 0) km += n3;
+      const long long row = ((long long)k * n2 + j) * n1;
+      gr[0] += G.w[0][q] * ((double)u[row + ip] - (double)u[row + im]);
+      gr[1] += G.w[1][q] * ((double)u[((long long)k * n2 + jp) * n1 + i] - (double)u[((long long)k * n2 + jm) * n1 + i]);
+      gr[2] += G.w[2][q] * ((double)u[((long long)kp * n2 + j) * n1 + i] - (double)u[((long long)km * n2 + j) * n1 + i]);
+    }
+    for (int s = 0; s < 3; ++s) acc[1 + s] += c * gr[s];
+  }
+  for (int q = 0; q < 4; ++q) {
+    const double t = block_sum(acc[q], sh);
+    if (threadIdx.x == 0) out[((long long)p * ns + nn) * 4 + q] = t;
+  }
+}
+
+// f[atom] = local partials (fixed order) - 4 h1h2h3 sum_{p of atom} gamma_p sum_n g_n Y W
+// (Eq. NonlocForce:Discrete; psi = U / sqrt(h1h2h3), so Y W = h1h2h3 (sum chi U)(sum chi grad U))
+__global__ void k_force_sum(const double* __restrict__ loc, int nby, const double* __restrict__ prj,
+                            const int* __restrict__ patom, const double* __restrict__ gamma, int nproj, int ns,
+                            const double* __restrict__ occ, double dv, int natom, double* f) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= natom) return;
+  for (int s = 0; s < 3; ++s) {
+    double fl = 0.0;
+    for (int b = 0; b < nby; ++b) fl += loc[((long long)I * nby + b) * 3 + s];
+    double fn = 0.0;
+    for (int p = 0; p < nproj; ++p) {
+      if (patom[p] != I) continue;
+      double t = 0.0;
+      for (int n = 0; n < ns; ++n) t += occ[n] * prj[((long long)p * ns + n) * 4] * prj[((long long)p * ns + n) * 4 + 1 + s];
+      fn += -4.0 * gamma[p] * dv * t;
+    }
+    f[3 * I + s] = fl;
+    f[3 * (natom + I) + s] = fn;
+  }
+}
 }  // namespace scf
 }  // namespace sparc
 
@@ -503,6 +631,9 @@ struct sparc_scf {
   void* d_Y = nullptr;
   size_t ybytes = 0;
   std::vector<double> lam_prev;
+  int nproj = 0;
+  int* d_patom = nullptr;          // atom of each projector (forces); null if not given
+  int last_ns = 0;                 // orbitals of the last iteration (occupations in d_occ)
 };
 
 namespace sparc {
@@ -511,7 +642,7 @@ namespace scf {
 static void free_scf(sparc_scf* S) {
   void* ps[] = {S->d_atoms, S->d_b, S->d_rho, S->d_phi, S->d_eps, S->d_vxc, S->d_vout, S->d_fres,
                 S->d_vnext, S->d_r, S->d_p, S->d_ap, S->d_X, S->d_F, S->d_part, S->d_sums,
-                S->d_scal, S->d_occ, S->d_v0, S->d_Y};
+                S->d_scal, S->d_occ, S->d_v0, S->d_Y, S->d_patom};
   for (void* p : ps)
     if (p) cudaFree(p);
 }
@@ -627,6 +758,17 @@ extern "C" sparc_status sparc_scf_create(sparc_ham* H, const sparc_scf_desc* d, 
   cudaStream_t st = 0;
   SPARC_CUDA(ctx, cudaMemcpy(S->d_atoms, S->atoms.data(), S->atoms.size() * sizeof(Atom), cudaMemcpyHostToDevice));
   SPARC_CUDA(ctx, cudaMemcpy(S->d_v0, d->v0, v0b, cudaMemcpyHostToDevice));
+  S->nproj = H->nproj;
+  if (d->proj_atom && H->nproj > 0) {
+    for (int p = 0; p < H->nproj; ++p)
+      if (d->proj_atom[p] < 0 || d->proj_atom[p] >= d->natom) {
+        free_scf(S);
+        delete S;
+        return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_scf_create: proj_atom out of range");
+      }
+    SPARC_CUDA(ctx, cudaMalloc(&S->d_patom, H->nproj * sizeof(int)));
+    SPARC_CUDA(ctx, cudaMemcpy(S->d_patom, d->proj_atom, H->nproj * sizeof(int), cudaMemcpyHostToDevice));
+  }
   SPARC_CUDA(ctx, cudaMemset(S->d_phi, 0, vb));
   SPARC_CUDA(ctx, cudaMemset(S->d_scal, 0, S_COUNT * sizeof(double)));
   // pseudocharges and self energy
@@ -775,9 +917,81 @@ extern "C" sparc_status sparc_scf_step(sparc_scf* S, sparc_dtype dtype, int m, v
   info->nelec = hs[S_NEL];
   info->vresid = sqrt(hs[S_RES2] / std::max(hs[S_VOUT2], 1e-300));
   info->poisson_iters = piters;
+  S->last_ns = ns;
   info->a0 = a0;
   info->a = a;
   info->b = b;
   ++S->iter;
+  return SPARC_OK;
+}
+
+extern "C" sparc_status sparc_scf_forces(sparc_scf* S, sparc_dtype dtype, const void* U, int ns, int64_t ld,
+                                         double* f_host, void* stream) {
+  if (!S || !U || !f_host) return SPARC_ERR_INVALID_ARG;
+  sparc_ham* H = S->H;
+  sparc_ctx* ctx = H->ctx;
+  const long long nd = H->gd.nd;
+  if (S->last_ns != ns || ns < 1 || ld < nd)
+    return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_scf_forces: needs the orbitals of the last sparc_scf_step");
+  if (dtype != SPARC_F64 && dtype != SPARC_F32)
+    return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_scf_forces: real orbitals (Gamma point) only");
+  if (H->nproj > 0 && !S->d_patom)
+    return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_scf_forces: sparc_scf_desc.proj_atom was not given");
+  SPARC_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int natom = (int)S->atoms.size();
+  GWeights G{};
+  for (int s2 = 0; s2 < 3; ++s2) {
+    const int no = H->gd.no;
+    double fo = 1.0;
+    for (int q = 2; q <= no; ++q) fo *= q;
+    for (int p = 0; p <= MAX_FD; ++p) {
+      if (p == 0 || p > no) { G.w[s2][p] = 0.0; continue; }
+      double den = 1.0;
+      for (int q = 2; q <= no - p; ++q) den *= q;
+      for (int q = 2; q <= no + p; ++q) den *= q;
+      G.w[s2][p] = ((p % 2) ? 1.0 : -1.0) * fo * fo / (H->grid.h[s2] * p * den);
+    }
+  }
+  int maxcube = 1;
+  for (const Atom& A : S->atoms) maxcube = std::max(maxcube, (2 * A.nb[0] + 1) * (2 * A.nb[1] + 1) * (2 * A.nb[2] + 1));
+  const int nby = ceil_div(maxcube, TPB);
+  double *d_loc = nullptr, *d_prj = nullptr, *d_f = nullptr;
+  const int np = H->nproj;
+  SPARC_CUDA(ctx, cudaMalloc(&d_loc, (size_t)natom * nby * 3 * sizeof(double)));
+  SPARC_CUDA(ctx, cudaMalloc(&d_prj, (size_t)std::max(np, 1) * ns * 4 * sizeof(double)));
+  SPARC_CUDA(ctx, cudaMalloc(&d_f, (size_t)natom * 6 * sizeof(double)));
+  k_force_local<<<dim3(natom, nby), TPB, 0, st>>>(H->gd.n1, H->gd.n2, H->gd.n3, H->grid.h[0], H->grid.h[1],
+                                                   H->grid.h[2], H->gd.no, S->W, G, S->d_atoms, S->d_phi, d_loc);
+  ++ctx->launches;
+  if (np > 0) {
+    sparc_status rc = ensure_vals(H, SPARC_F64);
+    if (rc != SPARC_OK) return rc;
+    if (dtype == SPARC_F64)
+      k_force_proj<double><<<dim3(np, ns), TPB, 0, st>>>((const double*)U, ld, H->gd.n1, H->gd.n2, H->gd.n3, H->gd.no,
+                                                          G, H->d_p_off, H->d_p_g, (const double*)H->d_p_val[SPARC_F64],
+                                                          ns, d_prj);
+    else
+      k_force_proj<float><<<dim3(np, ns), TPB, 0, st>>>((const float*)U, ld, H->gd.n1, H->gd.n2, H->gd.n3, H->gd.no,
+                                                         G, H->d_p_off, H->d_p_g, (const double*)H->d_p_val[SPARC_F64],
+                                                         ns, d_prj);
+    ++ctx->launches;
+  }
+  const double dv = H->grid.h[0] * H->grid.h[1] * H->grid.h[2];
+  k_force_sum<<<ceil_div(natom, 64), 64, 0, st>>>(d_loc, nby, d_prj, S->d_patom, H->d_gamma, np, ns, S->d_occ, dv,
+                                                   natom, d_f);
+  ++ctx->launches;
+  SPARC_LAUNCH(ctx, "forces");
+  std::vector<double> hf((size_t)natom * 6);
+  SPARC_CUDA(ctx, cudaMemcpyAsync(hf.data(), d_f, hf.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  SPARC_CUDA(ctx, cudaStreamSynchronize(st));
+  cudaFree(d_loc);
+  cudaFree(d_prj);
+  cudaFree(d_f);
+  for (int i = 0; i < 3 * natom; ++i) {
+    f_host[i] = hf[i] + hf[3 * natom + i];           // total
+    f_host[3 * natom + i] = hf[i];                   // local part
+    f_host[6 * natom + i] = hf[3 * natom + i];       // nonlocal part
+  }
   return SPARC_OK;
 }

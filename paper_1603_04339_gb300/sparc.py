@@ -25,7 +25,8 @@ EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_sync", "s
            "sparc_ham_set_veff", "sparc_ham_destroy", "sparc_apply_H", "sparc_cheb_filter",
            "sparc_lanczos_bounds", "sparc_rayleigh_ritz", "sparc_timing_enable", "sparc_timing_read",
            "sparc_launch_count", "sparc_apply_H_noalloc", "sparc_last_sweeps", "sparc_gram_f32",
-           "sparc_rotate_f32", "sparc_scf_create", "sparc_scf_step", "sparc_scf_read", "sparc_scf_destroy"]
+           "sparc_rotate_f32", "sparc_scf_create", "sparc_scf_step", "sparc_scf_read", "sparc_scf_destroy",
+           "sparc_scf_forces"]
 TIMED = {"hpass": 0, "gather": 1, "gram": 2, "eig": 3, "rotation": 4, "jacobi": 5, "fpass": 6}
 
 
@@ -42,7 +43,7 @@ class SparcNonlocal(ctypes.Structure):
 class SparcScfDesc(ctypes.Structure):
     _fields_ = [("natom", c_int), ("R", POINTER(c_double)), ("Z", POINTER(c_double)), ("rc", POINTER(c_double)),
                 ("kT", c_double), ("mix_beta", c_double), ("mix_history", c_int), ("poisson_tol", c_double),
-                ("v0", POINTER(c_double))]
+                ("v0", POINTER(c_double)), ("proj_atom", POINTER(c_int32))]
 
 
 class SparcScfInfo(ctypes.Structure):
@@ -107,11 +108,13 @@ def load(path: str = LIB_PATH):
     L.sparc_scf_step.argtypes = [c_void_p, c_int, c_int, c_void_p, c_int, c_int64, c_void_p,
                                  POINTER(SparcScfInfo), c_void_p]
     L.sparc_scf_read.argtypes = [c_void_p, c_int, c_void_p, c_void_p]
+    L.sparc_scf_forces.argtypes = [c_void_p, c_int, c_void_p, c_int, c_int64, POINTER(c_double), c_void_p]
     L.sparc_scf_destroy.argtypes = [c_void_p]
     L.sparc_scf_destroy.restype = None
     for name in ("sparc_timing_enable", "sparc_timing_read", "sparc_create", "sparc_sync", "sparc_ham_create", "sparc_ham_set_veff",
                  "sparc_apply_H", "sparc_cheb_filter", "sparc_lanczos_bounds", "sparc_rayleigh_ritz",
-                 "sparc_gram_f32", "sparc_rotate_f32", "sparc_scf_create", "sparc_scf_step", "sparc_scf_read"):
+                 "sparc_gram_f32", "sparc_rotate_f32", "sparc_scf_create", "sparc_scf_step", "sparc_scf_read",
+                 "sparc_scf_forces"):
         getattr(L, name).restype = c_int
     _lib = L
     return L
@@ -347,7 +350,8 @@ class Scf:
 
     FIELDS = {"b": 0, "rho": 1, "phi": 2, "vxc": 3, "vout": 4, "veff": 5}
 
-    def __init__(self, H: Hamiltonian, R, Z, rc, v0, kT=0.01, mix_beta=0.3, mix_history=7, poisson_tol=1e-10):
+    def __init__(self, H: Hamiltonian, R, Z, rc, v0, kT=0.01, mix_beta=0.3, mix_history=7, poisson_tol=1e-10,
+                 proj_atom=None):
         self.H = H
         self._R = np.ascontiguousarray(R, dtype=np.float64).reshape(-1)
         self._Z = np.ascontiguousarray(Z, dtype=np.float64)
@@ -366,6 +370,8 @@ class Scf:
         d.mix_history = int(mix_history)
         d.poisson_tol = float(poisson_tol)
         d.v0 = self._v0.ctypes.data_as(POINTER(c_double))
+        self._pa = None if proj_atom is None else np.ascontiguousarray(proj_atom, dtype=np.int32)
+        d.proj_atom = None if self._pa is None else self._pa.ctypes.data_as(POINTER(c_int32))
         h = c_void_p()
         H.ctx.check(load().sparc_scf_create(H.handle, ctypes.byref(d), ctypes.byref(h)))
         self.handle = h
@@ -373,7 +379,18 @@ class Scf:
 
     @classmethod
     def from_system(cls, H: Hamiltonian, sysd, **kw):
-        return cls(H, sysd.wl.atoms, sysd.Z, sysd.rc, sysd.v0, **kw)
+        return cls(H, sysd.wl.atoms, sysd.Z, sysd.rc, sysd.v0, proj_atom=sysd.wl.proj.atom, **kw)
+
+    def forces(self, U, ns=None, ld=None, stream=None, dtype=None):
+        """(f, f_loc, f_nloc), each (natom, 3), at the state of the last step (sparc_scf_forces)."""
+        ns = U.shape[0] if ns is None else ns
+        ld = U.shape[-1] if ld is None else ld
+        dt = dtype_code(U) if dtype is None else dtype
+        na = int(self._Z.size)
+        out = np.zeros(9 * na)
+        self.H.ctx.check(load().sparc_scf_forces(self.handle, dt, _ptr(U), int(ns), int(ld),
+                                                 out.ctypes.data_as(POINTER(c_double)), _stream(stream)))
+        return out[:3 * na].reshape(na, 3), out[3 * na:6 * na].reshape(na, 3), out[6 * na:].reshape(na, 3)
 
     def read(self, name: str, out, stream=None):
         """Copy a grid field (b, rho, phi, vxc, vout, veff) into the float64 CUDA tensor `out`."""

@@ -31,7 +31,7 @@ import numpy as np
 __all__ = [
     "Workload", "Projectors", "make_projectors", "gaussian_veff", "fcc_sites",
     "diamond_sites", "monkhorst_pack", "config1", "config2", "config3",
-    "small_case", "random_orbitals", "lanczos_start", "ScfSystem", "scf_small", "scf_fcc32",
+    "small_case", "random_orbitals", "lanczos_start", "ScfSystem", "scf_small", "scf_fcc32", "scf_pair",
 ]
 
 
@@ -331,3 +331,15 @@ def scf_fcc32(seed=1005, a=8.1, h=0.45, sigma=0.05, Z=3.0, rc_loc=0.8, rc_proj=1
                   seed)
     return ScfSystem(wl, np.full(len(sites), Z), np.full(len(sites), rc_loc), lanczos_start(nd, seed + 1),
                      random_orbitals(nd, ns, seed + 2))
+
+
+def scf_pair(R=None, n=(18, 18, 18), h=(0.5, 0.5, 0.5)) -> ScfSystem:
+    """Two atoms (Z = 1, local width 0.7 bohr, s+p projectors of width 0.9 bohr) in an
+    18^3 cell, 8 orbitals, m = 12: the force checks."""
+    if R is None:
+        R = np.array([[-1.13, 0.37, 0.21], [1.41, -0.29, -0.52]])
+    R = np.asarray(R, dtype=np.float64)
+    proj = make_projectors(n, h, R, 0.9, np.array([0.25, -0.2]), np.array([0.15, 0.3]))
+    nd = n[0] * n[1] * n[2]
+    wl = Workload("pair_18", tuple(n), tuple(h), 6, np.zeros((1, 3)), np.ones(1), np.zeros(nd), R, proj, 8, 12, 5)
+    return ScfSystem(wl, np.array([1.0, 1.0]), np.array([0.7, 0.7]), lanczos_start(nd, 6), random_orbitals(nd, 8, 5))

@@ -131,3 +131,49 @@ def test_scf_rejects_bad_arguments(ctx):
     eig = torch.zeros(1, dtype=torch.float64, device="cuda")
     with pytest.raises(sparc.SparcError):
         sparc.sparc_scf_step(S, U, eig, 6)
+
+
+def _converge_gpu(ctx, sysd, dtype, iters=60, tol=1e-11):
+    from paper_1603_04339_gb300 import sparc
+    wl = sysd.wl
+    H = sparc.Hamiltonian.from_workload(ctx, wl)
+    S = sparc.Scf.from_system(H, sysd, kT=KT, mix_beta=BETA, mix_history=HIST, poisson_tol=1e-13)
+    U = torch.from_numpy(sysd.U0.copy()).to(dtype).cuda()
+    eig = torch.zeros(wl.ns, dtype=torch.float64, device="cuda")
+    for it in range(iters):
+        info = sparc.sparc_scf_step(S, U, eig, wl.m)
+        if info["vresid"] < tol:
+            break
+    return S, U, info
+
+
+def test_forces_match_the_oracle_and_mixed_within_target(ctx):
+    """Forces (Section 3.6) at the converged FP64 state against the oracle's forces at
+    its own converged state (both to V residual 1e-11), and the mixed path's forces
+    within the 1e-4 Ha/bohr target."""
+    sysd = synth.scf_pair()
+    wl = sysd.wl
+    S, U, info = _converge_gpu(ctx, sysd, torch.float64)
+    assert info["vresid"] < 1e-11
+    f, fl, fn = S.forces(U)
+    # oracle
+    b, e_self, _ = SO.pseudocharge(wl.n, wl.h, 6, wl.atoms, sysd.Z, sysd.rc)
+    v_in = SO.lda(-b)[1]
+    Uo, lam_prev, xh, fh = sysd.U0.copy(), None, [], []
+    for it in range(80):
+        Hor = O.OracleH(wl, veff=v_in)
+        out = SO.scf_iteration(Hor, Uo, lam_prev, sysd.v0, b, e_self, sysd.nelec, KT, wl.m)
+        if np.linalg.norm(out["v_out"] - v_in) < 1e-11 * np.linalg.norm(out["v_out"]):
+            break
+        xh.append(v_in)
+        fh.append(out["v_out"] - v_in)
+        v_in = SO.anderson(xh, fh, BETA, HIST)
+        Uo, lam_prev = out["U"], out["lam"]
+    fo, flo, fno = SO.forces(wl.n, wl.h, 6, wl.atoms, sysd.Z, sysd.rc, out["phi"], wl.proj, out["U"], out["g"])
+    print("GPU forces", f.tolist(), "oracle", fo.tolist())
+    assert np.max(np.abs(fl - flo)) < 1e-8
+    assert np.max(np.abs(fn - fno)) < 1e-8
+    S32, U32, info32 = _converge_gpu(ctx, sysd, torch.float32, tol=1e-6)
+    f32, _, _ = S32.forces(U32)
+    print("mixed forces", f32.tolist(), "max |df|", float(np.max(np.abs(f32 - f))))
+    assert np.max(np.abs(f32 - f)) < 1e-4

@@ -158,3 +158,53 @@ def test_jellium_is_a_fixed_point_with_closed_form_energy():
     assert np.all(g[7:] < 1e-100)
     F_ref = 2 * np.sum(g[:7] * lam_ref) + vol * (eps0[0] - v0[0]) * rho0 + S.entropy_term(g, kT)
     assert abs(out["F"] - F_ref) < 1e-9 * abs(F_ref)
+
+
+def test_gradient_weights_textbook():
+    assert np.allclose(S.grad_weights(1, 1.0)[1:], [0.5])
+    assert np.allclose(S.grad_weights(2, 1.0)[1:], [2.0 / 3.0, -1.0 / 12.0])
+    x = np.linspace(0, 2 * math.pi, 24, endpoint=False)
+    f = np.sin(3 * x)
+    F = np.broadcast_to(f, (4, 5, 24)).copy()
+    g = S.grad_h(F, (24, 5, 4), (2 * math.pi / 24, 1.0, 1.0), 6)
+    assert np.allclose(g[0][0, 0], 3 * np.cos(3 * x), atol=2e-4)   # 12th-order error at 8 nodes/period
+    assert np.max(np.abs(g[1])) < 1e-13 and np.max(np.abs(g[2])) < 1e-13
+
+
+def test_forces_match_finite_differences_of_the_free_energy():
+    """The analytic forces (local + nonlocal, Section 3.6) at the converged SCF state
+    against -dF/dR by central differences of the converged free energy (the check the
+    paper makes), for one atom of a two-atom cell, and Newton's third law."""
+    from paper_1603_04339_gb300 import synth
+    base = synth.scf_pair()
+    n, h = base.wl.n, base.wl.h
+    Z, rc = base.Z, base.rc
+    R0 = base.wl.atoms
+    U0, v0 = base.U0, base.v0
+
+    def converged(R):
+        proj = synth.scf_pair(R).wl.proj
+        b, e_self, _ = S.pseudocharge(n, h, 6, R, Z, rc)
+        v_in = S.lda(-b)[1]
+        U, lam_prev, xh, fh = U0.copy(), None, [], []
+        for it in range(80):
+            H = O.OracleH(n=n, h=h, fd_radius=6, k=(0, 0, 0), veff=v_in, proj=proj)
+            out = S.scf_iteration(H, U, lam_prev, v0, b, e_self, 2.0, 0.01, 12)
+            if np.linalg.norm(out["v_out"] - v_in) < 1e-11 * np.linalg.norm(out["v_out"]):
+                return out, proj
+            xh.append(v_in)
+            fh.append(out["v_out"] - v_in)
+            v_in = S.anderson(xh, fh, 0.3, 7)
+            U, lam_prev = out["U"], out["lam"]
+        raise AssertionError("SCF did not converge")
+
+    out, proj = converged(R0)
+    f, _, _ = S.forces(n, h, 6, R0, Z, rc, out["phi"], proj, out["U"], out["g"])
+    assert np.max(np.abs(f[0] + f[1])) < 1e-5            # no net force on an isolated pair
+    d = 0.005
+    for s in range(3):
+        Rp, Rm = R0.copy(), R0.copy()
+        Rp[0, s] += d
+        Rm[0, s] -= d
+        fd = -(converged(Rp)[0]["F"] - converged(Rm)[0]["F"]) / (2 * d)
+        assert abs(fd - f[0, s]) < 5e-5, (s, fd, f[0, s])
