@@ -41,9 +41,12 @@ def _args():
     ap.add_argument("--e2e-steps", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-scf", action="store_true", help="skip the SCF time-to-solution comparison")
+    ap.add_argument("--no-kpoints", action="store_true",
+                    help="skip the 27-k-point complex64 filter throughput (batched and per k)")
     ap.add_argument("--cpu-sample-cols", type=int, default=1)
-    ap.add_argument("--mode", choices=["step", "filter"], default="step",
-                    help="filter: only the Chebyshev filter (for profiler captures)")
+    ap.add_argument("--mode", choices=["step", "filter", "kpoints"], default="step",
+                    help="filter: only the Chebyshev filter (for profiler captures); "
+                         "kpoints: the 27-k-point complex64 filter alone")
     ap.add_argument("--ns", type=int, default=None, help="orbitals (filter mode; default: the cell's 512)")
     return ap.parse_args()
 
@@ -174,6 +177,73 @@ def job_rate(ms_local, units_per_rank, world, dist=None, device="cpu"):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     return ms, world * units_per_rank / (ms * 1e-3) / 1e9
+
+
+def kpoint_filter_throughput(sparc, synth, torch, ctx, reps=2, tune=True):
+    """Complex64 filter of the 40^3 Si-like cell over all 27 Monkhorst-Pack k-points
+    (Ns=192, m=20): batched (sparc_cheb_filter_batch, launches shared by k-points,
+    grouping autotuned) against one sparc_cheb_filter call per k, both timed with
+    CUDA events after a warm-up run.  Inputs (2.65 GB per block set) exceed L2."""
+    import numpy as np
+    wl = synth.config3()
+    nk = len(wl.kpts)
+    Hs = [sparc.Hamiltonian.from_workload(ctx, wl, k) for k in range(nk)]
+    X = torch.empty((nk, wl.ns, wl.nd), dtype=torch.complex64, device="cuda")
+    for k in range(nk):
+        X[k] = torch.from_numpy(synth.random_orbitals(wl.nd, wl.ns, 4000 + k, complex_=True).astype(np.complex64))
+    Y = torch.empty_like(X)
+    a0 = [-2.5] * nk
+    b = [80.0] * nk
+    a = [a0[k] + (b[k] - a0[k]) * (wl.ns / wl.nd) ** (2.0 / 3.0) for k in range(nk)]
+    units = 0
+    if tune:
+        units, _ = sparc.sparc_autotune_filter(Hs, wl.m, a, b, a0, X, Y)
+    work = nk * wl.nd * wl.ns * wl.m
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0 = ctx.launches()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, (ctx.launches() - n0) // reps
+
+    def batched():
+        sparc.sparc_cheb_filter_batch(Hs, wl.m, a, b, a0, X, Y)
+
+    def per_k():
+        for k in range(nk):
+            sparc.sparc_cheb_filter(Hs[k], wl.m, a[k], b[k], a0[k], X[k], Y[k])
+
+    ms_b, l_b = timed(batched)
+    ms_k, l_k = timed(per_k)
+    for H in Hs:
+        H.close()
+    del X, Y
+    torch.cuda.empty_cache()
+    return {"workload": "40^3 Si-like cell, 64 s+p atoms, 3x3x3 MP k-points (27), Ns=192, m=20, complex64",
+            "batched": {"value": work / (ms_b * 1e-3) / 1e9, "unit": "Gpt-orb-deg/s", "ms_per_filter": ms_b,
+                        "launches_per_filter": l_b, "units_per_launch": units or None},
+            "per_k": {"value": work / (ms_k * 1e-3) / 1e9, "unit": "Gpt-orb-deg/s", "ms_per_filter": ms_k,
+                      "launches_per_filter": l_k},
+            "hbm_roof": {"gpt_orb_deg_per_s": _peaks()[0] / 24.0, "bytes_per_unit": 24,
+                         "frac_batched": work / (ms_b * 1e-3) / 1e9 / (_peaks()[0] / 24.0)}}
+
+
+def run_kpoints(args):
+    import json as _json
+    import torch
+    from paper_1603_04339_gb300 import build, synth
+    build.build()
+    from paper_1603_04339_gb300 import sparc
+    ctx = sparc.Context(0)
+    out = kpoint_filter_throughput(sparc, synth, torch, ctx, reps=max(1, args.steps))
+    print(_json.dumps({"mode": "kpoints", **out}), flush=True)
+    return 0
 
 
 def scf_time_to_solution(sparc, synth, torch, tol_per_atom=1e-5, max_iter=60):
@@ -400,6 +470,7 @@ def run_ours(args):
         "filter_only": {"value": units / ((fp_ms + ga_ms) / args.steps * 1e-3) / 1e9, "unit": UNIT},
         "clocks": ck, "e2e": e2e, "gpu_launches": int(launches), "cpu_baseline": cpu,
         "scf": None if (args.no_scf or world > 1) else scf_time_to_solution(sparc, synth, torch),
+        "kpoints": None if (args.no_kpoints or world > 1) else kpoint_filter_throughput(sparc, synth, torch, ctx),
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -448,6 +519,8 @@ def main():
         return run_reference(args)
     if args.mode == "filter":
         return run_filter_only(args)
+    if args.mode == "kpoints":
+        return run_kpoints(args)
     return run_ours(args)
 
 

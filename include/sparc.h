@@ -150,6 +150,46 @@ sparc_status sparc_cheb_filter(sparc_ham* H, sparc_dtype dtype, int m, double a,
                                double a0, const void* X, void* Y, int ns, int64_t ld,
                                void* stream);
 
+/* The filter of sparc_cheb_filter for nk Hamiltonians that differ only in the
+ * Bloch wavevector k (the k-point sum of the density, Section 2 and Section 4:
+ * one filter per k-point), run as one sequence of launches: with SPARC_C64 each
+ * launch of the H-pass and of the projection covers the blocks of up to 32
+ * k-points at once.
+ *   H[nk]: Hamiltonians on one context with equal grids (n, h, fd_radius) and
+ *          projector boxes (otherwise SPARC_ERR_INVALID_ARG); V_eff, projector
+ *          values and k are taken per k.  nk >= 1.
+ *   a[nk], b[nk], a0[nk]: host arrays, the bounds of each k (a0 < a < b).
+ *   X, Y: device, nk consecutive column-major Nd x ns blocks of leading
+ *         dimension ld (block k starts at element k * ns * ld); X is not
+ *         modified; X and Y may not overlap.
+ * Result: block k equals sparc_cheb_filter(H[k], dtype, m, a[k], b[k], a0[k],
+ * ...) bit for bit.  Other dtypes, and Hamiltonians outside the tiled kernel's
+ * range (fd_radius != 6), run one sparc_cheb_filter per k. */
+sparc_status sparc_cheb_filter_batch(sparc_ham* const* H, int nk, sparc_dtype dtype, int m,
+                                     const double* a, const double* b, const double* a0,
+                                     const void* X, void* Y, int ns, int64_t ld, void* stream);
+
+/* Launch-shape autotuner of the filter.  Times sparc_cheb_filter_batch (degree
+ * min(m, 3), arguments as there) for several numbers of orbital blocks (8
+ * orbitals each) per launch -- fractions and multiples of the number whose two
+ * live buffers fit in L2, all blocks of one k, all blocks of all k -- keeps the
+ * fastest in the context and returns it in *units (0 if the dtype has a single
+ * launch shape) with its time in *ms.  Later filter calls on this context with
+ * the same dtype, Nd, ns and nk use it (nk = 1 for sparc_cheb_filter).  Tuned:
+ * SPARC_F32 with nk = 1 and SPARC_C64 with nk > 1.  Synchronises `stream`;
+ * overwrites Y.  Make it before capturing filter calls into a CUDA graph. */
+sparc_status sparc_autotune_filter(sparc_ham* const* H, int nk, sparc_dtype dtype, int m,
+                                   const double* a, const double* b, const double* a0,
+                                   const void* X, void* Y, int ns, int64_t ld, void* stream,
+                                   int* units, double* ms);
+
+/* Set (units > 0) or clear (units = 0) the number of orbital blocks per filter
+ * launch that later filter calls on this context use for (dtype, Nd, ns, nk),
+ * e.g. a value that sparc_autotune_filter chose in an earlier process.  With
+ * nothing set the filter takes the grouping of its cost model. */
+sparc_status sparc_set_filter_units(sparc_ctx* ctx, sparc_dtype dtype, int64_t nd, int ns, int nk,
+                                    int units);
+
 /* Extremal-eigenvalue estimates by `ksteps` Lanczos steps with full
  * reorthogonalisation, in FP64 (Section 4: filter bounds by the Lanczos method).
  * v0: device start vector, Nd elements of F64 (k = 0) or C128 (k != 0); it is

@@ -177,6 +177,9 @@ struct sparc_ctx {
   cudaStream_t cap_stream = nullptr;
   std::map<std::tuple<int, int, void*, void*, void*>, cudaGraphExec_t> graphs;
   int last_sweeps = 0;
+  // units (blocks of NB orbitals) per filter launch chosen by sparc_autotune_filter,
+  // keyed by (dtype, Nd, ns, number of k-points)
+  std::map<std::tuple<int, long long, int, int>, int> tuned;
 };
 
 namespace sparc {

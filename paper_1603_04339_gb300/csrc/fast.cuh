@@ -55,7 +55,32 @@ struct Tables {
   SubBox* d_sb = nullptr;
   float* d_chi4 = nullptr;    // [box nodes][4], zero where a group has < 4 projectors
   Layout lay[2];
+  unsigned long long geom = 0;   // hash of the grid, groups and piece geometry (not phases)
 };
+
+// k-points of one batched complex launch.  The Hamiltonians of a batch share the
+// grid and the projector geometry (boxes, groups, per-CTA lists); each k keeps its
+// own piece phases, projector values, V_eff and Bloch phases of the faces.
+constexpr int KMAX = 32;
+struct KSlot {
+  const SubBox* sb;       // pieces with this k's phases (geometry as the batch's first H)
+  const float4* chi4;
+  const float* veff;
+  const float* gamma;
+  long long ubase;        // block-buffer unit of this slot's first block
+  float phx_r, phx_i, phy_r, phy_i, phz_r, phz_i;   // exp(i k_s L_s)
+  float alpha, shift, beta;                          // recurrence coefficients of this k
+};
+// A launch covers the units ubase(kk) + j for kk < nk, j < nbk.
+struct KSlots {
+  KSlot s[KMAX];
+  int nk, nbk;
+};
+// Fill the per-k fields of a slot from H (not ubase, alpha, shift, beta).
+void kslot(const sparc_ham* H, KSlot& s);
+// Hash of the geometry the batched kernels take from the first Hamiltonian: equal
+// hashes (with equal grids) mean one launch may serve several of them.
+unsigned long long geometry_hash(const sparc_ham* H);
 
 // Host: build the tables from the projector boxes (called by sparc_ham_create).
 sparc_status build_tables(sparc_ham* H, const sparc_nonlocal* nl);
@@ -78,6 +103,14 @@ template <class T>
 cudaError_t launch_pass(const sparc_ham* H, const T* Yin, const T* Yprev, T* Yout, const T* gc,
                         int nblk_total, int blk0, int nb, double alpha, double shift, double beta,
                         cudaStream_t st);
+
+// Complex64, batched over k: the same two steps for the units of `ks`; `gc` and
+// the block buffers hold nunit_total units ([unit][Nd][NB] and [p][unit][NB]);
+// geometry and launch shape from H0.
+cudaError_t launch_gather_k(const sparc_ham* H0, const cf32* Y, long long nunit_total, const KSlots& ks,
+                            cf32* gc, cf32* scratch, cudaStream_t st);
+cudaError_t launch_pass_k(const sparc_ham* H0, const cf32* Yin, const cf32* Yprev, cf32* Yout, const cf32* gc,
+                          long long nunit_total, const KSlots& ks, cudaStream_t st);
 
 }  // namespace fast
 }  // namespace sparc

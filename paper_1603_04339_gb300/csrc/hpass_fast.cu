@@ -124,6 +124,22 @@ sparc_status build_tables(sparc_ham* H, const sparc_nonlocal* nl) {
     g.sb1 = (int)sbs.size();
     off4 += sz;
   }
+  // FNV-1a over what the batched kernels share between Hamiltonians
+  {
+    unsigned long long hsh = 1469598103934665603ULL;
+    auto mix = [&](long long v) {
+      for (int i = 0; i < 8; ++i) { hsh ^= (unsigned long long)((v >> (8 * i)) & 0xFF); hsh *= 1099511628211ULL; }
+    };
+    for (int a = 0; a < 3; ++a) mix(n[a]);
+    mix(off4);
+    for (const Group& g : grps) { for (int s = 0; s < 4; ++s) mix(g.proj[s]); mix(g.sb0); mix(g.sb1); }
+    for (const SubBox& b : sbs) {
+      const int f[12] = {b.gx0, b.gx1, b.gy0, b.gy1, b.gz0, b.gz1, b.bx0, b.by0, b.bz0, b.nbx, b.nby, b.grp};
+      for (int v : f) mix(v);
+      mix(b.chi4_off);
+    }
+    T->geom = hsh;
+  }
   // per kernel tile shape: CTA item lists and per-z active slots
   T->ngrp = (int)grps.size();
   T->nsb = (int)sbs.size();
@@ -210,6 +226,22 @@ sparc_status build_tables(sparc_ham* H, const sparc_nonlocal* nl) {
     return fail(ctx, SPARC_ERR_OOM, "projector table allocation failed");
   }
   return SPARC_OK;
+}
+
+unsigned long long geometry_hash(const sparc_ham* H) {
+  const Tables* T = (const Tables*)H->fast;
+  return T ? T->geom : 0ULL;
+}
+
+void kslot(const sparc_ham* H, KSlot& s) {
+  const Tables* T = (const Tables*)H->fast;
+  s.sb = T->d_sb;
+  s.chi4 = (const float4*)T->d_chi4;
+  s.veff = H->d_veff32;
+  s.gamma = H->d_gamma32;
+  s.phx_r = (float)H->gd.ph_re[0]; s.phx_i = (float)H->gd.ph_im[0];
+  s.phy_r = (float)H->gd.ph_re[1]; s.phy_i = (float)H->gd.ph_im[1];
+  s.phz_r = (float)H->gd.ph_re[2]; s.phz_i = (float)H->gd.ph_im[2];
 }
 
 bool usable(const sparc_ham* H) {
@@ -321,7 +353,8 @@ template <class T> struct Smem {
 // Yprev may alias Yout (the recurrence is written in place): neither is restrict.
 template <class T>
 __global__ void __launch_bounds__(THREADS, 1)
-k_pass(PassArgs a, const T* __restrict__ Yin, const T* Yprev, T* Yout, const T* __restrict__ gc) {
+k_pass(PassArgs a, const __grid_constant__ KSlots ks, const T* __restrict__ Yin, const T* Yprev, T* Yout,
+       const T* __restrict__ gc) {
   constexpr int Q = 2 * R + 1;
   constexpr int RX = Shape<T>::RX, TY = Shape<T>::TY, PY = plane_rows<T>(), NRG = Smem<T>::NRG;
   constexpr int CH = (int)(NB * sizeof(T) / 16);    // 16-byte chunks per node
@@ -349,7 +382,9 @@ k_pass(PassArgs a, const T* __restrict__ Yin, const T* Yprev, T* Yout, const T* 
   const int tx0 = (tile % a.tiles_x) * TX, ty0 = (tile / a.tiles_x) * TY;
   const int zs = chunk * ZC;
   const int ze = min(zs + ZC, a.n3);
-  const int blk = a.blk0 + blockIdx.z;
+  const int kk = blockIdx.z / ks.nbk;
+  const KSlot& S = ks.s[kk];
+  const long long blk = S.ubase + blockIdx.z % ks.nbk;   // unit of the block buffers and gc
   const size_t boff = (size_t)blk * a.nd * NB;
   const T* Y = Yin + boff;
   const int n1 = a.n1, n2 = a.n2, n3 = a.n3;
@@ -364,7 +399,7 @@ k_pass(PassArgs a, const T* __restrict__ Yin, const T* Yprev, T* Yout, const T* 
   // ---- CTA tables: projector pieces (compact), their coefficients, per-(z, rows) activations
   const int it0 = __ldg(a.cptr + cta), nit = __ldg(a.cptr + cta + 1) - it0;
   for (int i = t; i < nit; i += THREADS) {
-    const SubBox b = a.sb[__ldg(a.citems + it0 + i)];
+    const SubBox b = S.sb[__ldg(a.citems + it0 + i)];
     Piece pc;
     pc.gy0 = b.gy0; pc.gy1 = b.gy1; pc.gx0 = b.gx0; pc.gx1 = b.gx1;
     pc.sy = b.nbx;
@@ -429,7 +464,7 @@ k_pass(PassArgs a, const T* __restrict__ Yin, const T* Yprev, T* Yout, const T* 
     int zw = zz;
     const int tz = wrap(zw, n3);
     float pr = 1.f, pi = 0.f;
-    if (FT<T>::cplx && tz != 0) phase_pow(a.phz_r, a.phz_i, tz, pr, pi);
+    if (FT<T>::cplx && tz != 0) phase_pow(S.phz_r, S.phz_i, tz, pr, pi);
     const T* src = Y + (size_t)zw * plane_el + ((size_t)gy * n1 + tx0 + xl0) * NB + o;
 #pragma unroll
     for (int r = 0; r < RX; ++r) dst[r] = vr[r] ? FT<T>::phase(fld(src + r * NB), pr, pi) : FT<T>::zero();
@@ -445,7 +480,7 @@ k_pass(PassArgs a, const T* __restrict__ Yin, const T* Yprev, T* Yout, const T* 
 #pragma unroll
     for (int i = 0; i < NHC; ++i)
       if (hs[i] >= 0) cp16(P + (hs[i] & 0xFFFFF), Yz + hg[i]);
-    if (vv) cp4(vbs + (size_t)b * TY * TX + t, a.veff + (size_t)zw * n1 * n2 + vg);
+    if (vv) cp4(vbs + (size_t)b * TY * TX + t, S.veff + (size_t)zw * n1 * n2 + vg);
     if (Yprev != nullptr) {
       T* Pp = yps + (size_t)b * TY * TX * NB;
       const T* Yp = Yprev + boff + (size_t)zw * plane_el;
@@ -464,9 +499,9 @@ k_pass(PassArgs a, const T* __restrict__ Yin, const T* Yprev, T* Yout, const T* 
         const int hw = hs[i] >> 20;
         if (hs[i] < 0 || (hw == 4 && tz == 0)) continue;
         float pr, pi, qr, qi, rr, ri;
-        phase_pow(a.phx_r, a.phx_i, hw % 3 - 1, pr, pi);
-        phase_pow(a.phy_r, a.phy_i, hw / 3 - 1, qr, qi);
-        phase_pow(a.phz_r, a.phz_i, tz, rr, ri);
+        phase_pow(S.phx_r, S.phx_i, hw % 3 - 1, pr, pi);
+        phase_pow(S.phy_r, S.phy_i, hw / 3 - 1, qr, qi);
+        phase_pow(S.phz_r, S.phz_i, tz, rr, ri);
         const float ar = pr * qr - pi * qi, ai = pr * qi + pi * qr;
         const float br = ar * rr - ai * ri, bi = ar * ri + ai * rr;
         float4* c = reinterpret_cast<float4*>(P + (hs[i] & 0xFFFFF));
@@ -509,7 +544,7 @@ k_pass(PassArgs a, const T* __restrict__ Yin, const T* Yprev, T* Yout, const T* 
       const float* V = vbs + (size_t)b * TY * TX + yl * TX + xl0;
 #pragma unroll
       for (int r = 0; r < RX; ++r) {
-        const float cc = a.c0 + V[r] - a.shift;
+        const float cc = a.c0 + V[r] - S.shift;
         T s;
         if constexpr (FT<T>::cplx) s = cf32{cc * q[R][r].x, cc * q[R][r].y};
         else s = cc * q[R][r];
@@ -548,7 +583,7 @@ k_pass(PassArgs a, const T* __restrict__ Yin, const T* Yprev, T* Yout, const T* 
 #pragma unroll
         for (int r = 0; r < RX; ++r) {
           const int gx = x0r + r;
-          c4[r] = (gx >= pc.gx0 && gx < pc.gx1) ? __ldg(a.chi4 + rowoff + gx) : make_float4(0.f, 0.f, 0.f, 0.f);
+          c4[r] = (gx >= pc.gx0 && gx < pc.gx1) ? __ldg(S.chi4 + rowoff + gx) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int r = 0; r < RX; ++r) {
@@ -569,11 +604,11 @@ k_pass(PassArgs a, const T* __restrict__ Yin, const T* Yprev, T* Yout, const T* 
         if (!vr[r]) continue;
         T v;
         if constexpr (FT<T>::cplx) {
-          v = cf32{a.alpha * acc[r].x, a.alpha * acc[r].y};
-          if (Yprev) { const T pv = Pp[r * NB]; v.x += a.beta * pv.x; v.y += a.beta * pv.y; }
+          v = cf32{S.alpha * acc[r].x, S.alpha * acc[r].y};
+          if (Yprev) { const T pv = Pp[r * NB]; v.x += S.beta * pv.x; v.y += S.beta * pv.y; }
         } else {
-          v = a.alpha * acc[r];
-          if (Yprev) v = fmaf(a.beta, Pp[r * NB], v);
+          v = S.alpha * acc[r];
+          if (Yprev) v = fmaf(S.beta, Pp[r * NB], v);
         }
         out[r * NB] = v;
       }
@@ -877,83 +912,6 @@ k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* 
   }
 }
 
-// gc[p][blk][lane] = gamma_p h^3 sum_{box} conj(chi~_p) Y, one CTA per (group, block).
-// A warp takes whole x-rows of a piece (4 nodes x 8 lanes per step, unrolled).
-template <class T>
-__global__ void __launch_bounds__(512)
-k_gather(const T* __restrict__ Y, long long nd, int n1, int n2, const Group* __restrict__ grp,
-         const SubBox* __restrict__ sbs, const float4* __restrict__ chi4,
-         const float* __restrict__ gamma, float dv, T* __restrict__ gc, int nblk_total, int blk0) {
-  __shared__ T red[512][4];
-  const int gi = blockIdx.x;
-  const int blk = blk0 + blockIdx.y;
-  const int o = threadIdx.x % NB, ng = (threadIdx.x / NB) % 4, warp = threadIdx.x / 32;
-  const Group G = grp[gi];
-  const T* Yb = Y + (size_t)blk * nd * NB;
-  T acc[4] = {FT<T>::zero(), FT<T>::zero(), FT<T>::zero(), FT<T>::zero()};
-  for (int sbi = G.sb0; sbi < G.sb1; ++sbi) {
-    const SubBox b = sbs[sbi];
-    const int wx = b.gx1 - b.gx0, wy = b.gy1 - b.gy0, wz = b.gz1 - b.gz0;
-    T s[4] = {FT<T>::zero(), FT<T>::zero(), FT<T>::zero(), FT<T>::zero()};
-    for (int row = warp; row < wy * wz; row += 16) {
-      const int iy = row % wy, iz = row / wy;
-      const long long yrow = ((long long)(b.gz0 + iz) * n2 + (b.gy0 + iy)) * n1 + b.gx0;
-      const long long crow = b.chi4_off + b.bx0 + (long long)b.nbx * ((b.by0 + iy) + (long long)b.nby * (b.bz0 + iz));
-#pragma unroll 4
-      for (int ix = ng; ix < wx; ix += 4) {
-        const float4 c4 = __ldg(chi4 + crow + ix);
-        const T y = fld(Yb + (size_t)(yrow + ix) * NB + o);
-        if constexpr (FT<T>::cplx) {
-          s[0].x += c4.x * y.x; s[0].y += c4.x * y.y;
-          s[1].x += c4.y * y.x; s[1].y += c4.y * y.y;
-          s[2].x += c4.z * y.x; s[2].y += c4.z * y.y;
-          s[3].x += c4.w * y.x; s[3].y += c4.w * y.y;
-        } else {
-          s[0] = fmaf(c4.x, y, s[0]); s[1] = fmaf(c4.y, y, s[1]);
-          s[2] = fmaf(c4.z, y, s[2]); s[3] = fmaf(c4.w, y, s[3]);
-        }
-      }
-    }
-#pragma unroll
-    for (int l = 0; l < 4; ++l) {   // conj(phase) of this piece
-      if constexpr (FT<T>::cplx) {
-        acc[l].x += b.ph_re * s[l].x + b.ph_im * s[l].y;
-        acc[l].y += b.ph_re * s[l].y - b.ph_im * s[l].x;
-      } else {
-        acc[l] += b.ph_re * s[l];
-      }
-    }
-  }
-#pragma unroll
-  for (int l = 0; l < 4; ++l) red[threadIdx.x][l] = acc[l];
-  __syncthreads();
-  for (int st = 256; st >= NB; st >>= 1) {
-    if (threadIdx.x < st)
-#pragma unroll
-      for (int l = 0; l < 4; ++l) {
-        if constexpr (FT<T>::cplx) {
-          red[threadIdx.x][l].x += red[threadIdx.x + st][l].x;
-          red[threadIdx.x][l].y += red[threadIdx.x + st][l].y;
-        } else {
-          red[threadIdx.x][l] += red[threadIdx.x + st][l];
-        }
-      }
-    __syncthreads();
-  }
-  if (threadIdx.x < NB) {
-#pragma unroll
-    for (int l = 0; l < 4; ++l) {
-      const int p = G.proj[l];
-      if (p < 0) continue;
-      const float f = gamma[p] * dv;
-      T v = red[threadIdx.x][l];
-      if constexpr (FT<T>::cplx) v = cf32{f * v.x, f * v.y};
-      else v = f * v;
-      gc[((size_t)p * nblk_total + blk) * NB + o] = v;
-    }
-  }
-}
-
 // s[b][l] += sum over this lane's nodes ix = xi, xi+4, .. < wx of chi_l(ix) Y_b(ix).
 // The row is taken in chunks of 4 NXS nodes; every load of a chunk is issued
 // before its first multiply, so a warp has (1 + NBM) NXS loads in flight.
@@ -996,18 +954,23 @@ __device__ __forceinline__ void gather_row(T (&s)[NBM][4], const float4* __restr
 // groups and the chi values of those 4 nodes are read once for all NBM blocks.
 // The row sums of a piece carry its constant phase; partial sums are reduced
 // over xi by shuffles and over the 8 warps in shared memory, in a fixed order.
-// part[((g * nslab + s) * 4 + l) * (nb * NB) + bi * NB + lane] gets the CTA sum.
+// Grid z runs over (k slot, octet of its nbk blocks); an octet never spans two k.
+// part[((g * nslab + s) * 4 + l) * (nk * nbk * NB) + (kk * nbk + bi) * NB + lane] gets the CTA sum.
 template <class T, int NBM>
 __global__ void __launch_bounds__(256, 2)
 k_gather_rows(const T* __restrict__ Y, long long nd, int n1, int n2, const Group* __restrict__ grp,
-              const SubBox* __restrict__ sbs, const float4* __restrict__ chi4, T* __restrict__ part,
-              int blk0, int nb, int nslab) {
+              const __grid_constant__ KSlots ks, T* __restrict__ part, int noct, int nslab) {
   __shared__ T red[8][NBM][4][NB];
-  const int gi = blockIdx.x, sl = blockIdx.y, q = blockIdx.z;
+  const int gi = blockIdx.x, sl = blockIdx.y;
+  const int kk = blockIdx.z / noct, q = blockIdx.z % noct;
+  const KSlot& S = ks.s[kk];
+  const SubBox* __restrict__ sbs = S.sb;
+  const float4* __restrict__ chi4 = S.chi4;
+  const int nb = ks.nbk;
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
   const int o = lane % NB, xi = lane / NB;
   const int nbv = min(NBM, nb - q * NBM);   // valid blocks of this octet (uniform per CTA)
-  const T* Yb = Y + (size_t)(blk0 + q * NBM) * nd * NB + o;
+  const T* Yb = Y + (size_t)(S.ubase + q * NBM) * nd * NB + o;
   const size_t bstride = (size_t)nd * NB;
   const Group G = grp[gi];
   T acc[NBM][4];
@@ -1077,8 +1040,8 @@ k_gather_rows(const T* __restrict__ Y, long long nd, int n1, int n2, const Group
       if constexpr (FT<T>::cplx) { v.x += red[w2][b][l][oo].x; v.y += red[w2][b][l][oo].y; }
       else v += red[w2][b][l][oo];
     }
-    const int bi = q * NBM + b;
-    part[((size_t)(gi * nslab + sl) * 4 + l) * ((size_t)nb * NB) + bi * NB + oo] = v;
+    const int bi = kk * nb + q * NBM + b;
+    part[((size_t)(gi * nslab + sl) * 4 + l) * ((size_t)ks.nk * nb * NB) + (size_t)bi * NB + oo] = v;
   }
 }
 
@@ -1206,6 +1169,30 @@ __global__ void k_gather_sum(const T* __restrict__ part, const Group* __restrict
   gc[((size_t)p * nblk_total + blk0 + bi) * NB + o] = v;
 }
 
+// The same for the units of a k batch: gamma per k, unit ubase(kk) + bi.
+__global__ void k_gather_sum_k(const cf32* __restrict__ part, const Group* __restrict__ grp,
+                               const __grid_constant__ KSlots ks, float dv, cf32* __restrict__ gc, int ngrp,
+                               int nslab, long long nunit_total) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nu = ks.nk * ks.nbk;
+  const long long per = 4LL * nu * NB;
+  if (t >= (long long)ngrp * per) return;
+  const int gi = (int)(t / per);
+  const int rem = (int)(t % per);
+  const int l = rem / (nu * NB), uu = (rem / NB) % nu, o = rem % NB;
+  const int p = grp[gi].proj[l];
+  if (p < 0) return;
+  const KSlot& S = ks.s[uu / ks.nbk];
+  float vx = 0.f, vy = 0.f;
+  for (int s = 0; s < nslab; ++s) {
+    const cf32 x = part[((size_t)(gi * nslab + s) * 4 + l) * ((size_t)nu * NB) + (size_t)uu * NB + o];
+    vx += x.x;
+    vy += x.y;
+  }
+  const float f = S.gamma[p] * dv;
+  gc[((size_t)p * nunit_total + S.ubase + uu % ks.nbk) * NB + o] = cf32{f * vx, f * vy};
+}
+
 // --------------------------------------------------------------------------- launchers
 
 constexpr int NSLAB_MAX = 16;
@@ -1223,20 +1210,43 @@ size_t gather_scratch_bytes(const sparc_ham* H, int nb, size_t esize) {
   return (size_t)std::max(1, Tb->ngrp) * NSLAB_MAX * 4 * nb * NB * esize;
 }
 
+cudaError_t launch_gather_k(const sparc_ham* H0, const cf32* Y, long long nunit_total, const KSlots& ks,
+                            cf32* gc, cf32* scratch, cudaStream_t st) {
+  const Tables* Tb = (const Tables*)H0->fast;
+  if (H0->nproj == 0 || Tb->ngrp == 0) return cudaSuccess;
+  const float dv = (float)(H0->grid.h[0] * H0->grid.h[1] * H0->grid.h[2]);
+  const int nslab = gather_slabs(H0);
+  cudaEvent_t t0 = timing_begin(H0->ctx, st);
+  constexpr int NBM = GatherOct<cf32>::v;
+  const int noct = ceil_div(ks.nbk, NBM);
+  const dim3 grid((unsigned)Tb->ngrp, (unsigned)nslab, (unsigned)(ks.nk * noct));
+  k_gather_rows<cf32, NBM><<<grid, 256, 0, st>>>(Y, H0->gd.nd, H0->gd.n1, H0->gd.n2, Tb->d_grp, ks, scratch,
+                                                 noct, nslab);
+  const long long tot = (long long)Tb->ngrp * 4 * ks.nk * ks.nbk * NB;
+  k_gather_sum_k<<<ceil_div(tot, 256), 256, 0, st>>>(scratch, Tb->d_grp, ks, dv, gc, Tb->ngrp, nslab,
+                                                      nunit_total);
+  H0->ctx->launches += 2;
+  timing_end(H0->ctx, TK_GATHER, t0, st);
+  return cudaGetLastError();
+}
+
 template <class T>
 cudaError_t launch_gather(const sparc_ham* H, const T* Y, int nblk_total, int blk0, int nb, T* gc,
                           T* scratch, cudaStream_t st) {
   const Tables* Tb = (const Tables*)H->fast;
   if (H->nproj == 0 || Tb->ngrp == 0) return cudaSuccess;
-  const float dv = (float)(H->grid.h[0] * H->grid.h[1] * H->grid.h[2]);
-  const int nslab = gather_slabs(H);
-  cudaEvent_t t0 = timing_begin(H->ctx, st);
   if constexpr (FT<T>::cplx) {
-    constexpr int NBM = GatherOct<T>::v;
-    const dim3 grid((unsigned)Tb->ngrp, (unsigned)nslab, (unsigned)ceil_div(nb, NBM));
-    k_gather_rows<T, NBM><<<grid, 256, 0, st>>>(Y, H->gd.nd, H->gd.n1, H->gd.n2, Tb->d_grp, Tb->d_sb,
-                                                (const float4*)Tb->d_chi4, scratch, blk0, nb, nslab);
+    KSlots ks;
+    ks.nk = 1;
+    ks.nbk = nb;
+    kslot(H, ks.s[0]);
+    ks.s[0].ubase = blk0;
+    ks.s[0].alpha = ks.s[0].shift = ks.s[0].beta = 0.f;
+    return launch_gather_k(H, Y, nblk_total, ks, gc, scratch, st);
   } else {
+    const float dv = (float)(H->grid.h[0] * H->grid.h[1] * H->grid.h[2]);
+    const int nslab = gather_slabs(H);
+    cudaEvent_t t0 = timing_begin(H->ctx, st);
     // pairs of blocks per CTA: as many as the group has, at most 4 pairs
     const int nb2 = std::min(4, (nb + 1) / 2);
     const dim3 grid((unsigned)Tb->ngrp, (unsigned)nslab, (unsigned)ceil_div(nb, 2 * nb2));
@@ -1250,28 +1260,24 @@ cudaError_t launch_gather(const sparc_ham* H, const T* Y, int nblk_total, int bl
       case 3: go(k_gather_rows_f2<3>); break;
       default: go(k_gather_rows_f2<4>); break;
     }
+    const long long tot = (long long)Tb->ngrp * 4 * nb * NB;
+    k_gather_sum<T><<<ceil_div(tot, 256), 256, 0, st>>>(scratch, Tb->d_grp, H->d_gamma32, dv, gc, Tb->ngrp,
+                                                        nslab, nblk_total, blk0, nb);
+    H->ctx->launches += 2;
+    timing_end(H->ctx, TK_GATHER, t0, st);
+    return cudaGetLastError();
   }
-  const long long tot = (long long)Tb->ngrp * 4 * nb * NB;
-  k_gather_sum<T><<<ceil_div(tot, 256), 256, 0, st>>>(scratch, Tb->d_grp, H->d_gamma32, dv, gc, Tb->ngrp,
-                                                      nslab, nblk_total, blk0, nb);
-  H->ctx->launches += 2;
-  timing_end(H->ctx, TK_GATHER, t0, st);
-  return cudaGetLastError();
 }
 
-template <class T>
-cudaError_t launch_pass(const sparc_ham* H, const T* Yin, const T* Yprev, T* Yout, const T* gc,
-                        int nblk_total, int blk0, int nb, double alpha, double shift, double beta,
-                        cudaStream_t st) {
-  const Tables* Tb = (const Tables*)H->fast;
-  const Layout& Lo = Tb->lay[FT<T>::cplx ? 1 : 0];
+// Geometry and stencil fields of the pass arguments (shared by every k of a batch).
+static PassArgs pass_args(const sparc_ham* H, const Layout& Lo) {
   PassArgs a;
   a.nd = H->gd.nd;
   a.n1 = H->gd.n1; a.n2 = H->gd.n2; a.n3 = H->gd.n3;
   a.tiles_x = Lo.tiles_x;
   a.nchunk = Lo.nchunk;
-  a.blk0 = blk0;
-  a.nblk_total = nblk_total;
+  a.blk0 = 0;
+  a.nblk_total = 0;
   for (int p = 0; p <= R; ++p) {
     a.cx[p] = (float)H->gd.coef[0][p];
     a.cy[p] = (float)H->gd.coef[1][p];
@@ -1281,38 +1287,71 @@ cudaError_t launch_pass(const sparc_ham* H, const T* Yin, const T* Yprev, T* You
   a.phx_r = (float)H->gd.ph_re[0]; a.phx_i = (float)H->gd.ph_im[0];
   a.phy_r = (float)H->gd.ph_re[1]; a.phy_i = (float)H->gd.ph_im[1];
   a.phz_r = (float)H->gd.ph_re[2]; a.phz_i = (float)H->gd.ph_im[2];
-  a.alpha = (float)alpha; a.shift = (float)shift; a.beta = (float)beta;
+  a.alpha = a.shift = a.beta = 0.f;
   for (int p = 0; p <= R; ++p) {
     a.cx2[p] = make_float2(a.cx[p], a.cx[p]);
     a.cy2[p] = make_float2(a.cy[p], a.cy[p]);
     a.cz2[p] = make_float2(a.cz[p], a.cz[p]);
   }
-  a.alpha2 = make_float2(a.alpha, a.alpha);
-  a.beta2 = make_float2(a.beta, a.beta);
+  a.alpha2 = a.beta2 = make_float2(0.f, 0.f);
   a.veff = H->d_veff32;
+  const Tables* Tb = (const Tables*)H->fast;
   a.cptr = Lo.d_cptr; a.citems = Lo.d_citems; a.sptr = Lo.d_sptr; a.sslots = Lo.d_sslots;
   a.sb = Tb->d_sb; a.grp = Tb->d_grp;
   a.chi4 = (const float4*)Tb->d_chi4;
-  const size_t smem = Smem<T>::total;
-  cudaEvent_t t0 = nullptr;
-  if constexpr (!FT<T>::cplx) {
+  return a;
+}
+
+cudaError_t launch_pass_k(const sparc_ham* H0, const cf32* Yin, const cf32* Yprev, cf32* Yout, const cf32* gc,
+                          long long nunit_total, const KSlots& ks, cudaStream_t st) {
+  const Tables* Tb = (const Tables*)H0->fast;
+  const Layout& Lo = Tb->lay[1];
+  PassArgs a = pass_args(H0, Lo);
+  a.nblk_total = (int)nunit_total;
+  const size_t smem = Smem<cf32>::total;
+  cudaError_t e = cudaFuncSetAttribute(k_pass<cf32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)(Lo.tiles_x * Lo.tiles_y), (unsigned)Lo.nchunk, (unsigned)(ks.nk * ks.nbk));
+  cudaEvent_t t0 = timing_begin(H0->ctx, st);
+  k_pass<cf32><<<grid, THREADS, smem, st>>>(a, ks, Yin, Yprev, Yout, gc);
+  ++H0->ctx->launches;
+  timing_end(H0->ctx, TK_FPASS, t0, st);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_pass(const sparc_ham* H, const T* Yin, const T* Yprev, T* Yout, const T* gc,
+                        int nblk_total, int blk0, int nb, double alpha, double shift, double beta,
+                        cudaStream_t st) {
+  if constexpr (FT<T>::cplx) {
+    KSlots ks;
+    ks.nk = 1;
+    ks.nbk = nb;
+    kslot(H, ks.s[0]);
+    ks.s[0].ubase = blk0;
+    ks.s[0].alpha = (float)alpha; ks.s[0].shift = (float)shift; ks.s[0].beta = (float)beta;
+    return launch_pass_k(H, Yin, Yprev, Yout, gc, nblk_total, ks, st);
+  } else {
+    const Tables* Tb = (const Tables*)H->fast;
+    const Layout& Lo = Tb->lay[0];
+    PassArgs a = pass_args(H, Lo);
+    a.blk0 = blk0;
+    a.nblk_total = nblk_total;
+    a.alpha = (float)alpha; a.shift = (float)shift; a.beta = (float)beta;
+    a.alpha2 = make_float2(a.alpha, a.alpha);
+    a.beta2 = make_float2(a.beta, a.beta);
+    const size_t smem = Smem<T>::total;
     // persistent CTAs over (tile, chunk, block) items
     cudaError_t e = cudaFuncSetAttribute(k_pass_f2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int nitems = Lo.tiles_x * Lo.tiles_y * Lo.nchunk * nb;
     const int nsm = H->ctx->nsm;
-    t0 = timing_begin(H->ctx, st);
+    cudaEvent_t t0 = timing_begin(H->ctx, st);
     k_pass_f2<<<std::min(nitems, std::max(nsm, 1)), THREADS, smem, st>>>(a, Yin, Yprev, Yout, gc, nitems);
-  } else {
-    cudaError_t e = cudaFuncSetAttribute(k_pass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)(Lo.tiles_x * Lo.tiles_y), (unsigned)Lo.nchunk, (unsigned)nb);
-    t0 = timing_begin(H->ctx, st);
-    k_pass<T><<<grid, THREADS, smem, st>>>(a, Yin, Yprev, Yout, gc);
+    ++H->ctx->launches;
+    timing_end(H->ctx, TK_FPASS, t0, st);
+    return cudaGetLastError();
   }
-  ++H->ctx->launches;
-  timing_end(H->ctx, TK_FPASS, t0, st);
-  return cudaGetLastError();
 }
 
 template <class T>

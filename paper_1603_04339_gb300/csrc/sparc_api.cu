@@ -276,6 +276,8 @@ sparc_status filter_block_fast(sparc_ham* H, int m, double a, double b, double a
     const double eff = (double)it / ((double)nsm * (double)((it + nsm - 1) / nsm));
     if (eff > best + 1e-9 || (std::abs(eff - best) <= 1e-9 && g > G)) { best = eff; G = g; }
   }
+  const auto tu = H->ctx->tuned.find(std::make_tuple((int)DtypeOf<T>::v, H->gd.nd, ns, 1));
+  if (tu != H->ctx->tuned.end()) G = std::max(1, std::min(nblk, tu->second));
   T* scratch = (T*)w.tail;
   SPARC_CUDA(H->ctx, launch_to_blocks<T>(X, ld, ns, B0, H->gd.nd, nblk, st));
   ++H->ctx->launches;
@@ -299,6 +301,112 @@ sparc_status filter_block_fast(sparc_ham* H, int m, double a, double b, double a
   }
   SPARC_CUDA(H->ctx, launch_from_blocks<T>(res, H->gd.nd, nblk, Y, ld, ns, st));
   ++H->ctx->launches;
+  return SPARC_OK;
+}
+
+// Launch grouping of a k batch: nkg k-points x nbk of their blocks per launch.
+// Minimises the modelled time -- waves of one-CTA-per-SM work items plus 0.05
+// wave per launch pair -- over groupings of at most `upl` units (0: any).
+struct KGroup { int nkg, nbk; };
+static KGroup kbatch_grouping(int nk, int nblk, int items_per_blk, int nsm, int upl) {
+  KGroup g{1, 1};
+  double best = 1e300;
+  for (int nkg = 1; nkg <= std::min(nk, fast::KMAX); ++nkg)
+    for (int d = 1; d <= nblk; ++d) {
+      const int nbk = ceil_div(nblk, d);
+      if (d > 1 && ceil_div(nblk, d - 1) == nbk) continue;
+      if (upl > 0 && nkg * nbk > upl && !(nkg == 1 && nbk == 1)) continue;
+      double cost = 0.0;
+      for (int k0 = 0; k0 < nk; k0 += nkg)
+        for (int b0 = 0; b0 < nblk; b0 += nbk) {
+          const long long it = (long long)std::min(nkg, nk - k0) * std::min(nbk, nblk - b0) * items_per_blk;
+          cost += (double)((it + nsm - 1) / nsm) + 0.05;
+        }
+      if (cost < best - 1e-9) { best = cost; g = {nkg, nbk}; }
+    }
+  return g;
+}
+
+// The complex64 filter of nk Hamiltonians that share the grid and projector
+// geometry: the same recurrence as filter_block_fast per k, with every gather
+// and pass launch covering the blocks of up to KMAX k-points.
+static sparc_status filter_kbatch(sparc_ham* const* Hs, int nk, int m, const double* a, const double* b,
+                                  const double* a0, const cf32* X, cf32* Y, int ns, long long ld,
+                                  cudaStream_t st) {
+  sparc_ham* H0 = Hs[0];
+  sparc_ctx* ctx = H0->ctx;
+  const int nblk = ceil_div(ns, NB);
+  const long long nd = H0->gd.nd;
+  const long long U = (long long)nk * nblk;
+  int upl = 0;
+  const auto tu = ctx->tuned.find(std::make_tuple((int)SPARC_C64, nd, ns, nk));
+  if (tu != ctx->tuned.end()) upl = tu->second;
+  const KGroup G = kbatch_grouping(nk, nblk, fast::items_per_block<cf32>(H0), ctx->nsm, upl);
+  const size_t bb = align256((size_t)U * nd * NB * sizeof(cf32));
+  const size_t gb = align256((size_t)std::max(1, H0->nproj) * U * NB * sizeof(cf32));
+  const size_t sb = align256(fast::gather_scratch_bytes(H0, G.nkg * G.nbk, sizeof(cf32)));
+  if (!ensure_ws(ctx, 2 * bb + gb + sb)) return fail(ctx, SPARC_ERR_OOM, "workspace allocation failed");
+  char* p = (char*)ctx->ws;
+  cf32* B0 = (cf32*)p;
+  cf32* B1 = (cf32*)(p + bb);
+  cf32* gc = (cf32*)(p + 2 * bb);
+  cf32* scratch = (cf32*)(p + 2 * bb + gb);
+  const size_t kx = (size_t)ns * (size_t)ld, kb = (size_t)nblk * nd * NB;
+  for (int k = 0; k < nk; ++k) {
+    SPARC_CUDA(ctx, launch_to_blocks<cf32>(X + k * kx, ld, ns, B0 + k * kb, nd, nblk, st));
+    ++ctx->launches;
+  }
+  std::vector<double> e(nk), c(nk), s1(nk), sg(nk);
+  for (int k = 0; k < nk; ++k) {
+    e[k] = 0.5 * (b[k] - a[k]);
+    c[k] = 0.5 * (b[k] + a[k]);
+    s1[k] = e[k] / (a0[k] - c[k]);
+  }
+  cf32* res = B1;
+  for (int k0 = 0; k0 < nk; k0 += G.nkg)
+    for (int b0 = 0; b0 < nblk; b0 += G.nbk) {
+      fast::KSlots ks;
+      ks.nk = std::min(G.nkg, nk - k0);
+      ks.nbk = std::min(G.nbk, nblk - b0);
+      for (int kk = 0; kk < ks.nk; ++kk) {
+        fast::kslot(Hs[k0 + kk], ks.s[kk]);
+        ks.s[kk].ubase = (long long)(k0 + kk) * nblk + b0;
+      }
+      auto coefs = [&](int j) {   // degree j + 1 of the recurrence, per k
+        for (int kk = 0; kk < ks.nk; ++kk) {
+          const int k = k0 + kk;
+          fast::KSlot& S = ks.s[kk];
+          S.shift = (float)c[k];
+          if (j == 0) {
+            sg[k] = s1[k];
+            S.alpha = (float)(s1[k] / e[k]);
+            S.beta = 0.f;
+          } else {
+            const double sn = 1.0 / (2.0 / s1[k] - sg[k]);
+            S.alpha = (float)(2.0 * sn / e[k]);
+            S.beta = (float)(-sg[k] * sn);
+            sg[k] = sn;
+          }
+        }
+      };
+      cf32* prev = B0;
+      cf32* cur = B1;
+      coefs(0);
+      SPARC_CUDA(ctx, fast::launch_gather_k(H0, prev, U, ks, gc, scratch, st));
+      SPARC_CUDA(ctx, fast::launch_pass_k(H0, prev, nullptr, cur, gc, U, ks, st));
+      for (int j = 1; j < m; ++j) {
+        coefs(j);
+        SPARC_CUDA(ctx, fast::launch_gather_k(H0, cur, U, ks, gc, scratch, st));
+        SPARC_CUDA(ctx, fast::launch_pass_k(H0, cur, prev, prev, gc, U, ks, st));
+        std::swap(cur, prev);
+      }
+      res = cur;
+    }
+  for (int k = 0; k < nk; ++k) {
+    SPARC_CUDA(ctx, launch_from_blocks<cf32>(res + k * kb, nd, nblk, Y + k * kx, ld, ns, st));
+    ++ctx->launches;
+  }
+  SPARC_LAUNCH(ctx, "filter batch");
   return SPARC_OK;
 }
 
@@ -628,6 +736,122 @@ sparc_status sparc_cheb_filter(sparc_ham* H, sparc_dtype dtype, int m, double a,
       return filter_block<cf32>(H, m, a, b, a0, (const cf32*)X, (cf32*)Y, ns, ld, st, w);
   }
   return SPARC_ERR_INVALID_ARG;
+}
+
+sparc_status sparc_cheb_filter_batch(sparc_ham* const* H, int nk, sparc_dtype dtype, int m, const double* a,
+                                     const double* b, const double* a0, const void* X, void* Y, int ns,
+                                     int64_t ld, void* stream) {
+  if (!H || nk < 1 || !H[0]) return SPARC_ERR_INVALID_ARG;
+  sparc_ctx* ctx = H[0]->ctx;
+  if (!a || !b || !a0) return fail(ctx, SPARC_ERR_INVALID_ARG, "null bounds array");
+  if ((int)dtype < 0 || (int)dtype > 3) return fail(ctx, SPARC_ERR_INVALID_ARG, "unknown dtype");
+  if (m < 1) return fail(ctx, SPARC_ERR_INVALID_ARG, "m must be >= 1");
+  if (ns < 1 || ld < H[0]->gd.nd || !X || !Y) return fail(ctx, SPARC_ERR_INVALID_ARG, "bad ns, ld, X or Y");
+  const size_t es = dtype_size(dtype);
+  const size_t kx = (size_t)ns * (size_t)ld;
+  const size_t span = ((size_t)(nk - 1) * kx + (size_t)(ns - 1) * (size_t)ld + (size_t)H[0]->gd.nd) * es;
+  const char* x0 = (const char*)X;
+  const char* y0 = (const char*)Y;
+  if (x0 < y0 + span && y0 < x0 + span) return fail(ctx, SPARC_ERR_INVALID_ARG, "X and Y overlap");
+  bool batch = dtype == SPARC_C64;
+  for (int k = 0; k < nk; ++k) {
+    sparc_ham* Hk = H[k];
+    if (!Hk || Hk->ctx != ctx) return fail(ctx, SPARC_ERR_INVALID_ARG, "Hamiltonians must share one context");
+    for (int s3 = 0; s3 < 3; ++s3)
+      if (Hk->grid.n[s3] != H[0]->grid.n[s3] || Hk->grid.h[s3] != H[0]->grid.h[s3])
+        return fail(ctx, SPARC_ERR_INVALID_ARG, "Hamiltonians of a batch must share the grid");
+    if (Hk->grid.fd_radius != H[0]->grid.fd_radius || Hk->nproj != H[0]->nproj)
+      return fail(ctx, SPARC_ERR_INVALID_ARG, "Hamiltonians of a batch must share the stencil and projectors");
+    if (!(a0[k] < a[k] && a[k] < b[k]) || !isfinite(a0[k]) || !isfinite(b[k]))
+      return fail(ctx, SPARC_ERR_INVALID_ARG, "filter bounds must satisfy a0 < a < b");
+    sparc_status s = check_block_args(Hk, dtype, x0 + k * kx * es, y0 + k * kx * es, ns, ld);
+    if (s != SPARC_OK) return s;
+    batch = batch && fast::usable(Hk) && fast::geometry_hash(Hk) == fast::geometry_hash(H[0]);
+  }
+  SPARC_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!batch) {
+    for (int k = 0; k < nk; ++k) {
+      sparc_status s = sparc_cheb_filter(H[k], dtype, m, a[k], b[k], a0[k], x0 + k * kx * es,
+                                         (char*)Y + k * kx * es, ns, ld, stream);
+      if (s != SPARC_OK) return s;
+    }
+    return SPARC_OK;
+  }
+  return filter_kbatch(H, nk, m, a, b, a0, (const cf32*)X, (cf32*)Y, ns, ld, st);
+}
+
+sparc_status sparc_set_filter_units(sparc_ctx* ctx, sparc_dtype dtype, int64_t nd, int ns, int nk, int units) {
+  if (!ctx) return SPARC_ERR_INVALID_ARG;
+  if ((int)dtype < 0 || (int)dtype > 3 || nd < 1 || ns < 1 || nk < 1 || units < 0)
+    return fail(ctx, SPARC_ERR_INVALID_ARG, "bad filter-units key or value");
+  const auto key = std::make_tuple((int)dtype, (long long)nd, ns, nk);
+  if (units == 0) ctx->tuned.erase(key);
+  else ctx->tuned[key] = units;
+  return SPARC_OK;
+}
+
+sparc_status sparc_autotune_filter(sparc_ham* const* H, int nk, sparc_dtype dtype, int m, const double* a,
+                                   const double* b, const double* a0, const void* X, void* Y, int ns,
+                                   int64_t ld, void* stream, int* units, double* ms) {
+  if (!H || nk < 1 || !H[0]) return SPARC_ERR_INVALID_ARG;
+  sparc_ctx* ctx = H[0]->ctx;
+  const bool kb = dtype == SPARC_C64 && nk > 1;
+  const bool f32 = dtype == SPARC_F32 && nk == 1;
+  const int nblk = ceil_div(std::max(ns, 1), NB);
+  const auto key = std::make_tuple((int)dtype, H[0]->gd.nd, ns, nk);
+  // candidate units per launch: multiples and fractions of the L2-sized group
+  const size_t per_unit = 2 * (size_t)H[0]->gd.nd * NB * (dtype == SPARC_F32 ? 4 : 8);
+  const int l2u = (int)std::max<size_t>(1, (size_t)90 * 1024 * 1024 / per_unit);
+  std::vector<int> cand;
+  if (kb || f32) {
+    for (int f : {1, 2, 4}) cand.push_back(std::max(1, l2u / f));
+    for (int f : {2, 4, 8}) cand.push_back(l2u * f);
+    cand.push_back(nblk);
+    if (kb) cand.push_back(nk * nblk);
+    std::sort(cand.begin(), cand.end());
+    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    if (f32) cand.erase(std::remove_if(cand.begin(), cand.end(), [&](int u) { return u > nblk; }), cand.end());
+  }
+  const int mt = std::min(m, 3);
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->tuned.erase(key);
+  if (cand.empty()) {   // nothing to tune for this type: the filter has one launch shape
+    if (units) *units = 0;
+    if (ms) *ms = 0.0;
+    return sparc_cheb_filter_batch(H, nk, dtype, mt, a, b, a0, X, Y, ns, ld, stream);
+  }
+  cudaEvent_t e0, e1;
+  SPARC_CUDA(ctx, cudaSetDevice(ctx->device));
+  SPARC_CUDA(ctx, cudaEventCreate(&e0));
+  SPARC_CUDA(ctx, cudaEventCreate(&e1));
+  int best_u = 0;
+  double best_ms = 1e300;
+  for (int u : cand) {
+    ctx->tuned[key] = u;
+    double tmin = 1e300;
+    for (int rep = 0; rep < 3; ++rep) {   // the first run warms up
+      cudaEventRecord(e0, st);
+      sparc_status s = sparc_cheb_filter_batch(H, nk, dtype, mt, a, b, a0, X, Y, ns, ld, stream);
+      if (s != SPARC_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); ctx->tuned.erase(key); return s; }
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        cudaEventDestroy(e0); cudaEventDestroy(e1);
+        ctx->tuned.erase(key);
+        return cuda_fail(ctx, cudaGetLastError(), "autotune timing");
+      }
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (rep > 0) tmin = std::min(tmin, (double)t);
+    }
+    if (tmin < best_ms) { best_ms = tmin; best_u = u; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->tuned[key] = best_u;
+  if (units) *units = best_u;
+  if (ms) *ms = best_ms;
+  return SPARC_OK;
 }
 
 }  // extern "C"

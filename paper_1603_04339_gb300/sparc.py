@@ -26,7 +26,8 @@ EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_sync", "s
            "sparc_lanczos_bounds", "sparc_rayleigh_ritz", "sparc_timing_enable", "sparc_timing_read",
            "sparc_launch_count", "sparc_apply_H_noalloc", "sparc_last_sweeps", "sparc_gram_f32",
            "sparc_rotate_f32", "sparc_scf_create", "sparc_scf_step", "sparc_scf_read", "sparc_scf_destroy",
-           "sparc_scf_forces"]
+           "sparc_scf_forces", "sparc_cheb_filter_batch", "sparc_autotune_filter",
+           "sparc_set_filter_units"]
 TIMED = {"hpass": 0, "gather": 1, "gram": 2, "eig": 3, "rotation": 4, "jacobi": 5, "fpass": 6}
 
 
@@ -109,6 +110,13 @@ def load(path: str = LIB_PATH):
                                  POINTER(SparcScfInfo), c_void_p]
     L.sparc_scf_read.argtypes = [c_void_p, c_int, c_void_p, c_void_p]
     L.sparc_scf_forces.argtypes = [c_void_p, c_int, c_void_p, c_int, c_int64, POINTER(c_double), c_void_p]
+    L.sparc_cheb_filter_batch.argtypes = [POINTER(c_void_p), c_int, c_int, c_int, POINTER(c_double),
+                                          POINTER(c_double), POINTER(c_double), c_void_p, c_void_p, c_int,
+                                          c_int64, c_void_p]
+    L.sparc_autotune_filter.argtypes = [POINTER(c_void_p), c_int, c_int, c_int, POINTER(c_double),
+                                        POINTER(c_double), POINTER(c_double), c_void_p, c_void_p, c_int,
+                                        c_int64, c_void_p, POINTER(c_int), POINTER(c_double)]
+    L.sparc_set_filter_units.argtypes = [c_void_p, c_int, c_int64, c_int, c_int, c_int]
     L.sparc_scf_destroy.argtypes = [c_void_p]
     L.sparc_scf_destroy.restype = None
     for name in ("sparc_timing_enable", "sparc_timing_read", "sparc_create", "sparc_sync", "sparc_ham_create", "sparc_ham_set_veff",
@@ -308,6 +316,43 @@ def sparc_cheb_filter(H: Hamiltonian, m, a, b, a0, X, Y, ns=None, ld=None, strea
     dt = dtype_code(X) if dtype is None else dtype
     H.ctx.check(load().sparc_cheb_filter(H.handle, dt, int(m), float(a), float(b), float(a0), _ptr(X),
                                          _ptr(Y), int(ns), int(ld), _stream(stream)))
+
+
+def _batch_args(Hs, a, b, a0):
+    nk = len(Hs)
+    hs = (c_void_p * nk)(*[h.handle for h in Hs])
+    arr = [(c_double * nk)(*[float(v) for v in x]) for x in (a, b, a0)]
+    return nk, hs, arr
+
+
+def sparc_cheb_filter_batch(Hs, m, a, b, a0, X, Y, stream=None, dtype=None):
+    """The filter for Hamiltonians Hs[k] that differ only in k, in shared launches.
+
+    X, Y: CUDA tensors of shape (nk, ns, ld) (block k = orbitals of k-point k);
+    a, b, a0: sequences of nk bounds."""
+    nk, hs, (aa, bb, cc) = _batch_args(Hs, a, b, a0)
+    assert X.shape[0] == nk and Y.shape == X.shape
+    dt = dtype_code(X) if dtype is None else dtype
+    Hs[0].ctx.check(load().sparc_cheb_filter_batch(hs, nk, dt, int(m), aa, bb, cc, _ptr(X), _ptr(Y),
+                                                   int(X.shape[1]), int(X.shape[2]), _stream(stream)))
+
+
+def sparc_autotune_filter(Hs, m, a, b, a0, X, Y, stream=None, dtype=None):
+    """Time the filter's launch shapes on (X, Y) and keep the fastest; returns (units, ms)."""
+    nk, hs, (aa, bb, cc) = _batch_args(Hs, a, b, a0)
+    if X.dim() == 2:
+        X, Y = X.unsqueeze(0), Y.unsqueeze(0)
+    dt = dtype_code(X) if dtype is None else dtype
+    units, ms = c_int(), c_double()
+    Hs[0].ctx.check(load().sparc_autotune_filter(hs, nk, dt, int(m), aa, bb, cc, _ptr(X), _ptr(Y),
+                                                 int(X.shape[1]), int(X.shape[2]), _stream(stream),
+                                                 ctypes.byref(units), ctypes.byref(ms)))
+    return units.value, ms.value
+
+
+def sparc_set_filter_units(ctx: Context, dtype, nd, ns, nk, units):
+    """Pin (units > 0) or clear (0) the orbital blocks per filter launch for (dtype, Nd, ns, nk)."""
+    ctx.check(load().sparc_set_filter_units(ctx.handle, int(dtype), int(nd), int(ns), int(nk), int(units)))
 
 
 def sparc_lanczos_bounds(H: Hamiltonian, ksteps, v0, stream=None):
