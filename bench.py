@@ -42,7 +42,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-scf", action="store_true", help="skip the SCF time-to-solution comparison")
     ap.add_argument("--no-kpoints", action="store_true",
-                    help="skip the 27-k-point complex64 filter throughput (batched and per k)")
+                    help="skip the batched filters: 27 k-points (complex64) and 16 uneven cells (FP32 graph)")
     ap.add_argument("--cpu-sample-cols", type=int, default=1)
     ap.add_argument("--mode", choices=["step", "filter", "kpoints"], default="step",
                     help="filter: only the Chebyshev filter (for profiler captures); "
@@ -234,6 +234,58 @@ def kpoint_filter_throughput(sparc, synth, torch, ctx, reps=2, tune=True):
                          "frac_batched": work / (ms_b * 1e-3) / 1e9 / (_peaks()[0] / 24.0)}}
 
 
+def cell_batch_throughput(sparc, synth, torch, ctx, reps=3, nbranch=8):
+    """FP32 filters of the uneven batch of 16 independent cells (grids 24^3..48^3,
+    slab and wire shapes, Ns 48..384, m 16..24): one sparc_cheb_filter per cell on
+    one stream against the same filters replayed from one CUDA graph with up to
+    `nbranch` concurrent branches; launch groupings autotuned per cell first."""
+    import numpy as np
+    cells = synth.config4()
+    Hs = [sparc.Hamiltonian.from_workload(ctx, c) for c in cells]
+    X = [torch.from_numpy(synth.random_orbitals(c.nd, c.ns, 5000 + i).astype(np.float32)).cuda()
+         for i, c in enumerate(cells)]
+    Y = [torch.empty_like(x) for x in X]
+    m = [c.m for c in cells]
+    a0 = [-2.5] * len(cells)
+    b = [60.0] * len(cells)
+    a = [a0[i] + (b[i] - a0[i]) * (c.ns / c.nd) ** (2.0 / 3.0) for i, c in enumerate(cells)]
+    for i, H in enumerate(Hs):
+        sparc.sparc_autotune_filter([H], m[i], [a[i]], [b[i]], [a0[i]], X[i], Y[i])
+    G = sparc.FilterGraph(Hs, m, a, b, a0, X, Y, nbranch=nbranch)
+    work = sum(c.nd * c.ns * c.m for c in cells)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0 = ctx.launches()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, (ctx.launches() - n0) // reps
+
+    def per_cell():
+        for i, H in enumerate(Hs):
+            sparc.sparc_cheb_filter(H, m[i], a[i], b[i], a0[i], X[i], Y[i])
+
+    def graph():
+        G.launch(torch.cuda.current_stream())
+
+    ms_s, l_s = timed(per_cell)
+    ms_g, l_g = timed(graph)
+    G.close()
+    for H in Hs:
+        H.close()
+    return {"workload": "16 independent cells: grids {24^3, 32^3, 40x40x64 slab, 24x24x96 wire, 48^3} at h=0.45, "
+                        "8-95 s+p atoms, Ns 48-384, m 16-24, FP32, Gamma",
+            "graph": {"value": work / (ms_g * 1e-3) / 1e9, "unit": "Gpt-orb-deg/s", "ms_per_batch": ms_g,
+                      "kernels_per_batch": l_g, "branches": nbranch},
+            "per_cell": {"value": work / (ms_s * 1e-3) / 1e9, "unit": "Gpt-orb-deg/s", "ms_per_batch": ms_s,
+                         "launches_per_batch": l_s}}
+
+
 def run_kpoints(args):
     import json as _json
     import torch
@@ -243,6 +295,8 @@ def run_kpoints(args):
     ctx = sparc.Context(0)
     out = kpoint_filter_throughput(sparc, synth, torch, ctx, reps=max(1, args.steps))
     print(_json.dumps({"mode": "kpoints", **out}), flush=True)
+    out = cell_batch_throughput(sparc, synth, torch, ctx, reps=max(1, args.steps))
+    print(_json.dumps({"mode": "cells", **out}), flush=True)
     return 0
 
 
@@ -471,6 +525,7 @@ def run_ours(args):
         "clocks": ck, "e2e": e2e, "gpu_launches": int(launches), "cpu_baseline": cpu,
         "scf": None if (args.no_scf or world > 1) else scf_time_to_solution(sparc, synth, torch),
         "kpoints": None if (args.no_kpoints or world > 1) else kpoint_filter_throughput(sparc, synth, torch, ctx),
+        "cells": None if (args.no_kpoints or world > 1) else cell_batch_throughput(sparc, synth, torch, ctx),
     }
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -190,6 +190,36 @@ sparc_status sparc_autotune_filter(sparc_ham* const* H, int nk, sparc_dtype dtyp
 sparc_status sparc_set_filter_units(sparc_ctx* ctx, sparc_dtype dtype, int64_t nd, int ns, int nk,
                                     int units);
 
+/* Filter graph: the filters of ncell independent cells -- each its own
+ * Hamiltonian (grid, projectors), ns, ld and degree m -- captured once into one
+ * CUDA graph whose branches (up to nbranch concurrent streams, cell i on branch
+ * i % nbranch) run at the same time, so that small cells fill the GPU together;
+ * one sparc_filter_graph_launch then runs every filter of the batch.  Each cell
+ * gets its own workspace, allocated here.  The launch shape of every cell is
+ * the one its filter call would take when the graph is captured, including a
+ * grouping chosen by sparc_autotune_filter (tune the cells first).
+ *   H[ncell]: Hamiltonians on one context; m, a, b, a0, ns, ld: host arrays
+ *   [ncell]; X[ncell], Y[ncell]: device pointers per cell (layout as
+ *   sparc_cheb_filter).  The buffers must stay valid while the graph exists.
+ * Result of a launch: Y[i] equals sparc_cheb_filter(H[i], dtype, m[i], a[i],
+ * b[i], a0[i], X[i], Y[i], ns[i], ld[i]) bit for bit.  Synchronous; no stream
+ * capture may be active on the calling thread. */
+typedef struct sparc_filter_graph sparc_filter_graph;
+sparc_status sparc_filter_graph_create(sparc_ham* const* H, int ncell, sparc_dtype dtype,
+                                       const int* m, const double* a, const double* b,
+                                       const double* a0, const void* const* X, void* const* Y,
+                                       const int* ns, const int64_t* ld, int nbranch,
+                                       sparc_filter_graph** G);
+/* New filter bounds for every cell (host arrays [ncell]): re-captures and
+ * updates the executable graph in place.  Synchronous. */
+sparc_status sparc_filter_graph_set_bounds(sparc_filter_graph* G, const double* a,
+                                           const double* b, const double* a0);
+/* Run the graph on `stream` (asynchronous). */
+sparc_status sparc_filter_graph_launch(sparc_filter_graph* G, void* stream);
+/* Free the graph and its workspaces (synchronises the device).  Uses no state
+ * of its context, so it may follow sparc_destroy of that context. */
+void sparc_filter_graph_destroy(sparc_filter_graph* G);
+
 /* Extremal-eigenvalue estimates by `ksteps` Lanczos steps with full
  * reorthogonalisation, in FP64 (Section 4: filter bounds by the Lanczos method).
  * v0: device start vector, Nd elements of F64 (k = 0) or C128 (k != 0); it is

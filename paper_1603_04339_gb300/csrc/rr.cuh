@@ -23,6 +23,13 @@ sparc_status apply_block(sparc_ham* H, const T* X, T* Y, int ns, long long ld, c
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Bytes of workspace one filter call of (H, dtype, ns) needs; with `base`, also lay
+// the block workspace out there.
+size_t filter_ws(sparc_ham* H, sparc_dtype dt, int ns, char* base, BlockWs* w);
+// The filter on a caller-laid-out workspace (arguments already checked).
+sparc_status filter_run(sparc_ham* H, sparc_dtype dtype, int m, double a, double b, double a0, const void* X,
+                        void* Y, int ns, long long ld, cudaStream_t st, const BlockWs& w);
+
 // Tensor-core (tcgen05, 3xTF32) products of FP32 orbitals (tc_gemm.cu).
 namespace tc {
 // G = A^T B (ns x ns, FP64, symmetrised) for column-major nd x ns FP32 A, B.

@@ -304,6 +304,39 @@ sparc_status filter_block_fast(sparc_ham* H, int m, double a, double b, double a
   return SPARC_OK;
 }
 
+size_t filter_ws(sparc_ham* H, sparc_dtype dt, int ns, char* base, BlockWs* w) {
+  const size_t es = dtype_size(dt);
+  const int nblk = ceil_div(ns, NB);
+  const size_t bb = align256((size_t)nblk * H->gd.nd * NB * es);
+  const size_t gb = align256((size_t)std::max(1, H->nproj) * nblk * NB * es);
+  size_t extra = 0;
+  if ((dt == SPARC_F32 || dt == SPARC_C64) && fast::usable(H)) extra = fast::gather_scratch_bytes(H, nblk, es);
+  if (base) {
+    w->b0 = base;
+    w->b1 = base + bb;
+    w->gc = base + 2 * bb;
+    w->tail = base + 2 * bb + gb;
+  }
+  return 2 * bb + gb + extra;
+}
+
+sparc_status filter_run(sparc_ham* H, sparc_dtype dtype, int m, double a, double b, double a0, const void* X,
+                        void* Y, int ns, long long ld, cudaStream_t st, const BlockWs& w) {
+  switch (dtype) {
+    case SPARC_F64:
+      return filter_block<double>(H, m, a, b, a0, (const double*)X, (double*)Y, ns, ld, st, w);
+    case SPARC_F32:
+      if (fast::usable(H)) return filter_block_fast<float>(H, m, a, b, a0, (const float*)X, (float*)Y, ns, ld, st, w);
+      return filter_block<float>(H, m, a, b, a0, (const float*)X, (float*)Y, ns, ld, st, w);
+    case SPARC_C128:
+      return filter_block<cf64>(H, m, a, b, a0, (const cf64*)X, (cf64*)Y, ns, ld, st, w);
+    case SPARC_C64:
+      if (fast::usable(H)) return filter_block_fast<cf32>(H, m, a, b, a0, (const cf32*)X, (cf32*)Y, ns, ld, st, w);
+      return filter_block<cf32>(H, m, a, b, a0, (const cf32*)X, (cf32*)Y, ns, ld, st, w);
+  }
+  return fail(H->ctx, SPARC_ERR_INVALID_ARG, "unknown dtype");
+}
+
 // Launch grouping of a k batch: nkg k-points x nbk of their blocks per launch.
 // Minimises the modelled time -- waves of one-CTA-per-SM work items plus 0.05
 // wave per launch pair -- over groupings of at most `upl` units (0: any).
@@ -711,31 +744,11 @@ sparc_status sparc_cheb_filter(sparc_ham* H, sparc_dtype dtype, int m, double a,
   sparc_status s = check_block_args(H, dtype, X, Y, ns, ld);
   if (s != SPARC_OK) return s;
   SPARC_CUDA(H->ctx, cudaSetDevice(H->ctx->device));
+  if (!ensure_ws(H->ctx, filter_ws(H, dtype, ns, nullptr, nullptr)))
+    return fail(H->ctx, SPARC_ERR_OOM, "workspace allocation failed");
   BlockWs w;
-  s = block_ws(H, dtype, ns, 0, &w, nullptr);
-  if (s != SPARC_OK) return s;
-  cudaStream_t st = (cudaStream_t)stream;
-  switch (dtype) {
-    case SPARC_F64:
-      return filter_block<double>(H, m, a, b, a0, (const double*)X, (double*)Y, ns, ld, st, w);
-    case SPARC_F32:
-      if (fast::usable(H)) {
-        s = block_ws(H, dtype, ns, fast::gather_scratch_bytes(H, ceil_div(ns, NB), sizeof(float)), &w, nullptr);
-        if (s != SPARC_OK) return s;
-        return filter_block_fast<float>(H, m, a, b, a0, (const float*)X, (float*)Y, ns, ld, st, w);
-      }
-      return filter_block<float>(H, m, a, b, a0, (const float*)X, (float*)Y, ns, ld, st, w);
-    case SPARC_C128:
-      return filter_block<cf64>(H, m, a, b, a0, (const cf64*)X, (cf64*)Y, ns, ld, st, w);
-    case SPARC_C64:
-      if (fast::usable(H)) {
-        s = block_ws(H, dtype, ns, fast::gather_scratch_bytes(H, ceil_div(ns, NB), sizeof(cf32)), &w, nullptr);
-        if (s != SPARC_OK) return s;
-        return filter_block_fast<cf32>(H, m, a, b, a0, (const cf32*)X, (cf32*)Y, ns, ld, st, w);
-      }
-      return filter_block<cf32>(H, m, a, b, a0, (const cf32*)X, (cf32*)Y, ns, ld, st, w);
-  }
-  return SPARC_ERR_INVALID_ARG;
+  filter_ws(H, dtype, ns, (char*)H->ctx->ws, &w);
+  return filter_run(H, dtype, m, a, b, a0, X, Y, ns, ld, (cudaStream_t)stream, w);
 }
 
 sparc_status sparc_cheb_filter_batch(sparc_ham* const* H, int nk, sparc_dtype dtype, int m, const double* a,

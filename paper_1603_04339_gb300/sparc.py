@@ -27,7 +27,8 @@ EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_sync", "s
            "sparc_launch_count", "sparc_apply_H_noalloc", "sparc_last_sweeps", "sparc_gram_f32",
            "sparc_rotate_f32", "sparc_scf_create", "sparc_scf_step", "sparc_scf_read", "sparc_scf_destroy",
            "sparc_scf_forces", "sparc_cheb_filter_batch", "sparc_autotune_filter",
-           "sparc_set_filter_units"]
+           "sparc_set_filter_units", "sparc_filter_graph_create", "sparc_filter_graph_set_bounds",
+           "sparc_filter_graph_launch", "sparc_filter_graph_destroy"]
 TIMED = {"hpass": 0, "gather": 1, "gram": 2, "eig": 3, "rotation": 4, "jacobi": 5, "fpass": 6}
 
 
@@ -117,6 +118,15 @@ def load(path: str = LIB_PATH):
                                         POINTER(c_double), POINTER(c_double), c_void_p, c_void_p, c_int,
                                         c_int64, c_void_p, POINTER(c_int), POINTER(c_double)]
     L.sparc_set_filter_units.argtypes = [c_void_p, c_int, c_int64, c_int, c_int, c_int]
+    L.sparc_filter_graph_create.argtypes = [POINTER(c_void_p), c_int, c_int, POINTER(c_int), POINTER(c_double),
+                                            POINTER(c_double), POINTER(c_double), POINTER(c_void_p),
+                                            POINTER(c_void_p), POINTER(c_int), POINTER(c_int64), c_int,
+                                            POINTER(c_void_p)]
+    L.sparc_filter_graph_set_bounds.argtypes = [c_void_p, POINTER(c_double), POINTER(c_double),
+                                                POINTER(c_double)]
+    L.sparc_filter_graph_launch.argtypes = [c_void_p, c_void_p]
+    L.sparc_filter_graph_destroy.argtypes = [c_void_p]
+    L.sparc_filter_graph_destroy.restype = None
     L.sparc_scf_destroy.argtypes = [c_void_p]
     L.sparc_scf_destroy.restype = None
     for name in ("sparc_timing_enable", "sparc_timing_read", "sparc_create", "sparc_sync", "sparc_ham_create", "sparc_ham_set_veff",
@@ -167,6 +177,7 @@ class Context:
         self.device = device
         self._hams = weakref.WeakSet()   # Hamiltonians of this context, closed with it
         self._scfs = weakref.WeakSet()   # SCF states, closed before the Hamiltonians
+        self._graphs = weakref.WeakSet()  # filter graphs, closed before the Hamiltonians
 
     def error(self) -> str:
         return load().sparc_last_error(self.handle).decode()
@@ -202,6 +213,8 @@ class Context:
 
     def close(self):
         if self.handle:
+            for Gr in list(self._graphs):
+                Gr.close()
             for S in list(self._scfs):
                 S.close()
             for H in list(self._hams):
@@ -353,6 +366,49 @@ def sparc_autotune_filter(Hs, m, a, b, a0, X, Y, stream=None, dtype=None):
 def sparc_set_filter_units(ctx: Context, dtype, nd, ns, nk, units):
     """Pin (units > 0) or clear (0) the orbital blocks per filter launch for (dtype, Nd, ns, nk)."""
     ctx.check(load().sparc_set_filter_units(ctx.handle, int(dtype), int(nd), int(ns), int(nk), int(units)))
+
+
+class FilterGraph:
+    """The filters of independent cells captured into one CUDA graph (sparc_filter_graph_*).
+
+    Hs, m, a, b, a0: per cell; X, Y: per-cell CUDA tensors of shape (ns, ld)."""
+
+    def __init__(self, Hs, m, a, b, a0, X, Y, nbranch=8, dtype=None):
+        n = len(Hs)
+        self.ctx = Hs[0].ctx
+        self._keep = (list(Hs), list(X), list(Y))
+        dt = dtype_code(X[0]) if dtype is None else dtype
+        hs = (c_void_p * n)(*[h.handle for h in Hs])
+        xs = (c_void_p * n)(*[_ptr(x) for x in X])
+        ys = (c_void_p * n)(*[_ptr(y) for y in Y])
+        ms = (c_int * n)(*[int(v) for v in m])
+        nss = (c_int * n)(*[int(x.shape[0]) for x in X])
+        lds = (c_int64 * n)(*[int(x.shape[-1]) for x in X])
+        dv = lambda v: (c_double * n)(*[float(t) for t in v])
+        self.n = n
+        h = c_void_p()
+        self.ctx.check(load().sparc_filter_graph_create(hs, n, dt, ms, dv(a), dv(b), dv(a0), xs, ys, nss, lds,
+                                                        int(nbranch), ctypes.byref(h)))
+        self.handle = h
+        self.ctx._graphs.add(self)
+
+    def set_bounds(self, a, b, a0):
+        dv = lambda v: (c_double * self.n)(*[float(t) for t in v])
+        self.ctx.check(load().sparc_filter_graph_set_bounds(self.handle, dv(a), dv(b), dv(a0)))
+
+    def launch(self, stream=None):
+        self.ctx.check(load().sparc_filter_graph_launch(self.handle, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().sparc_filter_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sparc_lanczos_bounds(H: Hamiltonian, ksteps, v0, stream=None):

@@ -96,15 +96,11 @@ def gaussian_veff(n, h, sites, depth, width, noise=0.0, rng=None):
     """V_eff(x) = sum_sites sum_{27 images} d * exp(-|x - R - T|^2 / w^2) (+ N(0, noise))."""
     xs = node_coords(n, h)
     L = np.array([n[s] * h[s] for s in range(3)])
-    Z, Y, X = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
-    v = np.zeros(Z.shape, dtype=np.float64)
+    v = np.zeros((n[2], n[1], n[0]), dtype=np.float64)
     for R, d, w in zip(sites, depth, width):
-        for tz in (-1, 0, 1):
-            for ty in (-1, 0, 1):
-                for tx in (-1, 0, 1):
-                    c = R + np.array([tx, ty, tz]) * L
-                    r2 = (X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2
-                    v += d * np.exp(-r2 / (w * w))
+        # the Gaussian and the 3x3x3 image set are both products over axes
+        g = [sum(np.exp(-((xs[s] - R[s] - t * L[s]) ** 2) / (w * w)) for t in (-1, 0, 1)) for s in range(3)]
+        v += d * (g[2][:, None, None] * g[1][None, :, None] * g[0][None, None, :])
     v = v.reshape(-1)
     if noise > 0.0:
         v = v + rng.normal(0.0, noise, size=v.shape)
@@ -258,6 +254,43 @@ def config3(seed=1003) -> Workload:
     kpts, kw = monkhorst_pack((3, 3, 3), (L, L, L))
     return Workload("config3_40^3_64atoms_27k_ns192_m20", n, h, 6, kpts, kw, veff, atoms, proj,
                     192, 20, seed)
+
+
+CELL_GRIDS = (("cube24", (24, 24, 24)), ("cube32", (32, 32, 32)), ("slab40x40x64", (40, 40, 64)),
+              ("wire24x24x96", (24, 24, 96)), ("cube48", (48, 48, 48)))
+
+
+def config4(seed=1004, ncell=16, h=0.45) -> list:
+    """Uneven batch of independent Gamma-point cells for the filter graph.
+
+    Per cell, drawn from the seed: the grid from {24^3, 32^3, 40x40x64 slab, 24x24x96
+    wire, 48^3} at h = 0.45 bohr; 8..96 s+p atoms, at most one per 60 bohr^3 of the
+    occupied region (slab: the middle half in z; wire: the middle half of each
+    cross-section axis; cubes: everything), uniform there; V_eff = atom Gaussians
+    (depth U[-2,0], width U[0.8,1.5]) + N(0, 0.01); projector width 1.0 bohr,
+    energies U[-1,1]; Ns = 4 x atoms x U[0.8,1.2] clipped to [48, 384]; m from
+    {16, 20, 24}."""
+    rng = np.random.default_rng(seed)
+    cells = []
+    for c in range(ncell):
+        kind, n = CELL_GRIDS[int(rng.integers(len(CELL_GRIDS)))]
+        hh = (h, h, h)
+        L = np.array([n[s] * h for s in range(3)])
+        occ = np.ones(3)
+        if kind.startswith("slab"):
+            occ[2] = 0.5
+        elif kind.startswith("wire"):
+            occ[0] = occ[1] = 0.5
+        vol = float(np.prod(L * occ))
+        natom = int(rng.integers(8, max(9, min(96, int(vol / 60.0)) + 1)))
+        atoms = (rng.uniform(-0.5, 0.5, size=(natom, 3)) * occ) * L
+        veff = _atoms_veff(n, hh, atoms, rng, 0.01)
+        proj = make_projectors(n, hh, atoms, 1.0, rng.uniform(-1, 1, natom), rng.uniform(-1, 1, natom))
+        ns = int(np.clip(round(4 * natom * rng.uniform(0.8, 1.2)), 48, 384))
+        m = int(rng.choice([16, 20, 24]))
+        cells.append(Workload(f"cell{c:02d}_{kind}_{natom}atoms_ns{ns}_m{m}", tuple(n), hh, 6, np.zeros((1, 3)),
+                              np.ones(1), veff, atoms, proj, ns, m, seed * 100 + c))
+    return cells
 
 
 def small_case(n=(14, 12, 13), h=(0.55, 0.6, 0.5), fd_radius=6, natom=2, k=(0.0, 0.0, 0.0),
