@@ -300,33 +300,51 @@ def run_kpoints(args):
     return 0
 
 
-def scf_time_to_solution(sparc, synth, torch, tol_per_atom=1e-5, max_iter=60):
-    """SCF on the 32-atom FCC cell (36^3 grid): the FP64 path run to V residual 1e-9
-    gives the reference free energy; for the FP64 and the mixed (FP32 orbitals) paths,
-    the device time until the free energy is within tol_per_atom per atom of it."""
+def scf_time_to_solution(sparc, synth, torch, tol_per_atom=1e-5, max_iter=80, train_cells=12):
+    """SCF on the 32-atom FCC cell (36^3 grid, Ns=72): the FP64 path run to V residual
+    1e-9 gives the reference free energy; for the FP64 path, the mixed path (FP32
+    orbitals) and the mixed path started from the learned density, the device time
+    until the free energy stays within tol_per_atom per atom of it.  The network is
+    trained first, with the library's kernels, on converged densities of
+    `train_cells` other seeded cells (its training time is reported apart; the
+    learned arm's time includes the descriptors and the prediction)."""
     import time as _t
+    from paper_1603_04339_gb300 import learned_density as LD
     sysd = synth.scf_fcc32()
     wl = sysd.wl
     natom = len(sysd.Z)
+    ctx = sparc.Context(torch.cuda.current_device())
+    t0 = _t.perf_counter()
+    D, T, _ = LD.dataset(ctx, range(2000, 2000 + train_cells), torch.float32)
+    t_data = _t.perf_counter() - t0
+    t0 = _t.perf_counter()
+    net, scale, lhist = LD.train(ctx, D, T, epochs=40)
+    torch.cuda.synchronize()
+    t_train = _t.perf_counter() - t0
+    del D, T
     runs = {}
-    for name, dt in (("fp64", torch.float64), ("mixed", torch.float32)):
-        ctx = sparc.Context(torch.cuda.current_device())
+    for name, dt in (("fp64", torch.float64), ("mixed", torch.float32), ("mixed_learned", torch.float32)):
         H = sparc.Hamiltonian.from_workload(ctx, wl)
-        S = sparc.Scf.from_system(H, sysd, kT=0.01, mix_beta=0.3, mix_history=7, poisson_tol=1e-10)
+        S = sparc.Scf.from_system(H, sysd, kT=0.01, mix_beta=0.3, mix_history=7, poisson_tol=1e-10, first_passes=4)
         U = torch.from_numpy(sysd.U0.copy()).to(dt).cuda()
         eig = torch.zeros(wl.ns, dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
         t0 = _t.perf_counter()
+        if name == "mixed_learned":
+            S.set_density(LD.predict(ctx, net, sysd), scale)
         hist = []
         for it in range(max_iter):
             info = sparc.sparc_scf_step(S, U, eig, wl.m)   # synchronises its stream
             hist.append((_t.perf_counter() - t0, info["free_energy"], info["vresid"]))
             if name == "fp64" and info["vresid"] < 1e-9:
                 break
-            if name == "mixed" and it >= 5 and info["vresid"] < 1e-6:
+            if name != "fp64" and it >= 5 and info["vresid"] < 1e-6:
                 break
         runs[name] = hist
-        ctx.close()
+        S.close()
+        H.close()
+    net.close()
+    ctx.close()
     E_ref = runs["fp64"][-1][1]
 
     def reach(hist):
@@ -335,14 +353,18 @@ def scf_time_to_solution(sparc, synth, torch, tol_per_atom=1e-5, max_iter=60):
                 return k + 1, t
         return None, None
 
-    out = {"workload": "32-atom perturbed-FCC cell, 36^3 grid h=0.45, Z=3 (N_e=96), Ns=58, m=20, "
-                       "kT=0.01 Ha, Anderson 0.3/7", "tolerance_ha_per_atom": tol_per_atom, "E_ref_ha": E_ref}
+    out = {"workload": "32-atom perturbed-FCC cell, 36^3 grid h=0.45, Z=3 (N_e=96), Ns=72, m=20, "
+                       "kT=0.01 Ha, Anderson 0.3/7, 4 CheFSI passes at the first iteration",
+           "tolerance_ha_per_atom": tol_per_atom, "E_ref_ha": E_ref,
+           "learned": {"train_cells": train_cells, "data_seconds": t_data, "train_seconds": t_train,
+                       "loss_initial": lhist[0], "loss_final": lhist[-1]}}
     for name, hist in runs.items():
         k, t = reach(hist)
         out[name] = {"iterations_to_tol": k, "seconds_to_tol": t, "iterations_run": len(hist),
                      "final_vresid": hist[-1][2], "final_dE_per_atom": abs(hist[-1][1] - E_ref) / natom}
-    if out["fp64"]["seconds_to_tol"] and out["mixed"]["seconds_to_tol"]:
-        out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds_to_tol"] / out["mixed"]["seconds_to_tol"]
+    for arm in ("mixed", "mixed_learned"):
+        if out["fp64"]["seconds_to_tol"] and out[arm]["seconds_to_tol"]:
+            out["speedup_" + arm + "_vs_fp64"] = out["fp64"]["seconds_to_tol"] / out[arm]["seconds_to_tol"]
     return out
 
 

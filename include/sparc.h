@@ -220,6 +220,47 @@ sparc_status sparc_filter_graph_launch(sparc_filter_graph* G, void* stream);
  * of its context, so it may follow sparc_destroy of that context. */
 void sparc_filter_graph_destroy(sparc_filter_graph* G);
 
+/* ---------------------------------------------------------------- learned density
+ * Project-added (not in the paper): a network that predicts a correction to the
+ * superposition of atomic densities from atom-centred descriptors, trained on
+ * densities that sparc_scf_step converged; its output feeds
+ * sparc_scf_set_density.  Everything runs in the library's kernels (FP32).
+ *
+ * Descriptors of grid node x (16 per node, widths s_k > 0 in bohr):
+ *   D_k(x) = sum_J sum_{T in {-1,0,1}^3 L} exp(-|x - R_J - T|^2 / s_k^2),
+ * nodes at -L/2 + i h (x fastest), the frame of sparc_grid.
+ * Network: y = relu(relu(D W1 + b1) W2 + b2) w3 + b3, W1 16x128, W2 128x128
+ * (row-major), parameters flat [W1, b1, W2, b2, w3, b3] (SPARC_MLP_NPARAM floats).
+ * Loss: mean over the points of (y - t)^2.  Optimiser: Adam (b1 = 0.9,
+ * b2 = 0.999, eps = 1e-8) with bias correction. */
+#define SPARC_MLP_NFEAT 16
+#define SPARC_MLP_NHID 128
+#define SPARC_MLP_NPARAM (16 * 128 + 128 + 128 * 128 + 128 + 128 + 1)
+typedef struct sparc_mlp sparc_mlp;
+/* Create with initial parameters (host, SPARC_MLP_NPARAM floats); Adam state zero. */
+sparc_status sparc_mlp_create(sparc_ctx* ctx, const float* theta, sparc_mlp** M);
+/* set != 0: replace the parameters (host) and reset Adam; set = 0: read them.
+ * Synchronises the device. */
+sparc_status sparc_mlp_params(sparc_mlp* M, float* theta, int set);
+/* D (device, Nd x 16 floats, row per node) for grid n[3], h[3] and natom atoms
+ * R (host, 3*natom), widths (host, 16).  Returns after the descriptors are
+ * written (synchronises `stream`). */
+sparc_status sparc_mlp_descriptors(sparc_ctx* ctx, const int* n, const double* h, int natom,
+                                   const double* R, const double* widths, float* D, void* stream);
+/* y[p] (device, np floats) = network(D[p]) for D (device, np x 16). */
+sparc_status sparc_mlp_forward(sparc_mlp* M, const float* D, int64_t np, float* y, void* stream);
+/* Gradient of the loss over the points idx[0..np) (device int64 row indices of D
+ * and t; NULL: rows 0..np-1) into grad (device, SPARC_MLP_NPARAM floats; may be
+ * NULL); *loss (host, may be NULL; then the call does not synchronise).  The
+ * per-CTA partial sums are reduced in a fixed order: bit-reproducible. */
+sparc_status sparc_mlp_grad(sparc_mlp* M, const float* D, const float* t, const int64_t* idx,
+                            int64_t np, float* grad, double* loss, void* stream);
+/* One Adam step with learning rate lr > 0 on the gradient of sparc_mlp_grad. */
+sparc_status sparc_mlp_train_step(sparc_mlp* M, const float* D, const float* t, const int64_t* idx,
+                                  int64_t np, float lr, double* loss, void* stream);
+/* Free (synchronises the device); uses no state of its context. */
+void sparc_mlp_destroy(sparc_mlp* M);
+
 /* Extremal-eigenvalue estimates by `ksteps` Lanczos steps with full
  * reorthogonalisation, in FP64 (Section 4: filter bounds by the Lanczos method).
  * v0: device start vector, Nd elements of F64 (k = 0) or C128 (k != 0); it is
@@ -286,6 +327,8 @@ typedef struct {
   double poisson_tol;    /* relative residual of the Poisson solve, > 0 */
   const double* v0;      /* Lanczos start vector, host: Nd doubles (k = 0) or Nd (re, im) pairs */
   const int32_t* proj_atom; /* [nproj of H] atom of each projector, for sparc_scf_forces; may be NULL */
+  int first_passes;      /* CheFSI passes of the first SCF iteration at the starting potential,
+                            0..64 (0 and 1: one; Section 4 repeats CheFSI there) */
 } sparc_scf_desc;
 
 typedef struct {
@@ -310,6 +353,13 @@ sparc_status sparc_scf_step(sparc_scf* S, sparc_dtype dtype, int m, void* U, int
 /* Copy one grid field (Nd doubles) to the device buffer dst: which = 0 b, 1 rho (last
  * iteration), 2 phi, 3 V_xc, 4 V_out, 5 the current V_eff of H (the next V_in). */
 sparc_status sparc_scf_read(const sparc_scf* S, int which, double* dst, void* stream);
+/* Starting density (project-added, not in the paper, which starts from the
+ * superposition of atomic densities): rho0 = max(-b + scale * dy, 0) scaled to
+ * N_e electrons, where -b is that superposition (the pseudocharges of the
+ * Gaussian atoms) and dy a correction (device, Nd floats; NULL: none).  Sets
+ * V_in = phi[rho0 + b] + V_xc[rho0] (Poisson and LDA as in sparc_scf_step).
+ * Only before the first sparc_scf_step of S. */
+sparc_status sparc_scf_set_density(sparc_scf* S, const float* dy, double scale, void* stream);
 void sparc_scf_destroy(sparc_scf* S);
 /* Atomic forces at the state of the last sparc_scf_step (Section 3.6): U are its
  * rotated orbitals (F64 or F32, Gamma point), with its occupations and electrostatic

@@ -217,23 +217,29 @@ def anderson(x_hist, f_hist, beta: float, m: int) -> np.ndarray:
     return (xk - dX @ gamma) + beta * (fk - dF @ gamma)
 
 
-def scf_iteration(H: "O.OracleH", U, lam_prev, v0, b, e_self, Ne, kT, m, lanczos_k=10):
+def scf_iteration(H: "O.OracleH", U, lam_prev, v0, b, e_self, Ne, kT, m, lanczos_k=10, passes=1):
     """One SCF iteration at fixed V_in = H.veff (Section 3.4 and Eq. EL), in the order
     the CUDA path takes it: filter bounds by Lanczos (Section 5; the cutoff is the
     largest previous Ritz value, or the Weyl estimate a0 + (b - a0)(Ns/Nd)^(2/3) at
-    the first iteration, and a0 the smallest), scaled Chebyshev filter, Rayleigh-Ritz,
-    Fermi level, density, Poisson, LDA, V_out = phi + V_xc and the free energy.
+    the first iteration, and a0 the smallest), scaled Chebyshev filter, Rayleigh-Ritz
+    (`passes` times: Section 4 repeats CheFSI at the first iteration's fixed
+    potential, each pass bounded by the previous pass's Ritz values), Fermi level,
+    density, Poisson, LDA, V_out = phi + V_xc and the free energy.
     Returns a dict of every intermediate."""
     U = np.atleast_2d(U)
     ns = U.shape[0]
-    a0, bb, _ = O.lanczos_bounds(H, v0, lanczos_k)
-    if lam_prev is None:
-        a = a0 + (bb - a0) * (ns / H.nd) ** (2.0 / 3.0)
-    else:
-        a0 = float(lam_prev[0])
-        a = float(lam_prev[-1])
-    Yf = O.cheb_filter(H, U, m, a, bb, a0)
-    lam, Uo, _, _ = O.rayleigh_ritz(H, Yf)
+    a0l, bb, _ = O.lanczos_bounds(H, v0, lanczos_k)
+    for _ in range(passes):
+        if lam_prev is None:
+            a0 = a0l
+            a = a0 + (bb - a0) * (ns / H.nd) ** (2.0 / 3.0)
+        else:
+            a0 = float(lam_prev[0])
+            a = float(lam_prev[-1])
+        Yf = O.cheb_filter(H, U, m, a, bb, a0)
+        lam, U, _, _ = O.rayleigh_ritz(H, Yf)
+        lam_prev = lam
+    Uo = U
     mu = fermi_level(lam, Ne, kT)
     g = occupations(lam, mu, kT)
     rho = density(Uo, g, H.h)
@@ -243,6 +249,22 @@ def scf_iteration(H: "O.OracleH", U, lam_prev, v0, b, e_self, Ne, kT, m, lanczos
     F, parts = free_energy(lam, g, rho, b, phi, eps, vxc, H.h, e_self, kT)
     return {"a0": a0, "a": a, "b": bb, "lam": lam, "U": Uo, "mu": mu, "g": g, "rho": rho,
             "phi": phi, "eps": eps, "vxc": vxc, "v_out": v_out, "F": F, "parts": parts}
+
+
+def starting_density(b, dy, scale, Ne, h):
+    """Starting density of the learned initial guess (project-added; the paper starts
+    from the superposition of atomic densities, which is -b for the Gaussian atoms):
+    rho0 = max(-b + scale dy, 0), scaled so that h1 h2 h3 sum rho0 = N_e."""
+    r = -np.asarray(b, dtype=np.float64)
+    if dy is not None:
+        r = r + scale * np.asarray(dy, dtype=np.float64)
+    r = np.maximum(r, 0.0)
+    return r * (Ne / (h[0] * h[1] * h[2] * r.sum()))
+
+
+def starting_potential(rho0, b, n, h, n_o):
+    """V_in = phi[rho0 + b] + V_xc[rho0] (Poisson and LDA of this module)."""
+    return poisson(rho0 + b, n, h, n_o) + lda(rho0)[1]
 
 
 def grad_weights(n_o: int, h: float) -> np.ndarray:

@@ -23,7 +23,7 @@ constexpr int NPAIR = MAXHIST * (MAXHIST + 1) / 2 + MAXHIST;   // Anderson dot p
 // slots of the scalar array
 enum {
   S_MU = 0, S_EBAND, S_ENT, S_NEL, S_EXC, S_EEL, S_RES2, S_VOUT2, S_MEAN, S_ESELF,
-  S_RHS2, S_RR0, S_RR1, S_DONE, S_ITERS, S_GAMMA = 16, S_COUNT = 32
+  S_RHS2, S_RR0, S_RR1, S_DONE, S_ITERS, S_GAMMA = 16, S_RHOSUM = 24, S_COUNT = 32
 };
 
 struct Weights {
@@ -356,6 +356,34 @@ __global__ void k_neg(const double* __restrict__ x, double* __restrict__ y, long
   if (g < nd) y[g] = -x[g];
 }
 
+// ------------------------------------------------------------------ starting density
+// rho = max(-b + scale dy, 0) (the superposition of atomic densities -b plus a
+// correction) and per-block partial sums of rho.
+__global__ void k_guess(const double* __restrict__ b, const float* __restrict__ dy, double scale, long long nd,
+                        double* __restrict__ rho, double* __restrict__ part) {
+  __shared__ double sh[TPB / 32];
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double r = 0.0;
+  if (g < nd) {
+    r = -b[g] + (dy ? scale * (double)dy[g] : 0.0);
+    r = r > 0.0 ? r : 0.0;
+    rho[g] = r;
+  }
+  const double t = block_sum(r, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// rho *= N_e / (dv sum rho), V = phi + V_xc
+__global__ void k_renorm_vin(double* __restrict__ rho, const double* __restrict__ scal, double Ne, double dv,
+                             long long nd) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < nd) rho[g] *= Ne / (dv * scal[S_RHOSUM]);
+}
+__global__ void k_add(const double* __restrict__ x, const double* __restrict__ y, double* __restrict__ z, long long nd) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < nd) z[g] = x[g] + y[g];
+}
+
 // ------------------------------------------------------------------ LDA
 // eps_xc, V_xc: Slater exchange and the Perdew-Wang 1992 correlation of the
 // unpolarised gas (parameters A, alpha1, beta1..beta4).
@@ -622,6 +650,7 @@ struct sparc_scf {
   std::vector<sparc::scf::Atom> atoms;
   double kT = 0.01, beta = 0.3, ptol = 1e-10, Ne = 0.0, e_self = 0.0;
   int hist = 7, nslot = 8, iter = 0, nblk = 0;
+  int first_passes = 1;            // CheFSI passes of the first iteration
   sparc::scf::Atom* d_atoms = nullptr;
   double *d_b = nullptr, *d_rho = nullptr, *d_phi = nullptr, *d_eps = nullptr, *d_vxc = nullptr;
   double *d_vout = nullptr, *d_fres = nullptr, *d_vnext = nullptr;
@@ -702,10 +731,11 @@ extern "C" sparc_status sparc_scf_create(sparc_ham* H, const sparc_scf_desc* d, 
   *out = nullptr;
   sparc_ctx* ctx = H->ctx;
   if (d->natom < 1 || !d->R || !d->Z || !d->rc || !d->v0 || !(d->kT > 0.0) || !(d->mix_beta > 0.0) ||
-      d->mix_history < 0 || d->mix_history > MAXHIST || !(d->poisson_tol > 0.0))
+      d->mix_history < 0 || d->mix_history > MAXHIST || !(d->poisson_tol > 0.0) || d->first_passes < 0 ||
+      d->first_passes > 64)
     return fail(ctx, SPARC_ERR_INVALID_ARG,
                 "sparc_scf_create: need natom >= 1, R, Z, rc, v0, kT > 0, mix_beta > 0, 0 <= mix_history <= 8, "
-                "poisson_tol > 0");
+                "poisson_tol > 0, 0 <= first_passes <= 64");
   SPARC_CUDA(ctx, cudaSetDevice(ctx->device));
   sparc_scf* S = new sparc_scf();
   S->H = H;
@@ -715,6 +745,7 @@ extern "C" sparc_status sparc_scf_create(sparc_ham* H, const sparc_scf_desc* d, 
   S->hist = d->mix_history;
   S->nslot = d->mix_history + 1;
   S->ptol = d->poisson_tol;
+  S->first_passes = std::max(1, d->first_passes);
   const long long nd = H->gd.nd;
   S->nblk = ceil_div(nd, TPB);
   for (int s = 0; s < 3; ++s)
@@ -817,6 +848,32 @@ extern "C" sparc_status sparc_scf_read(const sparc_scf* S, int which, double* ds
   return SPARC_OK;
 }
 
+extern "C" sparc_status sparc_scf_set_density(sparc_scf* S, const float* dy, double scale, void* stream) {
+  if (!S) return SPARC_ERR_INVALID_ARG;
+  sparc_ham* H = S->H;
+  sparc_ctx* ctx = H->ctx;
+  if (S->iter != 0) return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_scf_set_density: only before the first step");
+  if (!isfinite(scale)) return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_scf_set_density: scale must be finite");
+  SPARC_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long nd = H->gd.nd;
+  const int nb = S->nblk;
+  const double dv = H->grid.h[0] * H->grid.h[1] * H->grid.h[2];
+  k_guess<<<nb, TPB, 0, st>>>(S->d_b, dy, scale, nd, S->d_rho, S->d_part);
+  k_sum_parts<<<1, 32, 0, st>>>(S->d_part, nb, 1, 1, S->d_scal + S_RHOSUM);
+  k_renorm_vin<<<nb, TPB, 0, st>>>(S->d_rho, S->d_scal, S->Ne, dv, nd);
+  ctx->launches += 3;
+  SPARC_LAUNCH(ctx, "starting density");
+  int piters = 0;
+  sparc_status rc = poisson(S, st, &piters);
+  if (rc != SPARC_OK) return rc;
+  k_lda<<<nb, TPB, 0, st>>>(S->d_rho, nd, S->d_eps, S->d_vxc);
+  k_add<<<nb, TPB, 0, st>>>(S->d_phi, S->d_vxc, S->d_vnext, nd);
+  ctx->launches += 2;
+  SPARC_LAUNCH(ctx, "starting potential");
+  return sparc_ham_set_veff(H, S->d_vnext, 1, stream);
+}
+
 extern "C" sparc_status sparc_scf_step(sparc_scf* S, sparc_dtype dtype, int m, void* U, int ns, int64_t ld,
                                        double* eig, sparc_scf_info* info, void* stream) {
   if (!S || !U || !eig || !info) return SPARC_ERR_INVALID_ARG;
@@ -842,27 +899,33 @@ extern "C" sparc_status sparc_scf_step(sparc_scf* S, sparc_dtype dtype, int m, v
   }
   // 1. filter bounds: Lanczos upper bound; cutoff and lower end from the previous Ritz
   //    values, or the Lanczos lower end and a Weyl estimate at the first iteration
-  double a0 = 0.0, b = 0.0;
-  sparc_status rc = sparc_lanczos_bounds(H, 10, S->d_v0, &a0, &b, stream);
+  double a0l = 0.0, b = 0.0;
+  sparc_status rc = sparc_lanczos_bounds(H, 10, S->d_v0, &a0l, &b, stream);
   if (rc != SPARC_OK) return rc;
-  double a;
-  if ((int)S->lam_prev.size() == ns) {
-    a0 = S->lam_prev.front();
-    a = S->lam_prev.back();
-  } else {
-    a = a0 + (b - a0) * pow((double)ns / (double)nd, 2.0 / 3.0);
+  // 2. CheFSI: scaled filter and Rayleigh-Ritz (FP64, or mixed for FP32 data); the
+  //    first iteration repeats it at the fixed starting potential (Section 4)
+  const int passes = (S->iter == 0) ? S->first_passes : 1;
+  double a0 = a0l, a = 0.0;
+  for (int pass = 0; pass < passes; ++pass) {
+    if ((int)S->lam_prev.size() == ns) {
+      a0 = S->lam_prev.front();
+      a = S->lam_prev.back();
+    } else {
+      a0 = a0l;
+      a = a0 + (b - a0) * pow((double)ns / (double)nd, 2.0 / 3.0);
+    }
+    if (!(a < b)) a = 0.5 * (a0 + b);
+    if (!(a0 < a)) a0 = a - 1e-3 * (b - a);
+    rc = sparc_cheb_filter(H, dtype, m, a, b, a0, U, S->d_Y, ns, ld, stream);
+    if (rc != SPARC_OK) return rc;
+    const int mode = (dtype == SPARC_F32 || dtype == SPARC_C64) ? SPARC_RR_MIXED : SPARC_RR_FP64;
+    rc = sparc_rayleigh_ritz(H, dtype, S->d_Y, ns, ld, eig, mode, stream);
+    if (rc != SPARC_OK) return rc;
+    SPARC_CUDA(ctx, cudaMemcpyAsync(U, S->d_Y, ybytes, cudaMemcpyDeviceToDevice, st));
+    S->lam_prev.assign(ns, 0.0);
+    SPARC_CUDA(ctx, cudaMemcpyAsync(S->lam_prev.data(), eig, ns * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (pass + 1 < passes) SPARC_CUDA(ctx, cudaStreamSynchronize(st));
   }
-  if (!(a < b)) a = 0.5 * (a0 + b);
-  if (!(a0 < a)) a0 = a - 1e-3 * (b - a);
-  // 2. CheFSI: scaled filter and Rayleigh-Ritz (FP64, or mixed for FP32 data)
-  rc = sparc_cheb_filter(H, dtype, m, a, b, a0, U, S->d_Y, ns, ld, stream);
-  if (rc != SPARC_OK) return rc;
-  const int mode = (dtype == SPARC_F32 || dtype == SPARC_C64) ? SPARC_RR_MIXED : SPARC_RR_FP64;
-  rc = sparc_rayleigh_ritz(H, dtype, S->d_Y, ns, ld, eig, mode, stream);
-  if (rc != SPARC_OK) return rc;
-  SPARC_CUDA(ctx, cudaMemcpyAsync(U, S->d_Y, ybytes, cudaMemcpyDeviceToDevice, st));
-  S->lam_prev.assign(ns, 0.0);
-  SPARC_CUDA(ctx, cudaMemcpyAsync(S->lam_prev.data(), eig, ns * sizeof(double), cudaMemcpyDeviceToHost, st));
   // 3. Fermi level and occupations
   k_fermi<<<1, TPB, 0, st>>>(eig, ns, S->Ne, S->kT, S->d_occ, S->d_scal);
   // 4. density rho = 2 sum g |u|^2 / (h1h2h3)

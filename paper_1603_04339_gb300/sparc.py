@@ -28,7 +28,9 @@ EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_sync", "s
            "sparc_rotate_f32", "sparc_scf_create", "sparc_scf_step", "sparc_scf_read", "sparc_scf_destroy",
            "sparc_scf_forces", "sparc_cheb_filter_batch", "sparc_autotune_filter",
            "sparc_set_filter_units", "sparc_filter_graph_create", "sparc_filter_graph_set_bounds",
-           "sparc_filter_graph_launch", "sparc_filter_graph_destroy"]
+           "sparc_filter_graph_launch", "sparc_filter_graph_destroy", "sparc_scf_set_density",
+           "sparc_mlp_create", "sparc_mlp_params", "sparc_mlp_descriptors", "sparc_mlp_forward", "sparc_mlp_grad",
+           "sparc_mlp_train_step", "sparc_mlp_destroy"]
 TIMED = {"hpass": 0, "gather": 1, "gram": 2, "eig": 3, "rotation": 4, "jacobi": 5, "fpass": 6}
 
 
@@ -45,7 +47,7 @@ class SparcNonlocal(ctypes.Structure):
 class SparcScfDesc(ctypes.Structure):
     _fields_ = [("natom", c_int), ("R", POINTER(c_double)), ("Z", POINTER(c_double)), ("rc", POINTER(c_double)),
                 ("kT", c_double), ("mix_beta", c_double), ("mix_history", c_int), ("poisson_tol", c_double),
-                ("v0", POINTER(c_double)), ("proj_atom", POINTER(c_int32))]
+                ("v0", POINTER(c_double)), ("proj_atom", POINTER(c_int32)), ("first_passes", c_int)]
 
 
 class SparcScfInfo(ctypes.Structure):
@@ -127,6 +129,18 @@ def load(path: str = LIB_PATH):
     L.sparc_filter_graph_launch.argtypes = [c_void_p, c_void_p]
     L.sparc_filter_graph_destroy.argtypes = [c_void_p]
     L.sparc_filter_graph_destroy.restype = None
+    L.sparc_scf_set_density.argtypes = [c_void_p, c_void_p, c_double, c_void_p]
+    L.sparc_mlp_create.argtypes = [c_void_p, c_void_p, POINTER(c_void_p)]
+    L.sparc_mlp_params.argtypes = [c_void_p, c_void_p, c_int]
+    L.sparc_mlp_descriptors.argtypes = [c_void_p, POINTER(c_int), POINTER(c_double), c_int, c_void_p, c_void_p,
+                                        c_void_p, c_void_p]
+    L.sparc_mlp_forward.argtypes = [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]
+    L.sparc_mlp_grad.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, POINTER(c_double),
+                                 c_void_p]
+    L.sparc_mlp_train_step.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, ctypes.c_float,
+                                       POINTER(c_double), c_void_p]
+    L.sparc_mlp_destroy.argtypes = [c_void_p]
+    L.sparc_mlp_destroy.restype = None
     L.sparc_scf_destroy.argtypes = [c_void_p]
     L.sparc_scf_destroy.restype = None
     for name in ("sparc_timing_enable", "sparc_timing_read", "sparc_create", "sparc_sync", "sparc_ham_create", "sparc_ham_set_veff",
@@ -411,6 +425,73 @@ class FilterGraph:
             pass
 
 
+MLP_NFEAT, MLP_NHID = 16, 128
+MLP_NPARAM = MLP_NFEAT * MLP_NHID + MLP_NHID + MLP_NHID * MLP_NHID + MLP_NHID + MLP_NHID + 1
+
+
+class Mlp:
+    """The density network 16 -> 128 -> 128 -> 1 (sparc_mlp_*): parameters, Adam state."""
+
+    def __init__(self, ctx: Context, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        assert th.size == MLP_NPARAM
+        self.ctx = ctx
+        h = c_void_p()
+        ctx.check(load().sparc_mlp_create(ctx.handle, th.ctypes.data, ctypes.byref(h)))
+        self.handle = h
+        ctx._graphs.add(self)
+
+    def params(self):
+        out = np.zeros(MLP_NPARAM, np.float32)
+        self.ctx.check(load().sparc_mlp_params(self.handle, out.ctypes.data, 0))
+        return out
+
+    def set_params(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        self.ctx.check(load().sparc_mlp_params(self.handle, th.ctypes.data, 1))
+
+    def forward(self, D, y, stream=None):
+        """y[p] = network(D[p]) for a float32 CUDA tensor D of shape (N, 16)."""
+        self.ctx.check(load().sparc_mlp_forward(self.handle, _ptr(D), int(D.shape[0]), _ptr(y), _stream(stream)))
+
+    def grad(self, D, t, grad, idx=None, stream=None):
+        """Gradient of the mean squared error into the float32 CUDA tensor `grad`; returns the loss."""
+        loss = c_double()
+        n = int(idx.shape[0]) if idx is not None else int(D.shape[0])
+        self.ctx.check(load().sparc_mlp_grad(self.handle, _ptr(D), _ptr(t), _ptr(idx), n, _ptr(grad),
+                                             ctypes.byref(loss), _stream(stream)))
+        return loss.value
+
+    def train_step(self, D, t, lr, idx=None, want_loss=False, stream=None):
+        """One Adam step on the points idx (int64 CUDA tensor) or all rows of D."""
+        loss = c_double()
+        n = int(idx.shape[0]) if idx is not None else int(D.shape[0])
+        self.ctx.check(load().sparc_mlp_train_step(self.handle, _ptr(D), _ptr(t), _ptr(idx), n, float(lr),
+                                                   ctypes.byref(loss) if want_loss else None, _stream(stream)))
+        return loss.value if want_loss else None
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().sparc_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sparc_mlp_descriptors(ctx: Context, n, h, atoms, widths, D, stream=None):
+    """Descriptors D (float32 CUDA tensor (Nd, 16)) of the grid nodes for the atoms."""
+    nn = (c_int * 3)(*[int(v) for v in n])
+    hh = (c_double * 3)(*[float(v) for v in h])
+    R = np.ascontiguousarray(atoms, dtype=np.float64).reshape(-1)
+    w = np.ascontiguousarray(widths, dtype=np.float64)
+    ctx.check(load().sparc_mlp_descriptors(ctx.handle, nn, hh, int(R.size // 3), R.ctypes.data, w.ctypes.data,
+                                           _ptr(D), _stream(stream)))
+
+
 def sparc_lanczos_bounds(H: Hamiltonian, ksteps, v0, stream=None):
     """(a0, b) from `ksteps` Lanczos steps started at the device vector v0."""
     a0 = c_double()
@@ -452,7 +533,7 @@ class Scf:
     FIELDS = {"b": 0, "rho": 1, "phi": 2, "vxc": 3, "vout": 4, "veff": 5}
 
     def __init__(self, H: Hamiltonian, R, Z, rc, v0, kT=0.01, mix_beta=0.3, mix_history=7, poisson_tol=1e-10,
-                 proj_atom=None):
+                 proj_atom=None, first_passes=1):
         self.H = H
         self._R = np.ascontiguousarray(R, dtype=np.float64).reshape(-1)
         self._Z = np.ascontiguousarray(Z, dtype=np.float64)
@@ -473,6 +554,7 @@ class Scf:
         d.v0 = self._v0.ctypes.data_as(POINTER(c_double))
         self._pa = None if proj_atom is None else np.ascontiguousarray(proj_atom, dtype=np.int32)
         d.proj_atom = None if self._pa is None else self._pa.ctypes.data_as(POINTER(c_int32))
+        d.first_passes = int(first_passes)
         h = c_void_p()
         H.ctx.check(load().sparc_scf_create(H.handle, ctypes.byref(d), ctypes.byref(h)))
         self.handle = h
@@ -492,6 +574,11 @@ class Scf:
         self.H.ctx.check(load().sparc_scf_forces(self.handle, dt, _ptr(U), int(ns), int(ld),
                                                  out.ctypes.data_as(POINTER(c_double)), _stream(stream)))
         return out[:3 * na].reshape(na, 3), out[3 * na:6 * na].reshape(na, 3), out[6 * na:].reshape(na, 3)
+
+    def set_density(self, dy=None, scale=0.0, stream=None):
+        """Starting density max(-b + scale*dy, 0) normalised to N_e (sparc_scf_set_density);
+        dy: float32 CUDA tensor of Nd values, or None for the atomic superposition."""
+        self.H.ctx.check(load().sparc_scf_set_density(self.handle, _ptr(dy), float(scale), _stream(stream)))
 
     def read(self, name: str, out, stream=None):
         """Copy a grid field (b, rho, phi, vxc, vout, veff) into the float64 CUDA tensor `out`."""

@@ -349,10 +349,13 @@ def scf_small(n=(20, 20, 20), h=(0.5, 0.5, 0.5), natom=4, ns=12, m=12, seed=41, 
                      random_orbitals(nd, ns, seed + 2))
 
 
-def scf_fcc32(seed=1005, a=8.1, h=0.45, sigma=0.05, Z=3.0, rc_loc=0.8, rc_proj=1.2, ns=58, m=20) -> ScfSystem:
+def scf_fcc32(seed=1005, a=8.1, h=0.45, sigma=0.05, Z=3.0, rc_loc=0.8, rc_proj=1.2, ns=72, m=20) -> ScfSystem:
     """32 atoms on 2x2x2 perturbed FCC cells (a = 8.1 bohr, 36^3 grid at h = 0.45),
     Z = 3 (N_e = 96), local pseudopotential width 0.8 bohr, s+p projectors with
-    energies U[-0.5, 0.5] Ha, Ns = 58, m = 20 (the SCF cell of the learned-density study)."""
+    energies U[-0.5, 0.5] Ha, m = 20 (the SCF cell of the learned-density study).
+    Ns = 72 = 1.5 N_e/2: with 1.2 N_e/2 = 58 states the highest one of this metallic
+    cell lies 0.03 Ha above the Fermi level at k_B T = 0.01 Ha, keeps occupation 4e-2
+    and, converging slowest in the filter, stalls the SCF near residual 1e-4."""
     rng = np.random.default_rng(seed)
     n = int(round(2 * a / h))
     sites = fcc_sites((2, 2, 2), a, rng, sigma)

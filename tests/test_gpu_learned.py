@@ -1,0 +1,135 @@
+"""Learned initial density through the C ABI against the oracle, and what it gains.
+
+* descriptors, network output, the loss gradient (all tiles and CTAs, ragged tail,
+  gathered rows) and the Adam update against the FP64 oracle;
+* the starting density and potential of sparc_scf_set_density against the oracle;
+* a network trained with these kernels on converged densities of seeded 32-atom
+  cells seeds SCF runs on held-out cells: fewer iterations than the superposition
+  of atomic densities, the same free energy.
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as M
+from oracle import scf_oracle as SO
+from paper_1603_04339_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1603_04339_gb300 import build, sparc
+    build.build()
+    c = sparc.Context(0)
+    yield c
+    c.close()
+
+
+def _net_inputs(n, seed):
+    rng = np.random.default_rng(seed)
+    D = rng.uniform(0.0, 2.5, (n, M.NFEAT)).astype(np.float32)
+    t = rng.normal(0.0, 1.0, n).astype(np.float32)
+    return D, t
+
+
+def test_descriptors_match_the_oracle(ctx):
+    from paper_1603_04339_gb300 import learned_density as LD
+    from paper_1603_04339_gb300 import sparc
+    n, h = (12, 10, 14), (0.6, 0.7, 0.55)
+    rng = np.random.default_rng(4)
+    L = np.array([n[a] * h[a] for a in range(3)])
+    atoms = rng.uniform(-0.5, 0.5, (5, 3)) * L
+    D = torch.empty((n[0] * n[1] * n[2], 16), dtype=torch.float32, device="cuda")
+    sparc.sparc_mlp_descriptors(ctx, n, h, atoms, LD.widths(), D)
+    ref = M.descriptors(n, h, atoms, M.widths())
+    assert np.allclose(LD.widths(), M.widths(), rtol=0, atol=0)
+    err = np.max(np.abs(D.cpu().numpy() - ref) / (1.0 + np.abs(ref)))
+    assert err < 1e-6, err
+
+
+def test_forward_gradient_and_adam_match_the_oracle(ctx):
+    from paper_1603_04339_gb300 import sparc
+    th = M.init_params(11)
+    net = sparc.Mlp(ctx, th.astype(np.float32))
+    th32 = th.astype(np.float32).astype(np.float64)   # the network's FP32 parameters exactly
+    N = 64 * 152 * 2 + 37                             # two tiles per CTA and a ragged tail
+    D, t = _net_inputs(N, 5)
+    Dd, td = torch.from_numpy(D).cuda(), torch.from_numpy(t).cuda()
+    y = torch.empty(N, dtype=torch.float32, device="cuda")
+    net.forward(Dd, y)
+    yo, _ = M.forward(th32, D.astype(np.float64))
+    assert np.max(np.abs(y.cpu().numpy() - yo)) < 1e-5 * max(1.0, np.max(np.abs(yo)))
+    g = torch.empty(sparc.MLP_NPARAM, dtype=torch.float32, device="cuda")
+    loss = net.grad(Dd, td, g)
+    lo, go = M.loss_and_grad(th32, D.astype(np.float64), t.astype(np.float64))
+    gg = g.cpu().numpy().astype(np.float64)
+    assert abs(loss - lo) < 1e-5 * lo
+    assert np.linalg.norm(gg - go) < 2e-5 * np.linalg.norm(go), np.linalg.norm(gg - go) / np.linalg.norm(go)
+    assert np.max(np.abs(gg - go)) < 2e-5 * np.max(np.abs(go))
+    g2 = torch.empty_like(g)
+    net.grad(Dd, td, g2)
+    assert torch.equal(g, g2)                            # fixed-order reductions
+    # gathered rows: the gradient over D[idx]
+    idx = np.random.default_rng(6).choice(N, 3001, replace=False).astype(np.int64)
+    gi = torch.empty_like(g)
+    li = net.grad(Dd, td, gi, idx=torch.from_numpy(idx).cuda())
+    lo2, go2 = M.loss_and_grad(th32, D[idx].astype(np.float64), t[idx].astype(np.float64))
+    assert abs(li - lo2) < 1e-5 * lo2
+    assert np.linalg.norm(gi.cpu().numpy() - go2) < 2e-5 * np.linalg.norm(go2)
+    # one Adam step: the update of the oracle applied to the kernel's own gradient
+    net.train_step(Dd, td, 1e-3)
+    th1 = net.params().astype(np.float64)
+    ref, _, _ = M.adam(th32, gg, np.zeros_like(gg), np.zeros_like(gg), 1, 1e-3)
+    assert np.max(np.abs(th1 - ref)) < 1e-6
+    net.close()
+
+
+def test_starting_density_and_potential_match_the_oracle(ctx):
+    from paper_1603_04339_gb300 import sparc
+    sysd = synth.scf_small()
+    wl = sysd.wl
+    H = sparc.Hamiltonian.from_workload(ctx, wl)
+    S = sparc.Scf.from_system(H, sysd, poisson_tol=1e-13)
+    dy = np.random.default_rng(8).normal(0, 1, wl.nd).astype(np.float32)
+    S.set_density(torch.from_numpy(dy).cuda(), 0.004)
+    rho = torch.empty(wl.nd, dtype=torch.float64, device="cuda")
+    v = torch.empty_like(rho)
+    S.read("rho", rho)
+    S.read("veff", v)
+    torch.cuda.synchronize()
+    b, _, _ = SO.pseudocharge(wl.n, wl.h, 6, wl.atoms, sysd.Z, sysd.rc)
+    r0 = SO.starting_density(b, dy.astype(np.float64), 0.004, sysd.nelec, wl.h)
+    v0 = SO.starting_potential(r0, b, wl.n, wl.h, 6)
+    assert np.max(np.abs(rho.cpu().numpy() - r0)) < 1e-12 * np.max(r0)
+    # V_xc ~ rho^(1/3) magnifies the 1e-13 agreement of rho where rho is tiny
+    dv = np.abs(v.cpu().numpy() - v0)
+    big = r0 > 1e-4 * np.max(r0)
+    assert np.max(dv[big]) < 1e-9 * np.max(np.abs(v0))
+    assert np.max(dv) < 1e-6 * np.max(np.abs(v0))
+    S.close()
+    H.close()
+
+
+def test_learned_guess_saves_scf_iterations_on_held_out_cells(ctx):
+    from paper_1603_04339_gb300 import learned_density as LD
+    D, T, runs = LD.dataset(ctx, range(2000, 2016), torch.float32)
+    net, scale, hist = LD.train(ctx, D, T, epochs=40)
+    print("training loss (standardised):", " ".join(f"{v:.3f}" for v in hist[::5]), f"{hist[-1]:.3f}")
+    assert hist[-1] < 0.5 * hist[0]
+    gains = []
+    for seed in range(3000, 3004):
+        sysd = synth.scf_fcc32(seed=seed)
+        sad = LD.converge(ctx, sysd, torch.float32)
+        y = LD.predict(ctx, net, sysd)
+        lrn = LD.converge(ctx, sysd, torch.float32, dy=y, scale=scale)
+        natom = len(sysd.Z)
+        dF = abs(lrn.free_energy - sad.free_energy) / natom
+        print(f"cell {seed}: SAD {sad.iters} iterations ({sad.seconds:.3f} s), learned {lrn.iters} "
+              f"({lrn.seconds:.3f} s), |dF|/atom {dF:.1e} Ha")
+        assert sad.vresid < 1e-6 and lrn.vresid < 1e-6
+        assert dF < 1e-5
+        gains.append(sad.iters - lrn.iters)
+    assert np.mean(gains) > 0, gains
+    net.close()

@@ -208,3 +208,25 @@ def test_forces_match_finite_differences_of_the_free_energy():
         Rm[0, s] -= d
         fd = -(converged(Rp)[0]["F"] - converged(Rm)[0]["F"]) / (2 * d)
         assert abs(fd - f[0, s]) < 5e-5, (s, fd, f[0, s])
+
+
+def test_starting_density_normalisation_and_atomic_special_case():
+    """The learned starting density keeps N_e electrons for any correction, and with no
+    correction reduces to the atomic superposition -b whose potential has phi = 0."""
+    from paper_1603_04339_gb300 import synth
+    sysd = synth.scf_small()
+    wl = sysd.wl
+    b, _, _ = S.pseudocharge(wl.n, wl.h, 6, wl.atoms, sysd.Z, sysd.rc)
+    dv = wl.h[0] * wl.h[1] * wl.h[2]
+    rng = np.random.default_rng(2)
+    dy = rng.normal(0, 1, wl.nd)
+    for scale in (0.0, 1e-3, 0.05):
+        r = S.starting_density(b, dy, scale, sysd.nelec, wl.h)
+        assert np.all(r >= 0.0)
+        assert abs(dv * r.sum() - sysd.nelec) < 1e-12 * sysd.nelec
+    r0 = S.starting_density(b, None, 0.0, sysd.nelec, wl.h)
+    assert np.max(np.abs(r0 - np.maximum(-b, 0) * sysd.nelec / (dv * np.maximum(-b, 0).sum()))) < 1e-15
+    assert abs(dv * (-b).sum() - sysd.nelec) < 1e-7          # int b = -N_e
+    v = S.starting_potential(r0, b, wl.n, wl.h, 6)
+    # rho0 + b vanishes up to the clipped truncation tail of b, so phi is small
+    assert np.max(np.abs(v - S.lda(r0)[1])) < 1e-3 * np.max(np.abs(v))
