@@ -177,3 +177,27 @@ def test_forces_match_the_oracle_and_mixed_within_target(ctx):
     f32, _, _ = S32.forces(U32)
     print("mixed forces", f32.tolist(), "max |df|", float(np.max(np.abs(f32 - f))))
     assert np.max(np.abs(f32 - f)) < 1e-4
+
+
+def test_first_iteration_repeats_chefsi_like_the_oracle(ctx):
+    """Section 4: the first SCF iteration runs CheFSI several times at the fixed starting
+    potential before the density is formed; three passes against the oracle's."""
+    from paper_1603_04339_gb300 import sparc
+    sysd = synth.scf_small()
+    wl = sysd.wl
+    H = sparc.Hamiltonian.from_workload(ctx, wl)
+    S = sparc.Scf.from_system(H, sysd, kT=KT, mix_beta=BETA, mix_history=HIST, poisson_tol=1e-13, first_passes=3)
+    U = torch.from_numpy(sysd.U0.copy()).cuda()
+    eig = torch.zeros(wl.ns, dtype=torch.float64, device="cuda")
+    info = sparc.sparc_scf_step(S, U, eig, wl.m)
+    b, e_self, _ = SO.pseudocharge(wl.n, wl.h, 6, wl.atoms, sysd.Z, sysd.rc)
+    Hor = O.OracleH(wl, veff=SO.lda(-b)[1])
+    out = SO.scf_iteration(Hor, sysd.U0.copy(), None, sysd.v0, b, e_self, sysd.nelec, KT, wl.m, passes=3)
+    lam = eig.cpu().numpy()
+    assert np.max(np.abs(lam - out["lam"])) < 1e-9 * np.max(np.abs(out["lam"]))
+    rho = _field(S, "rho", wl.nd)
+    assert np.max(np.abs(rho - out["rho"])) < 1e-9 * np.max(out["rho"])
+    assert abs(info["free_energy"] - out["F"]) < 1e-9 * abs(out["F"])
+    assert abs(info["a"] - out["a"]) < 1e-9 * abs(out["a"]) and abs(info["a0"] - out["a0"]) < 1e-9 * abs(out["a0"])
+    S.close()
+    H.close()
