@@ -221,13 +221,20 @@ def kpoint_filter_throughput(sparc, synth, torch, ctx, reps=2, tune=True):
 
     ms_b, l_b = timed(batched)
     ms_k, l_k = timed(per_k)
+    # kernel split of one batched filter (event pairs around each launch)
+    ctx.timing(True)
+    batched()
+    torch.cuda.synchronize()
+    split = {k: ctx.timing_read(k)[0] for k in ("fpass", "gather")}
+    ctx.timing(False)
     for H in Hs:
         H.close()
     del X, Y
     torch.cuda.empty_cache()
     return {"workload": "40^3 Si-like cell, 64 s+p atoms, 3x3x3 MP k-points (27), Ns=192, m=20, complex64",
             "batched": {"value": work / (ms_b * 1e-3) / 1e9, "unit": "Gpt-orb-deg/s", "ms_per_filter": ms_b,
-                        "launches_per_filter": l_b, "units_per_launch": units or None},
+                        "launches_per_filter": l_b, "units_per_launch": units or None,
+                        "pass_ms": split["fpass"], "projection_ms": split["gather"]},
             "per_k": {"value": work / (ms_k * 1e-3) / 1e9, "unit": "Gpt-orb-deg/s", "ms_per_filter": ms_k,
                       "launches_per_filter": l_k},
             "hbm_roof": {"gpt_orb_deg_per_s": _peaks()[0] / 24.0, "bytes_per_unit": 24,

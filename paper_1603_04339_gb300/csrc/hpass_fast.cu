@@ -1,17 +1,21 @@
 // Tiled H-pass for FP32 and complex64 blocks (radius-6 FD stencil, the paper's
 // twelfth order), and the projection of the nonlocal operator by projector group.
 //
-// Kernel structure (one CTA = 16 x 16 nodes in (x, y) x one z-range x one block
-// of NB = 8 orbitals, 512 threads):
-//   * each thread owns RX = 4 x-consecutive nodes of one row for one orbital and
-//     keeps their values at z-6 .. z+6 in a register queue (the z part of the
-//     stencil comes from registers; the queue is rotated by unrolling 13 steps);
-//   * the (x, y) plane at z, with a 6-node halo, is staged in shared memory:
-//     nodes owned by the CTA come from the queues, the halo from global memory
-//     (L2) with Bloch-periodic wrap and phase; double-buffered, one barrier per z;
-//   * x and y neighbours come from the staged plane (a sliding window in x);
-//   * the nonlocal term sum_p chi~_p gc_p is added from the projector boxes that
-//     are active at (tile, z) (precomputed lists), 4 projectors per box at once;
+// Pass kernels (k_pass_f2 for FP32, k_pass_c2 for complex64): persistent CTAs of
+// 512 threads loop over items = (x-y tile, 13-plane z-chunk, block of NB = 8
+// orbitals); FP32 tiles are 16 x 16 nodes, complex64 tiles 16 x 8.
+//   * each thread owns 2 x-consecutive nodes x one float2 (an orbital pair, or the
+//     (re, im) of one complex orbital) and keeps their values at z-6 .. z+6 in a
+//     register queue; the z loop is unrolled over the chunk, so the queue rotates
+//     by renaming;
+//   * the (x, y) plane at z with its 6-node halo is staged in shared memory: owned
+//     nodes from the queues, the halo by cp.async from L2 with periodic wrap (and,
+//     for complex data, the Bloch phase of the face crossed); triple-buffered, one
+//     barrier per plane;
+//   * stencil terms are packed FFMA2/FADD2 with one partial sum per axis;
+//   * the nonlocal term sum_p chi~_p gc_p is added from the projector pieces active
+//     at (tile, z, rows) (precomputed lists), 4 projectors per piece; FP32 runs it
+//     on m16n8k8 TF32 fragments;
 //   * the Chebyshev recurrence is the epilogue: Yout = alpha (H - shift) Yin + beta Yprev.
 #include <algorithm>
 #include <array>
@@ -350,284 +354,6 @@ template <class T> struct Smem {
   static constexpr size_t total = planes + yprev + vb + desc + gcs + steps;
 };
 
-// Yprev may alias Yout (the recurrence is written in place): neither is restrict.
-template <class T>
-__global__ void __launch_bounds__(THREADS, 1)
-k_pass(PassArgs a, const __grid_constant__ KSlots ks, const T* __restrict__ Yin, const T* Yprev, T* Yout,
-       const T* __restrict__ gc) {
-  constexpr int Q = 2 * R + 1;
-  constexpr int RX = Shape<T>::RX, TY = Shape<T>::TY, PY = plane_rows<T>(), NRG = Smem<T>::NRG;
-  constexpr int CH = (int)(NB * sizeof(T) / 16);    // 16-byte chunks per node
-  constexpr int EPC = 16 / (int)sizeof(T);          // elements per chunk
-  constexpr int NHC = (PX * PY * CH + THREADS - 1) / THREADS;   // halo chunk slots per thread
-  constexpr int NPC = (TX * TY * CH + THREADS - 1) / THREADS;   // Y_{j-1} chunk slots per thread
-  static_assert((TX / RX) * TY * NB == THREADS, "tile shape must use all threads");
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T* planes = reinterpret_cast<T*>(smraw);
-  T* yps = reinterpret_cast<T*>(smraw + Smem<T>::planes);
-  float* vbs = reinterpret_cast<float*>(smraw + Smem<T>::planes + Smem<T>::yprev);
-  Piece* desc = reinterpret_cast<Piece*>(smraw + Smem<T>::planes + Smem<T>::yprev + Smem<T>::vb);
-  T* gcs = reinterpret_cast<T*>(smraw + Smem<T>::planes + Smem<T>::yprev + Smem<T>::vb + Smem<T>::desc);
-  int* steps = reinterpret_cast<int*>(smraw + Smem<T>::planes + Smem<T>::yprev + Smem<T>::vb +
-                                      Smem<T>::desc + Smem<T>::gcs);
-  const int t = threadIdx.x;
-  const int o = t % NB;
-  const int rs = (t / NB) % 4;
-  const int xr = (t / 32) % (TX / RX);
-  const int yg = t / (32 * (TX / RX));
-  const int yl = yg * 4 + rs, xl0 = xr * RX;
-  const int tile = blockIdx.x;
-  const int chunk = blockIdx.y;
-  const int cta = tile * a.nchunk + chunk;
-  const int tx0 = (tile % a.tiles_x) * TX, ty0 = (tile / a.tiles_x) * TY;
-  const int zs = chunk * ZC;
-  const int ze = min(zs + ZC, a.n3);
-  const int kk = blockIdx.z / ks.nbk;
-  const KSlot& S = ks.s[kk];
-  const long long blk = S.ubase + blockIdx.z % ks.nbk;   // unit of the block buffers and gc
-  const size_t boff = (size_t)blk * a.nd * NB;
-  const T* Y = Yin + boff;
-  const int n1 = a.n1, n2 = a.n2, n3 = a.n3;
-  const long long plane_el = (long long)n1 * n2 * NB;   // elements per z-plane of a block
-  const int gy = ty0 + yl;
-  const bool vy = gy < n2;
-  const int txv = min(TX, n1 - tx0), tyv = min(TY, n2 - ty0);
-  bool vr[RX];
-#pragma unroll
-  for (int r = 0; r < RX; ++r) vr[r] = vy && (tx0 + xl0 + r < n1);
-
-  // ---- CTA tables: projector pieces (compact), their coefficients, per-(z, rows) activations
-  const int it0 = __ldg(a.cptr + cta), nit = __ldg(a.cptr + cta + 1) - it0;
-  for (int i = t; i < nit; i += THREADS) {
-    const SubBox b = S.sb[__ldg(a.citems + it0 + i)];
-    Piece pc;
-    pc.gy0 = b.gy0; pc.gy1 = b.gy1; pc.gx0 = b.gx0; pc.gx1 = b.gx1;
-    pc.sy = b.nbx;
-    pc.sz = b.nbx * b.nby;
-    pc.base = (int)b.chi4_off + b.bx0 - b.gx0 + b.nbx * (b.by0 - b.gy0) + pc.sz * (b.bz0 - b.gz0);
-    pc.ph_re = b.ph_re; pc.ph_im = b.ph_im;
-    desc[i] = pc;
-    for (int l = 0; l < 4; ++l) {
-      const int p = a.grp[b.grp].proj[l];
-      for (int oo = 0; oo < NB; ++oo)
-        gcs[(i * 4 + l) * NB + oo] = (p >= 0) ? gc[((size_t)p * a.nblk_total + blk) * NB + oo] : FT<T>::zero();
-    }
-  }
-  constexpr int NL = Smem<T>::NL;
-  const size_t sb0 = (size_t)cta * NL;
-  const int s0 = __ldg(a.sptr + sb0);
-  for (int k = t; k <= NL; k += THREADS) steps[k] = __ldg(a.sptr + sb0 + k) - s0;
-  const int nst = __ldg(a.sptr + sb0 + NL) - s0;
-  for (int k = t; k < nst; k += THREADS) steps[NL + 1 + k] = __ldg(a.sslots + s0 + k);
-
-  // ---- per-thread copy descriptors (the same for every plane up to the z offset)
-  // hs: smem element offset in bits 0..19 and the face crossings (tx + 1) + 3 (ty + 1)
-  // in bits 20..23 (-1: no chunk); hg: in-plane global element offset
-  int hs[NHC], hg[NHC];
-#pragma unroll
-  for (int i = 0; i < NHC; ++i) {
-    const int idx = t + i * THREADS;
-    hs[i] = -1; hg[i] = 0;
-    if (idx < PX * PY * CH) {
-      const int pnt = idx / CH, ch = idx % CH;
-      const int sx = pnt % PX, sy = pnt / PX;
-      const int lx = sx - R, ly = sy - R;
-      if (!(lx >= 0 && lx < txv && ly >= 0 && ly < tyv)) {
-        int gxw = tx0 + lx, gyw = ty0 + ly;
-        const int tx = wrap(gxw, n1), ty = wrap(gyw, n2);
-        hs[i] = (sy * RP + sx * NB + ch * EPC) | (((tx + 1) + 3 * (ty + 1)) << 20);
-        hg[i] = (gyw * n1 + gxw) * NB + ch * EPC;
-      }
-    }
-  }
-  int ps[NPC], pg[NPC];   // Y_{j-1} chunks: smem and in-plane global element offsets
-#pragma unroll
-  for (int i = 0; i < NPC; ++i) {
-    const int idx = t + i * THREADS;
-    ps[i] = -1; pg[i] = 0;
-    if (idx < TX * TY * CH) {
-      const int node = idx / CH, ch = idx % CH;
-      const int lx = node % TX, ly = node / TX;
-      if (lx < txv && ly < tyv) {
-        ps[i] = node * NB + ch * EPC;
-        pg[i] = ((ty0 + ly) * n1 + tx0 + lx) * NB + ch * EPC;
-      }
-    }
-  }
-  const int vlx = t % TX, vly = t / TX;
-  const bool vv = t < TX * TY && vlx < txv && vly < tyv;
-  const int vg = (ty0 + vly) * n1 + tx0 + vlx;
-
-  // ---- queue of the thread's nodes at z-R .. z+R (q[i] holds z - R + i)
-  T q[Q][RX];
-  auto load_z = [&](int zz, T* dst) {
-    int zw = zz;
-    const int tz = wrap(zw, n3);
-    float pr = 1.f, pi = 0.f;
-    if (FT<T>::cplx && tz != 0) phase_pow(S.phz_r, S.phz_i, tz, pr, pi);
-    const T* src = Y + (size_t)zw * plane_el + ((size_t)gy * n1 + tx0 + xl0) * NB + o;
-#pragma unroll
-    for (int r = 0; r < RX; ++r) dst[r] = vr[r] ? FT<T>::phase(fld(src + r * NB), pr, pi) : FT<T>::zero();
-  };
-#pragma unroll
-  for (int i = 0; i < Q; ++i) load_z(zs - R + i, q[i]);
-
-  auto issue = [&](int zz, int b) {
-    int zw = zz;
-    wrap(zw, n3);
-    T* P = planes + (size_t)b * PY * RP;
-    const T* Yz = Y + (size_t)zw * plane_el;
-#pragma unroll
-    for (int i = 0; i < NHC; ++i)
-      if (hs[i] >= 0) cp16(P + (hs[i] & 0xFFFFF), Yz + hg[i]);
-    if (vv) cp4(vbs + (size_t)b * TY * TX + t, S.veff + (size_t)zw * n1 * n2 + vg);
-    if (Yprev != nullptr) {
-      T* Pp = yps + (size_t)b * TY * TX * NB;
-      const T* Yp = Yprev + boff + (size_t)zw * plane_el;
-#pragma unroll
-      for (int i = 0; i < NPC; ++i)
-        if (ps[i] >= 0) cp16(Pp + ps[i], Yp + pg[i]);
-    }
-  };
-  auto fixup = [&](int zz, int b) {   // Bloch phase of halo copies that crossed a face
-    if constexpr (FT<T>::cplx) {
-      int zw = zz;
-      const int tz = wrap(zw, n3);
-      T* P = planes + (size_t)b * PY * RP;
-#pragma unroll
-      for (int i = 0; i < NHC; ++i) {
-        const int hw = hs[i] >> 20;
-        if (hs[i] < 0 || (hw == 4 && tz == 0)) continue;
-        float pr, pi, qr, qi, rr, ri;
-        phase_pow(S.phx_r, S.phx_i, hw % 3 - 1, pr, pi);
-        phase_pow(S.phy_r, S.phy_i, hw / 3 - 1, qr, qi);
-        phase_pow(S.phz_r, S.phz_i, tz, rr, ri);
-        const float ar = pr * qr - pi * qi, ai = pr * qi + pi * qr;
-        const float br = ar * rr - ai * ri, bi = ar * ri + ai * rr;
-        float4* c = reinterpret_cast<float4*>(P + (hs[i] & 0xFFFFF));
-        const float4 v = *c;
-        *c = make_float4(v.x * br - v.y * bi, v.x * bi + v.y * br, v.z * br - v.w * bi, v.z * bi + v.w * br);
-      }
-    }
-  };
-  auto own = [&](const T* vals, int b) {
-    T* P = planes + (size_t)b * PY * RP;
-#pragma unroll
-    for (int r = 0; r < RX; ++r)
-      if (vr[r]) P[(yl + R) * RP + (xl0 + r + R) * NB + o] = vals[r];
-  };
-
-  issue(zs, 0);
-  cp_commit();
-  if (zs + 1 < ze) issue(zs + 1, 1);
-  cp_commit();
-  own(q[R], 0);
-  cp_wait1();
-  fixup(zs, 0);
-  __syncthreads();
-
-  for (int z = zs; z < ze; ++z) {
-    const int sidx = z - zs;
-    const int b = sidx % 3;
-    const T* P = planes + (size_t)b * PY * RP;
-    if (vy) {
-      T acc[RX];
-      const T* row = P + (yl + R) * RP + o;
-      // x window in registers for real data; complex data reads x neighbours from
-      // shared memory directly (the register queue already holds 2 floats per value)
-      constexpr int NW = FT<T>::cplx ? 1 : RX + 2 * R;
-      T w[NW];
-      if constexpr (!FT<T>::cplx) {
-#pragma unroll
-        for (int i = 0; i < NW; ++i) w[i] = row[(xl0 + i) * NB];
-      }
-      const float* V = vbs + (size_t)b * TY * TX + yl * TX + xl0;
-#pragma unroll
-      for (int r = 0; r < RX; ++r) {
-        const float cc = a.c0 + V[r] - S.shift;
-        T s;
-        if constexpr (FT<T>::cplx) s = cf32{cc * q[R][r].x, cc * q[R][r].y};
-        else s = cc * q[R][r];
-#pragma unroll
-        for (int p = 1; p <= R; ++p) {
-          const T u = P[(yl + R + p) * RP + (xl0 + r + R) * NB + o];
-          const T d = P[(yl + R - p) * RP + (xl0 + r + R) * NB + o];
-          if constexpr (FT<T>::cplx) {
-            const T xp = row[(xl0 + r + R + p) * NB], xm = row[(xl0 + r + R - p) * NB];
-            s.x += a.cx[p] * (xp.x + xm.x);
-            s.y += a.cx[p] * (xp.y + xm.y);
-            s.x += a.cy[p] * (u.x + d.x);
-            s.y += a.cy[p] * (u.y + d.y);
-            s.x += a.cz[p] * (q[R + p][r].x + q[R - p][r].x);
-            s.y += a.cz[p] * (q[R + p][r].y + q[R - p][r].y);
-          } else {
-            s = fmaf(a.cx[p], w[R + r + p] + w[R + r - p], s);
-            s = fmaf(a.cy[p], u + d, s);
-            s = fmaf(a.cz[p], q[R + p][r] + q[R - p][r], s);
-          }
-        }
-        acc[r] = s;
-      }
-      // nonlocal: pieces that touch this warp's 4 rows at z
-      const int ea = steps[sidx * NRG + yg], eb = steps[sidx * NRG + yg + 1];
-      const int x0r = tx0 + xl0;
-      for (int e = ea; e < eb; ++e) {
-        const int it = steps[NL + 1 + e];
-        const Piece pc = desc[it];
-        if (gy < pc.gy0 || gy >= pc.gy1) continue;
-        T gv[4];
-#pragma unroll
-        for (int l = 0; l < 4; ++l) gv[l] = gcs[(it * 4 + l) * NB + o];
-        const int rowoff = pc.base + pc.sy * gy + pc.sz * z;
-        float4 c4[RX];
-#pragma unroll
-        for (int r = 0; r < RX; ++r) {
-          const int gx = x0r + r;
-          c4[r] = (gx >= pc.gx0 && gx < pc.gx1) ? __ldg(S.chi4 + rowoff + gx) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int r = 0; r < RX; ++r) {
-          const T d = FT<T>::dot4(c4[r], gv);
-          if constexpr (FT<T>::cplx) {
-            acc[r].x += pc.ph_re * d.x - pc.ph_im * d.y;
-            acc[r].y += pc.ph_re * d.y + pc.ph_im * d.x;
-          } else {
-            acc[r] += d;   // real data: k = 0, the phase is 1
-          }
-        }
-      }
-      // recurrence epilogue
-      const T* Pp = yps + (size_t)b * TY * TX * NB + (yl * TX + xl0) * NB + o;
-      T* out = Yout + boff + (size_t)z * plane_el + ((size_t)gy * n1 + tx0 + xl0) * NB + o;
-#pragma unroll
-      for (int r = 0; r < RX; ++r) {
-        if (!vr[r]) continue;
-        T v;
-        if constexpr (FT<T>::cplx) {
-          v = cf32{S.alpha * acc[r].x, S.alpha * acc[r].y};
-          if (Yprev) { const T pv = Pp[r * NB]; v.x += S.beta * pv.x; v.y += S.beta * pv.y; }
-        } else {
-          v = S.alpha * acc[r];
-          if (Yprev) v = fmaf(S.beta, Pp[r * NB], v);
-        }
-        out[r * NB] = v;
-      }
-    }
-    // pipeline: own nodes of z+1 from the queue, copies for z+2, advance the queue
-    if (z + 1 < ze) own(q[R + 1], (sidx + 1) % 3);
-    if (z + 2 < ze) issue(z + 2, (sidx + 2) % 3);
-    cp_commit();
-#pragma unroll
-    for (int i = 0; i < Q - 1; ++i)
-#pragma unroll
-      for (int r = 0; r < RX; ++r) q[i][r] = q[i + 1][r];
-    load_z(z + R + 1, q[Q - 1]);
-    cp_wait1();
-    if (z + 1 < ze) fixup(z + 1, (sidx + 1) % 3);
-    __syncthreads();
-  }
-}
-
 // ---------------------------------------------------------------------------
 // FP32 pass with orbital pairs: each thread owns 2 x-consecutive nodes x 2
 // orbitals (a float2), so every stencil term is one packed FFMA2/FADD2 and every
@@ -906,6 +632,275 @@ k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* 
       cp_commit();
       load_z(z + R + 1, q[sidx % Q]);   // plane z - R is no longer needed
       cp_wait1();
+      __syncthreads();
+      }
+    }
+  }
+}
+
+// Complex64 pass in the form of the FP32 one: a cf32 value is a float2 (re, im) and
+// the stencil, V_eff and recurrence coefficients are real, so every stencil term is
+// one packed FFMA2/FADD2 on (re, im).  Each thread owns 2 x-consecutive nodes x one
+// orbital; a warp covers 4 rows x 8 orbitals at one x-run; the 13-plane z queue
+// rotates by renaming in the unrolled z loop; CTAs are persistent over (tile,
+// z-chunk, k-point unit) items.  Values that cross a face pick up the Bloch phase
+// of that face: the z queue when it loads a wrapped plane, the staged halo after
+// its copy lands (the x/y face crossings are encoded in the copy descriptors).
+__device__ __forceinline__ float2 cmul2(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// exp(i k L t) for a face crossing t in {-1, 0, 1} from exp(i k L) = (pr, pi)
+__device__ __forceinline__ float2 face_phase(float pr, float pi, int t) {
+  return t == 0 ? make_float2(1.f, 0.f) : make_float2(pr, t > 0 ? pi : -pi);
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+k_pass_c2(PassArgs a, const __grid_constant__ KSlots ks, const cf32* __restrict__ Yin, const cf32* Yprev,
+          cf32* Yout, const cf32* __restrict__ gc, int nitems) {
+  constexpr int Q = 2 * R + 1;
+  constexpr int TYC = Shape<cf32>::TY;
+  constexpr int PY = TYC + 2 * R;
+  constexpr int CH = NB * (int)sizeof(cf32) / 16;         // 16-byte chunks per node (4)
+  constexpr int NHC = (PX * PY * CH + THREADS - 1) / THREADS;
+  constexpr int NPC = (TX * TYC * CH + THREADS - 1) / THREADS;
+  constexpr int NRG = Smem<cf32>::NRG, NL = Smem<cf32>::NL;
+  static_assert(NRG == TYC / 4 && Smem<cf32>::NXR == 1, "one list per row group");
+  static_assert((TX / RX2) * 4 * NB * NRG == THREADS, "thread layout");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cf32* planes = reinterpret_cast<cf32*>(smraw);
+  cf32* yps = reinterpret_cast<cf32*>(smraw + Smem<cf32>::planes);
+  float* vbs = reinterpret_cast<float*>(smraw + Smem<cf32>::planes + Smem<cf32>::yprev);
+  Piece* desc = reinterpret_cast<Piece*>(smraw + Smem<cf32>::planes + Smem<cf32>::yprev + Smem<cf32>::vb);
+  cf32* gcs = reinterpret_cast<cf32*>(smraw + Smem<cf32>::planes + Smem<cf32>::yprev + Smem<cf32>::vb +
+                                      Smem<cf32>::desc);
+  int* steps = reinterpret_cast<int*>(smraw + Smem<cf32>::planes + Smem<cf32>::yprev + Smem<cf32>::vb +
+                                      Smem<cf32>::desc + Smem<cf32>::gcs);
+  const int t = threadIdx.x;
+  const int o = t % NB;                  // orbital
+  const int r4 = (t / NB) % 4;           // row within the warp
+  const int xr = (t / 32) % (TX / RX2);  // x-run
+  const int yg = t / 256;                // row group (0, 1)
+  const int yl = yg * 4 + r4, xl0 = xr * RX2;
+  const int n1 = a.n1, n2 = a.n2, n3 = a.n3;
+  const long long plane_el = (long long)n1 * n2 * NB;
+  const int ntiles = a.tiles_x * ((n2 + TYC - 1) / TYC);
+  auto ld2 = [](const cf32* p) { return *reinterpret_cast<const float2*>(p); };
+
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int tile = item % ntiles;
+    const int chunk = (item / ntiles) % a.nchunk;
+    const int j = item / (ntiles * a.nchunk);
+    const KSlot& S = ks.s[j / ks.nbk];
+    const long long blk = S.ubase + j % ks.nbk;
+    const int cta = tile * a.nchunk + chunk;
+    const int tx0 = (tile % a.tiles_x) * TX, ty0 = (tile / a.tiles_x) * TYC;
+    const int zs = chunk * ZC;
+    const int ze = min(zs + ZC, n3);
+    const size_t boff = (size_t)blk * a.nd * NB;
+    const cf32* Y = Yin + boff;
+    const int gy = ty0 + yl;
+    const bool vy = gy < n2;
+    const int txv = min(TX, n1 - tx0), tyv = min(TYC, n2 - ty0);
+    bool vr[RX2];
+#pragma unroll
+    for (int r = 0; r < RX2; ++r) vr[r] = vy && (tx0 + xl0 + r < n1);
+    const float2 alpha2 = make_float2(S.alpha, S.alpha), beta2 = make_float2(S.beta, S.beta);
+
+    // ---- item tables (the previous item's readers finished at its last barrier)
+    const int it0 = __ldg(a.cptr + cta), nit = __ldg(a.cptr + cta + 1) - it0;
+    for (int i = t; i < nit; i += THREADS) {
+      const SubBox b = S.sb[__ldg(a.citems + it0 + i)];
+      Piece pc;
+      pc.gy0 = b.gy0; pc.gy1 = b.gy1; pc.gx0 = b.gx0; pc.gx1 = b.gx1;
+      pc.sy = b.nbx;
+      pc.sz = b.nbx * b.nby;
+      pc.base = (int)b.chi4_off + b.bx0 - b.gx0 + b.nbx * (b.by0 - b.gy0) + pc.sz * (b.bz0 - b.gz0);
+      pc.ph_re = b.ph_re; pc.ph_im = b.ph_im;
+      desc[i] = pc;
+      for (int l = 0; l < 4; ++l) {
+        const int p = a.grp[b.grp].proj[l];
+        for (int oo = 0; oo < NB; ++oo)
+          gcs[(i * 4 + l) * NB + oo] = (p >= 0) ? gc[((size_t)p * a.nblk_total + blk) * NB + oo] : cf32{0.f, 0.f};
+      }
+    }
+    const size_t sb0 = (size_t)cta * NL;
+    const int s0 = __ldg(a.sptr + sb0);
+    for (int k = t; k <= NL; k += THREADS) steps[k] = __ldg(a.sptr + sb0 + k) - s0;
+    const int nst = __ldg(a.sptr + sb0 + NL) - s0;
+    for (int k = t; k < nst; k += THREADS) steps[NL + 1 + k] = __ldg(a.sslots + s0 + k);
+
+    // ---- copy descriptors: hs = smem element offset | (face crossings (tx+1) + 3 (ty+1)) << 20
+    int hs[NHC], hg[NHC];
+#pragma unroll
+    for (int i = 0; i < NHC; ++i) {
+      const int idx = t + i * THREADS;
+      hs[i] = -1; hg[i] = 0;
+      if (idx < PX * PY * CH) {
+        const int pnt = idx / CH, ch = idx % CH;
+        const int sx = pnt % PX, sy = pnt / PX;
+        const int lx = sx - R, ly = sy - R;
+        if (!(lx >= 0 && lx < txv && ly >= 0 && ly < tyv)) {
+          int gxw = tx0 + lx, gyw = ty0 + ly;
+          const int cx = wrap(gxw, n1), cy = wrap(gyw, n2);
+          hs[i] = (sy * RP + sx * NB + ch * 2) | (((cx + 1) + 3 * (cy + 1)) << 20);
+          hg[i] = (gyw * n1 + gxw) * NB + ch * 2;
+        }
+      }
+    }
+    int ps[NPC], pg[NPC];
+#pragma unroll
+    for (int i = 0; i < NPC; ++i) {
+      const int idx = t + i * THREADS;
+      ps[i] = -1; pg[i] = 0;
+      if (idx < TX * TYC * CH) {
+        const int node = idx / CH, ch = idx % CH;
+        const int lx = node % TX, ly = node / TX;
+        if (lx < txv && ly < tyv) {
+          ps[i] = node * NB + ch * 2;
+          pg[i] = ((ty0 + ly) * n1 + tx0 + lx) * NB + ch * 2;
+        }
+      }
+    }
+    const int vlx = t % TX, vly = t / TX;
+    const bool vv = t < TX * TYC && vlx < txv && vly < tyv;
+    const int vgo = (ty0 + vly) * n1 + tx0 + vlx;
+
+    float2 q[Q][RX2];
+    auto load_z = [&](int zz, float2* dst) {
+      int zw = zz;
+      const int cz = wrap(zw, n3);
+      const float2 ph = face_phase(S.phz_r, S.phz_i, cz);
+      const cf32* src = Y + (size_t)zw * plane_el + ((size_t)gy * n1 + tx0 + xl0) * NB + o;
+#pragma unroll
+      for (int r = 0; r < RX2; ++r) {
+        const float2 v = vr[r] ? __ldg(reinterpret_cast<const float2*>(src + r * NB)) : make_float2(0.f, 0.f);
+        dst[r] = cz ? cmul2(v, ph) : v;
+      }
+    };
+#pragma unroll
+    for (int i = 0; i < Q; ++i) load_z(zs - R + i, q[i]);
+
+    auto issue = [&](int zz, int b) {
+      int zw = zz;
+      wrap(zw, n3);
+      cf32* P = planes + (size_t)b * PY * RP;
+      const cf32* Yz = Y + (size_t)zw * plane_el;
+#pragma unroll
+      for (int i = 0; i < NHC; ++i)
+        if (hs[i] >= 0) cp16(P + (hs[i] & 0xFFFFF), Yz + hg[i]);
+      if (vv) cp4(vbs + (size_t)b * TYC * TX + t, S.veff + (size_t)zw * n1 * n2 + vgo);
+      if (Yprev != nullptr) {
+        cf32* Pp = yps + (size_t)b * TYC * TX * NB;
+        const cf32* Yp = Yprev + boff + (size_t)zw * plane_el;
+#pragma unroll
+        for (int i = 0; i < NPC; ++i)
+          if (ps[i] >= 0) cp16(Pp + ps[i], Yp + pg[i]);
+      }
+    };
+    // Bloch phase of the halo chunks this thread copied (after they landed)
+    auto fixup = [&](int zz, int b) {
+      int zw = zz;
+      const int cz = wrap(zw, n3);
+      const float2 pz = face_phase(S.phz_r, S.phz_i, cz);
+      cf32* P = planes + (size_t)b * PY * RP;
+#pragma unroll
+      for (int i = 0; i < NHC; ++i) {
+        const int hw = hs[i] >> 20;
+        if (hs[i] < 0 || (hw == 4 && cz == 0)) continue;
+        const float2 ph = cmul2(cmul2(face_phase(S.phx_r, S.phx_i, hw % 3 - 1), face_phase(S.phy_r, S.phy_i, hw / 3 - 1)), pz);
+        float4* c = reinterpret_cast<float4*>(P + (hs[i] & 0xFFFFF));
+        const float4 v = *c;
+        const float2 v0 = cmul2(make_float2(v.x, v.y), ph), v1 = cmul2(make_float2(v.z, v.w), ph);
+        *c = make_float4(v0.x, v0.y, v1.x, v1.y);
+      }
+    };
+    auto own = [&](const float2* vals, int b) {
+      cf32* P = planes + (size_t)b * PY * RP;
+#pragma unroll
+      for (int r = 0; r < RX2; ++r)
+        if (vr[r]) *reinterpret_cast<float2*>(P + (yl + R) * RP + (xl0 + r + R) * NB + o) = vals[r];
+    };
+
+    issue(zs, 0);
+    cp_commit();
+    if (zs + 1 < ze) issue(zs + 1, 1);
+    cp_commit();
+    own(q[R], 0);
+    cp_wait1();
+    fixup(zs, 0);
+    __syncthreads();
+
+#pragma unroll
+    for (int sidx = 0; sidx < ZC; ++sidx) {
+      const int z = zs + sidx;
+      if (z < ze) {   // uniform over the CTA; no break, so the loop unrolls completely
+      const int b = sidx % 3;
+      const cf32* P = planes + (size_t)b * PY * RP;
+      float2 acc[RX2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      if (vy) {
+        const cf32* row = P + (yl + R) * RP + o;
+        float2 w[RX2 + 2 * R];
+#pragma unroll
+        for (int i = 0; i < RX2 + 2 * R; ++i) w[i] = ld2(row + (xl0 + i) * NB);
+        const float* V = vbs + (size_t)b * TYC * TX + yl * TX + xl0;
+#pragma unroll
+        for (int r = 0; r < RX2; ++r) {
+          float2 sx = __fmul2_rn(f2(a.c0 + V[r] - S.shift), q[(sidx + R) % Q][r]);
+          float2 sy = make_float2(0.f, 0.f), sz = make_float2(0.f, 0.f);
+          const cf32* col = P + (xl0 + r + R) * NB + o;
+#pragma unroll
+          for (int p = 1; p <= R; ++p) {
+            const float2 u = ld2(col + (yl + R + p) * RP);
+            const float2 d = ld2(col + (yl + R - p) * RP);
+            sx = __ffma2_rn(a.cx2[p], __fadd2_rn(w[R + r + p], w[R + r - p]), sx);
+            sy = __ffma2_rn(a.cy2[p], __fadd2_rn(u, d), sy);
+            sz = __ffma2_rn(a.cz2[p], __fadd2_rn(q[(sidx + R + p) % Q][r], q[(sidx + R - p) % Q][r]), sz);
+          }
+          acc[r] = __fadd2_rn(sx, __fadd2_rn(sy, sz));
+        }
+        // nonlocal: sum over the pieces active at (z, this row group) of
+        // phase * sum_l chi_l(node) gc_l(orbital)
+        const int ea = steps[sidx * NRG + yg], eb = steps[sidx * NRG + yg + 1];
+        const int x0r = tx0 + xl0;
+        for (int e = ea; e < eb; ++e) {
+          const int it = steps[NL + 1 + e];
+          const int4 pa = *reinterpret_cast<const int4*>(&desc[it].gy0);   // gy0 gy1 gx0 gx1
+          if (gy < pa.x || gy >= pa.y) continue;
+          const int4 pb = *reinterpret_cast<const int4*>(&desc[it].base);  // base sy sz -
+          const float2 ph = *reinterpret_cast<const float2*>(&desc[it].ph_re);
+          const float2 g0 = ld2(gcs + (it * 4 + 0) * NB + o), g1 = ld2(gcs + (it * 4 + 1) * NB + o);
+          const float2 g2 = ld2(gcs + (it * 4 + 2) * NB + o), g3 = ld2(gcs + (it * 4 + 3) * NB + o);
+          const int rowoff = pb.x + pb.y * gy + pb.z * z;
+#pragma unroll
+          for (int r = 0; r < RX2; ++r) {
+            const int gx = x0r + r;
+            if (gx < pa.z || gx >= pa.w) continue;
+            const float4 c4 = __ldg(S.chi4 + rowoff + gx);
+            float2 d = __fmul2_rn(f2(c4.x), g0);
+            d = __ffma2_rn(f2(c4.y), g1, d);
+            d = __ffma2_rn(f2(c4.z), g2, d);
+            d = __ffma2_rn(f2(c4.w), g3, d);
+            acc[r] = __ffma2_rn(f2(ph.x), d, acc[r]);
+            acc[r] = __ffma2_rn(make_float2(-ph.y, ph.y), make_float2(d.y, d.x), acc[r]);
+          }
+        }
+        // recurrence epilogue
+        const cf32* Pp = yps + (size_t)b * TYC * TX * NB + (yl * TX + xl0) * NB + o;
+        cf32* out = Yout + boff + (size_t)z * plane_el + ((size_t)gy * n1 + tx0 + xl0) * NB + o;
+#pragma unroll
+        for (int r = 0; r < RX2; ++r) {
+          if (!vr[r]) continue;
+          float2 v = __fmul2_rn(alpha2, acc[r]);
+          if (Yprev) v = __ffma2_rn(beta2, ld2(Pp + r * NB), v);
+          *reinterpret_cast<float2*>(out + r * NB) = v;
+        }
+      }
+      if (z + 1 < ze) own(q[(sidx + R + 1) % Q], (sidx + 1) % 3);
+      if (z + 2 < ze) issue(z + 2, (sidx + 2) % 3);
+      cp_commit();
+      load_z(z + R + 1, q[sidx % Q]);   // plane z - R is no longer needed
+      cp_wait1();
+      if (z + 1 < ze) fixup(z + 1, (sidx + 1) % 3);
       __syncthreads();
       }
     }
@@ -1309,11 +1304,12 @@ cudaError_t launch_pass_k(const sparc_ham* H0, const cf32* Yin, const cf32* Ypre
   PassArgs a = pass_args(H0, Lo);
   a.nblk_total = (int)nunit_total;
   const size_t smem = Smem<cf32>::total;
-  cudaError_t e = cudaFuncSetAttribute(k_pass<cf32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_pass_c2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)(Lo.tiles_x * Lo.tiles_y), (unsigned)Lo.nchunk, (unsigned)(ks.nk * ks.nbk));
+  // persistent CTAs over (tile, chunk, unit) items
+  const int nitems = Lo.tiles_x * Lo.tiles_y * Lo.nchunk * ks.nk * ks.nbk;
   cudaEvent_t t0 = timing_begin(H0->ctx, st);
-  k_pass<cf32><<<grid, THREADS, smem, st>>>(a, ks, Yin, Yprev, Yout, gc);
+  k_pass_c2<<<std::min(nitems, std::max(H0->ctx->nsm, 1)), THREADS, smem, st>>>(a, ks, Yin, Yprev, Yout, gc, nitems);
   ++H0->ctx->launches;
   timing_end(H0->ctx, TK_FPASS, t0, st);
   return cudaGetLastError();
