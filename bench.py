@@ -48,6 +48,10 @@ def _args():
                     help="filter: only the Chebyshev filter (for profiler captures); "
                          "kpoints: the 27-k-point complex64 filter alone")
     ap.add_argument("--ns", type=int, default=None, help="orbitals (filter mode; default: the cell's 512)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="kpoints mode: the cost model's launch grouping, no autotuning (profiler captures)")
+    ap.add_argument("--nk", type=int, default=None,
+                    help="kpoints mode: the first NK k-points only (a smaller case for profiler captures)")
     return ap.parse_args()
 
 
@@ -179,14 +183,14 @@ def job_rate(ms_local, units_per_rank, world, dist=None, device="cpu"):
     return ms, world * units_per_rank / (ms * 1e-3) / 1e9
 
 
-def kpoint_filter_throughput(sparc, synth, torch, ctx, reps=2, tune=True):
+def kpoint_filter_throughput(sparc, synth, torch, ctx, reps=2, tune=True, nk=None):
     """Complex64 filter of the 40^3 Si-like cell over all 27 Monkhorst-Pack k-points
     (Ns=192, m=20): batched (sparc_cheb_filter_batch, launches shared by k-points,
     grouping autotuned) against one sparc_cheb_filter call per k, both timed with
     CUDA events after a warm-up run.  Inputs (2.65 GB per block set) exceed L2."""
     import numpy as np
     wl = synth.config3()
-    nk = len(wl.kpts)
+    nk = len(wl.kpts) if nk is None else min(int(nk), len(wl.kpts))
     Hs = [sparc.Hamiltonian.from_workload(ctx, wl, k) for k in range(nk)]
     X = torch.empty((nk, wl.ns, wl.nd), dtype=torch.complex64, device="cuda")
     for k in range(nk):
@@ -231,7 +235,7 @@ def kpoint_filter_throughput(sparc, synth, torch, ctx, reps=2, tune=True):
         H.close()
     del X, Y
     torch.cuda.empty_cache()
-    return {"workload": "40^3 Si-like cell, 64 s+p atoms, 3x3x3 MP k-points (27), Ns=192, m=20, complex64",
+    return {"workload": f"40^3 Si-like cell, 64 s+p atoms, 3x3x3 MP k-points ({nk} of 27), Ns=192, m=20, complex64",
             "batched": {"value": work / (ms_b * 1e-3) / 1e9, "unit": "Gpt-orb-deg/s", "ms_per_filter": ms_b,
                         "launches_per_filter": l_b, "units_per_launch": units or None,
                         "pass_ms": split["fpass"], "projection_ms": split["gather"]},
@@ -300,10 +304,12 @@ def run_kpoints(args):
     build.build()
     from paper_1603_04339_gb300 import sparc
     ctx = sparc.Context(0)
-    out = kpoint_filter_throughput(sparc, synth, torch, ctx, reps=max(1, args.steps))
+    out = kpoint_filter_throughput(sparc, synth, torch, ctx, reps=max(1, args.steps), nk=args.nk,
+                                   tune=not args.no_tune)
     print(_json.dumps({"mode": "kpoints", **out}), flush=True)
-    out = cell_batch_throughput(sparc, synth, torch, ctx, reps=max(1, args.steps))
-    print(_json.dumps({"mode": "cells", **out}), flush=True)
+    if args.nk is None:
+        out = cell_batch_throughput(sparc, synth, torch, ctx, reps=max(1, args.steps))
+        print(_json.dumps({"mode": "cells", **out}), flush=True)
     return 0
 
 
