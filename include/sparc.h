@@ -170,23 +170,29 @@ sparc_status sparc_cheb_filter_batch(sparc_ham* const* H, int nk, sparc_dtype dt
                                      const void* X, void* Y, int ns, int64_t ld, void* stream);
 
 /* Launch-shape autotuner of the filter.  Times sparc_cheb_filter_batch (degree
- * min(m, 3), arguments as there) for several numbers of orbital blocks (8
- * orbitals each) per launch -- fractions and multiples of the number whose two
- * live buffers fit in L2, all blocks of one k, all blocks of all k -- keeps the
- * fastest in the context and returns it in *units (0 if the dtype has a single
- * launch shape) with its time in *ms.  Later filter calls on this context with
- * the same dtype, Nd, ns and nk use it (nk = 1 for sparc_cheb_filter).  Tuned:
- * SPARC_F32 with nk = 1 and SPARC_C64 with nk > 1.  Synchronises `stream`;
- * overwrites Y.  Make it before capturing filter calls into a CUDA graph. */
+ * min(m, 3), arguments as there) for several launch configurations, keeps the
+ * fastest in the context and returns its code in *units (0 if the dtype has a
+ * single launch shape) with its time in *ms.  A code is
+ *   blocks per launch + SPARC_TUNE_SHAPE * tile shape,
+ * blocks of 8 orbitals per launch being fractions and multiples of the number
+ * whose two live buffers fit in L2, all blocks of one k, or all blocks of all k;
+ * the tile shape (SPARC_F32 only) is 0 for 16 x 16 nodes per CTA of 512 threads,
+ * 1 for 16 x 8 nodes per CTA of 256 threads (two CTAs per SM).  Later filter
+ * calls on this context with the same dtype, Nd, ns and nk use it (nk = 1 for
+ * sparc_cheb_filter).  Tuned: SPARC_F32 with nk = 1 and SPARC_C64 with nk > 1.
+ * Synchronises `stream`; overwrites Y.  Make it before capturing filter calls
+ * into a CUDA graph. */
+#define SPARC_TUNE_SHAPE (1 << 20)
 sparc_status sparc_autotune_filter(sparc_ham* const* H, int nk, sparc_dtype dtype, int m,
                                    const double* a, const double* b, const double* a0,
                                    const void* X, void* Y, int ns, int64_t ld, void* stream,
                                    int* units, double* ms);
 
-/* Set (units > 0) or clear (units = 0) the number of orbital blocks per filter
- * launch that later filter calls on this context use for (dtype, Nd, ns, nk),
- * e.g. a value that sparc_autotune_filter chose in an earlier process.  With
- * nothing set the filter takes the grouping of its cost model. */
+/* Set (units > 0) or clear (units = 0) the launch configuration code (as
+ * sparc_autotune_filter returns it: blocks per launch + SPARC_TUNE_SHAPE * tile
+ * shape) that later filter calls on this context use for (dtype, Nd, ns, nk),
+ * e.g. a code chosen in an earlier process.  With nothing set the filter takes
+ * the grouping of its cost model and the 16 x 16 tile. */
 sparc_status sparc_set_filter_units(sparc_ctx* ctx, sparc_dtype dtype, int64_t nd, int ns, int nk,
                                     int units);
 

@@ -177,8 +177,9 @@ struct sparc_ctx {
   cudaStream_t cap_stream = nullptr;
   std::map<std::tuple<int, int, void*, void*, void*>, cudaGraphExec_t> graphs;
   int last_sweeps = 0;
-  // units (blocks of NB orbitals) per filter launch chosen by sparc_autotune_filter,
-  // keyed by (dtype, Nd, ns, number of k-points)
+  // filter launch configuration chosen by sparc_autotune_filter, keyed by (dtype, Nd,
+  // ns, number of k-points): units (blocks of NB orbitals) per launch + TUNE_SHAPE x the
+  // FP32 pass tile shape
   std::map<std::tuple<int, long long, int, int>, int> tuned;
 };
 
@@ -210,6 +211,10 @@ bool sync_check();
   } while (0)
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// A tuned filter configuration packs units per launch (below TUNE_SHAPE) and the
+// FP32 pass tile shape (its multiple of TUNE_SHAPE).
+constexpr int TUNE_SHAPE = 1 << 20;
 
 // Timing hooks: bracket a launch with events on `st` while timing is enabled.
 enum TimedKernel { TK_HPASS = 0, TK_GATHER = 1, TK_GRAM = 2, TK_EIG = 3, TK_ROT = 4, TK_JAC = 5, TK_FPASS = 6 };

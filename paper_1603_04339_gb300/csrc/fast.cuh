@@ -37,7 +37,8 @@ struct Group {
   int sb0, sb1;         // sub-box range
 };
 
-// Per kernel tile shape (0: FP32 16x16, 1: complex64 16x8): for every CTA
+// Per kernel tile shape (0: FP32 16x16, 1: complex64 16x8, 2: FP32 16x8 for
+// 256-thread CTAs, two per SM): for every CTA
 // (tile, z-chunk) the pieces that touch it, and per z the CTA-local indices
 // of the pieces active in that plane.
 struct Layout {
@@ -54,7 +55,7 @@ struct Tables {
   Group* d_grp = nullptr;
   SubBox* d_sb = nullptr;
   float* d_chi4 = nullptr;    // [box nodes][4], zero where a group has < 4 projectors
-  Layout lay[2];
+  Layout lay[3];
   unsigned long long geom = 0;   // hash of the grid, groups and piece geometry (not phases)
 };
 
@@ -86,11 +87,15 @@ unsigned long long geometry_hash(const sparc_ham* H);
 sparc_status build_tables(sparc_ham* H, const sparc_nonlocal* nl);
 void free_tables(Tables& t);
 
+// FP32 pass tile shapes: 0 = 16 x 16 nodes, 512 threads, one CTA per SM;
+// 1 = 16 x 8 nodes, 256 threads, two CTAs per SM.
+constexpr int NSHAPE_F32 = 2;
+bool shape_usable(const sparc_ham* H, int shape);
 // Whether the tiled kernel handles this Hamiltonian (radius 6, FP32 element types).
 bool usable(const sparc_ham* H);
 // Work items (tile x z-chunk) of one block of orbitals for the element type T.
 template <class T>
-int items_per_block(const sparc_ham* H);
+int items_per_block(const sparc_ham* H, int shape = 0);
 
 // gc[p][blk][lane] for the blocks [blk0, blk0 + nb) (gamma_p h^3 chi~_p^H Y);
 // `scratch` holds gather_scratch_bytes(H, nb, sizeof(T)) bytes of per-slab partial sums.
@@ -102,7 +107,7 @@ cudaError_t launch_gather(const sparc_ham* H, const T* Y, int nblk_total, int bl
 template <class T>
 cudaError_t launch_pass(const sparc_ham* H, const T* Yin, const T* Yprev, T* Yout, const T* gc,
                         int nblk_total, int blk0, int nb, double alpha, double shift, double beta,
-                        cudaStream_t st);
+                        cudaStream_t st, int shape = 0);
 
 // Complex64, batched over k: the same two steps for the units of `ks`; `gc` and
 // the block buffers hold nunit_total units ([unit][Nd][NB] and [p][unit][NB]);

@@ -147,9 +147,9 @@ sparc_status build_tables(sparc_ham* H, const sparc_nonlocal* nl) {
   // per kernel tile shape: CTA item lists and per-z active slots
   T->ngrp = (int)grps.size();
   T->nsb = (int)sbs.size();
-  for (int si = 0; si < 2; ++si) {
+  for (int si = 0; si < 3; ++si) {
     Layout& Lo = T->lay[si];
-    const int TYk = (si == 0) ? Shape<float>::TY : Shape<cf32>::TY;
+    const int TYk = (si == 0) ? Shape<float>::TY : (si == 1) ? Shape<cf32>::TY : 8;
     Lo.tiles_x = ceil_div(n[0], TX);
     Lo.tiles_y = ceil_div(n[1], TYk);
     Lo.nchunk = ceil_div(n[2], ZC);
@@ -173,9 +173,9 @@ sparc_status build_tables(sparc_ham* H, const sparc_nonlocal* nl) {
     }
     // per (CTA, z, row group): CTA-local indices of the pieces that touch those rows;
     // a row group is the rows one warp covers (8 for FP32, 4 for complex64)
-    const int rgh = (si == 0) ? 8 : 4;
+    const int rgh = (si == 1) ? 4 : 8;
     const int nrg = TYk / rgh;
-    const int xrw = (si == 0) ? 2 : TX;          // x extent of a list (FP32: one warp's x-run)
+    const int xrw = (si == 1) ? TX : 2;          // x extent of a list (FP32: one warp's x-run)
     const int nxr = TX / xrw;
     std::vector<int> cptr(nct + 1, 0), citems, sptr((size_t)nct * ZC * nrg * nxr + 1, 0), sslots;
     Lo.max_items = 0;
@@ -246,6 +246,12 @@ void kslot(const sparc_ham* H, KSlot& s) {
   s.phx_r = (float)H->gd.ph_re[0]; s.phx_i = (float)H->gd.ph_im[0];
   s.phy_r = (float)H->gd.ph_re[1]; s.phy_i = (float)H->gd.ph_im[1];
   s.phz_r = (float)H->gd.ph_re[2]; s.phz_i = (float)H->gd.ph_im[2];
+}
+
+bool shape_usable(const sparc_ham* H, int shape) {
+  const Tables* T = (const Tables*)H->fast;
+  if (!usable(H) || shape < 0 || shape >= NSHAPE_F32) return false;
+  return shape == 0 || (T->lay[2].max_items <= MAXI && T->lay[2].max_steps <= MAXSTEP);
 }
 
 bool usable(const sparc_ham* H) {
@@ -339,9 +345,8 @@ struct __align__(16) Piece {
 
 constexpr int PX = TX + 2 * R;
 constexpr int RP = PX * NB + 8;     // row pitch in elements: rows of a warp land 8 banks apart
-template <class T> __host__ __device__ constexpr int plane_rows() { return Shape<T>::TY + 2 * R; }
-template <class T> struct Smem {
-  static constexpr int TY = Shape<T>::TY, PY = plane_rows<T>();
+template <class T, int TYv = Shape<T>::TY> struct Smem {
+  static constexpr int TY = TYv, PY = TYv + 2 * R;
   static constexpr int NRG = TY / (sizeof(T) == 4 ? 8 : 4);   // row groups of the z lists
   static constexpr int NXR = (sizeof(T) == 4) ? 8 : 1;         // x-runs of the z lists
   static constexpr int NL = ZC * NRG * NXR;                    // lists per CTA
@@ -394,23 +399,27 @@ __device__ __forceinline__ void mma_tf32x3(float (&d)[4], const float (&a)[4], c
   mma_tf32_16x8x8(d, ah, bh);
 }
 
-__global__ void __launch_bounds__(THREADS, 1)
+// TYT: tile rows (16 or 8); NT: threads (TYT * 32, two orbital pairs x 2 x-nodes each).
+template <int TYT, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT)
 k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* Yout,
           const float* __restrict__ gc, int nitems) {
   constexpr int Q = 2 * R + 1;
-  constexpr int PY = TY2 + 2 * R;
+  constexpr int PY = TYT + 2 * R;
+  using SM = Smem<float, TYT>;
+  static_assert(NT == TYT * 32, "two x-nodes x one orbital pair per thread");
   constexpr int CH = 2;                                  // 16-byte chunks per node (8 floats)
-  constexpr int NHC = (PX * PY * CH + THREADS - 1) / THREADS;
-  constexpr int NPC = (TX * TY2 * CH + THREADS - 1) / THREADS;
+  constexpr int NHC = (PX * PY * CH + NT - 1) / NT;
+  constexpr int NPC = (TX * TYT * CH + NT - 1) / NT;
   extern __shared__ __align__(16) unsigned char smraw[];
   float* planes = reinterpret_cast<float*>(smraw);
-  float* yps = reinterpret_cast<float*>(smraw + Smem<float>::planes);
-  float* vbs = reinterpret_cast<float*>(smraw + Smem<float>::planes + Smem<float>::yprev);
-  Piece* desc = reinterpret_cast<Piece*>(smraw + Smem<float>::planes + Smem<float>::yprev + Smem<float>::vb);
-  float* gcs = reinterpret_cast<float*>(smraw + Smem<float>::planes + Smem<float>::yprev + Smem<float>::vb +
-                                        Smem<float>::desc);
-  int* steps = reinterpret_cast<int*>(smraw + Smem<float>::planes + Smem<float>::yprev + Smem<float>::vb +
-                                      Smem<float>::desc + Smem<float>::gcs);
+  float* yps = reinterpret_cast<float*>(smraw + SM::planes);
+  float* vbs = reinterpret_cast<float*>(smraw + SM::planes + SM::yprev);
+  Piece* desc = reinterpret_cast<Piece*>(smraw + SM::planes + SM::yprev + SM::vb);
+  float* gcs = reinterpret_cast<float*>(smraw + SM::planes + SM::yprev + SM::vb +
+                                        SM::desc);
+  int* steps = reinterpret_cast<int*>(smraw + SM::planes + SM::yprev + SM::vb +
+                                      SM::desc + SM::gcs);
   const int t = threadIdx.x;
   const int op = t % 4;                  // orbital pair
   const int r8 = (t / 4) % 8;            // row within the warp
@@ -420,16 +429,16 @@ k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* 
   const int o2 = 2 * op;
   const int n1 = a.n1, n2 = a.n2, n3 = a.n3;
   const long long plane_el = (long long)n1 * n2 * NB;
-  const int ntiles = a.tiles_x * ((n2 + TY2 - 1) / TY2);
-  constexpr int NRG = Smem<float>::NRG, NXR = Smem<float>::NXR, NL = Smem<float>::NL;
-  static_assert(NRG == TY2 / 8 && NXR == TX / RX2, "one list per warp");
+  const int ntiles = a.tiles_x * ((n2 + TYT - 1) / TYT);
+  constexpr int NRG = SM::NRG, NXR = SM::NXR, NL = SM::NL;
+  static_assert(NRG == TYT / 8 && NXR == TX / RX2, "one list per warp");
 
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
     const int tile = item % ntiles;
     const int chunk = (item / ntiles) % a.nchunk;
     const int bi = item / (ntiles * a.nchunk);
     const int cta = tile * a.nchunk + chunk;
-    const int tx0 = (tile % a.tiles_x) * TX, ty0 = (tile / a.tiles_x) * TY2;
+    const int tx0 = (tile % a.tiles_x) * TX, ty0 = (tile / a.tiles_x) * TYT;
     const int zs = chunk * ZC;
     const int ze = min(zs + ZC, n3);
     const int blk = a.blk0 + bi;
@@ -437,14 +446,14 @@ k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* 
     const float* Y = Yin + boff;
     const int gy = ty0 + yl;
     const bool vy = gy < n2;
-    const int txv = min(TX, n1 - tx0), tyv = min(TY2, n2 - ty0);
+    const int txv = min(TX, n1 - tx0), tyv = min(TYT, n2 - ty0);
     bool vr[RX2];
 #pragma unroll
     for (int r = 0; r < RX2; ++r) vr[r] = vy && (tx0 + xl0 + r < n1);
 
     // ---- item tables
     const int it0 = __ldg(a.cptr + cta), nit = __ldg(a.cptr + cta + 1) - it0;
-    for (int i = t; i < nit; i += THREADS) {
+    for (int i = t; i < nit; i += NT) {
       const SubBox b = a.sb[__ldg(a.citems + it0 + i)];
       Piece pc;
       pc.gy0 = b.gy0; pc.gy1 = b.gy1; pc.gx0 = b.gx0; pc.gx1 = b.gx1;
@@ -461,15 +470,15 @@ k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* 
     }
     const size_t sb0 = (size_t)cta * NL;
     const int s0 = __ldg(a.sptr + sb0);
-    for (int k = t; k <= NL; k += THREADS) steps[k] = __ldg(a.sptr + sb0 + k) - s0;
+    for (int k = t; k <= NL; k += NT) steps[k] = __ldg(a.sptr + sb0 + k) - s0;
     const int nst = __ldg(a.sptr + sb0 + NL) - s0;
-    for (int k = t; k < nst; k += THREADS) steps[NL + 1 + k] = __ldg(a.sslots + s0 + k);
+    for (int k = t; k < nst; k += NT) steps[NL + 1 + k] = __ldg(a.sslots + s0 + k);
 
     // ---- copy descriptors
     int hs[NHC], hg[NHC];
 #pragma unroll
     for (int i = 0; i < NHC; ++i) {
-      const int idx = t + i * THREADS;
+      const int idx = t + i * NT;
       hs[i] = -1; hg[i] = 0;
       if (idx < PX * PY * CH) {
         const int pnt = idx / CH, ch = idx % CH;
@@ -487,9 +496,9 @@ k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* 
     int ps[NPC], pg[NPC];
 #pragma unroll
     for (int i = 0; i < NPC; ++i) {
-      const int idx = t + i * THREADS;
+      const int idx = t + i * NT;
       ps[i] = -1; pg[i] = 0;
-      if (idx < TX * TY2 * CH) {
+      if (idx < TX * TYT * CH) {
         const int node = idx / CH, ch = idx % CH;
         const int lx = node % TX, ly = node / TX;
         if (lx < txv && ly < tyv) {
@@ -499,7 +508,7 @@ k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* 
       }
     }
     const int vlx = t % TX, vly = t / TX;
-    const bool vv = t < TX * TY2 && vlx < txv && vly < tyv;
+    const bool vv = t < TX * TYT && vlx < txv && vly < tyv;
     const int vgo = (ty0 + vly) * n1 + tx0 + vlx;
 
     float2 q[Q][RX2];
@@ -522,9 +531,9 @@ k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* 
 #pragma unroll
       for (int i = 0; i < NHC; ++i)
         if (hs[i] >= 0) cp16(P + hs[i], Yz + hg[i]);
-      if (vv) cp4(vbs + (size_t)b * TY2 * TX + t, a.veff + (size_t)zw * n1 * n2 + vgo);
+      if (vv) cp4(vbs + (size_t)b * TYT * TX + t, a.veff + (size_t)zw * n1 * n2 + vgo);
       if (Yprev != nullptr) {
-        float* Pp = yps + (size_t)b * TY2 * TX * NB;
+        float* Pp = yps + (size_t)b * TYT * TX * NB;
         const float* Yp = Yprev + boff + (size_t)zw * plane_el;
 #pragma unroll
         for (int i = 0; i < NPC; ++i)
@@ -560,7 +569,7 @@ k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* 
         float2 w[RX2 + 2 * R];
 #pragma unroll
         for (int i = 0; i < RX2 + 2 * R; ++i) w[i] = lds2(row + (xl0 + i) * NB);
-        const float* V = vbs + (size_t)b * TY2 * TX + yl * TX + xl0;
+        const float* V = vbs + (size_t)b * TYT * TX + yl * TX + xl0;
 #pragma unroll
         for (int r = 0; r < RX2; ++r) {
           // one partial sum per axis: three short dependency chains instead of one long one
@@ -617,7 +626,7 @@ k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* 
       }
       if (vy) {
         // recurrence epilogue
-        const float* Pp = yps + (size_t)b * TY2 * TX * NB + (yl * TX + xl0) * NB + o2;
+        const float* Pp = yps + (size_t)b * TYT * TX * NB + (yl * TX + xl0) * NB + o2;
         float* out = Yout + boff + (size_t)z * plane_el + ((size_t)gy * n1 + tx0 + xl0) * NB + o2;
 #pragma unroll
         for (int r = 0; r < RX2; ++r) {
@@ -1318,7 +1327,7 @@ cudaError_t launch_pass_k(const sparc_ham* H0, const cf32* Yin, const cf32* Ypre
 template <class T>
 cudaError_t launch_pass(const sparc_ham* H, const T* Yin, const T* Yprev, T* Yout, const T* gc,
                         int nblk_total, int blk0, int nb, double alpha, double shift, double beta,
-                        cudaStream_t st) {
+                        cudaStream_t st, int shape) {
   if constexpr (FT<T>::cplx) {
     KSlots ks;
     ks.nk = 1;
@@ -1329,21 +1338,31 @@ cudaError_t launch_pass(const sparc_ham* H, const T* Yin, const T* Yprev, T* You
     return launch_pass_k(H, Yin, Yprev, Yout, gc, nblk_total, ks, st);
   } else {
     const Tables* Tb = (const Tables*)H->fast;
-    const Layout& Lo = Tb->lay[0];
+    const bool half = shape == 1 && shape_usable(H, 1);
+    const Layout& Lo = Tb->lay[half ? 2 : 0];
     PassArgs a = pass_args(H, Lo);
     a.blk0 = blk0;
     a.nblk_total = nblk_total;
     a.alpha = (float)alpha; a.shift = (float)shift; a.beta = (float)beta;
     a.alpha2 = make_float2(a.alpha, a.alpha);
     a.beta2 = make_float2(a.beta, a.beta);
-    const size_t smem = Smem<T>::total;
     // persistent CTAs over (tile, chunk, block) items
-    cudaError_t e = cudaFuncSetAttribute(k_pass_f2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     const int nitems = Lo.tiles_x * Lo.tiles_y * Lo.nchunk * nb;
-    const int nsm = H->ctx->nsm;
-    cudaEvent_t t0 = timing_begin(H->ctx, st);
-    k_pass_f2<<<std::min(nitems, std::max(nsm, 1)), THREADS, smem, st>>>(a, Yin, Yprev, Yout, gc, nitems);
+    const int nsm = std::max(H->ctx->nsm, 1);
+    cudaEvent_t t0 = nullptr;
+    if (half) {
+      constexpr size_t smem = Smem<float, 8>::total;
+      cudaError_t e = cudaFuncSetAttribute(k_pass_f2<8, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      t0 = timing_begin(H->ctx, st);
+      k_pass_f2<8, 256><<<std::min(nitems, 2 * nsm), 256, smem, st>>>(a, Yin, Yprev, Yout, gc, nitems);
+    } else {
+      constexpr size_t smem = Smem<float, 16>::total;
+      cudaError_t e = cudaFuncSetAttribute(k_pass_f2<16, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      t0 = timing_begin(H->ctx, st);
+      k_pass_f2<16, 512><<<std::min(nitems, nsm), 512, smem, st>>>(a, Yin, Yprev, Yout, gc, nitems);
+    }
     ++H->ctx->launches;
     timing_end(H->ctx, TK_FPASS, t0, st);
     return cudaGetLastError();
@@ -1351,19 +1370,20 @@ cudaError_t launch_pass(const sparc_ham* H, const T* Yin, const T* Yprev, T* You
 }
 
 template <class T>
-int items_per_block(const sparc_ham* H) {
-  const Layout& Lo = ((const Tables*)H->fast)->lay[FT<T>::cplx ? 1 : 0];
+int items_per_block(const sparc_ham* H, int shape) {
+  const int li = FT<T>::cplx ? 1 : (shape == 1 && shape_usable(H, 1)) ? 2 : 0;
+  const Layout& Lo = ((const Tables*)H->fast)->lay[li];
   return Lo.tiles_x * Lo.tiles_y * Lo.nchunk;
 }
-template int items_per_block<float>(const sparc_ham*);
-template int items_per_block<cf32>(const sparc_ham*);
+template int items_per_block<float>(const sparc_ham*, int);
+template int items_per_block<cf32>(const sparc_ham*, int);
 
 template cudaError_t launch_gather<float>(const sparc_ham*, const float*, int, int, int, float*, float*, cudaStream_t);
 template cudaError_t launch_gather<cf32>(const sparc_ham*, const cf32*, int, int, int, cf32*, cf32*, cudaStream_t);
 template cudaError_t launch_pass<float>(const sparc_ham*, const float*, const float*, float*, const float*,
-                                        int, int, int, double, double, double, cudaStream_t);
+                                        int, int, int, double, double, double, cudaStream_t, int);
 template cudaError_t launch_pass<cf32>(const sparc_ham*, const cf32*, const cf32*, cf32*, const cf32*,
-                                       int, int, int, double, double, double, cudaStream_t);
+                                       int, int, int, double, double, double, cudaStream_t, int);
 
 }  // namespace fast
 }  // namespace sparc

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cstdio>
 #include <new>
 
@@ -251,9 +252,9 @@ template sparc_status apply_block<cf64>(sparc_ham*, const cf64*, cf64*, int, lon
 template sparc_status apply_block<cf32>(sparc_ham*, const cf32*, cf32*, int, long long,
                                         cudaStream_t, const BlockWs&);
 
-// The filter on the tiled FP32 / complex64 kernels.  Blocks are processed in
-// groups whose two live buffers fit in L2 (about 72 MB), all m degrees per
-// group, so that the projection of each degree reads the block from L2.
+// The filter on the tiled FP32 / complex64 kernels: per degree one projection and
+// one pass launch over a group of blocks (all blocks unless a tuned configuration
+// groups them; a group runs all m degrees before the next group starts).
 template <class T>
 sparc_status filter_block_fast(sparc_ham* H, int m, double a, double b, double a0, const T* X, T* Y,
                                int ns, long long ld, cudaStream_t st, const BlockWs& w) {
@@ -263,21 +264,18 @@ sparc_status filter_block_fast(sparc_ham* H, int m, double a, double b, double a
   T* gc = (T*)w.gc;
   const double e = 0.5 * (b - a), c = 0.5 * (b + a);
   const double sigma1 = e / (a0 - c);
-  // blocks per group: the two live buffers of a group stay in L2 (<= 90 MB), and among
-  // those sizes take the one whose work items fill the SMs most evenly
-  const size_t per_blk = 2 * (size_t)H->gd.nd * NB * sizeof(T);
-  const int gmax = std::max(1, std::min(nblk, (int)((size_t)90 * 1024 * 1024 / per_blk)));
-  const int items_per_blk = fast::items_per_block<T>(H);
-  const int nsm = H->ctx->nsm;
-  int G = gmax;
-  double best = -1.0;
-  for (int g = std::max(1, gmax / 2); g <= gmax; ++g) {
-    const long long it = (long long)items_per_blk * g;
-    const double eff = (double)it / ((double)nsm * (double)((it + nsm - 1) / nsm));
-    if (eff > best + 1e-9 || (std::abs(eff - best) <= 1e-9 && g > G)) { best = eff; G = g; }
-  }
+  // Blocks per launch.  The pass and the projection are issue-bound far below HBM
+  // bandwidth, so keeping a group of blocks L2-resident across degrees does not pay
+  // for the partial last wave of every group launch: by default one launch per degree
+  // covers all blocks.  A tuned configuration (sparc_autotune_filter) may group blocks
+  // and, for FP32, choose the pass tile shape.
+  int shape = 0, G = nblk;
   const auto tu = H->ctx->tuned.find(std::make_tuple((int)DtypeOf<T>::v, H->gd.nd, ns, 1));
-  if (tu != H->ctx->tuned.end()) G = std::max(1, std::min(nblk, tu->second));
+  if (tu != H->ctx->tuned.end()) {
+    const int tunedG = tu->second & (TUNE_SHAPE - 1);
+    if (tunedG > 0) G = std::min(nblk, tunedG);
+    if constexpr (!std::is_same<T, cf32>::value) shape = tu->second / TUNE_SHAPE;
+  }
   T* scratch = (T*)w.tail;
   SPARC_CUDA(H->ctx, launch_to_blocks<T>(X, ld, ns, B0, H->gd.nd, nblk, st));
   ++H->ctx->launches;
@@ -288,12 +286,12 @@ sparc_status filter_block_fast(sparc_ham* H, int m, double a, double b, double a
     T* cur = B1;
     double sigma = sigma1;
     SPARC_CUDA(H->ctx, fast::launch_gather<T>(H, prev, nblk, g0, nb, gc, scratch, st));
-    SPARC_CUDA(H->ctx, fast::launch_pass<T>(H, prev, nullptr, cur, gc, nblk, g0, nb, sigma1 / e, c, 0.0, st));
+    SPARC_CUDA(H->ctx, fast::launch_pass<T>(H, prev, nullptr, cur, gc, nblk, g0, nb, sigma1 / e, c, 0.0, st, shape));
     for (int j = 1; j < m; ++j) {
       const double sigma_new = 1.0 / (2.0 / sigma1 - sigma);
       SPARC_CUDA(H->ctx, fast::launch_gather<T>(H, cur, nblk, g0, nb, gc, scratch, st));
       SPARC_CUDA(H->ctx, fast::launch_pass<T>(H, cur, prev, prev, gc, nblk, g0, nb, 2.0 * sigma_new / e, c,
-                                              -sigma * sigma_new, st));
+                                              -sigma * sigma_new, st, shape));
       std::swap(cur, prev);
       sigma = sigma_new;
     }
@@ -373,7 +371,7 @@ static sparc_status filter_kbatch(sparc_ham* const* Hs, int nk, int m, const dou
   const long long U = (long long)nk * nblk;
   int upl = 0;
   const auto tu = ctx->tuned.find(std::make_tuple((int)SPARC_C64, nd, ns, nk));
-  if (tu != ctx->tuned.end()) upl = tu->second;
+  if (tu != ctx->tuned.end()) upl = tu->second & (TUNE_SHAPE - 1);
   const KGroup G = kbatch_grouping(nk, nblk, fast::items_per_block<cf32>(H0), ctx->nsm, upl);
   const size_t bb = align256((size_t)U * nd * NB * sizeof(cf32));
   const size_t gb = align256((size_t)std::max(1, H0->nproj) * U * NB * sizeof(cf32));
@@ -825,6 +823,13 @@ sparc_status sparc_autotune_filter(sparc_ham* const* H, int nk, sparc_dtype dtyp
     std::sort(cand.begin(), cand.end());
     cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
     if (f32) cand.erase(std::remove_if(cand.begin(), cand.end(), [&](int u) { return u > nblk; }), cand.end());
+  }
+  // FP32: every blocks-per-launch candidate with each pass tile shape the grid allows
+  if (f32) {
+    const size_t nc = cand.size();
+    for (int sh = 1; sh < fast::NSHAPE_F32; ++sh)
+      if (fast::shape_usable(H[0], sh))
+        for (size_t i = 0; i < nc; ++i) cand.push_back(cand[i] + sh * TUNE_SHAPE);
   }
   const int mt = std::min(m, 3);
   cudaStream_t st = (cudaStream_t)stream;

@@ -17,6 +17,7 @@ import numpy as np
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libsparc.so")
 
 F64, F32, C128, C64 = 0, 1, 2, 3
+TUNE_SHAPE = 1 << 20   # launch configuration code = blocks per launch + TUNE_SHAPE * tile shape
 RR_FP64, RR_MIXED = 0, 1
 STATUS = {0: "SPARC_OK", 1: "SPARC_ERR_INVALID_ARG", 2: "SPARC_ERR_OOM", 3: "SPARC_ERR_CUDA",
           4: "SPARC_ERR_NOT_POSDEF", 5: "SPARC_ERR_NO_CONVERGENCE", 6: "SPARC_ERR_TIMEOUT"}

@@ -88,3 +88,29 @@ def test_filter_graph_rejects_bad_bounds(ctx):
     G.launch()
     torch.cuda.synchronize()
     G.close()
+
+
+def test_half_tile_fp32_pass_matches_full_tile_and_oracle(ctx):
+    """The FP32 pass with 16 x 8 tiles (256-thread CTAs, two per SM) takes every node
+    and projector piece in the order of the 16 x 16 tile, so the filter is the same bit
+    for bit; and it matches the oracle."""
+    from paper_1603_04339_gb300 import sparc
+    wl = synth.small_case(n=(24, 22, 26), natom=4, ns=37, m=9, seed=77)
+    H = sparc.Hamiltonian.from_workload(ctx, wl)
+    X = torch.from_numpy(synth.random_orbitals(wl.nd, wl.ns, 808).astype(np.float32)).cuda()
+    a0, b = -3.0, 60.0
+    a = a0 + (b - a0) * (wl.ns / wl.nd) ** (2.0 / 3.0)
+    outs = []
+    for code in (0, 2, 3 + sparc.TUNE_SHAPE, 1 + sparc.TUNE_SHAPE):
+        sparc.sparc_set_filter_units(ctx, sparc.F32, wl.nd, wl.ns, 1, code)
+        Y = torch.full_like(X, float("nan"))
+        sparc.sparc_cheb_filter(H, wl.m, a, b, a0, X, Y)
+        torch.cuda.synchronize()
+        outs.append(Y)
+    sparc.sparc_set_filter_units(ctx, sparc.F32, wl.nd, wl.ns, 1, 0)
+    for Y in outs[1:]:
+        assert torch.equal(Y, outs[0])
+    Hor = O.OracleH(wl)
+    cols = [0, 17, 36]
+    Yo = O.cheb_filter(Hor, X[cols].cpu().numpy().astype(np.float64), wl.m, a, b, a0)
+    assert _colerr(outs[2][cols].cpu().numpy().astype(np.float64), Yo) < 1e-4
