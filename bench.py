@@ -377,8 +377,16 @@ def scf_time_to_solution(sparc, synth, torch, tol_per_atom=1e-5, max_iter=80, tr
             if name != "fp64" and it >= 5 and info["vresid"] < 1e-6:
                 break
         runs[name] = hist
+        if name == "fp64":   # the converged density, to rate the two starting densities
+            rho_c = torch.empty(wl.nd, dtype=torch.float64, device="cuda")
+            bq = torch.empty_like(rho_c)
+            S.read("rho", rho_c)
+            S.read("b", bq)
         S.close()
         H.close()
+    y = LD.predict(ctx, net, sysd)
+    starts = {"atomic": (-bq).clamp(min=0.0), "learned": (-bq + scale * y.double()).clamp(min=0.0)}
+    start_err = {k: float((v * (rho_c.sum() / v.sum()) - rho_c).norm() / rho_c.norm()) for k, v in starts.items()}
     net.close()
     ctx.close()
     E_ref = runs["fp64"][-1][1]
@@ -393,7 +401,8 @@ def scf_time_to_solution(sparc, synth, torch, tol_per_atom=1e-5, max_iter=80, tr
                        "kT=0.01 Ha, Anderson 0.3/7, 4 CheFSI passes at the first iteration",
            "tolerance_ha_per_atom": tol_per_atom, "E_ref_ha": E_ref,
            "learned": {"train_cells": train_cells, "data_seconds": t_data, "train_seconds": t_train,
-                       "loss_initial": lhist[0], "loss_final": lhist[-1]}}
+                       "loss_initial": lhist[0], "loss_final": lhist[-1],
+                       "start_density_rel_error": start_err}}
     for name, hist in runs.items():
         k, t = reach(hist)
         out[name] = {"iterations_to_tol": k, "seconds_to_tol": t, "iterations_run": len(hist),
