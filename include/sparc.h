@@ -170,9 +170,10 @@ sparc_status sparc_cheb_filter_batch(sparc_ham* const* H, int nk, sparc_dtype dt
                                      const void* X, void* Y, int ns, int64_t ld, void* stream);
 
 /* Launch-shape autotuner of the filter.  Times sparc_cheb_filter_batch (degree
- * min(m, 3), arguments as there) for several launch configurations, keeps the
- * fastest in the context and returns its code in *units (0 if the dtype has a
- * single launch shape) with its time in *ms.  A code is
+ * min(m, 4), arguments as there) for several launch configurations, keeps the
+ * fastest in the context (among those within 3% of the fastest, the one with
+ * the most blocks per launch) and returns its code in *units (0 if the dtype has
+ * a single launch shape) with its time in *ms.  A code is
  *   blocks per launch + SPARC_TUNE_SHAPE * tile shape,
  * blocks of 8 orbitals per launch being fractions and multiples of the number
  * whose two live buffers fit in L2, all blocks of one k, or all blocks of all k;

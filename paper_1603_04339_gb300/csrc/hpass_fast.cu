@@ -726,10 +726,13 @@ k_pass_c2(PassArgs a, const __grid_constant__ KSlots ks, const cf32* __restrict_
       pc.base = (int)b.chi4_off + b.bx0 - b.gx0 + b.nbx * (b.by0 - b.gy0) + pc.sz * (b.bz0 - b.gz0);
       pc.ph_re = b.ph_re; pc.ph_im = b.ph_im;
       desc[i] = pc;
+      // the piece's Bloch phase folded into its coefficients: ph * gc
       for (int l = 0; l < 4; ++l) {
         const int p = a.grp[b.grp].proj[l];
-        for (int oo = 0; oo < NB; ++oo)
-          gcs[(i * 4 + l) * NB + oo] = (p >= 0) ? gc[((size_t)p * a.nblk_total + blk) * NB + oo] : cf32{0.f, 0.f};
+        for (int oo = 0; oo < NB; ++oo) {
+          const cf32 g = (p >= 0) ? gc[((size_t)p * a.nblk_total + blk) * NB + oo] : cf32{0.f, 0.f};
+          gcs[(i * 4 + l) * NB + oo] = cf32{b.ph_re * g.x - b.ph_im * g.y, b.ph_re * g.y + b.ph_im * g.x};
+        }
       }
     }
     const size_t sb0 = (size_t)cta * NL;
@@ -868,7 +871,7 @@ k_pass_c2(PassArgs a, const __grid_constant__ KSlots ks, const cf32* __restrict_
           acc[r] = __fadd2_rn(sx, __fadd2_rn(sy, sz));
         }
         // nonlocal: sum over the pieces active at (z, this row group) of
-        // phase * sum_l chi_l(node) gc_l(orbital)
+        // sum_l chi_l(node) (phase gc_l)(orbital)
         const int ea = steps[sidx * NRG + yg], eb = steps[sidx * NRG + yg + 1];
         const int x0r = tx0 + xl0;
         for (int e = ea; e < eb; ++e) {
@@ -876,7 +879,6 @@ k_pass_c2(PassArgs a, const __grid_constant__ KSlots ks, const cf32* __restrict_
           const int4 pa = *reinterpret_cast<const int4*>(&desc[it].gy0);   // gy0 gy1 gx0 gx1
           if (gy < pa.x || gy >= pa.y) continue;
           const int4 pb = *reinterpret_cast<const int4*>(&desc[it].base);  // base sy sz -
-          const float2 ph = *reinterpret_cast<const float2*>(&desc[it].ph_re);
           const float2 g0 = ld2(gcs + (it * 4 + 0) * NB + o), g1 = ld2(gcs + (it * 4 + 1) * NB + o);
           const float2 g2 = ld2(gcs + (it * 4 + 2) * NB + o), g3 = ld2(gcs + (it * 4 + 3) * NB + o);
           const int rowoff = pb.x + pb.y * gy + pb.z * z;
@@ -885,12 +887,10 @@ k_pass_c2(PassArgs a, const __grid_constant__ KSlots ks, const cf32* __restrict_
             const int gx = x0r + r;
             if (gx < pa.z || gx >= pa.w) continue;
             const float4 c4 = __ldg(S.chi4 + rowoff + gx);
-            float2 d = __fmul2_rn(f2(c4.x), g0);
-            d = __ffma2_rn(f2(c4.y), g1, d);
-            d = __ffma2_rn(f2(c4.z), g2, d);
-            d = __ffma2_rn(f2(c4.w), g3, d);
-            acc[r] = __ffma2_rn(f2(ph.x), d, acc[r]);
-            acc[r] = __ffma2_rn(make_float2(-ph.y, ph.y), make_float2(d.y, d.x), acc[r]);
+            acc[r] = __ffma2_rn(f2(c4.x), g0, acc[r]);
+            acc[r] = __ffma2_rn(f2(c4.y), g1, acc[r]);
+            acc[r] = __ffma2_rn(f2(c4.z), g2, acc[r]);
+            acc[r] = __ffma2_rn(f2(c4.w), g3, acc[r]);
           }
         }
         // recurrence epilogue

@@ -114,3 +114,25 @@ def test_half_tile_fp32_pass_matches_full_tile_and_oracle(ctx):
     cols = [0, 17, 36]
     Yo = O.cheb_filter(Hor, X[cols].cpu().numpy().astype(np.float64), wl.m, a, b, a0)
     assert _colerr(outs[2][cols].cpu().numpy().astype(np.float64), Yo) < 1e-4
+
+
+def test_filter_graph_of_complex_cells(ctx):
+    """A graph of two complex64 cells at different k equals their own filter calls."""
+    from paper_1603_04339_gb300 import sparc
+    cells = [synth.small_case(n=(16, 14, 15), natom=2, ns=12, m=5, k=(0.2, -0.1, 0.3), seed=21),
+             synth.small_case(n=(18, 16, 14), natom=3, ns=20, m=6, k=(-0.25, 0.0, 0.15), seed=22)]
+    Hs = [sparc.Hamiltonian.from_workload(ctx, c) for c in cells]
+    X = [torch.from_numpy(synth.random_orbitals(c.nd, c.ns, 70 + i, complex_=True).astype(np.complex64)).cuda()
+         for i, c in enumerate(cells)]
+    Y = [torch.full_like(x, float("nan")) for x in X]
+    m = [c.m for c in cells]
+    a, b, a0 = _bounds(cells)
+    G = sparc.FilterGraph(Hs, m, a, b, a0, X, Y, nbranch=2)
+    G.launch()
+    torch.cuda.synchronize()
+    for i, H in enumerate(Hs):
+        ref = torch.empty_like(X[i])
+        sparc.sparc_cheb_filter(H, m[i], a[i], b[i], a0[i], X[i], ref)
+        torch.cuda.synchronize()
+        assert torch.equal(ref, Y[i]), i
+    G.close()

@@ -141,10 +141,34 @@ def test_autotuned_grouping_keeps_the_result(ctx, si27):
     sparc.sparc_cheb_filter_batch(Hs, wl.m, a, b, a0, X, Y0)
     Yt = torch.empty_like(X)
     units, ms = sparc.sparc_autotune_filter(Hs, wl.m, a, b, a0, X, Yt)
-    print(f"autotuned units per launch {units}, {ms:.2f} ms for degree 3")
+    print(f"autotuned units per launch {units}, {ms:.2f} ms for degree 4")
     assert units > 0 and ms > 0
     Y1 = torch.empty_like(X)
     sparc.sparc_cheb_filter_batch(Hs, wl.m, a, b, a0, X, Y1)
     torch.cuda.synchronize()
     assert torch.equal(Y0, Y1)
     sparc.sparc_set_filter_units(ctx, sparc.C64, wl.nd, wl.ns, len(Hs), 0)
+
+
+def test_batch_of_more_k_points_than_one_launch_holds(ctx):
+    """35 k-points: launches hold at most 32 k slots, so the batch spans several
+    launch groups; still bit-identical to the per-k filter."""
+    from paper_1603_04339_gb300 import sparc
+    base = synth.small_case(n=(16, 14, 15), h=(0.55, 0.6, 0.5), natom=2, ns=9, m=4, seed=5)
+    L = np.array([base.n[s] * base.h[s] for s in range(3)])
+    rng = np.random.default_rng(9)
+    kpts = 2 * math.pi * rng.uniform(-0.5, 0.5, (35, 3)) / L
+    wl = synth.Workload("small_35k", base.n, base.h, 6, kpts, np.full(35, 1 / 35), base.veff, base.atoms,
+                        base.proj, base.ns, base.m, base.seed)
+    Hs = [sparc.Hamiltonian.from_workload(ctx, wl, k) for k in range(35)]
+    X = torch.from_numpy(np.stack([synth.random_orbitals(wl.nd, wl.ns, 50 + k, complex_=True)
+                                   for k in range(35)]).astype(np.complex64)).cuda()
+    a, b, a0 = _bounds(35, wl.nd, wl.ns)
+    Yref = _filter_each(sparc, Hs, wl.m, a, b, a0, X)
+    for units in (0, 3 * 2):
+        sparc.sparc_set_filter_units(ctx, sparc.C64, wl.nd, wl.ns, 35, units)
+        Y = torch.full_like(X, float("nan"))
+        sparc.sparc_cheb_filter_batch(Hs, wl.m, a, b, a0, X, Y)
+        torch.cuda.synchronize()
+        assert torch.equal(Y, Yref), units
+    sparc.sparc_set_filter_units(ctx, sparc.C64, wl.nd, wl.ns, 35, 0)

@@ -108,6 +108,12 @@ def test_starting_density_and_potential_match_the_oracle(ctx):
     big = r0 > 1e-4 * np.max(r0)
     assert np.max(dv[big]) < 1e-9 * np.max(np.abs(v0))
     assert np.max(dv) < 1e-6 * np.max(np.abs(v0))
+    # only before the first step
+    U = torch.from_numpy(sysd.U0.copy()).cuda()
+    eig = torch.zeros(wl.ns, dtype=torch.float64, device="cuda")
+    sparc.sparc_scf_step(S, U, eig, wl.m)
+    with pytest.raises(sparc.SparcError):
+        S.set_density(None, 0.0)
     S.close()
     H.close()
 
