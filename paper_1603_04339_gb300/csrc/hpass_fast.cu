@@ -938,11 +938,15 @@ __device__ __forceinline__ void gather_row(T (&s)[NBM][4], const float4* __restr
     for (int u = 0; u < NXS; ++u)
 #pragma unroll
       for (int b = 0; b < NBM; ++b) {
-        if constexpr (FT<T>::cplx) {
-          s[b][0].x = fmaf(c4[u].x, y[u][b].x, s[b][0].x); s[b][0].y = fmaf(c4[u].x, y[u][b].y, s[b][0].y);
-          s[b][1].x = fmaf(c4[u].y, y[u][b].x, s[b][1].x); s[b][1].y = fmaf(c4[u].y, y[u][b].y, s[b][1].y);
-          s[b][2].x = fmaf(c4[u].z, y[u][b].x, s[b][2].x); s[b][2].y = fmaf(c4[u].z, y[u][b].y, s[b][2].y);
-          s[b][3].x = fmaf(c4[u].w, y[u][b].x, s[b][3].x); s[b][3].y = fmaf(c4[u].w, y[u][b].y, s[b][3].y);
+        if constexpr (FT<T>::cplx) {   // (re, im) packed: one FFMA2 per projector
+          const float2 yv = make_float2(y[u][b].x, y[u][b].y);
+          const float cl[4] = {c4[u].x, c4[u].y, c4[u].z, c4[u].w};
+#pragma unroll
+          for (int l = 0; l < 4; ++l) {
+            const float2 r = __ffma2_rn(make_float2(cl[l], cl[l]), yv, make_float2(s[b][l].x, s[b][l].y));
+            s[b][l].x = r.x;
+            s[b][l].y = r.y;
+          }
         } else {
           s[b][0] = fmaf(c4[u].x, y[u][b], s[b][0]); s[b][1] = fmaf(c4[u].y, y[u][b], s[b][1]);
           s[b][2] = fmaf(c4[u].z, y[u][b], s[b][2]); s[b][3] = fmaf(c4[u].w, y[u][b], s[b][3]);
