@@ -117,10 +117,11 @@ def occupations(lam: np.ndarray, mu: float, kT: float) -> np.ndarray:
     return out
 
 
-def fermi_level(lam: np.ndarray, Ne: float, kT: float, wk: float = 1.0) -> float:
-    """lambda_f such that 2 sum_n w g_n = N_e, by Brent's method (Section 5)."""
+def fermi_level(lam: np.ndarray, Ne: float, kT: float, wk=1.0) -> float:
+    """lambda_f such that 2 sum_n w_n g_n = N_e, by Brent's method (Section 5); w: one
+    weight, or the k-point weight of every value (the Brillouin-zone sum of Eq. EL)."""
     lam = np.asarray(lam, dtype=np.float64)
-    f = lambda mu: 2.0 * wk * float(np.sum(occupations(lam, mu, kT))) - Ne
+    f = lambda mu: 2.0 * float(np.sum(wk * occupations(lam, mu, kT))) - Ne
     return scipy.optimize.brentq(f, lam.min() - 1.0, lam.max() + 1.0, xtol=1e-14, maxiter=500)
 
 
@@ -178,19 +179,19 @@ def lda(rho: np.ndarray):
     return eps, v
 
 
-def entropy_term(g: np.ndarray, kT: float, wk: float = 1.0) -> float:
-    """2 kT sum_n w (g ln g + (1-g) ln(1-g)), with 0 ln 0 = 0."""
+def entropy_term(g: np.ndarray, kT: float, wk=1.0) -> float:
+    """2 kT sum_n w_n (g ln g + (1-g) ln(1-g)), with 0 ln 0 = 0 (w as in fermi_level)."""
     g = np.asarray(g, dtype=np.float64)
     t = np.zeros_like(g)
     m = (g > 0) & (g < 1)
     t[m] = g[m] * np.log(g[m]) + (1.0 - g[m]) * np.log(1.0 - g[m])
-    return 2.0 * kT * wk * float(np.sum(t))
+    return 2.0 * kT * float(np.sum(wk * t))
 
 
 def free_energy(lam, g, rho, b, phi, eps_xc, v_xc, h, e_self, kT, e_c=0.0, wk=1.0):
     """Eq. FreeEnergy:GroundState:DFT:discrete.  Returns (F, parts)."""
     dv = h[0] * h[1] * h[2]
-    e_band = 2.0 * wk * float(np.sum(np.asarray(g) * np.asarray(lam)))
+    e_band = 2.0 * float(np.sum(wk * np.asarray(g) * np.asarray(lam)))
     e_xc = dv * float(np.sum(eps_xc * rho - v_xc * rho))
     e_el = dv * float(np.sum(0.5 * (b - rho) * phi))
     e_ent = entropy_term(g, kT, wk)
@@ -265,6 +266,47 @@ def starting_density(b, dy, scale, Ne, h):
 def starting_potential(rho0, b, n, h, n_o):
     """V_in = phi[rho0 + b] + V_xc[rho0] (Poisson and LDA of this module)."""
     return poisson(rho0 + b, n, h, n_o) + lda(rho0)[1]
+
+
+def scf_iteration_k(Hs, wk, Us, lam_prevs, v0, b, e_self, Ne, kT, m, lanczos_k=10, passes=1):
+    """One SCF iteration with the Brillouin-zone sum over k-points (Section 2: the
+    density and the electron count are k-point-weighted sums; Eq. EL): per k-point the
+    CheFSI of scf_iteration (its Lanczos start vector v0 is complex; a k = 0
+    Hamiltonian takes the first Nd doubles of its (re, im) storage, as the CUDA path
+    does), then one Fermi level for all Ritz values with their k-point weights,
+    rho = sum_k density(U_k, g_k, h, w_k), and the grid steps of scf_iteration."""
+    nk = len(Hs)
+    lams, Uo, bounds = [], [], []
+    for k in range(nk):
+        H = Hs[k]
+        v = v0 if H.is_complex else np.ascontiguousarray(v0, dtype=np.complex128).view(np.float64)[: H.nd]
+        a0l, bb, _ = O.lanczos_bounds(H, v, lanczos_k)
+        U, lp = np.atleast_2d(Us[k]), lam_prevs[k]
+        ns = U.shape[0]
+        for _ in range(passes):
+            if lp is None:
+                a0 = a0l
+                a = a0 + (bb - a0) * (ns / H.nd) ** (2.0 / 3.0)
+            else:
+                a0, a = float(lp[0]), float(lp[-1])
+            Yf = O.cheb_filter(H, U, m, a, bb, a0)
+            lp, U, _, _ = O.rayleigh_ritz(H, Yf)
+        lams.append(lp)
+        Uo.append(U)
+        bounds.append((a0, a, bb))
+    lam = np.concatenate(lams)
+    w = np.concatenate([np.full(len(l), wk[k]) for k, l in enumerate(lams)])
+    mu = fermi_level(lam, Ne, kT, w)
+    g = occupations(lam, mu, kT)
+    ns = len(lams[0])
+    H0 = Hs[0]
+    rho = sum(density(Uo[k], g[k * ns:(k + 1) * ns], H0.h, wk[k]) for k in range(nk))
+    phi = poisson(rho + b, H0.n, H0.h, H0.n_o)
+    eps, vxc = lda(rho)
+    v_out = phi + vxc
+    F, parts = free_energy(lam, g, rho, b, phi, eps, vxc, H0.h, e_self, kT, wk=w)
+    return {"lam": lam, "U": Uo, "mu": mu, "g": g, "rho": rho, "phi": phi, "v_out": v_out, "F": F,
+            "parts": parts, "bounds": bounds}
 
 
 def grad_weights(n_o: int, h: float) -> np.ndarray:

@@ -230,3 +230,24 @@ def test_starting_density_normalisation_and_atomic_special_case():
     v = S.starting_potential(r0, b, wl.n, wl.h, 6)
     # rho0 + b vanishes up to the clipped truncation tail of b, so phi is small
     assert np.max(np.abs(v - S.lda(r0)[1])) < 1e-3 * np.max(np.abs(v))
+
+
+def test_kpoint_iteration_reduces_to_gamma_for_repeated_kpoints():
+    """The Brillouin-zone sum with the Gamma point twice at weights 1/2 is the Gamma-point
+    iteration: the same Fermi level, density and free energy (a missing or doubled weight
+    would change the electron count, the density or the band energy)."""
+    from paper_1603_04339_gb300 import synth
+    sysd = synth.scf_small()
+    wl = sysd.wl
+    b, e_self, _ = S.pseudocharge(wl.n, wl.h, 6, wl.atoms, sysd.Z, sysd.rc)
+    H = O.OracleH(wl, veff=S.lda(-b)[1])
+    one = S.scf_iteration(H, sysd.U0.copy(), None, sysd.v0, b, e_self, sysd.nelec, 0.01, wl.m)
+    v0c = np.concatenate([sysd.v0, np.zeros(wl.nd)]).view(np.complex128)
+    two = S.scf_iteration_k([H, H], [0.5, 0.5], [sysd.U0.copy(), sysd.U0.copy()], [None, None], v0c, b, e_self,
+                            sysd.nelec, 0.01, wl.m)
+    assert np.allclose(two["lam"], np.concatenate([one["lam"], one["lam"]]), rtol=0, atol=1e-12)
+    assert abs(two["mu"] - one["mu"]) < 1e-12
+    assert np.max(np.abs(two["rho"] - one["rho"])) < 1e-12 * np.max(one["rho"])
+    assert abs(two["F"] - one["F"]) < 1e-11 * abs(one["F"])
+    dv = wl.h[0] * wl.h[1] * wl.h[2]
+    assert abs(dv * two["rho"].sum() - sysd.nelec) < 1e-9
