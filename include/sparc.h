@@ -352,8 +352,19 @@ typedef struct sparc_scf sparc_scf;
 /* Pseudocharges, self energy and the starting V_eff of H.  S uses H in every call but
  * sparc_scf_destroy, so H must outlive the calls on S. */
 sparc_status sparc_scf_create(sparc_ham* H, const sparc_scf_desc* d, sparc_scf** S);
+/* The same with the Brillouin-zone sum over nk k-points (Section 2; Eq. EL with the
+ * k-point weights): H[k] is H(k) for k-point k (equal grids, stencils and projector
+ * boxes, one context), wk[k] > 0 its weight (host; they should sum to 1).  The
+ * density is 2 sum_k w_k sum_n g_nk |psi_nk|^2 with one Fermi level for all k;
+ * every step updates V_eff of every H[k].  With any k != 0, d->v0 holds Nd complex
+ * values (2 Nd doubles). */
+sparc_status sparc_scf_create_k(sparc_ham* const* H, int nk, const double* wk, const sparc_scf_desc* d,
+                                sparc_scf** S);
 /* One iteration on the orbitals U (device, column-major Nd x ns, ld >= Nd, dtype F64, F32,
  * C128 or C64; updated in place to the rotated orbitals); eig: device, ns Ritz values.
+ * With nk k-points, U holds nk such blocks (k-point k at element k ns ld) and eig
+ * nk ns values; the filter of all k runs batched (sparc_cheb_filter_batch), and
+ * info's filter bounds are those of the first k-point.  nk ns <= 4096.
  * 2 ns must exceed N_e.  Synchronises `stream`. */
 sparc_status sparc_scf_step(sparc_scf* S, sparc_dtype dtype, int m, void* U, int ns, int64_t ld, double* eig,
                             sparc_scf_info* info, void* stream);
@@ -369,7 +380,7 @@ sparc_status sparc_scf_read(const sparc_scf* S, int which, double* dst, void* st
 sparc_status sparc_scf_set_density(sparc_scf* S, const float* dy, double scale, void* stream);
 void sparc_scf_destroy(sparc_scf* S);
 /* Atomic forces at the state of the last sparc_scf_step (Section 3.6): U are its
- * rotated orbitals (F64 or F32, Gamma point), with its occupations and electrostatic
+ * rotated orbitals (F64 or F32, Gamma point, one k-point), with its occupations and electrostatic
  * potential.  f_host (host, 9*natom doubles): [0, 3 natom) the forces, then the local
  * (Eq. LocalForce:Discrete) and the nonlocal (Eq. NonlocForce:Discrete, the projector
  * derivative moved onto nabla_h psi) parts, 3 per atom, Ha/bohr; the overlap

@@ -128,10 +128,12 @@ __device__ __forceinline__ double fermi_occ(double lam, double mu, double kT) {
   return 1.0 / (1.0 + exp(x));
 }
 
-// 2 sum_n g_n(mu) - Ne, summed by the block in a fixed order, result in every thread
-__device__ double nel_minus(const double* lam, int ns, double mu, double kT, double Ne, double* sh, double* bc) {
+// 2 sum_n w_n g_n(mu) - Ne (w: the k-point weight of each value, null: 1), summed by
+// the block in a fixed order, result in every thread
+__device__ double nel_minus(const double* lam, const double* wt, int ns, double mu, double kT, double Ne,
+                            double* sh, double* bc) {
   double v = 0.0;
-  for (int n = threadIdx.x; n < ns; n += blockDim.x) v += fermi_occ(lam[n], mu, kT);
+  for (int n = threadIdx.x; n < ns; n += blockDim.x) v += (wt ? wt[n] : 1.0) * fermi_occ(lam[n], mu, kT);
   const double s = block_sum(v, sh);
   if (threadIdx.x == 0) *bc = 2.0 * s - Ne;
   __syncthreads();
@@ -140,19 +142,21 @@ __device__ double nel_minus(const double* lam, int ns, double mu, double kT, dou
   return r;
 }
 
-// lambda_f with 2 sum g_n = Ne (Eq. EL), by Brent's method on [lam_min - 1, lam_max + 1]:
-// inverse quadratic interpolation or secant steps when they stay inside the bracket and
-// shrink fast enough, bisection otherwise.  Then the occupations, band energy, entropy
-// term and electron count.
-__global__ void __launch_bounds__(TPB) k_fermi(const double* __restrict__ lam, int ns, double Ne, double kT,
-                                               double* __restrict__ occ, double* scal) {
+// lambda_f with 2 sum_n w_n g_n = Ne (Eq. EL; with k-points the Brillouin-zone sum
+// weights each value by its k-point's weight w_n, null: 1), by Brent's method on
+// [lam_min - 1, lam_max + 1]: inverse quadratic interpolation or secant steps when they
+// stay inside the bracket and shrink fast enough, bisection otherwise.  Then the
+// occupations, band energy, entropy term and electron count.
+__global__ void __launch_bounds__(TPB) k_fermi(const double* __restrict__ lam, const double* __restrict__ wt,
+                                               int ns, double Ne, double kT, double* __restrict__ occ,
+                                               double* scal) {
   __shared__ double sh[32], bc;
   __shared__ double st[8];   // Brent state shared with the block: next abscissa, done flag
   double lo = lam[0], hi = lam[0];
   for (int n = 1; n < ns; ++n) { lo = fmin(lo, lam[n]); hi = fmax(hi, lam[n]); }
   double a = lo - 1.0, bb = hi + 1.0;
-  double fa = nel_minus(lam, ns, a, kT, Ne, sh, &bc);
-  double fb = nel_minus(lam, ns, bb, kT, Ne, sh, &bc);
+  double fa = nel_minus(lam, wt, ns, a, kT, Ne, sh, &bc);
+  double fb = nel_minus(lam, wt, ns, bb, kT, Ne, sh, &bc);
   double c = a, fc = fa, d = bb - a, e = d;
   const double xtol = 1e-14, eps = 2.220446049250313e-16;
   for (int it = 0; it < 300; ++it) {
@@ -196,16 +200,17 @@ __global__ void __launch_bounds__(TPB) k_fermi(const double* __restrict__ lam, i
     const bool done = st[1] != 0.0;
     __syncthreads();
     if (done) break;
-    fb = nel_minus(lam, ns, bb, kT, Ne, sh, &bc);
+    fb = nel_minus(lam, wt, ns, bb, kT, Ne, sh, &bc);
   }
   const double mu = bb;
   double eb = 0.0, en = 0.0, ne = 0.0;
   for (int n = threadIdx.x; n < ns; n += blockDim.x) {
     const double g = fermi_occ(lam[n], mu, kT);
+    const double w = wt ? wt[n] : 1.0;
     occ[n] = g;
-    eb += g * lam[n];
-    ne += g;
-    if (g > 0.0 && g < 1.0) en += g * log(g) + (1.0 - g) * log(1.0 - g);
+    eb += w * g * lam[n];
+    ne += w * g;
+    if (g > 0.0 && g < 1.0) en += w * (g * log(g) + (1.0 - g) * log(1.0 - g));
   }
   const double seb = block_sum(eb, sh);
   const double sen = block_sum(en, sh);
@@ -219,15 +224,17 @@ __global__ void __launch_bounds__(TPB) k_fermi(const double* __restrict__ lam, i
 }
 
 // ------------------------------------------------------------------ density
+// rho (+)= scale w sum_n g_n |U_n|^2: one k-point's share (accumulate after the first)
 template <class T>
 __global__ void __launch_bounds__(TPB) k_density(const T* __restrict__ U, long long ld, int ns, long long nd,
-                                                 const double* __restrict__ occ, double scale,
-                                                 double* __restrict__ rho) {
+                                                 const double* __restrict__ occ, double scale, double w,
+                                                 int accumulate, double* __restrict__ rho) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= nd) return;
   double s = 0.0;
   for (int n = 0; n < ns; ++n) s += occ[n] * Tr<T>::abs2(U[g + (long long)n * ld]);
-  rho[g] = scale * s;
+  const double v = scale * (w * s);
+  rho[g] = accumulate ? rho[g] + v : v;
 }
 
 // ------------------------------------------------------------------ Poisson (CG)
@@ -659,7 +666,11 @@ struct sparc_scf {
   double *d_part = nullptr, *d_sums = nullptr, *d_scal = nullptr, *d_occ = nullptr, *d_v0 = nullptr;
   void* d_Y = nullptr;
   size_t ybytes = 0;
-  std::vector<double> lam_prev;
+  std::vector<sparc_ham*> Hk;      // one Hamiltonian per k-point (Hk[0] == H)
+  std::vector<double> wk;          // k-point weights
+  std::vector<std::vector<double>> lamk;   // Ritz values of the last step, per k
+  double* d_wt = nullptr;          // weight of every Ritz value (nk > 1)
+  int wt_n = 0;
   int nproj = 0;
   int* d_patom = nullptr;          // atom of each projector (forces); null if not given
   int last_ns = 0;                 // orbitals of the last iteration (occupations in d_occ)
@@ -671,7 +682,7 @@ namespace scf {
 static void free_scf(sparc_scf* S) {
   void* ps[] = {S->d_atoms, S->d_b, S->d_rho, S->d_phi, S->d_eps, S->d_vxc, S->d_vout, S->d_fres,
                 S->d_vnext, S->d_r, S->d_p, S->d_ap, S->d_X, S->d_F, S->d_part, S->d_sums,
-                S->d_scal, S->d_occ, S->d_v0, S->d_Y, S->d_patom};
+                S->d_scal, S->d_occ, S->d_v0, S->d_Y, S->d_patom, S->d_wt};
   for (void* p : ps)
     if (p) cudaFree(p);
 }
@@ -726,10 +737,24 @@ static sparc_status poisson(sparc_scf* S, cudaStream_t st, int* iters) {
 using namespace sparc;
 using namespace sparc::scf;
 
-extern "C" sparc_status sparc_scf_create(sparc_ham* H, const sparc_scf_desc* d, sparc_scf** out) {
-  if (!H || !d || !out) return SPARC_ERR_INVALID_ARG;
+extern "C" sparc_status sparc_scf_create_k(sparc_ham* const* Hs, int nk, const double* wk, const sparc_scf_desc* d,
+                                           sparc_scf** out) {
+  if (!Hs || nk < 1 || !Hs[0] || !wk || !d || !out) return SPARC_ERR_INVALID_ARG;
   *out = nullptr;
+  sparc_ham* H = Hs[0];
   sparc_ctx* ctx = H->ctx;
+  bool any_cplx = false;
+  for (int k = 0; k < nk; ++k) {
+    const sparc_ham* Hk = Hs[k];
+    if (!Hk || Hk->ctx != ctx || !(wk[k] > 0.0) || !isfinite(wk[k]))
+      return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_scf_create_k: Hamiltonians on one context, weights > 0");
+    for (int a = 0; a < 3; ++a)
+      if (Hk->grid.n[a] != H->grid.n[a] || Hk->grid.h[a] != H->grid.h[a])
+        return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_scf_create_k: the k-points must share the grid");
+    if (Hk->grid.fd_radius != H->grid.fd_radius || Hk->nproj != H->nproj)
+      return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_scf_create_k: the k-points must share stencil and projectors");
+    any_cplx = any_cplx || Hk->gd.cplx;
+  }
   if (d->natom < 1 || !d->R || !d->Z || !d->rc || !d->v0 || !(d->kT > 0.0) || !(d->mix_beta > 0.0) ||
       d->mix_history < 0 || d->mix_history > MAXHIST || !(d->poisson_tol > 0.0) || d->first_passes < 0 ||
       d->first_passes > 64)
@@ -739,6 +764,9 @@ extern "C" sparc_status sparc_scf_create(sparc_ham* H, const sparc_scf_desc* d, 
   SPARC_CUDA(ctx, cudaSetDevice(ctx->device));
   sparc_scf* S = new sparc_scf();
   S->H = H;
+  S->Hk.assign(Hs, Hs + nk);
+  S->wk.assign(wk, wk + nk);
+  S->lamk.assign(nk, std::vector<double>());
   S->device = ctx->device;
   S->kT = d->kT;
   S->beta = d->mix_beta;
@@ -778,7 +806,7 @@ extern "C" sparc_status sparc_scf_create(sparc_ham* H, const sparc_scf_desc* d, 
   ok = ok && cudaMalloc(&S->d_sums, NPAIR * sizeof(double)) == cudaSuccess;
   ok = ok && cudaMalloc(&S->d_scal, S_COUNT * sizeof(double)) == cudaSuccess;
   ok = ok && cudaMalloc(&S->d_occ, 4096 * sizeof(double)) == cudaSuccess;
-  const size_t v0b = vb * (H->gd.cplx ? 2 : 1);
+  const size_t v0b = vb * (any_cplx ? 2 : 1);
   ok = ok && cudaMalloc(&S->d_v0, v0b) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -812,7 +840,8 @@ extern "C" sparc_status sparc_scf_create(sparc_ham* H, const sparc_scf_desc* d, 
   k_lda<<<S->nblk, TPB, 0, st>>>(S->d_rho, nd, S->d_eps, S->d_vxc);
   ctx->launches += 4;
   SPARC_LAUNCH(ctx, "scf setup");
-  sparc_status rc = sparc_ham_set_veff(H, S->d_vxc, 1, st);
+  sparc_status rc = SPARC_OK;
+  for (int k = 0; k < nk && rc == SPARC_OK; ++k) rc = sparc_ham_set_veff(Hs[k], S->d_vxc, 1, st);
   if (rc != SPARC_OK) {
     free_scf(S);
     delete S;
@@ -821,6 +850,11 @@ extern "C" sparc_status sparc_scf_create(sparc_ham* H, const sparc_scf_desc* d, 
   SPARC_CUDA(ctx, cudaMemcpy(&S->e_self, S->d_scal + S_ESELF, sizeof(double), cudaMemcpyDeviceToHost));
   *out = S;
   return SPARC_OK;
+}
+
+extern "C" sparc_status sparc_scf_create(sparc_ham* H, const sparc_scf_desc* d, sparc_scf** out) {
+  const double one = 1.0;
+  return sparc_scf_create_k(&H, 1, &one, d, out);
 }
 
 extern "C" void sparc_scf_destroy(sparc_scf* S) {
@@ -871,7 +905,11 @@ extern "C" sparc_status sparc_scf_set_density(sparc_scf* S, const float* dy, dou
   k_add<<<nb, TPB, 0, st>>>(S->d_phi, S->d_vxc, S->d_vnext, nd);
   ctx->launches += 2;
   SPARC_LAUNCH(ctx, "starting potential");
-  return sparc_ham_set_veff(H, S->d_vnext, 1, stream);
+  for (sparc_ham* Hk : S->Hk) {
+    rc = sparc_ham_set_veff(Hk, S->d_vnext, 1, stream);
+    if (rc != SPARC_OK) return rc;
+  }
+  return SPARC_OK;
 }
 
 extern "C" sparc_status sparc_scf_step(sparc_scf* S, sparc_dtype dtype, int m, void* U, int ns, int64_t ld,
@@ -880,13 +918,15 @@ extern "C" sparc_status sparc_scf_step(sparc_scf* S, sparc_dtype dtype, int m, v
   sparc_ham* H = S->H;
   sparc_ctx* ctx = H->ctx;
   const long long nd = H->gd.nd;
-  if (m < 1 || ns < 1 || ns > 4096 || ld < nd)
-    return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_scf_step: need m >= 1, 1 <= ns <= 4096, ld >= Nd");
+  const int nk = (int)S->Hk.size();
+  if (m < 1 || ns < 1 || ns > 4096 || ld < nd || (long long)nk * ns > 4096)
+    return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_scf_step: need m >= 1, 1 <= nk ns <= 4096, ld >= Nd");
   if (2.0 * ns < S->Ne) return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_scf_step: 2 ns must hold the electrons");
   SPARC_CUDA(ctx, cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
   const size_t es = dtype == SPARC_F64 ? 8 : dtype == SPARC_F32 ? 4 : dtype == SPARC_C128 ? 16 : 8;
-  const size_t ybytes = (size_t)ld * ns * es;
+  const size_t kbytes = (size_t)ld * ns * es;   // one k-point's orbitals
+  const size_t ybytes = kbytes * nk;
   if (ybytes > S->ybytes) {
     if (S->d_Y) cudaFree(S->d_Y);
     S->d_Y = nullptr;
@@ -897,47 +937,76 @@ extern "C" sparc_status sparc_scf_step(sparc_scf* S, sparc_dtype dtype, int m, v
     }
     S->ybytes = ybytes;
   }
-  // 1. filter bounds: Lanczos upper bound; cutoff and lower end from the previous Ritz
-  //    values, or the Lanczos lower end and a Weyl estimate at the first iteration
-  double a0l = 0.0, b = 0.0;
-  sparc_status rc = sparc_lanczos_bounds(H, 10, S->d_v0, &a0l, &b, stream);
-  if (rc != SPARC_OK) return rc;
+  if (nk > 1 && S->wt_n != nk * ns) {   // the weight of every Ritz value
+    std::vector<double> wt((size_t)nk * ns);
+    for (int k = 0; k < nk; ++k)
+      for (int n = 0; n < ns; ++n) wt[(size_t)k * ns + n] = S->wk[k];
+    if (S->d_wt) cudaFree(S->d_wt);
+    S->d_wt = nullptr;
+    S->wt_n = 0;
+    SPARC_CUDA(ctx, cudaMalloc(&S->d_wt, wt.size() * sizeof(double)));
+    SPARC_CUDA(ctx, cudaMemcpy(S->d_wt, wt.data(), wt.size() * sizeof(double), cudaMemcpyHostToDevice));
+    S->wt_n = nk * ns;
+  }
+  // 1. filter bounds per k: Lanczos upper bound; cutoff and lower end from the previous
+  //    Ritz values, or the Lanczos lower end and a Weyl estimate at the first iteration
+  std::vector<double> a0l(nk), b(nk), a0(nk), a(nk);
+  sparc_status rc = SPARC_OK;
+  for (int k = 0; k < nk; ++k) {
+    rc = sparc_lanczos_bounds(S->Hk[k], 10, S->d_v0, &a0l[k], &b[k], stream);
+    if (rc != SPARC_OK) return rc;
+  }
   // 2. CheFSI: scaled filter and Rayleigh-Ritz (FP64, or mixed for FP32 data); the
-  //    first iteration repeats it at the fixed starting potential (Section 4)
+  //    first iteration repeats it at the fixed starting potential (Section 4).  With
+  //    k-points one batched filter serves all of them.
   const int passes = (S->iter == 0) ? S->first_passes : 1;
-  double a0 = a0l, a = 0.0;
+  const int mode = (dtype == SPARC_F32 || dtype == SPARC_C64) ? SPARC_RR_MIXED : SPARC_RR_FP64;
   for (int pass = 0; pass < passes; ++pass) {
-    if ((int)S->lam_prev.size() == ns) {
-      a0 = S->lam_prev.front();
-      a = S->lam_prev.back();
-    } else {
-      a0 = a0l;
-      a = a0 + (b - a0) * pow((double)ns / (double)nd, 2.0 / 3.0);
+    for (int k = 0; k < nk; ++k) {
+      const std::vector<double>& lp = S->lamk[k];
+      if ((int)lp.size() == ns) {
+        a0[k] = lp.front();
+        a[k] = lp.back();
+      } else {
+        a0[k] = a0l[k];
+        a[k] = a0[k] + (b[k] - a0[k]) * pow((double)ns / (double)nd, 2.0 / 3.0);
+      }
+      if (!(a[k] < b[k])) a[k] = 0.5 * (a0[k] + b[k]);
+      if (!(a0[k] < a[k])) a0[k] = a[k] - 1e-3 * (b[k] - a[k]);
     }
-    if (!(a < b)) a = 0.5 * (a0 + b);
-    if (!(a0 < a)) a0 = a - 1e-3 * (b - a);
-    rc = sparc_cheb_filter(H, dtype, m, a, b, a0, U, S->d_Y, ns, ld, stream);
+    if (nk == 1) rc = sparc_cheb_filter(H, dtype, m, a[0], b[0], a0[0], U, S->d_Y, ns, ld, stream);
+    else rc = sparc_cheb_filter_batch(S->Hk.data(), nk, dtype, m, a.data(), b.data(), a0.data(), U, S->d_Y, ns, ld,
+                                      stream);
     if (rc != SPARC_OK) return rc;
-    const int mode = (dtype == SPARC_F32 || dtype == SPARC_C64) ? SPARC_RR_MIXED : SPARC_RR_FP64;
-    rc = sparc_rayleigh_ritz(H, dtype, S->d_Y, ns, ld, eig, mode, stream);
-    if (rc != SPARC_OK) return rc;
+    for (int k = 0; k < nk; ++k) {
+      rc = sparc_rayleigh_ritz(S->Hk[k], dtype, (char*)S->d_Y + k * kbytes, ns, ld, eig + (size_t)k * ns, mode, stream);
+      if (rc != SPARC_OK) return rc;
+    }
     SPARC_CUDA(ctx, cudaMemcpyAsync(U, S->d_Y, ybytes, cudaMemcpyDeviceToDevice, st));
-    S->lam_prev.assign(ns, 0.0);
-    SPARC_CUDA(ctx, cudaMemcpyAsync(S->lam_prev.data(), eig, ns * sizeof(double), cudaMemcpyDeviceToHost, st));
+    for (int k = 0; k < nk; ++k) {
+      S->lamk[k].assign(ns, 0.0);
+      SPARC_CUDA(ctx, cudaMemcpyAsync(S->lamk[k].data(), eig + (size_t)k * ns, ns * sizeof(double),
+                                      cudaMemcpyDeviceToHost, st));
+    }
     if (pass + 1 < passes) SPARC_CUDA(ctx, cudaStreamSynchronize(st));
   }
-  // 3. Fermi level and occupations
-  k_fermi<<<1, TPB, 0, st>>>(eig, ns, S->Ne, S->kT, S->d_occ, S->d_scal);
-  // 4. density rho = 2 sum g |u|^2 / (h1h2h3)
+  // 3. Fermi level and occupations over all k-points
+  k_fermi<<<1, TPB, 0, st>>>(eig, nk > 1 ? S->d_wt : nullptr, nk * ns, S->Ne, S->kT, S->d_occ, S->d_scal);
+  // 4. density rho = 2 sum_k w_k sum_n g_nk |u_nk|^2 / (h1h2h3)
   const double dv = H->grid.h[0] * H->grid.h[1] * H->grid.h[2];
   const int nb = S->nblk;
-  switch (dtype) {
-    case SPARC_F64: k_density<double><<<nb, TPB, 0, st>>>((const double*)U, ld, ns, nd, S->d_occ, 2.0 / dv, S->d_rho); break;
-    case SPARC_F32: k_density<float><<<nb, TPB, 0, st>>>((const float*)U, ld, ns, nd, S->d_occ, 2.0 / dv, S->d_rho); break;
-    case SPARC_C128: k_density<cf64><<<nb, TPB, 0, st>>>((const cf64*)U, ld, ns, nd, S->d_occ, 2.0 / dv, S->d_rho); break;
-    case SPARC_C64: k_density<cf32><<<nb, TPB, 0, st>>>((const cf32*)U, ld, ns, nd, S->d_occ, 2.0 / dv, S->d_rho); break;
+  for (int k = 0; k < nk; ++k) {
+    const char* Uk = (const char*)U + k * kbytes;
+    const double* occk = S->d_occ + (size_t)k * ns;
+    const double w = nk > 1 ? S->wk[k] : 1.0;
+    switch (dtype) {
+      case SPARC_F64: k_density<double><<<nb, TPB, 0, st>>>((const double*)Uk, ld, ns, nd, occk, 2.0 / dv, w, k, S->d_rho); break;
+      case SPARC_F32: k_density<float><<<nb, TPB, 0, st>>>((const float*)Uk, ld, ns, nd, occk, 2.0 / dv, w, k, S->d_rho); break;
+      case SPARC_C128: k_density<cf64><<<nb, TPB, 0, st>>>((const cf64*)Uk, ld, ns, nd, occk, 2.0 / dv, w, k, S->d_rho); break;
+      case SPARC_C64: k_density<cf32><<<nb, TPB, 0, st>>>((const cf32*)Uk, ld, ns, nd, occk, 2.0 / dv, w, k, S->d_rho); break;
+    }
   }
-  ctx->launches += 2;
+  ctx->launches += 1 + nk;
   SPARC_LAUNCH(ctx, "fermi and density");
   // 5. Poisson: -(1/4pi) lap phi = rho + b
   int piters = 0;
@@ -964,8 +1033,10 @@ extern "C" sparc_status sparc_scf_step(sparc_scf* S, sparc_dtype dtype, int m, v
   k_anderson_next<<<nb, TPB, 0, st>>>(S->d_X, S->d_F, nd, S->nslot, k, mm, S->beta, S->d_scal, S->d_vnext);
   ctx->launches += 4;
   SPARC_LAUNCH(ctx, "xc, energy and mixing");
-  rc = sparc_ham_set_veff(H, S->d_vnext, 1, stream);
-  if (rc != SPARC_OK) return rc;
+  for (sparc_ham* Hk : S->Hk) {
+    rc = sparc_ham_set_veff(Hk, S->d_vnext, 1, stream);
+    if (rc != SPARC_OK) return rc;
+  }
   double hs[S_COUNT];
   SPARC_CUDA(ctx, cudaMemcpyAsync(hs, S->d_scal, sizeof(hs), cudaMemcpyDeviceToHost, st));
   SPARC_CUDA(ctx, cudaStreamSynchronize(st));
@@ -981,9 +1052,9 @@ extern "C" sparc_status sparc_scf_step(sparc_scf* S, sparc_dtype dtype, int m, v
   info->vresid = sqrt(hs[S_RES2] / std::max(hs[S_VOUT2], 1e-300));
   info->poisson_iters = piters;
   S->last_ns = ns;
-  info->a0 = a0;
-  info->a = a;
-  info->b = b;
+  info->a0 = a0[0];   // the filter bounds of the first k-point
+  info->a = a[0];
+  info->b = b[0];
   ++S->iter;
   return SPARC_OK;
 }
@@ -996,6 +1067,7 @@ extern "C" sparc_status sparc_scf_forces(sparc_scf* S, sparc_dtype dtype, const 
   const long long nd = H->gd.nd;
   if (S->last_ns != ns || ns < 1 || ld < nd)
     return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_scf_forces: needs the orbitals of the last sparc_scf_step");
+  if (S->Hk.size() != 1) return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_scf_forces: one k-point (Gamma) only");
   if (dtype != SPARC_F64 && dtype != SPARC_F32)
     return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_scf_forces: real orbitals (Gamma point) only");
   if (H->nproj > 0 && !S->d_patom)

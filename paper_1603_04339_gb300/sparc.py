@@ -31,7 +31,7 @@ EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_sync", "s
            "sparc_set_filter_units", "sparc_filter_graph_create", "sparc_filter_graph_set_bounds",
            "sparc_filter_graph_launch", "sparc_filter_graph_destroy", "sparc_scf_set_density",
            "sparc_mlp_create", "sparc_mlp_params", "sparc_mlp_descriptors", "sparc_mlp_forward", "sparc_mlp_grad",
-           "sparc_mlp_train_step", "sparc_mlp_destroy"]
+           "sparc_mlp_train_step", "sparc_mlp_destroy", "sparc_scf_create_k"]
 TIMED = {"hpass": 0, "gather": 1, "gram": 2, "eig": 3, "rotation": 4, "jacobi": 5, "fpass": 6}
 
 
@@ -110,6 +110,8 @@ def load(path: str = LIB_PATH):
     L.sparc_rotate_f32.argtypes = [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int, c_void_p, c_int64,
                                    c_void_p]
     L.sparc_scf_create.argtypes = [c_void_p, POINTER(SparcScfDesc), POINTER(c_void_p)]
+    L.sparc_scf_create_k.argtypes = [POINTER(c_void_p), c_int, POINTER(c_double), POINTER(SparcScfDesc),
+                                     POINTER(c_void_p)]
     L.sparc_scf_step.argtypes = [c_void_p, c_int, c_int, c_void_p, c_int, c_int64, c_void_p,
                                  POINTER(SparcScfInfo), c_void_p]
     L.sparc_scf_read.argtypes = [c_void_p, c_int, c_void_p, c_void_p]
@@ -533,9 +535,14 @@ class Scf:
 
     FIELDS = {"b": 0, "rho": 1, "phi": 2, "vxc": 3, "vout": 4, "veff": 5}
 
-    def __init__(self, H: Hamiltonian, R, Z, rc, v0, kT=0.01, mix_beta=0.3, mix_history=7, poisson_tol=1e-10,
-                 proj_atom=None, first_passes=1):
+    def __init__(self, H, R, Z, rc, v0, kT=0.01, mix_beta=0.3, mix_history=7, poisson_tol=1e-10,
+                 proj_atom=None, first_passes=1, wk=None):
+        """H: a Hamiltonian, or a list of them (one per k-point, weights wk)."""
+        Hs = list(H) if isinstance(H, (list, tuple)) else [H]
+        H = Hs[0]
         self.H = H
+        self.Hs = Hs
+        self.nk = len(Hs)
         self._R = np.ascontiguousarray(R, dtype=np.float64).reshape(-1)
         self._Z = np.ascontiguousarray(Z, dtype=np.float64)
         self._rc = np.ascontiguousarray(rc, dtype=np.float64)
@@ -557,7 +564,14 @@ class Scf:
         d.proj_atom = None if self._pa is None else self._pa.ctypes.data_as(POINTER(c_int32))
         d.first_passes = int(first_passes)
         h = c_void_p()
-        H.ctx.check(load().sparc_scf_create(H.handle, ctypes.byref(d), ctypes.byref(h)))
+        if self.nk == 1 and wk is None:
+            H.ctx.check(load().sparc_scf_create(H.handle, ctypes.byref(d), ctypes.byref(h)))
+        else:
+            w = np.full(self.nk, 1.0 / self.nk) if wk is None else np.asarray(wk, dtype=np.float64)
+            self._wk = np.ascontiguousarray(w, dtype=np.float64)
+            hs = (c_void_p * self.nk)(*[x.handle for x in Hs])
+            H.ctx.check(load().sparc_scf_create_k(hs, self.nk, self._wk.ctypes.data_as(POINTER(c_double)),
+                                                  ctypes.byref(d), ctypes.byref(h)))
         self.handle = h
         H.ctx._scfs.add(self)
 
@@ -598,8 +612,10 @@ class Scf:
 
 
 def sparc_scf_step(S: Scf, U, eig, m, ns=None, ld=None, stream=None, dtype=None) -> dict:
-    """One SCF iteration on the orbitals U (ns, ld) in place; returns the sparc_scf_info fields."""
-    ns = U.shape[0] if ns is None else ns
+    """One SCF iteration on the orbitals U in place -- (ns, ld), or (nk, ns, ld) for a
+    k-point SCF with eig of nk*ns values; returns the sparc_scf_info fields."""
+    if ns is None:
+        ns = U.shape[-2]
     ld = U.shape[-1] if ld is None else ld
     dt = dtype_code(U) if dtype is None else dtype
     info = SparcScfInfo()

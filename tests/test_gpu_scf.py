@@ -201,3 +201,85 @@ def test_first_iteration_repeats_chefsi_like_the_oracle(ctx):
     assert abs(info["a"] - out["a"]) < 1e-9 * abs(out["a"]) and abs(info["a0"] - out["a0"]) < 1e-9 * abs(out["a0"])
     S.close()
     H.close()
+
+
+def _scf_two_k():
+    """The 20^3 SCF cell at two k-points (Gamma and a zone-boundary point along x),
+    weights 1/2 each."""
+    sysd = synth.scf_small()
+    wl = sysd.wl
+    L = wl.n[0] * wl.h[0]
+    kpts = np.array([[0.0, 0.0, 0.0], [np.pi / L, 0.0, 0.0]])
+    wl2 = synth.Workload("scf_small_2k", wl.n, wl.h, wl.fd_radius, kpts, np.array([0.5, 0.5]), wl.veff,
+                         wl.atoms, wl.proj, wl.ns, wl.m, wl.seed)
+    rng = np.random.default_rng(77)
+    v0 = rng.standard_normal(wl.nd) + 1j * rng.standard_normal(wl.nd)
+    U0 = [sysd.U0.astype(np.complex128),
+          synth.random_orbitals(wl.nd, wl.ns, 78, complex_=True)]
+    return sysd, wl2, v0, U0
+
+
+def test_two_kpoint_fp64_iterations_match_the_oracle(ctx):
+    """Section 2's Brillouin-zone sum: two k-points, one Fermi level, the weighted density;
+    two FP64 (complex128) iterations against the oracle's k-point iteration."""
+    from paper_1603_04339_gb300 import sparc
+    sysd, wl, v0, U0 = _scf_two_k()
+    Hs = [sparc.Hamiltonian.from_workload(ctx, wl, k) for k in range(2)]
+    S = sparc.Scf(Hs, wl.atoms, sysd.Z, sysd.rc, v0, kT=KT, mix_beta=BETA, mix_history=HIST, poisson_tol=1e-13,
+                  wk=[0.5, 0.5])
+    U = torch.from_numpy(np.stack(U0)).cuda()
+    eig = torch.zeros(2 * wl.ns, dtype=torch.float64, device="cuda")
+    b, e_self, _ = SO.pseudocharge(wl.n, wl.h, 6, wl.atoms, sysd.Z, sysd.rc)
+    v_in = SO.lda(-b)[1]
+    Uo, lps, xh, fh = [u.copy() for u in U0], [None, None], [], []
+    for it in range(2):
+        info = sparc.sparc_scf_step(S, U, eig, wl.m)
+        Hor = [O.OracleH(wl, k, veff=v_in) for k in range(2)]
+        out = SO.scf_iteration_k(Hor, [0.5, 0.5], Uo, lps, v0, b, e_self, sysd.nelec, KT, wl.m)
+        lam = eig.cpu().numpy()
+        assert np.max(np.abs(lam - out["lam"])) < 1e-9 * np.max(np.abs(out["lam"])), it
+        assert abs(info["fermi"] - out["mu"]) < 1e-9, it
+        assert abs(info["nelec"] - sysd.nelec) < 1e-9
+        rho = _field(S, "rho", wl.nd)
+        assert np.max(np.abs(rho - out["rho"])) < 1e-9 * np.max(out["rho"]), it
+        assert abs(info["free_energy"] - out["F"]) < 1e-9 * abs(out["F"]), it
+        xh.append(v_in)
+        fh.append(out["v_out"] - v_in)
+        v_next = SO.anderson(xh, fh, BETA, HIST)
+        veff = _field(S, "veff", wl.nd)
+        assert np.max(np.abs(veff - v_next)) < 1e-8 * np.max(np.abs(v_next)), it
+        v_in, Uo = v_next, out["U"]
+        lps = [out["lam"][:wl.ns], out["lam"][wl.ns:]]
+    S.close()
+    for H in Hs:
+        H.close()
+
+
+def test_two_kpoint_mixed_scf_reaches_the_fp64_energy(ctx):
+    """The k-point SCF converges; complex64 orbitals (batched filter, mixed Rayleigh-Ritz)
+    reach the complex128 free energy within 1e-5 Ha per atom."""
+    from paper_1603_04339_gb300 import sparc
+    sysd, wl, v0, U0 = _scf_two_k()
+    F = {}
+    for dt in (torch.complex128, torch.complex64):
+        Hs = [sparc.Hamiltonian.from_workload(ctx, wl, k) for k in range(2)]
+        S = sparc.Scf(Hs, wl.atoms, sysd.Z, sysd.rc, v0, kT=KT, mix_beta=BETA, mix_history=HIST,
+                      poisson_tol=1e-11, wk=[0.5, 0.5])
+        U = torch.from_numpy(np.stack(U0)).to(dt).cuda()
+        eig = torch.zeros(2 * wl.ns, dtype=torch.float64, device="cuda")
+        res = []
+        for it in range(40):
+            info = sparc.sparc_scf_step(S, U, eig, wl.m)
+            res.append(info["vresid"])
+            if info["vresid"] < 1e-7:
+                break
+        print(dt, "V residuals:", " ".join(f"{r:.1e}" for r in res))
+        assert res[-1] < 1e-6
+        F[dt] = info["free_energy"]
+        S.close()
+        for H in Hs:
+            H.close()
+    dF = abs(F[torch.complex64] - F[torch.complex128]) / len(sysd.Z)
+    print(f"two-k free energy: complex128 {F[torch.complex128]:.10f}, complex64 {F[torch.complex64]:.10f}, "
+          f"|dF|/atom {dF:.2e}")
+    assert dF < 1e-5
