@@ -266,34 +266,16 @@ template <class T> struct FT;
 template <> struct FT<float> {
   static constexpr bool cplx = false;
   __device__ static float zero() { return 0.f; }
-  __device__ static float phase(float v, float, float) { return v; }
-  __device__ static float dot4(float4 c, const float g[4]) { return c.x * g[0] + c.y * g[1] + c.z * g[2] + c.w * g[3]; }
 };
 template <> struct FT<cf32> {
   static constexpr bool cplx = true;
   __device__ static cf32 zero() { return {0.f, 0.f}; }
-  __device__ static cf32 phase(cf32 v, float pr, float pi) { return {v.x * pr - v.y * pi, v.x * pi + v.y * pr}; }
-  __device__ static cf32 dot4(float4 c, const cf32 g[4]) {
-    return {c.x * g[0].x + c.y * g[1].x + c.z * g[2].x + c.w * g[3].x,
-            c.x * g[0].y + c.y * g[1].y + c.z * g[2].y + c.w * g[3].y};
-  }
 };
 
 __device__ __forceinline__ float fld(const float* p) { return __ldg(p); }
 __device__ __forceinline__ cf32 fld(const cf32* p) {
   float2 v = __ldg(reinterpret_cast<const float2*>(p));
   return {v.x, v.y};
-}
-
-// Bloch phase exp(i k L t) from the per-axis phase exp(i k L) and an integer t (small |t|).
-__device__ __forceinline__ void phase_pow(float pr, float pi, int t, float& rr, float& ri) {
-  rr = 1.f; ri = 0.f;
-  const float qi = (t < 0) ? -pi : pi;
-  for (int a = 0; a < (t < 0 ? -t : t); ++a) {
-    const float x = rr * pr - ri * qi;
-    ri = rr * qi + ri * pr;
-    rr = x;
-  }
 }
 
 // Wrap g into [0, n) and return the number of cells crossed.
@@ -365,7 +347,7 @@ template <class T, int TYv = Shape<T>::TY> struct Smem {
 // shared-memory neighbour read is one 64-bit load.  A warp covers 8 rows x 4
 // orbital pairs at one x-run.  CTAs are persistent: they loop over (tile,
 // z-chunk, block) items, so the last wave is not partly empty.
-constexpr int RX2 = 2, TY2 = 16;
+constexpr int RX2 = 2;
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 lds2(const float* p) { return *reinterpret_cast<const float2*>(p); }
@@ -1210,8 +1192,7 @@ static int gather_slabs(const sparc_ham* H) {
   const int want = 6 * H->ctx->nsm;
   return std::max(1, std::min(NSLAB_MAX, ceil_div(want, std::max(1, Tb->ngrp))));
 }
-template <class T> struct GatherOct { static constexpr int v = 8; };
-template <> struct GatherOct<cf32> { static constexpr int v = 4; };
+constexpr int GATHER_OCT_C = 4;   // complex64 blocks per projection CTA
 
 size_t gather_scratch_bytes(const sparc_ham* H, int nb, size_t esize) {
   const Tables* Tb = (const Tables*)H->fast;
@@ -1225,7 +1206,7 @@ cudaError_t launch_gather_k(const sparc_ham* H0, const cf32* Y, long long nunit_
   const float dv = (float)(H0->grid.h[0] * H0->grid.h[1] * H0->grid.h[2]);
   const int nslab = gather_slabs(H0);
   cudaEvent_t t0 = timing_begin(H0->ctx, st);
-  constexpr int NBM = GatherOct<cf32>::v;
+  constexpr int NBM = GATHER_OCT_C;
   const int noct = ceil_div(ks.nbk, NBM);
   const dim3 grid((unsigned)Tb->ngrp, (unsigned)nslab, (unsigned)(ks.nk * noct));
   k_gather_rows<cf32, NBM><<<grid, 256, 0, st>>>(Y, H0->gd.nd, H0->gd.n1, H0->gd.n2, Tb->d_grp, ks, scratch,
