@@ -198,6 +198,7 @@ __global__ void __launch_bounds__(256) k_chol_blk(double* A, long long lda, doub
                                                   int* status) {
   __shared__ double S[MB][MB + 1];
   __shared__ double x[MB];
+  __shared__ double rdiag[MB];   // 1 / L_jj, one FP64 division per column (thread 0)
   __shared__ int bad;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) bad = 0;
@@ -216,11 +217,12 @@ __global__ void __launch_bounds__(256) k_chol_blk(double* A, long long lda, doub
         atomicOr(status, STATUS_NOT_POSDEF);
       } else {
         S[j][j] = sqrt(d);
+        rdiag[j] = 1.0 / S[j][j];
       }
     }
     __syncthreads();
     if (bad) return;
-    const double inv = 1.0 / S[j][j];
+    const double inv = rdiag[j];
     for (int i = j + 1 + tid; i < kb; i += nt) S[i][j] *= inv;
     __syncthreads();
     // trailing lower triangle (i, c), j < c <= i: 16 x 16 thread tiles, no index division
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(256) k_chol_blk(double* A, long long lda, doub
   // -(1/L_jj) Linv[j+1:, j+1:] L[j+1:, j], using the already inverted trailing block
   __shared__ double part[16][MB];
   for (int j = kb - 1; j >= 0; --j) {
-    const double ljj = 1.0 / S[j][j];
+    const double ljj = rdiag[j];
     // x_i = sum_{k=j+1..i} Linv[i][k] L[k][j]: 16 partial sums per row over k, then a fixed-order sum
     const int tx = tid & 15, ty = tid >> 4;
     for (int i = j + 1 + ty; i < kb; i += 16) {
