@@ -336,6 +336,9 @@ k_jacobi_round(const TW* __restrict__ A, TW* __restrict__ An, TW* __restrict__ V
                int r) {
   __shared__ Rot<TW> rp[16], rq[16];
   __shared__ int ip[16][2], iq[16][2];
+  // rounds are chained by programmatic dependent launch: wait until the previous round's
+  // grid has completed and its writes are visible (a no-op without such a dependency)
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
   const int half = npad / 2;
   const int tpa = (half + 15) / 16;           // pair tiles per side
   const int nta = tpa * tpa;
@@ -625,8 +628,25 @@ sparc_status jacobi(sparc_ctx* ctx, TJ* A0, TJ* A1, TJ* V, int n, double tol, in
     SPARC_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
     TJ* a = A0;
     TJ* b = A1;
+    // each round may begin launching while the previous one finishes (programmatic
+    // dependent launch); it waits for that round's results before it reads A or V
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nblocks);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = ctx->cap_stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     for (int r = 0; r < rounds; ++r) {
-      k_jacobi_round<TJ><<<nblocks, 256, 0, ctx->cap_stream>>>(a, b, V, n, npad, r % (npad - 1));
+      cudaError_t le = cudaLaunchKernelEx(&cfg, k_jacobi_round<TJ>, (const TJ*)a, b, V, n, npad, r % (npad - 1));
+      if (le != cudaSuccess) {
+        cudaStreamEndCapture(ctx->cap_stream, &g);
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(ctx, le, "jacobi round launch");
+      }
       std::swap(a, b);
     }
     SPARC_CUDA(ctx, cudaStreamEndCapture(ctx->cap_stream, &g));
