@@ -256,15 +256,18 @@ sparc_status sparc_mlp_descriptors(sparc_ctx* ctx, const int* n, const double* h
                                    const double* R, const double* widths, float* D, void* stream);
 /* y[p] (device, np floats) = network(D[p]) for D (device, np x 16). */
 sparc_status sparc_mlp_forward(sparc_mlp* M, const float* D, int64_t np, float* y, void* stream);
-/* Gradient of the loss over the points idx[0..np) (device int64 row indices of D
- * and t; NULL: rows 0..np-1) into grad (device, SPARC_MLP_NPARAM floats; may be
- * NULL); *loss (host, may be NULL; then the call does not synchronise).  The
- * per-CTA partial sums are reduced in a fixed order: bit-reproducible. */
-sparc_status sparc_mlp_grad(sparc_mlp* M, const float* D, const float* t, const int64_t* idx,
-                            int64_t np, float* grad, double* loss, void* stream);
+/* Gradient of the loss over the points idx[0..np) (device int64 row indices into
+ * the nrows rows of D and t; NULL: rows 0..np-1, np <= nrows) into grad (device,
+ * SPARC_MLP_NPARAM floats; may be NULL); *loss (host, may be NULL; then the call
+ * does not synchronise).  An index outside [0, nrows) is not read: the point
+ * counts as zero and the next synchronising call (sparc_sync) returns
+ * SPARC_ERR_INVALID_ARG.  The per-CTA partial sums are reduced in a fixed order:
+ * bit-reproducible. */
+sparc_status sparc_mlp_grad(sparc_mlp* M, const float* D, const float* t, int64_t nrows,
+                            const int64_t* idx, int64_t np, float* grad, double* loss, void* stream);
 /* One Adam step with learning rate lr > 0 on the gradient of sparc_mlp_grad. */
-sparc_status sparc_mlp_train_step(sparc_mlp* M, const float* D, const float* t, const int64_t* idx,
-                                  int64_t np, float lr, double* loss, void* stream);
+sparc_status sparc_mlp_train_step(sparc_mlp* M, const float* D, const float* t, int64_t nrows,
+                                  const int64_t* idx, int64_t np, float lr, double* loss, void* stream);
 /* Free (synchronises the device); uses no state of its context. */
 void sparc_mlp_destroy(sparc_mlp* M);
 

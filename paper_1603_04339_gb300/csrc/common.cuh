@@ -141,6 +141,7 @@ enum : int {
   STATUS_NOT_POSDEF = 1,
   STATUS_TIMEOUT = 2,
   STATUS_NO_CONVERGENCE = 4,
+  STATUS_BAD_INDEX = 8,
 };
 
 // ----------------------------------------------------------------- geometry passed to kernels

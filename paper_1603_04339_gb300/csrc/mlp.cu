@@ -60,21 +60,28 @@ __device__ void load_params(Smem& s, const float* __restrict__ th) {
   if (threadIdx.x == 0) s.b3 = th[OB3];
 }
 
-// Points [p0, p0 + TP) of the batch (row r of D is point idx[r], or r without idx)
-// into s.X (and targets into s.t); rows past np are zero and flagged by np.
+// Points [p0, p0 + TP) of the batch (point p is row idx[p] of D and t, or row p without
+// idx) into s.X (and targets into s.t); rows past np are zero.  A row index outside
+// [0, nrows) is not read: the point counts as zero and the status word records it.
 __device__ void load_tile(Smem& s, const float* __restrict__ D, const float* __restrict__ tgt,
-                          const long long* __restrict__ idx, long long p0, long long np) {
+                          const long long* __restrict__ idx, long long p0, long long np, long long nrows,
+                          int* status) {
   for (int e = threadIdx.x; e < TP * NF; e += THR) {
     const int r = e / NF, f = e % NF;
     const long long p = p0 + r;
     float v = 0.f;
-    if (p < np) v = D[(idx ? idx[p] : p) * NF + f];
+    if (p < np) {
+      const long long row = idx ? idx[p] : p;
+      if (row >= 0 && row < nrows) v = D[row * NF + f];
+      else if (f == 0) atomicOr(status, STATUS_BAD_INDEX);
+    }
     s.X[r][f] = v;
   }
   if (tgt)
     for (int r = threadIdx.x; r < TP; r += THR) {
       const long long p = p0 + r;
-      s.t[r] = p < np ? tgt[idx ? idx[p] : p] : 0.f;
+      const long long row = p < np ? (idx ? idx[p] : p) : -1;
+      s.t[r] = (row >= 0 && row < nrows) ? tgt[row] : 0.f;
     }
 }
 
@@ -142,7 +149,7 @@ k_mlp_forward(const float* __restrict__ th, const float* __restrict__ D, long lo
   load_params(s, th);
   for (long long p0 = (long long)blockIdx.x * TP; p0 < np; p0 += (long long)gridDim.x * TP) {
     __syncthreads();
-    load_tile(s, D, nullptr, nullptr, p0, np);
+    load_tile(s, D, nullptr, nullptr, p0, np, np, nullptr);
     __syncthreads();
     hidden_layers(s);
     const float v = output(s);
@@ -155,7 +162,8 @@ k_mlp_forward(const float* __restrict__ th, const float* __restrict__ D, long lo
 // partial loss sum_p (y_p - t_p)^2 into lpart[cta].
 __global__ void __launch_bounds__(THR, 1)
 k_mlp_grad(const float* __restrict__ th, const float* __restrict__ D, const float* __restrict__ tgt,
-           const long long* __restrict__ idx, long long np, float* __restrict__ part, double* __restrict__ lpart) {
+           const long long* __restrict__ idx, long long np, long long nrows, int* status, float* __restrict__ part,
+           double* __restrict__ lpart) {
   extern __shared__ __align__(16) unsigned char smraw[];
   Smem& s = *reinterpret_cast<Smem*>(smraw);
   const int tid = threadIdx.x;
@@ -176,7 +184,7 @@ k_mlp_grad(const float* __restrict__ th, const float* __restrict__ D, const floa
   double loss = 0.0;
   for (long long p0 = (long long)blockIdx.x * TP; p0 < np; p0 += (long long)gridDim.x * TP) {
     __syncthreads();
-    load_tile(s, D, tgt, idx, p0, np);
+    load_tile(s, D, tgt, idx, p0, np, nrows, status);
     __syncthreads();
     hidden_layers(s);
     // output and dL/dy = 2 (y - t) / N (zero for padding rows)
@@ -400,11 +408,11 @@ static void free_mlp(sparc_mlp* M) {
 }
 
 static sparc_status launch_grad(sparc_mlp* M, const float* D, const float* t, const long long* idx, long long np,
-                                cudaStream_t st) {
+                                long long nrows, cudaStream_t st) {
   const size_t smem = sizeof(Smem);
   SPARC_CUDA(M->ctx, cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int ncta = (int)std::min<long long>(M->ncta, (np + TP - 1) / TP);
-  k_mlp_grad<<<ncta, THR, smem, st>>>(M->d_theta, D, t, idx, np, M->d_part, M->d_lpart);
+  k_mlp_grad<<<ncta, THR, smem, st>>>(M->d_theta, D, t, idx, np, nrows, M->ctx->d_status, M->d_part, M->d_lpart);
   k_mlp_reduce<<<(NPAR + 255) / 256, 256, 0, st>>>(M->d_part, M->d_lpart, ncta, np, M->d_grad, M->d_loss);
   M->ctx->launches += 2;
   SPARC_LAUNCH(M->ctx, "mlp gradient");
@@ -500,12 +508,12 @@ sparc_status sparc_mlp_forward(sparc_mlp* M, const float* D, int64_t np, float* 
   return SPARC_OK;
 }
 
-sparc_status sparc_mlp_grad(sparc_mlp* M, const float* D, const float* t, const int64_t* idx, int64_t np,
-                            float* grad, double* loss, void* stream) {
-  if (!M || !D || !t || np < 1) return SPARC_ERR_INVALID_ARG;
+sparc_status sparc_mlp_grad(sparc_mlp* M, const float* D, const float* t, int64_t nrows, const int64_t* idx,
+                            int64_t np, float* grad, double* loss, void* stream) {
+  if (!M || !D || !t || np < 1 || nrows < 1 || (!idx && np > nrows)) return SPARC_ERR_INVALID_ARG;
   SPARC_CUDA(M->ctx, cudaSetDevice(M->ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
-  sparc_status s = launch_grad(M, D, t, (const long long*)idx, np, st);
+  sparc_status s = launch_grad(M, D, t, (const long long*)idx, np, nrows, st);
   if (s != SPARC_OK) return s;
   if (grad) SPARC_CUDA(M->ctx, cudaMemcpyAsync(grad, M->d_grad, NPAR * sizeof(float), cudaMemcpyDeviceToDevice, st));
   if (loss) {
@@ -515,12 +523,12 @@ sparc_status sparc_mlp_grad(sparc_mlp* M, const float* D, const float* t, const 
   return SPARC_OK;
 }
 
-sparc_status sparc_mlp_train_step(sparc_mlp* M, const float* D, const float* t, const int64_t* idx, int64_t np,
-                                  float lr, double* loss, void* stream) {
-  if (!M || !D || !t || np < 1 || !(lr > 0.f)) return SPARC_ERR_INVALID_ARG;
+sparc_status sparc_mlp_train_step(sparc_mlp* M, const float* D, const float* t, int64_t nrows, const int64_t* idx,
+                                  int64_t np, float lr, double* loss, void* stream) {
+  if (!M || !D || !t || np < 1 || nrows < 1 || (!idx && np > nrows) || !(lr > 0.f)) return SPARC_ERR_INVALID_ARG;
   SPARC_CUDA(M->ctx, cudaSetDevice(M->ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
-  sparc_status s = launch_grad(M, D, t, (const long long*)idx, np, st);
+  sparc_status s = launch_grad(M, D, t, (const long long*)idx, np, nrows, st);
   if (s != SPARC_OK) return s;
   const double b1 = 0.9, b2 = 0.999;
   ++M->step;

@@ -530,6 +530,7 @@ sparc_status sparc_sync(sparc_ctx* ctx, void* stream) {
   SPARC_CUDA(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)));
   if (word & STATUS_TIMEOUT) return fail(ctx, SPARC_ERR_TIMEOUT, "a bounded device wait gave up");
   if (word & STATUS_NOT_POSDEF) return fail(ctx, SPARC_ERR_NOT_POSDEF, "M~ not positive definite");
+  if (word & STATUS_BAD_INDEX) return fail(ctx, SPARC_ERR_INVALID_ARG, "a row index was outside its array");
   if (word & STATUS_NO_CONVERGENCE)
     return fail(ctx, SPARC_ERR_NO_CONVERGENCE, "subspace eigensolver did not converge");
   return SPARC_OK;

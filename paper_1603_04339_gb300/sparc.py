@@ -138,9 +138,9 @@ def load(path: str = LIB_PATH):
     L.sparc_mlp_descriptors.argtypes = [c_void_p, POINTER(c_int), POINTER(c_double), c_int, c_void_p, c_void_p,
                                         c_void_p, c_void_p]
     L.sparc_mlp_forward.argtypes = [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]
-    L.sparc_mlp_grad.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, POINTER(c_double),
-                                 c_void_p]
-    L.sparc_mlp_train_step.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, ctypes.c_float,
+    L.sparc_mlp_grad.argtypes = [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_void_p,
+                                 POINTER(c_double), c_void_p]
+    L.sparc_mlp_train_step.argtypes = [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_int64, ctypes.c_float,
                                        POINTER(c_double), c_void_p]
     L.sparc_mlp_destroy.argtypes = [c_void_p]
     L.sparc_mlp_destroy.restype = None
@@ -461,16 +461,17 @@ class Mlp:
         """Gradient of the mean squared error into the float32 CUDA tensor `grad`; returns the loss."""
         loss = c_double()
         n = int(idx.shape[0]) if idx is not None else int(D.shape[0])
-        self.ctx.check(load().sparc_mlp_grad(self.handle, _ptr(D), _ptr(t), _ptr(idx), n, _ptr(grad),
-                                             ctypes.byref(loss), _stream(stream)))
+        self.ctx.check(load().sparc_mlp_grad(self.handle, _ptr(D), _ptr(t), int(D.shape[0]), _ptr(idx), n,
+                                             _ptr(grad), ctypes.byref(loss), _stream(stream)))
         return loss.value
 
     def train_step(self, D, t, lr, idx=None, want_loss=False, stream=None):
         """One Adam step on the points idx (int64 CUDA tensor) or all rows of D."""
         loss = c_double()
         n = int(idx.shape[0]) if idx is not None else int(D.shape[0])
-        self.ctx.check(load().sparc_mlp_train_step(self.handle, _ptr(D), _ptr(t), _ptr(idx), n, float(lr),
-                                                   ctypes.byref(loss) if want_loss else None, _stream(stream)))
+        self.ctx.check(load().sparc_mlp_train_step(self.handle, _ptr(D), _ptr(t), int(D.shape[0]), _ptr(idx), n,
+                                                   float(lr), ctypes.byref(loss) if want_loss else None,
+                                                   _stream(stream)))
         return loss.value if want_loss else None
 
     def close(self):

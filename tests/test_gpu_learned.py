@@ -83,6 +83,12 @@ def test_forward_gradient_and_adam_match_the_oracle(ctx):
     th1 = net.params().astype(np.float64)
     ref, _, _ = M.adam(th32, gg, np.zeros_like(gg), np.zeros_like(gg), 1, 1e-3)
     assert np.max(np.abs(th1 - ref)) < 1e-6
+    # a row index outside D is not read; the status word reports it
+    bad = torch.tensor([0, 5, N + 3], dtype=torch.int64, device="cuda")
+    net.grad(Dd, td, gi, idx=bad)
+    with pytest.raises(sparc.SparcError):
+        ctx.sync()
+    ctx.sync()   # the word was cleared
     net.close()
 
 
