@@ -90,6 +90,8 @@ void free_tables(Tables& t);
 // FP32 pass tile shapes: 0 = 16 x 16 nodes, 512 threads, one CTA per SM;
 // 1 = 16 x 8 nodes, 256 threads, two CTAs per SM.
 constexpr int NSHAPE_F32 = 2;
+// launch_pass<float> shape for a plain H-apply: 16 x 16 tiles, stencil in difference form
+constexpr int SHAPE_DIFF = 16;
 bool shape_usable(const sparc_ham* H, int shape);
 // Whether the tiled kernel handles this Hamiltonian (radius 6, FP32 element types).
 bool usable(const sparc_ham* H);

@@ -382,7 +382,10 @@ __device__ __forceinline__ void mma_tf32x3(float (&d)[4], const float (&a)[4], c
 }
 
 // TYT: tile rows (16 or 8); NT: threads (TYT * 32, two orbital pairs x 2 x-nodes each).
-template <int TYT, int NT>
+// DIFF: the stencil in difference form sum_p c_p ((f_{+p} - f_0) + (f_{-p} - f_0)) plus
+// (V - shift) f_0, whose FP32 rounding stays relative to the differences rather than
+// to |c_0| f_0 (the form a plain H-apply for the Rayleigh-Ritz projections needs).
+template <int TYT, int NT, bool DIFF = false>
 __global__ void __launch_bounds__(NT, 512 / NT)
 k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* Yout,
           const float* __restrict__ gc, int nitems) {
@@ -555,16 +558,25 @@ k_pass_f2(PassArgs a, const float* __restrict__ Yin, const float* Yprev, float* 
 #pragma unroll
         for (int r = 0; r < RX2; ++r) {
           // one partial sum per axis: three short dependency chains instead of one long one
-          float2 sx = __fmul2_rn(f2(a.c0 + V[r] - a.shift), q[(sidx + R) % Q][r]);
+          const float2 xc = q[(sidx + R) % Q][r];
+          float2 sx = __fmul2_rn(f2((DIFF ? 0.f : a.c0) + V[r] - a.shift), xc);
           float2 sy = make_float2(0.f, 0.f), sz = make_float2(0.f, 0.f);
           const float* col = P + (xl0 + r + R) * NB + o2;
+          const float2 m1 = f2(-1.f);
 #pragma unroll
           for (int p = 1; p <= R; ++p) {
             const float2 u = lds2(col + (yl + R + p) * RP);
             const float2 d = lds2(col + (yl + R - p) * RP);
-            sx = __ffma2_rn(a.cx2[p], __fadd2_rn(w[R + r + p], w[R + r - p]), sx);
-            sy = __ffma2_rn(a.cy2[p], __fadd2_rn(u, d), sy);
-            sz = __ffma2_rn(a.cz2[p], __fadd2_rn(q[(sidx + R + p) % Q][r], q[(sidx + R - p) % Q][r]), sz);
+            const float2 qu = q[(sidx + R + p) % Q][r], qd = q[(sidx + R - p) % Q][r];
+            if constexpr (DIFF) {   // f - f0 is one rounding (exact when f and f0 are close)
+              sx = __ffma2_rn(a.cx2[p], __fadd2_rn(__ffma2_rn(m1, xc, w[R + r + p]), __ffma2_rn(m1, xc, w[R + r - p])), sx);
+              sy = __ffma2_rn(a.cy2[p], __fadd2_rn(__ffma2_rn(m1, xc, u), __ffma2_rn(m1, xc, d)), sy);
+              sz = __ffma2_rn(a.cz2[p], __fadd2_rn(__ffma2_rn(m1, xc, qu), __ffma2_rn(m1, xc, qd)), sz);
+            } else {
+              sx = __ffma2_rn(a.cx2[p], __fadd2_rn(w[R + r + p], w[R + r - p]), sx);
+              sy = __ffma2_rn(a.cy2[p], __fadd2_rn(u, d), sy);
+              sz = __ffma2_rn(a.cz2[p], __fadd2_rn(qu, qd), sz);
+            }
           }
           acc[r] = __fadd2_rn(sx, __fadd2_rn(sy, sz));
         }
@@ -1324,6 +1336,7 @@ cudaError_t launch_pass(const sparc_ham* H, const T* Yin, const T* Yprev, T* You
   } else {
     const Tables* Tb = (const Tables*)H->fast;
     const bool half = shape == 1 && shape_usable(H, 1);
+    const bool diff = shape == SHAPE_DIFF;
     const Layout& Lo = Tb->lay[half ? 2 : 0];
     PassArgs a = pass_args(H, Lo);
     a.blk0 = blk0;
@@ -1341,6 +1354,13 @@ cudaError_t launch_pass(const sparc_ham* H, const T* Yin, const T* Yprev, T* You
       if (e != cudaSuccess) return e;
       t0 = timing_begin(H->ctx, st);
       k_pass_f2<8, 256><<<std::min(nitems, 2 * nsm), 256, smem, st>>>(a, Yin, Yprev, Yout, gc, nitems);
+    } else if (diff) {
+      constexpr size_t smem = Smem<float, 16>::total;
+      cudaError_t e =
+          cudaFuncSetAttribute(k_pass_f2<16, 512, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      t0 = timing_begin(H->ctx, st);
+      k_pass_f2<16, 512, true><<<std::min(nitems, nsm), 512, smem, st>>>(a, Yin, Yprev, Yout, gc, nitems);
     } else {
       constexpr size_t smem = Smem<float, 16>::total;
       cudaError_t e = cudaFuncSetAttribute(k_pass_f2<16, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1349,7 +1369,7 @@ cudaError_t launch_pass(const sparc_ham* H, const T* Yin, const T* Yprev, T* You
       k_pass_f2<16, 512><<<std::min(nitems, nsm), 512, smem, st>>>(a, Yin, Yprev, Yout, gc, nitems);
     }
     ++H->ctx->launches;
-    timing_end(H->ctx, TK_FPASS, t0, st);
+    timing_end(H->ctx, diff ? TK_HPASS : TK_FPASS, t0, st);   // the plain H-apply is not a filter pass
     return cudaGetLastError();
   }
 }

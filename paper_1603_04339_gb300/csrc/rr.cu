@@ -703,12 +703,14 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
   constexpr bool TCP = std::is_same<T, float>::value;   // FP32 data: tensor-core Grams and rotation
   const size_t tcb = TCP ? align256(std::max(tc::gram_scratch_bytes(ctx, ns, nd), tc::rot_scratch_bytes(ns))) : 0;
   const size_t w1b = TCP ? hub : 0;   // U1, the orthonormalised basis
+  const size_t gsb = apply_scratch_bytes(H, DtypeOf<T>::v, ns);   // projection scratch of the H-apply
   const size_t extra = hub + 2 * partb + 10 * sm + dinvb + align256(nn * es) + 3 * align256(nn * sizeof(TS)) +
-                       align256(ns * sizeof(double)) + tcb + w1b + 256;
+                       align256(ns * sizeof(double)) + tcb + w1b + gsb + 256;
   BlockWs w;
   char* tail = nullptr;
   sparc_status s = block_ws(H, DtypeOf<T>::v, ns, extra, &w, &tail);
   if (s != SPARC_OK) return s;
+  if (gsb) { w.gs = tail; tail += gsb; }
   T* HU = (T*)tail; tail += hub;
   TW* partH = (TW*)tail; tail += partb;
   TW* partM = (TW*)tail; tail += partb;

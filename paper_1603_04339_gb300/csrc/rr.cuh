@@ -10,7 +10,11 @@ struct BlockWs {
   void* b1;   // interleaved block buffer
   void* gc;   // projector coefficients [nproj][nblk][NB]
   char* tail; // first byte after the block workspace (start of the caller's extra bytes)
+  void* gs = nullptr;   // projection scratch of the tiled FP32 H-apply (null: the generic kernels)
 };
+// Bytes of projection scratch the tiled FP32 H-apply needs for ns orbitals (0 where it
+// does not apply).
+size_t apply_scratch_bytes(sparc_ham* H, sparc_dtype dt, int ns);
 
 sparc_status ensure_vals(sparc_ham* H, sparc_dtype dt);
 sparc_status check_block_args(sparc_ham* H, sparc_dtype dt, const void* X, const void* Y, int ns,

@@ -204,6 +204,17 @@ sparc_status apply_block(sparc_ham* H, const T* X, T* Y, int ns, long long ld, c
   T* gc = (T*)w.gc;
   SPARC_CUDA(H->ctx, launch_to_blocks<T>(X, ld, ns, b0, H->gd.nd, nblk, st));
   ++H->ctx->launches;
+  if constexpr (std::is_same<T, float>::value) {
+    if (w.gs && fast::usable(H)) {   // the tiled pass in difference form, all blocks in one launch
+      SPARC_CUDA(H->ctx, fast::launch_gather<T>(H, b0, nblk, 0, nblk, gc, (T*)w.gs, st));
+      SPARC_CUDA(H->ctx, fast::launch_pass<T>(H, b0, nullptr, b1, gc, nblk, 0, nblk, 1.0, 0.0, 0.0, st,
+                                              fast::SHAPE_DIFF));
+      SPARC_CUDA(H->ctx, launch_from_blocks<T>(b1, H->gd.nd, nblk, Y, ld, ns, st));
+      ++H->ctx->launches;
+      SPARC_LAUNCH(H->ctx, "H apply");
+      return SPARC_OK;
+    }
+  }
   SPARC_CUDA(H->ctx, launch_nl_gather<T>(H, b0, NB, nblk, gc, st));
   SPARC_CUDA(H->ctx, launch_hpass<T>(H, b0, nullptr, b1, gc, NB, nblk, 1.0, 0.0, 0.0, true, st));
   SPARC_CUDA(H->ctx, launch_from_blocks<T>(b1, H->gd.nd, nblk, Y, ld, ns, st));
@@ -300,6 +311,12 @@ sparc_status filter_block_fast(sparc_ham* H, int m, double a, double b, double a
   SPARC_CUDA(H->ctx, launch_from_blocks<T>(res, H->gd.nd, nblk, Y, ld, ns, st));
   ++H->ctx->launches;
   return SPARC_OK;
+}
+
+size_t apply_scratch_bytes(sparc_ham* H, sparc_dtype dt, int ns) {
+  if (dt == SPARC_F32 && fast::usable(H))
+    return align256(fast::gather_scratch_bytes(H, ceil_div(ns, NB), sizeof(float)));
+  return 0;
 }
 
 size_t filter_ws(sparc_ham* H, sparc_dtype dt, int ns, char* base, BlockWs* w) {
@@ -721,8 +738,10 @@ sparc_status sparc_apply_H(sparc_ham* H, sparc_dtype dtype, const void* X, void*
   if (s != SPARC_OK) return s;
   SPARC_CUDA(H->ctx, cudaSetDevice(H->ctx->device));
   BlockWs w;
-  s = block_ws(H, dtype, ns, 0, &w, nullptr);
+  const size_t gsb = apply_scratch_bytes(H, dtype, ns);
+  s = block_ws(H, dtype, ns, gsb, &w, nullptr);
   if (s != SPARC_OK) return s;
+  if (gsb) w.gs = w.tail;
   cudaStream_t st = (cudaStream_t)stream;
   switch (dtype) {
     case SPARC_F64: return apply_block<double>(H, (const double*)X, (double*)Y, ns, ld, st, w);
