@@ -17,6 +17,10 @@ constexpr int RPARTS = 304; // reduction blocks (2 per SM)
 template <class T> __device__ __forceinline__ T lz_zero();
 template <> __device__ __forceinline__ double lz_zero<double>() { return 0.0; }
 template <> __device__ __forceinline__ cf64 lz_zero<cf64>() { return {0.0, 0.0}; }
+__device__ __forceinline__ double shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ cf64 shfl_xor(cf64 v, int o) {
+  return {__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)};
+}
 
 // part[b][i] = sum over this block's share of g of conj(V_i[g]) w[g], i < nv
 template <class T>
@@ -42,11 +46,13 @@ __global__ void __launch_bounds__(RB) k_multidot_part(const T* __restrict__ V, i
 // out[i] = sum_b part[b][i] in a fixed order (deterministic).
 template <class T>
 __global__ void k_multidot_final(const T* __restrict__ part, int nparts, int nv, T* __restrict__ out) {
-  const int i = threadIdx.x;
+  // one warp per dot product: lane-strided partial sums, then a fixed butterfly
+  const int i = blockIdx.x, lane = threadIdx.x;
   if (i >= nv) return;
   T acc = lz_zero<T>();
-  for (int b = 0; b < nparts; ++b) acc = add(acc, part[(size_t)b * 64 + i]);
-  out[i] = acc;
+  for (int b = lane; b < nparts; b += 32) acc = add(acc, part[(size_t)b * 64 + i]);
+  for (int o = 16; o > 0; o >>= 1) acc = add(acc, shfl_xor(acc, o));
+  if (lane == 0) out[i] = acc;
 }
 
 // alpha_j = Re(dot); w -= alpha_j v_j + beta_{j-1} v_{j-1}
@@ -114,13 +120,16 @@ __device__ int sturm_count(const double* a, const double* b, int k, double x) {
   return cnt;
 }
 
-// Smallest and largest eigenvalue of T by bisection on the Sturm count; writes
-// out[0] = theta_min, out[1] = theta_max + |beta_k|.
+// Smallest and largest eigenvalue of T by multisection on the Sturm count (one warp:
+// each step evaluates the count at 32 interior points and keeps the sub-interval where
+// it reaches its target, shrinking the bracket 33-fold); writes out[0] = theta_min,
+// out[1] = theta_max + |beta_k|.
 __global__ void k_tridiag_bounds(const double* __restrict__ alpha, const double* __restrict__ beta,
                                  int k, double* __restrict__ out) {
-  if (threadIdx.x != 0) return;
+  const int lane = threadIdx.x;
+  if (lane >= 32) return;
   double lo = alpha[0], hi = alpha[0];
-  for (int i = 0; i < k; ++i) {
+  for (int i = 0; i < k; ++i) {   // Gershgorin bracket
     const double r = (i > 0 ? fabs(beta[i - 1]) : 0.0) + (i + 1 < k ? fabs(beta[i]) : 0.0);
     lo = fmin(lo, alpha[i] - r);
     hi = fmax(hi, alpha[i] + r);
@@ -133,16 +142,29 @@ __global__ void k_tridiag_bounds(const double* __restrict__ alpha, const double*
     // which = 0: boundary of count 0 -> 1 (theta_min); which = 1: count k-1 -> k (theta_max)
     const int target = (which == 0) ? 1 : k;
     double l = lo, h = hi;
-    for (int it = 0; it < 200; ++it) {
-      const double mid = 0.5 * (l + h);
-      if (mid <= l || mid >= h) break;
-      if (sturm_count(alpha, beta, k, mid) >= target) h = mid;
-      else l = mid;
+    for (int it = 0; it < 40; ++it) {
+      const double x = l + (h - l) * (double)(lane + 1) / 33.0;
+      // the points are nondecreasing in the lane, so the counts are too, even where x
+      // rounds onto l or h
+      const unsigned hit = __ballot_sync(0xffffffffu, sturm_count(alpha, beta, k, x) >= target);
+      double nl = l, nh = h;
+      if (hit) {
+        const int j = __ffs(hit) - 1;   // first point at or past the boundary
+        nh = l + (h - l) * (double)(j + 1) / 33.0;
+        if (j > 0) nl = l + (h - l) * (double)j / 33.0;
+      } else {
+        nl = l + (h - l) * 32.0 / 33.0;
+      }
+      if (!(nl > l || nh < h)) break;   // no progress at FP64 resolution
+      l = nl;
+      h = nh;
     }
     res[which] = 0.5 * (l + h);
   }
-  out[0] = res[0];
-  out[1] = res[1] + fabs(beta[k - 1]);
+  if (lane == 0) {
+    out[0] = res[0];
+    out[1] = res[1] + fabs(beta[k - 1]);
+  }
 }
 
 template <class T>
@@ -174,7 +196,7 @@ sparc_status lanczos(sparc_ham* H, int ksteps, const T* v0, double* a0, double* 
   // ||v0|| and V_0
   k_multidot_part<T><<<RPARTS, RB, 0, st>>>(v0, 1, 0, v0, nd, part);
   ++ctx->launches;
-  k_multidot_final<T><<<1, 64, 0, st>>>(part, RPARTS, 1, dots);
+  k_multidot_final<T><<<1, 32, 0, st>>>(part, RPARTS, 1, dots);
   ++ctx->launches;
   k_start<T><<<EG, EB, 0, st>>>(v0, Vi(0), dots, nd);
   ++ctx->launches;
@@ -186,21 +208,21 @@ sparc_status lanczos(sparc_ham* H, int ksteps, const T* v0, double* a0, double* 
     // alpha_j = Re(v_j^H w); w -= alpha_j v_j + beta_{j-1} v_{j-1}
     k_multidot_part<T><<<RPARTS, RB, 0, st>>>(Vi(j), 1, 0, w, nd, part);
     ++ctx->launches;
-    k_multidot_final<T><<<1, 64, 0, st>>>(part, RPARTS, 1, dots);
+    k_multidot_final<T><<<1, 32, 0, st>>>(part, RPARTS, 1, dots);
     ++ctx->launches;
     k_three_term<T><<<EG, EB, 0, st>>>(w, Vi(j), j > 0 ? Vi(j - 1) : Vi(j), dots, alpha, beta, j, nd);
     ++ctx->launches;
     // full reorthogonalisation against v_0..v_j (the vectors are spaced by vstride)
     k_multidot_part<T><<<RPARTS, RB, 0, st>>>(V, j + 1, vstride, w, nd, part);
     ++ctx->launches;
-    k_multidot_final<T><<<1, 64, 0, st>>>(part, RPARTS, j + 1, dots);
+    k_multidot_final<T><<<j + 1, 32, 0, st>>>(part, RPARTS, j + 1, dots);
     ++ctx->launches;
     k_reorth<T><<<EG, EB, 0, st>>>(w, V, j + 1, vstride, dots, nd);
     ++ctx->launches;
     // beta_j = ||w||, v_{j+1} = w / beta_j
     k_multidot_part<T><<<RPARTS, RB, 0, st>>>(w, 1, 0, w, nd, part);
     ++ctx->launches;
-    k_multidot_final<T><<<1, 64, 0, st>>>(part, RPARTS, 1, dots);
+    k_multidot_final<T><<<1, 32, 0, st>>>(part, RPARTS, 1, dots);
     ++ctx->launches;
     k_normalise<T><<<EG, EB, 0, st>>>(w, j + 1 <= ksteps ? Vi(j + 1) : w, dots, beta, j,
                                       j + 1 < ksteps ? 1 : 0, nd);
