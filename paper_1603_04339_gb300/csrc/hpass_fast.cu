@@ -1205,6 +1205,14 @@ static int gather_slabs(const sparc_ham* H) {
   return std::max(1, std::min(NSLAB_MAX, ceil_div(want, std::max(1, Tb->ngrp))));
 }
 constexpr int GATHER_OCT_C = 4;   // complex64 blocks per projection CTA
+// FP32: slabs from the total block count (8 blocks per CTA at most), not the blocks of
+// one launch, so that every grouping of the same filter sums in the same order.
+static int gather_slabs_f2(const sparc_ham* H, int nblk_total) {
+  const Tables* Tb = (const Tables*)H->fast;
+  const int want = 6 * H->ctx->nsm;
+  const int octs = std::max(1, ceil_div(nblk_total, 8));
+  return std::max(1, std::min(NSLAB_MAX, ceil_div(want, std::max(1, Tb->ngrp) * octs)));
+}
 
 size_t gather_scratch_bytes(const sparc_ham* H, int nb, size_t esize) {
   const Tables* Tb = (const Tables*)H->fast;
@@ -1246,7 +1254,7 @@ cudaError_t launch_gather(const sparc_ham* H, const T* Y, int nblk_total, int bl
     return launch_gather_k(H, Y, nblk_total, ks, gc, scratch, st);
   } else {
     const float dv = (float)(H->grid.h[0] * H->grid.h[1] * H->grid.h[2]);
-    const int nslab = gather_slabs(H);
+    const int nslab = gather_slabs_f2(H, nblk_total);
     cudaEvent_t t0 = timing_begin(H->ctx, st);
     // pairs of blocks per CTA: as many as the group has, at most 4 pairs
     const int nb2 = std::min(4, (nb + 1) / 2);
