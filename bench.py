@@ -27,8 +27,8 @@ sys.path.insert(0, ROOT)
 METRIC = "CheFSI filter throughput (G point-orbital-degrees/s)"
 UNIT = "Gpt-orb-deg/s"
 WORKLOAD = "64^3 grid h=0.4, 128 perturbed-FCC s+p atoms, Ns=512, m=24, Gamma point"
-# DRAM bytes of k_pass_f2 per block of 8 orbitals per degree on this cell, from the ncu
-# capture summarised in profiles/k_pass_f2_64cube_32blocks.md ((579.43 + 242.48) MB / 32 blocks)
+# DRAM bytes of k_pass_f2 per block of 8 orbitals per degree on this cell, from one ncu
+# capture of a 32-block launch (579.43 MB read + 242.48 MB written)
 PASS_DRAM_BYTES_PER_BLOCK = (579.433984e6 + 242.480128e6) / 32
 
 
@@ -497,8 +497,8 @@ def run_ours(args):
     fp_launches = fp_n / args.steps
     achieved = bytes_step / (fp_ms / args.steps * 1e-3) / 1e9
     peak, peak_kind = _peaks()
-    # DRAM traffic: one ncu capture of a 32-block launch of this cell (profiles/
-    # k_pass_f2_64cube_32blocks.md: 579.43 MB read + 242.48 MB written), scaled by blocks
+    # DRAM traffic: one ncu capture of a 32-block launch of this cell (579.43 MB read +
+    # 242.48 MB written), scaled by blocks
     traffic = PASS_DRAM_BYTES_PER_BLOCK * (ns // 8) * m / fp_launches if fp_launches else None
 
     # ---- end to end through the C ABI with host buffers: every step copies its input from
