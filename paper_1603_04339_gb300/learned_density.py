@@ -47,6 +47,14 @@ class ScfRun:
     vresid: float
     rho: object          # CUDA float64 tensor, Nd
     b: object            # CUDA float64 tensor, Nd
+    residuals: list      # V residual of every iteration
+
+    def iterations_to(self, tol):
+        """First iteration (1-based) whose V residual is below tol, or None."""
+        for i, r in enumerate(self.residuals):
+            if r < tol:
+                return i + 1
+        return None
 
 
 def converge(ctx, sysd, dtype, tol=1e-6, max_iter=80, first_passes=4, dy=None, scale=0.0, kT=0.01):
@@ -63,8 +71,10 @@ def converge(ctx, sysd, dtype, tol=1e-6, max_iter=80, first_passes=4, dy=None, s
         S.set_density(dy, scale)
     info = None
     it = 0
+    res = []
     for it in range(1, max_iter + 1):
         info = sparc.sparc_scf_step(S, U, eig, wl.m)
+        res.append(info["vresid"])
         if info["vresid"] < tol:
             break
     torch.cuda.synchronize()
@@ -76,7 +86,7 @@ def converge(ctx, sysd, dtype, tol=1e-6, max_iter=80, first_passes=4, dy=None, s
     torch.cuda.synchronize()
     S.close()
     H.close()
-    return ScfRun(it, sec, info["free_energy"], info["vresid"], rho, b)
+    return ScfRun(it, sec, info["free_energy"], info["vresid"], rho, b, res)
 
 
 def descriptors(ctx, sysd):
