@@ -185,6 +185,9 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD,
+                                            "path": "FP64 Lanczos k=10, FP32 filter, mixed Rayleigh-Ritz",
+                                            "l2": "inputs larger than L2 (537 MB block)",
+                                            "parallelism": f"replicas x{args.gpus}",
                                             "sample": f"{args.cpu_sample_cols} of 512 orbitals, all 24 degrees"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"numpy FP64 oracle filter, {args.cpu_sample_cols} column(s) x 24 degrees"},
