@@ -12,6 +12,11 @@
  *                                                        (Eq. SubspaceGeneralizedEigenproblem)
  *   U    = U_f Y                                         (Eq. OrbitalTransformation)
  *
+ * Around the step: the SCF iteration at Gamma or over k-points with forces
+ * (sparc_scf_*, Sections 2, 3.4-3.6 and 5), filters batched over k-points and
+ * over independent cells in one CUDA graph with a launch-shape autotuner, and a
+ * learned initial density (sparc_mlp_*, project-added).
+ *
  * Conventions that hold for every entry point:
  *   - Grid: n1 x n2 x n3 nodes, spacings h1,h2,h3 (bohr); node (i,j,k), 0-based,
  *     sits at (-L1/2 + i h1, ...), L_s = n_s h_s; grid index g = i + n1 (j + n2 k).
