@@ -29,7 +29,8 @@
  *   - Calls are asynchronous on `stream` (a cudaStream_t, NULL = legacy default
  *     stream) unless stated otherwise.  Argument errors are returned at once;
  *     errors found by kernels (non-positive-definite M~, bounded waits that
- *     ran out) are latched in a device status word that sparc_sync() reads.
+ *     ran out, a row index outside its array) are latched in a device status
+ *     word that sparc_sync() reads.
  *   - The caller owns every buffer it passes.  The context owns its workspace,
  *     which grows on demand and is reused across calls; calls on one context
  *     must not overlap on different streams.
@@ -102,7 +103,11 @@ sparc_status sparc_create(sparc_ctx** ctx, int device);
 void sparc_destroy(sparc_ctx* ctx);
 /* One-line description of the last failure on this context ("" if none). */
 const char* sparc_last_error(const sparc_ctx* ctx);
-/* Synchronise `stream`, then read and clear the device status word. */
+/* Synchronise `stream`, then read and clear the device status word: a bounded
+ * wait that gave up -> SPARC_ERR_TIMEOUT; M~ not positive definite ->
+ * SPARC_ERR_NOT_POSDEF; a gathered row index outside its array ->
+ * SPARC_ERR_INVALID_ARG; the eigensolver's sweep limit -> SPARC_ERR_NO_CONVERGENCE
+ * (checked in that order when several are latched). */
 sparc_status sparc_sync(sparc_ctx* ctx, void* stream);
 
 /* Build H(k) on the context's device: copies the grid, V_eff (host, Nd doubles)
