@@ -305,11 +305,12 @@ __device__ Rot<TW> jacobi_rot(const TW* A, int n, int p, int q) {
   Rot<TW> u;
   u.c = (R)1; u.s = (R)0; u.eph = from_real<TW>(1.0);
   if (p >= n || q >= n) return u;
+  // the three entries are read together (one memory round trip, not two)
   const TW b = A[p + (long long)q * n];
-  const R ab = sqrt(Tr<TW>::abs2(b));
-  if (!(ab > (R)0)) return u;
   const R a = Tr<TW>::re(A[p + (long long)p * n]);
   const R d = Tr<TW>::re(A[q + (long long)q * n]);
+  const R ab = sqrt(Tr<TW>::abs2(b));
+  if (!(ab > (R)0)) return u;
   const R th = (d - a) / ((R)2 * ab);
   const R t = (th >= (R)0 ? (R)1 : (R)-1) / (fabs(th) + sqrt(th * th + (R)1));
   u.c = (R)1 / sqrt(t * t + (R)1);
