@@ -814,17 +814,19 @@ extern "C" sparc_status sparc_scf_create_k(sparc_ham* const* Hs, int nk, const d
     delete S;
     return fail(ctx, SPARC_ERR_OOM, "sparc_scf_create: device allocation failed");
   }
+  // from here on, every failure return frees S; success releases it to the caller
+  struct Owner {
+    sparc_scf* s;
+    ~Owner() { if (s) { free_scf(s); delete s; } }
+  } owner{S};
   cudaStream_t st = 0;
   SPARC_CUDA(ctx, cudaMemcpy(S->d_atoms, S->atoms.data(), S->atoms.size() * sizeof(Atom), cudaMemcpyHostToDevice));
   SPARC_CUDA(ctx, cudaMemcpy(S->d_v0, d->v0, v0b, cudaMemcpyHostToDevice));
   S->nproj = H->nproj;
   if (d->proj_atom && H->nproj > 0) {
     for (int p = 0; p < H->nproj; ++p)
-      if (d->proj_atom[p] < 0 || d->proj_atom[p] >= d->natom) {
-        free_scf(S);
-        delete S;
+      if (d->proj_atom[p] < 0 || d->proj_atom[p] >= d->natom)
         return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_scf_create: proj_atom out of range");
-      }
     SPARC_CUDA(ctx, cudaMalloc(&S->d_patom, H->nproj * sizeof(int)));
     SPARC_CUDA(ctx, cudaMemcpy(S->d_patom, d->proj_atom, H->nproj * sizeof(int), cudaMemcpyHostToDevice));
   }
@@ -842,12 +844,9 @@ extern "C" sparc_status sparc_scf_create_k(sparc_ham* const* Hs, int nk, const d
   SPARC_LAUNCH(ctx, "scf setup");
   sparc_status rc = SPARC_OK;
   for (int k = 0; k < nk && rc == SPARC_OK; ++k) rc = sparc_ham_set_veff(Hs[k], S->d_vxc, 1, st);
-  if (rc != SPARC_OK) {
-    free_scf(S);
-    delete S;
-    return rc;
-  }
+  if (rc != SPARC_OK) return rc;
   SPARC_CUDA(ctx, cudaMemcpy(&S->e_self, S->d_scal + S_ESELF, sizeof(double), cudaMemcpyDeviceToHost));
+  owner.s = nullptr;
   *out = S;
   return SPARC_OK;
 }
@@ -1091,11 +1090,18 @@ extern "C" sparc_status sparc_scf_forces(sparc_scf* S, sparc_dtype dtype, const 
   int maxcube = 1;
   for (const Atom& A : S->atoms) maxcube = std::max(maxcube, (2 * A.nb[0] + 1) * (2 * A.nb[1] + 1) * (2 * A.nb[2] + 1));
   const int nby = ceil_div(maxcube, TPB);
-  double *d_loc = nullptr, *d_prj = nullptr, *d_f = nullptr;
+  // per-call buffers, freed on every return path
+  struct DevDoubles {
+    double* p = nullptr;
+    ~DevDoubles() { if (p) cudaFree(p); }
+  } loc, prj, fo;
   const int np = H->nproj;
-  SPARC_CUDA(ctx, cudaMalloc(&d_loc, (size_t)natom * nby * 3 * sizeof(double)));
-  SPARC_CUDA(ctx, cudaMalloc(&d_prj, (size_t)std::max(np, 1) * ns * 4 * sizeof(double)));
-  SPARC_CUDA(ctx, cudaMalloc(&d_f, (size_t)natom * 6 * sizeof(double)));
+  SPARC_CUDA(ctx, cudaMalloc(&loc.p, (size_t)natom * nby * 3 * sizeof(double)));
+  SPARC_CUDA(ctx, cudaMalloc(&prj.p, (size_t)std::max(np, 1) * ns * 4 * sizeof(double)));
+  SPARC_CUDA(ctx, cudaMalloc(&fo.p, (size_t)natom * 6 * sizeof(double)));
+  double* const d_loc = loc.p;
+  double* const d_prj = prj.p;
+  double* const d_f = fo.p;
   k_force_local<<<dim3(natom, nby), TPB, 0, st>>>(H->gd.n1, H->gd.n2, H->gd.n3, H->grid.h[0], H->grid.h[1],
                                                    H->grid.h[2], H->gd.no, S->W, G, S->d_atoms, S->d_phi, d_loc);
   ++ctx->launches;
@@ -1120,9 +1126,6 @@ extern "C" sparc_status sparc_scf_forces(sparc_scf* S, sparc_dtype dtype, const 
   std::vector<double> hf((size_t)natom * 6);
   SPARC_CUDA(ctx, cudaMemcpyAsync(hf.data(), d_f, hf.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   SPARC_CUDA(ctx, cudaStreamSynchronize(st));
-  cudaFree(d_loc);
-  cudaFree(d_prj);
-  cudaFree(d_f);
   for (int i = 0; i < 3 * natom; ++i) {
     f_host[i] = hf[i] + hf[3 * natom + i];           // total
     f_host[3 * natom + i] = hf[i];                   // local part
