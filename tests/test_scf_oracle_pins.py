@@ -112,6 +112,38 @@ def test_fermi_level_symmetric_spectrum():
     assert abs(S.entropy_term(np.array([0.5]), 0.01) - 2 * 0.01 * math.log(0.5)) < 1e-15
 
 
+def test_fermi_dirac_occupations_minimise_the_band_plus_entropy_functional():
+    """Mermin's principle: at fixed electron count 2 sum g = N_e, the band energy plus the
+    entropy term, 2 sum g lambda + 2 kT sum (g ln g + (1-g) ln(1-g)), is stationary at
+    the Fermi-Dirac occupations with every partial derivative equal to 2 lambda_f, and
+    any count-preserving change of the occupations raises it.  A wrong sign or factor
+    of the entropy term, or of the occupation exponent, moves the minimum elsewhere."""
+    rng = np.random.default_rng(12)
+    lam = np.sort(rng.uniform(-0.4, 0.2, 24))
+    kT, Ne = 0.02, 22.0
+    mu = S.fermi_level(lam, Ne, kT)
+    g = S.occupations(lam, mu, kT)
+    F = lambda gg: 2.0 * float(np.sum(gg * lam)) + S.entropy_term(gg, kT)
+    # F is a sum of one term per state: differentiate state n's term alone, with a step
+    # inside (0, 1) that shrinks with g (1 - g) where ln g curves
+    f_n = lambda n, x: 2.0 * x * lam[n] + S.entropy_term(np.array([x]), kT)
+    checked = 0
+    for n in range(len(lam)):
+        eps = 1e-4 * min(g[n], 1.0 - g[n])
+        if eps < 1e-14:
+            continue
+        dF = (f_n(n, g[n] + eps) - f_n(n, g[n] - eps)) / (2 * eps)
+        assert abs(dF - 2.0 * mu) < 1e-6, (n, g[n], dF, 2 * mu)
+        checked += 1
+    assert checked >= 15
+    F0 = F(g)
+    for trial in range(20):
+        d = rng.standard_normal(len(g))
+        d -= d.mean()                             # keeps 2 sum g = N_e
+        t = 0.5 * min(np.min(g / (np.abs(d) + 1e-300)), np.min((1 - g) / (np.abs(d) + 1e-300)))
+        assert F(g + t * d) > F0
+
+
 def test_anderson_solves_a_linear_fixed_point_exactly():
     rng = np.random.default_rng(5)
     dim = 5
