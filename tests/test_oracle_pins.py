@@ -238,6 +238,39 @@ def test_grid_translation_across_boundary_preserves_spectrum():
             assert np.allclose(e, e_ref, atol=1e-10), shift
 
 
+def test_supercell_spectrum_folds_two_primitive_k_points():
+    """Bloch's theorem (Section 2): the cell doubled along x, at wavevector K, has the
+    spectrum of the primitive cell at K and at K + pi/L_x together.  V_eff and the atoms
+    repeat with the primitive period, so this fixes the size and the sign convention of
+    the Bloch phase on the stencil halo and on the projector images jointly (a phase of
+    the wrong size, or one part taking exp(-ikL) where the other takes exp(+ikL), breaks
+    the folding).  Radius-3 stencil to keep the dense supercell small."""
+    n_o = 3
+    n, h = (8, 7, 7), (0.55, 0.6, 0.6)
+    L = np.array([n[s] * h[s] for s in range(3)])
+    rng = np.random.default_rng(31)
+    V = rng.uniform(-1.0, 0.5, (n[2], n[1], n[0]))
+    R = np.array([-0.31, 0.17, -0.09]) * L            # R_x < 0, so R_x + L_x stays inside the doubled cell
+    gs, gp = np.array([0.7]), np.array([-0.4])
+    K = (0.21, -0.13, 0.37)
+    spec = []
+    for kx in (K[0], K[0] + math.pi / L[0]):
+        proj = synth.make_projectors(n, h, R[None, :], 0.5, gs, gp)
+        H = O.OracleH(n=n, h=h, fd_radius=n_o, k=(kx, K[1], K[2]), veff=V.reshape(-1), proj=proj)
+        spec.append(np.linalg.eigvalsh(H.dense()))
+    n2 = (2 * n[0], n[1], n[2])
+    # node i' of the doubled cell (x = -L_x + i' h) is primitive node i' - n_x/2 (mod n_x)
+    V2 = V[:, :, (np.arange(n2[0]) - n[0] // 2) % n[0]]
+    atoms2 = np.stack([R, R + np.array([L[0], 0.0, 0.0])])
+    proj2 = synth.make_projectors(n2, h, atoms2, 0.5, np.repeat(gs, 2), np.repeat(gp, 2))
+    H2 = O.OracleH(n=n2, h=h, fd_radius=n_o, k=K, veff=V2.reshape(-1), proj=proj2)
+    e2 = np.linalg.eigvalsh(H2.dense())
+    e1 = np.sort(np.concatenate(spec))
+    assert np.max(np.abs(e2 - e1)) < 1e-10 * np.max(np.abs(e1))
+    # and the two primitive k-points do differ, so the check has teeth
+    assert np.max(np.abs(spec[0] - spec[1])) > 1e-2
+
+
 # ---------------------------------------------------------------- Chebyshev filter (Eq. ChebFilter)
 
 def test_cheb_T_closed_form_matches_recurrence():
