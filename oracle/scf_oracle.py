@@ -331,6 +331,49 @@ def grad_h(F: np.ndarray, n, h, n_o: int) -> np.ndarray:
     return np.stack(out)
 
 
+def nonlocal_forces_bloch(n, h, n_o, k, proj, U, g, w=1.0, natom=None):
+    """Nonlocal forces of the Bloch orbitals of one k-point (Section 3.6, Eq.
+    NonlocForce:Discrete, with the image phases of Eq. NonlocalPS:FD):
+
+      f_J = -4 w sum_n g_n sum_{p of atom J} gamma_p Re(conj(Y_pn) W_pn),
+      Y_pn = h1h2h3 sum_g conj(chi~_p[g]) psi_n[g],
+      W_pn = h1h2h3 sum_g conj(chi~_p[g]) (nabla_h psi_n)[g],
+
+    psi = U / sqrt(h1h2h3) (rows of U), nabla_h the gradient of Eq.
+    gradient:approximate with the Bloch wrap of Section 3.1 (a neighbour across a face
+    carries exp(+-i k_s L_s)).  The derivative of chi~ with respect to the atom
+    position is moved onto psi by summation by parts, exact for the antisymmetric
+    nabla_h on two grid functions of the same k.  At k = 0 with real U this is the
+    nonlocal part of forces(); over k-points the forces add with the weights w."""
+    n = tuple(int(v) for v in n)
+    h = tuple(float(v) for v in h)
+    dv = h[0] * h[1] * h[2]
+    nd = n[0] * n[1] * n[2]
+    if natom is None:
+        natom = int(np.max(proj.atom)) + 1 if proj.nproj else 0
+    Hk = O.OracleH(n=n, h=h, fd_radius=n_o, k=k, veff=np.zeros(nd), proj=proj)
+    U = np.atleast_2d(np.asarray(U)).astype(np.complex128)
+    U3 = U.reshape((U.shape[0],) + n[::-1])
+    grads = []
+    for s in range(3):
+        ax = U3.ndim - 1 - s
+        kL = float(k[s]) * n[s] * h[s]
+        wg = grad_weights(n_o, h[s])
+        G = np.zeros_like(U3)
+        for p in range(1, n_o + 1):
+            G = G + wg[p] * (O._shift(U3, p, ax, n[s], kL) - O._shift(U3, -p, ax, n[s], kL))
+        grads.append(G.reshape(U.shape[0], nd))
+    gg = np.asarray(g, dtype=np.float64)
+    f = np.zeros((natom, 3))
+    for p, (gi, v) in enumerate(zip(Hk.pidx, Hk.pval)):
+        J = int(proj.atom[p])
+        Y = math.sqrt(dv) * (U[:, gi] @ np.conj(v))
+        for s in range(3):
+            W = math.sqrt(dv) * (grads[s][:, gi] @ np.conj(v))
+            f[J, s] += -4.0 * w * Hk.gamma[p] * float(np.sum(gg * np.real(np.conj(Y) * W)))
+    return f
+
+
 def forces(n, h, n_o, R, Z, rc, phi, proj, U, g, gamma_atoms=None):
     """Atomic forces at the Gamma point (Section 3.6): f = f_loc + f_c + f_nloc, with
     f_c = 0 (no overlapping pseudocharges, see the readings).

@@ -7,6 +7,7 @@ import pytest
 
 from oracle import scf_oracle as S
 from oracle import sparc_oracle as O
+from paper_1603_04339_gb300 import synth
 
 
 def test_local_potential_limits():
@@ -240,6 +241,70 @@ def test_forces_match_finite_differences_of_the_free_energy():
         Rm[0, s] -= d
         fd = -(converged(Rp)[0]["F"] - converged(Rm)[0]["F"]) / (2 * d)
         assert abs(fd - f[0, s]) < 5e-5, (s, fd, f[0, s])
+
+
+def _smooth_bloch_orbitals(n, h, k, ns, rng):
+    """ns orthonormal Bloch functions at k made of the 27 plane waves exp(i(k+G).x) with
+    |G_s| <= 2 pi / L_s (smooth on the grid, so the discrete sums stand for integrals)."""
+    import itertools
+    L = np.array([n[s] * h[s] for s in range(3)])
+    xs = synth.node_coords(n, h)
+    Zg, Yg, Xg = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+    P = np.stack([Xg.reshape(-1), Yg.reshape(-1), Zg.reshape(-1)], axis=1)
+    U = np.zeros((ns, P.shape[0]), np.complex128)
+    for t in itertools.product((-1, 0, 1), repeat=3):
+        q = np.asarray(k) + np.array(t) * 2 * math.pi / L
+        U += np.outer(rng.standard_normal(ns) + 1j * rng.standard_normal(ns), np.exp(1j * P @ q))
+    return np.linalg.qr(U.T)[0].T
+
+
+def test_bloch_nonlocal_force_is_minus_the_position_derivative_of_the_energy():
+    """At k != 0, with the atom's projector box wrapping two faces: the Bloch nonlocal
+    force (Section 3.6 with the phases of Eq. NonlocalPS:FD) equals minus the central
+    difference, in the atom position, of the nonlocal energy 2 sum_n g_n sum_p gamma_p
+    |Y_pn|^2 of fixed smooth orbitals (projectors rebuilt at each position).  The two
+    agree to about 4e-5 relative (the box truncation at 3 rc and the per-box
+    normalisation); a lost conjugate, a Bloch phase of the wrong sign in nabla_h or a
+    wrong prefactor is an O(1) error."""
+    n, h, n_o = (14, 13, 13), (0.5, 0.5, 0.5), 6
+    L = np.array([n[s] * h[s] for s in range(3)])
+    nd, dv = n[0] * n[1] * n[2], 0.125
+    rng = np.random.default_rng(3)
+    R = np.array([0.47, -0.41, 0.05]) * L
+    gs, gp = np.array([0.8]), np.array([-0.6])
+    k = (0.31, -0.17, 0.23)
+    U = _smooth_bloch_orbitals(n, h, k, 6, rng)
+    g = rng.uniform(0.2, 1.0, 6)
+
+    def energy(Rx):
+        proj = synth.make_projectors(n, h, Rx[None, :], 0.9, gs, gp)
+        H = O.OracleH(n=n, h=h, fd_radius=n_o, k=k, veff=np.zeros(nd), proj=proj)
+        c = H.nonlocal_coeffs(U / math.sqrt(dv))
+        return 2.0 * sum(H.gamma[p] * float(np.sum(g * np.abs(c[p]) ** 2)) for p in range(len(H.gamma)))
+
+    proj = synth.make_projectors(n, h, R[None, :], 0.9, gs, gp)
+    f = S.nonlocal_forces_bloch(n, h, n_o, k, proj, U, g)
+    d = 1e-3
+    fd = np.array([-(energy(R + d * e) - energy(R - d * e)) / (2 * d) for e in np.eye(3)])
+    assert np.max(np.abs(f[0] - fd)) < 3e-4 * np.max(np.abs(fd)), (f[0], fd)
+    # the k-point weight scales the force
+    assert np.allclose(S.nonlocal_forces_bloch(n, h, n_o, k, proj, U, g, w=0.25), 0.25 * f, rtol=1e-14, atol=0)
+
+
+def test_bloch_nonlocal_force_at_gamma_is_the_real_orbital_formula():
+    """At k = 0 with real orbitals the Bloch form reduces to the nonlocal part of the
+    Gamma-point forces (same discrete sums, so to rounding)."""
+    n, h, n_o = (14, 13, 13), (0.5, 0.5, 0.5), 6
+    L = np.array([n[s] * h[s] for s in range(3)])
+    nd = n[0] * n[1] * n[2]
+    rng = np.random.default_rng(4)
+    R = np.array([[0.45, -0.2, 0.1], [-0.3, 0.35, -0.44]]) * L
+    proj = synth.make_projectors(n, h, R, 0.9, np.array([0.8, -0.5]), np.array([-0.6, 0.3]))
+    U = np.linalg.qr(rng.standard_normal((nd, 5)))[0].T
+    g = rng.uniform(0.2, 1.0, 5)
+    _, _, f_nl = S.forces(n, h, n_o, R, np.array([1.0, 1.0]), np.array([0.7, 0.7]), np.zeros(nd), proj, U, g)
+    f = S.nonlocal_forces_bloch(n, h, n_o, (0.0, 0.0, 0.0), proj, U, g)
+    assert np.allclose(f, f_nl, rtol=0, atol=1e-12 * np.max(np.abs(f_nl)))
 
 
 def test_starting_density_normalisation_and_atomic_special_case():
