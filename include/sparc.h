@@ -129,17 +129,21 @@ sparc_status sparc_apply_H(sparc_ham* H, sparc_dtype dtype, const void* X, void*
 
 /* Y = H X like sparc_apply_H, but the call itself allocates no device memory.
  * The paper has no counterpart: this entry point exists for callers that
- * cannot allocate at the point of the call, such as code being captured into
- * a CUDA graph, applications whose device memory is owned by another pool,
- * or real-time loops that may not block on an allocator.  Its scratch is one
- * fixed array of SPARC_NOALLOC_SCRATCH_BYTES in the library image, present
- * on every GPU that loads the library until the process exits.
+ * cannot allocate device memory at the point of the call, such as applications
+ * whose device memory is owned by another allocator or pool (a framework's
+ * caching allocator, a fixed memory budget that must not be exceeded), or
+ * latency-bound loops that may not block on cudaMalloc, which can synchronise
+ * the device.  Its scratch is one fixed array of SPARC_NOALLOC_SCRATCH_BYTES in
+ * the library image, present on every GPU that loads the library until the
+ * process exits.
  *   - Limit: 2 * ceil(ns/8)*8*Nd + max(nproj,1)*ceil(ns/8)*8 elements of
  *     `dtype` (each part rounded up to 256 bytes) must fit in the array;
  *     larger problems are rejected with SPARC_ERR_INVALID_ARG and a message.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     (cudaGetSymbolAddress) with that device current and keeps it for the
+ *     life of the process; make that first call before any stream capture.
+ *     The kept address is stale after cudaDeviceReset on that device, so the
+ *     entry point may not be used after such a reset.
  *   - The projector values of H in `dtype` must already be on the device
  *     (any call of sparc_apply_H with that dtype and H uploads them);
  *     otherwise SPARC_ERR_INVALID_ARG.

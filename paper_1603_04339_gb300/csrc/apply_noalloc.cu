@@ -1,10 +1,10 @@
 // sparc_apply_H_noalloc: Y = H X with no device allocation in the call.
 //
-// Some callers cannot call cudaMalloc at the point where they need H X: code
-// that is being captured into a CUDA graph (allocation is not a capturable
-// operation), applications whose device memory is owned by another allocator
-// or pool that must not be bypassed, and real-time loops that may not block
-// on the driver's allocator.  sparc_apply_H grows the context workspace on
+// Some callers cannot call cudaMalloc at the point where they need H X:
+// applications whose device memory is owned by another allocator or pool that
+// must not be bypassed (a framework's caching allocator, a fixed memory budget),
+// and latency-bound loops that may not block on the driver's allocator, which
+// can synchronise the device.  sparc_apply_H grows the context workspace on
 // demand; this variant instead works in a fixed scratch array that lives in
 // the library image itself (a file-scope __device__ array), so the only
 // memory it touches is the caller's X and Y, the Hamiltonian's own arrays and
@@ -33,6 +33,7 @@ void* g_scratch_dev[kMaxDevices] = {};  // device address of g_noalloc_scratch, 
 // Device address of the scratch array on `device` (which must be current).
 // cudaGetSymbolAddress runs once per device, on the first call there; in host
 // code the array's name is only a host-side stand-in, so kernels get this address.
+// The address is kept for the life of the process (stale after cudaDeviceReset).
 cudaError_t scratch_address(int device, void** out) {
   std::lock_guard<std::mutex> lock(g_mu);
   if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;

@@ -327,8 +327,8 @@ def sparc_apply_H(H: Hamiltonian, X, Y, ns=None, ld=None, stream=None, dtype=Non
 def sparc_apply_H_noalloc(H: Hamiltonian, X, Y, ns=None, ld=None, stream=None, dtype=None):
     """Y = H X in the library's fixed scratch array: the call allocates no device memory.
 
-    For callers that cannot allocate when they need H X (graph capture, foreign
-    memory pools, real-time loops).  Needs the projector values of H in this
+    For callers that cannot allocate when they need H X (device memory owned by
+    another allocator or a fixed budget, loops that may not block on cudaMalloc).  Needs the projector values of H in this
     dtype on the device already (one sparc_apply_H call with the dtype uploads
     them); calls that overlap on the GPU share the scratch and race.
     """

@@ -1,6 +1,7 @@
 """Pins of the SCF oracle (oracle/scf_oracle.py) to facts outside itself: closed forms,
 limits, exact solutions of the discrete problems and a jellium fixed point."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -348,3 +349,79 @@ def test_kpoint_iteration_reduces_to_gamma_for_repeated_kpoints():
     assert abs(two["F"] - one["F"]) < 1e-11 * abs(one["F"])
     dv = wl.h[0] * wl.h[1] * wl.h[2]
     assert abs(dv * two["rho"].sum() - sysd.nelec) < 1e-9
+
+
+def _golden_pw92():
+    path = os.path.join(os.path.dirname(__file__), "golden", "pw92_correlation_expansions.txt")
+    out = {}
+    for line in open(path):
+        line = line.split("#")[0].split()
+        if line:
+            out[line[0]] = (float(line[1]), float(line[2]))
+    return out
+
+
+def _pw92_expansion_from_parameters():
+    """The high- and low-density coefficients implied by the oracle's six PW92
+    parameters (series of G(rs) at rs -> 0 and rs -> infinity)."""
+    A, a1, b1, b2, b3, b4 = S.PW92
+    l = math.log(2.0 * A * b1)
+    return {"c0": A, "c1": -2.0 * A * l, "c2": A * a1,
+            "c3": -2.0 * A * a1 * l + 8.0 * A ** 3 * b1 ** 2 - 2.0 * A * b3 / b1,
+            "d0": a1 / b4, "d1": a1 * b3 / b4 ** 2, "beta2": 2.0 * A * b1 ** 2}
+
+
+def test_pw92_parameters_reproduce_the_published_expansion_coefficients():
+    """Every one of A, alpha1, beta1..beta4 is tied to a coefficient of Perdew and
+    Wang's Table I (tests/golden): a typo or a swap of any parameter moves at
+    least one of c1 (beta1), beta2 = 2 A beta1^2, c2 (alpha1), c3 (beta3), d0 (beta4)
+    or d1 far outside its tolerance."""
+    gold = _golden_pw92()
+    got = _pw92_expansion_from_parameters()
+    for name, (val, tol) in gold.items():
+        assert abs(got[name] - val) < tol, (name, got[name], val)
+    assert abs(S.PW92[3] - got["beta2"]) < 1e-4
+    # a planted swap or typo is caught: each single change breaks a coefficient
+    base = list(S.PW92)
+    for i in range(6):
+        for bad in (base[i] * 1.01, base[(i + 1) % 6]):
+            trial = base.copy()
+            trial[i] = bad
+            saved = S.PW92
+            try:
+                S.PW92 = tuple(trial)
+                g2 = _pw92_expansion_from_parameters()
+            finally:
+                S.PW92 = saved
+            off = [abs(g2[n] - v) > t for n, (v, t) in gold.items()]
+            off.append(abs(trial[3] - g2["beta2"]) > 1e-4)
+            assert any(off), (i, bad)
+
+
+def test_pw92_correlation_has_the_published_asymptotic_series():
+    """The oracle's eps_c (eps_xc minus Slater exchange) follows the high-density
+    series c0 ln rs - c1 + c2 rs ln rs - c3 rs and the low-density series
+    -d0/rs + d1/rs^1.5, with the coefficients implied by its parameters (which the
+    previous test ties to Perdew and Wang's table): this pins the interpolation
+    formula itself.  rs stays >= 1e-4 so that subtracting the exchange energy
+    (which grows as 1/rs) keeps the rs terms above FP64 rounding."""
+    c = _pw92_expansion_from_parameters()
+
+    def ec(rs):
+        rs = np.asarray(rs, dtype=np.float64)
+        rho = 3.0 / (4.0 * math.pi * rs ** 3)
+        eps, _ = S.lda(rho)
+        ex = -(3.0 / (4.0 * math.pi)) * (9.0 * math.pi / 4.0) ** (1.0 / 3.0) / rs
+        return eps - ex
+
+    for rs in (1e-4, 3e-4):
+        g = ec(rs) - (c["c0"] * math.log(rs) - c["c1"])            # the rs-order terms
+        t = c["c2"] * rs * math.log(rs) - c["c3"] * rs
+        assert abs(g - t) < 1e-3 * abs(t), (rs, g, t)
+        # the c3 term alone is resolved (it is 1/7 of the rs-order terms here)
+        assert abs((g - c["c2"] * rs * math.log(rs)) / (-c["c3"] * rs) - 1.0) < 1e-2
+    for rs in (1e7, 1e8, 1e9):
+        e = float(ec(rs))
+        # remainder of the two-term series is O(1/rs^2) (coefficient about -3.7)
+        assert abs(e * rs + c["d0"] - c["d1"] / math.sqrt(rs)) < 5.0 / rs, (rs, e)
+        assert abs((e + c["d0"] / rs) * rs ** 1.5 - c["d1"]) < 5.0 / math.sqrt(rs), (rs, e)
