@@ -323,6 +323,36 @@ def cell_batch_throughput(sparc, synth, torch, ctx, reps=3, nbranch=8):
                          "launches_per_batch": l_s}}
 
 
+def fp64_filter_throughput(sparc, synth, torch, ctx, H, wl, X32, reps=2):
+    """The FP64 arm of the benchmark cell: the same Chebyshev filter (64^3, Ns=512,
+    m=24, bounds as in the step) on the FP64 path (generic FP64 pass and
+    projection), timed with CUDA events after a warm-up filter, beside the FP32
+    filter's figure of the same call."""
+    X = X32.to(torch.float64)
+    Y = torch.empty_like(X)
+    v0 = torch.from_numpy(synth.lanczos_start(wl.nd, 2003)).cuda()
+    a0, b = sparc.sparc_lanczos_bounds(H, 10, v0)
+    a = a0 + (b - a0) * (wl.ns / wl.nd) ** (2.0 / 3.0)
+    Y32 = torch.empty_like(X32)
+    out = {}
+    for name, (Xi, Yi) in (("fp64", (X, Y)), ("fp32", (X32, Y32))):
+        sparc.sparc_cheb_filter(H, wl.m, a, b, a0, Xi, Yi)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            sparc.sparc_cheb_filter(H, wl.m, a, b, a0, Xi, Yi)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"value": wl.nd * wl.ns * wl.m / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_filter": ms}
+    out["fp32_over_fp64"] = out["fp64"]["ms_per_filter"] / out["fp32"]["ms_per_filter"]
+    out["workload"] = WORKLOAD + ", the filter alone (one call, all 64 blocks of 8 orbitals)"
+    del X, Y, Y32
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_kpoints(args):
     import json as _json
     import torch
@@ -597,6 +627,7 @@ def run_ours(args):
                                   "jacobi_sweeps": sweeps},
         "filter_only": {"value": units / ((fp_ms + ga_ms) / args.steps * 1e-3) / 1e9, "unit": UNIT},
         "clocks": ck, "e2e": e2e, "gpu_launches": int(launches), "cpu_baseline": cpu,
+        "filter_fp64_vs_fp32": None if world > 1 else fp64_filter_throughput(sparc, synth, torch, ctx, H, wl, X),
         "scf": None if (args.no_scf or world > 1) else scf_time_to_solution(sparc, synth, torch),
         "kpoints": None if (args.no_kpoints or world > 1) else kpoint_filter_throughput(sparc, synth, torch, ctx),
         "cells": None if (args.no_kpoints or world > 1) else cell_batch_throughput(sparc, synth, torch, ctx),

@@ -12,7 +12,7 @@ CSRC = os.path.join(PKG, "csrc")
 OBJ = os.path.join(ROOT, "_build", "obj")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libsparc.so")
-SOURCES = ["hpass.cu", "hpass_fast.cu", "sparc_api.cu", "lanczos.cu", "rr.cu", "tc_gemm.cu", "scf.cu", "apply_noalloc.cu", "graph.cu", "mlp.cu"]
+SOURCES = ["hpass.cu", "hpass_fast.cu", "hpass_tma.cu", "sparc_api.cu", "lanczos.cu", "rr.cu", "tc_gemm.cu", "scf.cu", "apply_noalloc.cu", "graph.cu", "mlp.cu"]
 HEADERS = ["common.cuh", "ham.cuh", "rr.cuh", "fast.cuh", "ptx.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing",

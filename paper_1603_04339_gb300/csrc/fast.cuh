@@ -1,6 +1,9 @@
 // Tables and launchers of the tiled FP32 / complex64 H-pass (hpass_fast.cu).
 #pragma once
 
+#include <array>
+#include <vector>
+
 #include "ham.cuh"
 
 namespace sparc {
@@ -50,7 +53,40 @@ struct Layout {
   int* d_sslots = nullptr;    // CTA-local indices of the pieces touching those nodes at z
 };
 
+// Tables of the TMA-fed FP32 pass (hpass_tma.cu): per CTA (16 x 16 tile, z-chunk) the
+// projector groups (atom boxes) that meet it, and per (CTA, plane) a record of the
+// A fragments of the projector term for each of its 16 warps.
+constexpr int TMA_MAXG = 48;                 // projector groups per CTA, at most
+constexpr unsigned TMA_REC_MAX = 36864;      // bytes of one plane's record, at most
+constexpr int TMA_MAXTY = 16;                // tile rows (n2 <= 256)
+constexpr int TMA_MAXSEG = 4;                // y segments of one halo frame
+constexpr int TMA_NMAPS = 8;                 // distinct segment heights
+struct TmaTables {
+  bool ok = false;            // built: the grid and projectors fit the kernel's limits
+  int zl = 0, nchunk = 0, tiles_x = 0, tiles_y = 0;
+  int max_rec = 0;
+  // The halo frame of tile row ty, rows y = 16 ty - 6 .. 16 ty + 21 wrapped into [0, n2),
+  // as up to TMA_MAXSEG runs of consecutive y: run j starts at y = yseg[ty][j][0], lands
+  // at frame row yseg[ty][j][1] and has the height map_h[yseg[ty][j][2]] (-1: no run).
+  int nmaps = 0;
+  int map_h[TMA_NMAPS] = {};
+  int yseg[TMA_MAXTY][TMA_MAXSEG][3] = {};
+  int* d_cproj = nullptr;     // [cta][TMA_MAXG][4] projector index of (group slot, s/px/py/pz), -1 if none
+  int* d_cng = nullptr;       // [cta] groups of the CTA
+  int* d_rec = nullptr;       // [cta * zl + k] record offsets in 16-byte units (+ one end entry)
+  void* d_stream = nullptr;   // the records
+  size_t stream_bytes = 0;
+};
+
+// The same tables on the host, before upload.
+struct TmaHost {
+  TmaTables dims;                 // zl, nchunk, tiles, max_rec (no device pointers)
+  std::vector<int> cproj, cng, rec;
+  std::vector<uint32_t> words;    // the records
+};
+
 struct Tables {
+  TmaTables tma;
   int ngrp = 0, nsb = 0;
   Group* d_grp = nullptr;
   SubBox* d_sb = nullptr;
@@ -86,10 +122,36 @@ unsigned long long geometry_hash(const sparc_ham* H);
 // Host: build the tables from the projector boxes (called by sparc_ham_create).
 sparc_status build_tables(sparc_ham* H, const sparc_nonlocal* nl);
 void free_tables(Tables& t);
+// Host: the TMA pass tables from the projector groups, their boxes (lo[3], n[3]) and
+// box values chi4 ([box node][4]); leaves T->tma.ok false where the kernel does not apply.
+sparc_status build_tma_tables(sparc_ham* H, Tables* T, const std::vector<Group>& grps,
+                              const std::vector<std::array<int, 6>>& gbox, const std::vector<float>& chi4);
+void free_tma_tables(TmaTables& M);
+bool tma_frame_segments(int n2, TmaTables& M);
+bool tma_host_tables(const int n[3], const std::vector<Group>& grps, const std::vector<std::array<int, 6>>& gbox,
+                     const std::vector<float>& chi4, TmaHost& out);
+// Whether the TMA-fed FP32 pass applies to H (Gamma point, radius 6, n1 % 4 == 0, limits).
+bool tma_usable(const sparc_ham* H);
+// The TMA pass works on an x-padded block layout: every (y, z) row holds R ghost nodes
+// on each side, copies of the other end of the row (periodic wrap):
+//   B[blk][z][y][x'][NB], x' = x + R in [0, n1 + 2R); x' < R holds x = n1 - R + x',
+//   x' >= n1 + R holds x = x' - n1 - R.
+long long padded_nd(const sparc_ham* H);
+cudaError_t launch_to_blocks_px(const sparc_ham* H, const float* X, long long ld, int ns, float* B, int nblk,
+                                cudaStream_t st);
+cudaError_t launch_from_blocks_px(const sparc_ham* H, const float* B, int nblk, float* X, long long ld, int ns,
+                                  cudaStream_t st);
+// The TMA-fed FP32 pass: Yout = alpha (H - shift) Yin + beta Yprev for blocks [blk0, blk0 + nb)
+// of x-padded buffers (Yout's ghost nodes are written too).
+cudaError_t launch_pass_tma(const sparc_ham* H, const float* Yin, const float* Yprev, float* Yout, const float* gc,
+                            int nblk_total, int blk0, int nb, double alpha, double shift, double beta,
+                            cudaStream_t st);
 
 // FP32 pass tile shapes: 0 = 16 x 16 nodes, 512 threads, one CTA per SM;
-// 1 = 16 x 8 nodes, 256 threads, two CTAs per SM.
-constexpr int NSHAPE_F32 = 2;
+// 1 = 16 x 8 nodes, 256 threads, two CTAs per SM; 2 = the TMA-fed pass (16 x 16
+// tiles, z-chunks, one producer and 16 consumer warps), the default where it applies.
+constexpr int NSHAPE_F32 = 3;
+constexpr int SHAPE_TMA = 2;
 // launch_pass<float> shape for a plain H-apply: 16 x 16 tiles, stencil in difference form
 constexpr int SHAPE_DIFF = 16;
 bool shape_usable(const sparc_ham* H, int shape);
@@ -102,9 +164,10 @@ int items_per_block(const sparc_ham* H, int shape = 0);
 // gc[p][blk][lane] for the blocks [blk0, blk0 + nb) (gamma_p h^3 chi~_p^H Y);
 // `scratch` holds gather_scratch_bytes(H, nb, sizeof(T)) bytes of per-slab partial sums.
 size_t gather_scratch_bytes(const sparc_ham* H, int nb, size_t esize);
+// padded (FP32 only): Y is in the x-padded layout of the TMA pass.
 template <class T>
 cudaError_t launch_gather(const sparc_ham* H, const T* Y, int nblk_total, int blk0, int nb, T* gc,
-                          T* scratch, cudaStream_t st);
+                          T* scratch, cudaStream_t st, bool padded = false);
 // Yout = alpha (H - shift) Yin + beta Yprev for blocks [blk0, blk0 + nb).
 template <class T>
 cudaError_t launch_pass(const sparc_ham* H, const T* Yin, const T* Yprev, T* Yout, const T* gc,

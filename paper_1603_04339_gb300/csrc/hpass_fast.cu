@@ -31,6 +31,7 @@ namespace fast {
 // --------------------------------------------------------------------------- host tables
 
 void free_tables(Tables& t) {
+  free_tma_tables(t.tma);
   void* ps[] = {t.d_grp, t.d_sb, t.d_chi4};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -229,7 +230,7 @@ sparc_status build_tables(sparc_ham* H, const sparc_nonlocal* nl) {
     cudaGetLastError();
     return fail(ctx, SPARC_ERR_OOM, "projector table allocation failed");
   }
-  return SPARC_OK;
+  return build_tma_tables(H, T, grps, gbox, chi4);
 }
 
 unsigned long long geometry_hash(const sparc_ham* H) {
@@ -251,6 +252,7 @@ void kslot(const sparc_ham* H, KSlot& s) {
 bool shape_usable(const sparc_ham* H, int shape) {
   const Tables* T = (const Tables*)H->fast;
   if (!usable(H) || shape < 0 || shape >= NSHAPE_F32) return false;
+  if (shape == SHAPE_TMA) return tma_usable(H);
   return shape == 0 || (T->lay[2].max_items <= MAXI && T->lay[2].max_steps <= MAXSTEP);
 }
 
@@ -1082,9 +1084,11 @@ __device__ __forceinline__ void gather_row_f2(float2 (&s)[NB2][4], const float4*
   }
 }
 
+// rowp, xoff: row length and x offset of the block buffer (n1 and 0, or n1 + 12 and 6
+// for the x-padded layout of the TMA pass); nd: nodes per block of that layout.
 template <int NB2>
 __global__ void __launch_bounds__(256, 2)
-k_gather_rows_f2(const float* __restrict__ Y, long long nd, int n1, int n2, const Group* __restrict__ grp,
+k_gather_rows_f2(const float* __restrict__ Y, long long nd, int rowp, int xoff, int n2, const Group* __restrict__ grp,
                  const SubBox* __restrict__ sbs, const float4* __restrict__ chi4, float* __restrict__ part,
                  int blk0, int nb, int nslab) {
   constexpr int NBM = 2 * NB2;
@@ -1109,7 +1113,7 @@ k_gather_rows_f2(const float* __restrict__ Y, long long nd, int n1, int n2, cons
     const int first = (sl - rbase % nslab + nslab) % nslab;
     for (int row = first + warp * nslab; row < rows; row += 8 * nslab) {
       const int iy = row % wy, iz = row / wy;
-      const long long yrow = ((long long)(sb.gz0 + iz) * n2 + (sb.gy0 + iy)) * n1 + sb.gx0;
+      const long long yrow = ((long long)(sb.gz0 + iz) * n2 + (sb.gy0 + iy)) * rowp + sb.gx0 + xoff;
       const long long crow =
           sb.chi4_off + sb.bx0 + (long long)sb.nbx * ((sb.by0 + iy) + (long long)sb.nby * (sb.bz0 + iz));
       // real data: k = 0, every phase is 1; accumulate in place
@@ -1241,7 +1245,7 @@ cudaError_t launch_gather_k(const sparc_ham* H0, const cf32* Y, long long nunit_
 
 template <class T>
 cudaError_t launch_gather(const sparc_ham* H, const T* Y, int nblk_total, int blk0, int nb, T* gc,
-                          T* scratch, cudaStream_t st) {
+                          T* scratch, cudaStream_t st, bool padded) {
   const Tables* Tb = (const Tables*)H->fast;
   if (H->nproj == 0 || Tb->ngrp == 0) return cudaSuccess;
   if constexpr (FT<T>::cplx) {
@@ -1259,9 +1263,11 @@ cudaError_t launch_gather(const sparc_ham* H, const T* Y, int nblk_total, int bl
     // pairs of blocks per CTA: as many as the group has, at most 4 pairs
     const int nb2 = std::min(4, (nb + 1) / 2);
     const dim3 grid((unsigned)Tb->ngrp, (unsigned)nslab, (unsigned)ceil_div(nb, 2 * nb2));
+    const int rowp = padded ? H->gd.n1 + 2 * R : H->gd.n1;
+    const long long ndl = (long long)rowp * H->gd.n2 * H->gd.n3;
     auto go = [&](auto kern) {
-      kern<<<grid, 256, 0, st>>>(Y, H->gd.nd, H->gd.n1, H->gd.n2, Tb->d_grp, Tb->d_sb, (const float4*)Tb->d_chi4,
-                                 scratch, blk0, nb, nslab);
+      kern<<<grid, 256, 0, st>>>(Y, ndl, rowp, padded ? R : 0, H->gd.n2, Tb->d_grp, Tb->d_sb,
+                                 (const float4*)Tb->d_chi4, scratch, blk0, nb, nslab);
     };
     switch (nb2) {
       case 1: go(k_gather_rows_f2<1>); break;
@@ -1391,8 +1397,10 @@ int items_per_block(const sparc_ham* H, int shape) {
 template int items_per_block<float>(const sparc_ham*, int);
 template int items_per_block<cf32>(const sparc_ham*, int);
 
-template cudaError_t launch_gather<float>(const sparc_ham*, const float*, int, int, int, float*, float*, cudaStream_t);
-template cudaError_t launch_gather<cf32>(const sparc_ham*, const cf32*, int, int, int, cf32*, cf32*, cudaStream_t);
+template cudaError_t launch_gather<float>(const sparc_ham*, const float*, int, int, int, float*, float*, cudaStream_t,
+                                          bool);
+template cudaError_t launch_gather<cf32>(const sparc_ham*, const cf32*, int, int, int, cf32*, cf32*, cudaStream_t,
+                                         bool);
 template cudaError_t launch_pass<float>(const sparc_ham*, const float*, const float*, float*, const float*,
                                         int, int, int, double, double, double, cudaStream_t, int);
 template cudaError_t launch_pass<cf32>(const sparc_ham*, const cf32*, const cf32*, cf32*, const cf32*,

@@ -1,0 +1,781 @@
+// FP32 H-pass of the Chebyshev filter, fed by the tensor memory accelerator (TMA).
+//
+// One launch applies one filter degree (the three-term recurrence of Eq. ChebFilter)
+//     Yout = alpha (H - shift) Yin + beta Yprev
+// to the blocks [blk0, blk0 + nb) of the interleaved layout B[blk][z][y][x'][8 orbitals],
+// x-padded: each (y, z) row carries R ghost nodes at either end that repeat the other
+// end of the row, so that an x-halo never wraps (the pass writes them with the row),
+// with H = -1/2 lap_h (twelfth-order FD Laplacian, Eq. FD:Laplacian, weights
+// Eq. weightsLap) + V_eff + the Kleinman-Bylander projector term of Eq. NonlocalPS:FD,
+// at the Gamma point (real orbitals, periodic wrap).  Yprev may be null (first degree)
+// or alias Yout (the recurrence runs in place).
+//
+// Work: persistent CTAs loop over items = (16 x 16 (x, y) tile, z-chunk of up to 32
+// planes, block).  The item's planes z' = zs-6 .. ze+5 pass through a ring of three
+// shared-memory stages:
+//   * the last warp, before each of its steps, fills the stage two steps ahead (the
+//     producer role): for a plane of the chunk, the tile with its 6-node halo (28 x 28
+//     nodes: one cp.async.bulk.tensor box, split along y into up to three boxes where
+//     the rows wrap around the periodic y faces; the x wrap is in the ghost nodes),
+//     the tile's V_eff (tensor box), the projector
+//     fragment record of the plane (bulk copy) and, for the output plane z'-6, the
+//     tile's Yprev (tensor box); for the six planes on either side of the chunk only
+//     the tile's own 16 x 16 nodes (tensor box).  Completion is counted in bytes on
+//     the stage's "full" mbarrier; the consumers release a stage on its "empty" one.
+//   * all 16 warps consume: each thread owns the nodes (x, y) and (x, y+1) of the tile
+//     and one orbital pair (a float2).  The z part of the stencil is a scatter: plane
+//     z' adds c_|d| f(z') to the accumulators of the outputs z'+d, d = -6..6, kept
+//     in a ring of 13 registers that the unrolled step loop renames; the x and y
+//     parts, (c_0 + V - shift) f and the projector term go to the output z' itself;
+//     the output z'-6 is then complete and is written as alpha acc + beta Yprev.
+//   * the projector term sum_p chi_p(node) gc_p(orbital) runs on mma.sync m16n8k8
+//     TF32 products (3xTF32: about FP32 accuracy).  The host precomputes for every
+//     warp and plane the A fragments (chi of two projector groups of one atom box
+//     each at the warp's 16 nodes, zero outside the boxes), so the kernel does no
+//     index or bounds arithmetic for them; B (gc = gamma h^3 chi^T Y, split into TF32
+//     high and low parts) is staged in shared memory per item.
+// Every mbarrier wait is bounded: one that runs out latches STATUS_TIMEOUT in the
+// device status word and the kernel goes on, so it cannot hang.
+#include <cuda.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "fast.cuh"
+#include "ptx.cuh"
+
+namespace sparc {
+namespace fast {
+namespace tma {
+
+constexpr int MAXG = TMA_MAXG;
+constexpr uint32_t REC_MAX = TMA_REC_MAX;
+constexpr int TT = 16;                   // tile edge in x and y
+constexpr int FR = TT + 2 * R;           // 28: tile plus halo
+constexpr int ZLMAX = 32;                // output planes per z-chunk, at most
+constexpr int NBUF = 3;                  // stages in the ring
+constexpr int NCW = 16;                  // warps; the last one also produces
+constexpr int NTHR = NCW * 32;
+constexpr int DIST = 2;                  // steps the producer runs ahead (< NBUF)
+constexpr uint32_t FRAME_B = FR * FR * NB * 4;   // 25088
+constexpr uint32_t TILE_B = TT * TT * NB * 4;    // 8192
+constexpr uint32_t V_B = TT * TT * 4;            // 1024
+constexpr uint32_t OFF_YP = FRAME_B;
+constexpr uint32_t OFF_V = OFF_YP + TILE_B;
+constexpr uint32_t OFF_REC = OFF_V + V_B;        // 34304
+constexpr uint32_t STAGE_B = OFF_REC + REC_MAX;
+constexpr uint32_t OFF_GCS = NBUF * STAGE_B;
+constexpr uint32_t GCS_B = (MAXG + 1) * 32 * 8;
+constexpr uint32_t OFF_RECS = OFF_GCS + GCS_B;   // record offsets of two items: int[2][ZLMAX + 1]
+constexpr uint32_t OFF_BAR = OFF_RECS + 2 * (ZLMAX + 1) * 4 + 8;
+constexpr uint32_t SMEM_B = OFF_BAR + 2 * NBUF * 8;
+static_assert(OFF_BAR % 8 == 0, "mbarrier alignment");
+static_assert(STAGE_B % 128 == 0 && OFF_REC % 128 == 0 && OFF_YP % 128 == 0, "stage alignment");
+static_assert(SMEM_B <= 232448, "shared memory of one CTA");
+
+// --------------------------------------------------------------------------- host tables
+
+static int cover(int c, int lo, int nb, int n) {   // box-local index of coordinate c, or -1
+  int u = (c - lo) % n;
+  if (u < 0) u += n;
+  return u < nb ? u : -1;
+}
+
+}  // namespace tma
+
+// The tables on the host: false where the grid or the projectors exceed the kernel's
+// limits (groups per CTA, record size).
+bool tma_host_tables(const int n[3], const std::vector<Group>& grps, const std::vector<std::array<int, 6>>& gbox,
+                     const std::vector<float>& chi4, TmaHost& out) {
+  using namespace tma;
+  TmaTables& M = out.dims;
+  std::vector<int>& cproj = out.cproj;
+  std::vector<int>& cng = out.cng;
+  std::vector<int>& rec = out.rec;
+  std::vector<uint32_t>& words = out.words;
+  M.nchunk = ceil_div(n[2], ZLMAX);
+  M.zl = ceil_div(n[2], M.nchunk);
+  M.tiles_x = ceil_div(n[0], TT);
+  M.tiles_y = ceil_div(n[1], TT);
+  const int ncta = M.tiles_x * M.tiles_y * M.nchunk;
+  const int ngrp = (int)grps.size();
+  std::vector<long long> off4(ngrp);
+  {
+    long long o = 0;
+    for (int g = 0; g < ngrp; ++g) {
+      off4[g] = o;
+      o += (long long)gbox[g][3] * gbox[g][4] * gbox[g][5];
+    }
+  }
+  cproj.assign((size_t)ncta * MAXG * 4, -1);
+  cng.assign(ncta, 0);
+  rec.assign((size_t)ncta * M.zl + 1, 0);
+  words.clear();
+  words.reserve(1 << 20);
+  int max_rec = 0;
+  for (int cta = 0; cta < ncta; ++cta) {
+    const int tile = cta / M.nchunk, chunk = cta % M.nchunk;
+    const int x0 = (tile % M.tiles_x) * TT, y0 = (tile / M.tiles_x) * TT;
+    const int zs = chunk * M.zl, nz = std::min(M.zl, n[2] - zs);
+    const int xe = std::min(n[0], x0 + TT), ye = std::min(n[1], y0 + TT);
+    // the atom boxes (projector groups) that meet the tile over the chunk's planes
+    std::vector<int> loc;
+    std::vector<std::array<int, TT>> ux, uy;
+    std::vector<std::vector<int>> uz;
+    for (int G = 0; G < ngrp; ++G) {
+      std::array<int, TT> cx, cy;
+      bool hx = false, hy = false, hz = false;
+      for (int i = 0; i < TT; ++i) {
+        cx[i] = (x0 + i < xe) ? cover(x0 + i, gbox[G][0], gbox[G][3], n[0]) : -1;
+        cy[i] = (y0 + i < ye) ? cover(y0 + i, gbox[G][1], gbox[G][4], n[1]) : -1;
+        hx |= cx[i] >= 0;
+        hy |= cy[i] >= 0;
+      }
+      std::vector<int> cz(nz);
+      for (int k = 0; k < nz; ++k) {
+        cz[k] = cover(zs + k, gbox[G][2], gbox[G][5], n[2]);
+        hz |= cz[k] >= 0;
+      }
+      if (!(hx && hy && hz)) continue;
+      loc.push_back(G);
+      ux.push_back(cx);
+      uy.push_back(cy);
+      uz.push_back(cz);
+    }
+    if ((int)loc.size() > MAXG) return false;   // too many boxes per tile: the other kernels run
+    cng[cta] = (int)loc.size();
+    for (size_t g = 0; g < loc.size(); ++g)
+      for (int l = 0; l < 4; ++l) cproj[((size_t)cta * MAXG + g) * 4 + l] = grps[loc[g]].proj[l];
+    for (int k = 0; k < M.zl; ++k) {
+      rec[(size_t)cta * M.zl + k] = (int)(words.size() / 4);
+      if (k >= nz) continue;
+      // per warp: the local boxes active at its 16 nodes, in pairs (one mma round each)
+      std::vector<int> hdr(32, 0), ids;
+      std::vector<std::vector<int>> act(NCW);
+      for (int w = 0; w < NCW; ++w) {
+        const int xa = 8 * (w & 1), ya = 2 * (w >> 1);
+        for (size_t g = 0; g < loc.size(); ++g) {
+          if (uz[g][k] < 0) continue;
+          if (uy[g][ya] < 0 && uy[g][ya + 1] < 0) continue;
+          bool hx = false;
+          for (int i = 0; i < 8; ++i) hx |= ux[g][xa + i] >= 0;
+          if (hx) act[w].push_back((int)g);
+        }
+        hdr[w] = (int)ids.size();
+        for (size_t j = 0; j < act[w].size(); j += 2) {
+          const int g0 = act[w][j], g1 = (j + 1 < act[w].size()) ? act[w][j + 1] : MAXG;
+          ids.push_back(g0 | (g1 << 16));
+        }
+      }
+      const int nr = (int)ids.size();
+      hdr[NCW] = nr;
+      const int nid = (nr + 3) & ~3;
+      const int bytes = 128 + 4 * nid + 512 * nr;
+      max_rec = std::max(max_rec, bytes);
+      if (bytes > (int)REC_MAX) return false;   // record too large for a stage
+      for (int v : hdr) words.push_back((uint32_t)v);
+      for (int j = 0; j < nid; ++j) words.push_back(j < nr ? (uint32_t)ids[j] : 0u);
+      for (int w = 0; w < NCW; ++w) {
+        const int xa = 8 * (w & 1), ya = 2 * (w >> 1);
+        for (size_t j = 0; j < act[w].size(); j += 2) {
+          const int gg[2] = {act[w][j], (j + 1 < act[w].size()) ? act[w][j + 1] : -1};
+          for (int lane = 0; lane < 32; ++lane) {
+            const int gq = lane >> 2, cq = lane & 3;
+            float v[4] = {0.f, 0.f, 0.f, 0.f};   // (g0, node A), (g0, node B), (g1, A), (g1, B)
+            for (int h = 0; h < 2; ++h) {
+              const int g = gg[h];
+              if (g < 0) continue;
+              const int G = loc[g];
+              const int bx = ux[g][xa + gq];
+              const int bz = uz[g][k];
+              for (int r = 0; r < 2; ++r) {
+                const int by = uy[g][ya + r];
+                if (bx < 0 || by < 0 || bz < 0) continue;
+                const long long e = off4[G] + bx + (long long)gbox[G][3] * (by + (long long)gbox[G][4] * bz);
+                v[2 * h + r] = chi4[(size_t)e * 4 + cq];
+              }
+            }
+            for (int c = 0; c < 4; ++c) {
+              uint32_t u;
+              std::memcpy(&u, &v[c], 4);
+              words.push_back(u);
+            }
+          }
+        }
+      }
+    }
+  }
+  rec[(size_t)ncta * M.zl] = (int)(words.size() / 4);
+  if (words.size() / 4 >= (size_t)INT32_MAX) return false;
+  M.max_rec = max_rec;
+  return true;
+}
+
+// The y runs of every tile row's halo frame and the distinct run heights (one tensor
+// map each); false if the grid needs more than the kernel's limits.
+bool tma_frame_segments(int n2, TmaTables& M) {
+  using namespace tma;
+  if (M.tiles_y > TMA_MAXTY) return false;
+  M.nmaps = 0;
+  for (int ty = 0; ty < M.tiles_y; ++ty) {
+    for (int j = 0; j < TMA_MAXSEG; ++j) M.yseg[ty][j][0] = M.yseg[ty][j][1] = M.yseg[ty][j][2] = -1;
+    int r = 0, j = 0;
+    while (r < FR) {
+      if (j == TMA_MAXSEG) return false;
+      int y = (ty * TT - R + r) % n2;
+      if (y < 0) y += n2;
+      const int hgt = std::min(FR - r, n2 - y);
+      int mi = 0;
+      while (mi < M.nmaps && M.map_h[mi] != hgt) ++mi;
+      if (mi == M.nmaps) {
+        if (M.nmaps == TMA_NMAPS) return false;
+        M.map_h[M.nmaps++] = hgt;
+      }
+      M.yseg[ty][j][0] = y;
+      M.yseg[ty][j][1] = r;
+      M.yseg[ty][j][2] = mi;
+      r += hgt;
+      ++j;
+    }
+  }
+  return true;
+}
+
+sparc_status build_tma_tables(sparc_ham* H, Tables* T, const std::vector<Group>& grps,
+                              const std::vector<std::array<int, 6>>& gbox, const std::vector<float>& chi4) {
+  using namespace tma;
+  TmaTables& M = T->tma;
+  M = TmaTables();
+  const int n[3] = {H->gd.n1, H->gd.n2, H->gd.n3};
+  if (H->gd.cplx || H->gd.no != R || n[0] % 4 != 0) return SPARC_OK;   // not this kernel's case
+  TmaHost h;
+  if (!tma_host_tables(n, grps, gbox, chi4, h)) return SPARC_OK;
+  if (!tma_frame_segments(n[1], h.dims)) return SPARC_OK;
+  M = h.dims;
+  const std::vector<int>& cproj = h.cproj;
+  const std::vector<int>& cng = h.cng;
+  const std::vector<int>& rec = h.rec;
+  const std::vector<uint32_t>& words = h.words;
+  auto up = [&](void** d, const void* h, size_t bytes) -> bool {
+    if (cudaMalloc(d, std::max<size_t>(bytes, 16)) != cudaSuccess) return false;
+    return bytes == 0 || cudaMemcpy(*d, h, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+  };
+  if (!up((void**)&M.d_cproj, cproj.data(), cproj.size() * sizeof(int)) ||
+      !up((void**)&M.d_cng, cng.data(), cng.size() * sizeof(int)) ||
+      !up((void**)&M.d_rec, rec.data(), rec.size() * sizeof(int)) ||
+      !up(&M.d_stream, words.data(), words.size() * sizeof(uint32_t))) {
+    cudaGetLastError();
+    free_tma_tables(M);
+    return fail(H->ctx, SPARC_ERR_OOM, "TMA pass table allocation failed");
+  }
+  M.stream_bytes = words.size() * sizeof(uint32_t);
+  M.ok = true;
+  return SPARC_OK;
+}
+
+void free_tma_tables(TmaTables& M) {
+  void* ps[] = {M.d_cproj, M.d_cng, M.d_rec, M.d_stream};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  M = TmaTables();
+}
+
+bool tma_usable(const sparc_ham* H) {
+  const Tables* T = (const Tables*)H->fast;
+  return T != nullptr && T->tma.ok && usable(H);
+}
+
+namespace tma {
+
+// --------------------------------------------------------------------------- device code
+
+struct Args {
+  int n1, n2, n3, tiles_x, ntiles, nchunk, zl;
+  int n1p;                   // padded row length n1 + 2R
+  int blk0, nblk_total, nitems;
+  long long ndp;             // nodes per block of the padded layout
+  int yseg[TMA_MAXTY][TMA_MAXSEG][3];   // y runs of the halo frames (src y, frame row, map)
+  float2 cx2[R + 1], cy2[R + 1], cz2[R + 1];
+  float c0s;                 // sum of the centre coefficients minus the shift
+  float2 alpha2, beta2;
+  const float* yin;
+  const float* yprev;        // null on the first degree
+  float* yout;
+  const float* gc;           // [p][blk][NB]
+  const int* cproj;          // [cta][MAXG][4]
+  const int* cng;            // [cta]
+  const int* rec;            // [cta * zl + k] record offsets, 16-byte units
+  const unsigned char* stream;
+  int* status;
+};
+
+__device__ __forceinline__ void tma4(void* dst, const CUtensorMap* m, int c0, int c1, int c2, int c3, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::
+          "r"(ptx::saddr(dst)), "l"(m), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(ptx::saddr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma3(void* dst, const CUtensorMap* m, int c0, int c1, int c2, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(ptx::saddr(dst)), "l"(m), "r"(c0), "r"(c1), "r"(c2), "r"(ptx::saddr(bar))
+      : "memory");
+}
+// The tensor maps of a launch: halo-frame runs of each height, the tile of Yin and of
+// Yprev (16 x 16 nodes, padded layout) and V_eff.
+struct Maps {
+  CUtensorMap frame[TMA_NMAPS];
+  CUtensorMap tile_in, tile_prev, veff;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(ptx::saddr(b)) : "memory");
+}
+
+
+__device__ __forceinline__ float2 lds2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], float a0, float a1, float a2, float a3, float b0, float b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(__float_as_uint(a0)), "r"(__float_as_uint(a1)), "r"(__float_as_uint(a2)), "r"(__float_as_uint(a3)),
+        "r"(__float_as_uint(b0)), "r"(__float_as_uint(b1)));
+}
+
+struct Item {
+  int tile, chunk, bi, tx0, ty0, zs, nz, cta;
+};
+__device__ __forceinline__ Item decode(const Args& a, int item) {
+  Item it;
+  it.tile = item % a.ntiles;
+  const int rest = item / a.ntiles;
+  it.chunk = rest % a.nchunk;
+  it.bi = rest / a.nchunk;
+  it.tx0 = (it.tile % a.tiles_x) * TT;
+  it.ty0 = (it.tile / a.tiles_x) * TT;
+  it.zs = it.chunk * a.zl;
+  it.nz = min(a.zl, a.n3 - it.zs);
+  it.cta = it.tile * a.nchunk + it.chunk;
+  return it;
+}
+
+// The producer role: fill the stage of step (item, s) of this CTA (all 32 lanes of the
+// last warp call it).  recs: the record offsets of the item's planes (16-byte units,
+// entries 0 .. nz).  Returns false if the wait for the stage to be free ran out; once
+// a wait has run out (wait == false) no further waits are made, so that a broken
+// pipeline ends the kernel quickly instead of timing out at every step.
+__device__ __forceinline__ bool produce(const Args& a, const Maps& mp, unsigned char* smem, uint64_t* bars, int item,
+                                       int s, int g, const int* recs, bool wait) {
+  const int lane = threadIdx.x & 31;
+  const Item it = decode(a, item);
+  const int blk = a.blk0 + it.bi;
+  const int slot = g % NBUF;
+  unsigned char* st = smem + (size_t)slot * STAGE_B;
+  uint64_t* full = bars + slot;
+  uint64_t* empty = bars + NBUF + slot;
+  bool ok = true;
+  if (wait && g >= NBUF && !ptx::mbar_wait(empty, (uint32_t)((g / NBUF) - 1) & 1u)) ok = false;
+  const int p = it.zs - R + s;
+  int zw = p;
+  if (zw < 0) zw += a.n3;
+  else if (zw >= a.n3) zw -= a.n3;
+  const bool comp = s >= R && s < R + it.nz;
+  const bool yp = a.yprev != nullptr && s >= 2 * R;
+  const int k = comp ? s - R : 0;
+  const int o0 = recs[k];
+  const uint32_t rbytes = comp ? 16u * (uint32_t)(recs[k + 1] - o0) : 0u;
+  const uint32_t bytes = (comp ? FRAME_B + V_B + rbytes : TILE_B) + (yp ? TILE_B : 0u);
+  if (lane == 0) ptx::mbar_arrive_expect_tx(full, bytes);
+  __syncwarp();
+  const int zc = blk * a.n3 + zw;
+  if (comp) {
+    // halo frame: padded columns tx0 .. tx0+27 (nodes x = tx0-6 .. tx0+21), one box per y run
+    if (lane < TMA_MAXSEG) {
+      const int* sg = a.yseg[it.ty0 / TT][lane];
+      if (sg[2] >= 0) tma4(st + (size_t)sg[1] * FR * NB * 4, &mp.frame[sg[2]], 0, it.tx0, sg[0], zc, full);
+    }
+    if (lane == 29) tma3(st + OFF_V, &mp.veff, it.tx0, it.ty0, zw, full);
+    if (lane == 30) ptx::bulk_g2s(st + OFF_REC, a.stream + 16 * (size_t)o0, rbytes, full);
+  } else if (lane == 0) {
+    tma4(st, &mp.tile_in, 0, it.tx0 + R, it.ty0, zc, full);
+  }
+  if (yp && lane == 31) tma4(st + OFF_YP, &mp.tile_prev, 0, it.tx0 + R, it.ty0, blk * a.n3 + (p - R), full);
+  return ok;
+}
+
+// rec offsets of an item (entries 0 .. nz) into dst, by threads 0 .. ZLMAX
+__device__ __forceinline__ void stage_recs(const Args& a, int item, int* dst) {
+  const int t = threadIdx.x;
+  if (item < a.nitems && t <= ZLMAX) {
+    const Item it = decode(a, item);
+    if (t <= it.nz) dst[t] = __ldg(a.rec + (size_t)it.cta * a.zl + t);
+  }
+}
+
+__global__ void __launch_bounds__(NTHR, 1)
+k_pass_tma(const __grid_constant__ Maps mp, const __grid_constant__ Args a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OFF_BAR);
+  float2* gcs = reinterpret_cast<float2*>(smem + OFF_GCS);
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int b = 0; b < NBUF; ++b) {
+      ptx::mbar_init(bars + b, 1);
+      ptx::mbar_init(bars + NBUF + b, NCW);
+    }
+    ptx::mbar_init_fence();
+  }
+  int* recs = reinterpret_cast<int*>(smem + OFF_RECS);
+  stage_recs(a, blockIdx.x, recs);
+  stage_recs(a, blockIdx.x + gridDim.x, recs + (ZLMAX + 1));
+  __syncthreads();
+  const bool producer = warp == NCW - 1;
+  bool ok = true;
+  // producer cursor: the step DIST ahead of the consumers (item, step, steps of the item, local item index)
+  int pitem = blockIdx.x, ps = 0, pli = 0;
+  int pS = pitem < a.nitems ? decode(a, pitem).nz + 2 * R : 0;
+  auto produce_next = [&](int gp) {
+    if (pitem >= a.nitems) return;
+    ok &= produce(a, mp, smem, bars, pitem, ps, gp, recs + (pli & 1) * (ZLMAX + 1), ok);
+    if (++ps == pS) {
+      ps = 0;
+      ++pli;
+      pitem += gridDim.x;
+      pS = pitem < a.nitems ? decode(a, pitem).nz + 2 * R : 0;
+    }
+  };
+  if (producer)
+    for (int gp = 0; gp < DIST; ++gp) produce_next(gp);
+
+  // ---- every warp consumes
+  const int gq = lane >> 2, op = lane & 3;
+  const int xl = 8 * (warp & 1) + gq, yl = 2 * (warp >> 1);
+  const int fo = ((yl + R) * FR + xl + R) * NB + 2 * op;   // frame offset of node 0 (floats)
+  const int to = (yl * TT + xl) * NB + 2 * op;             // tile offset of node 0
+  const int vo = yl * TT + xl;
+  const size_t plane = (size_t)a.n1p * a.n2 * NB;   // one z-plane of a padded block
+  int g = 0, li = 0;
+  float2 acc[13][2];
+#pragma unroll
+  for (int i = 0; i < 13; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
+
+  for (int item = blockIdx.x; item < a.nitems; item += gridDim.x, ++li) {
+    const Item it = decode(a, item);
+    const int blk = a.blk0 + it.bi;
+    // projector coefficients of the item's boxes, split into TF32 high and low parts,
+    // in the B-fragment order (lane = 4 orbital + projector); slot MAXG is zero.
+    // The record offsets of the next item go to the buffer the producer left behind.
+    __syncthreads();   // every warp is past the previous item's last use of gcs
+    if (li > 0) stage_recs(a, item + gridDim.x, recs + ((li + 1) & 1) * (ZLMAX + 1));
+    {
+      const int ng = __ldg(a.cng + it.cta);
+      for (int idx = tid; idx < (MAXG + 1) * 32; idx += NCW * 32) {
+        const int gl = idx >> 5, ln = idx & 31;
+        if (gl < ng || gl == MAXG) {
+          float v = 0.f;
+          if (gl < ng) {
+            const int pp = __ldg(a.cproj + ((size_t)it.cta * MAXG + gl) * 4 + (ln & 3));
+            if (pp >= 0) v = __ldg(a.gc + ((size_t)pp * a.nblk_total + blk) * NB + (ln >> 2));
+          }
+          const float hi = tf32_hi(v);
+          gcs[idx] = make_float2(hi, v - hi);
+        }
+      }
+    }
+    __syncthreads();
+    const int gx = it.tx0 + xl, gy = it.ty0 + yl;
+    const bool v0 = gx < a.n1 && gy < a.n2, v1 = gx < a.n1 && gy + 1 < a.n2;
+    float* outp = a.yout + ((size_t)blk * a.ndp + (size_t)gy * a.n1p + gx + R) * NB + 2 * op;
+    // ghost copies: nodes x < R repeat at x' = x + n1 + R, nodes x >= n1 - R at x' = x - n1 + R
+    const long long gofs = gx < R ? (long long)a.n1 * NB : (gx >= a.n1 - R ? -(long long)a.n1 * NB : 0);
+    const int S = it.nz + 2 * R;
+    for (int s0 = 0; s0 < S; s0 += 13) {
+#pragma unroll
+      for (int i = 0; i < 13; ++i) {
+        const int s = s0 + i;
+        if (s < S) {
+          if (producer) produce_next(g + DIST);
+          const int slot = g % NBUF;
+          const unsigned char* st = smem + (size_t)slot * STAGE_B;
+          if (ok && !ptx::mbar_wait(bars + slot, (uint32_t)(g / NBUF) & 1u)) ok = false;
+          const float* F = reinterpret_cast<const float*>(st);
+          const bool comp = s >= R && s < R + it.nz;
+          float2 f0, f1;
+          if (comp) {
+            // y column of rows yl-6 .. yl+7 at the thread's x; rows 6 and 7 are its nodes
+            float2 col[2 * R + 2];
+#pragma unroll
+            for (int r = 0; r < 2 * R + 2; ++r) col[r] = lds2(F + fo + (r - R) * FR * NB);
+            f0 = col[R];
+            f1 = col[R + 1];
+            float2 ys0 = __fmul2_rn(a.cy2[1], __fadd2_rn(col[R + 1], col[R - 1]));
+            float2 ys1 = __fmul2_rn(a.cy2[1], __fadd2_rn(col[R + 2], col[R]));
+#pragma unroll
+            for (int q = 2; q <= R; ++q) {
+              ys0 = __ffma2_rn(a.cy2[q], __fadd2_rn(col[R + q], col[R - q]), ys0);
+              ys1 = __ffma2_rn(a.cy2[q], __fadd2_rn(col[R + 1 + q], col[R + 1 - q]), ys1);
+            }
+            float2 xs0, xs1;
+            {
+              float2 w[2 * R + 1];
+#pragma unroll
+              for (int q = 0; q <= 2 * R; ++q) w[q] = (q == R) ? f0 : lds2(F + fo + (q - R) * NB);
+              xs0 = __fmul2_rn(a.cx2[1], __fadd2_rn(w[R + 1], w[R - 1]));
+#pragma unroll
+              for (int q = 2; q <= R; ++q) xs0 = __ffma2_rn(a.cx2[q], __fadd2_rn(w[R + q], w[R - q]), xs0);
+            }
+            {
+              float2 w[2 * R + 1];
+#pragma unroll
+              for (int q = 0; q <= 2 * R; ++q) w[q] = (q == R) ? f1 : lds2(F + fo + FR * NB + (q - R) * NB);
+              xs1 = __fmul2_rn(a.cx2[1], __fadd2_rn(w[R + 1], w[R - 1]));
+#pragma unroll
+              for (int q = 2; q <= R; ++q) xs1 = __ffma2_rn(a.cx2[q], __fadd2_rn(w[R + q], w[R - q]), xs1);
+            }
+            const float* Vs = reinterpret_cast<const float*>(st + OFF_V);
+            const float2 cen0 = __fmul2_rn(f2(a.c0s + Vs[vo]), f0);
+            const float2 cen1 = __fmul2_rn(f2(a.c0s + Vs[vo + TT]), f1);
+            // projector term on the tensor cores (3xTF32)
+            float nl[4] = {0.f, 0.f, 0.f, 0.f};
+            {
+              const int* hdr = reinterpret_cast<const int*>(st + OFF_REC);
+              const int r0 = hdr[warp], r1 = hdr[warp + 1], nr = hdr[NCW];
+              const int* ids = hdr + 32;
+              const float4* A = reinterpret_cast<const float4*>(st + OFF_REC + 128 + 4 * ((nr + 3) & ~3));
+              for (int r = r0; r < r1; ++r) {
+                const int id = ids[r];
+                const float4 av = A[r * 32 + lane];
+                const float2 b0 = gcs[(id & 0xFFFF) * 32 + lane], b1 = gcs[(id >> 16) * 32 + lane];
+                const float h0 = tf32_hi(av.x), h1 = tf32_hi(av.y), h2 = tf32_hi(av.z), h3 = tf32_hi(av.w);
+                // low parts a - hi (exact: hi holds the leading bits of a)
+                const float2 l01 = __ffma2_rn(f2(-1.f), make_float2(h0, h1), make_float2(av.x, av.y));
+                const float2 l23 = __ffma2_rn(f2(-1.f), make_float2(h2, h3), make_float2(av.z, av.w));
+                mma_tf32(nl, l01.x, l01.y, l23.x, l23.y, b0.x, b1.x);
+                mma_tf32(nl, h0, h1, h2, h3, b0.y, b1.y);
+                mma_tf32(nl, h0, h1, h2, h3, b0.x, b1.x);
+              }
+            }
+            const float2 d0 = __fadd2_rn(__fadd2_rn(cen0, xs0), __fadd2_rn(ys0, make_float2(nl[0], nl[1])));
+            const float2 d1 = __fadd2_rn(__fadd2_rn(cen1, xs1), __fadd2_rn(ys1, make_float2(nl[2], nl[3])));
+            acc[(i + 7) % 13][0] = __fadd2_rn(acc[(i + 7) % 13][0], d0);
+            acc[(i + 7) % 13][1] = __fadd2_rn(acc[(i + 7) % 13][1], d1);
+          } else {
+            f0 = lds2(F + to);
+            f1 = lds2(F + to + TT * NB);
+          }
+          // z part: plane z' feeds the outputs z' +- d (slot of output z'+d: (i + 7 + d) % 13)
+#pragma unroll
+          for (int d = 1; d < R; ++d) {
+            acc[(i + 7 + d) % 13][0] = __ffma2_rn(a.cz2[d], f0, acc[(i + 7 + d) % 13][0]);
+            acc[(i + 7 + d) % 13][1] = __ffma2_rn(a.cz2[d], f1, acc[(i + 7 + d) % 13][1]);
+          }
+          acc[i % 13][0] = __fmul2_rn(a.cz2[R], f0);     // output z'+6 opens here
+          acc[i % 13][1] = __fmul2_rn(a.cz2[R], f1);
+#pragma unroll
+          for (int d = 1; d <= R; ++d) {
+            acc[(i + 7 - d) % 13][0] = __ffma2_rn(a.cz2[d], f0, acc[(i + 7 - d) % 13][0]);
+            acc[(i + 7 - d) % 13][1] = __ffma2_rn(a.cz2[d], f1, acc[(i + 7 - d) % 13][1]);
+          }
+          // output z'-6 is complete: recurrence epilogue
+          if (s >= 2 * R) {
+            float2 r0 = __fmul2_rn(a.alpha2, acc[(i + 1) % 13][0]);
+            float2 r1 = __fmul2_rn(a.alpha2, acc[(i + 1) % 13][1]);
+            if (a.yprev != nullptr) {
+              const float* P = reinterpret_cast<const float*>(st + OFF_YP);
+              r0 = __ffma2_rn(a.beta2, lds2(P + to), r0);
+              r1 = __ffma2_rn(a.beta2, lds2(P + to + TT * NB), r1);
+            }
+            float* o = outp + (size_t)(it.zs + s - 2 * R) * plane;
+            if (v0) *reinterpret_cast<float2*>(o) = r0;
+            if (v1) *reinterpret_cast<float2*>(o + (size_t)a.n1p * NB) = r1;
+            if (gofs != 0) {
+              if (v0) *reinterpret_cast<float2*>(o + gofs) = r0;
+              if (v1) *reinterpret_cast<float2*>(o + (size_t)a.n1p * NB + gofs) = r1;
+            }
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bars + NBUF + slot);
+          ++g;
+        }
+      }
+    }
+  }
+  if (!ok && lane == 0) atomicOr(a.status, STATUS_TIMEOUT);
+}
+
+// --------------------------------------------------------------------------- launcher
+
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiled encoder() {
+  static EncodeTiled fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiled)p;
+  });
+  return fn;
+}
+
+}  // namespace tma
+
+long long padded_nd(const sparc_ham* H) { return (long long)(H->gd.n1 + 2 * R) * H->gd.n2 * H->gd.n3; }
+
+namespace tma {
+
+// B (x-padded, ndp nodes per block) from the column-major X: 32 padded nodes x 8
+// orbitals per CTA, transposed through shared memory; ghost nodes read the other end
+// of their row.
+__global__ void __launch_bounds__(256) k_to_blocks_px(const float* __restrict__ X, long long ld, int ns,
+                                                     float* __restrict__ B, int n1, long long ndp) {
+  __shared__ float tile[NB][33];
+  const long long g0 = (long long)blockIdx.x * 32;
+  const int blk = blockIdx.y;
+  const int o = threadIdx.y, x = threadIdx.x;   // blockDim = (32, NB)
+  const int n = blk * NB + o;
+  const int n1p = n1 + 2 * R;
+  const long long gp = g0 + x;
+  float v = 0.f;
+  if (n < ns && gp < ndp) {
+    const long long row = gp / n1p;
+    int xs = (int)(gp - row * n1p) - R;
+    if (xs < 0) xs += n1;
+    else if (xs >= n1) xs -= n1;
+    v = X[row * n1 + xs + (long long)n * ld];
+  }
+  tile[o][x] = v;
+  __syncthreads();
+  const int t = threadIdx.y * 32 + threadIdx.x;
+  const int p = t / NB, l = t % NB;
+  if (g0 + p < ndp) B[((size_t)blk * ndp + g0 + p) * NB + l] = tile[l][p];
+}
+
+// X (column-major) from the interior nodes of the x-padded B.
+__global__ void __launch_bounds__(256) k_from_blocks_px(const float* __restrict__ B, int n1, long long nd,
+                                                       float* __restrict__ X, long long ld, int ns) {
+  __shared__ float tile[NB][33];
+  const long long g0 = (long long)blockIdx.x * 32;
+  const int blk = blockIdx.y;
+  const int n1p = n1 + 2 * R;
+  const long long ndp = nd / n1 * n1p;
+  const int t = threadIdx.y * 32 + threadIdx.x;
+  const int p = t / NB, l = t % NB;
+  if (g0 + p < nd) {
+    const long long g = g0 + p, row = g / n1;
+    tile[l][p] = B[((size_t)blk * ndp + row * n1p + (g - row * n1) + R) * NB + l];
+  }
+  __syncthreads();
+  const int o = threadIdx.y, x = threadIdx.x;
+  const int n = blk * NB + o;
+  const long long g = g0 + x;
+  if (n < ns && g < nd) X[g + (long long)n * ld] = tile[o][x];
+}
+
+// Tensor map of an x-padded block buffer: dims (8 orbitals, n1 + 2R, n2, n3 * nblk),
+// box (8, bx, by, 1).
+static bool map_blocks(CUtensorMap* m, const float* base, int n1p, int n2, int n3, int nblk, int bx, int by) {
+  const cuuint64_t dims[4] = {(cuuint64_t)NB, (cuuint64_t)n1p, (cuuint64_t)n2, (cuuint64_t)n3 * nblk};
+  const cuuint64_t strides[3] = {(cuuint64_t)NB * 4, (cuuint64_t)n1p * NB * 4, (cuuint64_t)n1p * n2 * NB * 4};
+  const cuuint32_t box[4] = {(cuuint32_t)NB, (cuuint32_t)bx, (cuuint32_t)by, 1};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  return encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void*)base, dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace tma
+
+cudaError_t launch_to_blocks_px(const sparc_ham* H, const float* X, long long ld, int ns, float* B, int nblk,
+                                cudaStream_t st) {
+  const long long ndp = padded_nd(H);
+  dim3 grid((unsigned)ceil_div(ndp, 32), (unsigned)nblk), block(32, NB);
+  tma::k_to_blocks_px<<<grid, block, 0, st>>>(X, ld, ns, B, H->gd.n1, ndp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_from_blocks_px(const sparc_ham* H, const float* B, int nblk, float* X, long long ld, int ns,
+                                  cudaStream_t st) {
+  dim3 grid((unsigned)ceil_div(H->gd.nd, 32), (unsigned)nblk), block(32, NB);
+  tma::k_from_blocks_px<<<grid, block, 0, st>>>(B, H->gd.n1, H->gd.nd, X, ld, ns);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pass_tma(const sparc_ham* H, const float* Yin, const float* Yprev, float* Yout, const float* gc,
+                            int nblk_total, int blk0, int nb, double alpha, double shift, double beta,
+                            cudaStream_t st) {
+  using namespace tma;
+  const Tables* Tb = (const Tables*)H->fast;
+  const TmaTables& M = Tb->tma;
+  if (!M.ok || encoder() == nullptr) return cudaErrorNotSupported;
+  const int n1 = H->gd.n1, n2 = H->gd.n2, n3 = H->gd.n3, n1p = n1 + 2 * R;
+  Maps mp;
+  for (int i = 0; i < M.nmaps; ++i)
+    if (!map_blocks(&mp.frame[i], Yin, n1p, n2, n3, nblk_total, FR, M.map_h[i])) return cudaErrorInvalidValue;
+  for (int i = M.nmaps; i < TMA_NMAPS; ++i) mp.frame[i] = mp.frame[0];
+  if (!map_blocks(&mp.tile_in, Yin, n1p, n2, n3, nblk_total, TT, TT) ||
+      !map_blocks(&mp.tile_prev, Yprev ? Yprev : Yin, n1p, n2, n3, nblk_total, TT, TT))
+    return cudaErrorInvalidValue;
+  {
+    const cuuint64_t dims[3] = {(cuuint64_t)n1, (cuuint64_t)n2, (cuuint64_t)n3};
+    const cuuint64_t strides[2] = {(cuuint64_t)n1 * 4, (cuuint64_t)n1 * n2 * 4};
+    const cuuint32_t box[3] = {TT, TT, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    if (encoder()(&mp.veff, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)H->d_veff32, dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  Args a;
+  a.n1 = n1; a.n2 = n2; a.n3 = n3;
+  a.n1p = n1p;
+  a.tiles_x = M.tiles_x;
+  a.ntiles = M.tiles_x * M.tiles_y;
+  a.nchunk = M.nchunk;
+  a.zl = M.zl;
+  a.blk0 = blk0;
+  a.nblk_total = nblk_total;
+  a.nitems = a.ntiles * M.nchunk * nb;
+  a.ndp = padded_nd(H);
+  std::memcpy(a.yseg, M.yseg, sizeof(a.yseg));
+  for (int p = 0; p <= R; ++p) {
+    const float cx = (float)H->gd.coef[0][p], cy = (float)H->gd.coef[1][p], cz = (float)H->gd.coef[2][p];
+    a.cx2[p] = make_float2(cx, cx);
+    a.cy2[p] = make_float2(cy, cy);
+    a.cz2[p] = make_float2(cz, cz);
+  }
+  a.c0s = (float)(2.0 * (H->gd.coef[0][0] + H->gd.coef[1][0] + H->gd.coef[2][0])) - (float)shift;
+  a.alpha2 = make_float2((float)alpha, (float)alpha);
+  a.beta2 = make_float2((float)beta, (float)beta);
+  a.yin = Yin;
+  a.yprev = Yprev;
+  a.yout = Yout;
+  a.gc = gc;
+  a.cproj = M.d_cproj;
+  a.cng = M.d_cng;
+  a.rec = M.d_rec;
+  a.stream = (const unsigned char*)M.d_stream;
+  a.status = H->ctx->d_status;
+  cudaError_t e = cudaFuncSetAttribute(k_pass_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_B);
+  if (e != cudaSuccess) return e;
+  const int grid = std::min(a.nitems, std::max(H->ctx->nsm, 1));
+  cudaEvent_t t0 = timing_begin(H->ctx, st);
+  k_pass_tma<<<grid, NTHR, SMEM_B, st>>>(mp, a);
+  ++H->ctx->launches;
+  timing_end(H->ctx, TK_FPASS, t0, st);
+  return cudaGetLastError();
+}
+
+}  // namespace fast
+}  // namespace sparc

@@ -281,13 +281,47 @@ sparc_status filter_block_fast(sparc_ham* H, int m, double a, double b, double a
   // covers all blocks.  A tuned configuration (sparc_autotune_filter) may group blocks
   // and, for FP32, choose the pass tile shape.
   int shape = 0, G = nblk;
+  if constexpr (std::is_same<T, float>::value)
+    if (fast::tma_usable(H)) shape = fast::SHAPE_TMA;   // the default where it applies
   const auto tu = H->ctx->tuned.find(std::make_tuple((int)DtypeOf<T>::v, H->gd.nd, ns, 1));
   if (tu != H->ctx->tuned.end()) {
     const int tunedG = tu->second & (TUNE_SHAPE - 1);
     if (tunedG > 0) G = std::min(nblk, tunedG);
     if constexpr (!std::is_same<T, cf32>::value) shape = tu->second / TUNE_SHAPE;
   }
+  // a tuned configuration is keyed by (dtype, Nd, ns), which other Hamiltonians may share:
+  // a tile shape that this H cannot take falls back to the 16 x 16 tiled pass
+  if constexpr (std::is_same<T, float>::value)
+    if (!fast::shape_usable(H, shape)) shape = 0;
   T* scratch = (T*)w.tail;
+  if constexpr (std::is_same<T, float>::value) {
+    if (shape == fast::SHAPE_TMA) {
+      // the TMA pass on x-padded block buffers (ghost nodes at both ends of every row)
+      SPARC_CUDA(H->ctx, fast::launch_to_blocks_px(H, X, ld, ns, B0, nblk, st));
+      ++H->ctx->launches;
+      T* res = B1;
+      for (int g0 = 0; g0 < nblk; g0 += G) {
+        const int nb = std::min(G, nblk - g0);
+        T* prev = B0;
+        T* cur = B1;
+        double sigma = sigma1;
+        SPARC_CUDA(H->ctx, fast::launch_gather<T>(H, prev, nblk, g0, nb, gc, scratch, st, true));
+        SPARC_CUDA(H->ctx, fast::launch_pass_tma(H, prev, nullptr, cur, gc, nblk, g0, nb, sigma1 / e, c, 0.0, st));
+        for (int j = 1; j < m; ++j) {
+          const double sigma_new = 1.0 / (2.0 / sigma1 - sigma);
+          SPARC_CUDA(H->ctx, fast::launch_gather<T>(H, cur, nblk, g0, nb, gc, scratch, st, true));
+          SPARC_CUDA(H->ctx, fast::launch_pass_tma(H, cur, prev, prev, gc, nblk, g0, nb, 2.0 * sigma_new / e, c,
+                                                   -sigma * sigma_new, st));
+          std::swap(cur, prev);
+          sigma = sigma_new;
+        }
+        res = cur;
+      }
+      SPARC_CUDA(H->ctx, fast::launch_from_blocks_px(H, res, nblk, Y, ld, ns, st));
+      ++H->ctx->launches;
+      return SPARC_OK;
+    }
+  }
   SPARC_CUDA(H->ctx, launch_to_blocks<T>(X, ld, ns, B0, H->gd.nd, nblk, st));
   ++H->ctx->launches;
   T* res = B1;
@@ -322,7 +356,9 @@ size_t apply_scratch_bytes(sparc_ham* H, sparc_dtype dt, int ns) {
 size_t filter_ws(sparc_ham* H, sparc_dtype dt, int ns, char* base, BlockWs* w) {
   const size_t es = dtype_size(dt);
   const int nblk = ceil_div(ns, NB);
-  const size_t bb = align256((size_t)nblk * H->gd.nd * NB * es);
+  // FP32 block buffers hold the x-padded layout of the TMA pass where it applies
+  const long long ndb = (dt == SPARC_F32 && fast::tma_usable(H)) ? fast::padded_nd(H) : H->gd.nd;
+  const size_t bb = align256((size_t)nblk * ndb * NB * es);
   const size_t gb = align256((size_t)std::max(1, H->nproj) * nblk * NB * es);
   size_t extra = 0;
   if ((dt == SPARC_F32 || dt == SPARC_C64) && fast::usable(H)) extra = fast::gather_scratch_bytes(H, nblk, es);
@@ -851,6 +887,11 @@ sparc_status sparc_autotune_filter(sparc_ham* const* H, int nk, sparc_dtype dtyp
       if (fast::shape_usable(H[0], sh))
         for (size_t i = 0; i < nc; ++i) cand.push_back(cand[i] + sh * TUNE_SHAPE);
   }
+  // preference among near-equal times: the TMA pass, then the 16 x 16 and 16 x 8 tiles
+  auto shape_rank = [](int code) {
+    const int sh = code / TUNE_SHAPE;
+    return sh == fast::SHAPE_TMA ? 0 : sh + 1;
+  };
   const int mt = std::min(m, 4);
   cudaStream_t st = (cudaStream_t)stream;
   ctx->tuned.erase(key);
@@ -886,7 +927,7 @@ sparc_status sparc_autotune_filter(sparc_ham* const* H, int nk, sparc_dtype dtyp
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   // the fastest, except that a configuration within 3% of it with more blocks per
-  // launch (fewer launches; then the smaller tile code) is preferred: the timed
+  // launch (fewer launches; then the preferred tile shape) is preferred: the timed
   // filter is short, and differences that small are within its run-to-run spread
   const double tbest = *std::min_element(tms.begin(), tms.end());
   int best_u = 0;
@@ -895,7 +936,7 @@ sparc_status sparc_autotune_filter(sparc_ham* const* H, int nk, sparc_dtype dtyp
     if (tms[i] > 1.03 * tbest) continue;
     const int u = cand[i], ub = best_u;
     const bool more = best_u == 0 || (u & (TUNE_SHAPE - 1)) > (ub & (TUNE_SHAPE - 1)) ||
-                      ((u & (TUNE_SHAPE - 1)) == (ub & (TUNE_SHAPE - 1)) && u < ub);
+                      ((u & (TUNE_SHAPE - 1)) == (ub & (TUNE_SHAPE - 1)) && shape_rank(u) < shape_rank(ub));
     if (more) { best_u = u; best_ms = tms[i]; }
   }
   ctx->tuned[key] = best_u;

@@ -90,30 +90,41 @@ def test_filter_graph_rejects_bad_bounds(ctx):
     G.close()
 
 
-def test_half_tile_fp32_pass_matches_full_tile_and_oracle(ctx):
+def test_fp32_pass_shapes_match_each_other_and_oracle(ctx):
     """The FP32 pass with 16 x 8 tiles (256-thread CTAs, two per SM) takes every node
     and projector piece in the order of the 16 x 16 tile, so the filter is the same bit
-    for bit; and it matches the oracle."""
+    for bit; the TMA-fed pass (the default here) is the same bit for bit over any
+    grouping of blocks per launch; all of them match the oracle."""
     from paper_1603_04339_gb300 import sparc
     wl = synth.small_case(n=(24, 22, 26), natom=4, ns=37, m=9, seed=77)
     H = sparc.Hamiltonian.from_workload(ctx, wl)
     X = torch.from_numpy(synth.random_orbitals(wl.nd, wl.ns, 808).astype(np.float32)).cuda()
     a0, b = -3.0, 60.0
     a = a0 + (b - a0) * (wl.ns / wl.nd) ** (2.0 / 3.0)
-    outs = []
-    for code in (0, 2, 3 + sparc.TUNE_SHAPE, 1 + sparc.TUNE_SHAPE):
-        sparc.sparc_set_filter_units(ctx, sparc.F32, wl.nd, wl.ns, 1, code)
-        Y = torch.full_like(X, float("nan"))
-        sparc.sparc_cheb_filter(H, wl.m, a, b, a0, X, Y)
-        torch.cuda.synchronize()
-        outs.append(Y)
-    sparc.sparc_set_filter_units(ctx, sparc.F32, wl.nd, wl.ns, 1, 0)
-    for Y in outs[1:]:
-        assert torch.equal(Y, outs[0])
+    TS = sparc.TUNE_SHAPE
+
+    def run(codes):
+        outs = []
+        for code in codes:
+            sparc.sparc_set_filter_units(ctx, sparc.F32, wl.nd, wl.ns, 1, code)
+            Y = torch.full_like(X, float("nan"))
+            sparc.sparc_cheb_filter(H, wl.m, a, b, a0, X, Y)
+            torch.cuda.synchronize()
+            outs.append(Y)
+        sparc.sparc_set_filter_units(ctx, sparc.F32, wl.nd, wl.ns, 1, 0)
+        return outs
+
+    tiled = run((5, 2, 3 + TS, 1 + TS))             # 16 x 16 and 16 x 8 tiles, groups of 5, 2, 3, 1 blocks
+    tma = run((0, 5 + 2 * TS, 2 + 2 * TS))          # default, and the TMA pass in groups of 5 and 2
+    for Y in tiled[1:]:
+        assert torch.equal(Y, tiled[0])
+    for Y in tma[1:]:
+        assert torch.equal(Y, tma[0])
     Hor = O.OracleH(wl)
     cols = [0, 17, 36]
     Yo = O.cheb_filter(Hor, X[cols].cpu().numpy().astype(np.float64), wl.m, a, b, a0)
-    assert _colerr(outs[2][cols].cpu().numpy().astype(np.float64), Yo) < 1e-4
+    assert _colerr(tiled[2][cols].cpu().numpy().astype(np.float64), Yo) < 1e-4
+    assert _colerr(tma[0][cols].cpu().numpy().astype(np.float64), Yo) < 1e-4
 
 
 def test_filter_graph_of_complex_cells(ctx):
