@@ -425,6 +425,30 @@ sparc_status sparc_launch_count(const sparc_ctx* ctx, int64_t* launches);
 /* Jacobi sweeps used by the last Rayleigh-Ritz call on this context. */
 sparc_status sparc_last_sweeps(const sparc_ctx* ctx, int* sweeps);
 
+/* Failure injection, for testing the error paths (not part of the method).  All
+ * injections are made on the host; none makes a kernel fault, trap or hang.
+ *   SPARC_INJECT_ALLOC_FAIL: the next `value` workspace growths of the context fail
+ *     as if the device allocation had failed (the calls return SPARC_ERR_OOM and
+ *     leave the context usable).
+ *   SPARC_INJECT_WAIT_LIMIT: bounded waits of the TMA-fed filter pass give up after
+ *     `value` SM clocks (0: the default, about 2^32 clocks).
+ *   SPARC_INJECT_STALL: the next launch of the TMA-fed filter pass stops filling its
+ *     shared-memory stages at step `value` of each CTA (-1: off), so that the waits
+ *     for that stage run out; no copy is left in flight.  The launch latches the
+ *     timeout in the status word: the next synchronising call returns
+ *     SPARC_ERR_TIMEOUT, and the outputs of that launch are undefined.
+ *   SPARC_INJECT_CG_MAX_ITERS: the Poisson solver of sparc_scf_step stops after
+ *     `value` conjugate-gradient iterations (0: the default 4000); short of its
+ *     tolerance, the step returns SPARC_ERR_NO_CONVERGENCE.
+ * SPARC_ERR_INVALID_ARG for an unknown `what`. */
+typedef enum {
+  SPARC_INJECT_ALLOC_FAIL = 1,
+  SPARC_INJECT_WAIT_LIMIT = 2,
+  SPARC_INJECT_STALL = 3,
+  SPARC_INJECT_CG_MAX_ITERS = 4
+} sparc_inject;
+sparc_status sparc_debug_inject(sparc_ctx* ctx, int what, int64_t value);
+
 #ifdef __cplusplus
 }
 #endif

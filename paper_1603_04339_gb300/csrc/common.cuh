@@ -182,6 +182,11 @@ struct sparc_ctx {
   // ns, number of k-points): units (blocks of NB orbitals) per launch + TUNE_SHAPE x the
   // FP32 pass tile shape
   std::map<std::tuple<int, long long, int, int>, int> tuned;
+  // failure injection (sparc_debug_inject)
+  int inject_alloc_fail = 0;        // workspace growths still to fail
+  long long inject_wait_limit = 0;  // clocks of the TMA pass's bounded waits (0: default)
+  int inject_stall = -1;            // step at which the next TMA pass stops producing
+  int inject_cg_max = 0;            // Poisson CG iteration cap (0: default)
 };
 
 namespace sparc {

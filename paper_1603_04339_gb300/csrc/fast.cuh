@@ -53,17 +53,17 @@ struct Layout {
   int* d_sslots = nullptr;    // CTA-local indices of the pieces touching those nodes at z
 };
 
-// Tables of the TMA-fed FP32 pass (hpass_tma.cu): per CTA (16 x 16 tile, z-chunk) the
-// projector groups (atom boxes) that meet it, and per (CTA, plane) a record of the
-// A fragments of the projector term for each of its 16 warps.
-constexpr int TMA_MAXG = 48;                 // projector groups per CTA, at most
-constexpr unsigned TMA_REC_MAX = 36864;      // bytes of one plane's record, at most
+// Tables of the TMA-fed FP32 pass (hpass_tma.cu): per tile column (16 x 16 (x, y) tile,
+// all z) the projector groups (atom boxes) that meet it, and per (tile, plane) a record
+// of the A fragments of the projector term for each of the 16 warps of a CTA.
+constexpr int TMA_MAXG = 64;                 // projector groups per tile column, at most
+constexpr unsigned TMA_REC_MAX = 36352;      // bytes of one plane's record, at most
 constexpr int TMA_MAXTY = 16;                // tile rows (n2 <= 256)
 constexpr int TMA_MAXSEG = 4;                // y segments of one halo frame
 constexpr int TMA_NMAPS = 8;                 // distinct segment heights
 struct TmaTables {
   bool ok = false;            // built: the grid and projectors fit the kernel's limits
-  int zl = 0, nchunk = 0, tiles_x = 0, tiles_y = 0;
+  int zl = 0, nchunk = 0, tiles_x = 0, tiles_y = 0;   // zl = n3, nchunk = 1 (per launch: see the launcher)
   int max_rec = 0;
   // The halo frame of tile row ty, rows y = 16 ty - 6 .. 16 ty + 21 wrapped into [0, n2),
   // as up to TMA_MAXSEG runs of consecutive y: run j starts at y = yseg[ty][j][0], lands
@@ -71,9 +71,9 @@ struct TmaTables {
   int nmaps = 0;
   int map_h[TMA_NMAPS] = {};
   int yseg[TMA_MAXTY][TMA_MAXSEG][3] = {};
-  int* d_cproj = nullptr;     // [cta][TMA_MAXG][4] projector index of (group slot, s/px/py/pz), -1 if none
-  int* d_cng = nullptr;       // [cta] groups of the CTA
-  int* d_rec = nullptr;       // [cta * zl + k] record offsets in 16-byte units (+ one end entry)
+  int* d_cproj = nullptr;     // [tile][TMA_MAXG][4] projector index of (group slot, s/px/py/pz), -1 if none
+  int* d_cng = nullptr;       // [tile] groups of the tile column
+  int* d_rec = nullptr;       // [tile * n3 + z] record offsets in 16-byte units (+ one end entry)
   void* d_stream = nullptr;   // the records
   size_t stream_bytes = 0;
 };

@@ -54,7 +54,7 @@ constexpr int MAXG = TMA_MAXG;
 constexpr uint32_t REC_MAX = TMA_REC_MAX;
 constexpr int TT = 16;                   // tile edge in x and y
 constexpr int FR = TT + 2 * R;           // 28: tile plus halo
-constexpr int ZLMAX = 32;                // output planes per z-chunk, at most
+constexpr int ZLMAX = 128;               // output planes per z-chunk, at most
 constexpr int NBUF = 3;                  // stages in the ring
 constexpr int NCW = 16;                  // warps; the last one also produces
 constexpr int NTHR = NCW * 32;
@@ -66,10 +66,15 @@ constexpr uint32_t OFF_YP = FRAME_B;
 constexpr uint32_t OFF_V = OFF_YP + TILE_B;
 constexpr uint32_t OFF_REC = OFF_V + V_B;        // 34304
 constexpr uint32_t STAGE_B = OFF_REC + REC_MAX;
+// per-item tables, filled ahead by cp.async: projector coefficients gc of the item's
+// boxes (two items), their projector indices (two items), record offsets (three items)
 constexpr uint32_t OFF_GCS = NBUF * STAGE_B;
-constexpr uint32_t GCS_B = (MAXG + 1) * 32 * 8;
-constexpr uint32_t OFF_RECS = OFF_GCS + GCS_B;   // record offsets of two items: int[2][ZLMAX + 1]
-constexpr uint32_t OFF_BAR = OFF_RECS + 2 * (ZLMAX + 1) * 4 + 8;
+constexpr uint32_t GCS_B = (MAXG + 1) * 32 * 4;    // one item: float[MAXG + 1][32]
+constexpr uint32_t OFF_CPJ = OFF_GCS + 2 * GCS_B;
+constexpr uint32_t CPJ_B = MAXG * 4 * 4;           // one item: int[MAXG][4]
+constexpr uint32_t OFF_RECS = OFF_CPJ + 2 * CPJ_B;
+constexpr int RECN = ZLMAX + 4;                    // ints per item (nz + 1 used), 16-byte multiple
+constexpr uint32_t OFF_BAR = OFF_RECS + 3 * RECN * 4;
 constexpr uint32_t SMEM_B = OFF_BAR + 2 * NBUF * 8;
 static_assert(OFF_BAR % 8 == 0, "mbarrier alignment");
 static_assert(STAGE_B % 128 == 0 && OFF_REC % 128 == 0 && OFF_YP % 128 == 0, "stage alignment");
@@ -95,11 +100,12 @@ bool tma_host_tables(const int n[3], const std::vector<Group>& grps, const std::
   std::vector<int>& cng = out.cng;
   std::vector<int>& rec = out.rec;
   std::vector<uint32_t>& words = out.words;
-  M.nchunk = ceil_div(n[2], ZLMAX);
-  M.zl = ceil_div(n[2], M.nchunk);
+  // tables per tile column (all z); the z-chunking of the work is chosen per launch
+  M.nchunk = 1;
+  M.zl = n[2];
   M.tiles_x = ceil_div(n[0], TT);
   M.tiles_y = ceil_div(n[1], TT);
-  const int ncta = M.tiles_x * M.tiles_y * M.nchunk;
+  const int ncta = M.tiles_x * M.tiles_y;
   const int ngrp = (int)grps.size();
   std::vector<long long> off4(ngrp);
   {
@@ -116,9 +122,9 @@ bool tma_host_tables(const int n[3], const std::vector<Group>& grps, const std::
   words.reserve(1 << 20);
   int max_rec = 0;
   for (int cta = 0; cta < ncta; ++cta) {
-    const int tile = cta / M.nchunk, chunk = cta % M.nchunk;
+    const int tile = cta;
     const int x0 = (tile % M.tiles_x) * TT, y0 = (tile / M.tiles_x) * TT;
-    const int zs = chunk * M.zl, nz = std::min(M.zl, n[2] - zs);
+    const int zs = 0, nz = n[2];
     const int xe = std::min(n[0], x0 + TT), ye = std::min(n[1], y0 + TT);
     // the atom boxes (projector groups) that meet the tile over the chunk's planes
     std::vector<int> loc;
@@ -144,7 +150,7 @@ bool tma_host_tables(const int n[3], const std::vector<Group>& grps, const std::
       uy.push_back(cy);
       uz.push_back(cz);
     }
-    if ((int)loc.size() > MAXG) return false;   // too many boxes per tile: the other kernels run
+    if ((int)loc.size() > MAXG) return false;   // too many boxes per tile column: the other kernels run
     cng[cta] = (int)loc.size();
     for (size_t g = 0; g < loc.size(); ++g)
       for (int l = 0; l < 4; ++l) cproj[((size_t)cta * MAXG + g) * 4 + l] = grps[loc[g]].proj[l];
@@ -304,11 +310,13 @@ struct Args {
   const float* yprev;        // null on the first degree
   float* yout;
   const float* gc;           // [p][blk][NB]
-  const int* cproj;          // [cta][MAXG][4]
-  const int* cng;            // [cta]
-  const int* rec;            // [cta * zl + k] record offsets, 16-byte units
+  const int* cproj;          // [tile][MAXG][4]
+  const int* cng;            // [tile]
+  const int* rec;            // [tile * n3 + z] record offsets, 16-byte units
   const unsigned char* stream;
   int* status;
+  long long wait_limit;      // SM clocks of a bounded wait
+  int stall;                 // failure injection: the producer stops at this step (-1: off)
 };
 
 __device__ __forceinline__ void tma4(void* dst, const CUtensorMap* m, int c0, int c1, int c2, int c3, uint64_t* bar) {
@@ -323,6 +331,33 @@ __device__ __forceinline__ void tma3(void* dst, const CUtensorMap* m, int c0, in
           "r"(ptx::saddr(dst)), "l"(m), "r"(c0), "r"(c1), "r"(c2), "r"(ptx::saddr(bar))
       : "memory");
 }
+// L2 cache policies: evict_last for data every block re-reads (the projector records),
+// evict_first for data read once (Yprev).
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          ptx::saddr(dst)),
+      "l"(src), "r"(bytes), "r"(ptx::saddr(bar)), "l"(pol)
+      : "memory");
+}
+__device__ __forceinline__ void tma4_hint(void* dst, const CUtensorMap* m, int c0, int c1, int c2, int c3, uint64_t* bar,
+                                          uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%2, %3, %4, %5}], [%6], %7;" ::
+          "r"(ptx::saddr(dst)), "l"(m), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(ptx::saddr(bar)), "l"(pol)
+      : "memory");
+}
+
 // The tensor maps of a launch: halo-frame runs of each height, the tile of Yin and of
 // Yprev (16 x 16 nodes, padded layout) and V_eff.
 struct Maps {
@@ -348,7 +383,7 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], float a0, float a1, floa
 }
 
 struct Item {
-  int tile, chunk, bi, tx0, ty0, zs, nz, cta;
+  int tile, chunk, bi, tx0, ty0, zs, nz;
 };
 __device__ __forceinline__ Item decode(const Args& a, int item) {
   Item it;
@@ -360,7 +395,6 @@ __device__ __forceinline__ Item decode(const Args& a, int item) {
   it.ty0 = (it.tile / a.tiles_x) * TT;
   it.zs = it.chunk * a.zl;
   it.nz = min(a.zl, a.n3 - it.zs);
-  it.cta = it.tile * a.nchunk + it.chunk;
   return it;
 }
 
@@ -379,7 +413,8 @@ __device__ __forceinline__ bool produce(const Args& a, const Maps& mp, unsigned 
   uint64_t* full = bars + slot;
   uint64_t* empty = bars + NBUF + slot;
   bool ok = true;
-  if (wait && g >= NBUF && !ptx::mbar_wait(empty, (uint32_t)((g / NBUF) - 1) & 1u)) ok = false;
+  if (a.stall >= 0 && g >= a.stall) return true;   // injected stall: from this step of the CTA on, nothing is issued
+  if (wait && g >= NBUF && !ptx::mbar_wait_lim(empty, (uint32_t)((g / NBUF) - 1) & 1u, a.wait_limit)) ok = false;
   const int p = it.zs - R + s;
   int zw = p;
   if (zw < 0) zw += a.n3;
@@ -400,28 +435,77 @@ __device__ __forceinline__ bool produce(const Args& a, const Maps& mp, unsigned 
       if (sg[2] >= 0) tma4(st + (size_t)sg[1] * FR * NB * 4, &mp.frame[sg[2]], 0, it.tx0, sg[0], zc, full);
     }
     if (lane == 29) tma3(st + OFF_V, &mp.veff, it.tx0, it.ty0, zw, full);
-    if (lane == 30) ptx::bulk_g2s(st + OFF_REC, a.stream + 16 * (size_t)o0, rbytes, full);
+    if (lane == 30) bulk_g2s_hint(st + OFF_REC, a.stream + 16 * (size_t)o0, rbytes, full, policy_evict_last());
   } else if (lane == 0) {
     tma4(st, &mp.tile_in, 0, it.tx0 + R, it.ty0, zc, full);
   }
-  if (yp && lane == 31) tma4(st + OFF_YP, &mp.tile_prev, 0, it.tx0 + R, it.ty0, blk * a.n3 + (p - R), full);
+  if (yp && lane == 31)
+    tma4_hint(st + OFF_YP, &mp.tile_prev, 0, it.tx0 + R, it.ty0, blk * a.n3 + (p - R), full, policy_evict_first());
   return ok;
 }
 
-// rec offsets of an item (entries 0 .. nz) into dst, by threads 0 .. ZLMAX
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
+  // 4-byte asynchronous copy; an invalid source copies nothing and zero-fills dst
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(ptx::saddr(dst)), "l"(src), "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Asynchronous per-item staging by all threads: the record offsets (entries 0 .. nz) and
+// the projector indices of an item (tile column), or its coefficients gc (projector
+// indices read from cpj, zero for absent projectors).
 __device__ __forceinline__ void stage_recs(const Args& a, int item, int* dst) {
   const int t = threadIdx.x;
   if (item < a.nitems && t <= ZLMAX) {
     const Item it = decode(a, item);
-    if (t <= it.nz) dst[t] = __ldg(a.rec + (size_t)it.cta * a.zl + t);
+    if (t <= it.nz) cp_async4(dst + t, a.rec + (size_t)it.tile * a.n3 + it.zs + t, true);
   }
+}
+__device__ __forceinline__ void stage_cproj(const Args& a, int item, int* dst) {
+  if (item >= a.nitems) return;
+  const Item it = decode(a, item);
+  for (int i = threadIdx.x; i < MAXG * 4; i += NTHR) cp_async4(dst + i, a.cproj + (size_t)it.tile * MAXG * 4 + i, true);
+}
+__device__ __forceinline__ void stage_gc(const Args& a, int item, const int* cpj, float* dst) {
+  if (item >= a.nitems) return;
+  const Item it = decode(a, item);
+  const int blk = a.blk0 + it.bi;
+  for (int idx = threadIdx.x; idx < MAXG * 32; idx += NTHR) {
+    const int pp = cpj[(idx >> 5) * 4 + (idx & 3)];
+    const float* src = a.gc + ((size_t)(pp < 0 ? 0 : pp) * a.nblk_total + blk) * NB + ((idx & 31) >> 2);
+    cp_async4(dst + idx, src, pp >= 0);
+  }
+}
+
+// Ring position I of a step of plane z': the output z' gets d (its x/y/centre/projector
+// part); plane z' feeds c_|d| f to the outputs z' + d, d = -6..6 (slot (I + 7 + d) mod 13;
+// the output z'+6 opens in slot I); e receives the completed output z'-6 (slot I + 1).
+template <int I>
+__device__ __forceinline__ void zstep(float2 (&acc)[13][2], const float2* cz2, float2 f0, float2 f1, float2 d0,
+                                      float2 d1, float2& e0, float2& e1) {
+  acc[(I + 7) % 13][0] = __fadd2_rn(acc[(I + 7) % 13][0], d0);
+  acc[(I + 7) % 13][1] = __fadd2_rn(acc[(I + 7) % 13][1], d1);
+#pragma unroll
+  for (int d = 1; d < R; ++d) {
+    acc[(I + 7 + d) % 13][0] = __ffma2_rn(cz2[d], f0, acc[(I + 7 + d) % 13][0]);
+    acc[(I + 7 + d) % 13][1] = __ffma2_rn(cz2[d], f1, acc[(I + 7 + d) % 13][1]);
+  }
+  acc[I][0] = __fmul2_rn(cz2[R], f0);
+  acc[I][1] = __fmul2_rn(cz2[R], f1);
+#pragma unroll
+  for (int d = 1; d <= R; ++d) {
+    acc[(I + 7 - d) % 13][0] = __ffma2_rn(cz2[d], f0, acc[(I + 7 - d) % 13][0]);
+    acc[(I + 7 - d) % 13][1] = __ffma2_rn(cz2[d], f1, acc[(I + 7 - d) % 13][1]);
+  }
+  e0 = acc[(I + 1) % 13][0];
+  e1 = acc[(I + 1) % 13][1];
 }
 
 __global__ void __launch_bounds__(NTHR, 1)
 k_pass_tma(const __grid_constant__ Maps mp, const __grid_constant__ Args a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OFF_BAR);
-  float2* gcs = reinterpret_cast<float2*>(smem + OFF_GCS);
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -432,8 +516,20 @@ k_pass_tma(const __grid_constant__ Maps mp, const __grid_constant__ Args a) {
     ptx::mbar_init_fence();
   }
   int* recs = reinterpret_cast<int*>(smem + OFF_RECS);
+  int* cpj = reinterpret_cast<int*>(smem + OFF_CPJ);
+  float* gcsb = reinterpret_cast<float*>(smem + OFF_GCS);
+  // tables of the first two items (record offsets, projector indices), then the
+  // coefficients of the first item; the zero slot MAXG of both coefficient buffers
   stage_recs(a, blockIdx.x, recs);
-  stage_recs(a, blockIdx.x + gridDim.x, recs + (ZLMAX + 1));
+  stage_recs(a, blockIdx.x + gridDim.x, recs + RECN);
+  stage_cproj(a, blockIdx.x, cpj);
+  stage_cproj(a, blockIdx.x + gridDim.x, cpj + MAXG * 4);
+  if (tid < 64) gcsb[(tid >> 5) * (GCS_B / 4) + MAXG * 32 + (tid & 31)] = 0.f;
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  stage_gc(a, blockIdx.x, cpj, gcsb);
+  cp_async_commit();
   __syncthreads();
   const bool producer = warp == NCW - 1;
   bool ok = true;
@@ -442,7 +538,7 @@ k_pass_tma(const __grid_constant__ Maps mp, const __grid_constant__ Args a) {
   int pS = pitem < a.nitems ? decode(a, pitem).nz + 2 * R : 0;
   auto produce_next = [&](int gp) {
     if (pitem >= a.nitems) return;
-    ok &= produce(a, mp, smem, bars, pitem, ps, gp, recs + (pli & 1) * (ZLMAX + 1), ok);
+    ok &= produce(a, mp, smem, bars, pitem, ps, gp, recs + (pli % 3) * RECN, ok);
     if (++ps == pS) {
       ps = 0;
       ++pli;
@@ -461,6 +557,8 @@ k_pass_tma(const __grid_constant__ Maps mp, const __grid_constant__ Args a) {
   const int vo = yl * TT + xl;
   const size_t plane = (size_t)a.n1p * a.n2 * NB;   // one z-plane of a padded block
   int g = 0, li = 0;
+  int cslot = 0;          // g mod NBUF
+  uint32_t cphase = 0;    // parity of (g / NBUF)
   float2 acc[13][2];
 #pragma unroll
   for (int i = 0; i < 13; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
@@ -468,142 +566,140 @@ k_pass_tma(const __grid_constant__ Maps mp, const __grid_constant__ Args a) {
   for (int item = blockIdx.x; item < a.nitems; item += gridDim.x, ++li) {
     const Item it = decode(a, item);
     const int blk = a.blk0 + it.bi;
-    // projector coefficients of the item's boxes, split into TF32 high and low parts,
-    // in the B-fragment order (lane = 4 orbital + projector); slot MAXG is zero.
-    // The record offsets of the next item go to the buffer the producer left behind.
-    __syncthreads();   // every warp is past the previous item's last use of gcs
-    if (li > 0) stage_recs(a, item + gridDim.x, recs + ((li + 1) & 1) * (ZLMAX + 1));
-    {
-      const int ng = __ldg(a.cng + it.cta);
-      for (int idx = tid; idx < (MAXG + 1) * 32; idx += NCW * 32) {
-        const int gl = idx >> 5, ln = idx & 31;
-        if (gl < ng || gl == MAXG) {
-          float v = 0.f;
-          if (gl < ng) {
-            const int pp = __ldg(a.cproj + ((size_t)it.cta * MAXG + gl) * 4 + (ln & 3));
-            if (pp >= 0) v = __ldg(a.gc + ((size_t)pp * a.nblk_total + blk) * NB + (ln >> 2));
-          }
-          const float hi = tf32_hi(v);
-          gcs[idx] = make_float2(hi, v - hi);
-        }
-      }
-    }
+    // The item's coefficients (gc of its boxes, B-fragment order: lane = 4 orbital +
+    // projector; slot MAXG is zero) were copied at the previous item's start.  Wait for
+    // this thread's copies, then let every warp finish the previous item; then start the
+    // copies of the next item's coefficients and of the tables of the item after it, into
+    // the buffers the previous item has left.
+    cp_async_wait_all();
     __syncthreads();
+    stage_gc(a, item + gridDim.x, cpj + ((li + 1) & 1) * MAXG * 4, gcsb + ((li + 1) & 1) * (GCS_B / 4));
+    stage_cproj(a, item + 2 * gridDim.x, cpj + (li & 1) * MAXG * 4);
+    stage_recs(a, item + 2 * gridDim.x, recs + ((li + 2) % 3) * RECN);
+    cp_async_commit();
+    const float* gcs = gcsb + (li & 1) * (GCS_B / 4);
     const int gx = it.tx0 + xl, gy = it.ty0 + yl;
     const bool v0 = gx < a.n1 && gy < a.n2, v1 = gx < a.n1 && gy + 1 < a.n2;
     float* outp = a.yout + ((size_t)blk * a.ndp + (size_t)gy * a.n1p + gx + R) * NB + 2 * op;
     // ghost copies: nodes x < R repeat at x' = x + n1 + R, nodes x >= n1 - R at x' = x - n1 + R
     const long long gofs = gx < R ? (long long)a.n1 * NB : (gx >= a.n1 - R ? -(long long)a.n1 * NB : 0);
     const int S = it.nz + 2 * R;
-    for (int s0 = 0; s0 < S; s0 += 13) {
+    int ring = 0;   // s mod 13: the accumulator of output z'+d sits in slot (ring + 7 + d) mod 13
+    for (int s = 0; s < S; ++s) {
+      if (producer) produce_next(g + DIST);
+      const int slot = cslot;
+      const unsigned char* st = smem + (size_t)slot * STAGE_B;
+      if (ok && !ptx::mbar_test(bars + slot, cphase) && !ptx::mbar_wait_lim(bars + slot, cphase, a.wait_limit))
+        ok = false;
+      const float* F = reinterpret_cast<const float*>(st);
+      const bool comp = s >= R && s < R + it.nz;
+      float2 f0, f1, d0 = make_float2(0.f, 0.f), d1 = make_float2(0.f, 0.f);
+      if (comp) {
+        // y column of rows yl-6 .. yl+7 at the thread's x; rows 6 and 7 are its nodes
+        float2 col[2 * R + 2];
 #pragma unroll
-      for (int i = 0; i < 13; ++i) {
-        const int s = s0 + i;
-        if (s < S) {
-          if (producer) produce_next(g + DIST);
-          const int slot = g % NBUF;
-          const unsigned char* st = smem + (size_t)slot * STAGE_B;
-          if (ok && !ptx::mbar_wait(bars + slot, (uint32_t)(g / NBUF) & 1u)) ok = false;
-          const float* F = reinterpret_cast<const float*>(st);
-          const bool comp = s >= R && s < R + it.nz;
-          float2 f0, f1;
-          if (comp) {
-            // y column of rows yl-6 .. yl+7 at the thread's x; rows 6 and 7 are its nodes
-            float2 col[2 * R + 2];
+        for (int r = 0; r < 2 * R + 2; ++r) col[r] = lds2(F + fo + (r - R) * FR * NB);
+        f0 = col[R];
+        f1 = col[R + 1];
+        float2 ys0 = __fmul2_rn(a.cy2[1], __fadd2_rn(col[R + 1], col[R - 1]));
+        float2 ys1 = __fmul2_rn(a.cy2[1], __fadd2_rn(col[R + 2], col[R]));
 #pragma unroll
-            for (int r = 0; r < 2 * R + 2; ++r) col[r] = lds2(F + fo + (r - R) * FR * NB);
-            f0 = col[R];
-            f1 = col[R + 1];
-            float2 ys0 = __fmul2_rn(a.cy2[1], __fadd2_rn(col[R + 1], col[R - 1]));
-            float2 ys1 = __fmul2_rn(a.cy2[1], __fadd2_rn(col[R + 2], col[R]));
+        for (int q = 2; q <= R; ++q) {
+          ys0 = __ffma2_rn(a.cy2[q], __fadd2_rn(col[R + q], col[R - q]), ys0);
+          ys1 = __ffma2_rn(a.cy2[q], __fadd2_rn(col[R + 1 + q], col[R + 1 - q]), ys1);
+        }
+        float2 xs0, xs1;
+        {
+          float2 w[2 * R + 1];
 #pragma unroll
-            for (int q = 2; q <= R; ++q) {
-              ys0 = __ffma2_rn(a.cy2[q], __fadd2_rn(col[R + q], col[R - q]), ys0);
-              ys1 = __ffma2_rn(a.cy2[q], __fadd2_rn(col[R + 1 + q], col[R + 1 - q]), ys1);
-            }
-            float2 xs0, xs1;
-            {
-              float2 w[2 * R + 1];
+          for (int q = 0; q <= 2 * R; ++q) w[q] = (q == R) ? f0 : lds2(F + fo + (q - R) * NB);
+          xs0 = __fmul2_rn(a.cx2[1], __fadd2_rn(w[R + 1], w[R - 1]));
 #pragma unroll
-              for (int q = 0; q <= 2 * R; ++q) w[q] = (q == R) ? f0 : lds2(F + fo + (q - R) * NB);
-              xs0 = __fmul2_rn(a.cx2[1], __fadd2_rn(w[R + 1], w[R - 1]));
+          for (int q = 2; q <= R; ++q) xs0 = __ffma2_rn(a.cx2[q], __fadd2_rn(w[R + q], w[R - q]), xs0);
+        }
+        {
+          float2 w[2 * R + 1];
 #pragma unroll
-              for (int q = 2; q <= R; ++q) xs0 = __ffma2_rn(a.cx2[q], __fadd2_rn(w[R + q], w[R - q]), xs0);
-            }
-            {
-              float2 w[2 * R + 1];
+          for (int q = 0; q <= 2 * R; ++q) w[q] = (q == R) ? f1 : lds2(F + fo + FR * NB + (q - R) * NB);
+          xs1 = __fmul2_rn(a.cx2[1], __fadd2_rn(w[R + 1], w[R - 1]));
 #pragma unroll
-              for (int q = 0; q <= 2 * R; ++q) w[q] = (q == R) ? f1 : lds2(F + fo + FR * NB + (q - R) * NB);
-              xs1 = __fmul2_rn(a.cx2[1], __fadd2_rn(w[R + 1], w[R - 1]));
-#pragma unroll
-              for (int q = 2; q <= R; ++q) xs1 = __ffma2_rn(a.cx2[q], __fadd2_rn(w[R + q], w[R - q]), xs1);
-            }
-            const float* Vs = reinterpret_cast<const float*>(st + OFF_V);
-            const float2 cen0 = __fmul2_rn(f2(a.c0s + Vs[vo]), f0);
-            const float2 cen1 = __fmul2_rn(f2(a.c0s + Vs[vo + TT]), f1);
-            // projector term on the tensor cores (3xTF32)
-            float nl[4] = {0.f, 0.f, 0.f, 0.f};
-            {
-              const int* hdr = reinterpret_cast<const int*>(st + OFF_REC);
-              const int r0 = hdr[warp], r1 = hdr[warp + 1], nr = hdr[NCW];
-              const int* ids = hdr + 32;
-              const float4* A = reinterpret_cast<const float4*>(st + OFF_REC + 128 + 4 * ((nr + 3) & ~3));
-              for (int r = r0; r < r1; ++r) {
-                const int id = ids[r];
-                const float4 av = A[r * 32 + lane];
-                const float2 b0 = gcs[(id & 0xFFFF) * 32 + lane], b1 = gcs[(id >> 16) * 32 + lane];
-                const float h0 = tf32_hi(av.x), h1 = tf32_hi(av.y), h2 = tf32_hi(av.z), h3 = tf32_hi(av.w);
-                // low parts a - hi (exact: hi holds the leading bits of a)
-                const float2 l01 = __ffma2_rn(f2(-1.f), make_float2(h0, h1), make_float2(av.x, av.y));
-                const float2 l23 = __ffma2_rn(f2(-1.f), make_float2(h2, h3), make_float2(av.z, av.w));
-                mma_tf32(nl, l01.x, l01.y, l23.x, l23.y, b0.x, b1.x);
-                mma_tf32(nl, h0, h1, h2, h3, b0.y, b1.y);
-                mma_tf32(nl, h0, h1, h2, h3, b0.x, b1.x);
-              }
-            }
-            const float2 d0 = __fadd2_rn(__fadd2_rn(cen0, xs0), __fadd2_rn(ys0, make_float2(nl[0], nl[1])));
-            const float2 d1 = __fadd2_rn(__fadd2_rn(cen1, xs1), __fadd2_rn(ys1, make_float2(nl[2], nl[3])));
-            acc[(i + 7) % 13][0] = __fadd2_rn(acc[(i + 7) % 13][0], d0);
-            acc[(i + 7) % 13][1] = __fadd2_rn(acc[(i + 7) % 13][1], d1);
-          } else {
-            f0 = lds2(F + to);
-            f1 = lds2(F + to + TT * NB);
+          for (int q = 2; q <= R; ++q) xs1 = __ffma2_rn(a.cx2[q], __fadd2_rn(w[R + q], w[R - q]), xs1);
+        }
+        const float* Vs = reinterpret_cast<const float*>(st + OFF_V);
+        const float2 cen0 = __fmul2_rn(f2(a.c0s + Vs[vo]), f0);
+        const float2 cen1 = __fmul2_rn(f2(a.c0s + Vs[vo + TT]), f1);
+        // projector term on the tensor cores (3xTF32); the three products of a round go to
+        // three accumulators, so that consecutive mma.sync do not wait on each other
+        float nl[4] = {0.f, 0.f, 0.f, 0.f}, nla[4] = {0.f, 0.f, 0.f, 0.f}, nlb[4] = {0.f, 0.f, 0.f, 0.f};
+        {
+          const int* hdr = reinterpret_cast<const int*>(st + OFF_REC);
+          const int r0 = hdr[warp], r1 = hdr[warp + 1], nr = hdr[NCW];
+          const int* ids = hdr + 32;
+          const float4* A = reinterpret_cast<const float4*>(st + OFF_REC + 128 + 4 * ((nr + 3) & ~3));
+          for (int r = r0; r < r1; ++r) {
+            const int id = ids[r];
+            const float4 av = A[r * 32 + lane];
+            const float bv0 = gcs[(id & 0xFFFF) * 32 + lane], bv1 = gcs[(id >> 16) * 32 + lane];
+            const float2 bh = make_float2(tf32_hi(bv0), tf32_hi(bv1));
+            const float2 bl = __ffma2_rn(f2(-1.f), bh, make_float2(bv0, bv1));
+            const float2 b0 = make_float2(bh.x, bl.x), b1 = make_float2(bh.y, bl.y);
+            const float h0 = tf32_hi(av.x), h1 = tf32_hi(av.y), h2 = tf32_hi(av.z), h3 = tf32_hi(av.w);
+            // low parts a - hi (exact: hi holds the leading bits of a)
+            const float2 l01 = __ffma2_rn(f2(-1.f), make_float2(h0, h1), make_float2(av.x, av.y));
+            const float2 l23 = __ffma2_rn(f2(-1.f), make_float2(h2, h3), make_float2(av.z, av.w));
+            mma_tf32(nla, l01.x, l01.y, l23.x, l23.y, b0.x, b1.x);
+            mma_tf32(nlb, h0, h1, h2, h3, b0.y, b1.y);
+            mma_tf32(nl, h0, h1, h2, h3, b0.x, b1.x);
           }
-          // z part: plane z' feeds the outputs z' +- d (slot of output z'+d: (i + 7 + d) % 13)
 #pragma unroll
-          for (int d = 1; d < R; ++d) {
-            acc[(i + 7 + d) % 13][0] = __ffma2_rn(a.cz2[d], f0, acc[(i + 7 + d) % 13][0]);
-            acc[(i + 7 + d) % 13][1] = __ffma2_rn(a.cz2[d], f1, acc[(i + 7 + d) % 13][1]);
-          }
-          acc[i % 13][0] = __fmul2_rn(a.cz2[R], f0);     // output z'+6 opens here
-          acc[i % 13][1] = __fmul2_rn(a.cz2[R], f1);
-#pragma unroll
-          for (int d = 1; d <= R; ++d) {
-            acc[(i + 7 - d) % 13][0] = __ffma2_rn(a.cz2[d], f0, acc[(i + 7 - d) % 13][0]);
-            acc[(i + 7 - d) % 13][1] = __ffma2_rn(a.cz2[d], f1, acc[(i + 7 - d) % 13][1]);
-          }
-          // output z'-6 is complete: recurrence epilogue
-          if (s >= 2 * R) {
-            float2 r0 = __fmul2_rn(a.alpha2, acc[(i + 1) % 13][0]);
-            float2 r1 = __fmul2_rn(a.alpha2, acc[(i + 1) % 13][1]);
-            if (a.yprev != nullptr) {
-              const float* P = reinterpret_cast<const float*>(st + OFF_YP);
-              r0 = __ffma2_rn(a.beta2, lds2(P + to), r0);
-              r1 = __ffma2_rn(a.beta2, lds2(P + to + TT * NB), r1);
-            }
-            float* o = outp + (size_t)(it.zs + s - 2 * R) * plane;
-            if (v0) *reinterpret_cast<float2*>(o) = r0;
-            if (v1) *reinterpret_cast<float2*>(o + (size_t)a.n1p * NB) = r1;
-            if (gofs != 0) {
-              if (v0) *reinterpret_cast<float2*>(o + gofs) = r0;
-              if (v1) *reinterpret_cast<float2*>(o + (size_t)a.n1p * NB + gofs) = r1;
-            }
-          }
-          __syncwarp();
-          if (lane == 0) mbar_arrive(bars + NBUF + slot);
-          ++g;
+          for (int c = 0; c < 4; ++c) nl[c] += nla[c] + nlb[c];
+        }
+        d0 = __fadd2_rn(__fadd2_rn(cen0, xs0), __fadd2_rn(ys0, make_float2(nl[0], nl[1])));
+        d1 = __fadd2_rn(__fadd2_rn(cen1, xs1), __fadd2_rn(ys1, make_float2(nl[2], nl[3])));
+      } else {
+        f0 = lds2(F + to);
+        f1 = lds2(F + to + TT * NB);
+      }
+      // z part and the output z' itself, in the ring position's specialisation (only
+      // this part depends on the ring position, so the step body exists once)
+      float2 e0, e1;
+      switch (ring) {
+        case 0: zstep<0>(acc, a.cz2, f0, f1, d0, d1, e0, e1); break;
+        case 1: zstep<1>(acc, a.cz2, f0, f1, d0, d1, e0, e1); break;
+        case 2: zstep<2>(acc, a.cz2, f0, f1, d0, d1, e0, e1); break;
+        case 3: zstep<3>(acc, a.cz2, f0, f1, d0, d1, e0, e1); break;
+        case 4: zstep<4>(acc, a.cz2, f0, f1, d0, d1, e0, e1); break;
+        case 5: zstep<5>(acc, a.cz2, f0, f1, d0, d1, e0, e1); break;
+        case 6: zstep<6>(acc, a.cz2, f0, f1, d0, d1, e0, e1); break;
+        case 7: zstep<7>(acc, a.cz2, f0, f1, d0, d1, e0, e1); break;
+        case 8: zstep<8>(acc, a.cz2, f0, f1, d0, d1, e0, e1); break;
+        case 9: zstep<9>(acc, a.cz2, f0, f1, d0, d1, e0, e1); break;
+        case 10: zstep<10>(acc, a.cz2, f0, f1, d0, d1, e0, e1); break;
+        case 11: zstep<11>(acc, a.cz2, f0, f1, d0, d1, e0, e1); break;
+        default: zstep<12>(acc, a.cz2, f0, f1, d0, d1, e0, e1); break;
+      }
+      // output z'-6 is complete: recurrence epilogue
+      if (s >= 2 * R) {
+        float2 r0 = __fmul2_rn(a.alpha2, e0);
+        float2 r1 = __fmul2_rn(a.alpha2, e1);
+        if (a.yprev != nullptr) {
+          const float* P = reinterpret_cast<const float*>(st + OFF_YP);
+          r0 = __ffma2_rn(a.beta2, lds2(P + to), r0);
+          r1 = __ffma2_rn(a.beta2, lds2(P + to + TT * NB), r1);
+        }
+        float* o = outp + (size_t)(it.zs + s - 2 * R) * plane;
+        if (v0) *reinterpret_cast<float2*>(o) = r0;
+        if (v1) *reinterpret_cast<float2*>(o + (size_t)a.n1p * NB) = r1;
+        if (gofs != 0) {
+          if (v0) *reinterpret_cast<float2*>(o + gofs) = r0;
+          if (v1) *reinterpret_cast<float2*>(o + (size_t)a.n1p * NB + gofs) = r1;
         }
       }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bars + NBUF + slot);
+      ++g;
+      if (++cslot == NBUF) { cslot = 0; cphase ^= 1u; }
+      ring = ring == 12 ? 0 : ring + 1;
     }
   }
   if (!ok && lane == 0) atomicOr(a.status, STATUS_TIMEOUT);
@@ -742,11 +838,17 @@ cudaError_t launch_pass_tma(const sparc_ham* H, const float* Yin, const float* Y
   a.n1p = n1p;
   a.tiles_x = M.tiles_x;
   a.ntiles = M.tiles_x * M.tiles_y;
-  a.nchunk = M.nchunk;
-  a.zl = M.zl;
+  // z-chunks per tile column: whole columns (twelve boundary planes per column) unless
+  // the launch would then have fewer than two items per multiprocessor; chunks of at
+  // least 16 planes and at most ZLMAX
+  const int nsm = std::max(H->ctx->nsm, 1);
+  int nchunk = ceil_div(n3, ZLMAX);
+  while (a.ntiles * nchunk * nb < 2 * nsm && n3 / (nchunk + 1) >= 16) ++nchunk;
+  a.nchunk = nchunk;
+  a.zl = ceil_div(n3, nchunk);
   a.blk0 = blk0;
   a.nblk_total = nblk_total;
-  a.nitems = a.ntiles * M.nchunk * nb;
+  a.nitems = a.ntiles * nchunk * nb;
   a.ndp = padded_nd(H);
   std::memcpy(a.yseg, M.yseg, sizeof(a.yseg));
   for (int p = 0; p <= R; ++p) {
@@ -767,9 +869,12 @@ cudaError_t launch_pass_tma(const sparc_ham* H, const float* Yin, const float* Y
   a.rec = M.d_rec;
   a.stream = (const unsigned char*)M.d_stream;
   a.status = H->ctx->d_status;
+  a.wait_limit = H->ctx->inject_wait_limit > 0 ? H->ctx->inject_wait_limit : (1LL << 32);
+  a.stall = H->ctx->inject_stall;
+  H->ctx->inject_stall = -1;   // one launch
   cudaError_t e = cudaFuncSetAttribute(k_pass_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_B);
   if (e != cudaSuccess) return e;
-  const int grid = std::min(a.nitems, std::max(H->ctx->nsm, 1));
+  const int grid = std::min(a.nitems, nsm);
   cudaEvent_t t0 = timing_begin(H->ctx, st);
   k_pass_tma<<<grid, NTHR, SMEM_B, st>>>(mp, a);
   ++H->ctx->launches;

@@ -33,6 +33,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
     if (clock64() - t0 > (1LL << 32)) return false;
   return true;
 }
+// The same with a limit of `limit` SM clocks.
+__device__ __forceinline__ bool mbar_wait_lim(uint64_t* b, uint32_t parity, long long limit) {
+  const long long t0 = clock64();
+  while (!mbar_test(b, parity))
+    if (clock64() - t0 > limit) return false;
+  return true;
+}
 // One arrival on b that also raises its expected transaction count by `bytes`.
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");

@@ -399,6 +399,154 @@ k_jacobi_round(const TW* __restrict__ A, TW* __restrict__ An, TW* __restrict__ V
   }
 }
 
+// ------------------------------------------------------------------ block Jacobi (FP32)
+// The parallel cyclic Jacobi method on index blocks of BJ = 16: the npad/BJ blocks are
+// paired round-robin (the scalar method's ordering on blocks), and a round rotates
+// every pair's 32 x 32 subproblem A[I, I] (I = the pair's two blocks) by one inner
+// cyclic sweep, accumulated into an orthogonal W_I, then applies all of them at once:
+// A <- J^T A J and V <- V J with J = blockdiag(W_I).  A sweep is npad/BJ - 1 rounds
+// instead of the scalar method's npad - 1, each two launches of a few microseconds.
+constexpr int BJ = 16;
+
+// local index l of pair k's 32 indices -> global index
+__device__ __forceinline__ int bj_index(int l, int bp, int bq) { return l < BJ ? BJ * bp + l : BJ * bq + (l - BJ); }
+
+// One CTA per block pair: W = the product of the rotations of one cyclic sweep over the
+// pair's 32 x 32 subproblem (rotations as jacobi_rot; indices >= n give the identity).
+__global__ void __launch_bounds__(256) k_bj_pair(const float* __restrict__ A, float* __restrict__ Wbuf, int n,
+                                                 int nbk, int r) {
+  __shared__ float S[2 * BJ][2 * BJ + 1];
+  __shared__ float W[2 * BJ][2 * BJ + 1];
+  __shared__ float rc[BJ], rs[BJ];
+  __shared__ int rp[BJ], rq[BJ];
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  const int k = blockIdx.x;
+  const int bp = rr_player(k, r, nbk), bq = rr_player(nbk - 1 - k, r, nbk);
+  const int t = threadIdx.x;
+  for (int e = t; e < 4 * BJ * BJ; e += 256) {
+    const int i = e % (2 * BJ), j = e / (2 * BJ);
+    const int gi = bj_index(i, bp, bq), gj = bj_index(j, bp, bq);
+    S[i][j] = (gi < n && gj < n) ? A[gi + (long long)gj * n] : (gi == gj ? 1.f : 0.f);
+    W[i][j] = (i == j) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  for (int rr = 0; rr < 2 * BJ - 1; ++rr) {
+    if (t < BJ) {
+      const int p = rr_player(t, rr, 2 * BJ), q = rr_player(2 * BJ - 1 - t, rr, 2 * BJ);
+      float c = 1.f, sn = 0.f;
+      const int gp = bj_index(p, bp, bq), gq = bj_index(q, bp, bq);
+      const float b = S[p][q];
+      if (gp < n && gq < n && b != 0.f) {
+        const float th = (S[q][q] - S[p][p]) / (2.f * b);
+        const float tt = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(th * th + 1.f));
+        c = 1.f / sqrtf(tt * tt + 1.f);
+        sn = tt * c;
+      }
+      rc[t] = c; rs[t] = sn; rp[t] = p; rq[t] = q;
+    }
+    __syncthreads();
+    {   // S <- R^T S R on the 2 x 2 block (pair x, pair y)
+      const int x = t % BJ, y = t / BJ;
+      const int i0 = rp[x], i1 = rq[x], j0 = rp[y], j1 = rq[y];
+      const float cx = rc[x], sx = rs[x], cy = rc[y], sy = rs[y];
+      const float a00 = S[i0][j0], a01 = S[i0][j1], a10 = S[i1][j0], a11 = S[i1][j1];
+      // rows: [r0; r1] = [[c, -s], [s, c]] [a0; a1] (the rotation [[c, s], [-s, c]] transposed)
+      const float b00 = cx * a00 - sx * a10, b01 = cx * a01 - sx * a11;
+      const float b10 = sx * a00 + cx * a10, b11 = sx * a01 + cx * a11;
+      __syncthreads();
+      S[i0][j0] = cy * b00 - sy * b01;
+      S[i0][j1] = sy * b00 + cy * b01;
+      S[i1][j0] = cy * b10 - sy * b11;
+      S[i1][j1] = sy * b10 + cy * b11;
+    }
+    // W <- W R (columns p, q)
+    for (int e = t; e < 2 * BJ * BJ; e += 256) {
+      const int i = e % (2 * BJ), x = e / (2 * BJ);
+      const int p = rp[x], q = rq[x];
+      const float w0 = W[i][p], w1 = W[i][q];
+      W[i][p] = rc[x] * w0 - rs[x] * w1;
+      W[i][q] = rs[x] * w0 + rc[x] * w1;
+    }
+    __syncthreads();
+  }
+  float* Wk = Wbuf + (size_t)k * 4 * BJ * BJ;
+  for (int e = t; e < 4 * BJ * BJ; e += 256) Wk[e] = W[e % (2 * BJ)][e / (2 * BJ)];
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+// A' = J^T A J (into An) and V <- V J for J = blockdiag(W_k): CTAs [0, np^2) compute the
+// 32 x 32 block (pair a, pair b) of A' = W_a^T A[I_a, I_b] W_b; the others the 32-row
+// blocks of V[:, I_k] W_k.
+__global__ void __launch_bounds__(256) k_bj_apply(const float* __restrict__ A, float* __restrict__ An, float* V,
+                                                  const float* __restrict__ Wbuf, int n, int nbk, int r) {
+  __shared__ float X[2 * BJ][2 * BJ + 1];
+  __shared__ float Wl[2 * BJ][2 * BJ + 1];
+  __shared__ float Wr[2 * BJ][2 * BJ + 1];
+  __shared__ float Tm[2 * BJ][2 * BJ + 1];
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  const int np = nbk / 2;
+  const int t = threadIdx.x;
+  const int bid = blockIdx.x;
+  if (bid < np * np) {
+    const int ka = bid % np, kb = bid / np;
+    const int ap = rr_player(ka, r, nbk), aq = rr_player(nbk - 1 - ka, r, nbk);
+    const int bp = rr_player(kb, r, nbk), bq = rr_player(nbk - 1 - kb, r, nbk);
+    const float* Wa = Wbuf + (size_t)ka * 4 * BJ * BJ;
+    const float* Wb = Wbuf + (size_t)kb * 4 * BJ * BJ;
+    for (int e = t; e < 4 * BJ * BJ; e += 256) {
+      const int i = e % (2 * BJ), j = e / (2 * BJ);
+      const int gi = bj_index(i, ap, aq), gj = bj_index(j, bp, bq);
+      X[i][j] = (gi < n && gj < n) ? A[gi + (long long)gj * n] : 0.f;
+      Wl[i][j] = Wa[e];
+      Wr[i][j] = Wb[e];
+    }
+    __syncthreads();
+    // each thread: 4 entries (rows i0 .. i0+3, column j) of T = X W_b, then of W_a^T T
+    const int j = t % (2 * BJ), i0 = (t / (2 * BJ)) * 4;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      float acc = 0.f;
+#pragma unroll 8
+      for (int l = 0; l < 2 * BJ; ++l) acc = fmaf(X[i0 + u][l], Wr[l][j], acc);
+      Tm[i0 + u][j] = acc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u;
+      float acc = 0.f;
+#pragma unroll 8
+      for (int l = 0; l < 2 * BJ; ++l) acc = fmaf(Wl[l][i], Tm[l][j], acc);
+      const int gi = bj_index(i, ap, aq), gj = bj_index(j, bp, bq);
+      if (gi < n && gj < n) An[gi + (long long)gj * n] = acc;
+    }
+  } else {
+    const int vb = bid - np * np;
+    const int rows = (n + 2 * BJ - 1) / (2 * BJ);
+    const int rb = vb % rows, k = vb / rows;
+    const int bp = rr_player(k, r, nbk), bq = rr_player(nbk - 1 - k, r, nbk);
+    const float* Wk = Wbuf + (size_t)k * 4 * BJ * BJ;
+    for (int e = t; e < 4 * BJ * BJ; e += 256) {
+      const int i = e % (2 * BJ), j = e / (2 * BJ);
+      const int gr = rb * 2 * BJ + i, gj = bj_index(j, bp, bq);
+      X[i][j] = (gr < n && gj < n) ? V[gr + (long long)gj * n] : 0.f;
+      Wl[i][j] = Wk[e];
+    }
+    __syncthreads();
+    const int j = t % (2 * BJ), i0 = (t / (2 * BJ)) * 4;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u;
+      float acc = 0.f;
+#pragma unroll 8
+      for (int l = 0; l < 2 * BJ; ++l) acc = fmaf(X[i][l], Wl[l][j], acc);
+      const int gr = rb * 2 * BJ + i, gj = bj_index(j, bp, bq);
+      if (gr < n && gj < n) V[gr + (long long)gj * n] = acc;
+    }
+  }
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 // out = in^T (n x n, column-major)
 __global__ void k_transpose(const double* __restrict__ in, double* __restrict__ out, int n) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -609,17 +757,26 @@ sparc_status chol_inverse(sparc_ctx* ctx, TW* A, TW* Li, int n, TW* Dinv, TW* tm
 
 // Parallel cyclic Jacobi on the n x n Hermitian A (ping-pong A0/A1, eigenvectors in V),
 // two sweeps per replay of a captured CUDA graph, until off(A) <= tol * |A|.
+// Whether the block Jacobi method takes an n x n problem of element type TJ.
+template <class TJ>
+constexpr bool bj_type() { return std::is_same<TJ, float>::value; }
+inline bool bj_usable(int n) { return n % (2 * BJ) == 0 && n >= 4 * BJ; }
+
 template <class TJ>
 sparc_status jacobi(sparc_ctx* ctx, TJ* A0, TJ* A1, TJ* V, int n, double tol, int max_sweeps, double* scal,
-                    TJ** result, int* sweeps_out, cudaStream_t st) {
+                    TJ** result, int* sweeps_out, cudaStream_t st, float* Wbuf = nullptr) {
+  const bool blockj = bj_type<TJ>() && Wbuf != nullptr && bj_usable(n);
   const int npad = n + (n & 1);
   const int half = npad / 2;
   const int nblocks = ((half + 15) / 16) * ((half + 15) / 16) + ((n + 63) / 64) * ((half + 3) / 4);
-  const int rounds = 2 * (npad - 1);
+  const int nbk = n / BJ, npair = nbk / 2;
+  // two sweeps per graph: 2 (npad - 1) scalar rounds, or 2 (nbk - 1) block rounds of two launches
+  const int rounds = blockj ? 2 * (nbk - 1) : 2 * (npad - 1);
   if (!ctx->cap_stream) {
     SPARC_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
   }
-  const auto key = std::make_tuple((int)sizeof(TJ) * 2 + (int)Tr<TJ>::cplx, n, (void*)A0, (void*)A1, (void*)V);
+  const auto key = std::make_tuple((int)sizeof(TJ) * 2 + (int)Tr<TJ>::cplx + (blockj ? 64 : 0), n, (void*)A0,
+                                   (void*)A1, (void*)V);
   cudaGraphExec_t ge = nullptr;
   auto it = ctx->graphs.find(key);
   if (it != ctx->graphs.end()) {
@@ -642,7 +799,21 @@ sparc_status jacobi(sparc_ctx* ctx, TJ* A0, TJ* A1, TJ* V, int n, double tol, in
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     for (int r = 0; r < rounds; ++r) {
-      cudaError_t le = cudaLaunchKernelEx(&cfg, k_jacobi_round<TJ>, (const TJ*)a, b, V, n, npad, r % (npad - 1));
+      cudaError_t le = cudaSuccess;
+      if (blockj) {
+        if constexpr (bj_type<TJ>()) {
+          cudaLaunchConfig_t c1 = cfg, c2 = cfg;
+          c1.gridDim = dim3((unsigned)npair);
+          c2.gridDim = dim3((unsigned)(npair * npair + ((n + 2 * BJ - 1) / (2 * BJ)) * npair));
+          const int rb = r % (nbk - 1);
+          le = cudaLaunchKernelEx(&c1, k_bj_pair, (const float*)a, Wbuf, n, nbk, rb);
+          if (le == cudaSuccess)
+            le = cudaLaunchKernelEx(&c2, k_bj_apply, (const float*)a, (float*)b, (float*)V, (const float*)Wbuf, n, nbk,
+                                    rb);
+        }
+      } else {
+        le = cudaLaunchKernelEx(&cfg, k_jacobi_round<TJ>, (const TJ*)a, b, V, n, npad, r % (npad - 1));
+      }
       if (le != cudaSuccess) {
         cudaStreamEndCapture(ctx->cap_stream, &g);
         if (g) cudaGraphDestroy(g);
@@ -663,7 +834,7 @@ sparc_status jacobi(sparc_ctx* ctx, TJ* A0, TJ* A1, TJ* V, int n, double tol, in
   cudaEvent_t tj = timing_begin(ctx, st);
   while (sweeps < max_sweeps && !converged) {
     SPARC_CUDA(ctx, cudaGraphLaunch(ge, st));
-    ctx->launches += rounds;
+    ctx->launches += blockj ? 2 * rounds : rounds;
     sweeps += 2;
     const int nbo = ceil_div(n, 8);
     k_offnorm<TJ><<<nbo, 256, 0, st>>>(A0, n, scal + 2);
@@ -705,8 +876,10 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
   const size_t tcb = TCP ? align256(std::max(tc::gram_scratch_bytes(ctx, ns, nd), tc::rot_scratch_bytes(ns))) : 0;
   const size_t w1b = TCP ? hub : 0;   // U1, the orthonormalised basis
   const size_t gsb = apply_scratch_bytes(H, DtypeOf<T>::v, ns);   // projection scratch of the H-apply
+  // rotations of the block Jacobi rounds (FP32 subproblems of the mixed mode)
+  const size_t wjb = (bj_type<TS>() && bj_usable(ns)) ? align256((size_t)(ns / BJ / 2) * 4 * BJ * BJ * sizeof(float)) : 0;
   const size_t extra = hub + 2 * partb + 10 * sm + dinvb + align256(nn * es) + 3 * align256(nn * sizeof(TS)) +
-                       align256(ns * sizeof(double)) + tcb + w1b + gsb + 256;
+                       align256(ns * sizeof(double)) + tcb + w1b + gsb + wjb + 256;
   BlockWs w;
   char* tail = nullptr;
   sparc_status s = block_ws(H, DtypeOf<T>::v, ns, extra, &w, &tail);
@@ -732,6 +905,7 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
   TS* SV = (TS*)tail; tail += align256(nn * sizeof(TS));
   double* lam = (double*)tail; tail += align256(ns * sizeof(double));
   void* tcs = tail; tail += tcb;
+  float* Wjb = wjb ? (float*)tail : nullptr; tail += wjb;
   T* W1 = (T*)tail;
   const long long pcap = (long long)(partb / ew);
 
@@ -827,7 +1001,7 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
     ++ctx->launches;
     SPARC_LAUNCH(ctx, "subspace matrix");
     TS* Sres = nullptr;
-    s = jacobi<TS>(ctx, S0, S1, SV, ns, 1e-10, 40, scal, &Sres, &sweeps, st);
+    s = jacobi<TS>(ctx, S0, S1, SV, ns, 1e-10, 40, scal, &Sres, &sweeps, st, Wjb);
     if (s != SPARC_OK) return s;
     k_convert<TS, TW><<<ceil_div(nn, 256), 256, 0, st>>>(SV, A1, nn);
     ++ctx->launches;

@@ -707,7 +707,7 @@ static sparc_status poisson(sparc_scf* S, cudaStream_t st, int* iters) {
   ctx->launches += 8;
   double* part2 = S->d_part + 2 * (size_t)nb;
   int it = 0;
-  const int batch = 25, max_it = 4000;
+  const int batch = 25, max_it = ctx->inject_cg_max > 0 ? ctx->inject_cg_max : 4000;
   double hs[2] = {0.0, 0.0};
   while (it < max_it) {
     for (int q = 0; q < batch; ++q, ++it) {

@@ -73,6 +73,10 @@ static void timing_reset(sparc_ctx* ctx) {
 
 bool ensure_ws(sparc_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->ws_bytes) return true;
+  if (ctx->inject_alloc_fail > 0) {   // injected failure: the workspace is left as it is
+    --ctx->inject_alloc_fail;
+    return false;
+  }
   if (ctx->ws) {
     cudaDeviceSynchronize();
     cudaFree(ctx->ws);
@@ -536,6 +540,17 @@ sparc_status sparc_last_sweeps(const sparc_ctx* ctx, int* sweeps) {
   if (!ctx || !sweeps) return SPARC_ERR_INVALID_ARG;
   *sweeps = ctx->last_sweeps;
   return SPARC_OK;
+}
+
+sparc_status sparc_debug_inject(sparc_ctx* ctx, int what, int64_t value) {
+  if (!ctx) return SPARC_ERR_INVALID_ARG;
+  switch (what) {
+    case SPARC_INJECT_ALLOC_FAIL: ctx->inject_alloc_fail = (int)std::max<int64_t>(0, value); return SPARC_OK;
+    case SPARC_INJECT_WAIT_LIMIT: ctx->inject_wait_limit = std::max<int64_t>(0, value); return SPARC_OK;
+    case SPARC_INJECT_STALL: ctx->inject_stall = value < 0 ? -1 : (int)value; return SPARC_OK;
+    case SPARC_INJECT_CG_MAX_ITERS: ctx->inject_cg_max = (int)std::max<int64_t>(0, value); return SPARC_OK;
+  }
+  return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_debug_inject: unknown injection");
 }
 
 sparc_status sparc_launch_count(const sparc_ctx* ctx, int64_t* launches) {

@@ -31,7 +31,7 @@ EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_sync", "s
            "sparc_set_filter_units", "sparc_filter_graph_create", "sparc_filter_graph_set_bounds",
            "sparc_filter_graph_launch", "sparc_filter_graph_destroy", "sparc_scf_set_density",
            "sparc_mlp_create", "sparc_mlp_params", "sparc_mlp_descriptors", "sparc_mlp_forward", "sparc_mlp_grad",
-           "sparc_mlp_train_step", "sparc_mlp_destroy", "sparc_scf_create_k"]
+           "sparc_mlp_train_step", "sparc_mlp_destroy", "sparc_scf_create_k", "sparc_debug_inject"]
 TIMED = {"hpass": 0, "gather": 1, "gram": 2, "eig": 3, "rotation": 4, "jacobi": 5, "fpass": 6}
 
 
@@ -101,6 +101,8 @@ def load(path: str = LIB_PATH):
     L.sparc_launch_count.argtypes = [c_void_p, POINTER(c_int64)]
     L.sparc_last_sweeps.argtypes = [c_void_p, POINTER(c_int)]
     L.sparc_last_sweeps.restype = c_int
+    L.sparc_debug_inject.argtypes = [c_void_p, c_int, c_int64]
+    L.sparc_debug_inject.restype = c_int
     L.sparc_apply_H_noalloc.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_int, c_int64, c_void_p]
     L.sparc_apply_H_noalloc.restype = c_int
     L.sparc_launch_count.restype = c_int
@@ -221,6 +223,12 @@ class Context:
         n = c_int()
         self.check(load().sparc_last_sweeps(self.handle, ctypes.byref(n)))
         return n.value
+
+    def inject(self, what: str, value: int):
+        """Failure injection for tests of the error paths (sparc_debug_inject):
+        what = 'alloc_fail' | 'wait_limit' | 'stall' | 'cg_max_iters'."""
+        code = {"alloc_fail": 1, "wait_limit": 2, "stall": 3, "cg_max_iters": 4}[what]
+        self.check(load().sparc_debug_inject(self.handle, code, int(value)))
 
     def launches(self) -> int:
         """Kernels launched by this context so far (sparc_launch_count)."""
