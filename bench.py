@@ -44,9 +44,15 @@ def _args():
     ap.add_argument("--no-kpoints", action="store_true",
                     help="skip the batched filters: 27 k-points (complex64) and 16 uneven cells (FP32 graph)")
     ap.add_argument("--cpu-sample-cols", type=int, default=1)
-    ap.add_argument("--mode", choices=["step", "filter", "kpoints"], default="step",
+    ap.add_argument("--mode", choices=["step", "filter", "kpoints", "learned"], default="step",
                     help="filter: only the Chebyshev filter (for profiler captures); "
-                         "kpoints: the 27-k-point complex64 filter alone")
+                         "kpoints: the 27-k-point complex64 filter alone; "
+                         "learned: the learned initial density trained on --train-cells cells, "
+                         "judged on --heldout others")
+    ap.add_argument("--train-cells", type=int, default=500, help="learned mode: training cells")
+    ap.add_argument("--heldout", type=int, default=50, help="learned mode: held-out cells")
+    ap.add_argument("--epochs", type=int, default=20, help="learned mode: training epochs")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 filter arm of the step line")
     ap.add_argument("--ns", type=int, default=None, help="orbitals (filter mode; default: the cell's 512)")
     ap.add_argument("--no-tune", action="store_true",
                     help="kpoints mode: the cost model's launch grouping, no autotuning (profiler captures)")
@@ -353,6 +359,69 @@ def fp64_filter_throughput(sparc, synth, torch, ctx, H, wl, X32, reps=2):
     return out
 
 
+def run_learned(args):
+    """The learned initial density at the scale of the 500-cell study: the network is
+    trained (the library's kernels) on the converged densities of `--train-cells`
+    seeded 32-atom cells and judged on `--heldout` other cells by the mixed SCF's
+    iterations to a V residual of 1e-6 from the atomic superposition and from the
+    prediction, and by the final free energies.  Prints one JSON line."""
+    import statistics as stt
+    import time as _t
+    import torch
+    from paper_1603_04339_gb300 import build, synth
+    build.build()
+    from paper_1603_04339_gb300 import sparc
+    from paper_1603_04339_gb300 import learned_density as LD
+    ctx = sparc.Context(0)
+    t0 = _t.perf_counter()
+    D, T, runs = LD.dataset(ctx, range(2000, 2000 + args.train_cells), torch.float32)
+    t_data = _t.perf_counter() - t0
+    t0 = _t.perf_counter()
+    net, scale, lhist = LD.train(ctx, D, T, epochs=args.epochs)
+    torch.cuda.synchronize()
+    t_train = _t.perf_counter() - t0
+    del D, T
+    torch.cuda.empty_cache()
+    cells = []
+    for seed in range(3000, 3000 + args.heldout):
+        sysd = synth.scf_fcc32(seed=seed)
+        base = LD.converge(ctx, sysd, torch.float32, tol=1e-6)
+        y = LD.predict(ctx, net, sysd)
+        lrn = LD.converge(ctx, sysd, torch.float32, tol=1e-6, dy=y, scale=scale)
+        rho_c = base.rho
+        starts = {"atomic": (-base.b).clamp(min=0.0), "learned": (-base.b + scale * y.double()).clamp(min=0.0)}
+        err = {k: float((v * (rho_c.sum() / v.sum()) - rho_c).norm() / rho_c.norm()) for k, v in starts.items()}
+        cells.append({"seed": seed, "iters_atomic": base.iterations_to(1e-6), "iters_learned": lrn.iterations_to(1e-6),
+                      "iters3_atomic": base.iterations_to(1e-3), "iters3_learned": lrn.iterations_to(1e-3),
+                      "seconds_atomic": base.seconds, "seconds_learned": lrn.seconds,
+                      "dF_per_atom": abs(base.free_energy - lrn.free_energy) / 32.0,
+                      "start_err_atomic": err["atomic"], "start_err_learned": err["learned"]})
+    ctx.close()
+
+    def ms(key):
+        v = [c[key] for c in cells if c[key] is not None]
+        return {"mean": stt.mean(v), "sd": stt.stdev(v) if len(v) > 1 else 0.0, "n": len(v)}
+
+    diff = [c["iters_atomic"] - c["iters_learned"] for c in cells
+            if c["iters_atomic"] is not None and c["iters_learned"] is not None]
+    dmean = stt.mean(diff)
+    dsd = stt.stdev(diff) if len(diff) > 1 else 0.0
+    out = {"mode": "learned",
+           "workload": "32-atom perturbed-FCC cells, 36^3 grid h=0.45, Z=3, Ns=72, m=20, mixed SCF to V residual 1e-6",
+           "train_cells": args.train_cells, "heldout_cells": args.heldout, "epochs": args.epochs,
+           "data_seconds": t_data, "train_seconds": t_train, "loss_initial": lhist[0], "loss_final": lhist[-1],
+           "iters_to_1e-6": {"atomic": ms("iters_atomic"), "learned": ms("iters_learned"),
+                             "saved_mean": dmean, "saved_sd": dsd,
+                             "saved_t": dmean / (dsd / len(diff) ** 0.5) if dsd > 0 else None},
+           "iters_to_1e-3": {"atomic": ms("iters3_atomic"), "learned": ms("iters3_learned")},
+           "seconds_to_1e-6": {"atomic": ms("seconds_atomic"), "learned": ms("seconds_learned")},
+           "start_density_rel_error": {"atomic": ms("start_err_atomic"), "learned": ms("start_err_learned")},
+           "dF_per_atom": {"max": max(c["dF_per_atom"] for c in cells), "mean": stt.mean(c["dF_per_atom"] for c in cells)},
+           "cells": cells}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_kpoints(args):
     import json as _json
     import torch
@@ -627,7 +696,8 @@ def run_ours(args):
                                   "jacobi_sweeps": sweeps},
         "filter_only": {"value": units / ((fp_ms + ga_ms) / args.steps * 1e-3) / 1e9, "unit": UNIT},
         "clocks": ck, "e2e": e2e, "gpu_launches": int(launches), "cpu_baseline": cpu,
-        "filter_fp64_vs_fp32": None if world > 1 else fp64_filter_throughput(sparc, synth, torch, ctx, H, wl, X),
+        "filter_fp64_vs_fp32": None if (world > 1 or args.no_fp64) else fp64_filter_throughput(sparc, synth, torch,
+                                                                                                 ctx, H, wl, X),
         "scf": None if (args.no_scf or world > 1) else scf_time_to_solution(sparc, synth, torch),
         "kpoints": None if (args.no_kpoints or world > 1) else kpoint_filter_throughput(sparc, synth, torch, ctx),
         "cells": None if (args.no_kpoints or world > 1) else cell_batch_throughput(sparc, synth, torch, ctx),
@@ -681,6 +751,8 @@ def main():
         return run_filter_only(args)
     if args.mode == "kpoints":
         return run_kpoints(args)
+    if args.mode == "learned":
+        return run_learned(args)
     return run_ours(args)
 
 

@@ -397,12 +397,15 @@ sparc_status sparc_scf_read(const sparc_scf* S, int which, double* dst, void* st
 sparc_status sparc_scf_set_density(sparc_scf* S, const float* dy, double scale, void* stream);
 void sparc_scf_destroy(sparc_scf* S);
 /* Atomic forces at the state of the last sparc_scf_step (Section 3.6): U are its
- * rotated orbitals (F64 or F32, Gamma point, one k-point), with its occupations and electrostatic
- * potential.  f_host (host, 9*natom doubles): [0, 3 natom) the forces, then the local
- * (Eq. LocalForce:Discrete) and the nonlocal (Eq. NonlocForce:Discrete, the projector
- * derivative moved onto nabla_h psi) parts, 3 per atom, Ha/bohr; the overlap
- * correction f_c is zero (E_c = 0).  Needs sparc_scf_desc.proj_atom when H has
- * projectors.  Synchronises `stream`. */
+ * rotated orbitals, with its occupations and electrostatic potential: F64 or F32 at
+ * the Gamma point (one k-point), or C128 / C64 Bloch orbitals of every k-point of S
+ * (nk consecutive ns x ld blocks, as sparc_scf_step takes them).  f_host (host,
+ * 9*natom doubles): [0, 3 natom) the forces, then the local (Eq. LocalForce:Discrete)
+ * and the nonlocal (Eq. NonlocForce:Discrete, the projector derivative moved onto
+ * nabla_h psi; for Bloch orbitals with the image phases of Eq. NonlocalPS:FD, the
+ * Bloch-wrapped gradient and the k-point weights) parts, 3 per atom, Ha/bohr; the
+ * overlap correction f_c is zero (E_c = 0).  Needs sparc_scf_desc.proj_atom when H
+ * has projectors.  Synchronises `stream`. */
 sparc_status sparc_scf_forces(sparc_scf* S, sparc_dtype dtype, const void* U, int ns, int64_t ld, double* f_host,
                               void* stream);
 

@@ -199,19 +199,22 @@ __global__ void __launch_bounds__(256) k_chol_blk(double* A, long long lda, doub
   __shared__ double S[MB][MB + 1];
   __shared__ double x[MB];
   __shared__ double rdiag[MB];   // 1 / L_jj, one FP64 division per column (thread 0)
+  __shared__ double a0[MB];      // the block's diagonal before the factorisation
   __shared__ int bad;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) bad = 0;
   for (int e = tid; e < kb * kb; e += nt) {
     const int i = e % kb, j = e / kb;
-    S[i][j] = i >= j ? A[i + (long long)j * lda] : 0.0;
+    const double v = i >= j ? A[i + (long long)j * lda] : 0.0;
+    S[i][j] = v;
+    if (i == j) a0[i] = v;
   }
   __syncthreads();
   for (int j = 0; j < kb; ++j) {
     if (tid == 0) {
       // S[j][j] holds a_jj minus the updates of the columns before j
       const double d = S[j][j];
-      const double ajj = A[j + (long long)j * lda];
+      const double ajj = a0[j];
       if (!(d > 1e-14 * ajj) || !isfinite(d)) {
         bad = 1;
         atomicOr(status, STATUS_NOT_POSDEF);
@@ -501,23 +504,25 @@ __global__ void __launch_bounds__(256) k_bj_apply(const float* __restrict__ A, f
       Wr[i][j] = Wb[e];
     }
     __syncthreads();
-    // each thread: 4 entries (rows i0 .. i0+3, column j) of T = X W_b, then of W_a^T T
-    const int j = t % (2 * BJ), i0 = (t / (2 * BJ)) * 4;
+    // each thread: 4 entries (row i, columns j0 .. j0+3) of T = X W_b, then of W_a^T T;
+    // a warp covers the 32 rows of a column, so its stores into column-major A' coalesce
+    const int i = t % (2 * BJ), j0 = (t / (2 * BJ)) * 4;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       float acc = 0.f;
 #pragma unroll 8
-      for (int l = 0; l < 2 * BJ; ++l) acc = fmaf(X[i0 + u][l], Wr[l][j], acc);
-      Tm[i0 + u][j] = acc;
+      for (int l = 0; l < 2 * BJ; ++l) acc = fmaf(X[i][l], Wr[l][j0 + u], acc);
+      Tm[i][j0 + u] = acc;
     }
     __syncthreads();
+    const int gi = bj_index(i, ap, aq);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int i = i0 + u;
+      const int j = j0 + u;
       float acc = 0.f;
 #pragma unroll 8
       for (int l = 0; l < 2 * BJ; ++l) acc = fmaf(Wl[l][i], Tm[l][j], acc);
-      const int gi = bj_index(i, ap, aq), gj = bj_index(j, bp, bq);
+      const int gj = bj_index(j, bp, bq);
       if (gi < n && gj < n) An[gi + (long long)gj * n] = acc;
     }
   } else {
@@ -533,14 +538,15 @@ __global__ void __launch_bounds__(256) k_bj_apply(const float* __restrict__ A, f
       Wl[i][j] = Wk[e];
     }
     __syncthreads();
-    const int j = t % (2 * BJ), i0 = (t / (2 * BJ)) * 4;
+    const int i = t % (2 * BJ), j0 = (t / (2 * BJ)) * 4;
+    const int gr = rb * 2 * BJ + i;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int i = i0 + u;
+      const int j = j0 + u;
       float acc = 0.f;
 #pragma unroll 8
       for (int l = 0; l < 2 * BJ; ++l) acc = fmaf(X[i][l], Wl[l][j], acc);
-      const int gr = rb * 2 * BJ + i, gj = bj_index(j, bp, bq);
+      const int gj = bj_index(j, bp, bq);
       if (gr < n && gj < n) V[gr + (long long)gj * n] = acc;
     }
   }
@@ -672,6 +678,14 @@ __global__ void k_rayleigh(const TW* __restrict__ Qm, const TW* __restrict__ Z, 
     den += Tr<TW>::abs2(q);
   }
   lam[i] = num / den;
+}
+
+// G <- (3 I - G) / 2 (n x n): the Newton-Schulz factor from the Gram G = V^T V.
+__global__ void k_ns_coef(double* G, int n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n * n) return;
+  const int i = (int)(t % n), j = (int)(t / n);
+  G[t] = (i == j ? 1.5 : 0.0) - 0.5 * G[t];
 }
 
 template <class TA, class TB>
@@ -1003,13 +1017,25 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
     TS* Sres = nullptr;
     s = jacobi<TS>(ctx, S0, S1, SV, ns, 1e-10, 40, scal, &Sres, &sweeps, st, Wjb);
     if (s != SPARC_OK) return s;
-    k_convert<TS, TW><<<ceil_div(nn, 256), 256, 0, st>>>(SV, A1, nn);
-    ++ctx->launches;
     // FP32 Jacobi vectors are orthonormal to about (rotations per vector) x u32; one
-    // Newton-Schulz step in FP64, V <- V (3 I - V^H V) / 2, squares that error
-    SPARC_CUDA(ctx, (gemm64<TW, true, false>(ctx, ns, ns, ns, A1, ns, A1, ns, T1, ns, 1.0, 0.0, partH, pcap, st)));
-    SPARC_CUDA(ctx, cudaMemcpyAsync(Vj, A1, nn * sizeof(TW), cudaMemcpyDeviceToDevice, st));
-    SPARC_CUDA(ctx, (gemm64<TW, false, false>(ctx, ns, ns, ns, A1, ns, T1, ns, Vj, ns, -0.5, 1.5, partH, pcap, st)));
+    // Newton-Schulz step, V <- V (3 I - V^H V) / 2, squares that error
+    if constexpr (TCP) {
+      // real data: the step on the tensor cores (3xTF32 Gram with FP64 sums, 3xTF32
+      // product): V ends orthonormal to about 1e-7, below the FP32 rounding of the
+      // orbitals it rotates
+      SPARC_CUDA(ctx, tc::gram(ctx, (const float*)SV, ns, (const float*)SV, ns, ns, ns, (double*)T1, tcs, st));
+      k_ns_coef<<<ceil_div(nn, 256), 256, 0, st>>>((double*)T1, ns);
+      ++ctx->launches;
+      SPARC_CUDA(ctx, tc::rotate(ctx, (const float*)SV, ns, (const double*)T1, ns, ns, (float*)S1, ns, tcs, st));
+      k_convert<TS, TW><<<ceil_div(nn, 256), 256, 0, st>>>(S1, Vj, nn);
+      ++ctx->launches;
+    } else {
+      k_convert<TS, TW><<<ceil_div(nn, 256), 256, 0, st>>>(SV, A1, nn);
+      ++ctx->launches;
+      SPARC_CUDA(ctx, (gemm64<TW, true, false>(ctx, ns, ns, ns, A1, ns, A1, ns, T1, ns, 1.0, 0.0, partH, pcap, st)));
+      SPARC_CUDA(ctx, cudaMemcpyAsync(Vj, A1, nn * sizeof(TW), cudaMemcpyDeviceToDevice, st));
+      SPARC_CUDA(ctx, (gemm64<TW, false, false>(ctx, ns, ns, ns, A1, ns, T1, ns, Vj, ns, -0.5, 1.5, partH, pcap, st)));
+    }
     SPARC_CUDA(ctx, (gemm64<TW, false, false>(ctx, ns, ns, ns, A0, ns, Vj, ns, T1, ns, 1.0, 0.0, partH, pcap, st)));
     k_rayleigh<TW><<<ceil_div(ns, 128), 128, 0, st>>>(Vj, T1, ns, lam);
     ++ctx->launches;

@@ -625,6 +625,117 @@ __global__ void __launch_bounds__(TPB) k_force_proj(const T* __restrict__ U, lon
   }
 }
 
+// The same projections for Bloch orbitals of one k-point (complex U, complex chi~ with the
+// image phases of Eq. NonlocalPS:FD): out[(p * ns + n) * 8 + 2 q + {0, 1}] = (Re, Im) of
+// sum conj(chi~) u (q = 0) and of sum conj(chi~) (nabla_h u)_s (q = 1 + s), where a
+// neighbour across the upper face of axis s carries exp(+i k_s L_s) and across the lower
+// face exp(-i k_s L_s) (the Bloch wrap of Section 3.1).
+template <class T>
+__global__ void __launch_bounds__(TPB) k_force_proj_c(const T* __restrict__ U, long long ld, int n1, int n2, int n3,
+                                                      int no, GWeights G, const long long* __restrict__ p_off,
+                                                      const int* __restrict__ p_g, const cf64* __restrict__ p_val,
+                                                      double phr0, double phi0, double phr1, double phi1, double phr2,
+                                                      double phi2, int ns, double* out) {
+  __shared__ double sh[32];
+  const int p = blockIdx.x, nn = blockIdx.y;
+  const T* u = U + (long long)nn * ld;
+  const double phr[3] = {phr0, phr1, phr2}, phi[3] = {phi0, phi1, phi2};
+  double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  // u at node (i, j, k) times the phase of `t` face crossings along axis s (t in -1, 0, 1)
+  auto val = [&](int i, int j, int k, int s, int t, double& re, double& im) {
+    const T v = u[((long long)k * n2 + j) * n1 + i];
+    const double vr = (double)v.x, vi = (double)v.y;
+    if (t == 0) { re = vr; im = vi; return; }
+    const double cr = phr[s], ci = t > 0 ? phi[s] : -phi[s];
+    re = vr * cr - vi * ci;
+    im = vr * ci + vi * cr;
+  };
+  for (long long e = p_off[p] + threadIdx.x; e < p_off[p + 1]; e += blockDim.x) {
+    const int g = p_g[e];
+    const cf64 c = p_val[e];
+    const int i = g % n1, j = (g / n1) % n2, k = g / (n1 * n2);
+    double ur, ui;
+    val(i, j, k, 0, 0, ur, ui);
+    double gr[3] = {0.0, 0.0, 0.0}, gi[3] = {0.0, 0.0, 0.0};
+    for (int q = 1; q <= no; ++q) {
+      double ar, ai, br, bi;
+      {
+        int ip = i + q, im = i - q, tp = 0, tm = 0;
+        if (ip >= n1) { ip -= n1; tp = 1; }
+        if (im < 0) { im += n1; tm = -1; }
+        val(ip, j, k, 0, tp, ar, ai);
+        val(im, j, k, 0, tm, br, bi);
+        gr[0] += G.w[0][q] * (ar - br);
+        gi[0] += G.w[0][q] * (ai - bi);
+      }
+      {
+        int jp = j + q, jm = j - q, tp = 0, tm = 0;
+        if (jp >= n2) { jp -= n2; tp = 1; }
+        if (jm < 0) { jm += n2; tm = -1; }
+        val(i, jp, k, 1, tp, ar, ai);
+        val(i, jm, k, 1, tm, br, bi);
+        gr[1] += G.w[1][q] * (ar - br);
+        gi[1] += G.w[1][q] * (ai - bi);
+      }
+      {
+        int kp = k + q, km = k - q, tp = 0, tm = 0;
+        if (kp >= n3) { kp -= n3; tp = 1; }
+        if (km < 0) { km += n3; tm = -1; }
+        val(i, j, kp, 2, tp, ar, ai);
+        val(i, j, km, 2, tm, br, bi);
+        gr[2] += G.w[2][q] * (ar - br);
+        gi[2] += G.w[2][q] * (ai - bi);
+      }
+    }
+    // conj(c) * (x + i y) = (c.x x + c.y y) + i (c.x y - c.y x)
+    acc[0] += c.x * ur + c.y * ui;
+    acc[1] += c.x * ui - c.y * ur;
+    for (int s2 = 0; s2 < 3; ++s2) {
+      acc[2 + 2 * s2] += c.x * gr[s2] + c.y * gi[s2];
+      acc[3 + 2 * s2] += c.x * gi[s2] - c.y * gr[s2];
+    }
+  }
+  for (int q = 0; q < 8; ++q) {
+    const double t = block_sum(acc[q], sh);
+    if (threadIdx.x == 0) out[((long long)p * ns + nn) * 8 + q] = t;
+  }
+}
+
+// fn[3 I + s] += -4 w h1h2h3 sum_{p of atom I} gamma_p sum_n g_n Re(conj(Y_pn) W_pns) for the
+// projections of one k-point (Eq. NonlocForce:Discrete with the k-point weight w; fixed order).
+__global__ void k_force_acc_k(const double* __restrict__ prj, const int* __restrict__ patom,
+                              const double* __restrict__ gamma, int nproj, int ns, const double* __restrict__ occ,
+                              double wdv, int natom, double* fn) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= natom) return;
+  for (int s = 0; s < 3; ++s) {
+    double acc = 0.0;
+    for (int p = 0; p < nproj; ++p) {
+      if (patom[p] != I) continue;
+      double t = 0.0;
+      for (int n = 0; n < ns; ++n) {
+        const double* q = prj + ((long long)p * ns + n) * 8;
+        t += occ[n] * (q[0] * q[2 + 2 * s] + q[1] * q[3 + 2 * s]);
+      }
+      acc += -4.0 * gamma[p] * wdv * t;
+    }
+    fn[3 * I + s] += acc;
+  }
+}
+
+// f[I] = local partials (fixed order) into f[3 I + s]; fn copied into f[3 (natom + I) + s].
+__global__ void k_force_fin(const double* __restrict__ loc, int nby, const double* __restrict__ fn, int natom,
+                            double* f) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= natom) return;
+  for (int s = 0; s < 3; ++s) {
+    double fl = 0.0;
+    for (int b = 0; b < nby; ++b) fl += loc[((long long)I * nby + b) * 3 + s];
+    f[3 * I + s] = fl;
+    f[3 * (natom + I) + s] = fn[3 * I + s];
+  }
+}
+
 // f[atom] = local partials (fixed order) - 4 h1h2h3 sum_{p of atom} gamma_p sum_n g_n Y W
 // (Eq. NonlocForce:Discrete; psi = U / sqrt(h1h2h3), so Y W = h1h2h3 (sum chi U)(sum chi grad U))
 __global__ void k_force_sum(const double* __restrict__ loc, int nby, const double* __restrict__ prj,
@@ -1066,9 +1177,11 @@ extern "C" sparc_status sparc_scf_forces(sparc_scf* S, sparc_dtype dtype, const 
   const long long nd = H->gd.nd;
   if (S->last_ns != ns || ns < 1 || ld < nd)
     return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_scf_forces: needs the orbitals of the last sparc_scf_step");
-  if (S->Hk.size() != 1) return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_scf_forces: one k-point (Gamma) only");
-  if (dtype != SPARC_F64 && dtype != SPARC_F32)
-    return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_scf_forces: real orbitals (Gamma point) only");
+  const int nk = (int)S->Hk.size();
+  const bool cplx = dtype == SPARC_C128 || dtype == SPARC_C64;
+  if ((int)dtype < 0 || (int)dtype > 3) return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_scf_forces: unknown dtype");
+  if (!cplx && (nk != 1 || H->gd.cplx))
+    return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_scf_forces: real orbitals need one k-point at Gamma");
   if (H->nproj > 0 && !S->d_patom)
     return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_scf_forces: sparc_scf_desc.proj_atom was not given");
   SPARC_CUDA(ctx, cudaSetDevice(ctx->device));
@@ -1097,14 +1210,54 @@ extern "C" sparc_status sparc_scf_forces(sparc_scf* S, sparc_dtype dtype, const 
   } loc, prj, fo;
   const int np = H->nproj;
   SPARC_CUDA(ctx, cudaMalloc(&loc.p, (size_t)natom * nby * 3 * sizeof(double)));
-  SPARC_CUDA(ctx, cudaMalloc(&prj.p, (size_t)std::max(np, 1) * ns * 4 * sizeof(double)));
-  SPARC_CUDA(ctx, cudaMalloc(&fo.p, (size_t)natom * 6 * sizeof(double)));
+  SPARC_CUDA(ctx, cudaMalloc(&prj.p, (size_t)std::max(np, 1) * ns * (cplx ? 8 : 4) * sizeof(double)));
+  SPARC_CUDA(ctx, cudaMalloc(&fo.p, (size_t)natom * (cplx ? 9 : 6) * sizeof(double)));
   double* const d_loc = loc.p;
   double* const d_prj = prj.p;
   double* const d_f = fo.p;
   k_force_local<<<dim3(natom, nby), TPB, 0, st>>>(H->gd.n1, H->gd.n2, H->gd.n3, H->grid.h[0], H->grid.h[1],
                                                    H->grid.h[2], H->gd.no, S->W, G, S->d_atoms, S->d_phi, d_loc);
   ++ctx->launches;
+  const double dvk = H->grid.h[0] * H->grid.h[1] * H->grid.h[2];
+  if (cplx) {
+    // Bloch orbitals: the nonlocal force summed over the k-points with their weights
+    double* d_fn = d_f + 6 * (size_t)natom;
+    SPARC_CUDA(ctx, cudaMemsetAsync(d_fn, 0, 3 * (size_t)natom * sizeof(double), st));
+    const size_t es = dtype == SPARC_C128 ? 16 : 8;
+    for (int k = 0; k < nk && np > 0; ++k) {
+      sparc_ham* Hk = S->Hk[k];
+      sparc_status rc = ensure_vals(Hk, SPARC_C128);
+      if (rc != SPARC_OK) return rc;
+      const void* Uk = (const char*)U + (size_t)k * ld * ns * es;
+      const cf64* pv = (const cf64*)Hk->d_p_val[SPARC_C128];
+      const double* ph_r = Hk->gd.ph_re;
+      const double* ph_i = Hk->gd.ph_im;
+      if (dtype == SPARC_C128)
+        k_force_proj_c<cf64><<<dim3(np, ns), TPB, 0, st>>>((const cf64*)Uk, ld, H->gd.n1, H->gd.n2, H->gd.n3, H->gd.no,
+                                                            G, Hk->d_p_off, Hk->d_p_g, pv, ph_r[0], ph_i[0], ph_r[1],
+                                                            ph_i[1], ph_r[2], ph_i[2], ns, d_prj);
+      else
+        k_force_proj_c<cf32><<<dim3(np, ns), TPB, 0, st>>>((const cf32*)Uk, ld, H->gd.n1, H->gd.n2, H->gd.n3, H->gd.no,
+                                                            G, Hk->d_p_off, Hk->d_p_g, pv, ph_r[0], ph_i[0], ph_r[1],
+                                                            ph_i[1], ph_r[2], ph_i[2], ns, d_prj);
+      const double w = nk > 1 ? S->wk[k] : 1.0;
+      k_force_acc_k<<<ceil_div(natom, 64), 64, 0, st>>>(d_prj, S->d_patom, H->d_gamma, np, ns, S->d_occ + (size_t)k * ns,
+                                                        w * dvk, natom, d_fn);
+      ctx->launches += 2;
+    }
+    k_force_fin<<<ceil_div(natom, 64), 64, 0, st>>>(d_loc, nby, d_fn, natom, d_f);
+    ++ctx->launches;
+    SPARC_LAUNCH(ctx, "forces");
+    std::vector<double> hf((size_t)natom * 6);
+    SPARC_CUDA(ctx, cudaMemcpyAsync(hf.data(), d_f, hf.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SPARC_CUDA(ctx, cudaStreamSynchronize(st));
+    for (int i = 0; i < 3 * natom; ++i) {
+      f_host[i] = hf[i] + hf[3 * natom + i];
+      f_host[3 * natom + i] = hf[i];
+      f_host[6 * natom + i] = hf[3 * natom + i];
+    }
+    return SPARC_OK;
+  }
   if (np > 0) {
     sparc_status rc = ensure_vals(H, SPARC_F64);
     if (rc != SPARC_OK) return rc;

@@ -589,8 +589,9 @@ class Scf:
         return cls(H, sysd.wl.atoms, sysd.Z, sysd.rc, sysd.v0, proj_atom=sysd.wl.proj.atom, **kw)
 
     def forces(self, U, ns=None, ld=None, stream=None, dtype=None):
-        """(f, f_loc, f_nloc), each (natom, 3), at the state of the last step (sparc_scf_forces)."""
-        ns = U.shape[0] if ns is None else ns
+        """(f, f_loc, f_nloc), each (natom, 3), at the state of the last step (sparc_scf_forces);
+        U: (ns, ld) at Gamma, or (nk, ns, ld) Bloch orbitals of every k-point."""
+        ns = U.shape[-2] if ns is None else ns
         ld = U.shape[-1] if ld is None else ld
         dt = dtype_code(U) if dtype is None else dtype
         na = int(self._Z.size)

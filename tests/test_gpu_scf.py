@@ -283,3 +283,45 @@ def test_two_kpoint_mixed_scf_reaches_the_fp64_energy(ctx):
     print(f"two-k free energy: complex128 {F[torch.complex128]:.10f}, complex64 {F[torch.complex64]:.10f}, "
           f"|dF|/atom {dF:.2e}")
     assert dF < 1e-5
+
+
+def test_two_kpoint_forces_match_the_oracle(ctx):
+    """Section 3.6 with Bloch orbitals: the converged two-k SCF's forces.  The local part
+    equals the oracle's local force at the GPU's electrostatic potential; the nonlocal
+    part the oracle's nonlocal_forces_bloch summed over the k-points with their weights,
+    at the GPU's orbitals and occupations (Fermi level from its Ritz values), to
+    1e-8 Ha/bohr; complex64 orbitals within 1e-4 Ha/bohr of complex128."""
+    from paper_1603_04339_gb300 import sparc
+    sysd, wl, v0, U0 = _scf_two_k()
+    res = {}
+    for dt in (torch.complex128, torch.complex64):
+        Hs = [sparc.Hamiltonian.from_workload(ctx, wl, k) for k in range(2)]
+        S = sparc.Scf(Hs, wl.atoms, sysd.Z, sysd.rc, v0, kT=KT, mix_beta=BETA, mix_history=HIST,
+                      poisson_tol=1e-12, wk=[0.5, 0.5], proj_atom=wl.proj.atom)
+        U = torch.from_numpy(np.stack(U0)).to(dt).cuda()
+        eig = torch.zeros(2 * wl.ns, dtype=torch.float64, device="cuda")
+        for it in range(60):
+            info = sparc.sparc_scf_step(S, U, eig, wl.m)
+            if info["vresid"] < (1e-9 if dt == torch.complex128 else 1e-6):
+                break
+        f, fl, fn = S.forces(U)
+        res[dt] = (f, fl, fn, U.cpu().numpy().astype(np.complex128), eig.cpu().numpy(), _field(S, "phi", wl.nd))
+        S.close()
+        for H in Hs:
+            H.close()
+    f, fl, fn, Uh, lam, phi = res[torch.complex128]
+    wts = np.repeat([0.5, 0.5], wl.ns)
+    mu = SO.fermi_level(lam, sysd.nelec, KT, wts)
+    g = SO.occupations(lam, mu, KT)
+    _, flo, _ = SO.forces(wl.n, wl.h, 6, wl.atoms, sysd.Z, sysd.rc, phi, wl.proj,
+                          np.zeros((1, wl.nd)), np.zeros(1))
+    fno = sum(SO.nonlocal_forces_bloch(wl.n, wl.h, 6, wl.kpts[k], wl.proj, Uh[k], g[k * wl.ns:(k + 1) * wl.ns],
+                                       w=0.5, natom=len(sysd.Z)) for k in range(2))
+    print("two-k forces", f.tolist(), "local err", float(np.max(np.abs(fl - flo))),
+          "nonlocal err", float(np.max(np.abs(fn - fno))))
+    assert np.max(np.abs(fl - flo)) < 1e-8
+    assert np.max(np.abs(fn - fno)) < 1e-8
+    assert np.max(np.abs(fn)) > 1e-4                       # a nonzero nonlocal force is checked
+    f32 = res[torch.complex64][0]
+    print("complex64 vs complex128 forces: max |df|", float(np.max(np.abs(f32 - f))))
+    assert np.max(np.abs(f32 - f)) < 1e-4
