@@ -427,6 +427,11 @@ sparc_status sparc_timing_read(sparc_ctx* ctx, int which, double* ms_total, int6
 sparc_status sparc_launch_count(const sparc_ctx* ctx, int64_t* launches);
 /* Jacobi sweeps used by the last Rayleigh-Ritz call on this context. */
 sparc_status sparc_last_sweeps(const sparc_ctx* ctx, int* sweeps);
+/* max |M~1 - I| of the last mixed-mode FP32 Rayleigh-Ritz call on this context: how far
+ * from orthonormal its first (FP32 Cholesky) orthonormalisation left the basis, as
+ * measured by the Gram of that basis (Section 3.4; -1 before any such call).  At or
+ * below 1e-3 the second factorisation ran as a short series in it, above in FP64. */
+sparc_status sparc_last_ortho_err(const sparc_ctx* ctx, double* err);
 
 /* Failure injection, for testing the error paths (not part of the method).  All
  * injections are made on the host; none makes a kernel fault, trap or hang.
@@ -443,12 +448,17 @@ sparc_status sparc_last_sweeps(const sparc_ctx* ctx, int* sweeps);
  *   SPARC_INJECT_CG_MAX_ITERS: the Poisson solver of sparc_scf_step stops after
  *     `value` conjugate-gradient iterations (0: the default 4000); short of its
  *     tolerance, the step returns SPARC_ERR_NO_CONVERGENCE.
+ *   SPARC_INJECT_FP64_ORTHO: the mixed-mode FP32 Rayleigh-Ritz takes its FP64
+ *     fallbacks as if the fast paths had failed: value 1, the second factorisation
+ *     (in the orthonormalised basis) in FP64 instead of the series; value 2, also the
+ *     first orthonormalisation in FP64 instead of the scaled FP32 Cholesky; 0, off.
  * SPARC_ERR_INVALID_ARG for an unknown `what`. */
 typedef enum {
   SPARC_INJECT_ALLOC_FAIL = 1,
   SPARC_INJECT_WAIT_LIMIT = 2,
   SPARC_INJECT_STALL = 3,
-  SPARC_INJECT_CG_MAX_ITERS = 4
+  SPARC_INJECT_CG_MAX_ITERS = 4,
+  SPARC_INJECT_FP64_ORTHO = 5
 } sparc_inject;
 sparc_status sparc_debug_inject(sparc_ctx* ctx, int what, int64_t value);
 

@@ -178,6 +178,7 @@ struct sparc_ctx {
   cudaStream_t cap_stream = nullptr;
   std::map<std::tuple<int, int, void*, void*, void*>, cudaGraphExec_t> graphs;
   int last_sweeps = 0;
+  double last_ortho_err = -1.0;   // max |U1^T U1 - I| of the last mixed Rayleigh-Ritz (-1: none)
   // filter launch configuration chosen by sparc_autotune_filter, keyed by (dtype, Nd,
   // ns, number of k-points): units (blocks of NB orbitals) per launch + TUNE_SHAPE x the
   // FP32 pass tile shape
@@ -187,6 +188,7 @@ struct sparc_ctx {
   long long inject_wait_limit = 0;  // clocks of the TMA pass's bounded waits (0: default)
   int inject_stall = -1;            // step at which the next TMA pass stops producing
   int inject_cg_max = 0;            // Poisson CG iteration cap (0: default)
+  int inject_fp64_ortho = 0;        // mixed RR: 1 second, 2 both orthonormalisations in FP64
 };
 
 namespace sparc {

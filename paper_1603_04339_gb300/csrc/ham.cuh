@@ -50,6 +50,14 @@ cudaError_t launch_to_blocks(const T* X, long long ld, int ns, T* B, long long n
 template <class T>
 cudaError_t launch_from_blocks(const T* B, long long nd, int nblk, T* X, long long ld, int ns,
                                cudaStream_t st);
+// The same between X and a row layout: nd = rows x n1 nodes, each row held as n1 + 2 pad
+// nodes in the blocks (pad ghost nodes at either end repeat the other end of the row).
+template <class T>
+cudaError_t launch_to_blocks_rows(const T* X, long long ld, int ns, T* B, long long nd, int n1, int pad,
+                                  int nblk, cudaStream_t st);
+template <class T>
+cudaError_t launch_from_blocks_rows(const T* B, long long nd, int n1, int pad, int nblk, T* X, long long ld,
+                                    int ns, cudaStream_t st);
 // gc[p][blk][lane] = gamma_p * h1h2h3 * sum_g conj(chi~_p[g]) Y[blk][g][lane]
 template <class T>
 cudaError_t launch_nl_gather(const sparc_ham* H, const T* Y, int nbl, int nblk, T* gc,

@@ -174,6 +174,61 @@ __global__ void __launch_bounds__(256) k_from_blocks(const T* __restrict__ B, lo
   if (n < ns && g < nd) X[g + (long long)n * ld] = tile[o][x];
 }
 
+// The same moves, a CTA per (rows of one block): the nodes form rows of n1, and the
+// block holds each row as n1 + 2 pad nodes, x' = x + pad, where x' < pad and
+// x' >= n1 + pad repeat the other end of the row (the periodic wrap in x; pad = 0 for
+// the plain layout).  Thread (x', part) moves the 16 bytes of 16 / sizeof(T)
+// orbitals of node x' in every row of the CTA: reads along a row are coalesced per
+// orbital, writes contiguous; orbitals past ns read as zero.  nd = nrows n1.
+template <class T>
+__global__ void __launch_bounds__(1024) k_to_blocks_rows(const T* __restrict__ X, long long ld, int ns,
+                                                        T* __restrict__ B, int n1, int pad, long long nrows,
+                                                        int rpc) {
+  constexpr int EPT = 16 / (int)sizeof(T), TPN = NB / EPT;
+  const int n1p = n1 + 2 * pad;
+  const int t = threadIdx.x;
+  if (t >= TPN * n1p) return;
+  const int xp = t / TPN, part = t % TPN;
+  const int xs = ((xp - pad) % n1 + n1) % n1;
+  const int blk = blockIdx.y;
+  const int c0 = blk * NB + part * EPT;
+  const long long r0 = (long long)blockIdx.x * rpc, r1 = min(nrows, r0 + rpc);
+  T* Bb = B + (size_t)blk * nrows * n1p * NB + part * EPT;
+#pragma unroll 4
+  for (long long r = r0; r < r1; ++r) {
+    const long long g = r * n1 + xs;
+    union { T v[EPT]; uint4 u; } w;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e)
+      w.v[e] = c0 + e < ns ? X[g + (long long)(c0 + e) * ld] : Tr<T>::zero();
+    *reinterpret_cast<uint4*>(Bb + (size_t)(r * n1p + xp) * NB) = w.u;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(1024) k_from_blocks_rows(const T* __restrict__ B, int n1, int pad,
+                                                          long long nrows, int rpc, T* __restrict__ X,
+                                                          long long ld, int ns) {
+  constexpr int EPT = 16 / (int)sizeof(T), TPN = NB / EPT;
+  const int n1p = n1 + 2 * pad;
+  const int t = threadIdx.x;
+  if (t >= TPN * n1) return;
+  const int x = t / TPN, part = t % TPN;
+  const int blk = blockIdx.y;
+  const int c0 = blk * NB + part * EPT;
+  const long long r0 = (long long)blockIdx.x * rpc, r1 = min(nrows, r0 + rpc);
+  const T* Bb = B + (size_t)blk * nrows * n1p * NB + part * EPT;
+#pragma unroll 4
+  for (long long r = r0; r < r1; ++r) {
+    const long long g = r * n1 + x;
+    union { T v[EPT]; uint4 u; } w;
+    w.u = *reinterpret_cast<const uint4*>(Bb + (size_t)(r * n1p + x + pad) * NB);
+#pragma unroll
+    for (int e = 0; e < EPT; ++e)
+      if (c0 + e < ns) X[g + (long long)(c0 + e) * ld] = w.v[e];
+  }
+}
+
 template <class T>
 const typename Tr<T>::R* veff_of(const sparc_ham* H);
 template <> const double* veff_of<double>(const sparc_ham* H) { return H->d_veff; }
@@ -190,20 +245,59 @@ template <> const float* gamma_of<cf32>(const sparc_ham* H) { return H->d_gamma3
 
 }  // namespace
 
+// Rows per CTA of the row kernels: about 16 KB moved per CTA.
+template <class T>
+static int rows_per_cta(int n1p) {
+  return std::max(1, (int)(16384 / ((size_t)n1p * NB * sizeof(T))));
+}
+
+template <class T>
+cudaError_t launch_to_blocks_rows(const T* X, long long ld, int ns, T* B, long long nd, int n1, int pad,
+                                  int nblk, cudaStream_t st) {
+  constexpr int TPN = NB / (16 / (int)sizeof(T));
+  const int n1p = n1 + 2 * pad;
+  if (TPN * n1p > 1024 || n1 <= 0 || nd % n1 != 0) return cudaErrorInvalidValue;
+  const long long nrows = nd / n1;
+  const int rpc = rows_per_cta<T>(n1p);
+  dim3 grid((unsigned)ceil_div(nrows, (long long)rpc), (unsigned)nblk);
+  k_to_blocks_rows<T><<<grid, (unsigned)ceil_div(TPN * n1p, 32) * 32, 0, st>>>(X, ld, ns, B, n1, pad, nrows, rpc);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_from_blocks_rows(const T* B, long long nd, int n1, int pad, int nblk, T* X, long long ld,
+                                    int ns, cudaStream_t st) {
+  constexpr int TPN = NB / (16 / (int)sizeof(T));
+  const int n1p = n1 + 2 * pad;
+  if (TPN * n1p > 1024 || n1 <= 0 || nd % n1 != 0) return cudaErrorInvalidValue;
+  const long long nrows = nd / n1;
+  const int rpc = rows_per_cta<T>(n1p);
+  dim3 grid((unsigned)ceil_div(nrows, (long long)rpc), (unsigned)nblk);
+  k_from_blocks_rows<T><<<grid, (unsigned)ceil_div(TPN * n1, 32) * 32, 0, st>>>(B, n1, pad, nrows, rpc, X, ld, ns);
+  return cudaGetLastError();
+}
+
+// The plain layout [blk][g][NB] as rows of 128 nodes (the last one ragged).
 template <class T>
 cudaError_t launch_to_blocks(const T* X, long long ld, int ns, T* B, long long nd, int nblk,
                              cudaStream_t st) {
-  dim3 grid((unsigned)ceil_div(nd, 32), (unsigned)nblk), block(32, NB);
-  k_to_blocks<T><<<grid, block, 0, st>>>(X, ld, ns, B, nd);
-  return cudaGetLastError();
+  if (nd % 128 != 0) {
+    dim3 grid((unsigned)ceil_div(nd, 32), (unsigned)nblk), block(32, NB);
+    k_to_blocks<T><<<grid, block, 0, st>>>(X, ld, ns, B, nd);
+    return cudaGetLastError();
+  }
+  return launch_to_blocks_rows<T>(X, ld, ns, B, nd, 128, 0, nblk, st);
 }
 
 template <class T>
 cudaError_t launch_from_blocks(const T* B, long long nd, int nblk, T* X, long long ld, int ns,
                                cudaStream_t st) {
-  dim3 grid((unsigned)ceil_div(nd, 32), (unsigned)nblk), block(32, NB);
-  k_from_blocks<T><<<grid, block, 0, st>>>(B, nd, X, ld, ns);
-  return cudaGetLastError();
+  if (nd % 128 != 0) {
+    dim3 grid((unsigned)ceil_div(nd, 32), (unsigned)nblk), block(32, NB);
+    k_from_blocks<T><<<grid, block, 0, st>>>(B, nd, X, ld, ns);
+    return cudaGetLastError();
+  }
+  return launch_from_blocks_rows<T>(B, nd, 128, 0, nblk, X, ld, ns, st);
 }
 
 template <class T>
@@ -252,6 +346,10 @@ cudaError_t launch_hpass(const sparc_ham* H, const T* Yin, const T* Yprev, T* Yo
 }
 
 #define SPARC_INST(T)                                                                          \
+  template cudaError_t launch_to_blocks_rows<T>(const T*, long long, int, T*, long long, int, int, \
+                                                int, cudaStream_t);                            \
+  template cudaError_t launch_from_blocks_rows<T>(const T*, long long, int, int, int, T*,      \
+                                                  long long, int, cudaStream_t);               \
   template cudaError_t launch_to_blocks<T>(const T*, long long, int, T*, long long, int,       \
                                            cudaStream_t);                                      \
   template cudaError_t launch_from_blocks<T>(const T*, long long, int, T*, long long, int,     \

@@ -731,54 +731,6 @@ long long padded_nd(const sparc_ham* H) { return (long long)(H->gd.n1 + 2 * R) *
 
 namespace tma {
 
-// B (x-padded, ndp nodes per block) from the column-major X: 32 padded nodes x 8
-// orbitals per CTA, transposed through shared memory; ghost nodes read the other end
-// of their row.
-__global__ void __launch_bounds__(256) k_to_blocks_px(const float* __restrict__ X, long long ld, int ns,
-                                                     float* __restrict__ B, int n1, long long ndp) {
-  __shared__ float tile[NB][33];
-  const long long g0 = (long long)blockIdx.x * 32;
-  const int blk = blockIdx.y;
-  const int o = threadIdx.y, x = threadIdx.x;   // blockDim = (32, NB)
-  const int n = blk * NB + o;
-  const int n1p = n1 + 2 * R;
-  const long long gp = g0 + x;
-  float v = 0.f;
-  if (n < ns && gp < ndp) {
-    const long long row = gp / n1p;
-    int xs = (int)(gp - row * n1p) - R;
-    if (xs < 0) xs += n1;
-    else if (xs >= n1) xs -= n1;
-    v = X[row * n1 + xs + (long long)n * ld];
-  }
-  tile[o][x] = v;
-  __syncthreads();
-  const int t = threadIdx.y * 32 + threadIdx.x;
-  const int p = t / NB, l = t % NB;
-  if (g0 + p < ndp) B[((size_t)blk * ndp + g0 + p) * NB + l] = tile[l][p];
-}
-
-// X (column-major) from the interior nodes of the x-padded B.
-__global__ void __launch_bounds__(256) k_from_blocks_px(const float* __restrict__ B, int n1, long long nd,
-                                                       float* __restrict__ X, long long ld, int ns) {
-  __shared__ float tile[NB][33];
-  const long long g0 = (long long)blockIdx.x * 32;
-  const int blk = blockIdx.y;
-  const int n1p = n1 + 2 * R;
-  const long long ndp = nd / n1 * n1p;
-  const int t = threadIdx.y * 32 + threadIdx.x;
-  const int p = t / NB, l = t % NB;
-  if (g0 + p < nd) {
-    const long long g = g0 + p, row = g / n1;
-    tile[l][p] = B[((size_t)blk * ndp + row * n1p + (g - row * n1) + R) * NB + l];
-  }
-  __syncthreads();
-  const int o = threadIdx.y, x = threadIdx.x;
-  const int n = blk * NB + o;
-  const long long g = g0 + x;
-  if (n < ns && g < nd) X[g + (long long)n * ld] = tile[o][x];
-}
-
 // Tensor map of an x-padded block buffer: dims (8 orbitals, n1 + 2R, n2, n3 * nblk),
 // box (8, bx, by, 1).
 static bool map_blocks(CUtensorMap* m, const float* base, int n1p, int n2, int n3, int nblk, int bx, int by) {
@@ -795,17 +747,12 @@ static bool map_blocks(CUtensorMap* m, const float* base, int n1p, int n2, int n
 
 cudaError_t launch_to_blocks_px(const sparc_ham* H, const float* X, long long ld, int ns, float* B, int nblk,
                                 cudaStream_t st) {
-  const long long ndp = padded_nd(H);
-  dim3 grid((unsigned)ceil_div(ndp, 32), (unsigned)nblk), block(32, NB);
-  tma::k_to_blocks_px<<<grid, block, 0, st>>>(X, ld, ns, B, H->gd.n1, ndp);
-  return cudaGetLastError();
+  return launch_to_blocks_rows<float>(X, ld, ns, B, H->gd.nd, H->gd.n1, R, nblk, st);
 }
 
 cudaError_t launch_from_blocks_px(const sparc_ham* H, const float* B, int nblk, float* X, long long ld, int ns,
                                   cudaStream_t st) {
-  dim3 grid((unsigned)ceil_div(H->gd.nd, 32), (unsigned)nblk), block(32, NB);
-  tma::k_from_blocks_px<<<grid, block, 0, st>>>(B, H->gd.n1, H->gd.nd, X, ld, ns);
-  return cudaGetLastError();
+  return launch_from_blocks_rows<float>(B, H->gd.nd, H->gd.n1, R, nblk, X, ld, ns, st);
 }
 
 cudaError_t launch_pass_tma(const sparc_ham* H, const float* Yin, const float* Yprev, float* Yout, const float* gc,

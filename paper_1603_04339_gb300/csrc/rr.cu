@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
 #include <tuple>
 #include <type_traits>
 #include <vector>
@@ -188,24 +189,26 @@ __global__ void __launch_bounds__(1024) k_chol(TW* A, int n, int* status) {
   }
 }
 
-// Diagonal block of the blocked Cholesky, FP64, in shared memory (one CTA):
-// the kb x kb block at A (leading dimension lda, lower part read) is factored
+// Diagonal block of the blocked Cholesky, FP64 or FP32 (TS), in shared memory (one
+// CTA): the kb x kb block at A (leading dimension lda, lower part read) is factored
 // right-looking, L is written back over the block (strict upper part zeroed), and
 // L^-1 is formed in place (column-oriented, from the last column to the first)
-// and written to Dk (leading dimension ldd).  Pivot rule as k_chol.
-template <int MB>
-__global__ void __launch_bounds__(256) k_chol_blk(double* A, long long lda, double* Dk, long long ldd, int kb,
+// and written to Dk (leading dimension ldd).  A pivot at or below 1e-14 (FP64) or
+// 1e-6 (FP32) of its original diagonal entry, or not finite, flags NOT_POSDEF.
+template <class TS, int MB>
+__global__ void __launch_bounds__(256) k_chol_blk(TS* A, long long lda, TS* Dk, long long ldd, int kb,
                                                   int* status) {
-  __shared__ double S[MB][MB + 1];
-  __shared__ double x[MB];
-  __shared__ double rdiag[MB];   // 1 / L_jj, one FP64 division per column (thread 0)
-  __shared__ double a0[MB];      // the block's diagonal before the factorisation
+  constexpr TS PIVTOL = sizeof(TS) == 8 ? (TS)1e-14 : (TS)1e-6;
+  __shared__ TS S[MB][MB + 1];
+  __shared__ TS x[MB];
+  __shared__ TS rdiag[MB];   // 1 / L_jj, one division per column (thread 0)
+  __shared__ TS a0[MB];      // the block's diagonal before the factorisation
   __shared__ int bad;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) bad = 0;
   for (int e = tid; e < kb * kb; e += nt) {
     const int i = e % kb, j = e / kb;
-    const double v = i >= j ? A[i + (long long)j * lda] : 0.0;
+    const TS v = i >= j ? A[i + (long long)j * lda] : (TS)0;
     S[i][j] = v;
     if (i == j) a0[i] = v;
   }
@@ -213,50 +216,50 @@ __global__ void __launch_bounds__(256) k_chol_blk(double* A, long long lda, doub
   for (int j = 0; j < kb; ++j) {
     if (tid == 0) {
       // S[j][j] holds a_jj minus the updates of the columns before j
-      const double d = S[j][j];
-      const double ajj = a0[j];
-      if (!(d > 1e-14 * ajj) || !isfinite(d)) {
+      const TS d = S[j][j];
+      const TS ajj = a0[j];
+      if (!(d > PIVTOL * ajj) || !isfinite(d)) {
         bad = 1;
         atomicOr(status, STATUS_NOT_POSDEF);
       } else {
         S[j][j] = sqrt(d);
-        rdiag[j] = 1.0 / S[j][j];
+        rdiag[j] = (TS)1 / S[j][j];
       }
     }
     __syncthreads();
     if (bad) return;
-    const double inv = rdiag[j];
+    const TS inv = rdiag[j];
     for (int i = j + 1 + tid; i < kb; i += nt) S[i][j] *= inv;
     __syncthreads();
     // trailing lower triangle (i, c), j < c <= i: 16 x 16 thread tiles, no index division
     const int tx = tid & 15, ty = tid >> 4;
     for (int i = j + 1 + ty; i < kb; i += 16) {
-      const double lij = S[i][j];
+      const TS lij = S[i][j];
       for (int c = j + 1 + tx; c <= i; c += 16) S[i][c] -= lij * S[c][j];
     }
     __syncthreads();
   }
   for (int e = tid; e < kb * kb; e += nt) {
     const int i = e % kb, j = e / kb;
-    A[i + (long long)j * lda] = i >= j ? S[i][j] : 0.0;
+    A[i + (long long)j * lda] = i >= j ? S[i][j] : (TS)0;
   }
   __syncthreads();
   // in-place inverse: for j = kb-1 .. 0, column j below the diagonal becomes
   // -(1/L_jj) Linv[j+1:, j+1:] L[j+1:, j], using the already inverted trailing block
-  __shared__ double part[16][MB];
+  __shared__ TS part[16][MB];
   for (int j = kb - 1; j >= 0; --j) {
-    const double ljj = rdiag[j];
+    const TS ljj = rdiag[j];
     // x_i = sum_{k=j+1..i} Linv[i][k] L[k][j]: 16 partial sums per row over k, then a fixed-order sum
     const int tx = tid & 15, ty = tid >> 4;
     for (int i = j + 1 + ty; i < kb; i += 16) {
-      double s = 0.0;
+      TS s = 0;
       for (int k = j + 1 + tx; k <= i; k += 16) s += S[i][k] * S[k][j];
       part[tx][i] = s;
     }
     __syncthreads();
     for (int i = j + 1 + tid; i < kb; i += nt) {
-      double s = 0.0;
-      for (int q = 0; q < 16; ++q) s += (j + 1 + q <= i) ? part[q][i] : 0.0;
+      TS s = 0;
+      for (int q = 0; q < 16; ++q) s += (j + 1 + q <= i) ? part[q][i] : (TS)0;
       x[i] = -ljj * s;
     }
     __syncthreads();
@@ -266,7 +269,7 @@ __global__ void __launch_bounds__(256) k_chol_blk(double* A, long long lda, doub
   }
   for (int e = tid; e < kb * kb; e += nt) {
     const int i = e % kb, j = e / kb;
-    Dk[i + (long long)j * ldd] = i >= j ? S[i][j] : 0.0;
+    Dk[i + (long long)j * ldd] = i >= j ? S[i][j] : (TS)0;
   }
 }
 
@@ -635,6 +638,10 @@ __global__ void k_narrow(const TW* __restrict__ a, T* __restrict__ b, long long 
 
 // ------------------------------------------------------------------ blocked FP64 Cholesky pieces
 constexpr int CB = 64;   // Cholesky / inverse block
+// Largest max |E| of M~1 = I + E for the series factorisation of the mixed mode
+// (the truncation errors are |E|^5 and below, under the FP64 rounding of the FP32
+// products' corrections)
+constexpr double EPS_SERIES = 1e-3;
 
 // dst (M x N, ldd) = src (M x N, lds)
 template <class TW>
@@ -688,6 +695,92 @@ __global__ void k_ns_coef(double* G, int n) {
   G[t] = (i == j ? 1.5 : 0.0) - 0.5 * G[t];
 }
 
+// ------------------------------------------------------------------ mixed-mode orthonormalisation
+// s_i = M_ii^(-1/2) and Mf = diag(s) M diag(s) in FP32 (unit diagonal): the diagonally
+// scaled Gram whose FP32 Cholesky orthonormalises the filtered block.
+__global__ void k_scale_unit(const double* __restrict__ M, int n, double* __restrict__ s, float* __restrict__ Mf,
+                             int* status) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n * n) return;
+  const int i = (int)(t % n), j = (int)(t / n);
+  const double di = M[i + (long long)i * n], dj = M[j + (long long)j * n];
+  if (!(di > 0.0) || !(dj > 0.0) || !isfinite(di) || !isfinite(dj)) {
+    if (i == j) {
+      atomicOr(status, STATUS_NOT_POSDEF);
+      s[i] = 0.0;
+    }
+    Mf[t] = 0.f;
+    return;
+  }
+  const double si = rsqrt(di), sj = rsqrt(dj);
+  if (i == j) s[i] = si;
+  Mf[t] = (float)(M[t] * si * sj);
+}
+
+// T[i + j n] = s_i Li[j + i n] for j >= i, else 0: (diag(s) Li^T), the right factor
+// U -> U diag(s) Li^T of the scaled Cholesky orthonormalisation (Li = L'^-1, lower).
+__global__ void k_t1_scaled(const float* __restrict__ Li, const double* __restrict__ s, int n,
+                            double* __restrict__ T) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n * n) return;
+  const int i = (int)(t % n), j = (int)(t / n);
+  T[t] = j >= i ? s[i] * (double)Li[j + (long long)i * n] : 0.0;
+}
+
+// E = M - I and max |E_ij| (the bit pattern of a non-negative double, so that an
+// integer maximum orders it; NaN orders above every finite value) into emax.
+__global__ void __launch_bounds__(256) k_eminus(const double* __restrict__ M, int n, double* __restrict__ E,
+                                                unsigned long long* emax) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long m = 0ull;
+  if (t < (long long)n * n) {
+    const int i = (int)(t % n), j = (int)(t / n);
+    const double v = M[t] - (i == j ? 1.0 : 0.0);
+    E[t] = v;
+    m = (unsigned long long)__double_as_longlong(fabs(v));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long q = __shfl_xor_sync(0xffffffffu, m, o);
+    m = q > m ? q : m;
+  }
+  __shared__ unsigned long long wm[8];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = wm[w] > m ? wm[w] : m;
+    atomicMax(emax, m);
+  }
+}
+
+// F = Phi(E - G): the strictly lower part of E - G plus half its diagonal, zero above
+// (G may be null).  The lower-triangular F with (I + F)(I + F)^T = I + E is the fixed
+// point F = Phi(E - F F^T).
+__global__ void k_phi(const double* __restrict__ E, const double* __restrict__ G, int n, double* __restrict__ F) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n * n) return;
+  const int i = (int)(t % n), j = (int)(t / n);
+  const double v = E[t] - (G ? G[t] : 0.0);
+  F[t] = i > j ? v : (i == j ? 0.5 * v : 0.0);
+}
+
+// Y = I - X
+__global__ void k_i_minus(const double* __restrict__ X, int n, double* __restrict__ Y) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n * n) return;
+  Y[t] = (t % n == t / n ? 1.0 : 0.0) - X[t];
+}
+
+// A = sym(H) + P + P^T + sym(Q): C = (I + K) H (I + K)^T with P = K H, Q = P K^T.
+__global__ void k_csum(const double* __restrict__ Hm, const double* __restrict__ P, const double* __restrict__ Q,
+                       int n, double* __restrict__ A) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n * n) return;
+  const int i = (int)(t % n), j = (int)(t / n);
+  const long long tt = j + (long long)i * n;
+  A[t] = 0.5 * (Hm[t] + Hm[tt]) + (P[t] + P[tt]) + 0.5 * (Q[t] + Q[tt]);
+}
+
 template <class TA, class TB>
 __global__ void k_convert(const TA* __restrict__ a, TB* __restrict__ b, long long n) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -725,9 +818,9 @@ sparc_status chol_inverse(sparc_ctx* ctx, TW* A, TW* Li, int n, TW* Dinv, TW* tm
     TW* Dk = Dinv + (size_t)kblk * CB * CB;
     TW* Akk = A + k0 + (long long)k0 * n;
     // diagonal block: contiguous copy, one-CTA factor and inverse, copies back
-    if constexpr (std::is_same<TW, double>::value) {
+    if constexpr (std::is_same<TW, double>::value || std::is_same<TW, float>::value) {
       // factor and invert the block in shared memory, one launch
-      k_chol_blk<CB><<<1, 256, 0, st>>>(Akk, n, Dk, CB, kb, ctx->d_status);
+      k_chol_blk<TW, CB><<<1, 256, 0, st>>>(Akk, n, Dk, CB, kb, ctx->d_status);
       ctx->launches += 1;
     } else {
       TW* blk = part;                     // kb x kb, leading dimension kb
@@ -937,16 +1030,37 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
     SPARC_LAUNCH(ctx, "gram M0");
     timing_end(ctx, TK_GRAM, tg, st);
     cudaEvent_t t0 = timing_begin(ctx, st);
-    s = chol_inverse<TW>(ctx, Ms, Li, ns, Dinv, T1, partH, pcap, st);
-    if (s != SPARC_OK) return s;
+    // FP32 Cholesky of the diagonally scaled Gram, D^-1/2 M~ D^-1/2 = L' L'^T (unit
+    // diagonal), U1 = U D^-1/2 L'^-T.  How closely U1 comes out orthonormal is all its
+    // rounding decides: the Gram of U1 below measures what is left and the second
+    // factorisation removes it.  A failed FP32 factorisation falls back to FP64.
+    float* M32 = S0;
+    float* Li32 = S1;
     int w0 = 0;
-    SPARC_CUDA(ctx, cudaMemcpyAsync(&w0, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
-    SPARC_CUDA(ctx, cudaStreamSynchronize(st));
+    if (ctx->inject_fp64_ortho >= 2) {
+      w0 = STATUS_NOT_POSDEF;   // injected: as if the FP32 factorisation had failed
+    } else {
+      k_scale_unit<<<ceil_div(nn, 256), 256, 0, st>>>((const double*)Ms, ns, lam, M32, ctx->d_status);
+      ++ctx->launches;
+      s = chol_inverse<float>(ctx, M32, Li32, ns, (float*)Dinv, SV, (float*)partH, 2 * pcap, st);
+      if (s != SPARC_OK) return s;
+      SPARC_CUDA(ctx, cudaMemcpyAsync(&w0, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+      SPARC_CUDA(ctx, cudaStreamSynchronize(st));
+    }
     if (w0 & STATUS_NOT_POSDEF) {
       cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st);
-      return fail(ctx, SPARC_ERR_NOT_POSDEF, "M~ = U^H U is not positive definite");
+      s = chol_inverse<TW>(ctx, Ms, Li, ns, Dinv, T1, partH, pcap, st);
+      if (s != SPARC_OK) return s;
+      SPARC_CUDA(ctx, cudaMemcpyAsync(&w0, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+      SPARC_CUDA(ctx, cudaStreamSynchronize(st));
+      if (w0 & STATUS_NOT_POSDEF) {
+        cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st);
+        return fail(ctx, SPARC_ERR_NOT_POSDEF, "M~ = U^H U is not positive definite");
+      }
+      k_transpose<<<ceil_div(nn, 256), 256, 0, st>>>((const double*)Li, (double*)T1, ns);
+    } else {
+      k_t1_scaled<<<ceil_div(nn, 256), 256, 0, st>>>(Li32, lam, ns, (double*)T1);
     }
-    k_transpose<<<ceil_div(nn, 256), 256, 0, st>>>((const double*)Li, (double*)T1, ns);
     ++ctx->launches;
     timing_end(ctx, TK_EIG, t0, st);
     cudaEvent_t t1 = timing_begin(ctx, st);
@@ -981,21 +1095,84 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
   }
   timing_end(ctx, TK_GRAM, tg, st);
   cudaEvent_t te = timing_begin(ctx, st);
-  // 3. M~ = L L^H (blocked, FP64) and Linv = L^-1
-  s = chol_inverse<TW>(ctx, Ms, Li, ns, Dinv, T1, partH, pcap, st);
-  if (s != SPARC_OK) return s;
-  int word = 0;
-  SPARC_CUDA(ctx, cudaMemcpyAsync(&word, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
-  SPARC_CUDA(ctx, cudaStreamSynchronize(st));
-  if (word & STATUS_NOT_POSDEF) {
-    cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st);
-    return fail(ctx, SPARC_ERR_NOT_POSDEF, "M~ = U^H U is not positive definite");
+  // In the orthonormalised basis M~1 = I + E with E of the order of the FP32 rounding
+  // of the first factorisation.  Where max |E| <= EPS_SERIES its factor and inverse
+  // are short series in E (below) whose small products run in FP32; otherwise the
+  // blocked FP64 factorisation.
+  bool series = false;
+  if constexpr (TCP) {
+    unsigned long long* emax = (unsigned long long*)scal;
+    SPARC_CUDA(ctx, cudaMemsetAsync(emax, 0, sizeof(unsigned long long), st));
+    k_eminus<<<ceil_div(nn, 256), 256, 0, st>>>((const double*)Ms, ns, (double*)A1, emax);
+    ++ctx->launches;
+    unsigned long long eb = 0;
+    SPARC_CUDA(ctx, cudaMemcpyAsync(&eb, emax, sizeof(eb), cudaMemcpyDeviceToHost, st));
+    SPARC_CUDA(ctx, cudaStreamSynchronize(st));
+    double e;
+    std::memcpy(&e, &eb, sizeof(e));
+    series = e <= EPS_SERIES && ctx->inject_fp64_ortho == 0;
+    ctx->last_ortho_err = e;
   }
-  // 4. C = Linv H~ Linv^H (symmetrised) into A0
-  SPARC_CUDA(ctx, (gemm64<TW, false, false>(ctx, ns, ns, ns, Li, ns, Hs, ns, T1, ns, 1.0, 0.0, partH, pcap, st)));
-  SPARC_CUDA(ctx, (gemm64<TW, false, true>(ctx, ns, ns, ns, T1, ns, Li, ns, Yr, ns, 1.0, 0.0, partH, pcap, st)));
-  k_reduce_sym<TW><<<ceil_div(nn, 256), 256, 0, st>>>(Yr, 1, nn, ns, A0);
-  ++ctx->launches;
+  TW* Kc = Li;   // series: K = (I + F)^-1 - I, Linv = I + K
+  if constexpr (TCP) {
+    if (series) {
+      double* E = (double*)A1;
+      double* F = (double*)Vj;
+      double* G = (double*)Qs;
+      // 3'. F lower triangular with (I + F)(I + F)^T = I + E: F = Phi(E - F F^T),
+      // iterated from F = Phi(E); each pass gains a power of |E| (|E|^5 after four)
+      k_phi<<<ceil_div(nn, 256), 256, 0, st>>>(E, nullptr, ns, F);
+      ++ctx->launches;
+      for (int it = 0; it < 3; ++it) {
+        SPARC_CUDA(ctx, (gemm<double, double, float, double, false, true>(ctx, ns, ns, ns, F, ns, F, ns, G, ns, 1,
+                                                                          nn, 1.0, st)));
+        k_phi<<<ceil_div(nn, 256), 256, 0, st>>>(E, G, ns, F);
+        ++ctx->launches;
+      }
+      // K = (I + F)^-1 - I = -F (I - F (I - F (I - F))), error |F|^5
+      double* Ta = (double*)Yr;
+      double* Tb = (double*)T1;
+      k_i_minus<<<ceil_div(nn, 256), 256, 0, st>>>(F, ns, Ta);
+      ++ctx->launches;
+      for (int it = 0; it < 2; ++it) {
+        k_identity<double><<<ceil_div(nn, 256), 256, 0, st>>>(Tb, ns);
+        ++ctx->launches;
+        SPARC_CUDA(ctx, (gemm<double, double, float, double, false, false>(ctx, ns, ns, ns, F, ns, Ta, ns, Tb, ns, 1,
+                                                                           nn, -1.0, st, 1.0)));
+        std::swap(Ta, Tb);
+      }
+      SPARC_CUDA(ctx, (gemm<double, double, float, double, false, false>(ctx, ns, ns, ns, F, ns, Ta, ns,
+                                                                         (double*)Kc, ns, 1, nn, -1.0, st)));
+      // 4'. C = (I + K) H~ (I + K)^T = H~ + P + P^T + P K^T with P = K H~; the
+      // corrections are O(|K| |H~|), so their FP32 products are FP64-accurate in C
+      double* P = (double*)T1;
+      double* Q = (double*)Yr;
+      SPARC_CUDA(ctx, (gemm<double, double, float, double, false, false>(ctx, ns, ns, ns, (const double*)Kc, ns,
+                                                                         (const double*)Hs, ns, P, ns, 1, nn, 1.0,
+                                                                         st)));
+      SPARC_CUDA(ctx, (gemm<double, double, float, double, false, true>(ctx, ns, ns, ns, P, ns, (const double*)Kc, ns,
+                                                                        Q, ns, 1, nn, 1.0, st)));
+      k_csum<<<ceil_div(nn, 256), 256, 0, st>>>((const double*)Hs, P, Q, ns, (double*)A0);
+      ++ctx->launches;
+    }
+  }
+  if (!series) {
+    // 3. M~ = L L^H (blocked, FP64) and Linv = L^-1
+    s = chol_inverse<TW>(ctx, Ms, Li, ns, Dinv, T1, partH, pcap, st);
+    if (s != SPARC_OK) return s;
+    int word = 0;
+    SPARC_CUDA(ctx, cudaMemcpyAsync(&word, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SPARC_CUDA(ctx, cudaStreamSynchronize(st));
+    if (word & STATUS_NOT_POSDEF) {
+      cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st);
+      return fail(ctx, SPARC_ERR_NOT_POSDEF, "M~ = U^H U is not positive definite");
+    }
+    // 4. C = Linv H~ Linv^H (symmetrised) into A0
+    SPARC_CUDA(ctx, (gemm64<TW, false, false>(ctx, ns, ns, ns, Li, ns, Hs, ns, T1, ns, 1.0, 0.0, partH, pcap, st)));
+    SPARC_CUDA(ctx, (gemm64<TW, false, true>(ctx, ns, ns, ns, T1, ns, Li, ns, Yr, ns, 1.0, 0.0, partH, pcap, st)));
+    k_reduce_sym<TW><<<ceil_div(nn, 256), 256, 0, st>>>(Yr, 1, nn, ns, A0);
+    ++ctx->launches;
+  }
   int sweeps = 0;
   if (!mixed) {
     // 5a. FP64 Jacobi on C; eigenvalues from the converged diagonal
@@ -1043,8 +1220,16 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
     ++ctx->launches;
   }
   ctx->last_sweeps = sweeps;
-  // 6. Ritz vectors of the pencil: Yr = Linv^H Q
-  SPARC_CUDA(ctx, (gemm64<TW, true, false>(ctx, ns, ns, ns, Li, ns, Qs, ns, Yr, ns, 1.0, 0.0, partH, pcap, st)));
+  // 6. Ritz vectors of the pencil: Yr = Linv^H Q (series: Q + K^T Q)
+  if (series) {
+    SPARC_CUDA(ctx, cudaMemcpyAsync(Yr, Qs, nn * sizeof(TW), cudaMemcpyDeviceToDevice, st));
+    if constexpr (TCP)
+      SPARC_CUDA(ctx, (gemm<double, double, float, double, true, false>(ctx, ns, ns, ns, (const double*)Kc, ns,
+                                                                        (const double*)Qs, ns, (double*)Yr, ns, 1,
+                                                                        nn, 1.0, st, 1.0)));
+  } else {
+    SPARC_CUDA(ctx, (gemm64<TW, true, false>(ctx, ns, ns, ns, Li, ns, Qs, ns, Yr, ns, 1.0, 0.0, partH, pcap, st)));
+  }
   // 7. rotation U <- U Yr (into HU, then back into U)
   if constexpr (!TCP) {
     k_narrow<TW, T><<<ceil_div(nn, 256), 256, 0, st>>>(Yr, YrT, nn);

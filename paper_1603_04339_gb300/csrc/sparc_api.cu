@@ -542,6 +542,12 @@ sparc_status sparc_last_sweeps(const sparc_ctx* ctx, int* sweeps) {
   return SPARC_OK;
 }
 
+sparc_status sparc_last_ortho_err(const sparc_ctx* ctx, double* err) {
+  if (!ctx || !err) return SPARC_ERR_INVALID_ARG;
+  *err = ctx->last_ortho_err;
+  return SPARC_OK;
+}
+
 sparc_status sparc_debug_inject(sparc_ctx* ctx, int what, int64_t value) {
   if (!ctx) return SPARC_ERR_INVALID_ARG;
   switch (what) {
@@ -549,6 +555,7 @@ sparc_status sparc_debug_inject(sparc_ctx* ctx, int what, int64_t value) {
     case SPARC_INJECT_WAIT_LIMIT: ctx->inject_wait_limit = std::max<int64_t>(0, value); return SPARC_OK;
     case SPARC_INJECT_STALL: ctx->inject_stall = value < 0 ? -1 : (int)value; return SPARC_OK;
     case SPARC_INJECT_CG_MAX_ITERS: ctx->inject_cg_max = (int)std::max<int64_t>(0, value); return SPARC_OK;
+    case SPARC_INJECT_FP64_ORTHO: ctx->inject_fp64_ortho = (int)std::min<int64_t>(2, std::max<int64_t>(0, value)); return SPARC_OK;
   }
   return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_debug_inject: unknown injection");
 }

@@ -25,7 +25,7 @@ STATUS = {0: "SPARC_OK", 1: "SPARC_ERR_INVALID_ARG", 2: "SPARC_ERR_OOM", 3: "SPA
 EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_sync", "sparc_ham_create",
            "sparc_ham_set_veff", "sparc_ham_destroy", "sparc_apply_H", "sparc_cheb_filter",
            "sparc_lanczos_bounds", "sparc_rayleigh_ritz", "sparc_timing_enable", "sparc_timing_read",
-           "sparc_launch_count", "sparc_apply_H_noalloc", "sparc_last_sweeps", "sparc_gram_f32",
+           "sparc_launch_count", "sparc_apply_H_noalloc", "sparc_last_sweeps", "sparc_last_ortho_err", "sparc_gram_f32",
            "sparc_rotate_f32", "sparc_scf_create", "sparc_scf_step", "sparc_scf_read", "sparc_scf_destroy",
            "sparc_scf_forces", "sparc_cheb_filter_batch", "sparc_autotune_filter",
            "sparc_set_filter_units", "sparc_filter_graph_create", "sparc_filter_graph_set_bounds",
@@ -101,6 +101,8 @@ def load(path: str = LIB_PATH):
     L.sparc_launch_count.argtypes = [c_void_p, POINTER(c_int64)]
     L.sparc_last_sweeps.argtypes = [c_void_p, POINTER(c_int)]
     L.sparc_last_sweeps.restype = c_int
+    L.sparc_last_ortho_err.argtypes = [c_void_p, POINTER(ctypes.c_double)]
+    L.sparc_last_ortho_err.restype = c_int
     L.sparc_debug_inject.argtypes = [c_void_p, c_int, c_int64]
     L.sparc_debug_inject.restype = c_int
     L.sparc_apply_H_noalloc.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_int, c_int64, c_void_p]
@@ -224,10 +226,16 @@ class Context:
         self.check(load().sparc_last_sweeps(self.handle, ctypes.byref(n)))
         return n.value
 
+    def last_ortho_err(self) -> float:
+        """max |U1^T U1 - I| of the last mixed FP32 Rayleigh-Ritz (sparc_last_ortho_err)."""
+        e = ctypes.c_double(0.0)
+        self.check(load().sparc_last_ortho_err(self.handle, ctypes.byref(e)))
+        return e.value
+
     def inject(self, what: str, value: int):
         """Failure injection for tests of the error paths (sparc_debug_inject):
-        what = 'alloc_fail' | 'wait_limit' | 'stall' | 'cg_max_iters'."""
-        code = {"alloc_fail": 1, "wait_limit": 2, "stall": 3, "cg_max_iters": 4}[what]
+        what = 'alloc_fail' | 'wait_limit' | 'stall' | 'cg_max_iters' | 'fp64_ortho'."""
+        code = {"alloc_fail": 1, "wait_limit": 2, "stall": 3, "cg_max_iters": 4, "fp64_ortho": 5}[what]
         self.check(load().sparc_debug_inject(self.handle, code, int(value)))
 
     def launches(self) -> int:

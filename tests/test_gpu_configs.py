@@ -202,12 +202,24 @@ def test_mixed_rayleigh_ritz_matches_oracle_at_ns256(ctx):
     a = a0 + (b - a0) * (ns / wl.nd) ** (2.0 / 3.0)
     sparc.sparc_cheb_filter(H, wl.m, a, b, a0, Xd, Yd)
     Y = Yd.cpu().numpy().astype(np.float64)                 # the block both sides project
-    eig = torch.zeros(ns, dtype=torch.float64, device="cuda")
-    sparc.sparc_rayleigh_ritz(H, Yd, eig, sparc.RR_MIXED)
-    torch.cuda.synchronize()
     lam_ref, _, _, _ = O.rayleigh_ritz(Hor, Y)
-    d = np.abs(eig.cpu().numpy() - lam_ref)
-    print(f"mixed RR vs oracle at Ns=256: max {d.max():.3e} Ha over [{lam_ref[0]:.4f}, {lam_ref[-1]:.4f}]")
-    assert d.max() < 1e-6, d.max()
-    U = Yd.to(torch.float64)
-    assert float((U @ U.T - torch.eye(ns, dtype=torch.float64, device="cuda")).abs().max()) < 5e-5
+    # default: FP32 scaled Cholesky, then the series factorisation of I + E; then the
+    # FP64 fallbacks of the second (1) and of both (2) orthonormalisations
+    for force in (0, 1, 2):
+        U32 = Yd.clone()
+        eig = torch.zeros(ns, dtype=torch.float64, device="cuda")
+        ctx.inject("fp64_ortho", force)
+        try:
+            sparc.sparc_rayleigh_ritz(H, U32, eig, sparc.RR_MIXED)
+            torch.cuda.synchronize()
+        finally:
+            ctx.inject("fp64_ortho", 0)
+        d = np.abs(eig.cpu().numpy() - lam_ref)
+        err = ctx.last_ortho_err()
+        print(f"mixed RR (fp64_ortho={force}) vs oracle at Ns=256: max {d.max():.3e} Ha over "
+              f"[{lam_ref[0]:.4f}, {lam_ref[-1]:.4f}]; max |U1^T U1 - I| = {err:.2e}")
+        assert d.max() < 1e-6, (force, d.max())
+        if force == 0:
+            assert 0.0 <= err <= 1e-3, err     # the series path ran
+        U = U32.to(torch.float64)
+        assert float((U @ U.T - torch.eye(ns, dtype=torch.float64, device="cuda")).abs().max()) < 5e-5

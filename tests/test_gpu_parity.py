@@ -178,8 +178,10 @@ def test_rayleigh_ritz_fp64_matches_oracle(ctx, dt, k):
     assert _projector_err(U, Uref, lam_ref) < 1e-9
 
 
-@pytest.mark.parametrize("dt,k", [("f32", (0, 0, 0)), ("c64", (0.2, 0.1, -0.25))])
-def test_rayleigh_ritz_mixed_matches_oracle(ctx, dt, k):
+@pytest.mark.parametrize("dt,k,force", [("f32", (0, 0, 0), 0), ("f32", (0, 0, 0), 1), ("f32", (0, 0, 0), 2),
+                                         ("c64", (0.2, 0.1, -0.25), 0)])
+def test_rayleigh_ritz_mixed_matches_oracle(ctx, dt, k, force):
+    """force: the FP32 path's FP64 fallbacks (1: second orthonormalisation, 2: both)."""
     from paper_1603_04339_gb300 import sparc
     wl = synth.small_case(n=(16, 18, 17), natom=3, k=k, seed=62)
     H = _ham(ctx, wl)
@@ -190,10 +192,29 @@ def test_rayleigh_ritz_mixed_matches_oracle(ctx, dt, k):
     Yf = O.cheb_filter(Hor, X, 8, a0 + 0.05 * (b - a0), b, a0).astype(NPDT[dt])
     Ud = torch.from_numpy(Yf).cuda()
     eig = torch.zeros(ns, dtype=torch.float64, device="cuda")
-    sparc.sparc_rayleigh_ritz(H, Ud, eig, sparc.RR_MIXED)
-    torch.cuda.synchronize()
+    ctx.inject("fp64_ortho", force)
+    try:
+        sparc.sparc_rayleigh_ritz(H, Ud, eig, sparc.RR_MIXED)
+        torch.cuda.synchronize()
+    finally:
+        ctx.inject("fp64_ortho", 0)
     lam_ref, _, _, _ = O.rayleigh_ritz(Hor, Yf.astype(np.complex128 if Hor.is_complex else np.float64))
     assert np.max(np.abs(eig.cpu().numpy() - lam_ref)) < 1e-6
+
+
+def test_mixed_not_positive_definite_is_reported(ctx):
+    """A rank-deficient FP32 block: the FP32 Cholesky fails, its FP64 fallback fails
+    too, and the call reports NOT_POSDEF with the status word cleared."""
+    from paper_1603_04339_gb300 import sparc
+    wl = synth.small_case(n=(14, 14, 14), natom=1, seed=73)
+    H = _ham(ctx, wl)
+    U = torch.randn((6, wl.nd), dtype=torch.float32, device="cuda")
+    U[4] = U[2]
+    eig = torch.zeros(6, dtype=torch.float64, device="cuda")
+    with pytest.raises(sparc.SparcError) as e:
+        sparc.sparc_rayleigh_ritz(H, U, eig, sparc.RR_MIXED)
+    assert e.value.code == 4
+    ctx.sync()
 
 
 def test_invalid_arguments_are_reported(ctx):
