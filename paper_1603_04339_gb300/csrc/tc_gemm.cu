@@ -19,7 +19,10 @@
 // Rotation  C = U Yr (Nd x Ns): one CTA per (128 grid rows, 256 columns); Yr is
 //   split and swizzled once into its shared-memory images, U is split and
 //   transposed to K-major on its way into shared memory.
+#include <cuda.h>
+
 #include <algorithm>
+#include <mutex>
 
 #include "ptx.cuh"
 #include "rr.cuh"
@@ -82,6 +85,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+// the same for 16 consecutive columns
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
@@ -264,6 +277,228 @@ k_gram_tc(const float* __restrict__ A, long long lda, const float* __restrict__ 
   if (warp == 0) tmem_free(tmem, 2 * GN);
 }
 
+// ------------------------------------------------------------------ Gram, TMA-fed
+// The same partials from a CTA of 16 warps fed by the tensor memory accelerator:
+//   * loads: each k-tile of A and B (32 grid points x 128 columns, K-major: the
+//     columns are contiguous in the grid index) arrives by cp.async.bulk.tensor in the
+//     128-byte swizzle the MMA reads, into a 3-stage ring;
+//   * all warps split each landed tile in place into its TF32 high part and the
+//     remainder (a second image), then, every GCH k-tiles, drain the finished FP32 TMEM
+//     chunk into float-float accumulators in registers (TwoSum: the GPU's FP64 rate
+//     would make FP64 adds the bottleneck);
+//   * the 12 MMAs of a k-tile (3xTF32) go into one of two TMEM accumulator pairs,
+//     alternating per chunk, so that a chunk drains while the next accumulates.
+// Lane 0 of warp 0 issues the loads and lane 0 of warp 1 the MMAs.  Neither role may
+// block behind the others, so both run as non-blocking steps polled from every wait
+// loop of their warps.  Every wait is bounded; one that runs out latches
+// STATUS_TIMEOUT and raises the CTA's abort flag, and the CTA winds down (in-flight
+// copies and MMAs waited for, with bounds) before it frees its TMEM.
+constexpr int TTHREADS = 512;
+constexpr int TST = 3;                         // ring stages
+constexpr int TSTAGE = 4 * TILE_A;             // A_hi, A_lo, B_hi, B_lo (64 KB)
+constexpr int TSMEM = TST * TSTAGE + 1024;
+
+__device__ __forceinline__ void tma2(uint32_t dst, const CUtensorMap* m, int c0, int c1, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(dst), "l"(m), "r"(c0), "r"(c1), "r"(saddr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
+}
+__device__ __forceinline__ void two_sum(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  const float ap = s - bp;
+  lo += (hi - ap) + (x - bp);
+  hi = s;
+}
+
+struct GramRing {
+  uint64_t full[TST], conv[TST], mmad[TST], accd[2], tfree[2];
+  int abort_flag;
+  // role state (one thread each): next k-tile to load (pt) and to multiply (mt)
+  int pt, mt;
+  int nkt, i0, j0;
+  long long kt0;
+  uint32_t tmem, sm;
+};
+
+// One non-blocking step of the load role (producer) or of the MMA role: issue what the
+// barriers allow, return.  Kept out of line so that only the two role threads pay for
+// its registers.
+__device__ __noinline__ void gram_poll(GramRing* R, const CUtensorMap* ma, const CUtensorMap* mb, bool producer) {
+  if (producer) {
+    int pt = R->pt;
+    while (pt < R->nkt) {   // a stage is free once the MMAs of its previous tile are done
+      const int s = pt % TST;
+      if (pt >= TST && !ptx::mbar_test(&R->mmad[s], (uint32_t)((pt / TST) - 1) & 1u)) break;
+      const uint32_t st = R->sm + (uint32_t)(s * TSTAGE);
+      ptx::mbar_arrive_expect_tx(&R->full[s], 2 * TILE_A);
+      const int g0 = (int)((R->kt0 + pt) * BK);
+      tma2(st, ma, g0, R->i0, &R->full[s]);
+      tma2(st + 2 * TILE_A, mb, g0, R->j0, &R->full[s]);
+      ++pt;
+    }
+    R->pt = pt;
+  } else {
+    constexpr uint32_t IDESC = idesc_tf32(BM, GN);
+    int mt = R->mt;
+    while (mt < R->nkt) {
+      const int s = mt % TST, c = mt / GCH, b = c & 1;
+      if (!ptx::mbar_test(&R->conv[s], (uint32_t)(mt / TST) & 1u)) break;
+      if (mt % GCH == 0 && c >= 2 && !ptx::mbar_test(&R->tfree[b], (uint32_t)((c / 2) - 1) & 1u)) break;
+      tc_after();
+      const uint32_t b0 = R->sm + (uint32_t)(s * TSTAGE);
+      const uint32_t d = R->tmem + (uint32_t)(b * 2 * GN);
+      mma_ktile(d, d + GN, b0, b0 + TILE_A, b0 + 2 * TILE_A, b0 + 3 * TILE_A, IDESC, mt % GCH == 0);
+      mma_commit(&R->mmad[s]);
+      if (mt % GCH == GCH - 1 || mt == R->nkt - 1) mma_commit(&R->accd[b]);
+      ++mt;
+    }
+    R->mt = mt;
+  }
+}
+
+__global__ void __launch_bounds__(TTHREADS, 1)
+k_gram_tma(const __grid_constant__ CUtensorMap ma, const __grid_constant__ CUtensorMap mb, long long nd, int nt,
+           int nsplit, double* __restrict__ part, int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ GramRing R;
+  __shared__ uint32_t tmem_base;
+  const uint32_t raw = saddr(smem_raw);
+  uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  int pr = blockIdx.x, ti = 0;
+  while (pr >= nt - ti) { pr -= nt - ti; ++ti; }
+  const int tj = ti + pr;
+  const int sp = blockIdx.y;
+  const long long nkt_all = (nd + BK - 1) / BK;
+  const long long kt0 = nkt_all * sp / nsplit;
+  const int nkt = (int)(nkt_all * (sp + 1) / nsplit - kt0);
+  double* P = part + (size_t)(blockIdx.x * nsplit + sp) * (BM * GN);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (nkt <= 0) {
+    for (int e = threadIdx.x; e < BM * GN; e += TTHREADS) P[e] = 0.0;
+    return;
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TST; ++s) {
+      mbar_init(&R.full[s], 1);
+      mbar_init(&R.conv[s], 16);
+      mbar_init(&R.mmad[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&R.accd[b], 1);
+      mbar_init(&R.tfree[b], 16);
+    }
+    R.abort_flag = 0;
+    R.pt = 0;
+    R.mt = 0;
+    R.nkt = nkt;
+    R.i0 = ti * BM;
+    R.j0 = tj * GN;
+    R.kt0 = kt0;
+    R.sm = saddr(sm);
+    ptx::mbar_init_fence();
+  }
+  if (warp == 0) tmem_alloc(&tmem_base, 4 * GN);   // two (D, Ds) pairs: 512 columns
+  tc_before();
+  __syncthreads();
+  if (threadIdx.x == 0) R.tmem = tmem_base;
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = tmem_base;
+  const int nchunk = (nkt + GCH - 1) / GCH;
+  volatile int* abort_flag = &R.abort_flag;
+  const bool producer = threadIdx.x == 0, issuer = threadIdx.x == 32;
+  auto poll = [&]() {
+    if (producer || issuer) gram_poll(&R, &ma, &mb, producer);
+  };
+  // bounded wait for a phase, stepping this thread's roles meanwhile
+  auto wait = [&](uint64_t* b, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!ptx::mbar_test(b, parity)) {
+      poll();
+      if (*abort_flag) return false;
+      if (clock64() - t0 > (1LL << 32)) {
+        *abort_flag = 1;
+        return false;
+      }
+    }
+    return true;
+  };
+  float ahi[32], alo[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) ahi[c] = alo[c] = 0.f;
+  const int row = 32 * (warp & 3) + lane;          // TMEM lane = output row i
+  const int col0 = (warp >> 2) * 32;                // 32 output columns j
+  int drained = 0;
+  auto drain = [&](int c) {
+    const int b = c & 1;
+    if (!wait(&R.accd[b], (uint32_t)(c / 2) & 1u)) return false;
+    tc_after();
+    const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(b * 2 * GN + col0);
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {   // a_hi b_hi (h = 0, 1), then the cross terms (h = 2, 3)
+      float v[16];
+      tmem_ld16(ta + (uint32_t)((h >> 1) * GN + 16 * (h & 1)), v);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) two_sum(ahi[16 * (h & 1) + q], alo[16 * (h & 1) + q], v[q]);
+    }
+    tc_before();
+    __syncwarp();
+    if (lane == 0) arrive(&R.tfree[b]);
+    return true;
+  };
+  poll();
+  bool ok = true;
+  for (int t = 0; t < nkt && ok; ++t) {
+    const int s = t % TST;
+    if (!wait(&R.full[s], (uint32_t)(t / TST) & 1u)) { ok = false; break; }
+    // split the 2048 16-byte chunks of the stage's A and B images: hi in place, lo beside
+    uint8_t* st = sm + s * TSTAGE;
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+      const int f = (int)threadIdx.x + TTHREADS * q;              // 0 .. 2047
+      uint8_t* img = st + (f < 1024 ? 0 : 2 * TILE_A) + 16 * (f & 1023);
+      float4 x = *(const float4*)img, h, l;
+      split4(x, h, l);
+      *(float4*)img = h;
+      *(float4*)(img + TILE_A) = l;
+    }
+    proxy_fence();
+    __syncwarp();
+    if (lane == 0) arrive(&R.conv[s]);
+    poll();
+    if (t % GCH == GCH / 2 && drained < t / GCH) ok = drain(drained++);
+  }
+  while (ok && drained < nchunk) ok = drain(drained++);
+  if (ok) {
+#pragma unroll
+    for (int q = 0; q < 32; ++q) P[(size_t)(col0 + q) * BM + row] = (double)ahi[q] + (double)alo[q];
+  }
+  // wind down: the loads issued and the MMAs committed complete before TMEM is freed
+  if (producer) {
+    const int pt = R.pt;
+    for (int t = (pt > TST ? pt - TST : 0); t < pt; ++t) {
+      const long long c0 = clock64();
+      while (!ptx::mbar_test(&R.full[t % TST], (uint32_t)(t / TST) & 1u))
+        if (clock64() - c0 > (1LL << 32)) break;
+    }
+  }
+  if (issuer && R.mt > 0) {
+    const int mt = R.mt;
+    const long long c0 = clock64();
+    while (!ptx::mbar_test(&R.mmad[(mt - 1) % TST], (uint32_t)((mt - 1) / TST) & 1u))
+      if (clock64() - c0 > (1LL << 32)) break;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(status, STATUS_TIMEOUT);
+  tc_after();
+  if (warp == 0) tmem_free(tmem, 4 * GN);
+}
+
 // G[i + j ns] from the partials: fixed-order sum over splits; tile pairs below the
 // diagonal are the transposes of those above; diagonal tiles are symmetrised.
 __global__ void k_gram_reduce(const double* __restrict__ part, int nt, int nsplit, int ns, double* __restrict__ G) {
@@ -426,6 +661,35 @@ size_t gram_scratch_bytes(const sparc_ctx* ctx, int ns, long long nd) {
   return (size_t)(nt * (nt + 1) / 2) * gram_nsplit(ctx, ns, nd) * BM * GN * sizeof(double);
 }
 
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiled encoder() {
+  static EncodeTiled fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiled)p;
+  });
+  return fn;
+}
+// Tensor map of a column-major nd x ns FP32 operand: boxes of 32 grid points x 128
+// columns in the 128-byte swizzle (the K-major layout of the MMA's operand images);
+// points past nd and columns past ns read as zero.
+static bool map_operand(CUtensorMap* m, const float* X, long long ldx, long long nd, int ns) {
+  const cuuint64_t dims[2] = {(cuuint64_t)nd, (cuuint64_t)ns};
+  const cuuint64_t strides[1] = {(cuuint64_t)ldx * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+  const cuuint32_t es[2] = {1, 1};
+  return encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)X, dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t gram(sparc_ctx* ctx, const float* A, long long lda, const float* B, long long ldb, long long nd, int ns,
                  double* G, void* scratch, cudaStream_t st) {
   const int nt = ceil_div(ns, BM);
@@ -434,7 +698,13 @@ cudaError_t gram(sparc_ctx* ctx, const float* A, long long lda, const float* B, 
   const bool vec = (lda % 4 == 0) && (ldb % 4 == 0) && (nd % 4 == 0) && ((uintptr_t)A % 16 == 0) &&
                    ((uintptr_t)B % 16 == 0);
   cudaError_t e;
-  if (vec) {
+  CUtensorMap ma, mb;
+  if (vec && encoder() != nullptr && map_operand(&ma, A, lda, nd, ns) && map_operand(&mb, B, ldb, nd, ns)) {
+    e = cudaFuncSetAttribute(k_gram_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, TSMEM);
+    if (e != cudaSuccess) return e;
+    k_gram_tma<<<dim3(pairs, nsplit), TTHREADS, TSMEM, st>>>(ma, mb, nd, nt, nsplit, (double*)scratch,
+                                                              ctx->d_status);
+  } else if (vec) {
     e = cudaFuncSetAttribute(k_gram_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, GSMEM);
     if (e != cudaSuccess) return e;
     k_gram_tc<true><<<dim3(pairs, nsplit), GTHREADS, GSMEM, st>>>(A, lda, B, ldb, nd, ns, nt, nsplit,

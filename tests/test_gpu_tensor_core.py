@@ -34,8 +34,11 @@ def _orbitals(nd, ns, ld, seed):
 
 
 @pytest.mark.parametrize("nd,ns,pad", [(4096, 128, 0), (3001, 130, 3), (8192, 300, 0), (777, 1, 1),
-                                       (65536, 512, 0)])
+                                       (65536, 512, 0), (4100, 200, 4), (96, 40, 0)])
 def test_gram_matches_fp64_product(ctx, nd, ns, pad):
+    """Leading dimensions and nd that are multiples of 4 take the TMA-fed kernel
+    (ragged last k-tile and columns past ns read as zero from the tensor map); the
+    others the register-staged one."""
     from paper_1603_04339_gb300 import sparc
     # B = D A with a diagonal D on the grid, like H U: the exact G = A^T D A is symmetric,
     # which the library assumes (it computes the tiles on and above the diagonal)
