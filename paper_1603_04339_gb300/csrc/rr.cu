@@ -417,16 +417,73 @@ constexpr int BJ = 16;
 // local index l of pair k's 32 indices -> global index
 __device__ __forceinline__ int bj_index(int l, int bp, int bq) { return l < BJ ? BJ * bp + l : BJ * bq + (l - BJ); }
 
+// rotation of the pair (p, q) of pair subproblem S (local indices; global bp, bq blocks):
+// the rotation of jacobi_rot, t = sign(th)/(|th| + sqrt(th^2 + 1)) with th = d/(2b),
+// d = S_qq - S_pp, b = S_pq, written as t = sign(d) 2b / (|d| + sqrt(d^2 + 4b^2)) and
+// evaluated with the approximate reciprocal and reciprocal square root (a few ulp):
+// the rotations' small departure from orthogonality is removed afterwards by the
+// Newton-Schulz step, and the eigenvalues come from FP64 Rayleigh quotients.
+__device__ __forceinline__ void bj_rot(const float (&S)[2 * BJ][2 * BJ + 1], int p, int q, int bp, int bq, int n,
+                                       float& c, float& sn) {
+  c = 1.f;
+  sn = 0.f;
+  const int gp = bj_index(p, bp, bq), gq = bj_index(q, bp, bq);
+  const float b = S[p][q];
+  if (gp < n && gq < n && b != 0.f) {
+    const float d = S[q][q] - S[p][p];
+    const float b2 = 2.f * b;
+    const float r2 = fmaf(d, d, b2 * b2);
+    const float rt = r2 * rsqrtf(r2);
+    const float tt = __fdividef(d >= 0.f ? b2 : -b2, fabsf(d) + rt);
+    c = rsqrtf(fmaf(tt, tt, 1.f));
+    sn = tt * c;
+  }
+}
+
+// One cyclic sweep over the pair subproblem S (32 x 32, in shared memory), its rotations
+// accumulated into W (identity on entry) and stored as the pair's rotation Wbuf[k].
+__device__ __forceinline__ void bj_pair_sweep(float (&S)[2 * BJ][2 * BJ + 1], float (&W)[2 * BJ][2 * BJ + 1],
+                                              float* __restrict__ Wbuf, int n, int bp, int bq, int k) {
+  const int t = threadIdx.x;
+  // thread (x, y): the 2 x 2 block (pair x rows, pair y columns) of S and rows 2y, 2y+1
+  // of W's pair-x columns.  Every thread computes the two rotations it needs from the
+  // same entries (identical arithmetic, identical results), so a round is one read
+  // phase and one write phase.
+  const int x = t % BJ, y = t / BJ;
+  for (int rr = 0; rr < 2 * BJ - 1; ++rr) {
+    const int i0 = rr_player(x, rr, 2 * BJ), i1 = rr_player(2 * BJ - 1 - x, rr, 2 * BJ);
+    const int j0 = rr_player(y, rr, 2 * BJ), j1 = rr_player(2 * BJ - 1 - y, rr, 2 * BJ);
+    float cx, sx, cy, sy;
+    bj_rot(S, i0, i1, bp, bq, n, cx, sx);
+    bj_rot(S, j0, j1, bp, bq, n, cy, sy);
+    const float a00 = S[i0][j0], a01 = S[i0][j1], a10 = S[i1][j0], a11 = S[i1][j1];
+    const float w00 = W[2 * y][i0], w01 = W[2 * y][i1], w10 = W[2 * y + 1][i0], w11 = W[2 * y + 1][i1];
+    // rows: [r0; r1] = [[c, -s], [s, c]] [a0; a1] (the rotation [[c, s], [-s, c]] transposed)
+    const float b00 = cx * a00 - sx * a10, b01 = cx * a01 - sx * a11;
+    const float b10 = sx * a00 + cx * a10, b11 = sx * a01 + cx * a11;
+    __syncthreads();
+    S[i0][j0] = cy * b00 - sy * b01;
+    S[i0][j1] = sy * b00 + cy * b01;
+    S[i1][j0] = cy * b10 - sy * b11;
+    S[i1][j1] = sy * b10 + cy * b11;
+    // W <- W R (columns i0, i1)
+    W[2 * y][i0] = cx * w00 - sx * w01;
+    W[2 * y][i1] = sx * w00 + cx * w01;
+    W[2 * y + 1][i0] = cx * w10 - sx * w11;
+    W[2 * y + 1][i1] = sx * w10 + cx * w11;
+    __syncthreads();
+  }
+  float* Wk = Wbuf + (size_t)k * 4 * BJ * BJ;
+  for (int e = t; e < 4 * BJ * BJ; e += 256) Wk[e] = W[e % (2 * BJ)][e / (2 * BJ)];
+  __syncthreads();
+}
+
 // One CTA per block pair: W = the product of the rotations of one cyclic sweep over the
 // pair's 32 x 32 subproblem (rotations as jacobi_rot; indices >= n give the identity).
-__global__ void __launch_bounds__(256) k_bj_pair(const float* __restrict__ A, float* __restrict__ Wbuf, int n,
-                                                 int nbk, int r) {
+__device__ __forceinline__ void bj_pair_body(const float* __restrict__ A, float* __restrict__ Wbuf, int n, int nbk,
+                                             int r, int k) {
   __shared__ float S[2 * BJ][2 * BJ + 1];
   __shared__ float W[2 * BJ][2 * BJ + 1];
-  __shared__ float rc[BJ], rs[BJ];
-  __shared__ int rp[BJ], rq[BJ];
-  asm volatile("griddepcontrol.wait;\n" ::: "memory");
-  const int k = blockIdx.x;
   const int bp = rr_player(k, r, nbk), bq = rr_player(nbk - 1 - k, r, nbk);
   const int t = threadIdx.x;
   for (int e = t; e < 4 * BJ * BJ; e += 256) {
@@ -436,63 +493,27 @@ __global__ void __launch_bounds__(256) k_bj_pair(const float* __restrict__ A, fl
     W[i][j] = (i == j) ? 1.f : 0.f;
   }
   __syncthreads();
-  for (int rr = 0; rr < 2 * BJ - 1; ++rr) {
-    if (t < BJ) {
-      const int p = rr_player(t, rr, 2 * BJ), q = rr_player(2 * BJ - 1 - t, rr, 2 * BJ);
-      float c = 1.f, sn = 0.f;
-      const int gp = bj_index(p, bp, bq), gq = bj_index(q, bp, bq);
-      const float b = S[p][q];
-      if (gp < n && gq < n && b != 0.f) {
-        const float th = (S[q][q] - S[p][p]) / (2.f * b);
-        const float tt = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(th * th + 1.f));
-        c = 1.f / sqrtf(tt * tt + 1.f);
-        sn = tt * c;
-      }
-      rc[t] = c; rs[t] = sn; rp[t] = p; rq[t] = q;
-    }
-    __syncthreads();
-    {   // S <- R^T S R on the 2 x 2 block (pair x, pair y)
-      const int x = t % BJ, y = t / BJ;
-      const int i0 = rp[x], i1 = rq[x], j0 = rp[y], j1 = rq[y];
-      const float cx = rc[x], sx = rs[x], cy = rc[y], sy = rs[y];
-      const float a00 = S[i0][j0], a01 = S[i0][j1], a10 = S[i1][j0], a11 = S[i1][j1];
-      // rows: [r0; r1] = [[c, -s], [s, c]] [a0; a1] (the rotation [[c, s], [-s, c]] transposed)
-      const float b00 = cx * a00 - sx * a10, b01 = cx * a01 - sx * a11;
-      const float b10 = sx * a00 + cx * a10, b11 = sx * a01 + cx * a11;
-      __syncthreads();
-      S[i0][j0] = cy * b00 - sy * b01;
-      S[i0][j1] = sy * b00 + cy * b01;
-      S[i1][j0] = cy * b10 - sy * b11;
-      S[i1][j1] = sy * b10 + cy * b11;
-    }
-    // W <- W R (columns p, q)
-    for (int e = t; e < 2 * BJ * BJ; e += 256) {
-      const int i = e % (2 * BJ), x = e / (2 * BJ);
-      const int p = rp[x], q = rq[x];
-      const float w0 = W[i][p], w1 = W[i][q];
-      W[i][p] = rc[x] * w0 - rs[x] * w1;
-      W[i][q] = rs[x] * w0 + rc[x] * w1;
-    }
-    __syncthreads();
-  }
-  float* Wk = Wbuf + (size_t)k * 4 * BJ * BJ;
-  for (int e = t; e < 4 * BJ * BJ; e += 256) Wk[e] = W[e % (2 * BJ)][e / (2 * BJ)];
+  bj_pair_sweep(S, W, Wbuf, n, bp, bq, k);
+}
+
+__global__ void __launch_bounds__(256) k_bj_pair(const float* __restrict__ A, float* __restrict__ Wbuf, int n,
+                                                 int nbk, int r) {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  bj_pair_body(A, Wbuf, n, nbk, r, blockIdx.x);
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
 
 // A' = J^T A J (into An) and V <- V J for J = blockdiag(W_k): CTAs [0, np^2) compute the
 // 32 x 32 block (pair a, pair b) of A' = W_a^T A[I_a, I_b] W_b; the others the 32-row
 // blocks of V[:, I_k] W_k.
-__global__ void __launch_bounds__(256) k_bj_apply(const float* __restrict__ A, float* __restrict__ An, float* V,
-                                                  const float* __restrict__ Wbuf, int n, int nbk, int r) {
+__device__ __forceinline__ void bj_apply_body(const float* __restrict__ A, float* __restrict__ An, float* V,
+                                              const float* __restrict__ Wbuf, int n, int nbk, int r, int bid) {
   __shared__ float X[2 * BJ][2 * BJ + 1];
   __shared__ float Wl[2 * BJ][2 * BJ + 1];
   __shared__ float Wr[2 * BJ][2 * BJ + 1];
   __shared__ float Tm[2 * BJ][2 * BJ + 1];
-  asm volatile("griddepcontrol.wait;\n" ::: "memory");
   const int np = nbk / 2;
   const int t = threadIdx.x;
-  const int bid = blockIdx.x;
   if (bid < np * np) {
     const int ka = bid % np, kb = bid / np;
     const int ap = rr_player(ka, r, nbk), aq = rr_player(nbk - 1 - ka, r, nbk);
@@ -553,6 +574,13 @@ __global__ void __launch_bounds__(256) k_bj_apply(const float* __restrict__ A, f
       if (gr < n && gj < n) V[gr + (long long)gj * n] = acc;
     }
   }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_bj_apply(const float* __restrict__ A, float* __restrict__ An, float* V,
+                                                  const float* __restrict__ Wbuf, int n, int nbk, int r) {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  bj_apply_body(A, An, V, Wbuf, n, nbk, r, blockIdx.x);
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
 
@@ -905,8 +933,8 @@ sparc_status jacobi(sparc_ctx* ctx, TJ* A0, TJ* A1, TJ* V, int n, double tol, in
     cfg.stream = ctx->cap_stream;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    for (int r = 0; r < rounds; ++r) {
-      cudaError_t le = cudaSuccess;
+    cudaError_t le = cudaSuccess;
+    for (int r = 0; r < rounds && le == cudaSuccess; ++r) {
       if (blockj) {
         if constexpr (bj_type<TJ>()) {
           cudaLaunchConfig_t c1 = cfg, c2 = cfg;
@@ -921,12 +949,12 @@ sparc_status jacobi(sparc_ctx* ctx, TJ* A0, TJ* A1, TJ* V, int n, double tol, in
       } else {
         le = cudaLaunchKernelEx(&cfg, k_jacobi_round<TJ>, (const TJ*)a, b, V, n, npad, r % (npad - 1));
       }
-      if (le != cudaSuccess) {
-        cudaStreamEndCapture(ctx->cap_stream, &g);
-        if (g) cudaGraphDestroy(g);
-        return cuda_fail(ctx, le, "jacobi round launch");
-      }
       std::swap(a, b);
+    }
+    if (le != cudaSuccess) {
+      cudaStreamEndCapture(ctx->cap_stream, &g);
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(ctx, le, "jacobi round launch");
     }
     SPARC_CUDA(ctx, cudaStreamEndCapture(ctx->cap_stream, &g));
     cudaError_t e = cudaGraphInstantiate(&ge, g, 0);

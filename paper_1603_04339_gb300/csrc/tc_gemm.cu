@@ -281,9 +281,10 @@ k_gram_tc(const float* __restrict__ A, long long lda, const float* __restrict__ 
 // The same partials from a CTA of 16 warps fed by the tensor memory accelerator:
 //   * loads: each k-tile of A and B (32 grid points x 128 columns, K-major: the
 //     columns are contiguous in the grid index) arrives by cp.async.bulk.tensor in the
-//     128-byte swizzle the MMA reads, into a 3-stage ring;
+//     128-byte swizzle the MMA reads, into a ring of NH slots (four k-tiles in flight);
 //   * all warps split each landed tile in place into its TF32 high part and the
-//     remainder (a second image), then, every GCH k-tiles, drain the finished FP32 TMEM
+//     remainder, whose images go to a ring of NL slots (a slot is free once the MMAs of
+//     the k-tile NL before are done), then, every GCH k-tiles, drain the finished FP32 TMEM
 //     chunk into float-float accumulators in registers (TwoSum: the GPU's FP64 rate
 //     would make FP64 adds the bottleneck);
 //   * the 12 MMAs of a k-tile (3xTF32) go into one of two TMEM accumulator pairs,
@@ -294,9 +295,10 @@ k_gram_tc(const float* __restrict__ A, long long lda, const float* __restrict__ 
 // STATUS_TIMEOUT and raises the CTA's abort flag, and the CTA winds down (in-flight
 // copies and MMAs waited for, with bounds) before it frees its TMEM.
 constexpr int TTHREADS = 512;
-constexpr int TST = 3;                         // ring stages
-constexpr int TSTAGE = 4 * TILE_A;             // A_hi, A_lo, B_hi, B_lo (64 KB)
-constexpr int TSMEM = TST * TSTAGE + 1024;
+constexpr int TST = 5;                         // NH: slots of landed (then high-part) images
+constexpr int TLO = 2;                         // NL: slots of low-part images
+constexpr int TSTAGE = 2 * TILE_A;             // A, B (32 KB)
+constexpr int TSMEM = (TST + TLO) * TSTAGE + 1024;
 
 __device__ __forceinline__ void tma2(uint32_t dst, const CUtensorMap* m, int c0, int c1, uint64_t* bar) {
   asm volatile(
@@ -338,7 +340,7 @@ __device__ __noinline__ void gram_poll(GramRing* R, const CUtensorMap* ma, const
       ptx::mbar_arrive_expect_tx(&R->full[s], 2 * TILE_A);
       const int g0 = (int)((R->kt0 + pt) * BK);
       tma2(st, ma, g0, R->i0, &R->full[s]);
-      tma2(st + 2 * TILE_A, mb, g0, R->j0, &R->full[s]);
+      tma2(st + TILE_A, mb, g0, R->j0, &R->full[s]);
       ++pt;
     }
     R->pt = pt;
@@ -350,9 +352,10 @@ __device__ __noinline__ void gram_poll(GramRing* R, const CUtensorMap* ma, const
       if (!ptx::mbar_test(&R->conv[s], (uint32_t)(mt / TST) & 1u)) break;
       if (mt % GCH == 0 && c >= 2 && !ptx::mbar_test(&R->tfree[b], (uint32_t)((c / 2) - 1) & 1u)) break;
       tc_after();
-      const uint32_t b0 = R->sm + (uint32_t)(s * TSTAGE);
+      const uint32_t h0 = R->sm + (uint32_t)(s * TSTAGE);
+      const uint32_t l0 = R->sm + (uint32_t)((TST + mt % TLO) * TSTAGE);
       const uint32_t d = R->tmem + (uint32_t)(b * 2 * GN);
-      mma_ktile(d, d + GN, b0, b0 + TILE_A, b0 + 2 * TILE_A, b0 + 3 * TILE_A, IDESC, mt % GCH == 0);
+      mma_ktile(d, d + GN, h0, l0, h0 + TILE_A, l0 + TILE_A, IDESC, mt % GCH == 0);
       mma_commit(&R->mmad[s]);
       if (mt % GCH == GCH - 1 || mt == R->nkt - 1) mma_commit(&R->accd[b]);
       ++mt;
@@ -456,16 +459,19 @@ k_gram_tma(const __grid_constant__ CUtensorMap ma, const __grid_constant__ CUten
   for (int t = 0; t < nkt && ok; ++t) {
     const int s = t % TST;
     if (!wait(&R.full[s], (uint32_t)(t / TST) & 1u)) { ok = false; break; }
-    // split the 2048 16-byte chunks of the stage's A and B images: hi in place, lo beside
-    uint8_t* st = sm + s * TSTAGE;
+    // the low slot is free once the MMAs of k-tile t - TLO are done
+    if (t >= TLO && !wait(&R.mmad[(t - TLO) % TST], (uint32_t)((t - TLO) / TST) & 1u)) { ok = false; break; }
+    // split the 2048 16-byte chunks of the k-tile's A and B images: hi in place, lo to its slot
+    uint8_t* hs = sm + s * TSTAGE;
+    uint8_t* ls = sm + (TST + t % TLO) * TSTAGE;
 #pragma unroll 1
     for (int q = 0; q < 4; ++q) {
       const int f = (int)threadIdx.x + TTHREADS * q;              // 0 .. 2047
-      uint8_t* img = st + (f < 1024 ? 0 : 2 * TILE_A) + 16 * (f & 1023);
-      float4 x = *(const float4*)img, h, l;
+      const int off = (f < 1024 ? 0 : TILE_A) + 16 * (f & 1023);
+      float4 x = *(const float4*)(hs + off), h, l;
       split4(x, h, l);
-      *(float4*)img = h;
-      *(float4*)(img + TILE_A) = l;
+      *(float4*)(hs + off) = h;
+      *(float4*)(ls + off) = l;
     }
     proxy_fence();
     __syncwarp();
