@@ -27,9 +27,9 @@ sys.path.insert(0, ROOT)
 METRIC = "CheFSI filter throughput (G point-orbital-degrees/s)"
 UNIT = "Gpt-orb-deg/s"
 WORKLOAD = "64^3 grid h=0.4, 128 perturbed-FCC s+p atoms, Ns=512, m=24, Gamma point"
-# DRAM bytes of k_pass_f2 per block of 8 orbitals per degree on this cell, from one ncu
-# capture of a 32-block launch (579.43 MB read + 242.48 MB written)
-PASS_DRAM_BYTES_PER_BLOCK = (579.433984e6 + 242.480128e6) / 32
+# DRAM bytes of the filter pass k_pass_tma per block of 8 orbitals per degree on this
+# cell, from one ncu capture of a 32-block launch (701.20 MB read + 287.26 MB written)
+PASS_DRAM_BYTES_PER_BLOCK = (701.196032e6 + 287.256320e6) / 32
 
 
 def _args():
@@ -591,7 +591,7 @@ def run_ours(args):
     units = nd * ns * m
     ms, value = job_rate(ms, units, world, dist if world > 1 else None, "cuda")
 
-    # ---- roofline of the dominant kernel: the tiled filter pass k_pass_f2
+    # ---- roofline of the dominant kernel: the TMA-fed filter pass k_pass_tma
     # algorithmic bytes per step: degrees 2..m read Y_j and Y_{j-1} and write Y_{j+1}
     # (3 x 4 B per point-orbital), degree 1 reads Y_0 and writes Y_1 (2 x 4 B)
     s = 4
@@ -599,8 +599,8 @@ def run_ours(args):
     fp_launches = fp_n / args.steps
     achieved = bytes_step / (fp_ms / args.steps * 1e-3) / 1e9
     peak, peak_kind = _peaks()
-    # DRAM traffic: one ncu capture of a 32-block launch of this cell (579.43 MB read +
-    # 242.48 MB written), scaled by blocks
+    # DRAM traffic: one ncu capture of a 32-block launch of this cell (701.20 MB read +
+    # 287.26 MB written), scaled by blocks
     traffic = PASS_DRAM_BYTES_PER_BLOCK * (ns // 8) * m / fp_launches if fp_launches else None
 
     # ---- end to end through the C ABI with host buffers: every step copies its input from
@@ -686,7 +686,7 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (537 MB block)", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "k_pass_f2", "launches_per_step": fp_launches,
+                     "kernel": "k_pass_tma", "launches_per_step": fp_launches,
                      "avg_launch_ms": fp_ms / max(fp_n, 1),
                      "algorithmic_bytes_per_launch": bytes_step / max(fp_launches, 1)},
         "breakdown_ms_per_step": {"filter_pass": fp_ms / args.steps, "other_hpass": hp_ms / args.steps,
