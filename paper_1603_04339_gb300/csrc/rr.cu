@@ -633,29 +633,35 @@ __global__ void k_offnorm_sum(const double* part, int nb, double* out) {
   out[1] = b;
 }
 
-// Ascending order of the diagonal: eig[rank] = A_ii, Q[:, rank] = V[:, i]
-// (ties broken by index, so the order is deterministic).
-// vals != nullptr: sort by vals[i] instead of the diagonal of A.
+// Ascending order of the diagonal: eig[rank] = A_ii, perm[rank] = i (ties broken by
+// index, so the order is deterministic); vals != nullptr: sort by vals[i] instead of
+// the diagonal of A.  One CTA; the keys go through shared memory (n <= 1024).
 template <class TW>
-__global__ void __launch_bounds__(1024) k_sort(const TW* __restrict__ A, const double* __restrict__ vals,
-                                               const TW* __restrict__ V, int n, double* __restrict__ eig,
-                                               TW* __restrict__ Q) {
-  __shared__ int perm[1024];
+__global__ void __launch_bounds__(1024) k_sort(const TW* __restrict__ A, const double* __restrict__ vals, int n,
+                                               double* __restrict__ eig, int* __restrict__ perm) {
+  __shared__ double key[1024];
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    key[i] = vals ? vals[i] : (double)Tr<TW>::re(A[i + (long long)i * n]);
+  __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double li = vals ? vals[i] : (double)Tr<TW>::re(A[i + (long long)i * n]);
+    const double li = key[i];
     int rank = 0;
     for (int j = 0; j < n; ++j) {
-      const double lj = vals ? vals[j] : (double)Tr<TW>::re(A[j + (long long)j * n]);
+      const double lj = key[j];
       if (lj < li || (lj == li && j < i)) ++rank;
     }
     perm[rank] = i;
     eig[rank] = li;
   }
-  __syncthreads();
-  for (long long t = threadIdx.x; t < (long long)n * n; t += blockDim.x) {
-    const int row = (int)(t % n), col = (int)(t / n);
-    Q[t] = V[row + (long long)perm[col] * n];
-  }
+}
+
+// Q[:, rank] = V[:, perm[rank]] (n x n), over the whole GPU
+template <class TW>
+__global__ void k_permute_cols(const TW* __restrict__ V, const int* __restrict__ perm, int n, TW* __restrict__ Q) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n * n) return;
+  const int row = (int)(t % n), col = (int)(t / n);
+  Q[t] = V[row + (long long)perm[col] * n];
 }
 
 template <class TW, class T>
@@ -1210,8 +1216,9 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
     TW* Ares = nullptr;
     s = jacobi<TW>(ctx, A0, A1, Vj, ns, 1e-26, 40, scal, &Ares, &sweeps, st);
     if (s != SPARC_OK) return s;
-    k_sort<TW><<<1, 1024, 0, st>>>(Ares, nullptr, Vj, ns, eig, Qs);
-    ++ctx->launches;
+    k_sort<TW><<<1, 1024, 0, st>>>(Ares, nullptr, ns, eig, (int*)scal);
+    k_permute_cols<TW><<<ceil_div(nn, 256), 256, 0, st>>>(Vj, (const int*)scal, ns, Qs);
+    ctx->launches += 2;
   } else {
     // 5b. FP32 Jacobi on C for the eigenvectors, FP64 Rayleigh quotients for the eigenvalues
     k_convert<TW, TS><<<ceil_div(nn, 256), 256, 0, st>>>(A0, S0, nn);
@@ -1244,8 +1251,9 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
     SPARC_CUDA(ctx, (gemm64<TW, false, false>(ctx, ns, ns, ns, A0, ns, Vj, ns, T1, ns, 1.0, 0.0, partH, pcap, st)));
     k_rayleigh<TW><<<ceil_div(ns, 128), 128, 0, st>>>(Vj, T1, ns, lam);
     ++ctx->launches;
-    k_sort<TW><<<1, 1024, 0, st>>>(nullptr, lam, Vj, ns, eig, Qs);
-    ++ctx->launches;
+    k_sort<TW><<<1, 1024, 0, st>>>(nullptr, lam, ns, eig, (int*)scal);
+    k_permute_cols<TW><<<ceil_div(nn, 256), 256, 0, st>>>(Vj, (const int*)scal, ns, Qs);
+    ctx->launches += 2;
   }
   ctx->last_sweeps = sweeps;
   // 6. Ritz vectors of the pencil: Yr = Linv^H Q (series: Q + K^T Q)

@@ -282,19 +282,20 @@ k_gram_tc(const float* __restrict__ A, long long lda, const float* __restrict__ 
 //   * loads: each k-tile of A and B (32 grid points x 128 columns, K-major: the
 //     columns are contiguous in the grid index) arrives by cp.async.bulk.tensor in the
 //     128-byte swizzle the MMA reads, into a ring of NH slots (four k-tiles in flight);
-//   * all warps split each landed tile in place into its TF32 high part and the
+//   * warps 0..14 split each landed tile in place into its TF32 high part and the
 //     remainder, whose images go to a ring of NL slots (a slot is free once the MMAs of
-//     the k-tile NL before are done), then, every GCH k-tiles, drain the finished FP32 TMEM
+//     the k-tile NL before are done); all 16 warps, every GCH k-tiles, drain the finished FP32 TMEM
 //     chunk into float-float accumulators in registers (TwoSum: the GPU's FP64 rate
 //     would make FP64 adds the bottleneck);
 //   * the 12 MMAs of a k-tile (3xTF32) go into one of two TMEM accumulator pairs,
 //     alternating per chunk, so that a chunk drains while the next accumulates.
-// Lane 0 of warp 0 issues the loads and lane 0 of warp 1 the MMAs.  Neither role may
-// block behind the others, so both run as non-blocking steps polled from every wait
-// loop of their warps.  Every wait is bounded; one that runs out latches
-// STATUS_TIMEOUT and raises the CTA's abort flag, and the CTA winds down (in-flight
-// copies and MMAs waited for, with bounds) before it frees its TMEM.
+// Lane 0 of warp 15 issues the loads and the MMAs, as non-blocking steps in a loop that
+// also drains that warp's share of each completed chunk; it splits no tiles, so an MMA
+// goes out as soon as the last splitting warp arrives.  Every wait is bounded; one that
+// runs out latches STATUS_TIMEOUT and raises the CTA's abort flag, and the CTA winds
+// down (in-flight copies and MMAs waited for, with bounds) before it frees its TMEM.
 constexpr int TTHREADS = 512;
+constexpr int NCTL = 15;                       // the control warp; warps 0 .. NCTL-1 split tiles
 constexpr int TST = 5;                         // NH: slots of landed (then high-part) images
 constexpr int TLO = 2;                         // NL: slots of low-part images
 constexpr int TSTAGE = 2 * TILE_A;             // A, B (32 KB)
@@ -388,7 +389,7 @@ k_gram_tma(const __grid_constant__ CUtensorMap ma, const __grid_constant__ CUten
   if (threadIdx.x == 0) {
     for (int s = 0; s < TST; ++s) {
       mbar_init(&R.full[s], 1);
-      mbar_init(&R.conv[s], 16);
+      mbar_init(&R.conv[s], NCTL);
       mbar_init(&R.mmad[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -414,15 +415,13 @@ k_gram_tma(const __grid_constant__ CUtensorMap ma, const __grid_constant__ CUten
   const uint32_t tmem = tmem_base;
   const int nchunk = (nkt + GCH - 1) / GCH;
   volatile int* abort_flag = &R.abort_flag;
-  const bool producer = threadIdx.x == 0, issuer = threadIdx.x == 32;
-  auto poll = [&]() {
-    if (producer || issuer) gram_poll(&R, &ma, &mb, producer);
-  };
-  // bounded wait for a phase, stepping this thread's roles meanwhile
+  // warp 15 is the control warp: its lane 0 issues the loads and the MMAs, and the warp
+  // drains its share of TMEM; warps 0..14 split the landed tiles and drain theirs
+  const bool control = warp == NCTL;
+  // bounded wait for a phase
   auto wait = [&](uint64_t* b, uint32_t parity) {
     const long long t0 = clock64();
     while (!ptx::mbar_test(b, parity)) {
-      poll();
       if (*abort_flag) return false;
       if (clock64() - t0 > (1LL << 32)) {
         *abort_flag = 1;
@@ -437,9 +436,8 @@ k_gram_tma(const __grid_constant__ CUtensorMap ma, const __grid_constant__ CUten
   const int row = 32 * (warp & 3) + lane;          // TMEM lane = output row i
   const int col0 = (warp >> 2) * 32;                // 32 output columns j
   int drained = 0;
-  auto drain = [&](int c) {
+  auto drain_now = [&](int c) {
     const int b = c & 1;
-    if (!wait(&R.accd[b], (uint32_t)(c / 2) & 1u)) return false;
     tc_after();
     const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(b * 2 * GN + col0);
 #pragma unroll
@@ -452,52 +450,86 @@ k_gram_tma(const __grid_constant__ CUtensorMap ma, const __grid_constant__ CUten
     tc_before();
     __syncwarp();
     if (lane == 0) arrive(&R.tfree[b]);
-    return true;
   };
-  poll();
   bool ok = true;
-  for (int t = 0; t < nkt && ok; ++t) {
-    const int s = t % TST;
-    if (!wait(&R.full[s], (uint32_t)(t / TST) & 1u)) { ok = false; break; }
-    // the low slot is free once the MMAs of k-tile t - TLO are done
-    if (t >= TLO && !wait(&R.mmad[(t - TLO) % TST], (uint32_t)((t - TLO) / TST) & 1u)) { ok = false; break; }
-    // split the 2048 16-byte chunks of the k-tile's A and B images: hi in place, lo to its slot
-    uint8_t* hs = sm + s * TSTAGE;
-    uint8_t* ls = sm + (TST + t % TLO) * TSTAGE;
-#pragma unroll 1
-    for (int q = 0; q < 4; ++q) {
-      const int f = (int)threadIdx.x + TTHREADS * q;              // 0 .. 2047
-      const int off = (f < 1024 ? 0 : TILE_A) + 16 * (f & 1023);
-      float4 x = *(const float4*)(hs + off), h, l;
-      split4(x, h, l);
-      *(float4*)(hs + off) = h;
-      *(float4*)(ls + off) = l;
+  if (control) {
+    // steps of the two roles until every MMA is issued, draining each chunk as it
+    // completes; bounded by the time without progress
+    long long t0 = clock64();
+    while (ok) {
+      int progress = 0;
+      if (lane == 0) {
+        const int pt = R.pt, mt = R.mt;
+        gram_poll(&R, &ma, &mb, true);
+        gram_poll(&R, &ma, &mb, false);
+        progress = (R.pt != pt) || (R.mt != mt);
+      }
+      progress = __shfl_sync(0xffffffffu, progress, 0);
+      if (drained < nchunk) {
+        const int b = drained & 1;
+        const int ready = __shfl_sync(0xffffffffu, lane == 0 ? (int)ptx::mbar_test(&R.accd[b], (uint32_t)(drained / 2) & 1u) : 0, 0);
+        if (ready) {
+          drain_now(drained++);
+          progress = 1;
+        }
+      }
+      const int done = __shfl_sync(0xffffffffu, lane == 0 ? (int)(R.mt == nkt) : 0, 0);
+      if (done && drained == nchunk) break;
+      if (progress) t0 = clock64();
+      if (*abort_flag) ok = false;
+      else if (clock64() - t0 > (1LL << 32)) {
+        *abort_flag = 1;
+        ok = false;
+      }
     }
-    proxy_fence();
-    __syncwarp();
-    if (lane == 0) arrive(&R.conv[s]);
-    poll();
-    if (t % GCH == GCH / 2 && drained < t / GCH) ok = drain(drained++);
+  } else {
+    for (int t = 0; t < nkt && ok; ++t) {
+      const int s = t % TST;
+      if (!wait(&R.full[s], (uint32_t)(t / TST) & 1u)) { ok = false; break; }
+      // the low slot is free once the MMAs of k-tile t - TLO are done
+      if (t >= TLO && !wait(&R.mmad[(t - TLO) % TST], (uint32_t)((t - TLO) / TST) & 1u)) { ok = false; break; }
+      // split the 2048 16-byte chunks of the k-tile's A and B images: hi in place, lo to its slot
+      uint8_t* hs = sm + s * TSTAGE;
+      uint8_t* ls = sm + (TST + t % TLO) * TSTAGE;
+#pragma unroll 1
+      for (int f = (int)threadIdx.x; f < 2048; f += NCTL * 32) {
+        const int off = (f < 1024 ? 0 : TILE_A) + 16 * (f & 1023);
+        float4 x = *(const float4*)(hs + off), h, l;
+        split4(x, h, l);
+        *(float4*)(hs + off) = h;
+        *(float4*)(ls + off) = l;
+      }
+      proxy_fence();
+      __syncwarp();
+      if (lane == 0) arrive(&R.conv[s]);
+      if (t % GCH == GCH / 2 && drained < t / GCH) {
+        ok = wait(&R.accd[drained & 1], (uint32_t)(drained / 2) & 1u);
+        if (ok) drain_now(drained++);
+      }
+    }
+    while (ok && drained < nchunk) {
+      ok = wait(&R.accd[drained & 1], (uint32_t)(drained / 2) & 1u);
+      if (ok) drain_now(drained++);
+    }
   }
-  while (ok && drained < nchunk) ok = drain(drained++);
   if (ok) {
 #pragma unroll
     for (int q = 0; q < 32; ++q) P[(size_t)(col0 + q) * BM + row] = (double)ahi[q] + (double)alo[q];
   }
   // wind down: the loads issued and the MMAs committed complete before TMEM is freed
-  if (producer) {
+  if (control && lane == 0) {
     const int pt = R.pt;
     for (int t = (pt > TST ? pt - TST : 0); t < pt; ++t) {
       const long long c0 = clock64();
       while (!ptx::mbar_test(&R.full[t % TST], (uint32_t)(t / TST) & 1u))
         if (clock64() - c0 > (1LL << 32)) break;
     }
-  }
-  if (issuer && R.mt > 0) {
-    const int mt = R.mt;
-    const long long c0 = clock64();
-    while (!ptx::mbar_test(&R.mmad[(mt - 1) % TST], (uint32_t)((mt - 1) / TST) & 1u))
-      if (clock64() - c0 > (1LL << 32)) break;
+    if (R.mt > 0) {
+      const int mt = R.mt;
+      const long long c0 = clock64();
+      while (!ptx::mbar_test(&R.mmad[(mt - 1) % TST], (uint32_t)((mt - 1) / TST) & 1u))
+        if (clock64() - c0 > (1LL << 32)) break;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0 && *abort_flag) atomicOr(status, STATUS_TIMEOUT);
