@@ -417,19 +417,18 @@ constexpr int BJ = 16;
 // local index l of pair k's 32 indices -> global index
 __device__ __forceinline__ int bj_index(int l, int bp, int bq) { return l < BJ ? BJ * bp + l : BJ * bq + (l - BJ); }
 
-// rotation of the pair (p, q) of pair subproblem S (local indices; global bp, bq blocks):
-// the rotation of jacobi_rot, t = sign(th)/(|th| + sqrt(th^2 + 1)) with th = d/(2b),
-// d = S_qq - S_pp, b = S_pq, written as t = sign(d) 2b / (|d| + sqrt(d^2 + 4b^2)) and
-// evaluated with the approximate reciprocal and reciprocal square root (a few ulp):
-// the rotations' small departure from orthogonality is removed afterwards by the
-// Newton-Schulz step, and the eigenvalues come from FP64 Rayleigh quotients.
-__device__ __forceinline__ void bj_rot(const float (&S)[2 * BJ][2 * BJ + 1], int p, int q, int bp, int bq, int n,
-                                       float& c, float& sn) {
+// rotation of the pair (p, q) of pair subproblem S (local indices): the rotation of
+// jacobi_rot, t = sign(th)/(|th| + sqrt(th^2 + 1)) with th = d/(2b), d = S_qq - S_pp,
+// b = S_pq, written as t = sign(d) 2b / (|d| + sqrt(d^2 + 4b^2)) and evaluated with the
+// approximate reciprocal and reciprocal square root (a few ulp): the rotations' small
+// departure from orthogonality is removed afterwards by the Newton-Schulz step, and the
+// eigenvalues come from FP64 Rayleigh quotients.  (n is a multiple of 2 BJ on this
+// path, so every index of a pair subproblem is in range.)
+__device__ __forceinline__ void bj_rot(const float (&S)[2 * BJ][2 * BJ + 1], int p, int q, float& c, float& sn) {
   c = 1.f;
   sn = 0.f;
-  const int gp = bj_index(p, bp, bq), gq = bj_index(q, bp, bq);
   const float b = S[p][q];
-  if (gp < n && gq < n && b != 0.f) {
+  if (b != 0.f) {
     const float d = S[q][q] - S[p][p];
     const float b2 = 2.f * b;
     const float r2 = fmaf(d, d, b2 * b2);
@@ -443,19 +442,26 @@ __device__ __forceinline__ void bj_rot(const float (&S)[2 * BJ][2 * BJ + 1], int
 // One cyclic sweep over the pair subproblem S (32 x 32, in shared memory), its rotations
 // accumulated into W (identity on entry) and stored as the pair's rotation Wbuf[k].
 __device__ __forceinline__ void bj_pair_sweep(float (&S)[2 * BJ][2 * BJ + 1], float (&W)[2 * BJ][2 * BJ + 1],
-                                              float* __restrict__ Wbuf, int n, int bp, int bq, int k) {
+                                              float* __restrict__ Wbuf, int k) {
+  // the inner round-robin schedule: (p, q) of pair x in round rr, packed p | q << 8
+  __shared__ unsigned short sched[2 * BJ - 1][BJ];
   const int t = threadIdx.x;
+  for (int e = t; e < (2 * BJ - 1) * BJ; e += blockDim.x) {
+    const int rr = e / BJ, x = e % BJ;
+    sched[rr][x] = (unsigned short)(rr_player(x, rr, 2 * BJ) | (rr_player(2 * BJ - 1 - x, rr, 2 * BJ) << 8));
+  }
+  __syncthreads();
   // thread (x, y): the 2 x 2 block (pair x rows, pair y columns) of S and rows 2y, 2y+1
   // of W's pair-x columns.  Every thread computes the two rotations it needs from the
   // same entries (identical arithmetic, identical results), so a round is one read
   // phase and one write phase.
   const int x = t % BJ, y = t / BJ;
   for (int rr = 0; rr < 2 * BJ - 1; ++rr) {
-    const int i0 = rr_player(x, rr, 2 * BJ), i1 = rr_player(2 * BJ - 1 - x, rr, 2 * BJ);
-    const int j0 = rr_player(y, rr, 2 * BJ), j1 = rr_player(2 * BJ - 1 - y, rr, 2 * BJ);
+    const unsigned sx_ = sched[rr][x], sy_ = sched[rr][y];
+    const int i0 = sx_ & 0xFF, i1 = sx_ >> 8, j0 = sy_ & 0xFF, j1 = sy_ >> 8;
     float cx, sx, cy, sy;
-    bj_rot(S, i0, i1, bp, bq, n, cx, sx);
-    bj_rot(S, j0, j1, bp, bq, n, cy, sy);
+    bj_rot(S, i0, i1, cx, sx);
+    bj_rot(S, j0, j1, cy, sy);
     const float a00 = S[i0][j0], a01 = S[i0][j1], a10 = S[i1][j0], a11 = S[i1][j1];
     const float w00 = W[2 * y][i0], w01 = W[2 * y][i1], w10 = W[2 * y + 1][i0], w11 = W[2 * y + 1][i1];
     // rows: [r0; r1] = [[c, -s], [s, c]] [a0; a1] (the rotation [[c, s], [-s, c]] transposed)
@@ -493,7 +499,7 @@ __device__ __forceinline__ void bj_pair_body(const float* __restrict__ A, float*
     W[i][j] = (i == j) ? 1.f : 0.f;
   }
   __syncthreads();
-  bj_pair_sweep(S, W, Wbuf, n, bp, bq, k);
+  bj_pair_sweep(S, W, Wbuf, k);
 }
 
 __global__ void __launch_bounds__(256) k_bj_pair(const float* __restrict__ A, float* __restrict__ Wbuf, int n,
@@ -508,12 +514,15 @@ __global__ void __launch_bounds__(256) k_bj_pair(const float* __restrict__ A, fl
 // blocks of V[:, I_k] W_k.
 __device__ __forceinline__ void bj_apply_body(const float* __restrict__ A, float* __restrict__ An, float* V,
                                               const float* __restrict__ Wbuf, int n, int nbk, int r, int bid) {
+  // X rows of 33 floats (its column reads vary the row across a warp); the operands read
+  // as one broadcast float4 per k (all lanes of a warp share j0) in rows of 36
   __shared__ float X[2 * BJ][2 * BJ + 1];
-  __shared__ float Wl[2 * BJ][2 * BJ + 1];
-  __shared__ float Wr[2 * BJ][2 * BJ + 1];
-  __shared__ float Tm[2 * BJ][2 * BJ + 1];
+  __shared__ __align__(16) float Wl[2 * BJ][2 * BJ + 4];
+  __shared__ __align__(16) float Wr[2 * BJ][2 * BJ + 4];
+  __shared__ __align__(16) float Tm[2 * BJ][2 * BJ + 4];
   const int np = nbk / 2;
   const int t = threadIdx.x;
+  const int i = t % (2 * BJ), j0 = (t / (2 * BJ)) * 4;
   if (bid < np * np) {
     const int ka = bid % np, kb = bid / np;
     const int ap = rr_player(ka, r, nbk), aq = rr_player(nbk - 1 - ka, r, nbk);
@@ -521,33 +530,42 @@ __device__ __forceinline__ void bj_apply_body(const float* __restrict__ A, float
     const float* Wa = Wbuf + (size_t)ka * 4 * BJ * BJ;
     const float* Wb = Wbuf + (size_t)kb * 4 * BJ * BJ;
     for (int e = t; e < 4 * BJ * BJ; e += 256) {
-      const int i = e % (2 * BJ), j = e / (2 * BJ);
-      const int gi = bj_index(i, ap, aq), gj = bj_index(j, bp, bq);
-      X[i][j] = (gi < n && gj < n) ? A[gi + (long long)gj * n] : 0.f;
-      Wl[i][j] = Wa[e];
-      Wr[i][j] = Wb[e];
+      const int ii = e % (2 * BJ), jj = e / (2 * BJ);
+      const int gi = bj_index(ii, ap, aq), gj = bj_index(jj, bp, bq);
+      X[ii][jj] = (gi < n && gj < n) ? A[gi + (long long)gj * n] : 0.f;
+      Wl[ii][jj] = Wa[e];
+      Wr[ii][jj] = Wb[e];
     }
     __syncthreads();
     // each thread: 4 entries (row i, columns j0 .. j0+3) of T = X W_b, then of W_a^T T;
     // a warp covers the 32 rows of a column, so its stores into column-major A' coalesce
-    const int i = t % (2 * BJ), j0 = (t / (2 * BJ)) * 4;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      float acc = 0.f;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 8
-      for (int l = 0; l < 2 * BJ; ++l) acc = fmaf(X[i][l], Wr[l][j0 + u], acc);
-      Tm[i][j0 + u] = acc;
+    for (int l = 0; l < 2 * BJ; ++l) {
+      const float x = X[i][l];
+      const float4 w = *reinterpret_cast<const float4*>(&Wr[l][j0]);
+      acc[0] = fmaf(x, w.x, acc[0]);
+      acc[1] = fmaf(x, w.y, acc[1]);
+      acc[2] = fmaf(x, w.z, acc[2]);
+      acc[3] = fmaf(x, w.w, acc[3]);
     }
+    *reinterpret_cast<float4*>(&Tm[i][j0]) = make_float4(acc[0], acc[1], acc[2], acc[3]);
     __syncthreads();
+    float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+    for (int l = 0; l < 2 * BJ; ++l) {
+      const float wl = Wl[l][i];
+      const float4 tv = *reinterpret_cast<const float4*>(&Tm[l][j0]);
+      o[0] = fmaf(wl, tv.x, o[0]);
+      o[1] = fmaf(wl, tv.y, o[1]);
+      o[2] = fmaf(wl, tv.z, o[2]);
+      o[3] = fmaf(wl, tv.w, o[3]);
+    }
     const int gi = bj_index(i, ap, aq);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int j = j0 + u;
-      float acc = 0.f;
-#pragma unroll 8
-      for (int l = 0; l < 2 * BJ; ++l) acc = fmaf(Wl[l][i], Tm[l][j], acc);
-      const int gj = bj_index(j, bp, bq);
-      if (gi < n && gj < n) An[gi + (long long)gj * n] = acc;
+      const int gj = bj_index(j0 + u, bp, bq);
+      if (gi < n && gj < n) An[gi + (long long)gj * n] = o[u];
     }
   } else {
     const int vb = bid - np * np;
@@ -556,22 +574,27 @@ __device__ __forceinline__ void bj_apply_body(const float* __restrict__ A, float
     const int bp = rr_player(k, r, nbk), bq = rr_player(nbk - 1 - k, r, nbk);
     const float* Wk = Wbuf + (size_t)k * 4 * BJ * BJ;
     for (int e = t; e < 4 * BJ * BJ; e += 256) {
-      const int i = e % (2 * BJ), j = e / (2 * BJ);
-      const int gr = rb * 2 * BJ + i, gj = bj_index(j, bp, bq);
-      X[i][j] = (gr < n && gj < n) ? V[gr + (long long)gj * n] : 0.f;
-      Wl[i][j] = Wk[e];
+      const int ii = e % (2 * BJ), jj = e / (2 * BJ);
+      const int gr = rb * 2 * BJ + ii, gj = bj_index(jj, bp, bq);
+      X[ii][jj] = (gr < n && gj < n) ? V[gr + (long long)gj * n] : 0.f;
+      Wl[ii][jj] = Wk[e];
     }
     __syncthreads();
-    const int i = t % (2 * BJ), j0 = (t / (2 * BJ)) * 4;
     const int gr = rb * 2 * BJ + i;
+    float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+    for (int l = 0; l < 2 * BJ; ++l) {
+      const float x = X[i][l];
+      const float4 w = *reinterpret_cast<const float4*>(&Wl[l][j0]);
+      o[0] = fmaf(x, w.x, o[0]);
+      o[1] = fmaf(x, w.y, o[1]);
+      o[2] = fmaf(x, w.z, o[2]);
+      o[3] = fmaf(x, w.w, o[3]);
+    }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int j = j0 + u;
-      float acc = 0.f;
-#pragma unroll 8
-      for (int l = 0; l < 2 * BJ; ++l) acc = fmaf(X[i][l], Wl[l][j], acc);
-      const int gj = bj_index(j, bp, bq);
-      if (gr < n && gj < n) V[gr + (long long)gj * n] = acc;
+      const int gj = bj_index(j0 + u, bp, bq);
+      if (gr < n && gj < n) V[gr + (long long)gj * n] = o[u];
     }
   }
   __syncthreads();
