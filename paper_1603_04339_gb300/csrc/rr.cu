@@ -1121,7 +1121,7 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
     ++ctx->launches;
     timing_end(ctx, TK_EIG, t0, st);
     cudaEvent_t t1 = timing_begin(ctx, st);
-    SPARC_CUDA(ctx, tc::rotate(ctx, U, ld, (const double*)T1, nd, ns, W1, nd, tcs, st));   // U1
+    SPARC_CUDA(ctx, tc::rotate(ctx, U, ld, (const double*)T1, nd, ns, W1, nd, tcs, st, true));   // U1 (T1 upper triangular)
     SPARC_LAUNCH(ctx, "orthonormalise");
     timing_end(ctx, TK_ROT, t1, st);
     Ub = W1;

@@ -43,7 +43,7 @@ cudaError_t gram(sparc_ctx* ctx, const float* A, long long lda, const float* B, 
 // C = U Yr (nd x ns, FP32) for column-major FP32 U and FP64 ns x ns Yr; C must not overlap U.
 size_t rot_scratch_bytes(int ns);
 cudaError_t rotate(sparc_ctx* ctx, const float* U, long long ldu, const double* Yr, long long nd, int ns, float* C,
-                   long long ldc, void* scratch, cudaStream_t st);
+                   long long ldc, void* scratch, cudaStream_t st, bool upper = false);
 }  // namespace tc
 
 }  // namespace sparc

@@ -577,8 +577,8 @@ __global__ void k_rot_pack(const double* __restrict__ Yr, int ns, int nkt, int n
 // C[g + n ldc] = sum_k U[g + k ldu] Yr[k + n ns] for g in [128 blockIdx.y, +128),
 // n in [256 blockIdx.x, +256).
 __global__ void __launch_bounds__(THREADS, 1)
-k_rot_tc(const float* __restrict__ U, long long ldu, const float* __restrict__ bp, long long nd, int ns, int nkt,
-         float* __restrict__ C, long long ldc, int* status) {
+k_rot_tc(const float* __restrict__ U, long long ldu, const float* __restrict__ bp, long long nd, int ns, int nkt_all,
+         float* __restrict__ C, long long ldc, int* status, int upper) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t bar[RST];
   __shared__ uint32_t tmem_base;
@@ -586,6 +586,8 @@ k_rot_tc(const float* __restrict__ U, long long ldu, const float* __restrict__ b
   uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
   const int nh = blockIdx.x;
   const long long m0 = (long long)blockIdx.y * BM;
+  // Yr upper triangular: columns of half nh take rows k < (nh + 1) RN only
+  const int nkt = upper ? min(nkt_all, ((nh + 1) * RN + BK - 1) / BK) : nkt_all;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < RST; ++s) mbar_init(&bar[s], 1);
@@ -609,7 +611,7 @@ k_rot_tc(const float* __restrict__ U, long long ldu, const float* __restrict__ b
     }
   };
   auto load_b = [&](int t, int s) {   // the hi and lo images of Yr, 64 KB
-    const float* src = bp + (size_t)(nh * nkt + t) * 2 * (RN * BK);
+    const float* src = bp + (size_t)(nh * nkt_all + t) * 2 * (RN * BK);
     const uint32_t dst = saddr(sm + s * RSTAGE + 2 * TILE_A);
 #pragma unroll 4
     for (int q = 0; q < (2 * RN * BK * 4) / (16 * THREADS); ++q) {
@@ -765,7 +767,7 @@ size_t rot_scratch_bytes(int ns) {
 }
 
 cudaError_t rotate(sparc_ctx* ctx, const float* U, long long ldu, const double* Yr, long long nd, int ns, float* C,
-                   long long ldc, void* scratch, cudaStream_t st) {
+                   long long ldc, void* scratch, cudaStream_t st, bool upper) {
   const int nkt = ceil_div(ns, BK), nnh = ceil_div(ns, RN);
   if ((nd + BM - 1) / BM > 65535) return cudaErrorInvalidValue;   // grid y limit
   const long long npack = (long long)nnh * nkt * RN * BK;
@@ -773,7 +775,7 @@ cudaError_t rotate(sparc_ctx* ctx, const float* U, long long ldu, const double* 
   cudaError_t e = cudaFuncSetAttribute(k_rot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, RSMEM);
   if (e != cudaSuccess) return e;
   k_rot_tc<<<dim3(nnh, (unsigned)ceil_div(nd, BM)), THREADS, RSMEM, st>>>(U, ldu, (const float*)scratch, nd, ns, nkt,
-                                                                          C, ldc, ctx->d_status);
+                                                                          C, ldc, ctx->d_status, upper ? 1 : 0);
   ctx->launches += 2;
   return cudaGetLastError();
 }
