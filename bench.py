@@ -240,13 +240,13 @@ def kpoint_filter_throughput(sparc, synth, torch, ctx, reps=2, tune=True, nk=Non
         fn()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        n0 = ctx.launches()
+        n0, g0 = ctx.launches(), ctx.graph_launches()
         e0.record()
         for _ in range(reps):
             fn()
         e1.record()
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps, (ctx.launches() - n0) // reps
+        return e0.elapsed_time(e1) / reps, (ctx.launches() - n0) // reps, (ctx.graph_launches() - g0) / reps
 
     def batched():
         sparc.sparc_cheb_filter_batch(Hs, wl.m, a, b, a0, X, Y)
@@ -255,8 +255,8 @@ def kpoint_filter_throughput(sparc, synth, torch, ctx, reps=2, tune=True, nk=Non
         for k in range(nk):
             sparc.sparc_cheb_filter(Hs[k], wl.m, a[k], b[k], a0[k], X[k], Y[k])
 
-    ms_b, l_b = timed(batched)
-    ms_k, l_k = timed(per_k)
+    ms_b, l_b, gl_b = timed(batched)
+    ms_k, l_k, _ = timed(per_k)
     # kernel split of one batched filter (event pairs around each launch)
     ctx.timing(True)
     batched()
@@ -269,7 +269,8 @@ def kpoint_filter_throughput(sparc, synth, torch, ctx, reps=2, tune=True, nk=Non
     torch.cuda.empty_cache()
     return {"workload": f"40^3 Si-like cell, 64 s+p atoms, 3x3x3 MP k-points ({nk} of 27), Ns=192, m=20, complex64",
             "batched": {"value": work / (ms_b * 1e-3) / 1e9, "unit": "Gpt-orb-deg/s", "ms_per_filter": ms_b,
-                        "launches_per_filter": l_b, "units_per_launch": units or None,
+                        "launches_per_filter": l_b, "graph_launches_per_filter": gl_b,
+                        "units_per_launch": units or None,
                         "pass_ms": split["fpass"], "projection_ms": split["gather"]},
             "per_k": {"value": work / (ms_k * 1e-3) / 1e9, "unit": "Gpt-orb-deg/s", "ms_per_filter": ms_k,
                       "launches_per_filter": l_k},

@@ -178,7 +178,12 @@ sparc_status sparc_cheb_filter(sparc_ham* H, sparc_dtype dtype, int m, double a,
  *         modified; X and Y may not overlap.
  * Result: block k equals sparc_cheb_filter(H[k], dtype, m, a[k], b[k], a0[k],
  * ...) bit for bit.  Other dtypes, and Hamiltonians outside the tiled kernel's
- * range (fd_radius != 6), run one sparc_cheb_filter per k. */
+ * range (fd_radius != 6), run one sparc_cheb_filter per k.
+ * With SPARC_C64 the call's launches are captured once into a CUDA graph held by
+ * the context and replayed, one graph launch per call; a call with the same
+ * Hamiltonians, sizes and buffers but new bounds updates that graph in place.  (With
+ * kernel timing on, the launches are issued one by one.)  Do not call it from inside
+ * a stream capture. */
 sparc_status sparc_cheb_filter_batch(sparc_ham* const* H, int nk, sparc_dtype dtype, int m,
                                      const double* a, const double* b, const double* a0,
                                      const void* X, void* Y, int ns, int64_t ld, void* stream);
@@ -423,8 +428,12 @@ sparc_status sparc_scf_forces(sparc_scf* S, sparc_dtype dtype, const void* U, in
  *   which = 6: the tiled FP32 / complex64 filter pass (k_pass_f2, k_pass_c2) */
 sparc_status sparc_timing_enable(sparc_ctx* ctx, int on);
 sparc_status sparc_timing_read(sparc_ctx* ctx, int which, double* ms_total, int64_t* launches);
-/* Number of kernels this context has launched since it was created. */
+/* Number of kernels this context has launched since it was created (kernels run from
+ * a CUDA graph included, counted when the graph runs). */
 sparc_status sparc_launch_count(const sparc_ctx* ctx, int64_t* launches);
+/* Number of CUDA graph launches of this context since it was created: the captured
+ * Jacobi sweeps, filter graphs and k-point batch filters (each one host launch). */
+sparc_status sparc_graph_launch_count(const sparc_ctx* ctx, int64_t* launches);
 /* Jacobi sweeps used by the last Rayleigh-Ritz call on this context. */
 sparc_status sparc_last_sweeps(const sparc_ctx* ctx, int* sweeps);
 /* max |M~1 - I| of the last mixed-mode FP32 Rayleigh-Ritz call on this context: how far

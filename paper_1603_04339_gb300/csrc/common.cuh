@@ -179,6 +179,19 @@ struct sparc_ctx {
   std::map<std::tuple<int, int, void*, void*, void*>, cudaGraphExec_t> graphs;
   int last_sweeps = 0;
   double last_ortho_err = -1.0;   // max |U1^T U1 - I| of the last mixed Rayleigh-Ritz (-1: none)
+  // the last k-point batch filter, captured as one graph: its arguments and executable
+  struct KBatchGraph {
+    std::vector<const void*> H;
+    int m = 0, ns = 0, nkg = 0, nbk = 0;
+    long long ld = 0;
+    const void* X = nullptr;
+    void* Y = nullptr;
+    void* ws = nullptr;
+    std::vector<double> a, b, a0;
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;
+  } kbg;
+  long long graph_launches = 0;    // graph launches of this context (instrumentation)
   // filter launch configuration chosen by sparc_autotune_filter, keyed by (dtype, Nd,
   // ns, number of k-points): units (blocks of NB orbitals) per launch + TUNE_SHAPE x the
   // FP32 pass tile shape

@@ -201,6 +201,7 @@ sparc_status sparc_filter_graph_launch(sparc_filter_graph* G, void* stream) {
   SPARC_CUDA(G->ctx, cudaSetDevice(G->ctx->device));
   SPARC_CUDA(G->ctx, cudaGraphLaunch(G->exec, (cudaStream_t)stream));
   G->ctx->launches += G->kernels;
+  ++G->ctx->graph_launches;
   return SPARC_OK;
 }
 

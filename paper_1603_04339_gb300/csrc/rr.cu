@@ -999,6 +999,7 @@ sparc_status jacobi(sparc_ctx* ctx, TJ* A0, TJ* A1, TJ* V, int n, double tol, in
   while (sweeps < max_sweeps && !converged) {
     SPARC_CUDA(ctx, cudaGraphLaunch(ge, st));
     ctx->launches += blockj ? 2 * rounds : rounds;
+    ++ctx->graph_launches;
     sweeps += 2;
     const int nbo = ceil_div(n, 8);
     k_offnorm<TJ><<<nbo, 256, 0, st>>>(A0, n, scal + 2);

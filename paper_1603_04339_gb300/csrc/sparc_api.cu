@@ -415,25 +415,15 @@ static KGroup kbatch_grouping(int nk, int nblk, int items_per_blk, int nsm, int 
   return g;
 }
 
-// The complex64 filter of nk Hamiltonians that share the grid and projector
-// geometry: the same recurrence as filter_block_fast per k, with every gather
-// and pass launch covering the blocks of up to KMAX k-points.
-static sparc_status filter_kbatch(sparc_ham* const* Hs, int nk, int m, const double* a, const double* b,
-                                  const double* a0, const cf32* X, cf32* Y, int ns, long long ld,
-                                  cudaStream_t st) {
+// The launches of the k-point batch filter below, issued on st.
+static sparc_status kbatch_launches(sparc_ham* const* Hs, int nk, int m, const double* a, const double* b,
+                                    const double* a0, const cf32* X, cf32* Y, int ns, long long ld, const KGroup& G,
+                                    size_t bb, size_t gb, cudaStream_t st) {
   sparc_ham* H0 = Hs[0];
   sparc_ctx* ctx = H0->ctx;
   const int nblk = ceil_div(ns, NB);
   const long long nd = H0->gd.nd;
   const long long U = (long long)nk * nblk;
-  int upl = 0;
-  const auto tu = ctx->tuned.find(std::make_tuple((int)SPARC_C64, nd, ns, nk));
-  if (tu != ctx->tuned.end()) upl = tu->second & (TUNE_SHAPE - 1);
-  const KGroup G = kbatch_grouping(nk, nblk, fast::items_per_block<cf32>(H0), ctx->nsm, upl);
-  const size_t bb = align256((size_t)U * nd * NB * sizeof(cf32));
-  const size_t gb = align256((size_t)std::max(1, H0->nproj) * U * NB * sizeof(cf32));
-  const size_t sb = align256(fast::gather_scratch_bytes(H0, G.nkg * G.nbk, sizeof(cf32)));
-  if (!ensure_ws(ctx, 2 * bb + gb + sb)) return fail(ctx, SPARC_ERR_OOM, "workspace allocation failed");
   char* p = (char*)ctx->ws;
   cf32* B0 = (cf32*)p;
   cf32* B1 = (cf32*)(p + bb);
@@ -498,6 +488,88 @@ static sparc_status filter_kbatch(sparc_ham* const* Hs, int nk, int m, const dou
   return SPARC_OK;
 }
 
+// The complex64 filter of nk Hamiltonians that share the grid and projector
+// geometry: the same recurrence as filter_block_fast per k, with every gather
+// and pass launch covering the blocks of up to KMAX k-points.  Its launches are
+// captured into one CUDA graph and replayed, so that a call is one host launch; a
+// call with the same arguments but new bounds updates the graph's parameters.  With
+// per-kernel timing on (or the synchronous debug check) the launches are issued
+// directly.
+static sparc_status filter_kbatch(sparc_ham* const* Hs, int nk, int m, const double* a, const double* b,
+                                  const double* a0, const cf32* X, cf32* Y, int ns, long long ld,
+                                  cudaStream_t st) {
+  sparc_ham* H0 = Hs[0];
+  sparc_ctx* ctx = H0->ctx;
+  const int nblk = ceil_div(ns, NB);
+  const long long nd = H0->gd.nd;
+  const long long U = (long long)nk * nblk;
+  int upl = 0;
+  const auto tu = ctx->tuned.find(std::make_tuple((int)SPARC_C64, nd, ns, nk));
+  if (tu != ctx->tuned.end()) upl = tu->second & (TUNE_SHAPE - 1);
+  const KGroup G = kbatch_grouping(nk, nblk, fast::items_per_block<cf32>(H0), ctx->nsm, upl);
+  const size_t bb = align256((size_t)U * nd * NB * sizeof(cf32));
+  const size_t gb = align256((size_t)std::max(1, H0->nproj) * U * NB * sizeof(cf32));
+  const size_t sb = align256(fast::gather_scratch_bytes(H0, G.nkg * G.nbk, sizeof(cf32)));
+  if (!ensure_ws(ctx, 2 * bb + gb + sb)) return fail(ctx, SPARC_ERR_OOM, "workspace allocation failed");
+  if (ctx->timing || sync_check())
+    return kbatch_launches(Hs, nk, m, a, b, a0, X, Y, ns, ld, G, bb, gb, st);
+  sparc_ctx::KBatchGraph& K = ctx->kbg;
+  const bool same = K.exec && (int)K.H.size() == nk && std::equal(K.H.begin(), K.H.end(), (const void* const*)Hs) &&
+                    K.m == m && K.ns == ns && K.ld == ld && K.X == X && K.Y == Y && K.ws == ctx->ws &&
+                    K.nkg == G.nkg && K.nbk == G.nbk;
+  const bool bounds = same && std::equal(K.a.begin(), K.a.end(), a) && std::equal(K.b.begin(), K.b.end(), b) &&
+                      std::equal(K.a0.begin(), K.a0.end(), a0);
+  if (!bounds) {
+    if (!ctx->cap_stream) SPARC_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    const long long l0 = ctx->launches;
+    SPARC_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    sparc_status s = kbatch_launches(Hs, nk, m, a, b, a0, X, Y, ns, ld, G, bb, gb, ctx->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+    const long long kernels = ctx->launches - l0;
+    ctx->launches = l0;
+    if (s != SPARC_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    SPARC_CUDA(ctx, e);
+    bool updated = false;
+    if (same) {
+      cudaGraphExecUpdateResultInfo info;
+      updated = cudaGraphExecUpdate(K.exec, g, &info) == cudaSuccess;
+      if (!updated) cudaGetLastError();
+    }
+    if (!updated) {
+      if (K.exec) cudaGraphExecDestroy(K.exec);
+      K.exec = nullptr;
+      const cudaError_t ei = cudaGraphInstantiate(&K.exec, g, 0);
+      if (ei != cudaSuccess) {
+        cudaGraphDestroy(g);
+        K.exec = nullptr;
+        return cuda_fail(ctx, ei, "k-point batch graph instantiation");
+      }
+    }
+    cudaGraphDestroy(g);
+    K.H.assign((const void* const*)Hs, (const void* const*)Hs + nk);
+    K.m = m;
+    K.ns = ns;
+    K.ld = ld;
+    K.X = X;
+    K.Y = Y;
+    K.ws = ctx->ws;
+    K.nkg = G.nkg;
+    K.nbk = G.nbk;
+    K.a.assign(a, a + nk);
+    K.b.assign(b, b + nk);
+    K.a0.assign(a0, a0 + nk);
+    K.kernels = kernels;
+  }
+  SPARC_CUDA(ctx, cudaGraphLaunch(K.exec, st));
+  ctx->launches += K.kernels;
+  ++ctx->graph_launches;
+  return SPARC_OK;
+}
+
 }  // namespace sparc
 
 using namespace sparc;
@@ -539,6 +611,12 @@ sparc_status sparc_timing_enable(sparc_ctx* ctx, int on) {
 sparc_status sparc_last_sweeps(const sparc_ctx* ctx, int* sweeps) {
   if (!ctx || !sweeps) return SPARC_ERR_INVALID_ARG;
   *sweeps = ctx->last_sweeps;
+  return SPARC_OK;
+}
+
+sparc_status sparc_graph_launch_count(const sparc_ctx* ctx, int64_t* launches) {
+  if (!ctx || !launches) return SPARC_ERR_INVALID_ARG;
+  *launches = ctx->graph_launches;
   return SPARC_OK;
 }
 
@@ -588,6 +666,7 @@ void sparc_destroy(sparc_ctx* ctx) {
   timing_reset(ctx);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+  if (ctx->kbg.exec) cudaGraphExecDestroy(ctx->kbg.exec);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->d_status) cudaFree(ctx->d_status);

@@ -25,7 +25,7 @@ STATUS = {0: "SPARC_OK", 1: "SPARC_ERR_INVALID_ARG", 2: "SPARC_ERR_OOM", 3: "SPA
 EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_sync", "sparc_ham_create",
            "sparc_ham_set_veff", "sparc_ham_destroy", "sparc_apply_H", "sparc_cheb_filter",
            "sparc_lanczos_bounds", "sparc_rayleigh_ritz", "sparc_timing_enable", "sparc_timing_read",
-           "sparc_launch_count", "sparc_apply_H_noalloc", "sparc_last_sweeps", "sparc_last_ortho_err", "sparc_gram_f32",
+           "sparc_launch_count", "sparc_graph_launch_count", "sparc_apply_H_noalloc", "sparc_last_sweeps", "sparc_last_ortho_err", "sparc_gram_f32",
            "sparc_rotate_f32", "sparc_scf_create", "sparc_scf_step", "sparc_scf_read", "sparc_scf_destroy",
            "sparc_scf_forces", "sparc_cheb_filter_batch", "sparc_autotune_filter",
            "sparc_set_filter_units", "sparc_filter_graph_create", "sparc_filter_graph_set_bounds",
@@ -103,6 +103,8 @@ def load(path: str = LIB_PATH):
     L.sparc_last_sweeps.restype = c_int
     L.sparc_last_ortho_err.argtypes = [c_void_p, POINTER(ctypes.c_double)]
     L.sparc_last_ortho_err.restype = c_int
+    L.sparc_graph_launch_count.argtypes = [c_void_p, POINTER(c_int64)]
+    L.sparc_graph_launch_count.restype = c_int
     L.sparc_debug_inject.argtypes = [c_void_p, c_int, c_int64]
     L.sparc_debug_inject.restype = c_int
     L.sparc_apply_H_noalloc.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_int, c_int64, c_void_p]
@@ -224,6 +226,12 @@ class Context:
         """Jacobi sweeps of the last Rayleigh-Ritz call (sparc_last_sweeps)."""
         n = c_int()
         self.check(load().sparc_last_sweeps(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def graph_launches(self) -> int:
+        """CUDA graph launches of this context (sparc_graph_launch_count)."""
+        n = c_int64()
+        self.check(load().sparc_graph_launch_count(self.handle, ctypes.byref(n)))
         return n.value
 
     def last_ortho_err(self) -> float:

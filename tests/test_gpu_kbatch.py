@@ -85,6 +85,28 @@ def test_batch_equals_per_k_filter_and_oracle_small(ctx):
         assert err < 1e-4, (k, err)
 
 
+def test_batch_runs_as_one_graph_launch_and_updates_bounds(ctx):
+    """A complex64 batch call is one graph launch; a repeat with new bounds updates
+    the captured graph in place and still equals the per-k filters bit for bit."""
+    from paper_1603_04339_gb300 import sparc
+    wl = _small_multi_k()
+    nk = len(wl.kpts)
+    Hs = [sparc.Hamiltonian.from_workload(ctx, wl, k) for k in range(nk)]
+    X = np.stack([synth.random_orbitals(wl.nd, wl.ns, 310 + k, complex_=True) for k in range(nk)])
+    Xd = torch.from_numpy(X.astype(np.complex64)).cuda()
+    Y = torch.empty_like(Xd)
+    for shift in (0.0, 1.5, 0.0):
+        a, b, a0 = _bounds(nk, wl.nd, wl.ns, a0=-3.0 - shift, b=60.0 + shift)
+        g0 = ctx.graph_launches()
+        for _ in range(2):
+            sparc.sparc_cheb_filter_batch(Hs, wl.m, a, b, a0, Xd, Y)
+        torch.cuda.synchronize()
+        assert ctx.graph_launches() - g0 == 2
+        assert torch.equal(Y, _filter_each(sparc, Hs, wl.m, a, b, a0, Xd)), shift
+    for H in Hs:
+        H.close()
+
+
 def test_batch_rejects_mismatched_hamiltonians(ctx):
     from paper_1603_04339_gb300 import sparc
     wl = _small_multi_k()
