@@ -273,6 +273,75 @@ __global__ void __launch_bounds__(256) k_chol_blk(TS* A, long long lda, TS* Dk, 
   }
 }
 
+// The same for FP32 blocks of up to 64, left-looking with one thread per row: column j
+// is L_jj = sqrt(a_jj - sum_{k<j} L_jk^2), L_ij = (a_ij - sum_{k<j} L_ik L_jk) / L_jj,
+// two barriers per column; then thread j forms column j of L^-1 by forward
+// substitution, X_jj = 1 / L_jj, X_ij = -(sum_{k=j}^{i-1} L_ik X_kj) / L_ii, with no
+// barrier (each thread owns its column).  Same pivot rule as k_chol_blk<float>.
+__global__ void __launch_bounds__(64) k_chol_blk_f32(float* A, long long lda, float* Dk, long long ldd, int kb,
+                                                     int* status) {
+  __shared__ float L[64][65];
+  __shared__ float X[64][65];
+  __shared__ float piv;
+  __shared__ int bad;
+  const int t = threadIdx.x;
+  if (t == 0) bad = 0;
+  float ajj = 0.f;   // thread t: its original diagonal entry
+  for (int k = 0; k < 64; ++k) {
+    const float v = (t < kb && k <= t) ? A[t + (long long)k * lda] : 0.f;
+    L[t][k] = v;
+    if (k == t) ajj = v;
+  }
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    float s0 = 0.f, s1 = 0.f;
+    if (t >= j && t < kb) {
+      int k = 0;
+      for (; k + 1 < j; k += 2) {
+        s0 = fmaf(L[t][k], L[j][k], s0);
+        s1 = fmaf(L[t][k + 1], L[j][k + 1], s1);
+      }
+      if (k < j) s0 = fmaf(L[t][k], L[j][k], s0);
+    }
+    const float sv = (t >= j && t < kb) ? L[t][j] - (s0 + s1) : 0.f;
+    if (t == j) {
+      if (!(sv > 1e-6f * ajj) || !isfinite(sv)) {
+        bad = 1;
+        atomicOr(status, STATUS_NOT_POSDEF);
+      } else {
+        piv = sqrtf(sv);
+      }
+    }
+    __syncthreads();
+    if (bad) return;
+    const float p = piv;
+    if (t > j && t < kb) L[t][j] = sv / p;
+    if (t == j) L[j][j] = p;
+    __syncthreads();
+  }
+  // column t of the inverse
+  if (t < kb) {
+    for (int i = 0; i < t; ++i) X[i][t] = 0.f;
+    X[t][t] = 1.f / L[t][t];
+    for (int i = t + 1; i < kb; ++i) {
+      float s0 = 0.f, s1 = 0.f;
+      int k = t;
+      for (; k + 1 < i; k += 2) {
+        s0 = fmaf(L[i][k], X[k][t], s0);
+        s1 = fmaf(L[i][k + 1], X[k + 1][t], s1);
+      }
+      if (k < i) s0 = fmaf(L[i][k], X[k][t], s0);
+      X[i][t] = -(s0 + s1) / L[i][i];
+    }
+  }
+  __syncthreads();
+  for (int e = t; e < kb * kb; e += 64) {
+    const int i = e % kb, j = e / kb;
+    A[i + (long long)j * lda] = i >= j ? L[i][j] : 0.f;
+    Dk[i + (long long)j * ldd] = i >= j ? X[i][j] : 0.f;
+  }
+}
+
 // Linv = L^-1 for lower-triangular L (one CTA, one thread per column).
 template <class TW>
 __global__ void __launch_bounds__(1024) k_trinv(const TW* __restrict__ L, TW* __restrict__ Li, int n) {
@@ -864,6 +933,26 @@ cudaError_t gemm64(sparc_ctx* ctx, int M, int N, int K, const TW* A, long long l
   return cudaGetLastError();
 }
 
+// C = alpha op(A) op(B) + beta C with FP32 products of FP64 operands (the small
+// corrections of the mixed mode), split over K so that the GPU is filled: nz partials
+// in `part` (at least nz M N doubles) summed in a fixed order by k_reduce_axpby.
+template <bool ACT, bool BCT>
+cudaError_t gemm_f32p(sparc_ctx* ctx, int M, int N, int K, const double* A, long long lda, const double* B,
+                      long long ldb, double* C, long long ldc, double alpha, double beta, double* part, long long cap,
+                      cudaStream_t st) {
+  const int tiles = ceil_div(M, 64) * ceil_div(N, 64);
+  int nz = std::max(1, std::min(ceil_div(2 * std::max(ctx->nsm, 1), tiles), K / 64));
+  while (nz > 1 && (long long)nz * M * N > cap) --nz;
+  if (nz == 1) return gemm<double, double, float, double, ACT, BCT>(ctx, M, N, K, A, lda, B, ldb, C, ldc, 1, 0, alpha,
+                                                                   st, beta);
+  cudaError_t e = gemm<double, double, float, double, ACT, BCT>(ctx, M, N, K, A, lda, B, ldb, part, M, nz,
+                                                                (long long)M * N, 1.0, st);
+  if (e != cudaSuccess) return e;
+  k_reduce_axpby<double><<<ceil_div((long long)M * N, 256), 256, 0, st>>>(part, nz, M, N, alpha, beta, C, ldc);
+  ++ctx->launches;
+  return cudaGetLastError();
+}
+
 // Blocked right-looking Cholesky of the n x n Hermitian A (lower factor in place)
 // and L^-1 into Li; Dinv receives the inverted diagonal blocks.
 template <class TW>
@@ -875,8 +964,11 @@ sparc_status chol_inverse(sparc_ctx* ctx, TW* A, TW* Li, int n, TW* Dinv, TW* tm
     TW* Dk = Dinv + (size_t)kblk * CB * CB;
     TW* Akk = A + k0 + (long long)k0 * n;
     // diagonal block: contiguous copy, one-CTA factor and inverse, copies back
-    if constexpr (std::is_same<TW, double>::value || std::is_same<TW, float>::value) {
+    if constexpr (std::is_same<TW, float>::value) {
       // factor and invert the block in shared memory, one launch
+      k_chol_blk_f32<<<1, 64, 0, st>>>(Akk, n, Dk, CB, kb, ctx->d_status);
+      ctx->launches += 1;
+    } else if constexpr (std::is_same<TW, double>::value) {
       k_chol_blk<TW, CB><<<1, 256, 0, st>>>(Akk, n, Dk, CB, kb, ctx->d_status);
       ctx->launches += 1;
     } else {
@@ -1182,8 +1274,8 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
       k_phi<<<ceil_div(nn, 256), 256, 0, st>>>(E, nullptr, ns, F);
       ++ctx->launches;
       for (int it = 0; it < 3; ++it) {
-        SPARC_CUDA(ctx, (gemm<double, double, float, double, false, true>(ctx, ns, ns, ns, F, ns, F, ns, G, ns, 1,
-                                                                          nn, 1.0, st)));
+        SPARC_CUDA(ctx, (gemm_f32p<false, true>(ctx, ns, ns, ns, F, ns, F, ns, G, ns, 1.0, 0.0, (double*)partH, pcap,
+                                                st)));
         k_phi<<<ceil_div(nn, 256), 256, 0, st>>>(E, G, ns, F);
         ++ctx->launches;
       }
@@ -1195,21 +1287,20 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
       for (int it = 0; it < 2; ++it) {
         k_identity<double><<<ceil_div(nn, 256), 256, 0, st>>>(Tb, ns);
         ++ctx->launches;
-        SPARC_CUDA(ctx, (gemm<double, double, float, double, false, false>(ctx, ns, ns, ns, F, ns, Ta, ns, Tb, ns, 1,
-                                                                           nn, -1.0, st, 1.0)));
+        SPARC_CUDA(ctx, (gemm_f32p<false, false>(ctx, ns, ns, ns, F, ns, Ta, ns, Tb, ns, -1.0, 1.0, (double*)partH,
+                                                 pcap, st)));
         std::swap(Ta, Tb);
       }
-      SPARC_CUDA(ctx, (gemm<double, double, float, double, false, false>(ctx, ns, ns, ns, F, ns, Ta, ns,
-                                                                         (double*)Kc, ns, 1, nn, -1.0, st)));
+      SPARC_CUDA(ctx, (gemm_f32p<false, false>(ctx, ns, ns, ns, F, ns, Ta, ns, (double*)Kc, ns, -1.0, 0.0,
+                                               (double*)partH, pcap, st)));
       // 4'. C = (I + K) H~ (I + K)^T = H~ + P + P^T + P K^T with P = K H~; the
       // corrections are O(|K| |H~|), so their FP32 products are FP64-accurate in C
       double* P = (double*)T1;
       double* Q = (double*)Yr;
-      SPARC_CUDA(ctx, (gemm<double, double, float, double, false, false>(ctx, ns, ns, ns, (const double*)Kc, ns,
-                                                                         (const double*)Hs, ns, P, ns, 1, nn, 1.0,
-                                                                         st)));
-      SPARC_CUDA(ctx, (gemm<double, double, float, double, false, true>(ctx, ns, ns, ns, P, ns, (const double*)Kc, ns,
-                                                                        Q, ns, 1, nn, 1.0, st)));
+      SPARC_CUDA(ctx, (gemm_f32p<false, false>(ctx, ns, ns, ns, (const double*)Kc, ns, (const double*)Hs, ns, P, ns,
+                                               1.0, 0.0, (double*)partH, pcap, st)));
+      SPARC_CUDA(ctx, (gemm_f32p<false, true>(ctx, ns, ns, ns, P, ns, (const double*)Kc, ns, Q, ns, 1.0, 0.0,
+                                              (double*)partH, pcap, st)));
       k_csum<<<ceil_div(nn, 256), 256, 0, st>>>((const double*)Hs, P, Q, ns, (double*)A0);
       ++ctx->launches;
     }
@@ -1284,9 +1375,8 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
   if (series) {
     SPARC_CUDA(ctx, cudaMemcpyAsync(Yr, Qs, nn * sizeof(TW), cudaMemcpyDeviceToDevice, st));
     if constexpr (TCP)
-      SPARC_CUDA(ctx, (gemm<double, double, float, double, true, false>(ctx, ns, ns, ns, (const double*)Kc, ns,
-                                                                        (const double*)Qs, ns, (double*)Yr, ns, 1,
-                                                                        nn, 1.0, st, 1.0)));
+      SPARC_CUDA(ctx, (gemm_f32p<true, false>(ctx, ns, ns, ns, (const double*)Kc, ns, (const double*)Qs, ns,
+                                              (double*)Yr, ns, 1.0, 1.0, (double*)partH, pcap, st)));
   } else {
     SPARC_CUDA(ctx, (gemm64<TW, true, false>(ctx, ns, ns, ns, Li, ns, Qs, ns, Yr, ns, 1.0, 0.0, partH, pcap, st)));
   }
