@@ -177,8 +177,9 @@ sparc_status sparc_cheb_filter(sparc_ham* H, sparc_dtype dtype, int m, double a,
  *         dimension ld (block k starts at element k * ns * ld); X is not
  *         modified; X and Y may not overlap.
  * Result: block k equals sparc_cheb_filter(H[k], dtype, m, a[k], b[k], a0[k],
- * ...) bit for bit.  Other dtypes, and Hamiltonians outside the tiled kernel's
- * range (fd_radius != 6), run one sparc_cheb_filter per k.
+ * ...) bit for bit.  Other dtypes, Hamiltonians outside the tiled kernel's range
+ * (fd_radius != 6), and Hamiltonians on the TMA-fed pass (sparc_filter_kernel) whose
+ * projector values differ between k, run one sparc_cheb_filter per k.
  * With SPARC_C64 the call's launches are captured once into a CUDA graph held by
  * the context and replayed, one graph launch per call; a call with the same
  * Hamiltonians, sizes and buffers but new bounds updates that graph in place.  (With
@@ -187,6 +188,19 @@ sparc_status sparc_cheb_filter(sparc_ham* H, sparc_dtype dtype, int m, double a,
 sparc_status sparc_cheb_filter_batch(sparc_ham* const* H, int nk, sparc_dtype dtype, int m,
                                      const double* a, const double* b, const double* a0,
                                      const void* X, void* Y, int ns, int64_t ld, void* stream);
+
+/* Which H-pass kernel sparc_cheb_filter(H, dtype, ...) runs (the recurrence step of
+ * Eq. ChebFilter, the H-apply of Section 3.1):
+ *   SPARC_KERNEL_GENERIC (0): the per-node kernel (FP64, complex128, fd_radius != 6);
+ *   SPARC_KERNEL_TILED (1): the tiled FP32 / complex64 pass;
+ *   SPARC_KERNEL_TMA (2): the TMA-fed pass on x-padded blocks (FP32 at the Gamma
+ *     point; complex64 at any k, with the projector slots split by periodic image)
+ * (without a tuned tile shape).  Returns SPARC_ERR_INVALID_ARG for a null H or
+ * out, an unknown dtype or a real dtype for a complex Hamiltonian. */
+#define SPARC_KERNEL_GENERIC 0
+#define SPARC_KERNEL_TILED 1
+#define SPARC_KERNEL_TMA 2
+sparc_status sparc_filter_kernel(const sparc_ham* H, sparc_dtype dtype, int* out);
 
 /* Launch-shape autotuner of the filter.  Times sparc_cheb_filter_batch (degree
  * min(m, 4), arguments as there) for several launch configurations, keeps the

@@ -53,16 +53,20 @@ struct Layout {
   int* d_sslots = nullptr;    // CTA-local indices of the pieces touching those nodes at z
 };
 
-// Tables of the TMA-fed FP32 pass (hpass_tma.cu): per tile column (16 x 16 (x, y) tile,
-// all z) the projector groups (atom boxes) that meet it, and per (tile, plane) a record
-// of the A fragments of the projector term for each of the 16 warps of a CTA.
-constexpr int TMA_MAXG = 64;                 // projector groups per tile column, at most
+// Tables of the TMA-fed passes (hpass_tma.cu): per tile column (16 x 16 (x, y) tile,
+// all z) the projector slots that meet it, and per (tile, plane) a record of the A
+// fragments of the projector term for each of the 16 warps of a CTA.  A slot is a
+// projector group (atom box); for complex (k-point) Hamiltonians it is a group in one
+// periodic image t = (tx, ty, tz) of the cell, so that its Bloch factor exp(-i k.(t L))
+// is one constant that the kernel folds into the slot's coefficients.
+constexpr int TMA_MAXG = 64;                 // projector slots per tile column, at most
 constexpr unsigned TMA_REC_MAX = 36352;      // bytes of one plane's record, at most
 constexpr int TMA_MAXTY = 16;                // tile rows (n2 <= 256)
 constexpr int TMA_MAXSEG = 4;                // y segments of one halo frame
 constexpr int TMA_NMAPS = 8;                 // distinct segment heights
 struct TmaTables {
   bool ok = false;            // built: the grid and projectors fit the kernel's limits
+  bool cplx = false;          // slots split by periodic image (complex Hamiltonian)
   int zl = 0, nchunk = 0, tiles_x = 0, tiles_y = 0;   // zl = n3, nchunk = 1 (per launch: see the launcher)
   int max_rec = 0;
   // The halo frame of tile row ty, rows y = 16 ty - 6 .. 16 ty + 21 wrapped into [0, n2),
@@ -72,7 +76,9 @@ struct TmaTables {
   int map_h[TMA_NMAPS] = {};
   int yseg[TMA_MAXTY][TMA_MAXSEG][3] = {};
   int* d_cproj = nullptr;     // [tile][TMA_MAXG][4] projector index of (group slot, s/px/py/pz), -1 if none
-  int* d_cng = nullptr;       // [tile] groups of the tile column
+  int* d_cng = nullptr;       // [tile] slots of the tile column
+  int* d_cimg = nullptr;      // [tile][TMA_MAXG] image of the slot: (tx+1) | (ty+1) << 2 | (tz+1) << 4
+  unsigned long long rec_hash = 0;   // hash of the record values (projector values at the nodes)
   int* d_rec = nullptr;       // [tile * n3 + z] record offsets in 16-byte units (+ one end entry)
   void* d_stream = nullptr;   // the records
   size_t stream_bytes = 0;
@@ -81,12 +87,13 @@ struct TmaTables {
 // The same tables on the host, before upload.
 struct TmaHost {
   TmaTables dims;                 // zl, nchunk, tiles, max_rec (no device pointers)
-  std::vector<int> cproj, cng, rec;
+  std::vector<int> cproj, cng, rec, cimg;
   std::vector<uint32_t> words;    // the records
 };
 
 struct Tables {
-  TmaTables tma;
+  TmaTables tma;              // folded slots: the FP32 pass (real Hamiltonians)
+  TmaTables tmac;             // slots split by image: the complex64 pass
   int ngrp = 0, nsb = 0;
   Group* d_grp = nullptr;
   SubBox* d_sb = nullptr;
@@ -128,10 +135,15 @@ sparc_status build_tma_tables(sparc_ham* H, Tables* T, const std::vector<Group>&
                               const std::vector<std::array<int, 6>>& gbox, const std::vector<float>& chi4);
 void free_tma_tables(TmaTables& M);
 bool tma_frame_segments(int n2, TmaTables& M);
+// images: one slot per (group, periodic image) instead of one per group.
 bool tma_host_tables(const int n[3], const std::vector<Group>& grps, const std::vector<std::array<int, 6>>& gbox,
-                     const std::vector<float>& chi4, TmaHost& out);
-// Whether the TMA-fed FP32 pass applies to H (Gamma point, radius 6, n1 % 4 == 0, limits).
+                     const std::vector<float>& chi4, TmaHost& out, bool images = false);
+// Whether the TMA-fed FP32 pass applies to H (Gamma point, radius 6, n1 % 4 == 0,
+// n1 >= 2R, the table limits).
 bool tma_usable(const sparc_ham* H);
+// Whether the TMA-fed complex64 pass applies to H (any k; as above, and every halo-frame
+// row within one cell of the grid in y).
+bool tma_usable_c(const sparc_ham* H);
 // The TMA pass works on an x-padded block layout: every (y, z) row holds R ghost nodes
 // on each side, copies of the other end of the row (periodic wrap):
 //   B[blk][z][y][x'][NB], x' = x + R in [0, n1 + 2R); x' < R holds x = n1 - R + x',
@@ -141,11 +153,22 @@ cudaError_t launch_to_blocks_px(const sparc_ham* H, const float* X, long long ld
                                 cudaStream_t st);
 cudaError_t launch_from_blocks_px(const sparc_ham* H, const float* B, int nblk, float* X, long long ld, int ns,
                                   cudaStream_t st);
+// Complex64: ghost nodes hold the Bloch image, x' < R: conj(ph_x) Y(x + n1), x' >= n1 + R:
+// ph_x Y(x - n1), ph_x = exp(i k_x L_x).
+cudaError_t launch_to_blocks_px(const sparc_ham* H, const cf32* X, long long ld, int ns, cf32* B, int nblk,
+                                cudaStream_t st);
+cudaError_t launch_from_blocks_px(const sparc_ham* H, const cf32* B, int nblk, cf32* X, long long ld, int ns,
+                                  cudaStream_t st);
 // The TMA-fed FP32 pass: Yout = alpha (H - shift) Yin + beta Yprev for blocks [blk0, blk0 + nb)
 // of x-padded buffers (Yout's ghost nodes are written too).
 cudaError_t launch_pass_tma(const sparc_ham* H, const float* Yin, const float* Yprev, float* Yout, const float* gc,
                             int nblk_total, int blk0, int nb, double alpha, double shift, double beta,
                             cudaStream_t st);
+// Whether the complex TMA pass of H0 may serve H in one batched launch: the same grid,
+// projector slots and record values (the per-k phases, V_eff and gamma may differ).
+bool tma_batch_compatible(const sparc_ham* H0, const sparc_ham* H);
+// Work items of one block (FP32) or unit (complex: two half-units) per z-chunk.
+int tma_items_per_unit(const sparc_ham* H);
 
 // FP32 pass tile shapes: 0 = 16 x 16 nodes, 512 threads, one CTA per SM;
 // 1 = 16 x 8 nodes, 256 threads, two CTAs per SM; 2 = the TMA-fed pass (16 x 16
@@ -164,7 +187,7 @@ int items_per_block(const sparc_ham* H, int shape = 0);
 // gc[p][blk][lane] for the blocks [blk0, blk0 + nb) (gamma_p h^3 chi~_p^H Y);
 // `scratch` holds gather_scratch_bytes(H, nb, sizeof(T)) bytes of per-slab partial sums.
 size_t gather_scratch_bytes(const sparc_ham* H, int nb, size_t esize);
-// padded (FP32 only): Y is in the x-padded layout of the TMA pass.
+// padded: Y is in the x-padded layout of the TMA passes.
 template <class T>
 cudaError_t launch_gather(const sparc_ham* H, const T* Y, int nblk_total, int blk0, int nb, T* gc,
                           T* scratch, cudaStream_t st, bool padded = false);
@@ -177,10 +200,16 @@ cudaError_t launch_pass(const sparc_ham* H, const T* Yin, const T* Yprev, T* You
 // Complex64, batched over k: the same two steps for the units of `ks`; `gc` and
 // the block buffers hold nunit_total units ([unit][Nd][NB] and [p][unit][NB]);
 // geometry and launch shape from H0.
+// padded: Y in the x-padded layout of the TMA passes.
 cudaError_t launch_gather_k(const sparc_ham* H0, const cf32* Y, long long nunit_total, const KSlots& ks,
-                            cf32* gc, cf32* scratch, cudaStream_t st);
+                            cf32* gc, cf32* scratch, cudaStream_t st, bool padded = false);
 cudaError_t launch_pass_k(const sparc_ham* H0, const cf32* Yin, const cf32* Yprev, cf32* Yout, const cf32* gc,
                           long long nunit_total, const KSlots& ks, cudaStream_t st);
+// The TMA-fed complex64 pass over the units of `ks` in x-padded buffers (hpass_tma.cu);
+// every H of the batch passes tma_batch_compatible with H0.  Uses alpha, shift, beta,
+// veff and the face phases of the slots.
+cudaError_t launch_pass_tma_k(const sparc_ham* H0, const cf32* Yin, const cf32* Yprev, cf32* Yout, const cf32* gc,
+                              long long nunit_total, const KSlots& ks, cudaStream_t st);
 
 }  // namespace fast
 }  // namespace sparc

@@ -51,10 +51,12 @@ template <class T>
 cudaError_t launch_from_blocks(const T* B, long long nd, int nblk, T* X, long long ld, int ns,
                                cudaStream_t st);
 // The same between X and a row layout: nd = rows x n1 nodes, each row held as n1 + 2 pad
-// nodes in the blocks (pad ghost nodes at either end repeat the other end of the row).
+// nodes in the blocks (pad ghost nodes at either end repeat the other end of the row;
+// for complex data times the Bloch factor ph = exp(i k_x L_x) on the right, conj(ph) on
+// the left).
 template <class T>
 cudaError_t launch_to_blocks_rows(const T* X, long long ld, int ns, T* B, long long nd, int n1, int pad,
-                                  int nblk, cudaStream_t st);
+                                  int nblk, cudaStream_t st, cf32 ph = cf32{1.f, 0.f});
 template <class T>
 cudaError_t launch_from_blocks_rows(const T* B, long long nd, int n1, int pad, int nblk, T* X, long long ld,
                                     int ns, cudaStream_t st);

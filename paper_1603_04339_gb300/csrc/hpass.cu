@@ -7,6 +7,8 @@
 // orbitals of one grid node are one contiguous 32-byte sector (FP32), the
 // projector values of a node are shared by its 8 lanes, and every node-index
 // computation is shared by those lanes.
+#include <type_traits>
+
 #include "ham.cuh"
 
 namespace sparc {
@@ -180,16 +182,20 @@ __global__ void __launch_bounds__(256) k_from_blocks(const T* __restrict__ B, lo
 // the plain layout).  Thread (x', part) moves the 16 bytes of 16 / sizeof(T)
 // orbitals of node x' in every row of the CTA: reads along a row are coalesced per
 // orbital, writes contiguous; orbitals past ns read as zero.  nd = nrows n1.
+// Complex data are Bloch-periodic (Section 3.1): a ghost node x = x' - pad outside
+// [0, n1) holds its image's value times ph^t, t = floor(x / n1), ph = exp(i k_x L_x).
 template <class T>
 __global__ void __launch_bounds__(1024) k_to_blocks_rows(const T* __restrict__ X, long long ld, int ns,
                                                         T* __restrict__ B, int n1, int pad, long long nrows,
-                                                        int rpc) {
+                                                        int rpc, cf32 ph) {
   constexpr int EPT = 16 / (int)sizeof(T), TPN = NB / EPT;
   const int n1p = n1 + 2 * pad;
   const int t = threadIdx.x;
   if (t >= TPN * n1p) return;
   const int xp = t / TPN, part = t % TPN;
   const int xs = ((xp - pad) % n1 + n1) % n1;
+  // phase of this thread's node: 1 inside the row, ph (right ghosts) or conj(ph) (left)
+  const cf32 gph = xp < pad ? cf32{ph.x, -ph.y} : (xp >= n1 + pad ? ph : cf32{1.f, 0.f});
   const int blk = blockIdx.y;
   const int c0 = blk * NB + part * EPT;
   const long long r0 = (long long)blockIdx.x * rpc, r1 = min(nrows, r0 + rpc);
@@ -201,6 +207,10 @@ __global__ void __launch_bounds__(1024) k_to_blocks_rows(const T* __restrict__ X
 #pragma unroll
     for (int e = 0; e < EPT; ++e)
       w.v[e] = c0 + e < ns ? X[g + (long long)(c0 + e) * ld] : Tr<T>::zero();
+    if constexpr (std::is_same<T, cf32>::value) {
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) w.v[e] = w.v[e] * gph;
+    }
     *reinterpret_cast<uint4*>(Bb + (size_t)(r * n1p + xp) * NB) = w.u;
   }
 }
@@ -253,14 +263,15 @@ static int rows_per_cta(int n1p) {
 
 template <class T>
 cudaError_t launch_to_blocks_rows(const T* X, long long ld, int ns, T* B, long long nd, int n1, int pad,
-                                  int nblk, cudaStream_t st) {
+                                  int nblk, cudaStream_t st, cf32 ph) {
   constexpr int TPN = NB / (16 / (int)sizeof(T));
   const int n1p = n1 + 2 * pad;
   if (TPN * n1p > 1024 || n1 <= 0 || nd % n1 != 0) return cudaErrorInvalidValue;
   const long long nrows = nd / n1;
   const int rpc = rows_per_cta<T>(n1p);
   dim3 grid((unsigned)ceil_div(nrows, (long long)rpc), (unsigned)nblk);
-  k_to_blocks_rows<T><<<grid, (unsigned)ceil_div(TPN * n1p, 32) * 32, 0, st>>>(X, ld, ns, B, n1, pad, nrows, rpc);
+  k_to_blocks_rows<T><<<grid, (unsigned)ceil_div(TPN * n1p, 32) * 32, 0, st>>>(X, ld, ns, B, n1, pad, nrows, rpc,
+                                                                                 ph);
   return cudaGetLastError();
 }
 
@@ -347,7 +358,7 @@ cudaError_t launch_hpass(const sparc_ham* H, const T* Yin, const T* Yprev, T* Yo
 
 #define SPARC_INST(T)                                                                          \
   template cudaError_t launch_to_blocks_rows<T>(const T*, long long, int, T*, long long, int, int, \
-                                                int, cudaStream_t);                            \
+                                                int, cudaStream_t, cf32);                      \
   template cudaError_t launch_from_blocks_rows<T>(const T*, long long, int, int, int, T*,      \
                                                   long long, int, cudaStream_t);               \
   template cudaError_t launch_to_blocks<T>(const T*, long long, int, T*, long long, int,       \

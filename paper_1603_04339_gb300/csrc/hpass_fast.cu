@@ -32,6 +32,7 @@ namespace fast {
 
 void free_tables(Tables& t) {
   free_tma_tables(t.tma);
+  free_tma_tables(t.tmac);
   void* ps[] = {t.d_grp, t.d_sb, t.d_chi4};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -962,7 +963,7 @@ __device__ __forceinline__ void gather_row(T (&s)[NBM][4], const float4* __restr
 // part[((g * nslab + s) * 4 + l) * (nk * nbk * NB) + (kk * nbk + bi) * NB + lane] gets the CTA sum.
 template <class T, int NBM>
 __global__ void __launch_bounds__(256, 2)
-k_gather_rows(const T* __restrict__ Y, long long nd, int n1, int n2, const Group* __restrict__ grp,
+k_gather_rows(const T* __restrict__ Y, long long nd, int rowp, int xoff, int n2, const Group* __restrict__ grp,
               const __grid_constant__ KSlots ks, T* __restrict__ part, int noct, int nslab) {
   __shared__ T red[8][NBM][4][NB];
   const int gi = blockIdx.x, sl = blockIdx.y;
@@ -990,7 +991,7 @@ k_gather_rows(const T* __restrict__ Y, long long nd, int n1, int n2, const Group
     const int first = (sl - rbase % nslab + nslab) % nslab;
     for (int row = first + warp * nslab; row < rows; row += 8 * nslab) {
       const int iy = row % wy, iz = row / wy;
-      const long long yrow = ((long long)(sb.gz0 + iz) * n2 + (sb.gy0 + iy)) * n1 + sb.gx0;
+      const long long yrow = ((long long)(sb.gz0 + iz) * n2 + (sb.gy0 + iy)) * rowp + sb.gx0 + xoff;
       const long long crow =
           sb.chi4_off + sb.bx0 + (long long)sb.nbx * ((sb.by0 + iy) + (long long)sb.nby * (sb.bz0 + iz));
       if constexpr (FT<T>::cplx) {
@@ -1224,7 +1225,7 @@ size_t gather_scratch_bytes(const sparc_ham* H, int nb, size_t esize) {
 }
 
 cudaError_t launch_gather_k(const sparc_ham* H0, const cf32* Y, long long nunit_total, const KSlots& ks,
-                            cf32* gc, cf32* scratch, cudaStream_t st) {
+                            cf32* gc, cf32* scratch, cudaStream_t st, bool padded) {
   const Tables* Tb = (const Tables*)H0->fast;
   if (H0->nproj == 0 || Tb->ngrp == 0) return cudaSuccess;
   const float dv = (float)(H0->grid.h[0] * H0->grid.h[1] * H0->grid.h[2]);
@@ -1233,7 +1234,9 @@ cudaError_t launch_gather_k(const sparc_ham* H0, const cf32* Y, long long nunit_
   constexpr int NBM = GATHER_OCT_C;
   const int noct = ceil_div(ks.nbk, NBM);
   const dim3 grid((unsigned)Tb->ngrp, (unsigned)nslab, (unsigned)(ks.nk * noct));
-  k_gather_rows<cf32, NBM><<<grid, 256, 0, st>>>(Y, H0->gd.nd, H0->gd.n1, H0->gd.n2, Tb->d_grp, ks, scratch,
+  const int rowp = padded ? H0->gd.n1 + 2 * R : H0->gd.n1;
+  const long long ndl = (long long)rowp * H0->gd.n2 * H0->gd.n3;
+  k_gather_rows<cf32, NBM><<<grid, 256, 0, st>>>(Y, ndl, rowp, padded ? R : 0, H0->gd.n2, Tb->d_grp, ks, scratch,
                                                  noct, nslab);
   const long long tot = (long long)Tb->ngrp * 4 * ks.nk * ks.nbk * NB;
   k_gather_sum_k<<<ceil_div(tot, 256), 256, 0, st>>>(scratch, Tb->d_grp, ks, dv, gc, Tb->ngrp, nslab,
@@ -1255,7 +1258,7 @@ cudaError_t launch_gather(const sparc_ham* H, const T* Y, int nblk_total, int bl
     kslot(H, ks.s[0]);
     ks.s[0].ubase = blk0;
     ks.s[0].alpha = ks.s[0].shift = ks.s[0].beta = 0.f;
-    return launch_gather_k(H, Y, nblk_total, ks, gc, scratch, st);
+    return launch_gather_k(H, Y, nblk_total, ks, gc, scratch, st, padded);
   } else {
     const float dv = (float)(H->grid.h[0] * H->grid.h[1] * H->grid.h[2]);
     const int nslab = gather_slabs_f2(H, nblk_total);

@@ -41,6 +41,7 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "fast.cuh"
@@ -87,18 +88,26 @@ static int cover(int c, int lo, int nb, int n) {   // box-local index of coordin
   if (u < 0) u += n;
   return u < nb ? u : -1;
 }
+// Box-local index of grid coordinate c in periodic image t (the box node lo + u lies at
+// grid node lo + u - t n), or -1.
+static int cover_img(int c, int t, int lo, int nb, int n) {
+  const int u = c + t * n - lo;
+  return (u >= 0 && u < nb) ? u : -1;
+}
+static int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
 }  // namespace tma
 
 // The tables on the host: false where the grid or the projectors exceed the kernel's
-// limits (groups per CTA, record size).
+// limits (slots per CTA, record size, images beyond the neighbouring cells).
 bool tma_host_tables(const int n[3], const std::vector<Group>& grps, const std::vector<std::array<int, 6>>& gbox,
-                     const std::vector<float>& chi4, TmaHost& out) {
+                     const std::vector<float>& chi4, TmaHost& out, bool images) {
   using namespace tma;
   TmaTables& M = out.dims;
   std::vector<int>& cproj = out.cproj;
   std::vector<int>& cng = out.cng;
   std::vector<int>& rec = out.rec;
+  std::vector<int>& cimg = out.cimg;
   std::vector<uint32_t>& words = out.words;
   // tables per tile column (all z); the z-chunking of the work is chosen per launch
   M.nchunk = 1;
@@ -116,6 +125,7 @@ bool tma_host_tables(const int n[3], const std::vector<Group>& grps, const std::
     }
   }
   cproj.assign((size_t)ncta * MAXG * 4, -1);
+  cimg.assign((size_t)ncta * MAXG, 1 | (1 << 2) | (1 << 4));   // image (0, 0, 0)
   cng.assign(ncta, 0);
   rec.assign((size_t)ncta * M.zl + 1, 0);
   words.clear();
@@ -126,34 +136,64 @@ bool tma_host_tables(const int n[3], const std::vector<Group>& grps, const std::
     const int x0 = (tile % M.tiles_x) * TT, y0 = (tile / M.tiles_x) * TT;
     const int zs = 0, nz = n[2];
     const int xe = std::min(n[0], x0 + TT), ye = std::min(n[1], y0 + TT);
-    // the atom boxes (projector groups) that meet the tile over the chunk's planes
-    std::vector<int> loc;
+    // the slots that meet the tile over the chunk's planes: the atom boxes (projector
+    // groups), with images split (one slot per image whose nodes meet the tile)
+    std::vector<int> loc, limg;
     std::vector<std::array<int, TT>> ux, uy;
     std::vector<std::vector<int>> uz;
     for (int G = 0; G < ngrp; ++G) {
-      std::array<int, TT> cx, cy;
-      bool hx = false, hy = false, hz = false;
-      for (int i = 0; i < TT; ++i) {
-        cx[i] = (x0 + i < xe) ? cover(x0 + i, gbox[G][0], gbox[G][3], n[0]) : -1;
-        cy[i] = (y0 + i < ye) ? cover(y0 + i, gbox[G][1], gbox[G][4], n[1]) : -1;
-        hx |= cx[i] >= 0;
-        hy |= cy[i] >= 0;
+      const int* lo = &gbox[G][0];
+      const int* nb = &gbox[G][3];
+      // candidate images per axis: all of them (folded, t = 0 stands for every image)
+      // or each image of the unwrapped box [lo, lo + nb)
+      int t0[3], t1[3];
+      for (int ax = 0; ax < 3; ++ax) {
+        t0[ax] = images ? floordiv(lo[ax], n[ax]) : 0;
+        t1[ax] = images ? floordiv(lo[ax] + nb[ax] - 1, n[ax]) : 0;
+        if (t0[ax] < -1 || t1[ax] > 1) return false;   // images beyond the neighbouring cells
       }
-      std::vector<int> cz(nz);
-      for (int k = 0; k < nz; ++k) {
-        cz[k] = cover(zs + k, gbox[G][2], gbox[G][5], n[2]);
-        hz |= cz[k] >= 0;
+      auto cov = [&](int c, int t, int ax) {
+        return images ? cover_img(c, t, lo[ax], nb[ax], n[ax]) : cover(c, lo[ax], nb[ax], n[ax]);
+      };
+      for (int tz = t0[2]; tz <= t1[2]; ++tz) {
+        std::vector<int> cz(nz);
+        bool hz = false;
+        for (int k = 0; k < nz; ++k) {
+          cz[k] = cov(zs + k, tz, 2);
+          hz |= cz[k] >= 0;
+        }
+        if (!hz) continue;
+        for (int ty = t0[1]; ty <= t1[1]; ++ty) {
+          std::array<int, TT> cy;
+          bool hy = false;
+          for (int i = 0; i < TT; ++i) {
+            cy[i] = (y0 + i < ye) ? cov(y0 + i, ty, 1) : -1;
+            hy |= cy[i] >= 0;
+          }
+          if (!hy) continue;
+          for (int tx = t0[0]; tx <= t1[0]; ++tx) {
+            std::array<int, TT> cx;
+            bool hx = false;
+            for (int i = 0; i < TT; ++i) {
+              cx[i] = (x0 + i < xe) ? cov(x0 + i, tx, 0) : -1;
+              hx |= cx[i] >= 0;
+            }
+            if (!hx) continue;
+            loc.push_back(G);
+            limg.push_back((tx + 1) | ((ty + 1) << 2) | ((tz + 1) << 4));
+            ux.push_back(cx);
+            uy.push_back(cy);
+            uz.push_back(cz);
+          }
+        }
       }
-      if (!(hx && hy && hz)) continue;
-      loc.push_back(G);
-      ux.push_back(cx);
-      uy.push_back(cy);
-      uz.push_back(cz);
     }
-    if ((int)loc.size() > MAXG) return false;   // too many boxes per tile column: the other kernels run
+    if ((int)loc.size() > MAXG) return false;   // too many slots per tile column: the other kernels run
     cng[cta] = (int)loc.size();
-    for (size_t g = 0; g < loc.size(); ++g)
+    for (size_t g = 0; g < loc.size(); ++g) {
       for (int l = 0; l < 4; ++l) cproj[((size_t)cta * MAXG + g) * 4 + l] = grps[loc[g]].proj[l];
+      cimg[(size_t)cta * MAXG + g] = limg[g];
+    }
     for (int k = 0; k < M.zl; ++k) {
       rec[(size_t)cta * M.zl + k] = (int)(words.size() / 4);
       if (k >= nz) continue;
@@ -249,26 +289,57 @@ bool tma_frame_segments(int n2, TmaTables& M) {
   return true;
 }
 
-sparc_status build_tma_tables(sparc_ham* H, Tables* T, const std::vector<Group>& grps,
-                              const std::vector<std::array<int, 6>>& gbox, const std::vector<float>& chi4) {
+// One table set: folded slots (images = false, the FP32 pass at the Gamma point) or
+// slots split by periodic image (the complex pass); M.ok stays false where the grid or
+// the projectors exceed the kernel's limits.
+static sparc_status build_tma_set(sparc_ham* H, TmaTables& M, const std::vector<Group>& grps,
+                                  const std::vector<std::array<int, 6>>& gbox, const std::vector<float>& chi4,
+                                  bool images) {
   using namespace tma;
-  TmaTables& M = T->tma;
   M = TmaTables();
   const int n[3] = {H->gd.n1, H->gd.n2, H->gd.n3};
-  if (H->gd.cplx || H->gd.no != R || n[0] % 4 != 0) return SPARC_OK;   // not this kernel's case
+  // not this kernel's case: another radius; V_eff rows not 16-byte multiples; rows
+  // shorter than their two ghost runs; planes that a z-chunk's halo would wrap twice
+  if (H->gd.no != R || n[0] % 4 != 0 || n[0] < 2 * R || n[2] <= R) return SPARC_OK;
+  if (images) {
+    // the complex pass applies one Bloch factor per halo-frame row: every frame row
+    // y = 16 ty - 6 .. 16 ty + 21 lies within one cell of [0, n2)
+    if (n[1] <= R) return SPARC_OK;
+    for (int y0 = 0; y0 < n[1]; y0 += TT)
+      if (y0 + TT + R - 1 >= 2 * n[1]) return SPARC_OK;
+  }
   TmaHost h;
-  if (!tma_host_tables(n, grps, gbox, chi4, h)) return SPARC_OK;
+  if (!tma_host_tables(n, grps, gbox, chi4, h, images)) return SPARC_OK;
   if (!tma_frame_segments(n[1], h.dims)) return SPARC_OK;
   M = h.dims;
+  M.cplx = images;
   const std::vector<int>& cproj = h.cproj;
   const std::vector<int>& cng = h.cng;
   const std::vector<int>& rec = h.rec;
+  const std::vector<int>& cimg = h.cimg;
   const std::vector<uint32_t>& words = h.words;
+  {
+    // FNV-1a over everything a launch takes from the tables (the batched complex pass
+    // serves several Hamiltonians with the tables of one)
+    unsigned long long hsh = 1469598103934665603ULL;
+    auto mix = [&](const void* p, size_t bytes) {
+      const unsigned char* c = (const unsigned char*)p;
+      for (size_t i = 0; i < bytes; ++i) { hsh ^= c[i]; hsh *= 1099511628211ULL; }
+    };
+    mix(n, sizeof(int) * 3);
+    mix(cproj.data(), cproj.size() * sizeof(int));
+    mix(cimg.data(), cimg.size() * sizeof(int));
+    mix(cng.data(), cng.size() * sizeof(int));
+    mix(rec.data(), rec.size() * sizeof(int));
+    mix(words.data(), words.size() * sizeof(uint32_t));
+    M.rec_hash = hsh;
+  }
   auto up = [&](void** d, const void* h, size_t bytes) -> bool {
     if (cudaMalloc(d, std::max<size_t>(bytes, 16)) != cudaSuccess) return false;
     return bytes == 0 || cudaMemcpy(*d, h, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
   };
   if (!up((void**)&M.d_cproj, cproj.data(), cproj.size() * sizeof(int)) ||
+      !up((void**)&M.d_cimg, cimg.data(), cimg.size() * sizeof(int)) ||
       !up((void**)&M.d_cng, cng.data(), cng.size() * sizeof(int)) ||
       !up((void**)&M.d_rec, rec.data(), rec.size() * sizeof(int)) ||
       !up(&M.d_stream, words.data(), words.size() * sizeof(uint32_t))) {
@@ -281,8 +352,21 @@ sparc_status build_tma_tables(sparc_ham* H, Tables* T, const std::vector<Group>&
   return SPARC_OK;
 }
 
+// A real Hamiltonian gets both sets (FP32 filters take the folded one; complex64 filters
+// the split one, which a k-point batch shares with the complex Hamiltonians); a complex
+// one the split set only.
+sparc_status build_tma_tables(sparc_ham* H, Tables* T, const std::vector<Group>& grps,
+                              const std::vector<std::array<int, 6>>& gbox, const std::vector<float>& chi4) {
+  T->tma = TmaTables();
+  if (!H->gd.cplx) {
+    const sparc_status s = build_tma_set(H, T->tma, grps, gbox, chi4, false);
+    if (s != SPARC_OK) return s;
+  }
+  return build_tma_set(H, T->tmac, grps, gbox, chi4, true);
+}
+
 void free_tma_tables(TmaTables& M) {
-  void* ps[] = {M.d_cproj, M.d_cng, M.d_rec, M.d_stream};
+  void* ps[] = {M.d_cproj, M.d_cimg, M.d_cng, M.d_rec, M.d_stream};
   for (void* p : ps)
     if (p) cudaFree(p);
   M = TmaTables();
@@ -291,6 +375,24 @@ void free_tma_tables(TmaTables& M) {
 bool tma_usable(const sparc_ham* H) {
   const Tables* T = (const Tables*)H->fast;
   return T != nullptr && T->tma.ok && usable(H);
+}
+
+bool tma_usable_c(const sparc_ham* H) {
+  const Tables* T = (const Tables*)H->fast;
+  return T != nullptr && T->tmac.ok && usable(H);
+}
+
+int tma_items_per_unit(const sparc_ham* H) {
+  const TmaTables& M = ((const Tables*)H->fast)->tmac;
+  return M.tiles_x * M.tiles_y * 2;
+}
+
+bool tma_batch_compatible(const sparc_ham* H0, const sparc_ham* H) {
+  if (!tma_usable_c(H0) || !tma_usable_c(H)) return false;
+  const TmaTables& A = ((const Tables*)H0->fast)->tmac;
+  const TmaTables& B = ((const Tables*)H->fast)->tmac;
+  return A.rec_hash == B.rec_hash && A.stream_bytes == B.stream_bytes && H0->gd.n1 == H->gd.n1 &&
+         H0->gd.n2 == H->gd.n2 && H0->gd.n3 == H->gd.n3;
 }
 
 namespace tma {
@@ -314,6 +416,7 @@ struct Args {
   const int* cng;            // [tile]
   const int* rec;            // [tile * n3 + z] record offsets, 16-byte units
   const unsigned char* stream;
+  const int* cimg;           // [tile][MAXG] slot images (complex pass)
   int* status;
   long long wait_limit;      // SM clocks of a bounded wait
   int stall;                 // failure injection: the producer stops at this step (-1: off)
@@ -359,11 +462,37 @@ __device__ __forceinline__ void tma4_hint(void* dst, const CUtensorMap* m, int c
 }
 
 // The tensor maps of a launch: halo-frame runs of each height, the tile of Yin and of
-// Yprev (16 x 16 nodes, padded layout) and V_eff.
-struct Maps {
+// Yprev (16 x 16 nodes, padded layout) and V_eff (one per k of a complex launch).
+template <bool CX>
+struct MapsT {
   CUtensorMap frame[TMA_NMAPS];
-  CUtensorMap tile_in, tile_prev, veff;
+  CUtensorMap tile_in, tile_prev;
+  CUtensorMap veff[CX ? KMAX : 1];
 };
+
+// Per-k fields of a complex launch: it covers the units ubase[kk] + j, j < nbk, kk < nk,
+// each as two halves of four complex orbitals (items are half-units).
+struct KArgs {
+  int nk, nbk;
+  long long ubase[KMAX];
+  float2 alpha2[KMAX], beta2[KMAX];
+  float c0s[KMAX];
+  float2 phx[KMAX], phy[KMAX], phz[KMAX];   // exp(i k_s L_s)
+};
+struct KArgsNone {
+  int unused;
+};
+template <bool CX>
+using KArgsT = typename std::conditional<CX, KArgs, KArgsNone>::type;
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 conj2(float2 a) { return make_float2(a.x, -a.y); }
+// ph^t for t in {-1, 0, 1}
+__device__ __forceinline__ float2 face(float2 ph, int t) {
+  return t == 0 ? make_float2(1.f, 0.f) : (t > 0 ? ph : conj2(ph));
+}
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(ptx::saddr(b)) : "memory");
@@ -382,10 +511,14 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], float a0, float a1, floa
         "r"(__float_as_uint(b0)), "r"(__float_as_uint(b1)));
 }
 
+// A work item: tile column, z-chunk and block (FP32) or half-unit (complex: half h of
+// unit blk, the k slot kk).
 struct Item {
   int tile, chunk, bi, tx0, ty0, zs, nz;
+  int blk, h, kk;
 };
-__device__ __forceinline__ Item decode(const Args& a, int item) {
+template <bool CX>
+__device__ __forceinline__ Item decode(const Args& a, const KArgsT<CX>& ka, int item) {
   Item it;
   it.tile = item % a.ntiles;
   const int rest = item / a.ntiles;
@@ -395,6 +528,16 @@ __device__ __forceinline__ Item decode(const Args& a, int item) {
   it.ty0 = (it.tile / a.tiles_x) * TT;
   it.zs = it.chunk * a.zl;
   it.nz = min(a.zl, a.n3 - it.zs);
+  if constexpr (CX) {
+    const int u = it.bi >> 1;
+    it.h = it.bi & 1;
+    it.kk = u / ka.nbk;
+    it.blk = (int)(ka.ubase[it.kk] + u % ka.nbk);
+  } else {
+    it.h = 0;
+    it.kk = 0;
+    it.blk = a.blk0 + it.bi;
+  }
   return it;
 }
 
@@ -403,11 +546,13 @@ __device__ __forceinline__ Item decode(const Args& a, int item) {
 // entries 0 .. nz).  Returns false if the wait for the stage to be free ran out; once
 // a wait has run out (wait == false) no further waits are made, so that a broken
 // pipeline ends the kernel quickly instead of timing out at every step.
-__device__ __forceinline__ bool produce(const Args& a, const Maps& mp, unsigned char* smem, uint64_t* bars, int item,
-                                       int s, int g, const int* recs, bool wait) {
+template <bool CX>
+__device__ __forceinline__ bool produce(const Args& a, const KArgsT<CX>& ka, const MapsT<CX>& mp, unsigned char* smem,
+                                       uint64_t* bars, int item, int s, int g, const int* recs, bool wait) {
   const int lane = threadIdx.x & 31;
-  const Item it = decode(a, item);
-  const int blk = a.blk0 + it.bi;
+  const Item it = decode<CX>(a, ka, item);
+  const int blk = it.blk;
+  const int c0 = CX ? 8 * it.h : 0;   // first float of the node's half (complex: 16 floats a node)
   const int slot = g % NBUF;
   unsigned char* st = smem + (size_t)slot * STAGE_B;
   uint64_t* full = bars + slot;
@@ -432,15 +577,15 @@ __device__ __forceinline__ bool produce(const Args& a, const Maps& mp, unsigned 
     // halo frame: padded columns tx0 .. tx0+27 (nodes x = tx0-6 .. tx0+21), one box per y run
     if (lane < TMA_MAXSEG) {
       const int* sg = a.yseg[it.ty0 / TT][lane];
-      if (sg[2] >= 0) tma4(st + (size_t)sg[1] * FR * NB * 4, &mp.frame[sg[2]], 0, it.tx0, sg[0], zc, full);
+      if (sg[2] >= 0) tma4(st + (size_t)sg[1] * FR * NB * 4, &mp.frame[sg[2]], c0, it.tx0, sg[0], zc, full);
     }
-    if (lane == 29) tma3(st + OFF_V, &mp.veff, it.tx0, it.ty0, zw, full);
+    if (lane == 29) tma3(st + OFF_V, &mp.veff[CX ? it.kk : 0], it.tx0, it.ty0, zw, full);
     if (lane == 30) bulk_g2s_hint(st + OFF_REC, a.stream + 16 * (size_t)o0, rbytes, full, policy_evict_last());
   } else if (lane == 0) {
-    tma4(st, &mp.tile_in, 0, it.tx0 + R, it.ty0, zc, full);
+    tma4(st, &mp.tile_in, c0, it.tx0 + R, it.ty0, zc, full);
   }
   if (yp && lane == 31)
-    tma4_hint(st + OFF_YP, &mp.tile_prev, 0, it.tx0 + R, it.ty0, blk * a.n3 + (p - R), full, policy_evict_first());
+    tma4_hint(st + OFF_YP, &mp.tile_prev, c0, it.tx0 + R, it.ty0, blk * a.n3 + (p - R), full, policy_evict_first());
   return ok;
 }
 
@@ -455,26 +600,50 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Asynchronous per-item staging by all threads: the record offsets (entries 0 .. nz) and
 // the projector indices of an item (tile column), or its coefficients gc (projector
 // indices read from cpj, zero for absent projectors).
-__device__ __forceinline__ void stage_recs(const Args& a, int item, int* dst) {
+template <bool CX>
+__device__ __forceinline__ void stage_recs(const Args& a, const KArgsT<CX>& ka, int item, int* dst) {
   const int t = threadIdx.x;
   if (item < a.nitems && t <= ZLMAX) {
-    const Item it = decode(a, item);
+    const Item it = decode<CX>(a, ka, item);
     if (t <= it.nz) cp_async4(dst + t, a.rec + (size_t)it.tile * a.n3 + it.zs + t, true);
   }
 }
-__device__ __forceinline__ void stage_cproj(const Args& a, int item, int* dst) {
+template <bool CX>
+__device__ __forceinline__ void stage_cproj(const Args& a, const KArgsT<CX>& ka, int item, int* dst) {
   if (item >= a.nitems) return;
-  const Item it = decode(a, item);
+  const Item it = decode<CX>(a, ka, item);
   for (int i = threadIdx.x; i < MAXG * 4; i += NTHR) cp_async4(dst + i, a.cproj + (size_t)it.tile * MAXG * 4 + i, true);
 }
-__device__ __forceinline__ void stage_gc(const Args& a, int item, const int* cpj, float* dst) {
+// Complex: B column n = lane >> 2 of a slot is component n & 1 (re, im) of orbital
+// 4 h + (n >> 1); the Bloch factor of the slot is applied after the copies landed
+// (phase_gc).
+template <bool CX>
+__device__ __forceinline__ void stage_gc(const Args& a, const KArgsT<CX>& ka, int item, const int* cpj, float* dst) {
   if (item >= a.nitems) return;
-  const Item it = decode(a, item);
-  const int blk = a.blk0 + it.bi;
+  const Item it = decode<CX>(a, ka, item);
   for (int idx = threadIdx.x; idx < MAXG * 32; idx += NTHR) {
-    const int pp = cpj[(idx >> 5) * 4 + (idx & 3)];
-    const float* src = a.gc + ((size_t)(pp < 0 ? 0 : pp) * a.nblk_total + blk) * NB + ((idx & 31) >> 2);
+    const int l = idx & 31;
+    const int pp = cpj[(idx >> 5) * 4 + (l & 3)];
+    const size_t row = ((size_t)(pp < 0 ? 0 : pp) * a.nblk_total + it.blk) * NB;
+    const float* src = CX ? a.gc + (row + 4 * it.h + (l >> 3)) * 2 + ((l >> 2) & 1) : a.gc + row + (l >> 2);
     cp_async4(dst + idx, src, pp >= 0);
+  }
+}
+
+// The Bloch factors of an item's slots, folded into its staged coefficients: slot g in
+// periodic image t gets exp(-i k.(t L)) = prod_s ph_s^(-t_s) (the factor of the image's
+// projector values at the grid nodes, Eq. NonlocalPS:FD); (re, im) of (slot, orbital c,
+// projector k) sit at lanes 8 c + k and 8 c + 4 + k.
+__device__ __forceinline__ void phase_gc(const Args& a, const KArgs& ka, const Item& it, float* gcs) {
+  const float2 px = ka.phx[it.kk], py = ka.phy[it.kk], pz = ka.phz[it.kk];
+  for (int q = threadIdx.x; q < MAXG * 16; q += NTHR) {
+    const int g = q >> 4, c = (q >> 2) & 3, k = q & 3;
+    const int code = __ldg(a.cimg + (size_t)it.tile * MAXG + g);
+    const float2 ph = cmul(cmul(face(px, 1 - (code & 3)), face(py, 1 - ((code >> 2) & 3))), face(pz, 1 - (code >> 4)));
+    float* v = gcs + g * 32 + 8 * c + k;
+    const float re = v[0], im = v[4];
+    v[0] = ph.x * re - ph.y * im;
+    v[4] = ph.x * im + ph.y * re;
   }
 }
 
@@ -502,8 +671,16 @@ __device__ __forceinline__ void zstep(float2 (&acc)[13][2], const float2* cz2, f
   e1 = acc[(I + 1) % 13][1];
 }
 
+// CX: complex64 units (16 floats a node), taken as half-units of four complex orbitals
+// (one float2 each), so that the frames, stencil and projector products are those of the
+// FP32 pass; the Bloch factors enter at the periodic faces (Section 3.1): x in the ghost
+// nodes the epilogue writes, y on the frame rows that crossed a face, z on the halo planes
+// that crossed one, and in the projector slots' coefficients (phase_gc).
+template <bool CX>
 __global__ void __launch_bounds__(NTHR, 1)
-k_pass_tma(const __grid_constant__ Maps mp, const __grid_constant__ Args a) {
+k_pass_tma(const __grid_constant__ MapsT<CX> mp, const __grid_constant__ Args a,
+           const __grid_constant__ KArgsT<CX> ka) {
+  constexpr int NF = CX ? 2 * NB : NB;   // floats per node of the block buffers
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OFF_BAR);
   const int tid = threadIdx.x;
@@ -520,30 +697,30 @@ k_pass_tma(const __grid_constant__ Maps mp, const __grid_constant__ Args a) {
   float* gcsb = reinterpret_cast<float*>(smem + OFF_GCS);
   // tables of the first two items (record offsets, projector indices), then the
   // coefficients of the first item; the zero slot MAXG of both coefficient buffers
-  stage_recs(a, blockIdx.x, recs);
-  stage_recs(a, blockIdx.x + gridDim.x, recs + RECN);
-  stage_cproj(a, blockIdx.x, cpj);
-  stage_cproj(a, blockIdx.x + gridDim.x, cpj + MAXG * 4);
+  stage_recs<CX>(a, ka, blockIdx.x, recs);
+  stage_recs<CX>(a, ka, blockIdx.x + gridDim.x, recs + RECN);
+  stage_cproj<CX>(a, ka, blockIdx.x, cpj);
+  stage_cproj<CX>(a, ka, blockIdx.x + gridDim.x, cpj + MAXG * 4);
   if (tid < 64) gcsb[(tid >> 5) * (GCS_B / 4) + MAXG * 32 + (tid & 31)] = 0.f;
   cp_async_commit();
   cp_async_wait_all();
   __syncthreads();
-  stage_gc(a, blockIdx.x, cpj, gcsb);
+  stage_gc<CX>(a, ka, blockIdx.x, cpj, gcsb);
   cp_async_commit();
   __syncthreads();
   const bool producer = warp == NCW - 1;
   bool ok = true;
   // producer cursor: the step DIST ahead of the consumers (item, step, steps of the item, local item index)
   int pitem = blockIdx.x, ps = 0, pli = 0;
-  int pS = pitem < a.nitems ? decode(a, pitem).nz + 2 * R : 0;
+  int pS = pitem < a.nitems ? decode<CX>(a, ka, pitem).nz + 2 * R : 0;
   auto produce_next = [&](int gp) {
     if (pitem >= a.nitems) return;
-    ok &= produce(a, mp, smem, bars, pitem, ps, gp, recs + (pli % 3) * RECN, ok);
+    ok &= produce<CX>(a, ka, mp, smem, bars, pitem, ps, gp, recs + (pli % 3) * RECN, ok);
     if (++ps == pS) {
       ps = 0;
       ++pli;
       pitem += gridDim.x;
-      pS = pitem < a.nitems ? decode(a, pitem).nz + 2 * R : 0;
+      pS = pitem < a.nitems ? decode<CX>(a, ka, pitem).nz + 2 * R : 0;
     }
   };
   if (producer)
@@ -555,7 +732,7 @@ k_pass_tma(const __grid_constant__ Maps mp, const __grid_constant__ Args a) {
   const int fo = ((yl + R) * FR + xl + R) * NB + 2 * op;   // frame offset of node 0 (floats)
   const int to = (yl * TT + xl) * NB + 2 * op;             // tile offset of node 0
   const int vo = yl * TT + xl;
-  const size_t plane = (size_t)a.n1p * a.n2 * NB;   // one z-plane of a padded block
+  const size_t plane = (size_t)a.n1p * a.n2 * NF;   // one z-plane of a padded block
   int g = 0, li = 0;
   int cslot = 0;          // g mod NBUF
   uint32_t cphase = 0;    // parity of (g / NBUF)
@@ -564,8 +741,8 @@ k_pass_tma(const __grid_constant__ Maps mp, const __grid_constant__ Args a) {
   for (int i = 0; i < 13; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
 
   for (int item = blockIdx.x; item < a.nitems; item += gridDim.x, ++li) {
-    const Item it = decode(a, item);
-    const int blk = a.blk0 + it.bi;
+    const Item it = decode<CX>(a, ka, item);
+    const int blk = it.blk;
     // The item's coefficients (gc of its boxes, B-fragment order: lane = 4 orbital +
     // projector; slot MAXG is zero) were copied at the previous item's start.  Wait for
     // this thread's copies, then let every warp finish the previous item; then start the
@@ -573,16 +750,39 @@ k_pass_tma(const __grid_constant__ Maps mp, const __grid_constant__ Args a) {
     // the buffers the previous item has left.
     cp_async_wait_all();
     __syncthreads();
-    stage_gc(a, item + gridDim.x, cpj + ((li + 1) & 1) * MAXG * 4, gcsb + ((li + 1) & 1) * (GCS_B / 4));
-    stage_cproj(a, item + 2 * gridDim.x, cpj + (li & 1) * MAXG * 4);
-    stage_recs(a, item + 2 * gridDim.x, recs + ((li + 2) % 3) * RECN);
+    if constexpr (CX) {
+      phase_gc(a, ka, it, gcsb + (li & 1) * (GCS_B / 4));
+      __syncthreads();
+    }
+    stage_gc<CX>(a, ka, item + gridDim.x, cpj + ((li + 1) & 1) * MAXG * 4, gcsb + ((li + 1) & 1) * (GCS_B / 4));
+    stage_cproj<CX>(a, ka, item + 2 * gridDim.x, cpj + (li & 1) * MAXG * 4);
+    stage_recs<CX>(a, ka, item + 2 * gridDim.x, recs + ((li + 2) % 3) * RECN);
     cp_async_commit();
     const float* gcs = gcsb + (li & 1) * (GCS_B / 4);
     const int gx = it.tx0 + xl, gy = it.ty0 + yl;
     const bool v0 = gx < a.n1 && gy < a.n2, v1 = gx < a.n1 && gy + 1 < a.n2;
-    float* outp = a.yout + ((size_t)blk * a.ndp + (size_t)gy * a.n1p + gx + R) * NB + 2 * op;
+    float* outp = a.yout + ((size_t)blk * a.ndp + (size_t)gy * a.n1p + gx + R) * NF + (CX ? 8 * it.h : 0) + 2 * op;
     // ghost copies: nodes x < R repeat at x' = x + n1 + R, nodes x >= n1 - R at x' = x - n1 + R
-    const long long gofs = gx < R ? (long long)a.n1 * NB : (gx >= a.n1 - R ? -(long long)a.n1 * NB : 0);
+    const long long gofs = gx < R ? (long long)a.n1 * NF : (gx >= a.n1 - R ? -(long long)a.n1 * NF : 0);
+    // recurrence coefficients; complex: per k, with the Bloch factors of the faces
+    float2 alpha2, beta2, gph = make_float2(1.f, 0.f), phy = make_float2(1.f, 0.f);
+    float c0s;
+    int nlo = 0, rhi = 2 * R + 2;   // column entries r < nlo lie below y = 0, r >= rhi at y >= n2
+    if constexpr (CX) {
+      alpha2 = ka.alpha2[it.kk];
+      beta2 = ka.beta2[it.kk];
+      c0s = ka.c0s[it.kk];
+      const float2 px = ka.phx[it.kk];
+      gph = gx < R ? px : conj2(px);   // the ghost of x < R lies at x + n1: ph_x; of x >= n1 - R at x - n1
+      phy = ka.phy[it.kk];
+      const int yb = it.ty0 + yl - R;   // y of column entry 0
+      nlo = max(0, -yb);
+      rhi = min(2 * R + 2, a.n2 - yb);
+    } else {
+      alpha2 = a.alpha2;
+      beta2 = a.beta2;
+      c0s = a.c0s;
+    }
     const int S = it.nz + 2 * R;
     int ring = 0;   // s mod 13: the accumulator of output z'+d sits in slot (ring + 7 + d) mod 13
     for (int s = 0; s < S; ++s) {
@@ -599,6 +799,17 @@ k_pass_tma(const __grid_constant__ Maps mp, const __grid_constant__ Args a) {
         float2 col[2 * R + 2];
 #pragma unroll
         for (int r = 0; r < 2 * R + 2; ++r) col[r] = lds2(F + fo + (r - R) * FR * NB);
+        if constexpr (CX) {
+          // rows of the frame that crossed a y face: the image's value times ph_y^t
+          if (nlo > 0 || rhi < 2 * R + 2) {
+#pragma unroll
+            for (int r = 0; r < 2 * R + 2; ++r) {
+              if (r == R || r == R + 1) continue;   // the thread's own nodes never cross
+              if (r < nlo) col[r] = cmul(col[r], conj2(phy));
+              else if (r >= rhi) col[r] = cmul(col[r], phy);
+            }
+          }
+        }
         f0 = col[R];
         f1 = col[R + 1];
         float2 ys0 = __fmul2_rn(a.cy2[1], __fadd2_rn(col[R + 1], col[R - 1]));
@@ -626,8 +837,8 @@ k_pass_tma(const __grid_constant__ Maps mp, const __grid_constant__ Args a) {
           for (int q = 2; q <= R; ++q) xs1 = __ffma2_rn(a.cx2[q], __fadd2_rn(w[R + q], w[R - q]), xs1);
         }
         const float* Vs = reinterpret_cast<const float*>(st + OFF_V);
-        const float2 cen0 = __fmul2_rn(f2(a.c0s + Vs[vo]), f0);
-        const float2 cen1 = __fmul2_rn(f2(a.c0s + Vs[vo + TT]), f1);
+        const float2 cen0 = __fmul2_rn(f2(c0s + Vs[vo]), f0);
+        const float2 cen1 = __fmul2_rn(f2(c0s + Vs[vo + TT]), f1);
         // projector term on the tensor cores (3xTF32); the three products of a round go to
         // three accumulators, so that consecutive mma.sync do not wait on each other
         float nl[4] = {0.f, 0.f, 0.f, 0.f}, nla[4] = {0.f, 0.f, 0.f, 0.f}, nlb[4] = {0.f, 0.f, 0.f, 0.f};
@@ -659,6 +870,15 @@ k_pass_tma(const __grid_constant__ Maps mp, const __grid_constant__ Args a) {
       } else {
         f0 = lds2(F + to);
         f1 = lds2(F + to + TT * NB);
+        if constexpr (CX) {
+          // a halo plane that crossed a z face: ph_z^t
+          const int p = it.zs - R + s;
+          if (p < 0 || p >= a.n3) {
+            const float2 pz = p < 0 ? conj2(ka.phz[it.kk]) : ka.phz[it.kk];
+            f0 = cmul(f0, pz);
+            f1 = cmul(f1, pz);
+          }
+        }
       }
       // z part and the output z' itself, in the ring position's specialisation (only
       // this part depends on the ring position, so the step body exists once)
@@ -680,19 +900,23 @@ k_pass_tma(const __grid_constant__ Maps mp, const __grid_constant__ Args a) {
       }
       // output z'-6 is complete: recurrence epilogue
       if (s >= 2 * R) {
-        float2 r0 = __fmul2_rn(a.alpha2, e0);
-        float2 r1 = __fmul2_rn(a.alpha2, e1);
+        float2 r0 = __fmul2_rn(alpha2, e0);
+        float2 r1 = __fmul2_rn(alpha2, e1);
         if (a.yprev != nullptr) {
           const float* P = reinterpret_cast<const float*>(st + OFF_YP);
-          r0 = __ffma2_rn(a.beta2, lds2(P + to), r0);
-          r1 = __ffma2_rn(a.beta2, lds2(P + to + TT * NB), r1);
+          r0 = __ffma2_rn(beta2, lds2(P + to), r0);
+          r1 = __ffma2_rn(beta2, lds2(P + to + TT * NB), r1);
         }
         float* o = outp + (size_t)(it.zs + s - 2 * R) * plane;
         if (v0) *reinterpret_cast<float2*>(o) = r0;
-        if (v1) *reinterpret_cast<float2*>(o + (size_t)a.n1p * NB) = r1;
+        if (v1) *reinterpret_cast<float2*>(o + (size_t)a.n1p * NF) = r1;
         if (gofs != 0) {
+          if constexpr (CX) {
+            r0 = cmul(r0, gph);
+            r1 = cmul(r1, gph);
+          }
           if (v0) *reinterpret_cast<float2*>(o + gofs) = r0;
-          if (v1) *reinterpret_cast<float2*>(o + (size_t)a.n1p * NB + gofs) = r1;
+          if (v1) *reinterpret_cast<float2*>(o + (size_t)a.n1p * NF + gofs) = r1;
         }
       }
       __syncwarp();
@@ -731,16 +955,105 @@ long long padded_nd(const sparc_ham* H) { return (long long)(H->gd.n1 + 2 * R) *
 
 namespace tma {
 
-// Tensor map of an x-padded block buffer: dims (8 orbitals, n1 + 2R, n2, n3 * nblk),
-// box (8, bx, by, 1).
-static bool map_blocks(CUtensorMap* m, const float* base, int n1p, int n2, int n3, int nblk, int bx, int by) {
-  const cuuint64_t dims[4] = {(cuuint64_t)NB, (cuuint64_t)n1p, (cuuint64_t)n2, (cuuint64_t)n3 * nblk};
-  const cuuint64_t strides[3] = {(cuuint64_t)NB * 4, (cuuint64_t)n1p * NB * 4, (cuuint64_t)n1p * n2 * NB * 4};
+// Tensor map of an x-padded block buffer of nf floats a node (8: FP32 block; 16:
+// complex64 unit): dims (nf, n1 + 2R, n2, n3 * nblk), box (8, bx, by, 1).
+static bool map_blocks(CUtensorMap* m, const float* base, int nf, int n1p, int n2, int n3, long long nblk, int bx,
+                       int by) {
+  const cuuint64_t dims[4] = {(cuuint64_t)nf, (cuuint64_t)n1p, (cuuint64_t)n2, (cuuint64_t)n3 * nblk};
+  const cuuint64_t strides[3] = {(cuuint64_t)nf * 4, (cuuint64_t)n1p * nf * 4, (cuuint64_t)n1p * n2 * nf * 4};
   const cuuint32_t box[4] = {(cuuint32_t)NB, (cuuint32_t)bx, (cuuint32_t)by, 1};
   const cuuint32_t es[4] = {1, 1, 1, 1};
   return encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void*)base, dims, strides, box, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static bool map_veff(CUtensorMap* m, const float* veff, int n1, int n2, int n3) {
+  const cuuint64_t dims[3] = {(cuuint64_t)n1, (cuuint64_t)n2, (cuuint64_t)n3};
+  const cuuint64_t strides[2] = {(cuuint64_t)n1 * 4, (cuuint64_t)n1 * n2 * 4};
+  const cuuint32_t box[3] = {TT, TT, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)veff, dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// One launch over nunits work units (FP32 blocks blk0 .. blk0 + nunits - 1, or the complex
+// half-units of ks); the per-launch fields of Args and the maps of the geometry of H.
+template <bool CX>
+static cudaError_t launch_tma(const sparc_ham* H, const float* Yin, const float* Yprev, float* Yout, const float* gc,
+                              long long nblk_total, int blk0, int nunits, double alpha, double shift, double beta,
+                              const KArgsT<CX>& ka, const KSlots* ks, cudaStream_t st) {
+  const Tables* Tb = (const Tables*)H->fast;
+  const TmaTables& M = CX ? Tb->tmac : Tb->tma;
+  if (!M.ok || M.cplx != CX || encoder() == nullptr) return cudaErrorNotSupported;
+  constexpr int NF = CX ? 2 * NB : NB;
+  const int n1 = H->gd.n1, n2 = H->gd.n2, n3 = H->gd.n3, n1p = n1 + 2 * R;
+  MapsT<CX> mp;
+  for (int i = 0; i < M.nmaps; ++i)
+    if (!map_blocks(&mp.frame[i], Yin, NF, n1p, n2, n3, nblk_total, FR, M.map_h[i])) return cudaErrorInvalidValue;
+  for (int i = M.nmaps; i < TMA_NMAPS; ++i) mp.frame[i] = mp.frame[0];
+  if (!map_blocks(&mp.tile_in, Yin, NF, n1p, n2, n3, nblk_total, TT, TT) ||
+      !map_blocks(&mp.tile_prev, Yprev ? Yprev : Yin, NF, n1p, n2, n3, nblk_total, TT, TT))
+    return cudaErrorInvalidValue;
+  if constexpr (CX) {
+    for (int kk = 0; kk < KMAX; ++kk)
+      if (kk < ks->nk ? !map_veff(&mp.veff[kk], ks->s[kk].veff, n1, n2, n3) : false) return cudaErrorInvalidValue;
+    for (int kk = ks->nk; kk < KMAX; ++kk) mp.veff[kk] = mp.veff[0];
+  } else {
+    if (!map_veff(&mp.veff[0], H->d_veff32, n1, n2, n3)) return cudaErrorInvalidValue;
+  }
+  Args a;
+  a.n1 = n1; a.n2 = n2; a.n3 = n3;
+  a.n1p = n1p;
+  a.tiles_x = M.tiles_x;
+  a.ntiles = M.tiles_x * M.tiles_y;
+  // z-chunks per tile column: whole columns (twelve boundary planes per column) unless
+  // the launch would then have fewer than two items per multiprocessor; chunks of at
+  // least 16 planes and at most ZLMAX
+  const int nsm = std::max(H->ctx->nsm, 1);
+  int nchunk = ceil_div(n3, ZLMAX);
+  while ((long long)a.ntiles * nchunk * nunits < 2 * nsm && n3 / (nchunk + 1) >= 16) ++nchunk;
+  a.nchunk = nchunk;
+  a.zl = ceil_div(n3, nchunk);
+  a.blk0 = blk0;
+  a.nblk_total = (int)nblk_total;
+  const long long nitems = (long long)a.ntiles * nchunk * nunits;
+  if (nitems >= INT32_MAX || nblk_total >= INT32_MAX) return cudaErrorInvalidValue;
+  a.nitems = (int)nitems;
+  a.ndp = padded_nd(H);
+  std::memcpy(a.yseg, M.yseg, sizeof(a.yseg));
+  for (int p = 0; p <= R; ++p) {
+    const float cx = (float)H->gd.coef[0][p], cy = (float)H->gd.coef[1][p], cz = (float)H->gd.coef[2][p];
+    a.cx2[p] = make_float2(cx, cx);
+    a.cy2[p] = make_float2(cy, cy);
+    a.cz2[p] = make_float2(cz, cz);
+  }
+  const double csum = 2.0 * (H->gd.coef[0][0] + H->gd.coef[1][0] + H->gd.coef[2][0]);
+  a.c0s = (float)csum - (float)shift;
+  a.alpha2 = make_float2((float)alpha, (float)alpha);
+  a.beta2 = make_float2((float)beta, (float)beta);
+  a.yin = Yin;
+  a.yprev = Yprev;
+  a.yout = Yout;
+  a.gc = gc;
+  a.cproj = M.d_cproj;
+  a.cng = M.d_cng;
+  a.rec = M.d_rec;
+  a.stream = (const unsigned char*)M.d_stream;
+  a.cimg = M.d_cimg;
+  a.status = H->ctx->d_status;
+  a.wait_limit = H->ctx->inject_wait_limit > 0 ? H->ctx->inject_wait_limit : (1LL << 32);
+  a.stall = H->ctx->inject_stall;
+  H->ctx->inject_stall = -1;   // one launch
+  cudaError_t e = cudaFuncSetAttribute(k_pass_tma<CX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_B);
+  if (e != cudaSuccess) return e;
+  const int grid = (int)std::min<long long>(a.nitems, nsm);
+  cudaEvent_t t0 = timing_begin(H->ctx, st);
+  k_pass_tma<CX><<<grid, NTHR, SMEM_B, st>>>(mp, a, ka);
+  ++H->ctx->launches;
+  timing_end(H->ctx, TK_FPASS, t0, st);
+  return cudaGetLastError();
 }
 
 }  // namespace tma
@@ -755,78 +1068,45 @@ cudaError_t launch_from_blocks_px(const sparc_ham* H, const float* B, int nblk, 
   return launch_from_blocks_rows<float>(B, H->gd.nd, H->gd.n1, R, nblk, X, ld, ns, st);
 }
 
+cudaError_t launch_to_blocks_px(const sparc_ham* H, const cf32* X, long long ld, int ns, cf32* B, int nblk,
+                                cudaStream_t st) {
+  const cf32 ph{(float)H->gd.ph_re[0], (float)H->gd.ph_im[0]};
+  return launch_to_blocks_rows<cf32>(X, ld, ns, B, H->gd.nd, H->gd.n1, R, nblk, st, ph);
+}
+
+cudaError_t launch_from_blocks_px(const sparc_ham* H, const cf32* B, int nblk, cf32* X, long long ld, int ns,
+                                  cudaStream_t st) {
+  return launch_from_blocks_rows<cf32>(B, H->gd.nd, H->gd.n1, R, nblk, X, ld, ns, st);
+}
+
 cudaError_t launch_pass_tma(const sparc_ham* H, const float* Yin, const float* Yprev, float* Yout, const float* gc,
                             int nblk_total, int blk0, int nb, double alpha, double shift, double beta,
                             cudaStream_t st) {
+  return tma::launch_tma<false>(H, Yin, Yprev, Yout, gc, nblk_total, blk0, nb, alpha, shift, beta,
+                                tma::KArgsNone{0}, nullptr, st);
+}
+
+cudaError_t launch_pass_tma_k(const sparc_ham* H0, const cf32* Yin, const cf32* Yprev, cf32* Yout, const cf32* gc,
+                              long long nunit_total, const KSlots& ks, cudaStream_t st) {
   using namespace tma;
-  const Tables* Tb = (const Tables*)H->fast;
-  const TmaTables& M = Tb->tma;
-  if (!M.ok || encoder() == nullptr) return cudaErrorNotSupported;
-  const int n1 = H->gd.n1, n2 = H->gd.n2, n3 = H->gd.n3, n1p = n1 + 2 * R;
-  Maps mp;
-  for (int i = 0; i < M.nmaps; ++i)
-    if (!map_blocks(&mp.frame[i], Yin, n1p, n2, n3, nblk_total, FR, M.map_h[i])) return cudaErrorInvalidValue;
-  for (int i = M.nmaps; i < TMA_NMAPS; ++i) mp.frame[i] = mp.frame[0];
-  if (!map_blocks(&mp.tile_in, Yin, n1p, n2, n3, nblk_total, TT, TT) ||
-      !map_blocks(&mp.tile_prev, Yprev ? Yprev : Yin, n1p, n2, n3, nblk_total, TT, TT))
-    return cudaErrorInvalidValue;
-  {
-    const cuuint64_t dims[3] = {(cuuint64_t)n1, (cuuint64_t)n2, (cuuint64_t)n3};
-    const cuuint64_t strides[2] = {(cuuint64_t)n1 * 4, (cuuint64_t)n1 * n2 * 4};
-    const cuuint32_t box[3] = {TT, TT, 1};
-    const cuuint32_t es[3] = {1, 1, 1};
-    if (encoder()(&mp.veff, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)H->d_veff32, dims, strides, box, es,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return cudaErrorInvalidValue;
+  if (ks.nk < 1 || ks.nk > KMAX || ks.nbk < 1) return cudaErrorInvalidValue;
+  KArgs ka;
+  std::memset(&ka, 0, sizeof(ka));
+  ka.nk = ks.nk;
+  ka.nbk = ks.nbk;
+  const double csum = 2.0 * (H0->gd.coef[0][0] + H0->gd.coef[1][0] + H0->gd.coef[2][0]);
+  for (int kk = 0; kk < ks.nk; ++kk) {
+    const KSlot& S = ks.s[kk];
+    ka.ubase[kk] = S.ubase;
+    ka.alpha2[kk] = make_float2(S.alpha, S.alpha);
+    ka.beta2[kk] = make_float2(S.beta, S.beta);
+    ka.c0s[kk] = (float)csum - S.shift;
+    ka.phx[kk] = make_float2(S.phx_r, S.phx_i);
+    ka.phy[kk] = make_float2(S.phy_r, S.phy_i);
+    ka.phz[kk] = make_float2(S.phz_r, S.phz_i);
   }
-  Args a;
-  a.n1 = n1; a.n2 = n2; a.n3 = n3;
-  a.n1p = n1p;
-  a.tiles_x = M.tiles_x;
-  a.ntiles = M.tiles_x * M.tiles_y;
-  // z-chunks per tile column: whole columns (twelve boundary planes per column) unless
-  // the launch would then have fewer than two items per multiprocessor; chunks of at
-  // least 16 planes and at most ZLMAX
-  const int nsm = std::max(H->ctx->nsm, 1);
-  int nchunk = ceil_div(n3, ZLMAX);
-  while (a.ntiles * nchunk * nb < 2 * nsm && n3 / (nchunk + 1) >= 16) ++nchunk;
-  a.nchunk = nchunk;
-  a.zl = ceil_div(n3, nchunk);
-  a.blk0 = blk0;
-  a.nblk_total = nblk_total;
-  a.nitems = a.ntiles * nchunk * nb;
-  a.ndp = padded_nd(H);
-  std::memcpy(a.yseg, M.yseg, sizeof(a.yseg));
-  for (int p = 0; p <= R; ++p) {
-    const float cx = (float)H->gd.coef[0][p], cy = (float)H->gd.coef[1][p], cz = (float)H->gd.coef[2][p];
-    a.cx2[p] = make_float2(cx, cx);
-    a.cy2[p] = make_float2(cy, cy);
-    a.cz2[p] = make_float2(cz, cz);
-  }
-  a.c0s = (float)(2.0 * (H->gd.coef[0][0] + H->gd.coef[1][0] + H->gd.coef[2][0])) - (float)shift;
-  a.alpha2 = make_float2((float)alpha, (float)alpha);
-  a.beta2 = make_float2((float)beta, (float)beta);
-  a.yin = Yin;
-  a.yprev = Yprev;
-  a.yout = Yout;
-  a.gc = gc;
-  a.cproj = M.d_cproj;
-  a.cng = M.d_cng;
-  a.rec = M.d_rec;
-  a.stream = (const unsigned char*)M.d_stream;
-  a.status = H->ctx->d_status;
-  a.wait_limit = H->ctx->inject_wait_limit > 0 ? H->ctx->inject_wait_limit : (1LL << 32);
-  a.stall = H->ctx->inject_stall;
-  H->ctx->inject_stall = -1;   // one launch
-  cudaError_t e = cudaFuncSetAttribute(k_pass_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_B);
-  if (e != cudaSuccess) return e;
-  const int grid = std::min(a.nitems, nsm);
-  cudaEvent_t t0 = timing_begin(H->ctx, st);
-  k_pass_tma<<<grid, NTHR, SMEM_B, st>>>(mp, a);
-  ++H->ctx->launches;
-  timing_end(H->ctx, TK_FPASS, t0, st);
-  return cudaGetLastError();
+  return launch_tma<true>(H0, (const float*)Yin, (const float*)Yprev, (float*)Yout, (const float*)gc, nunit_total,
+                          0, 2 * ks.nk * ks.nbk, 0.0, 0.0, 0.0, ka, &ks, st);
 }
 
 }  // namespace fast

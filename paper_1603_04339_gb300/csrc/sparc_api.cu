@@ -325,6 +325,41 @@ sparc_status filter_block_fast(sparc_ham* H, int m, double a, double b, double a
       ++H->ctx->launches;
       return SPARC_OK;
     }
+  } else if constexpr (std::is_same<T, cf32>::value) {
+    if (fast::tma_usable_c(H)) {
+      // the complex TMA pass on x-padded block buffers (ghost nodes carry the Bloch factor)
+      SPARC_CUDA(H->ctx, fast::launch_to_blocks_px(H, X, ld, ns, B0, nblk, st));
+      ++H->ctx->launches;
+      T* res = B1;
+      for (int g0 = 0; g0 < nblk; g0 += G) {
+        fast::KSlots ks;
+        ks.nk = 1;
+        ks.nbk = std::min(G, nblk - g0);
+        fast::kslot(H, ks.s[0]);
+        ks.s[0].ubase = g0;
+        ks.s[0].shift = (float)c;
+        T* prev = B0;
+        T* cur = B1;
+        double sigma = sigma1;
+        ks.s[0].alpha = (float)(sigma1 / e);
+        ks.s[0].beta = 0.f;
+        SPARC_CUDA(H->ctx, fast::launch_gather<T>(H, prev, nblk, g0, ks.nbk, gc, scratch, st, true));
+        SPARC_CUDA(H->ctx, fast::launch_pass_tma_k(H, prev, nullptr, cur, gc, nblk, ks, st));
+        for (int j = 1; j < m; ++j) {
+          const double sigma_new = 1.0 / (2.0 / sigma1 - sigma);
+          ks.s[0].alpha = (float)(2.0 * sigma_new / e);
+          ks.s[0].beta = (float)(-sigma * sigma_new);
+          SPARC_CUDA(H->ctx, fast::launch_gather<T>(H, cur, nblk, g0, ks.nbk, gc, scratch, st, true));
+          SPARC_CUDA(H->ctx, fast::launch_pass_tma_k(H, cur, prev, prev, gc, nblk, ks, st));
+          std::swap(cur, prev);
+          sigma = sigma_new;
+        }
+        res = cur;
+      }
+      SPARC_CUDA(H->ctx, fast::launch_from_blocks_px(H, res, nblk, Y, ld, ns, st));
+      ++H->ctx->launches;
+      return SPARC_OK;
+    }
   }
   SPARC_CUDA(H->ctx, launch_to_blocks<T>(X, ld, ns, B0, H->gd.nd, nblk, st));
   ++H->ctx->launches;
@@ -360,8 +395,9 @@ size_t apply_scratch_bytes(sparc_ham* H, sparc_dtype dt, int ns) {
 size_t filter_ws(sparc_ham* H, sparc_dtype dt, int ns, char* base, BlockWs* w) {
   const size_t es = dtype_size(dt);
   const int nblk = ceil_div(ns, NB);
-  // FP32 block buffers hold the x-padded layout of the TMA pass where it applies
-  const long long ndb = (dt == SPARC_F32 && fast::tma_usable(H)) ? fast::padded_nd(H) : H->gd.nd;
+  // FP32 and complex64 block buffers hold the x-padded layout of the TMA pass where it applies
+  const bool tma = (dt == SPARC_F32 && fast::tma_usable(H)) || (dt == SPARC_C64 && fast::tma_usable_c(H));
+  const long long ndb = tma ? fast::padded_nd(H) : H->gd.nd;
   const size_t bb = align256((size_t)nblk * ndb * NB * es);
   const size_t gb = align256((size_t)std::max(1, H->nproj) * nblk * NB * es);
   size_t extra = 0;
@@ -416,13 +452,15 @@ static KGroup kbatch_grouping(int nk, int nblk, int items_per_blk, int nsm, int 
 }
 
 // The launches of the k-point batch filter below, issued on st.
+// tma: every H passes fast::tma_batch_compatible with H0 and the block buffers hold the
+// x-padded layout of the TMA pass.
 static sparc_status kbatch_launches(sparc_ham* const* Hs, int nk, int m, const double* a, const double* b,
                                     const double* a0, const cf32* X, cf32* Y, int ns, long long ld, const KGroup& G,
-                                    size_t bb, size_t gb, cudaStream_t st) {
+                                    size_t bb, size_t gb, bool tma, cudaStream_t st) {
   sparc_ham* H0 = Hs[0];
   sparc_ctx* ctx = H0->ctx;
   const int nblk = ceil_div(ns, NB);
-  const long long nd = H0->gd.nd;
+  const long long nd = tma ? fast::padded_nd(H0) : H0->gd.nd;
   const long long U = (long long)nk * nblk;
   char* p = (char*)ctx->ws;
   cf32* B0 = (cf32*)p;
@@ -431,7 +469,8 @@ static sparc_status kbatch_launches(sparc_ham* const* Hs, int nk, int m, const d
   cf32* scratch = (cf32*)(p + 2 * bb + gb);
   const size_t kx = (size_t)ns * (size_t)ld, kb = (size_t)nblk * nd * NB;
   for (int k = 0; k < nk; ++k) {
-    SPARC_CUDA(ctx, launch_to_blocks<cf32>(X + k * kx, ld, ns, B0 + k * kb, nd, nblk, st));
+    if (tma) SPARC_CUDA(ctx, fast::launch_to_blocks_px(Hs[k], X + k * kx, ld, ns, B0 + k * kb, nblk, st));
+    else SPARC_CUDA(ctx, launch_to_blocks<cf32>(X + k * kx, ld, ns, B0 + k * kb, nd, nblk, st));
     ++ctx->launches;
   }
   std::vector<double> e(nk), c(nk), s1(nk), sg(nk);
@@ -469,19 +508,24 @@ static sparc_status kbatch_launches(sparc_ham* const* Hs, int nk, int m, const d
       };
       cf32* prev = B0;
       cf32* cur = B1;
+      auto pass = [&](const cf32* in, const cf32* pv, cf32* out) {
+        return tma ? fast::launch_pass_tma_k(H0, in, pv, out, gc, U, ks, st)
+                   : fast::launch_pass_k(H0, in, pv, out, gc, U, ks, st);
+      };
       coefs(0);
-      SPARC_CUDA(ctx, fast::launch_gather_k(H0, prev, U, ks, gc, scratch, st));
-      SPARC_CUDA(ctx, fast::launch_pass_k(H0, prev, nullptr, cur, gc, U, ks, st));
+      SPARC_CUDA(ctx, fast::launch_gather_k(H0, prev, U, ks, gc, scratch, st, tma));
+      SPARC_CUDA(ctx, pass(prev, nullptr, cur));
       for (int j = 1; j < m; ++j) {
         coefs(j);
-        SPARC_CUDA(ctx, fast::launch_gather_k(H0, cur, U, ks, gc, scratch, st));
-        SPARC_CUDA(ctx, fast::launch_pass_k(H0, cur, prev, prev, gc, U, ks, st));
+        SPARC_CUDA(ctx, fast::launch_gather_k(H0, cur, U, ks, gc, scratch, st, tma));
+        SPARC_CUDA(ctx, pass(cur, prev, prev));
         std::swap(cur, prev);
       }
       res = cur;
     }
   for (int k = 0; k < nk; ++k) {
-    SPARC_CUDA(ctx, launch_from_blocks<cf32>(res + k * kb, nd, nblk, Y + k * kx, ld, ns, st));
+    if (tma) SPARC_CUDA(ctx, fast::launch_from_blocks_px(Hs[k], res + k * kb, nblk, Y + k * kx, ld, ns, st));
+    else SPARC_CUDA(ctx, launch_from_blocks<cf32>(res + k * kb, nd, nblk, Y + k * kx, ld, ns, st));
     ++ctx->launches;
   }
   SPARC_LAUNCH(ctx, "filter batch");
@@ -506,13 +550,16 @@ static sparc_status filter_kbatch(sparc_ham* const* Hs, int nk, int m, const dou
   int upl = 0;
   const auto tu = ctx->tuned.find(std::make_tuple((int)SPARC_C64, nd, ns, nk));
   if (tu != ctx->tuned.end()) upl = tu->second & (TUNE_SHAPE - 1);
-  const KGroup G = kbatch_grouping(nk, nblk, fast::items_per_block<cf32>(H0), ctx->nsm, upl);
-  const size_t bb = align256((size_t)U * nd * NB * sizeof(cf32));
+  const bool tma = fast::tma_usable_c(H0);
+  const int ipu = tma ? fast::tma_items_per_unit(H0) : fast::items_per_block<cf32>(H0);
+  const KGroup G = kbatch_grouping(nk, nblk, ipu, ctx->nsm, upl);
+  const long long ndb = tma ? fast::padded_nd(H0) : nd;
+  const size_t bb = align256((size_t)U * ndb * NB * sizeof(cf32));
   const size_t gb = align256((size_t)std::max(1, H0->nproj) * U * NB * sizeof(cf32));
   const size_t sb = align256(fast::gather_scratch_bytes(H0, G.nkg * G.nbk, sizeof(cf32)));
   if (!ensure_ws(ctx, 2 * bb + gb + sb)) return fail(ctx, SPARC_ERR_OOM, "workspace allocation failed");
   if (ctx->timing || sync_check())
-    return kbatch_launches(Hs, nk, m, a, b, a0, X, Y, ns, ld, G, bb, gb, st);
+    return kbatch_launches(Hs, nk, m, a, b, a0, X, Y, ns, ld, G, bb, gb, tma, st);
   sparc_ctx::KBatchGraph& K = ctx->kbg;
   const bool same = K.exec && (int)K.H.size() == nk && std::equal(K.H.begin(), K.H.end(), (const void* const*)Hs) &&
                     K.m == m && K.ns == ns && K.ld == ld && K.X == X && K.Y == Y && K.ws == ctx->ws &&
@@ -523,7 +570,7 @@ static sparc_status filter_kbatch(sparc_ham* const* Hs, int nk, int m, const dou
     if (!ctx->cap_stream) SPARC_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
     const long long l0 = ctx->launches;
     SPARC_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-    sparc_status s = kbatch_launches(Hs, nk, m, a, b, a0, X, Y, ns, ld, G, bb, gb, ctx->cap_stream);
+    sparc_status s = kbatch_launches(Hs, nk, m, a, b, a0, X, Y, ns, ld, G, bb, gb, tma, ctx->cap_stream);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
     const long long kernels = ctx->launches - l0;
@@ -935,6 +982,11 @@ sparc_status sparc_cheb_filter_batch(sparc_ham* const* H, int nk, sparc_dtype dt
     sparc_status s = check_block_args(Hk, dtype, x0 + k * kx * es, y0 + k * kx * es, ns, ld);
     if (s != SPARC_OK) return s;
     batch = batch && fast::usable(Hk) && fast::geometry_hash(Hk) == fast::geometry_hash(H[0]);
+    // the TMA pass serves the batch with the tables of H[0]: every H[k] on it, with the
+    // same records (projector values at the nodes), so that each k's result is that of
+    // its own filter
+    if (batch && (fast::tma_usable_c(Hk) || fast::tma_usable_c(H[0])))
+      batch = fast::tma_batch_compatible(H[0], Hk);
   }
   SPARC_CUDA(ctx, cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
@@ -947,6 +999,15 @@ sparc_status sparc_cheb_filter_batch(sparc_ham* const* H, int nk, sparc_dtype dt
     return SPARC_OK;
   }
   return filter_kbatch(H, nk, m, a, b, a0, (const cf32*)X, (cf32*)Y, ns, ld, st);
+}
+
+sparc_status sparc_filter_kernel(const sparc_ham* H, sparc_dtype dtype, int* out) {
+  if (!H || !out || (int)dtype < 0 || (int)dtype > 3) return SPARC_ERR_INVALID_ARG;
+  if (H->gd.cplx && (dtype == SPARC_F64 || dtype == SPARC_F32)) return SPARC_ERR_INVALID_ARG;
+  *out = SPARC_KERNEL_GENERIC;
+  if (dtype == SPARC_F32 && fast::usable(H)) *out = fast::tma_usable(H) ? SPARC_KERNEL_TMA : SPARC_KERNEL_TILED;
+  if (dtype == SPARC_C64 && fast::usable(H)) *out = fast::tma_usable_c(H) ? SPARC_KERNEL_TMA : SPARC_KERNEL_TILED;
+  return SPARC_OK;
 }
 
 sparc_status sparc_set_filter_units(sparc_ctx* ctx, sparc_dtype dtype, int64_t nd, int ns, int nk, int units) {

@@ -31,7 +31,9 @@ EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_sync", "s
            "sparc_set_filter_units", "sparc_filter_graph_create", "sparc_filter_graph_set_bounds",
            "sparc_filter_graph_launch", "sparc_filter_graph_destroy", "sparc_scf_set_density",
            "sparc_mlp_create", "sparc_mlp_params", "sparc_mlp_descriptors", "sparc_mlp_forward", "sparc_mlp_grad",
-           "sparc_mlp_train_step", "sparc_mlp_destroy", "sparc_scf_create_k", "sparc_debug_inject"]
+           "sparc_mlp_train_step", "sparc_mlp_destroy", "sparc_scf_create_k", "sparc_debug_inject",
+           "sparc_filter_kernel"]
+KERNEL_GENERIC, KERNEL_TILED, KERNEL_TMA = 0, 1, 2
 TIMED = {"hpass": 0, "gather": 1, "gram": 2, "eig": 3, "rotation": 4, "jacobi": 5, "fpass": 6}
 
 
@@ -122,6 +124,8 @@ def load(path: str = LIB_PATH):
                                  POINTER(SparcScfInfo), c_void_p]
     L.sparc_scf_read.argtypes = [c_void_p, c_int, c_void_p, c_void_p]
     L.sparc_scf_forces.argtypes = [c_void_p, c_int, c_void_p, c_int, c_int64, POINTER(c_double), c_void_p]
+    L.sparc_filter_kernel.argtypes = [c_void_p, c_int, POINTER(c_int)]
+    L.sparc_filter_kernel.restype = c_int
     L.sparc_cheb_filter_batch.argtypes = [POINTER(c_void_p), c_int, c_int, c_int, POINTER(c_double),
                                           POINTER(c_double), POINTER(c_double), c_void_p, c_void_p, c_int,
                                           c_int64, c_void_p]
@@ -316,6 +320,13 @@ class Hamiltonian:
     @classmethod
     def from_workload(cls, ctx, wl, kidx=0):
         return cls(ctx, wl.n, wl.h, wl.fd_radius, wl.kpts[kidx], wl.veff, wl.proj)
+
+    def filter_kernel(self, dtype) -> int:
+        """The H-pass kernel sparc_cheb_filter runs for this H and dtype
+        (sparc_filter_kernel: KERNEL_GENERIC, KERNEL_TILED or KERNEL_TMA)."""
+        out = c_int(-1)
+        self.ctx.check(load().sparc_filter_kernel(self.handle, int(dtype), ctypes.byref(out)))
+        return out.value
 
     def close(self):
         if getattr(self, "handle", None):
