@@ -200,8 +200,9 @@ cudaError_t launch_pass(const sparc_ham* H, const T* Yin, const T* Yprev, T* You
 // Complex64, batched over k: the same two steps for the units of `ks`; `gc` and
 // the block buffers hold nunit_total units ([unit][Nd][NB] and [p][unit][NB]);
 // geometry and launch shape from H0.
-// padded: Y in the x-padded layout of the TMA passes.
-cudaError_t launch_gather_k(const sparc_ham* H0, const cf32* Y, long long nunit_total, const KSlots& ks,
+// nblk_k: blocks of one k in total (fixes the summation order); padded: Y in the x-padded
+// layout of the TMA passes.
+cudaError_t launch_gather_k(const sparc_ham* H0, const cf32* Y, long long nunit_total, const KSlots& ks, int nblk_k,
                             cf32* gc, cf32* scratch, cudaStream_t st, bool padded = false);
 cudaError_t launch_pass_k(const sparc_ham* H0, const cf32* Yin, const cf32* Yprev, cf32* Yout, const cf32* gc,
                           long long nunit_total, const KSlots& ks, cudaStream_t st);

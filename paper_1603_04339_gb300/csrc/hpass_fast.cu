@@ -1203,13 +1203,16 @@ __global__ void k_gather_sum_k(const cf32* __restrict__ part, const Group* __res
 // --------------------------------------------------------------------------- launchers
 
 constexpr int NSLAB_MAX = 16;
-// Row slabs per projector group: enough CTAs for about six per SM, at most 16.
-static int gather_slabs(const sparc_ham* H) {
+constexpr int GATHER_OCT_C = 4;   // complex64 blocks per projection CTA
+// Complex64: row slabs per projector group such that the blocks of one k give about six
+// CTAs per SM (at most 16).  From the k's block count, not the launch's units, so that a
+// batch over k and the per-k filter sum in the same order.
+static int gather_slabs(const sparc_ham* H, int nblk_k) {
   const Tables* Tb = (const Tables*)H->fast;
   const int want = 6 * H->ctx->nsm;
-  return std::max(1, std::min(NSLAB_MAX, ceil_div(want, std::max(1, Tb->ngrp))));
+  const int octs = std::max(1, ceil_div(nblk_k, GATHER_OCT_C));
+  return std::max(1, std::min(NSLAB_MAX, ceil_div(want, std::max(1, Tb->ngrp) * octs)));
 }
-constexpr int GATHER_OCT_C = 4;   // complex64 blocks per projection CTA
 // FP32: slabs from the total block count (8 blocks per CTA at most), not the blocks of
 // one launch, so that every grouping of the same filter sums in the same order.
 static int gather_slabs_f2(const sparc_ham* H, int nblk_total) {
@@ -1224,12 +1227,12 @@ size_t gather_scratch_bytes(const sparc_ham* H, int nb, size_t esize) {
   return (size_t)std::max(1, Tb->ngrp) * NSLAB_MAX * 4 * nb * NB * esize;
 }
 
-cudaError_t launch_gather_k(const sparc_ham* H0, const cf32* Y, long long nunit_total, const KSlots& ks,
+cudaError_t launch_gather_k(const sparc_ham* H0, const cf32* Y, long long nunit_total, const KSlots& ks, int nblk_k,
                             cf32* gc, cf32* scratch, cudaStream_t st, bool padded) {
   const Tables* Tb = (const Tables*)H0->fast;
   if (H0->nproj == 0 || Tb->ngrp == 0) return cudaSuccess;
   const float dv = (float)(H0->grid.h[0] * H0->grid.h[1] * H0->grid.h[2]);
-  const int nslab = gather_slabs(H0);
+  const int nslab = gather_slabs(H0, nblk_k);
   cudaEvent_t t0 = timing_begin(H0->ctx, st);
   constexpr int NBM = GATHER_OCT_C;
   const int noct = ceil_div(ks.nbk, NBM);
@@ -1258,7 +1261,7 @@ cudaError_t launch_gather(const sparc_ham* H, const T* Y, int nblk_total, int bl
     kslot(H, ks.s[0]);
     ks.s[0].ubase = blk0;
     ks.s[0].alpha = ks.s[0].shift = ks.s[0].beta = 0.f;
-    return launch_gather_k(H, Y, nblk_total, ks, gc, scratch, st, padded);
+    return launch_gather_k(H, Y, nblk_total, ks, nblk_total, gc, scratch, st, padded);
   } else {
     const float dv = (float)(H->grid.h[0] * H->grid.h[1] * H->grid.h[2]);
     const int nslab = gather_slabs_f2(H, nblk_total);

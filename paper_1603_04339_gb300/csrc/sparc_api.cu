@@ -513,11 +513,11 @@ static sparc_status kbatch_launches(sparc_ham* const* Hs, int nk, int m, const d
                    : fast::launch_pass_k(H0, in, pv, out, gc, U, ks, st);
       };
       coefs(0);
-      SPARC_CUDA(ctx, fast::launch_gather_k(H0, prev, U, ks, gc, scratch, st, tma));
+      SPARC_CUDA(ctx, fast::launch_gather_k(H0, prev, U, ks, nblk, gc, scratch, st, tma));
       SPARC_CUDA(ctx, pass(prev, nullptr, cur));
       for (int j = 1; j < m; ++j) {
         coefs(j);
-        SPARC_CUDA(ctx, fast::launch_gather_k(H0, cur, U, ks, gc, scratch, st, tma));
+        SPARC_CUDA(ctx, fast::launch_gather_k(H0, cur, U, ks, nblk, gc, scratch, st, tma));
         SPARC_CUDA(ctx, pass(cur, prev, prev));
         std::swap(cur, prev);
       }
