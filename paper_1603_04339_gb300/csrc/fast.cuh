@@ -64,6 +64,8 @@ constexpr unsigned TMA_REC_MAX = 36352;      // bytes of one plane's record, at 
 constexpr int TMA_MAXTY = 16;                // tile rows (n2 <= 256)
 constexpr int TMA_MAXSEG = 4;                // y segments of one halo frame
 constexpr int TMA_NMAPS = 8;                 // distinct segment heights
+constexpr unsigned TMA_REC_MAX_C = 30080;    // complex pass: bytes of one plane's record, at most
+constexpr int TMA_MAXTILE_C = 256;           // complex pass: tile columns, at most
 struct TmaTables {
   bool ok = false;            // built: the grid and projectors fit the kernel's limits
   bool cplx = false;          // slots split by periodic image (complex Hamiltonian)
@@ -74,6 +76,10 @@ struct TmaTables {
   // at frame row yseg[ty][j][1] and has the height map_h[yseg[ty][j][2]] (-1: no run).
   int nmaps = 0;
   int map_h[TMA_NMAPS] = {};
+  // work items of one block (FP32: one per tile) or unit (complex: tile | half << 16 |
+  // dual mode << 17 per entry; full tiles twice, narrow tiles once as dual items)
+  int nts = 0;
+  int tsmap[2 * TMA_MAXTILE_C] = {};
   int yseg[TMA_MAXTY][TMA_MAXSEG][3] = {};
   int* d_cproj = nullptr;     // [tile][TMA_MAXG][4] projector index of (group slot, s/px/py/pz), -1 if none
   int* d_cng = nullptr;       // [tile] slots of the tile column

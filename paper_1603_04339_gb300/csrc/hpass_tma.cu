@@ -52,34 +52,57 @@ namespace fast {
 namespace tma {
 
 constexpr int MAXG = TMA_MAXG;
-constexpr uint32_t REC_MAX = TMA_REC_MAX;
 constexpr int TT = 16;                   // tile edge in x and y
 constexpr int FR = TT + 2 * R;           // 28: tile plus halo
 constexpr int ZLMAX = 128;               // output planes per z-chunk, at most
-constexpr int NBUF = 3;                  // stages in the ring
 constexpr int NCW = 16;                  // warps; the last one also produces
 constexpr int NTHR = NCW * 32;
-constexpr int DIST = 2;                  // steps the producer runs ahead (< NBUF)
 constexpr uint32_t FRAME_B = FR * FR * NB * 4;   // 25088
 constexpr uint32_t TILE_B = TT * TT * NB * 4;    // 8192
 constexpr uint32_t V_B = TT * TT * 4;            // 1024
-constexpr uint32_t OFF_YP = FRAME_B;
-constexpr uint32_t OFF_V = OFF_YP + TILE_B;
-constexpr uint32_t OFF_REC = OFF_V + V_B;        // 34304
-constexpr uint32_t STAGE_B = OFF_REC + REC_MAX;
-// per-item tables, filled ahead by cp.async: projector coefficients gc of the item's
-// boxes (two items), their projector indices (two items), record offsets (three items)
-constexpr uint32_t OFF_GCS = NBUF * STAGE_B;
-constexpr uint32_t GCS_B = (MAXG + 1) * 32 * 4;    // one item: float[MAXG + 1][32]
-constexpr uint32_t OFF_CPJ = OFF_GCS + 2 * GCS_B;
-constexpr uint32_t CPJ_B = MAXG * 4 * 4;           // one item: int[MAXG][4]
-constexpr uint32_t OFF_RECS = OFF_CPJ + 2 * CPJ_B;
-constexpr int RECN = ZLMAX + 4;                    // ints per item (nz + 1 used), 16-byte multiple
-constexpr uint32_t OFF_BAR = OFF_RECS + 3 * RECN * 4;
-constexpr uint32_t SMEM_B = OFF_BAR + 2 * NBUF * 8;
-static_assert(OFF_BAR % 8 == 0, "mbarrier alignment");
-static_assert(STAGE_B % 128 == 0 && OFF_REC % 128 == 0 && OFF_YP % 128 == 0, "stage alignment");
-static_assert(SMEM_B <= 232448, "shared memory of one CTA");
+constexpr uint32_t GCS_B = (MAXG + 1) * 32 * 4;  // coefficients of one item (half): float[MAXG + 1][32]
+constexpr uint32_t CPJ_B = MAXG * 4 * 4;         // projector indices of one item: int[MAXG][4]
+constexpr int RECN = ZLMAX + 4;                  // record offsets of one item (nz + 1 used), 16-byte multiple
+
+// Shared-memory layout of a CTA: a ring of NBUF stages, each a halo frame (or the tile of
+// a boundary plane), the Yprev tile, V_eff and the plane's record; then per-item tables,
+// filled ahead by cp.async: coefficients gc of the item's slots (two items), their
+// projector indices (two items), record offsets (three items); then the mbarriers.
+// FP32: three stages, the producer two steps ahead.  Complex: two stages, the producer one
+// step ahead, each with room for both halves of a unit (the dual items of narrow tiles:
+// frames, tiles and Yprev of half 1 after those of half 0; coefficients of both halves).
+template <bool CX>
+struct Lay {
+  static constexpr int NBUF = CX ? 2 : 3;             // stages in the ring
+  static constexpr int DIST = CX ? 1 : 2;             // steps the producer runs ahead (< NBUF)
+  static constexpr int NH = CX ? 2 : 1;               // halves a stage holds
+  static constexpr uint32_t REC = CX ? TMA_REC_MAX_C : TMA_REC_MAX;
+  static constexpr uint32_t OFF_YP = NH * FRAME_B;
+  static constexpr uint32_t OFF_V = OFF_YP + NH * TILE_B;
+  static constexpr uint32_t OFF_REC = OFF_V + V_B;
+  static constexpr uint32_t STAGE_B = OFF_REC + REC;
+  static constexpr uint32_t OFF_GCS = NBUF * STAGE_B;
+  static constexpr uint32_t GCS_ITEM = NH * GCS_B;
+  static constexpr uint32_t OFF_CPJ = OFF_GCS + 2 * GCS_ITEM;
+  static constexpr uint32_t OFF_RECS = OFF_CPJ + 2 * CPJ_B;
+  static constexpr uint32_t OFF_BAR = OFF_RECS + 3 * RECN * 4;
+  static constexpr uint32_t SMEM_B = OFF_BAR + 2 * NBUF * 8;
+  static_assert(OFF_BAR % 8 == 0, "mbarrier alignment");
+  static_assert(STAGE_B % 128 == 0 && OFF_REC % 128 == 0 && OFF_YP % 128 == 0 && FRAME_B % 128 == 0,
+                "stage alignment");
+  static_assert(SMEM_B <= 232448, "shared memory of one CTA");
+};
+
+// Node origin (xa, ya) of warp w's 8 x 2 nodes in a tile, and the half of the unit it
+// computes in a dual item: mode 0, a full tile (2 x 8 warps); mode 1, a tile of at most 8
+// valid columns (x-dual: even warps half 0, odd warps half 1, both at x 0..7); mode 2, a
+// tile of more than 8 valid columns and at most 8 valid rows (y-dual: warps 0..7 half 0,
+// warps 8..15 half 1, both at y 0..7).
+__host__ __device__ __forceinline__ void warp_origin(int md, int w, int& xa, int& ya, int& wh) {
+  if (md == 1) { xa = 0; ya = 2 * (w >> 1); wh = w & 1; }
+  else if (md == 2) { xa = 8 * (w & 1); ya = 2 * ((w >> 1) & 3); wh = w >> 3; }
+  else { xa = 8 * (w & 1); ya = 2 * (w >> 1); wh = 0; }
+}
 
 // --------------------------------------------------------------------------- host tables
 
@@ -109,6 +132,7 @@ bool tma_host_tables(const int n[3], const std::vector<Group>& grps, const std::
   std::vector<int>& rec = out.rec;
   std::vector<int>& cimg = out.cimg;
   std::vector<uint32_t>& words = out.words;
+  const uint32_t rec_max = images ? TMA_REC_MAX_C : TMA_REC_MAX;
   // tables per tile column (all z); the z-chunking of the work is chosen per launch
   M.nchunk = 1;
   M.zl = n[2];
@@ -136,6 +160,8 @@ bool tma_host_tables(const int n[3], const std::vector<Group>& grps, const std::
     const int x0 = (tile % M.tiles_x) * TT, y0 = (tile / M.tiles_x) * TT;
     const int zs = 0, nz = n[2];
     const int xe = std::min(n[0], x0 + TT), ye = std::min(n[1], y0 + TT);
+    // complex tables: a narrow tile runs as dual items (both halves of a unit)
+    const int md = !images ? 0 : (xe - x0 <= 8 ? 1 : (ye - y0 <= 8 ? 2 : 0));
     // the slots that meet the tile over the chunk's planes: the atom boxes (projector
     // groups), with images split (one slot per image whose nodes meet the tile)
     std::vector<int> loc, limg;
@@ -201,7 +227,8 @@ bool tma_host_tables(const int n[3], const std::vector<Group>& grps, const std::
       std::vector<int> hdr(32, 0), ids;
       std::vector<std::vector<int>> act(NCW);
       for (int w = 0; w < NCW; ++w) {
-        const int xa = 8 * (w & 1), ya = 2 * (w >> 1);
+        int xa, ya, wh;
+        warp_origin(md, w, xa, ya, wh);
         for (size_t g = 0; g < loc.size(); ++g) {
           if (uz[g][k] < 0) continue;
           if (uy[g][ya] < 0 && uy[g][ya + 1] < 0) continue;
@@ -220,11 +247,12 @@ bool tma_host_tables(const int n[3], const std::vector<Group>& grps, const std::
       const int nid = (nr + 3) & ~3;
       const int bytes = 128 + 4 * nid + 512 * nr;
       max_rec = std::max(max_rec, bytes);
-      if (bytes > (int)REC_MAX) return false;   // record too large for a stage
+      if (bytes > (int)rec_max) return false;   // record too large for a stage
       for (int v : hdr) words.push_back((uint32_t)v);
       for (int j = 0; j < nid; ++j) words.push_back(j < nr ? (uint32_t)ids[j] : 0u);
       for (int w = 0; w < NCW; ++w) {
-        const int xa = 8 * (w & 1), ya = 2 * (w >> 1);
+        int xa, ya, wh;
+        warp_origin(md, w, xa, ya, wh);
         for (size_t j = 0; j < act[w].size(); j += 2) {
           const int gg[2] = {act[w][j], (j + 1 < act[w].size()) ? act[w][j + 1] : -1};
           for (int lane = 0; lane < 32; ++lane) {
@@ -256,6 +284,24 @@ bool tma_host_tables(const int n[3], const std::vector<Group>& grps, const std::
   rec[(size_t)ncta * M.zl] = (int)(words.size() / 4);
   if (words.size() / 4 >= (size_t)INT32_MAX) return false;
   M.max_rec = max_rec;
+  // the work items of one unit: (tile, half) for full tiles, (tile, dual mode) for narrow
+  // ones (complex tables); one per tile for the FP32 tables
+  M.nts = 0;
+  if (images) {
+    if (ncta > TMA_MAXTILE_C) return false;
+    for (int t = 0; t < ncta; ++t) {
+      const int x0 = (t % M.tiles_x) * TT, y0 = (t / M.tiles_x) * TT;
+      const int md = n[0] - x0 <= 8 ? 1 : (n[1] - y0 <= 8 ? 2 : 0);
+      if (md == 0) {
+        M.tsmap[M.nts++] = t;
+        M.tsmap[M.nts++] = t | (1 << 16);
+      } else {
+        M.tsmap[M.nts++] = t | (md << 17);
+      }
+    }
+  } else {
+    M.nts = ncta;
+  }
   return true;
 }
 
@@ -382,10 +428,7 @@ bool tma_usable_c(const sparc_ham* H) {
   return T != nullptr && T->tmac.ok && usable(H);
 }
 
-int tma_items_per_unit(const sparc_ham* H) {
-  const TmaTables& M = ((const Tables*)H->fast)->tmac;
-  return M.tiles_x * M.tiles_y * 2;
-}
+int tma_items_per_unit(const sparc_ham* H) { return ((const Tables*)H->fast)->tmac.nts; }
 
 bool tma_batch_compatible(const sparc_ham* H0, const sparc_ham* H) {
   if (!tma_usable_c(H0) || !tma_usable_c(H)) return false;
@@ -474,6 +517,8 @@ struct MapsT {
 // each as two halves of four complex orbitals (items are half-units).
 struct KArgs {
   int nk, nbk;
+  int nts;                          // work items of one unit per z-chunk
+  int tsmap[2 * TMA_MAXTILE_C];     // tile | half << 16 | dual mode << 17 of each
   long long ubase[KMAX];
   float2 alpha2[KMAX], beta2[KMAX];
   float c0s[KMAX];
@@ -511,33 +556,40 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], float a0, float a1, floa
         "r"(__float_as_uint(b0)), "r"(__float_as_uint(b1)));
 }
 
-// A work item: tile column, z-chunk and block (FP32) or half-unit (complex: half h of
-// unit blk, the k slot kk).
+// A work item: tile column, z-chunk and block (FP32) or unit part (complex: half h of
+// unit blk, or both halves for a dual item of mode md > 0; kk the k slot).
 struct Item {
-  int tile, chunk, bi, tx0, ty0, zs, nz;
-  int blk, h, kk;
+  int tile, chunk, tx0, ty0, zs, nz;
+  int blk, h, md, kk;
 };
 template <bool CX>
 __device__ __forceinline__ Item decode(const Args& a, const KArgsT<CX>& ka, int item) {
   Item it;
-  it.tile = item % a.ntiles;
-  const int rest = item / a.ntiles;
-  it.chunk = rest % a.nchunk;
-  it.bi = rest / a.nchunk;
+  int u;
+  if constexpr (CX) {
+    const int e = ka.tsmap[item % ka.nts];
+    const int rest = item / ka.nts;
+    it.chunk = rest % a.nchunk;
+    u = rest / a.nchunk;
+    it.tile = e & 0xFFFF;
+    it.h = (e >> 16) & 1;
+    it.md = e >> 17;
+    it.kk = u / ka.nbk;
+    it.blk = (int)(ka.ubase[it.kk] + u % ka.nbk);
+  } else {
+    it.tile = item % a.ntiles;
+    const int rest = item / a.ntiles;
+    it.chunk = rest % a.nchunk;
+    u = rest / a.nchunk;
+    it.h = 0;
+    it.md = 0;
+    it.kk = 0;
+    it.blk = a.blk0 + u;
+  }
   it.tx0 = (it.tile % a.tiles_x) * TT;
   it.ty0 = (it.tile / a.tiles_x) * TT;
   it.zs = it.chunk * a.zl;
   it.nz = min(a.zl, a.n3 - it.zs);
-  if constexpr (CX) {
-    const int u = it.bi >> 1;
-    it.h = it.bi & 1;
-    it.kk = u / ka.nbk;
-    it.blk = (int)(ka.ubase[it.kk] + u % ka.nbk);
-  } else {
-    it.h = 0;
-    it.kk = 0;
-    it.blk = a.blk0 + it.bi;
-  }
   return it;
 }
 
@@ -545,21 +597,24 @@ __device__ __forceinline__ Item decode(const Args& a, const KArgsT<CX>& ka, int 
 // last warp call it).  recs: the record offsets of the item's planes (16-byte units,
 // entries 0 .. nz).  Returns false if the wait for the stage to be free ran out; once
 // a wait has run out (wait == false) no further waits are made, so that a broken
-// pipeline ends the kernel quickly instead of timing out at every step.
+// pipeline ends the kernel quickly instead of timing out at every step.  A dual item
+// loads the frames (tiles) and Yprev tiles of both halves.
 template <bool CX>
 __device__ __forceinline__ bool produce(const Args& a, const KArgsT<CX>& ka, const MapsT<CX>& mp, unsigned char* smem,
                                        uint64_t* bars, int item, int s, int g, const int* recs, bool wait) {
+  using L = Lay<CX>;
   const int lane = threadIdx.x & 31;
   const Item it = decode<CX>(a, ka, item);
   const int blk = it.blk;
   const int c0 = CX ? 8 * it.h : 0;   // first float of the node's half (complex: 16 floats a node)
-  const int slot = g % NBUF;
-  unsigned char* st = smem + (size_t)slot * STAGE_B;
+  const int nh = (CX && it.md) ? 2 : 1;
+  const int slot = g % L::NBUF;
+  unsigned char* st = smem + (size_t)slot * L::STAGE_B;
   uint64_t* full = bars + slot;
-  uint64_t* empty = bars + NBUF + slot;
+  uint64_t* empty = bars + L::NBUF + slot;
   bool ok = true;
   if (a.stall >= 0 && g >= a.stall) return true;   // injected stall: from this step of the CTA on, nothing is issued
-  if (wait && g >= NBUF && !ptx::mbar_wait_lim(empty, (uint32_t)((g / NBUF) - 1) & 1u, a.wait_limit)) ok = false;
+  if (wait && g >= L::NBUF && !ptx::mbar_wait_lim(empty, (uint32_t)((g / L::NBUF) - 1) & 1u, a.wait_limit)) ok = false;
   const int p = it.zs - R + s;
   int zw = p;
   if (zw < 0) zw += a.n3;
@@ -569,23 +624,30 @@ __device__ __forceinline__ bool produce(const Args& a, const KArgsT<CX>& ka, con
   const int k = comp ? s - R : 0;
   const int o0 = recs[k];
   const uint32_t rbytes = comp ? 16u * (uint32_t)(recs[k + 1] - o0) : 0u;
-  const uint32_t bytes = (comp ? FRAME_B + V_B + rbytes : TILE_B) + (yp ? TILE_B : 0u);
+  const uint32_t bytes = (comp ? nh * FRAME_B + V_B + rbytes : nh * TILE_B) + (yp ? nh * TILE_B : 0u);
   if (lane == 0) ptx::mbar_arrive_expect_tx(full, bytes);
   __syncwarp();
   const int zc = blk * a.n3 + zw;
   if (comp) {
-    // halo frame: padded columns tx0 .. tx0+27 (nodes x = tx0-6 .. tx0+21), one box per y run
-    if (lane < TMA_MAXSEG) {
-      const int* sg = a.yseg[it.ty0 / TT][lane];
-      if (sg[2] >= 0) tma4(st + (size_t)sg[1] * FR * NB * 4, &mp.frame[sg[2]], c0, it.tx0, sg[0], zc, full);
+    // halo frame: padded columns tx0 .. tx0+27 (nodes x = tx0-6 .. tx0+21), one box per y
+    // run; lanes 4 .. 7 the frame of half 1 of a dual item
+    if (lane < TMA_MAXSEG * nh) {
+      const int hh = lane / TMA_MAXSEG;
+      const int* sg = a.yseg[it.ty0 / TT][lane % TMA_MAXSEG];
+      if (sg[2] >= 0)
+        tma4(st + hh * FRAME_B + (size_t)sg[1] * FR * NB * 4, &mp.frame[sg[2]], c0 + 8 * hh, it.tx0, sg[0], zc,
+             full);
     }
-    if (lane == 29) tma3(st + OFF_V, &mp.veff[CX ? it.kk : 0], it.tx0, it.ty0, zw, full);
-    if (lane == 30) bulk_g2s_hint(st + OFF_REC, a.stream + 16 * (size_t)o0, rbytes, full, policy_evict_last());
-  } else if (lane == 0) {
-    tma4(st, &mp.tile_in, c0, it.tx0 + R, it.ty0, zc, full);
+    if (lane == 29) tma3(st + L::OFF_V, &mp.veff[CX ? it.kk : 0], it.tx0, it.ty0, zw, full);
+    if (lane == 30) bulk_g2s_hint(st + L::OFF_REC, a.stream + 16 * (size_t)o0, rbytes, full, policy_evict_last());
+  } else if (lane < nh) {
+    tma4(st + lane * FRAME_B, &mp.tile_in, c0 + 8 * lane, it.tx0 + R, it.ty0, zc, full);
   }
-  if (yp && lane == 31)
-    tma4_hint(st + OFF_YP, &mp.tile_prev, c0, it.tx0 + R, it.ty0, blk * a.n3 + (p - R), full, policy_evict_first());
+  if (yp && lane >= 32 - nh) {
+    const int hh = 31 - lane;
+    tma4_hint(st + L::OFF_YP + hh * TILE_B, &mp.tile_prev, c0 + 8 * hh, it.tx0 + R, it.ty0, blk * a.n3 + (p - R), full,
+              policy_evict_first());
+  }
   return ok;
 }
 
@@ -615,32 +677,37 @@ __device__ __forceinline__ void stage_cproj(const Args& a, const KArgsT<CX>& ka,
   for (int i = threadIdx.x; i < MAXG * 4; i += NTHR) cp_async4(dst + i, a.cproj + (size_t)it.tile * MAXG * 4 + i, true);
 }
 // Complex: B column n = lane >> 2 of a slot is component n & 1 (re, im) of orbital
-// 4 h + (n >> 1); the Bloch factor of the slot is applied after the copies landed
-// (phase_gc).
+// 4 h + (n >> 1); a dual item stages both halves (half 1 GCS_B bytes after half 0); the
+// Bloch factor of the slot is applied after the copies landed (phase_gc).
 template <bool CX>
 __device__ __forceinline__ void stage_gc(const Args& a, const KArgsT<CX>& ka, int item, const int* cpj, float* dst) {
   if (item >= a.nitems) return;
   const Item it = decode<CX>(a, ka, item);
-  for (int idx = threadIdx.x; idx < MAXG * 32; idx += NTHR) {
-    const int l = idx & 31;
-    const int pp = cpj[(idx >> 5) * 4 + (l & 3)];
+  const int nh = (CX && it.md) ? 2 : 1;
+  for (int idx = threadIdx.x; idx < nh * MAXG * 32; idx += NTHR) {
+    const int hl = idx / (MAXG * 32), i = idx - hl * (MAXG * 32);
+    const int l = i & 31;
+    const int pp = cpj[(i >> 5) * 4 + (l & 3)];
     const size_t row = ((size_t)(pp < 0 ? 0 : pp) * a.nblk_total + it.blk) * NB;
-    const float* src = CX ? a.gc + (row + 4 * it.h + (l >> 3)) * 2 + ((l >> 2) & 1) : a.gc + row + (l >> 2);
-    cp_async4(dst + idx, src, pp >= 0);
+    const float* src =
+        CX ? a.gc + (row + 4 * (it.h + hl) + (l >> 3)) * 2 + ((l >> 2) & 1) : a.gc + row + (l >> 2);
+    cp_async4(dst + hl * (GCS_B / 4) + i, src, pp >= 0);
   }
 }
 
 // The Bloch factors of an item's slots, folded into its staged coefficients: slot g in
 // periodic image t gets exp(-i k.(t L)) = prod_s ph_s^(-t_s) (the factor of the image's
 // projector values at the grid nodes, Eq. NonlocalPS:FD); (re, im) of (slot, orbital c,
-// projector k) sit at lanes 8 c + k and 8 c + 4 + k.
+// projector k) sit at lanes 8 c + k and 8 c + 4 + k; both halves of a dual item.
 __device__ __forceinline__ void phase_gc(const Args& a, const KArgs& ka, const Item& it, float* gcs) {
   const float2 px = ka.phx[it.kk], py = ka.phy[it.kk], pz = ka.phz[it.kk];
-  for (int q = threadIdx.x; q < MAXG * 16; q += NTHR) {
-    const int g = q >> 4, c = (q >> 2) & 3, k = q & 3;
+  const int nh = it.md ? 2 : 1;
+  for (int q = threadIdx.x; q < nh * MAXG * 16; q += NTHR) {
+    const int hl = q / (MAXG * 16), r = q - hl * (MAXG * 16);
+    const int g = r >> 4, c = (r >> 2) & 3, k = r & 3;
     const int code = __ldg(a.cimg + (size_t)it.tile * MAXG + g);
     const float2 ph = cmul(cmul(face(px, 1 - (code & 3)), face(py, 1 - ((code >> 2) & 3))), face(pz, 1 - (code >> 4)));
-    float* v = gcs + g * 32 + 8 * c + k;
+    float* v = gcs + hl * (GCS_B / 4) + g * 32 + 8 * c + k;
     const float re = v[0], im = v[4];
     v[0] = ph.x * re - ph.y * im;
     v[4] = ph.x * im + ph.y * re;
@@ -680,28 +747,29 @@ template <bool CX>
 __global__ void __launch_bounds__(NTHR, 1)
 k_pass_tma(const __grid_constant__ MapsT<CX> mp, const __grid_constant__ Args a,
            const __grid_constant__ KArgsT<CX> ka) {
+  using L = Lay<CX>;
   constexpr int NF = CX ? 2 * NB : NB;   // floats per node of the block buffers
   extern __shared__ __align__(1024) unsigned char smem[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OFF_BAR);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    for (int b = 0; b < NBUF; ++b) {
+    for (int b = 0; b < L::NBUF; ++b) {
       ptx::mbar_init(bars + b, 1);
-      ptx::mbar_init(bars + NBUF + b, NCW);
+      ptx::mbar_init(bars + L::NBUF + b, NCW);
     }
     ptx::mbar_init_fence();
   }
-  int* recs = reinterpret_cast<int*>(smem + OFF_RECS);
-  int* cpj = reinterpret_cast<int*>(smem + OFF_CPJ);
-  float* gcsb = reinterpret_cast<float*>(smem + OFF_GCS);
+  int* recs = reinterpret_cast<int*>(smem + L::OFF_RECS);
+  int* cpj = reinterpret_cast<int*>(smem + L::OFF_CPJ);
+  float* gcsb = reinterpret_cast<float*>(smem + L::OFF_GCS);
   // tables of the first two items (record offsets, projector indices), then the
-  // coefficients of the first item; the zero slot MAXG of both coefficient buffers
+  // coefficients of the first item; the zero slot MAXG of every coefficient buffer
   stage_recs<CX>(a, ka, blockIdx.x, recs);
   stage_recs<CX>(a, ka, blockIdx.x + gridDim.x, recs + RECN);
   stage_cproj<CX>(a, ka, blockIdx.x, cpj);
   stage_cproj<CX>(a, ka, blockIdx.x + gridDim.x, cpj + MAXG * 4);
-  if (tid < 64) gcsb[(tid >> 5) * (GCS_B / 4) + MAXG * 32 + (tid & 31)] = 0.f;
+  if (tid < 64 * L::NH) gcsb[(tid >> 5) * (GCS_B / 4) + MAXG * 32 + (tid & 31)] = 0.f;
   cp_async_commit();
   cp_async_wait_all();
   __syncthreads();
@@ -724,14 +792,10 @@ k_pass_tma(const __grid_constant__ MapsT<CX> mp, const __grid_constant__ Args a,
     }
   };
   if (producer)
-    for (int gp = 0; gp < DIST; ++gp) produce_next(gp);
+    for (int gp = 0; gp < L::DIST; ++gp) produce_next(gp);
 
   // ---- every warp consumes
   const int gq = lane >> 2, op = lane & 3;
-  const int xl = 8 * (warp & 1) + gq, yl = 2 * (warp >> 1);
-  const int fo = ((yl + R) * FR + xl + R) * NB + 2 * op;   // frame offset of node 0 (floats)
-  const int to = (yl * TT + xl) * NB + 2 * op;             // tile offset of node 0
-  const int vo = yl * TT + xl;
   const size_t plane = (size_t)a.n1p * a.n2 * NF;   // one z-plane of a padded block
   int g = 0, li = 0;
   int cslot = 0;          // g mod NBUF
@@ -751,17 +815,27 @@ k_pass_tma(const __grid_constant__ MapsT<CX> mp, const __grid_constant__ Args a,
     cp_async_wait_all();
     __syncthreads();
     if constexpr (CX) {
-      phase_gc(a, ka, it, gcsb + (li & 1) * (GCS_B / 4));
+      phase_gc(a, ka, it, gcsb + (li & 1) * (L::GCS_ITEM / 4));
       __syncthreads();
     }
-    stage_gc<CX>(a, ka, item + gridDim.x, cpj + ((li + 1) & 1) * MAXG * 4, gcsb + ((li + 1) & 1) * (GCS_B / 4));
+    stage_gc<CX>(a, ka, item + gridDim.x, cpj + ((li + 1) & 1) * MAXG * 4, gcsb + ((li + 1) & 1) * (L::GCS_ITEM / 4));
     stage_cproj<CX>(a, ka, item + 2 * gridDim.x, cpj + (li & 1) * MAXG * 4);
     stage_recs<CX>(a, ka, item + 2 * gridDim.x, recs + ((li + 2) % 3) * RECN);
     cp_async_commit();
-    const float* gcs = gcsb + (li & 1) * (GCS_B / 4);
+    // this warp's nodes (x, y), (x, y + 1) with x = tx0 + xl + gq, y = ty0 + yl, and the
+    // half it computes (a dual item's warps split between the halves)
+    int xl, yl, wh;
+    warp_origin(CX ? it.md : 0, warp, xl, yl, wh);
+    xl += gq;
+    const int fo = wh * (FRAME_B / 4) + ((yl + R) * FR + xl + R) * NB + 2 * op;   // frame offset of node 0 (floats)
+    const int to = wh * (FRAME_B / 4) + (yl * TT + xl) * NB + 2 * op;             // tile offset of node 0
+    const int tp = wh * (TILE_B / 4) + (yl * TT + xl) * NB + 2 * op;              // Yprev tile offset of node 0
+    const int vo = yl * TT + xl;
+    const float* gcs = gcsb + (li & 1) * (L::GCS_ITEM / 4) + wh * (GCS_B / 4);
     const int gx = it.tx0 + xl, gy = it.ty0 + yl;
     const bool v0 = gx < a.n1 && gy < a.n2, v1 = gx < a.n1 && gy + 1 < a.n2;
-    float* outp = a.yout + ((size_t)blk * a.ndp + (size_t)gy * a.n1p + gx + R) * NF + (CX ? 8 * it.h : 0) + 2 * op;
+    float* outp =
+        a.yout + ((size_t)blk * a.ndp + (size_t)gy * a.n1p + gx + R) * NF + (CX ? 8 * (it.h + wh) : 0) + 2 * op;
     // ghost copies: nodes x < R repeat at x' = x + n1 + R, nodes x >= n1 - R at x' = x - n1 + R
     const long long gofs = gx < R ? (long long)a.n1 * NF : (gx >= a.n1 - R ? -(long long)a.n1 * NF : 0);
     // recurrence coefficients; complex: per k, with the Bloch factors of the faces
@@ -786,9 +860,9 @@ k_pass_tma(const __grid_constant__ MapsT<CX> mp, const __grid_constant__ Args a,
     const int S = it.nz + 2 * R;
     int ring = 0;   // s mod 13: the accumulator of output z'+d sits in slot (ring + 7 + d) mod 13
     for (int s = 0; s < S; ++s) {
-      if (producer) produce_next(g + DIST);
+      if (producer) produce_next(g + L::DIST);
       const int slot = cslot;
-      const unsigned char* st = smem + (size_t)slot * STAGE_B;
+      const unsigned char* st = smem + (size_t)slot * L::STAGE_B;
       if (ok && !ptx::mbar_test(bars + slot, cphase) && !ptx::mbar_wait_lim(bars + slot, cphase, a.wait_limit))
         ok = false;
       const float* F = reinterpret_cast<const float*>(st);
@@ -836,17 +910,17 @@ k_pass_tma(const __grid_constant__ MapsT<CX> mp, const __grid_constant__ Args a,
 #pragma unroll
           for (int q = 2; q <= R; ++q) xs1 = __ffma2_rn(a.cx2[q], __fadd2_rn(w[R + q], w[R - q]), xs1);
         }
-        const float* Vs = reinterpret_cast<const float*>(st + OFF_V);
+        const float* Vs = reinterpret_cast<const float*>(st + L::OFF_V);
         const float2 cen0 = __fmul2_rn(f2(c0s + Vs[vo]), f0);
         const float2 cen1 = __fmul2_rn(f2(c0s + Vs[vo + TT]), f1);
         // projector term on the tensor cores (3xTF32); the three products of a round go to
         // three accumulators, so that consecutive mma.sync do not wait on each other
         float nl[4] = {0.f, 0.f, 0.f, 0.f}, nla[4] = {0.f, 0.f, 0.f, 0.f}, nlb[4] = {0.f, 0.f, 0.f, 0.f};
         {
-          const int* hdr = reinterpret_cast<const int*>(st + OFF_REC);
+          const int* hdr = reinterpret_cast<const int*>(st + L::OFF_REC);
           const int r0 = hdr[warp], r1 = hdr[warp + 1], nr = hdr[NCW];
           const int* ids = hdr + 32;
-          const float4* A = reinterpret_cast<const float4*>(st + OFF_REC + 128 + 4 * ((nr + 3) & ~3));
+          const float4* A = reinterpret_cast<const float4*>(st + L::OFF_REC + 128 + 4 * ((nr + 3) & ~3));
           for (int r = r0; r < r1; ++r) {
             const int id = ids[r];
             const float4 av = A[r * 32 + lane];
@@ -903,9 +977,9 @@ k_pass_tma(const __grid_constant__ MapsT<CX> mp, const __grid_constant__ Args a,
         float2 r0 = __fmul2_rn(alpha2, e0);
         float2 r1 = __fmul2_rn(alpha2, e1);
         if (a.yprev != nullptr) {
-          const float* P = reinterpret_cast<const float*>(st + OFF_YP);
-          r0 = __ffma2_rn(beta2, lds2(P + to), r0);
-          r1 = __ffma2_rn(beta2, lds2(P + to + TT * NB), r1);
+          const float* P = reinterpret_cast<const float*>(st + L::OFF_YP);
+          r0 = __ffma2_rn(beta2, lds2(P + tp), r0);
+          r1 = __ffma2_rn(beta2, lds2(P + tp + TT * NB), r1);
         }
         float* o = outp + (size_t)(it.zs + s - 2 * R) * plane;
         if (v0) *reinterpret_cast<float2*>(o) = r0;
@@ -920,9 +994,9 @@ k_pass_tma(const __grid_constant__ MapsT<CX> mp, const __grid_constant__ Args a,
         }
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(bars + NBUF + slot);
+      if (lane == 0) mbar_arrive(bars + L::NBUF + slot);
       ++g;
-      if (++cslot == NBUF) { cslot = 0; cphase ^= 1u; }
+      if (++cslot == L::NBUF) { cslot = 0; cphase ^= 1u; }
       ring = ring == 12 ? 0 : ring + 1;
     }
   }
@@ -979,11 +1053,11 @@ static bool map_veff(CUtensorMap* m, const float* veff, int n1, int n2, int n3) 
 }
 
 // One launch over nunits work units (FP32 blocks blk0 .. blk0 + nunits - 1, or the complex
-// half-units of ks); the per-launch fields of Args and the maps of the geometry of H.
+// units of ks); the per-launch fields of Args and the maps of the geometry of H.
 template <bool CX>
 static cudaError_t launch_tma(const sparc_ham* H, const float* Yin, const float* Yprev, float* Yout, const float* gc,
                               long long nblk_total, int blk0, int nunits, double alpha, double shift, double beta,
-                              const KArgsT<CX>& ka, const KSlots* ks, cudaStream_t st) {
+                              KArgsT<CX>& ka, const KSlots* ks, cudaStream_t st) {
   const Tables* Tb = (const Tables*)H->fast;
   const TmaTables& M = CX ? Tb->tmac : Tb->tma;
   if (!M.ok || M.cplx != CX || encoder() == nullptr) return cudaErrorNotSupported;
@@ -1012,13 +1086,18 @@ static cudaError_t launch_tma(const sparc_ham* H, const float* Yin, const float*
   // the launch would then have fewer than two items per multiprocessor; chunks of at
   // least 16 planes and at most ZLMAX
   const int nsm = std::max(H->ctx->nsm, 1);
+  const int per_unit = CX ? M.nts : a.ntiles;   // items of one unit per z-chunk
+  if constexpr (CX) {
+    ka.nts = M.nts;
+    std::memcpy(ka.tsmap, M.tsmap, sizeof(ka.tsmap));
+  }
   int nchunk = ceil_div(n3, ZLMAX);
-  while ((long long)a.ntiles * nchunk * nunits < 2 * nsm && n3 / (nchunk + 1) >= 16) ++nchunk;
+  while ((long long)per_unit * nchunk * nunits < 2 * nsm && n3 / (nchunk + 1) >= 16) ++nchunk;
   a.nchunk = nchunk;
   a.zl = ceil_div(n3, nchunk);
   a.blk0 = blk0;
   a.nblk_total = (int)nblk_total;
-  const long long nitems = (long long)a.ntiles * nchunk * nunits;
+  const long long nitems = (long long)per_unit * nchunk * nunits;
   if (nitems >= INT32_MAX || nblk_total >= INT32_MAX) return cudaErrorInvalidValue;
   a.nitems = (int)nitems;
   a.ndp = padded_nd(H);
@@ -1046,11 +1125,12 @@ static cudaError_t launch_tma(const sparc_ham* H, const float* Yin, const float*
   a.wait_limit = H->ctx->inject_wait_limit > 0 ? H->ctx->inject_wait_limit : (1LL << 32);
   a.stall = H->ctx->inject_stall;
   H->ctx->inject_stall = -1;   // one launch
-  cudaError_t e = cudaFuncSetAttribute(k_pass_tma<CX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_B);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_pass_tma<CX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay<CX>::SMEM_B);
   if (e != cudaSuccess) return e;
   const int grid = (int)std::min<long long>(a.nitems, nsm);
   cudaEvent_t t0 = timing_begin(H->ctx, st);
-  k_pass_tma<CX><<<grid, NTHR, SMEM_B, st>>>(mp, a, ka);
+  k_pass_tma<CX><<<grid, NTHR, Lay<CX>::SMEM_B, st>>>(mp, a, ka);
   ++H->ctx->launches;
   timing_end(H->ctx, TK_FPASS, t0, st);
   return cudaGetLastError();
@@ -1082,8 +1162,8 @@ cudaError_t launch_from_blocks_px(const sparc_ham* H, const cf32* B, int nblk, c
 cudaError_t launch_pass_tma(const sparc_ham* H, const float* Yin, const float* Yprev, float* Yout, const float* gc,
                             int nblk_total, int blk0, int nb, double alpha, double shift, double beta,
                             cudaStream_t st) {
-  return tma::launch_tma<false>(H, Yin, Yprev, Yout, gc, nblk_total, blk0, nb, alpha, shift, beta,
-                                tma::KArgsNone{0}, nullptr, st);
+  tma::KArgsNone none{0};
+  return tma::launch_tma<false>(H, Yin, Yprev, Yout, gc, nblk_total, blk0, nb, alpha, shift, beta, none, nullptr, st);
 }
 
 cudaError_t launch_pass_tma_k(const sparc_ham* H0, const cf32* Yin, const cf32* Yprev, cf32* Yout, const cf32* gc,
@@ -1106,7 +1186,7 @@ cudaError_t launch_pass_tma_k(const sparc_ham* H0, const cf32* Yin, const cf32* 
     ka.phz[kk] = make_float2(S.phz_r, S.phz_i);
   }
   return launch_tma<true>(H0, (const float*)Yin, (const float*)Yprev, (float*)Yout, (const float*)gc, nunit_total,
-                          0, 2 * ks.nk * ks.nbk, 0.0, 0.0, 0.0, ka, &ks, st);
+                          0, ks.nk * ks.nbk, 0.0, 0.0, 0.0, ka, &ks, st);
 }
 
 }  // namespace fast
