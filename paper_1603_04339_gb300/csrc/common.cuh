@@ -176,6 +176,7 @@ struct sparc_ctx {
   std::vector<cudaEvent_t> ev_pool;
   // captured Jacobi sweeps, keyed by (element kind, n, buffers)
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t cap_stream2 = nullptr;   // the second branch of a captured graph (block Jacobi V updates)
   std::map<std::tuple<int, int, void*, void*, void*>, cudaGraphExec_t> graphs;
   int last_sweeps = 0;
   double last_ortho_err = -1.0;   // max |U1^T U1 - I| of the last mixed Rayleigh-Ritz (-1: none)

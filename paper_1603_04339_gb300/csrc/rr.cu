@@ -475,204 +475,236 @@ k_jacobi_round(const TW* __restrict__ A, TW* __restrict__ An, TW* __restrict__ V
 }
 
 // ------------------------------------------------------------------ block Jacobi (FP32)
-// The parallel cyclic Jacobi method on index blocks of BJ = 16: the npad/BJ blocks are
-// paired round-robin (the scalar method's ordering on blocks), and a round rotates
-// every pair's 32 x 32 subproblem A[I, I] (I = the pair's two blocks) by one inner
+// The parallel cyclic Jacobi method on index blocks of BJ (16 or 32): the npad/BJ blocks
+// are paired round-robin (the scalar method's ordering on blocks), and a round rotates
+// every pair's 2BJ x 2BJ subproblem A[I, I] (I = the pair's two blocks) by one inner
 // cyclic sweep, accumulated into an orthogonal W_I, then applies all of them at once:
 // A <- J^T A J and V <- V J with J = blockdiag(W_I).  A sweep is npad/BJ - 1 rounds
-// instead of the scalar method's npad - 1, each two launches of a few microseconds.
-constexpr int BJ = 16;
+// instead of the scalar method's npad - 1, each two launches.
+constexpr int BJ_MAX = 16;
 
-// local index l of pair k's 32 indices -> global index
+// local index l of pair k's 2 BJ indices -> global index
+template <int BJ>
 __device__ __forceinline__ int bj_index(int l, int bp, int bq) { return l < BJ ? BJ * bp + l : BJ * bq + (l - BJ); }
 
 // rotation of the pair (p, q) of pair subproblem S (local indices): the rotation of
-// jacobi_rot, t = sign(th)/(|th| + sqrt(th^2 + 1)) with th = d/(2b), d = S_qq - S_pp,
-// b = S_pq, written as t = sign(d) 2b / (|d| + sqrt(d^2 + 4b^2)) and evaluated with the
-// approximate reciprocal and reciprocal square root (a few ulp): the rotations' small
-// departure from orthogonality is removed afterwards by the Newton-Schulz step, and the
-// eigenvalues come from FP64 Rayleigh quotients.  (n is a multiple of 2 BJ on this
-// path, so every index of a pair subproblem is in range.)
+// jacobi_rot (the angle theta in [-pi/4, pi/4] with tan 2 theta = 2b/d, d = S_qq - S_pp,
+// b = S_pq), from the half-angle identities: cos 2 theta = |d| / r, sin 2 theta =
+// sign(d) 2b / r with r = sqrt(d^2 + 4b^2), c^2 = (1 + cos 2 theta)/2 in [1/2, 1] (no
+// cancellation), c = c^2 / sqrt(c^2), s = sin 2 theta / (2c).  Two dependent reciprocal
+// square roots (the approximate ones, a few ulp) and no division: the rotation of an
+// inner round is on the critical path of the pair solve.  Its small departure from
+// orthogonality is removed afterwards by the Newton-Schulz step, and the eigenvalues come
+// from FP64 Rayleigh quotients.  b = 0 gives the identity.  (n is a multiple of 2 BJ on
+// this path, so every index of a pair subproblem is in range.)
+template <int BJ>
 __device__ __forceinline__ void bj_rot(const float (&S)[2 * BJ][2 * BJ + 1], int p, int q, float& c, float& sn) {
-  c = 1.f;
-  sn = 0.f;
   const float b = S[p][q];
-  if (b != 0.f) {
-    const float d = S[q][q] - S[p][p];
-    const float b2 = 2.f * b;
-    const float r2 = fmaf(d, d, b2 * b2);
-    const float rt = r2 * rsqrtf(r2);
-    const float tt = __fdividef(d >= 0.f ? b2 : -b2, fabsf(d) + rt);
-    c = rsqrtf(fmaf(tt, tt, 1.f));
-    sn = tt * c;
-  }
+  const float d = S[q][q] - S[p][p];
+  const float b2 = 2.f * b;
+  const float rs = rsqrtf(fmaf(d, d, b2 * b2));
+  const float cos2 = fabsf(d) * rs;
+  const float sin2 = (d >= 0.f ? b2 : -b2) * rs;
+  const float h = fmaf(0.5f, cos2, 0.5f);
+  const float qh = rsqrtf(h);
+  c = b != 0.f ? h * qh : 1.f;
+  sn = b != 0.f ? 0.5f * sin2 * qh : 0.f;
 }
 
-// One cyclic sweep over the pair subproblem S (32 x 32, in shared memory), its rotations
-// accumulated into W (identity on entry) and stored as the pair's rotation Wbuf[k].
-__device__ __forceinline__ void bj_pair_sweep(float (&S)[2 * BJ][2 * BJ + 1], float (&W)[2 * BJ][2 * BJ + 1],
+// player of position x in round rr of the round-robin schedule of 2 BJ players
+// (rr_player without the division: x - 1 + rr < 2 (2 BJ - 1))
+template <int BJ>
+__device__ __forceinline__ int bj_player(int x, int rr) {
+  int v = x - 1 + rr;
+  v = v >= 2 * BJ - 1 ? v - (2 * BJ - 1) : v;
+  return x == 0 ? 0 : 1 + v;
+}
+
+// One cyclic sweep over the pair subproblem S (2BJ x 2BJ, in shared memory), its
+// rotations accumulated into W (identity on entry) and stored as the pair's rotation
+// Wbuf[k].  BJ^2 threads.  S and W are double-buffered: inner round rr reads buffer
+// rr & 1 and writes the other, so a round needs one barrier.
+template <int BJ>
+__device__ __forceinline__ void bj_pair_sweep(float (&S)[2][2 * BJ][2 * BJ + 1], float (&W)[2][2 * BJ][2 * BJ + 1],
                                               float* __restrict__ Wbuf, int k) {
-  // the inner round-robin schedule: (p, q) of pair x in round rr, packed p | q << 8
-  __shared__ unsigned short sched[2 * BJ - 1][BJ];
   const int t = threadIdx.x;
-  for (int e = t; e < (2 * BJ - 1) * BJ; e += blockDim.x) {
-    const int rr = e / BJ, x = e % BJ;
-    sched[rr][x] = (unsigned short)(rr_player(x, rr, 2 * BJ) | (rr_player(2 * BJ - 1 - x, rr, 2 * BJ) << 8));
-  }
-  __syncthreads();
   // thread (x, y): the 2 x 2 block (pair x rows, pair y columns) of S and rows 2y, 2y+1
   // of W's pair-x columns.  Every thread computes the two rotations it needs from the
   // same entries (identical arithmetic, identical results), so a round is one read
   // phase and one write phase.
   const int x = t % BJ, y = t / BJ;
   for (int rr = 0; rr < 2 * BJ - 1; ++rr) {
-    const unsigned sx_ = sched[rr][x], sy_ = sched[rr][y];
-    const int i0 = sx_ & 0xFF, i1 = sx_ >> 8, j0 = sy_ & 0xFF, j1 = sy_ >> 8;
+    const int cb = rr & 1, nb = cb ^ 1;
+    // the inner round-robin schedule: pair x of round rr is (i0, i1), pair y is (j0, j1)
+    const int i0 = bj_player<BJ>(x, rr), i1 = bj_player<BJ>(2 * BJ - 1 - x, rr);
+    const int j0 = bj_player<BJ>(y, rr), j1 = bj_player<BJ>(2 * BJ - 1 - y, rr);
     float cx, sx, cy, sy;
-    bj_rot(S, i0, i1, cx, sx);
-    bj_rot(S, j0, j1, cy, sy);
-    const float a00 = S[i0][j0], a01 = S[i0][j1], a10 = S[i1][j0], a11 = S[i1][j1];
-    const float w00 = W[2 * y][i0], w01 = W[2 * y][i1], w10 = W[2 * y + 1][i0], w11 = W[2 * y + 1][i1];
+    bj_rot<BJ>(S[cb], i0, i1, cx, sx);
+    bj_rot<BJ>(S[cb], j0, j1, cy, sy);
+    const float a00 = S[cb][i0][j0], a01 = S[cb][i0][j1], a10 = S[cb][i1][j0], a11 = S[cb][i1][j1];
+    const float w00 = W[cb][2 * y][i0], w01 = W[cb][2 * y][i1], w10 = W[cb][2 * y + 1][i0],
+                w11 = W[cb][2 * y + 1][i1];
     // rows: [r0; r1] = [[c, -s], [s, c]] [a0; a1] (the rotation [[c, s], [-s, c]] transposed)
     const float b00 = cx * a00 - sx * a10, b01 = cx * a01 - sx * a11;
     const float b10 = sx * a00 + cx * a10, b11 = sx * a01 + cx * a11;
-    __syncthreads();
-    S[i0][j0] = cy * b00 - sy * b01;
-    S[i0][j1] = sy * b00 + cy * b01;
-    S[i1][j0] = cy * b10 - sy * b11;
-    S[i1][j1] = sy * b10 + cy * b11;
+    // the threads' 2 x 2 blocks cover every entry of S and of W: the next buffers are
+    // written whole
+    S[nb][i0][j0] = cy * b00 - sy * b01;
+    S[nb][i0][j1] = sy * b00 + cy * b01;
+    S[nb][i1][j0] = cy * b10 - sy * b11;
+    S[nb][i1][j1] = sy * b10 + cy * b11;
     // W <- W R (columns i0, i1)
-    W[2 * y][i0] = cx * w00 - sx * w01;
-    W[2 * y][i1] = sx * w00 + cx * w01;
-    W[2 * y + 1][i0] = cx * w10 - sx * w11;
-    W[2 * y + 1][i1] = sx * w10 + cx * w11;
+    W[nb][2 * y][i0] = cx * w00 - sx * w01;
+    W[nb][2 * y][i1] = sx * w00 + cx * w01;
+    W[nb][2 * y + 1][i0] = cx * w10 - sx * w11;
+    W[nb][2 * y + 1][i1] = sx * w10 + cx * w11;
     __syncthreads();
   }
+  constexpr int fb = (2 * BJ - 1) & 1;   // the buffer of the last round's writes
   float* Wk = Wbuf + (size_t)k * 4 * BJ * BJ;
-  for (int e = t; e < 4 * BJ * BJ; e += 256) Wk[e] = W[e % (2 * BJ)][e / (2 * BJ)];
+  for (int e = t; e < 4 * BJ * BJ; e += BJ * BJ) Wk[e] = W[fb][e % (2 * BJ)][e / (2 * BJ)];
   __syncthreads();
 }
 
-// One CTA per block pair: W = the product of the rotations of one cyclic sweep over the
-// pair's 32 x 32 subproblem (rotations as jacobi_rot; indices >= n give the identity).
-__device__ __forceinline__ void bj_pair_body(const float* __restrict__ A, float* __restrict__ Wbuf, int n, int nbk,
-                                             int r, int k) {
-  __shared__ float S[2 * BJ][2 * BJ + 1];
-  __shared__ float W[2 * BJ][2 * BJ + 1];
+// One CTA (BJ^2 threads) per block pair: W = the product of the rotations of one cyclic
+// sweep over the pair's 2BJ x 2BJ subproblem (rotations as jacobi_rot).
+template <int BJ>
+__global__ void __launch_bounds__(BJ * BJ) k_bj_pair(const float* __restrict__ A, float* __restrict__ Wbuf, int n,
+                                                     int nbk, int r) {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  __shared__ float S[2][2 * BJ][2 * BJ + 1];
+  __shared__ float W[2][2 * BJ][2 * BJ + 1];
+  const int k = blockIdx.x;
   const int bp = rr_player(k, r, nbk), bq = rr_player(nbk - 1 - k, r, nbk);
   const int t = threadIdx.x;
-  for (int e = t; e < 4 * BJ * BJ; e += 256) {
+  for (int e = t; e < 4 * BJ * BJ; e += BJ * BJ) {
     const int i = e % (2 * BJ), j = e / (2 * BJ);
-    const int gi = bj_index(i, bp, bq), gj = bj_index(j, bp, bq);
-    S[i][j] = (gi < n && gj < n) ? A[gi + (long long)gj * n] : (gi == gj ? 1.f : 0.f);
-    W[i][j] = (i == j) ? 1.f : 0.f;
+    const int gi = bj_index<BJ>(i, bp, bq), gj = bj_index<BJ>(j, bp, bq);
+    S[0][i][j] = A[gi + (long long)gj * n];
+    W[0][i][j] = (i == j) ? 1.f : 0.f;
   }
   __syncthreads();
-  bj_pair_sweep(S, W, Wbuf, k);
-}
-
-__global__ void __launch_bounds__(256) k_bj_pair(const float* __restrict__ A, float* __restrict__ Wbuf, int n,
-                                                 int nbk, int r) {
-  asm volatile("griddepcontrol.wait;\n" ::: "memory");
-  bj_pair_body(A, Wbuf, n, nbk, r, blockIdx.x);
+  bj_pair_sweep<BJ>(S, W, Wbuf, k);
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
 
-// A' = J^T A J (into An) and V <- V J for J = blockdiag(W_k): CTAs [0, np^2) compute the
-// 32 x 32 block (pair a, pair b) of A' = W_a^T A[I_a, I_b] W_b; the others the 32-row
-// blocks of V[:, I_k] W_k.
-__device__ __forceinline__ void bj_apply_body(const float* __restrict__ A, float* __restrict__ An, float* V,
-                                              const float* __restrict__ Wbuf, int n, int nbk, int r, int bid) {
-  // X rows of 33 floats (its column reads vary the row across a warp); the operands read
-  // as one broadcast float4 per k (all lanes of a warp share j0) in rows of 36
-  __shared__ float X[2 * BJ][2 * BJ + 1];
-  __shared__ __align__(16) float Wl[2 * BJ][2 * BJ + 4];
-  __shared__ __align__(16) float Wr[2 * BJ][2 * BJ + 4];
-  __shared__ __align__(16) float Tm[2 * BJ][2 * BJ + 4];
+// Shared memory of k_bj_apply: X rows of 2BJ + 1 floats (its column reads vary the row
+// across a warp); the operands in rows of 2BJ + 4, read as broadcast float4 (all lanes of
+// a warp share the column group)
+template <int BJ>
+constexpr size_t bj_apply_smem() {
+  return (size_t)(((2 * BJ) * (2 * BJ + 1) + 3) & ~3) * 4 + 3 * (size_t)(2 * BJ) * (2 * BJ + 4) * 4;
+}
+
+// A' = J^T A J (into An; part 0) or V <- V J (part 1) for J = blockdiag(W_k), 256 threads.
+// Part 0: CTA (a, b), a <= b (np (np + 1) / 2 CTAs), computes the 2BJ x 2BJ block
+// A'[I_a, I_b] = W_a^T A[I_a, I_b] W_b and stores it and its transpose A'[I_b, I_a] (A
+// stays exactly symmetric).  Part 1: CTA (row block, k) the 2BJ-row block of V[:, I_k] W_k.
+// Thread (i, column group): CPT entries (row i, CPT consecutive columns) of each product.
+template <int BJ>
+__global__ void __launch_bounds__(256) k_bj_apply(const float* __restrict__ A, float* __restrict__ An, float* V,
+                                                  const float* __restrict__ Wbuf, int n, int nbk, int r, int part) {
+  constexpr int NI = 2 * BJ, NW = 2 * BJ + 4, CPT = NI * NI / 256;
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  extern __shared__ __align__(16) float bj_sm[];
+  float(*X)[NI + 1] = reinterpret_cast<float(*)[NI + 1]>(bj_sm);
+  float(*Wl)[NW] = reinterpret_cast<float(*)[NW]>(bj_sm + ((NI * (NI + 1) + 3) & ~3));   // 16-byte aligned rows
+  float(*Wr)[NW] = Wl + NI;
+  float(*Tm)[NW] = Wr + NI;
   const int np = nbk / 2;
-  const int t = threadIdx.x;
-  const int i = t % (2 * BJ), j0 = (t / (2 * BJ)) * 4;
-  if (bid < np * np) {
-    const int ka = bid % np, kb = bid / np;
+  const int t = threadIdx.x, bid = blockIdx.x;
+  const int i = t % NI, j0 = (t / NI) * CPT;
+  if (part == 0) {
+    // bid = kb (kb + 1) / 2 + ka, ka <= kb
+    int kb = (int)((sqrtf(8.f * (float)bid + 1.f) - 1.f) * 0.5f);
+    while ((kb + 1) * (kb + 2) / 2 <= bid) ++kb;
+    while (kb * (kb + 1) / 2 > bid) --kb;
+    const int ka = bid - kb * (kb + 1) / 2;
     const int ap = rr_player(ka, r, nbk), aq = rr_player(nbk - 1 - ka, r, nbk);
     const int bp = rr_player(kb, r, nbk), bq = rr_player(nbk - 1 - kb, r, nbk);
-    const float* Wa = Wbuf + (size_t)ka * 4 * BJ * BJ;
-    const float* Wb = Wbuf + (size_t)kb * 4 * BJ * BJ;
-    for (int e = t; e < 4 * BJ * BJ; e += 256) {
-      const int ii = e % (2 * BJ), jj = e / (2 * BJ);
-      const int gi = bj_index(ii, ap, aq), gj = bj_index(jj, bp, bq);
-      X[ii][jj] = (gi < n && gj < n) ? A[gi + (long long)gj * n] : 0.f;
+    const float* Wa = Wbuf + (size_t)ka * NI * NI;
+    const float* Wb = Wbuf + (size_t)kb * NI * NI;
+    for (int e = t; e < NI * NI; e += 256) {
+      const int ii = e % NI, jj = e / NI;
+      X[ii][jj] = A[bj_index<BJ>(ii, ap, aq) + (long long)bj_index<BJ>(jj, bp, bq) * n];
       Wl[ii][jj] = Wa[e];
       Wr[ii][jj] = Wb[e];
     }
     __syncthreads();
-    // each thread: 4 entries (row i, columns j0 .. j0+3) of T = X W_b, then of W_a^T T;
-    // a warp covers the 32 rows of a column, so its stores into column-major A' coalesce
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 8
-    for (int l = 0; l < 2 * BJ; ++l) {
-      const float x = X[i][l];
-      const float4 w = *reinterpret_cast<const float4*>(&Wr[l][j0]);
-      acc[0] = fmaf(x, w.x, acc[0]);
-      acc[1] = fmaf(x, w.y, acc[1]);
-      acc[2] = fmaf(x, w.z, acc[2]);
-      acc[3] = fmaf(x, w.w, acc[3]);
-    }
-    *reinterpret_cast<float4*>(&Tm[i][j0]) = make_float4(acc[0], acc[1], acc[2], acc[3]);
-    __syncthreads();
-    float o[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 8
-    for (int l = 0; l < 2 * BJ; ++l) {
-      const float wl = Wl[l][i];
-      const float4 tv = *reinterpret_cast<const float4*>(&Tm[l][j0]);
-      o[0] = fmaf(wl, tv.x, o[0]);
-      o[1] = fmaf(wl, tv.y, o[1]);
-      o[2] = fmaf(wl, tv.z, o[2]);
-      o[3] = fmaf(wl, tv.w, o[3]);
-    }
-    const int gi = bj_index(i, ap, aq);
+    // T = X W_b, then W_a^T T; a warp covers consecutive rows of a column group, so its
+    // stores into column-major A' coalesce
+    float acc[CPT];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int gj = bj_index(j0 + u, bp, bq);
-      if (gi < n && gj < n) An[gi + (long long)gj * n] = o[u];
+    for (int u = 0; u < CPT; ++u) acc[u] = 0.f;
+#pragma unroll 8
+    for (int l = 0; l < NI; ++l) {
+      const float x = X[i][l];
+#pragma unroll
+      for (int u = 0; u < CPT; u += 4) {
+        const float4 w = *reinterpret_cast<const float4*>(&Wr[l][j0 + u]);
+        acc[u] = fmaf(x, w.x, acc[u]);
+        acc[u + 1] = fmaf(x, w.y, acc[u + 1]);
+        acc[u + 2] = fmaf(x, w.z, acc[u + 2]);
+        acc[u + 3] = fmaf(x, w.w, acc[u + 3]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < CPT; u += 4)
+      *reinterpret_cast<float4*>(&Tm[i][j0 + u]) = make_float4(acc[u], acc[u + 1], acc[u + 2], acc[u + 3]);
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) acc[u] = 0.f;
+#pragma unroll 8
+    for (int l = 0; l < NI; ++l) {
+      const float wl = Wl[l][i];
+#pragma unroll
+      for (int u = 0; u < CPT; u += 4) {
+        const float4 tv = *reinterpret_cast<const float4*>(&Tm[l][j0 + u]);
+        acc[u] = fmaf(wl, tv.x, acc[u]);
+        acc[u + 1] = fmaf(wl, tv.y, acc[u + 1]);
+        acc[u + 2] = fmaf(wl, tv.z, acc[u + 2]);
+        acc[u + 3] = fmaf(wl, tv.w, acc[u + 3]);
+      }
+    }
+    const int gi = bj_index<BJ>(i, ap, aq);
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) An[gi + (long long)bj_index<BJ>(j0 + u, bp, bq) * n] = acc[u];
+    if (ka != kb) {
+#pragma unroll
+      for (int u = 0; u < CPT; ++u) An[bj_index<BJ>(j0 + u, bp, bq) + (long long)gi * n] = acc[u];
     }
   } else {
-    const int vb = bid - np * np;
-    const int rows = (n + 2 * BJ - 1) / (2 * BJ);
+    const int vb = bid;
+    const int rows = n / NI;
     const int rb = vb % rows, k = vb / rows;
     const int bp = rr_player(k, r, nbk), bq = rr_player(nbk - 1 - k, r, nbk);
-    const float* Wk = Wbuf + (size_t)k * 4 * BJ * BJ;
-    for (int e = t; e < 4 * BJ * BJ; e += 256) {
-      const int ii = e % (2 * BJ), jj = e / (2 * BJ);
-      const int gr = rb * 2 * BJ + ii, gj = bj_index(jj, bp, bq);
-      X[ii][jj] = (gr < n && gj < n) ? V[gr + (long long)gj * n] : 0.f;
+    const float* Wk = Wbuf + (size_t)k * NI * NI;
+    for (int e = t; e < NI * NI; e += 256) {
+      const int ii = e % NI, jj = e / NI;
+      X[ii][jj] = V[rb * NI + ii + (long long)bj_index<BJ>(jj, bp, bq) * n];
       Wl[ii][jj] = Wk[e];
     }
     __syncthreads();
-    const int gr = rb * 2 * BJ + i;
-    float o[4] = {0.f, 0.f, 0.f, 0.f};
+    const int gr = rb * NI + i;
+    float acc[CPT];
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) acc[u] = 0.f;
 #pragma unroll 8
-    for (int l = 0; l < 2 * BJ; ++l) {
+    for (int l = 0; l < NI; ++l) {
       const float x = X[i][l];
-      const float4 w = *reinterpret_cast<const float4*>(&Wl[l][j0]);
-      o[0] = fmaf(x, w.x, o[0]);
-      o[1] = fmaf(x, w.y, o[1]);
-      o[2] = fmaf(x, w.z, o[2]);
-      o[3] = fmaf(x, w.w, o[3]);
+#pragma unroll
+      for (int u = 0; u < CPT; u += 4) {
+        const float4 w = *reinterpret_cast<const float4*>(&Wl[l][j0 + u]);
+        acc[u] = fmaf(x, w.x, acc[u]);
+        acc[u + 1] = fmaf(x, w.y, acc[u + 1]);
+        acc[u + 2] = fmaf(x, w.z, acc[u + 2]);
+        acc[u + 3] = fmaf(x, w.w, acc[u + 3]);
+      }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int gj = bj_index(j0 + u, bp, bq);
-      if (gr < n && gj < n) V[gr + (long long)gj * n] = o[u];
-    }
+    for (int u = 0; u < CPT; ++u) V[gr + (long long)bj_index<BJ>(j0 + u, bp, bq) * n] = acc[u];
   }
   __syncthreads();
-}
-
-__global__ void __launch_bounds__(256) k_bj_apply(const float* __restrict__ A, float* __restrict__ An, float* V,
-                                                  const float* __restrict__ Wbuf, int n, int nbk, int r) {
-  asm volatile("griddepcontrol.wait;\n" ::: "memory");
-  bj_apply_body(A, An, V, Wbuf, n, nbk, r, blockIdx.x);
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
 
@@ -1012,27 +1044,38 @@ sparc_status chol_inverse(sparc_ctx* ctx, TW* A, TW* Li, int n, TW* Dinv, TW* tm
 }
 
 // Parallel cyclic Jacobi on the n x n Hermitian A (ping-pong A0/A1, eigenvectors in V),
-// two sweeps per replay of a captured CUDA graph, until off(A) <= tol * |A|.
+// one sweep per replay of a captured CUDA graph (one graph from each buffer: a sweep
+// has an odd number of rounds), until off(A)^2 <= tol |A|^2 or off(A) stagnates at the
+// rounding floor of the element type.
 // Whether the block Jacobi method takes an n x n problem of element type TJ.
 template <class TJ>
 constexpr bool bj_type() { return std::is_same<TJ, float>::value; }
-inline bool bj_usable(int n) { return n % (2 * BJ) == 0 && n >= 4 * BJ; }
+// Block size of the block method for an n x n problem: 16 where n is a multiple of 32
+// (at least two block pairs); 0: the scalar method.  (Blocks of 32 were measured 2x
+// slower at n = 512: the 64 x 64 inner sweep's 63 rounds on 1024 threads dominate.)
+inline int bj_size(int n) { return (n % 32 == 0 && n >= 64) ? 16 : 0; }
 
 template <class TJ>
 sparc_status jacobi(sparc_ctx* ctx, TJ* A0, TJ* A1, TJ* V, int n, double tol, int max_sweeps, double* scal,
                     TJ** result, int* sweeps_out, cudaStream_t st, float* Wbuf = nullptr) {
-  const bool blockj = bj_type<TJ>() && Wbuf != nullptr && bj_usable(n);
+  const int bjs = (bj_type<TJ>() && Wbuf != nullptr) ? bj_size(n) : 0;
+  const bool blockj = bjs > 0;
   const int npad = n + (n & 1);
   const int half = npad / 2;
   const int nblocks = ((half + 15) / 16) * ((half + 15) / 16) + ((n + 63) / 64) * ((half + 3) / 4);
-  const int nbk = n / BJ, npair = nbk / 2;
-  // two sweeps per graph: 2 (npad - 1) scalar rounds, or 2 (nbk - 1) block rounds of two launches
-  const int rounds = blockj ? 2 * (nbk - 1) : 2 * (npad - 1);
+  const int nbk = blockj ? n / bjs : 0, npair = nbk / 2;
+  // one sweep per graph: npad - 1 scalar rounds, or nbk - 1 block rounds of two launches
+  const int rounds = blockj ? nbk - 1 : npad - 1;
   if (!ctx->cap_stream) {
     SPARC_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
   }
-  const auto key = std::make_tuple((int)sizeof(TJ) * 2 + (int)Tr<TJ>::cplx + (blockj ? 64 : 0), n, (void*)A0,
-                                   (void*)A1, (void*)V);
+  if (blockj && !ctx->cap_stream2) {
+    SPARC_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream2, cudaStreamNonBlocking));
+  }
+  // the sweep graph that starts from buffer par (0: A0, 1: A1); its result lands in the other
+  auto sweep_graph = [&](int par, cudaGraphExec_t* out) -> sparc_status {
+  const auto key = std::make_tuple((int)sizeof(TJ) * 2 + (int)Tr<TJ>::cplx + 64 * bjs + 4096 * par, n,
+                                   (void*)A0, (void*)A1, (void*)V);
   cudaGraphExec_t ge = nullptr;
   auto it = ctx->graphs.find(key);
   if (it != ctx->graphs.end()) {
@@ -1040,8 +1083,8 @@ sparc_status jacobi(sparc_ctx* ctx, TJ* A0, TJ* A1, TJ* V, int n, double tol, in
   } else {
     cudaGraph_t g = nullptr;
     SPARC_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-    TJ* a = A0;
-    TJ* b = A1;
+    TJ* a = par ? A1 : A0;
+    TJ* b = par ? A0 : A1;
     // each round may begin launching while the previous one finishes (programmatic
     // dependent launch); it waits for that round's results before it reads A or V
     cudaLaunchAttribute attr[1];
@@ -1055,23 +1098,51 @@ sparc_status jacobi(sparc_ctx* ctx, TJ* A0, TJ* A1, TJ* V, int n, double tol, in
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaError_t le = cudaSuccess;
+    // block method: the V updates run on a second branch (cap_stream2), beside the next
+    // round's pair solves, which use few SMs; the rotations are double-buffered (round r
+    // in Wbuf half r & 1), and the pair solve of round r + 2 waits for the V update of r
+    cudaEvent_t evp = nullptr, evv[2] = {nullptr, nullptr};
+    if (blockj) {
+      le = cudaEventCreateWithFlags(&evp, cudaEventDisableTiming);
+      if (le == cudaSuccess) le = cudaEventCreateWithFlags(&evv[0], cudaEventDisableTiming);
+      if (le == cudaSuccess) le = cudaEventCreateWithFlags(&evv[1], cudaEventDisableTiming);
+    }
+    const size_t wh = (size_t)npair * 4 * 16 * 16;   // floats of one round's rotations
     for (int r = 0; r < rounds && le == cudaSuccess; ++r) {
       if (blockj) {
         if constexpr (bj_type<TJ>()) {
-          cudaLaunchConfig_t c1 = cfg, c2 = cfg;
+          cudaLaunchConfig_t c1 = cfg, c2 = cfg, c3 = cfg;
           c1.gridDim = dim3((unsigned)npair);
-          c2.gridDim = dim3((unsigned)(npair * npair + ((n + 2 * BJ - 1) / (2 * BJ)) * npair));
+          c1.blockDim = dim3((unsigned)(bjs * bjs));
+          c2.gridDim = dim3((unsigned)(npair * (npair + 1) / 2));
+          c2.dynamicSmemBytes = bj_apply_smem<16>();
+          c3.gridDim = dim3((unsigned)((n / (2 * bjs)) * npair));
+          c3.dynamicSmemBytes = bj_apply_smem<16>();
+          c3.stream = ctx->cap_stream2;
           const int rb = r % (nbk - 1);
-          le = cudaLaunchKernelEx(&c1, k_bj_pair, (const float*)a, Wbuf, n, nbk, rb);
+          float* Wr = Wbuf + (r & 1) * wh;
+          if (r >= 2) le = cudaStreamWaitEvent(ctx->cap_stream, evv[r & 1], 0);
+          if (le == cudaSuccess) le = cudaLaunchKernelEx(&c1, k_bj_pair<16>, (const float*)a, Wr, n, nbk, rb);
+          if (le == cudaSuccess) le = cudaEventRecord(evp, ctx->cap_stream);
           if (le == cudaSuccess)
-            le = cudaLaunchKernelEx(&c2, k_bj_apply, (const float*)a, (float*)b, (float*)V, (const float*)Wbuf, n, nbk,
-                                    rb);
+            le = cudaLaunchKernelEx(&c2, k_bj_apply<16>, (const float*)a, (float*)b, (float*)V, (const float*)Wr, n,
+                                    nbk, rb, 0);
+          if (le == cudaSuccess) le = cudaStreamWaitEvent(ctx->cap_stream2, evp, 0);
+          if (le == cudaSuccess)
+            le = cudaLaunchKernelEx(&c3, k_bj_apply<16>, (const float*)a, (float*)b, (float*)V, (const float*)Wr, n,
+                                    nbk, rb, 1);
+          if (le == cudaSuccess) le = cudaEventRecord(evv[r & 1], ctx->cap_stream2);
         }
       } else {
         le = cudaLaunchKernelEx(&cfg, k_jacobi_round<TJ>, (const TJ*)a, b, V, n, npad, r % (npad - 1));
       }
       std::swap(a, b);
     }
+    // join the V branch
+    if (blockj && le == cudaSuccess) le = cudaStreamWaitEvent(ctx->cap_stream, evv[(rounds - 1) & 1], 0);
+    if (evp) cudaEventDestroy(evp);
+    for (cudaEvent_t ev : evv)
+      if (ev) cudaEventDestroy(ev);
     if (le != cudaSuccess) {
       cudaStreamEndCapture(ctx->cap_stream, &g);
       if (g) cudaGraphDestroy(g);
@@ -1083,29 +1154,39 @@ sparc_status jacobi(sparc_ctx* ctx, TJ* A0, TJ* A1, TJ* V, int n, double tol, in
     SPARC_CUDA(ctx, e);
     ctx->graphs[key] = ge;
   }
+  *out = ge;
+  return SPARC_OK;
+  };
+  cudaGraphExec_t ges[2];
+  for (int par = 0; par < 2; ++par) {
+    const sparc_status s = sweep_graph(par, &ges[par]);
+    if (s != SPARC_OK) return s;
+  }
   double hs[2];
   double prev_off = -1.0;
   int sweeps = 0;
   bool converged = false;
   cudaEvent_t tj = timing_begin(ctx, st);
   while (sweeps < max_sweeps && !converged) {
-    SPARC_CUDA(ctx, cudaGraphLaunch(ge, st));
+    const int par = sweeps & 1;
+    SPARC_CUDA(ctx, cudaGraphLaunch(ges[par], st));
     ctx->launches += blockj ? 2 * rounds : rounds;
     ++ctx->graph_launches;
-    sweeps += 2;
+    ++sweeps;
     const int nbo = ceil_div(n, 8);
-    k_offnorm<TJ><<<nbo, 256, 0, st>>>(A0, n, scal + 2);
+    k_offnorm<TJ><<<nbo, 256, 0, st>>>(par ? A0 : A1, n, scal + 2);
     k_offnorm_sum<<<1, 32, 0, st>>>(scal + 2, nbo, scal);
     ctx->launches += 2;
     SPARC_CUDA(ctx, cudaMemcpyAsync(hs, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     SPARC_CUDA(ctx, cudaStreamSynchronize(st));
     // converged, or stagnated at the rounding floor of the element type (Jacobi
-    // converges quadratically, so two sweeps that do not halve off(A) are at the floor)
-    converged = !(hs[0] > tol * hs[1]) || (sweeps >= 4 && prev_off >= 0.0 && hs[0] > 0.5 * prev_off);
+    // converges quadratically, so from the fourth sweep on a sweep that leaves off(A)^2
+    // above 0.7 of its previous value is at the floor)
+    converged = !(hs[0] > tol * hs[1]) || (sweeps >= 4 && prev_off >= 0.0 && hs[0] > 0.7 * prev_off);
     prev_off = hs[0];
   }
   timing_end(ctx, TK_JAC, tj, st);
-  *result = A0;   // an even number of rounds leaves the matrix in A0
+  *result = (sweeps & 1) ? A1 : A0;   // each sweep moves the matrix to the other buffer
   *sweeps_out = sweeps;
   if (!converged) return fail(ctx, SPARC_ERR_NO_CONVERGENCE, "Jacobi sweep limit reached");
   return SPARC_OK;
@@ -1134,7 +1215,9 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
   const size_t w1b = TCP ? hub : 0;   // U1, the orthonormalised basis
   const size_t gsb = apply_scratch_bytes(H, DtypeOf<T>::v, ns);   // projection scratch of the H-apply
   // rotations of the block Jacobi rounds (FP32 subproblems of the mixed mode)
-  const size_t wjb = (bj_type<TS>() && bj_usable(ns)) ? align256((size_t)(ns / BJ / 2) * 4 * BJ * BJ * sizeof(float)) : 0;
+  // (block size b: ns / b / 2 pairs of 4 b^2 floats, that is 2 b ns floats, twice: the
+  // rotations of two consecutive rounds)
+  const size_t wjb = (bj_type<TS>() && bj_size(ns) > 0) ? align256((size_t)4 * BJ_MAX * ns * sizeof(float)) : 0;
   const size_t extra = hub + 2 * partb + 10 * sm + dinvb + align256(nn * es) + 3 * align256(nn * sizeof(TS)) +
                        align256(ns * sizeof(double)) + tcb + w1b + gsb + wjb + 256;
   BlockWs w;
