@@ -600,11 +600,10 @@ __device__ __forceinline__ Item decode(const Args& a, const KArgsT<CX>& ka, int 
 // pipeline ends the kernel quickly instead of timing out at every step.  A dual item
 // loads the frames (tiles) and Yprev tiles of both halves.
 template <bool CX>
-__device__ __forceinline__ bool produce(const Args& a, const KArgsT<CX>& ka, const MapsT<CX>& mp, unsigned char* smem,
-                                       uint64_t* bars, int item, int s, int g, const int* recs, bool wait) {
+__device__ __forceinline__ bool produce(const Args& a, const MapsT<CX>& mp, unsigned char* smem, uint64_t* bars,
+                                       const Item& it, int s, int g, const int* recs, bool wait) {
   using L = Lay<CX>;
   const int lane = threadIdx.x & 31;
-  const Item it = decode<CX>(a, ka, item);
   const int blk = it.blk;
   const int c0 = CX ? 8 * it.h : 0;   // first float of the node's half (complex: 16 floats a node)
   const int nh = (CX && it.md) ? 2 : 1;
@@ -779,16 +778,24 @@ k_pass_tma(const __grid_constant__ MapsT<CX> mp, const __grid_constant__ Args a,
   const bool producer = warp == NCW - 1;
   bool ok = true;
   // producer cursor: the step DIST ahead of the consumers (item, step, steps of the item, local item index)
+  // (complex: the item decoded once per item, its per-k fields coming from the parameter
+  // space; FP32: decoded at every step, a few integer operations)
   int pitem = blockIdx.x, ps = 0, pli = 0;
+  Item pit;
+  if constexpr (CX) pit = decode<CX>(a, ka, pitem < a.nitems ? pitem : 0);
   int pS = pitem < a.nitems ? decode<CX>(a, ka, pitem).nz + 2 * R : 0;
   auto produce_next = [&](int gp) {
     if (pitem >= a.nitems) return;
-    ok &= produce<CX>(a, ka, mp, smem, bars, pitem, ps, gp, recs + (pli % 3) * RECN, ok);
+    if constexpr (CX) ok &= produce<CX>(a, mp, smem, bars, pit, ps, gp, recs + (pli % 3) * RECN, ok);
+    else ok &= produce<CX>(a, mp, smem, bars, decode<CX>(a, ka, pitem), ps, gp, recs + (pli % 3) * RECN, ok);
     if (++ps == pS) {
       ps = 0;
       ++pli;
       pitem += gridDim.x;
-      pS = pitem < a.nitems ? decode<CX>(a, ka, pitem).nz + 2 * R : 0;
+      if (pitem < a.nitems) {
+        if constexpr (CX) pit = decode<CX>(a, ka, pitem);
+      }
+      pS = pitem < a.nitems ? (CX ? pit.nz : decode<CX>(a, ka, pitem).nz) + 2 * R : 0;
     }
   };
   if (producer)
