@@ -759,24 +759,30 @@ __global__ void k_offnorm_sum(const double* part, int nb, double* out) {
 
 // Ascending order of the diagonal: eig[rank] = A_ii, perm[rank] = i (ties broken by
 // index, so the order is deterministic); vals != nullptr: sort by vals[i] instead of
-// the diagonal of A.  One CTA; the keys go through shared memory (n <= 1024).
+// the diagonal of A.  Each CTA holds all n keys in shared memory (n <= 1024) as
+// order-preserving 64-bit integers (integer compares: the FP64 ones run at the FP64
+// rate) and ranks 128 of them.
+__device__ __forceinline__ unsigned long long sort_key(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
+}
 template <class TW>
-__global__ void __launch_bounds__(1024) k_sort(const TW* __restrict__ A, const double* __restrict__ vals, int n,
-                                               double* __restrict__ eig, int* __restrict__ perm) {
-  __shared__ double key[1024];
+__global__ void __launch_bounds__(128) k_sort(const TW* __restrict__ A, const double* __restrict__ vals, int n,
+                                              double* __restrict__ eig, int* __restrict__ perm) {
+  __shared__ unsigned long long key[1024];
   for (int i = threadIdx.x; i < n; i += blockDim.x)
-    key[i] = vals ? vals[i] : (double)Tr<TW>::re(A[i + (long long)i * n]);
+    key[i] = sort_key(vals ? vals[i] : (double)Tr<TW>::re(A[i + (long long)i * n]));
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double li = key[i];
-    int rank = 0;
-    for (int j = 0; j < n; ++j) {
-      const double lj = key[j];
-      if (lj < li || (lj == li && j < i)) ++rank;
-    }
-    perm[rank] = i;
-    eig[rank] = li;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const unsigned long long ki = key[i];
+  int rank = 0;
+  for (int j = 0; j < n; ++j) {
+    const unsigned long long kj = key[j];
+    rank += (kj < ki || (kj == ki && j < i)) ? 1 : 0;
   }
+  perm[rank] = i;
+  eig[rank] = vals ? vals[i] : (double)Tr<TW>::re(A[i + (long long)i * n]);
 }
 
 // Q[:, rank] = V[:, perm[rank]] (n x n), over the whole GPU
@@ -834,15 +840,21 @@ __global__ void k_reduce_axpby(const TW* __restrict__ P, int nz, int M, int N, d
 // lam[i] = Re(q_i^H z_i) / Re(q_i^H q_i)   (FP64 Rayleigh quotients, one column per thread)
 template <class TW>
 __global__ void k_rayleigh(const TW* __restrict__ Qm, const TW* __restrict__ Z, int n, double* lam) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per column: lanes over k (coalesced), partial sums reduced in a fixed order
+  const int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (i >= n) return;
   double num = 0.0, den = 0.0;
-  for (int k = 0; k < n; ++k) {
+  for (int k = lane; k < n; k += 32) {
     const TW q = Qm[k + (long long)i * n];
     num += Tr<TW>::re(mul(Tr<TW>::conj(q), Z[k + (long long)i * n]));
     den += Tr<TW>::abs2(q);
   }
-  lam[i] = num / den;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    num += __shfl_xor_sync(0xffffffffu, num, o);
+    den += __shfl_xor_sync(0xffffffffu, den, o);
+  }
+  if (lane == 0) lam[i] = num / den;
 }
 
 // G <- (3 I - G) / 2 (n x n): the Newton-Schulz factor from the Gram G = V^T V.
@@ -1414,7 +1426,7 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
     TW* Ares = nullptr;
     s = jacobi<TW>(ctx, A0, A1, Vj, ns, 1e-26, 40, scal, &Ares, &sweeps, st);
     if (s != SPARC_OK) return s;
-    k_sort<TW><<<1, 1024, 0, st>>>(Ares, nullptr, ns, eig, (int*)scal);
+    k_sort<TW><<<ceil_div(ns, 128), 128, 0, st>>>(Ares, nullptr, ns, eig, (int*)scal);
     k_permute_cols<TW><<<ceil_div(nn, 256), 256, 0, st>>>(Vj, (const int*)scal, ns, Qs);
     ctx->launches += 2;
   } else {
@@ -1447,9 +1459,9 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
       SPARC_CUDA(ctx, (gemm64<TW, false, false>(ctx, ns, ns, ns, A1, ns, T1, ns, Vj, ns, -0.5, 1.5, partH, pcap, st)));
     }
     SPARC_CUDA(ctx, (gemm64<TW, false, false>(ctx, ns, ns, ns, A0, ns, Vj, ns, T1, ns, 1.0, 0.0, partH, pcap, st)));
-    k_rayleigh<TW><<<ceil_div(ns, 128), 128, 0, st>>>(Vj, T1, ns, lam);
+    k_rayleigh<TW><<<ceil_div(ns, 8), 256, 0, st>>>(Vj, T1, ns, lam);
     ++ctx->launches;
-    k_sort<TW><<<1, 1024, 0, st>>>(nullptr, lam, ns, eig, (int*)scal);
+    k_sort<TW><<<ceil_div(ns, 128), 128, 0, st>>>(nullptr, lam, ns, eig, (int*)scal);
     k_permute_cols<TW><<<ceil_div(nn, 256), 256, 0, st>>>(Vj, (const int*)scal, ns, Qs);
     ctx->launches += 2;
   }
