@@ -28,8 +28,8 @@ METRIC = "CheFSI filter throughput (G point-orbital-degrees/s)"
 UNIT = "Gpt-orb-deg/s"
 WORKLOAD = "64^3 grid h=0.4, 128 perturbed-FCC s+p atoms, Ns=512, m=24, Gamma point"
 # DRAM bytes of the filter pass k_pass_tma per block of 8 orbitals per degree on this
-# cell, from one ncu capture of a 32-block launch (701.20 MB read + 287.26 MB written)
-PASS_DRAM_BYTES_PER_BLOCK = (701.196032e6 + 287.256320e6) / 32
+# cell, from one ncu capture of a 32-block launch (701.76 MB read + 292.53 MB written)
+PASS_DRAM_BYTES_PER_BLOCK = (701.758976e6 + 292.532224e6) / 32
 
 
 def _args():
