@@ -432,14 +432,15 @@ sparc_status sparc_scf_forces(sparc_scf* S, sparc_dtype dtype, const void* U, in
  * launch of the kernels below is bracketed by CUDA events recorded on the
  * stream it is launched on.  sparc_timing_read() synchronises those events and
  * returns the summed device time (ms) and the launch count since the last
- * enable; it is valid after the launches have completed.
+ * enable; it is valid after the launches have completed.  Launches issued while
+ * their stream is being captured into a CUDA graph are not timed.
  *   which = 0: the H-apply / Chebyshev-recurrence pass of the generic kernel (k_hpass)
  *   which = 1: the nonlocal projection (k_nl_gather)
  *   which = 2: the Gram products of Rayleigh-Ritz (and sparc_gram_f32)
  *   which = 3: the Cholesky + subspace eigensolve of Rayleigh-Ritz
  *   which = 4: the subspace rotation of Rayleigh-Ritz (and sparc_rotate_f32)
  *   which = 5: the Jacobi sweeps of the subspace eigensolve (inside which = 3)
- *   which = 6: the tiled FP32 / complex64 filter pass (k_pass_f2, k_pass_c2) */
+ *   which = 6: the FP32 / complex64 filter pass (k_pass_tma, k_pass_f2, k_pass_c2) */
 sparc_status sparc_timing_enable(sparc_ctx* ctx, int on);
 sparc_status sparc_timing_read(sparc_ctx* ctx, int which, double* ms_total, int64_t* launches);
 /* Number of kernels this context has launched since it was created (kernels run from

@@ -34,6 +34,14 @@ sparc_status cuda_fail(sparc_ctx* ctx, cudaError_t e, const char* where) {
 
 cudaEvent_t timing_begin(sparc_ctx* ctx, cudaStream_t st) {
   if (!ctx->timing) return nullptr;
+  // launches being captured into a CUDA graph are not timed (an event recorded during
+  // capture would become a graph node, not a timestamp)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (cs != cudaStreamCaptureStatusNone) return nullptr;
   cudaEvent_t e = nullptr;
   if (!ctx->ev_pool.empty()) {
     e = ctx->ev_pool.back();
