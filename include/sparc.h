@@ -435,7 +435,7 @@ sparc_status sparc_scf_forces(sparc_scf* S, sparc_dtype dtype, const void* U, in
  * enable; it is valid after the launches have completed.  Launches issued while
  * their stream is being captured into a CUDA graph are not timed.
  *   which = 0: the H-apply / Chebyshev-recurrence pass of the generic kernel (k_hpass)
- *   which = 1: the nonlocal projection (k_nl_gather)
+ *   which = 1: the nonlocal projection (k_nl_gather, k_gather_rows, k_gather_rows_f2)
  *   which = 2: the Gram products of Rayleigh-Ritz (and sparc_gram_f32)
  *   which = 3: the Cholesky + subspace eigensolve of Rayleigh-Ritz
  *   which = 4: the subspace rotation of Rayleigh-Ritz (and sparc_rotate_f32)
