@@ -587,6 +587,9 @@ def run_ours(args):
     ro_ms, _ = ctx.timing_read("rotation")
     ja_ms, _ = ctx.timing_read("jacobi")
     fp_ms, fp_n = ctx.timing_read("fpass")
+    or_ms, _ = ctx.timing_read("ortho")
+    se_ms, _ = ctx.timing_read("series")
+    ri_ms, _ = ctx.timing_read("ritz")
     sweeps = ctx.last_sweeps()
     ctx.timing(False)
     units = nd * ns * m
@@ -694,7 +697,9 @@ def run_ours(args):
                                   "gather": ga_ms / args.steps,
                                   "gram": gr_ms / args.steps, "chol_eig": ei_ms / args.steps,
                                   "rotation": ro_ms / args.steps, "jacobi": ja_ms / args.steps,
-                                  "jacobi_sweeps": sweeps},
+                                  "jacobi_sweeps": sweeps,
+                                  "eig_parts": {"ortho_chol": or_ms / args.steps, "series": se_ms / args.steps,
+                                                "jacobi": ja_ms / args.steps, "ritz": ri_ms / args.steps}},
         "filter_only": {"value": units / ((fp_ms + ga_ms) / args.steps * 1e-3) / 1e9, "unit": UNIT},
         "clocks": ck, "e2e": e2e, "gpu_launches": int(launches), "cpu_baseline": cpu,
         "filter_fp64_vs_fp32": None if (world > 1 or args.no_fp64) else fp64_filter_throughput(sparc, synth, torch,

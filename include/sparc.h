@@ -440,7 +440,11 @@ sparc_status sparc_scf_forces(sparc_scf* S, sparc_dtype dtype, const void* U, in
  *   which = 3: the Cholesky + subspace eigensolve of Rayleigh-Ritz
  *   which = 4: the subspace rotation of Rayleigh-Ritz (and sparc_rotate_f32)
  *   which = 5: the Jacobi sweeps of the subspace eigensolve (inside which = 3)
- *   which = 6: the FP32 / complex64 filter pass (k_pass_tma, k_pass_f2, k_pass_c2) */
+ *   which = 6: the FP32 / complex64 filter pass (k_pass_tma, k_pass_f2, k_pass_c2)
+ *   which = 7, 8, 9: parts of which = 3 in the mixed mode of FP32 data: the first
+ *     orthonormalisation's FP32 factorisation; the second factorisation (series or
+ *     FP64) with the reduction of H~; the Ritz pairs after the sweeps (Newton-Schulz
+ *     step, Rayleigh quotients, order) */
 sparc_status sparc_timing_enable(sparc_ctx* ctx, int on);
 sparc_status sparc_timing_read(sparc_ctx* ctx, int which, double* ms_total, int64_t* launches);
 /* Number of kernels this context has launched since it was created (kernels run from

@@ -169,7 +169,7 @@ struct sparc_ctx {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   // kernel timing: event pairs per timed kernel class
-  static constexpr int NTIMED = 7;
+  static constexpr int NTIMED = 10;
   long long launches = 0;          // kernels launched by this context (instrumentation)
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[NTIMED];
@@ -177,7 +177,9 @@ struct sparc_ctx {
   // captured Jacobi sweeps, keyed by (element kind, n, buffers)
   cudaStream_t cap_stream = nullptr;
   cudaStream_t cap_stream2 = nullptr;   // the second branch of a captured graph (block Jacobi V updates)
+  cudaStream_t aux_stream[3] = {};       // branches of the FP32 triangular inverse
   std::map<std::tuple<int, int, void*, void*, void*>, cudaGraphExec_t> graphs;
+  std::map<std::tuple<int, int, void*, void*, void*>, long long> graph_kernels;   // kernels per replay
   int last_sweeps = 0;
   double last_ortho_err = -1.0;   // max |U1^T U1 - I| of the last mixed Rayleigh-Ritz (-1: none)
   // the last k-point batch filter, captured as one graph: its arguments and executable
@@ -239,7 +241,11 @@ inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 constexpr int TUNE_SHAPE = 1 << 20;
 
 // Timing hooks: bracket a launch with events on `st` while timing is enabled.
-enum TimedKernel { TK_HPASS = 0, TK_GATHER = 1, TK_GRAM = 2, TK_EIG = 3, TK_ROT = 4, TK_JAC = 5, TK_FPASS = 6 };
+// TK_ORTHO, TK_SERIES, TK_RITZ: parts of TK_EIG (mixed Rayleigh-Ritz): the first
+// orthonormalisation's factorisation, the second factorisation with the reduction of H~,
+// and the Ritz pairs after the sweeps (Newton-Schulz step, Rayleigh quotients, order)
+enum TimedKernel { TK_HPASS = 0, TK_GATHER = 1, TK_GRAM = 2, TK_EIG = 3, TK_ROT = 4, TK_JAC = 5, TK_FPASS = 6,
+                   TK_ORTHO = 7, TK_SERIES = 8, TK_RITZ = 9 };
 cudaEvent_t timing_begin(sparc_ctx* ctx, cudaStream_t st);
 void timing_end(sparc_ctx* ctx, int which, cudaEvent_t begin, cudaStream_t st);
 

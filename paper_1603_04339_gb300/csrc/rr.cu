@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(64) k_chol_blk_f32(float* A, long long lda, fl
                                                      int* status) {
   __shared__ float L[64][65];
   __shared__ float X[64][65];
-  __shared__ float piv;
+  __shared__ float rd[64];   // 1 / L_jj
   __shared__ int bad;
   const int t = threadIdx.x;
   if (t == 0) bad = 0;
@@ -309,20 +309,20 @@ __global__ void __launch_bounds__(64) k_chol_blk_f32(float* A, long long lda, fl
         bad = 1;
         atomicOr(status, STATUS_NOT_POSDEF);
       } else {
-        piv = sqrtf(sv);
+        const float r = rsqrtf(sv);   // L_jj = sv r, 1 / L_jj = r (a few ulp)
+        L[j][j] = sv * r;
+        rd[j] = r;
       }
     }
     __syncthreads();
     if (bad) return;
-    const float p = piv;
-    if (t > j && t < kb) L[t][j] = sv / p;
-    if (t == j) L[j][j] = p;
+    if (t > j && t < kb) L[t][j] = sv * rd[j];
     __syncthreads();
   }
-  // column t of the inverse
+  // column t of the inverse (multiplications by the stored reciprocals of the diagonal)
   if (t < kb) {
     for (int i = 0; i < t; ++i) X[i][t] = 0.f;
-    X[t][t] = 1.f / L[t][t];
+    X[t][t] = rd[t];
     for (int i = t + 1; i < kb; ++i) {
       float s0 = 0.f, s1 = 0.f;
       int k = t;
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(64) k_chol_blk_f32(float* A, long long lda, fl
         s1 = fmaf(L[i][k + 1], X[k + 1][t], s1);
       }
       if (k < i) s0 = fmaf(L[i][k], X[k][t], s0);
-      X[i][t] = -(s0 + s1) / L[i][i];
+      X[i][t] = -(s0 + s1) * rd[i];
     }
   }
   __syncthreads();
@@ -997,6 +997,16 @@ cudaError_t gemm_f32p(sparc_ctx* ctx, int M, int N, int K, const double* A, long
   return cudaGetLastError();
 }
 
+// Li's diagonal blocks (cb x cb, the last one ragged) from the block inverses Dinv.
+template <class TW>
+__global__ void k_copy_diag(const TW* __restrict__ Dinv, int cb, TW* __restrict__ Li, int n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int blk = (int)(t / ((long long)cb * cb)), r = (int)(t % ((long long)cb * cb));
+  const int i = r % cb, j = r / cb;
+  const int gi = blk * cb + i, gj = blk * cb + j;
+  if (gi < n && gj < n) Li[gi + (long long)gj * n] = Dinv[(size_t)blk * cb * cb + i + (size_t)j * cb];
+}
+
 // Blocked right-looking Cholesky of the n x n Hermitian A (lower factor in place)
 // and L^-1 into Li; Dinv receives the inverted diagonal blocks.
 template <class TW>
@@ -1028,19 +1038,69 @@ sparc_status chol_inverse(sparc_ctx* ctx, TW* A, TW* Li, int n, TW* Dinv, TW* tm
     SPARC_LAUNCH(ctx, "cholesky block");
     const int m2 = n - k0 - kb;
     if (m2 > 0) {
-      // T = A21 L_kk^-H ; A22 -= T T^H ; A21 = T
-      SPARC_CUDA(ctx, (gemm64<TW, false, true>(ctx, m2, kb, kb, A + (k0 + kb) + (long long)k0 * n, n, Dk, CB,
-                                               tmp, m2, 1.0, 0.0, part, cap, st)));
-      SPARC_CUDA(ctx, (gemm64<TW, false, true>(ctx, m2, m2, kb, tmp, m2, tmp, m2,
-                                               A + (k0 + kb) + (long long)(k0 + kb) * n, n, -1.0, 1.0, part, cap, st)));
-      k_copy2d<TW><<<ceil_div((long long)m2 * kb, 256), 256, 0, st>>>(tmp, m2, A + (k0 + kb) + (long long)k0 * n, n, m2, kb);
-      ++ctx->launches;
+      TW* A21 = A + (k0 + kb) + (long long)k0 * n;
+      if constexpr (std::is_same<TW, float>::value) {
+        // A21 <- T = A21 L_kk^-H in place (one 64-column tile: each CTA reads its rows of
+        // A21 whole before it writes them); A22 -= T T^H
+        SPARC_CUDA(ctx, (gemm<TW, TW, TW, TW, false, true>(ctx, m2, kb, kb, A21, n, Dk, CB, A21, n, 1, 0, 1.0, st)));
+        SPARC_CUDA(ctx, (gemm64<TW, false, true>(ctx, m2, m2, kb, A21, n, A21, n,
+                                                 A + (k0 + kb) + (long long)(k0 + kb) * n, n, -1.0, 1.0, part, cap,
+                                                 st)));
+      } else {
+        // T = A21 L_kk^-H ; A22 -= T T^H ; A21 = T
+        SPARC_CUDA(ctx, (gemm64<TW, false, true>(ctx, m2, kb, kb, A21, n, Dk, CB, tmp, m2, 1.0, 0.0, part, cap, st)));
+        SPARC_CUDA(ctx, (gemm64<TW, false, true>(ctx, m2, m2, kb, tmp, m2, tmp, m2,
+                                                 A + (k0 + kb) + (long long)(k0 + kb) * n, n, -1.0, 1.0, part, cap,
+                                                 st)));
+        k_copy2d<TW><<<ceil_div((long long)m2 * kb, 256), 256, 0, st>>>(tmp, m2, A21, n, m2, kb);
+        ++ctx->launches;
+      }
     }
   }
-  // L^-1 by block rows: Li_ij = -Dinv_i (sum_{k<i} L_ik Li_kj)
   k_fill0<TW><<<ceil_div((long long)n * n, 256), 256, 0, st>>>(Li, (long long)n * n);
   ++ctx->launches;
   SPARC_LAUNCH(ctx, "inverse init");
+  if constexpr (std::is_same<TW, float>::value) {
+    // L^-1 by recursive doubling: its diagonal blocks are the Dinv blocks; at width w the
+    // off-diagonal block of each pair of consecutive w-ranges a, b is
+    // Li[b, a] = -Li[b, b] L[b, a] Li[a, a].  The pairs of one width are independent and
+    // run on up to four streams (branches of the captured graph), each with its own part
+    // of tmp and of the split-K scratch: a chain of 3 widths x 2 GEMMs at n = 512 instead
+    // of 8 block rows x 3 launches.
+    k_copy_diag<TW><<<ceil_div((long long)nbk * CB * CB, 256), 256, 0, st>>>(Dinv, CB, Li, n);
+    ++ctx->launches;
+    for (int b = 0; b < 3; ++b)
+      if (!ctx->aux_stream[b]) SPARC_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux_stream[b], cudaStreamNonBlocking));
+    cudaEvent_t ev[5] = {};
+    for (cudaEvent_t& e : ev) SPARC_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaError_t le = cudaSuccess;
+    for (int w = CB; w < n && le == cudaSuccess; w *= 2) {
+      const int npairs = ceil_div(n - w, 2 * w);   // pairs with a non-empty b range
+      const int nbr = std::min(4, npairs);
+      le = cudaEventRecord(ev[0], st);   // fork
+      for (int br = 1; br < nbr && le == cudaSuccess; ++br) le = cudaStreamWaitEvent(ctx->aux_stream[br - 1], ev[0], 0);
+      for (int pr = 0; pr < npairs && le == cudaSuccess; ++pr) {
+        const int a0 = 2 * w * pr, b0 = a0 + w, wb = std::min(w, n - b0);
+        cudaStream_t bs = (pr % nbr) == 0 ? st : ctx->aux_stream[(pr % nbr) - 1];
+        TW* tp = tmp + (size_t)(pr % nbr) * w * w;
+        TW* pp = part + (size_t)(pr % nbr) * (cap / nbr);
+        le = gemm64<TW, false, false>(ctx, wb, w, w, A + b0 + (long long)a0 * n, n, Li + a0 + (long long)a0 * n, n, tp,
+                                      wb, 1.0, 0.0, pp, cap / nbr, bs);
+        if (le == cudaSuccess)
+          le = gemm64<TW, false, false>(ctx, wb, w, wb, Li + b0 + (long long)b0 * n, n, tp, wb,
+                                        Li + b0 + (long long)a0 * n, n, -1.0, 0.0, pp, cap / nbr, bs);
+      }
+      for (int br = 1; br < nbr && le == cudaSuccess; ++br) {   // join
+        le = cudaEventRecord(ev[br], ctx->aux_stream[br - 1]);
+        if (le == cudaSuccess) le = cudaStreamWaitEvent(st, ev[br], 0);
+      }
+    }
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    SPARC_CUDA(ctx, le);
+    SPARC_LAUNCH(ctx, "triangular inverse");
+    return SPARC_OK;
+  }
+  // L^-1 by block rows: Li_ij = -Dinv_i (sum_{k<i} L_ik Li_kj)
   for (int iblk = 0; iblk < nbk; ++iblk) {
     const int i0 = iblk * CB, ib = std::min(CB, n - i0);
     TW* Di = Dinv + (size_t)iblk * CB * CB;
@@ -1282,6 +1342,7 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
     SPARC_LAUNCH(ctx, "gram M0");
     timing_end(ctx, TK_GRAM, tg, st);
     cudaEvent_t t0 = timing_begin(ctx, st);
+    cudaEvent_t to = timing_begin(ctx, st);
     // FP32 Cholesky of the diagonally scaled Gram, D^-1/2 M~ D^-1/2 = L' L'^T (unit
     // diagonal), U1 = U D^-1/2 L'^-T.  How closely U1 comes out orthonormal is all its
     // rounding decides: the Gram of U1 below measures what is left and the second
@@ -1292,10 +1353,44 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
     if (ctx->inject_fp64_ortho >= 2) {
       w0 = STATUS_NOT_POSDEF;   // injected: as if the FP32 factorisation had failed
     } else {
-      k_scale_unit<<<ceil_div(nn, 256), 256, 0, st>>>((const double*)Ms, ns, lam, M32, ctx->d_status);
-      ++ctx->launches;
-      s = chol_inverse<float>(ctx, M32, Li32, ns, (float*)Dinv, SV, (float*)partH, 2 * pcap, st);
-      if (s != SPARC_OK) return s;
+      // the scaling and the blocked factorisation and inverse: a chain of small launches,
+      // captured once per size and workspace into a CUDA graph and replayed (eagerly with
+      // the synchronous debug check)
+      auto factor = [&](cudaStream_t fs) -> sparc_status {
+        k_scale_unit<<<ceil_div(nn, 256), 256, 0, fs>>>((const double*)Ms, ns, lam, M32, ctx->d_status);
+        ++ctx->launches;
+        return chol_inverse<float>(ctx, M32, Li32, ns, (float*)Dinv, SV, (float*)partH, 2 * pcap, fs);
+      };
+      if (sync_check()) {
+        s = factor(st);
+        if (s != SPARC_OK) return s;
+      } else {
+        const auto key = std::make_tuple(1 << 20, ns, (void*)Ms, (void*)M32, (void*)Li32);
+        auto it = ctx->graphs.find(key);
+        if (it == ctx->graphs.end()) {
+          if (!ctx->cap_stream) SPARC_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+          const long long l0 = ctx->launches;
+          SPARC_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+          s = factor(ctx->cap_stream);
+          cudaGraph_t g = nullptr;
+          const cudaError_t ec = cudaStreamEndCapture(ctx->cap_stream, &g);
+          ctx->graph_kernels[key] = ctx->launches - l0;
+          ctx->launches = l0;
+          if (s != SPARC_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+          }
+          SPARC_CUDA(ctx, ec);
+          cudaGraphExec_t ge = nullptr;
+          const cudaError_t ei = cudaGraphInstantiate(&ge, g, 0);
+          cudaGraphDestroy(g);
+          SPARC_CUDA(ctx, ei);
+          it = ctx->graphs.emplace(key, ge).first;
+        }
+        SPARC_CUDA(ctx, cudaGraphLaunch(it->second, st));
+        ctx->launches += ctx->graph_kernels[key];
+        ++ctx->graph_launches;
+      }
       SPARC_CUDA(ctx, cudaMemcpyAsync(&w0, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
       SPARC_CUDA(ctx, cudaStreamSynchronize(st));
     }
@@ -1314,6 +1409,7 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
       k_t1_scaled<<<ceil_div(nn, 256), 256, 0, st>>>(Li32, lam, ns, (double*)T1);
     }
     ++ctx->launches;
+    timing_end(ctx, TK_ORTHO, to, st);
     timing_end(ctx, TK_EIG, t0, st);
     cudaEvent_t t1 = timing_begin(ctx, st);
     SPARC_CUDA(ctx, tc::rotate(ctx, U, ld, (const double*)T1, nd, ns, W1, nd, tcs, st, true));   // U1 (T1 upper triangular)
@@ -1347,6 +1443,7 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
   }
   timing_end(ctx, TK_GRAM, tg, st);
   cudaEvent_t te = timing_begin(ctx, st);
+  cudaEvent_t tser = timing_begin(ctx, st);
   // In the orthonormalised basis M~1 = I + E with E of the order of the FP32 rounding
   // of the first factorisation.  Where max |E| <= EPS_SERIES its factor and inverse
   // are short series in E (below) whose small products run in FP32; otherwise the
@@ -1424,7 +1521,9 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
     k_reduce_sym<TW><<<ceil_div(nn, 256), 256, 0, st>>>(Yr, 1, nn, ns, A0);
     ++ctx->launches;
   }
+  timing_end(ctx, TK_SERIES, tser, st);
   int sweeps = 0;
+  cudaEvent_t tritz = nullptr;
   if (!mixed) {
     // 5a. FP64 Jacobi on C; eigenvalues from the converged diagonal
     k_identity<TW><<<ceil_div(nn, 256), 256, 0, st>>>(Vj, ns);
@@ -1446,6 +1545,7 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
     TS* Sres = nullptr;
     s = jacobi<TS>(ctx, S0, S1, SV, ns, 1e-10, 40, scal, &Sres, &sweeps, st, Wjb);
     if (s != SPARC_OK) return s;
+    tritz = timing_begin(ctx, st);
     // FP32 Jacobi vectors are orthonormal to about (rotations per vector) x u32; one
     // Newton-Schulz step, V <- V (3 I - V^H V) / 2, squares that error
     if constexpr (TCP) {
@@ -1472,6 +1572,7 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
     k_permute_cols<TW><<<ceil_div(nn, 256), 256, 0, st>>>(Vj, (const int*)scal, ns, Qs);
     ctx->launches += 2;
   }
+  timing_end(ctx, TK_RITZ, tritz, st);
   ctx->last_sweeps = sweeps;
   // 6. Ritz vectors of the pencil: Yr = Linv^H Q (series: Q + K^T Q)
   if (series) {

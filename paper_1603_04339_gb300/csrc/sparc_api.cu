@@ -724,6 +724,8 @@ void sparc_destroy(sparc_ctx* ctx) {
   if (ctx->kbg.exec) cudaGraphExecDestroy(ctx->kbg.exec);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->cap_stream2) cudaStreamDestroy(ctx->cap_stream2);
+  for (cudaStream_t& a : ctx->aux_stream)
+    if (a) cudaStreamDestroy(a);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->d_status) cudaFree(ctx->d_status);
   delete ctx;

@@ -34,7 +34,8 @@ EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_sync", "s
            "sparc_mlp_train_step", "sparc_mlp_destroy", "sparc_scf_create_k", "sparc_debug_inject",
            "sparc_filter_kernel"]
 KERNEL_GENERIC, KERNEL_TILED, KERNEL_TMA = 0, 1, 2
-TIMED = {"hpass": 0, "gather": 1, "gram": 2, "eig": 3, "rotation": 4, "jacobi": 5, "fpass": 6}
+TIMED = {"hpass": 0, "gather": 1, "gram": 2, "eig": 3, "rotation": 4, "jacobi": 5, "fpass": 6,
+         "ortho": 7, "series": 8, "ritz": 9}
 
 
 class SparcGrid(ctypes.Structure):
