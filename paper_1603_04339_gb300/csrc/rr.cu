@@ -1329,6 +1329,40 @@ sparc_status jacobi(sparc_ctx* ctx, TJ* A0, TJ* A1, TJ* V, int n, double tol, in
 }
 
 // ------------------------------------------------------------------ driver
+// Run `launches` (a chain of small launches with fixed sizes and buffers) on st: captured
+// once per key into a CUDA graph held by the context and replayed after that, so that the
+// chain costs one host launch; issued directly with the synchronous debug check.
+template <class F>
+static sparc_status replay(sparc_ctx* ctx, const std::tuple<int, int, void*, void*, void*>& key, cudaStream_t st,
+                           F&& launches) {
+  if (sync_check()) return launches(st);
+  auto it = ctx->graphs.find(key);
+  if (it == ctx->graphs.end()) {
+    if (!ctx->cap_stream) SPARC_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    const long long l0 = ctx->launches;
+    SPARC_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const sparc_status s = launches(ctx->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(ctx->cap_stream, &g);
+    ctx->graph_kernels[key] = ctx->launches - l0;
+    ctx->launches = l0;
+    if (s != SPARC_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    SPARC_CUDA(ctx, ec);
+    cudaGraphExec_t ge = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    SPARC_CUDA(ctx, ei);
+    it = ctx->graphs.emplace(key, ge).first;
+  }
+  SPARC_CUDA(ctx, cudaGraphLaunch(it->second, st));
+  ctx->launches += ctx->graph_kernels[key];
+  ++ctx->graph_launches;
+  return SPARC_OK;
+}
+
 template <class T, class TC>
 sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig, bool mixed, cudaStream_t st) {
   using TW = typename Wide<T>::W;
@@ -1418,36 +1452,8 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
         ++ctx->launches;
         return chol_inverse<float>(ctx, M32, Li32, ns, (float*)Dinv, SV, (float*)partH, 2 * pcap, fs);
       };
-      if (sync_check()) {
-        s = factor(st);
-        if (s != SPARC_OK) return s;
-      } else {
-        const auto key = std::make_tuple(1 << 20, ns, (void*)Ms, (void*)M32, (void*)Li32);
-        auto it = ctx->graphs.find(key);
-        if (it == ctx->graphs.end()) {
-          if (!ctx->cap_stream) SPARC_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
-          const long long l0 = ctx->launches;
-          SPARC_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-          s = factor(ctx->cap_stream);
-          cudaGraph_t g = nullptr;
-          const cudaError_t ec = cudaStreamEndCapture(ctx->cap_stream, &g);
-          ctx->graph_kernels[key] = ctx->launches - l0;
-          ctx->launches = l0;
-          if (s != SPARC_OK) {
-            if (g) cudaGraphDestroy(g);
-            return s;
-          }
-          SPARC_CUDA(ctx, ec);
-          cudaGraphExec_t ge = nullptr;
-          const cudaError_t ei = cudaGraphInstantiate(&ge, g, 0);
-          cudaGraphDestroy(g);
-          SPARC_CUDA(ctx, ei);
-          it = ctx->graphs.emplace(key, ge).first;
-        }
-        SPARC_CUDA(ctx, cudaGraphLaunch(it->second, st));
-        ctx->launches += ctx->graph_kernels[key];
-        ++ctx->graph_launches;
-      }
+      s = replay(ctx, std::make_tuple(1 << 20, ns, (void*)Ms, (void*)M32, (void*)Li32), st, factor);
+      if (s != SPARC_OK) return s;
       SPARC_CUDA(ctx, cudaMemcpyAsync(&w0, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
       SPARC_CUDA(ctx, cudaStreamSynchronize(st));
     }
@@ -1522,43 +1528,49 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
   TW* Kc = Li;   // series: K = (I + F)^-1 - I, Linv = I + K
   if constexpr (TCP) {
     if (series) {
-      double* E = (double*)A1;
-      double* F = (double*)Vj;
-      double* G = (double*)Qs;
-      // 3'. F lower triangular with (I + F)(I + F)^T = I + E: F = Phi(E - F F^T),
-      // iterated from F = Phi(E); each pass gains a power of |E| (|E|^5 after four)
-      k_phi<<<ceil_div(nn, 256), 256, 0, st>>>(E, nullptr, ns, F);
-      ++ctx->launches;
-      for (int it = 0; it < 3; ++it) {
-        SPARC_CUDA(ctx, (gemm_f32p<false, true>(ctx, ns, ns, ns, F, ns, F, ns, G, ns, 1.0, 0.0, (double*)partH, pcap,
-                                                st)));
-        k_phi<<<ceil_div(nn, 256), 256, 0, st>>>(E, G, ns, F);
+      // the series' chain of small launches, replayed from a CUDA graph
+      auto series_launches = [&](cudaStream_t fs) -> sparc_status {
+        double* E = (double*)A1;
+        double* F = (double*)Vj;
+        double* G = (double*)Qs;
+        // 3'. F lower triangular with (I + F)(I + F)^T = I + E: F = Phi(E - F F^T),
+        // iterated from F = Phi(E); each pass gains a power of |E| (|E|^5 after four)
+        k_phi<<<ceil_div(nn, 256), 256, 0, fs>>>(E, nullptr, ns, F);
         ++ctx->launches;
-      }
-      // K = (I + F)^-1 - I = -F (I - F (I - F (I - F))), error |F|^5
-      double* Ta = (double*)Yr;
-      double* Tb = (double*)T1;
-      k_i_minus<<<ceil_div(nn, 256), 256, 0, st>>>(F, ns, Ta);
-      ++ctx->launches;
-      for (int it = 0; it < 2; ++it) {
-        k_identity<double><<<ceil_div(nn, 256), 256, 0, st>>>(Tb, ns);
+        for (int it = 0; it < 3; ++it) {
+          SPARC_CUDA(ctx, (gemm_f32p<false, true>(ctx, ns, ns, ns, F, ns, F, ns, G, ns, 1.0, 0.0, (double*)partH, pcap,
+                                                  fs)));
+          k_phi<<<ceil_div(nn, 256), 256, 0, fs>>>(E, G, ns, F);
+          ++ctx->launches;
+        }
+        // K = (I + F)^-1 - I = -F (I - F (I - F (I - F))), error |F|^5
+        double* Ta = (double*)Yr;
+        double* Tb = (double*)T1;
+        k_i_minus<<<ceil_div(nn, 256), 256, 0, fs>>>(F, ns, Ta);
         ++ctx->launches;
-        SPARC_CUDA(ctx, (gemm_f32p<false, false>(ctx, ns, ns, ns, F, ns, Ta, ns, Tb, ns, -1.0, 1.0, (double*)partH,
-                                                 pcap, st)));
-        std::swap(Ta, Tb);
-      }
-      SPARC_CUDA(ctx, (gemm_f32p<false, false>(ctx, ns, ns, ns, F, ns, Ta, ns, (double*)Kc, ns, -1.0, 0.0,
-                                               (double*)partH, pcap, st)));
-      // 4'. C = (I + K) H~ (I + K)^T = H~ + P + P^T + P K^T with P = K H~; the
-      // corrections are O(|K| |H~|), so their FP32 products are FP64-accurate in C
-      double* P = (double*)T1;
-      double* Q = (double*)Yr;
-      SPARC_CUDA(ctx, (gemm_f32p<false, false>(ctx, ns, ns, ns, (const double*)Kc, ns, (const double*)Hs, ns, P, ns,
-                                               1.0, 0.0, (double*)partH, pcap, st)));
-      SPARC_CUDA(ctx, (gemm_f32p<false, true>(ctx, ns, ns, ns, P, ns, (const double*)Kc, ns, Q, ns, 1.0, 0.0,
-                                              (double*)partH, pcap, st)));
-      k_csum<<<ceil_div(nn, 256), 256, 0, st>>>((const double*)Hs, P, Q, ns, (double*)A0);
-      ++ctx->launches;
+        for (int it = 0; it < 2; ++it) {
+          k_identity<double><<<ceil_div(nn, 256), 256, 0, fs>>>(Tb, ns);
+          ++ctx->launches;
+          SPARC_CUDA(ctx, (gemm_f32p<false, false>(ctx, ns, ns, ns, F, ns, Ta, ns, Tb, ns, -1.0, 1.0, (double*)partH,
+                                                   pcap, fs)));
+          std::swap(Ta, Tb);
+        }
+        SPARC_CUDA(ctx, (gemm_f32p<false, false>(ctx, ns, ns, ns, F, ns, Ta, ns, (double*)Kc, ns, -1.0, 0.0,
+                                                 (double*)partH, pcap, fs)));
+        // 4'. C = (I + K) H~ (I + K)^T = H~ + P + P^T + P K^T with P = K H~; the
+        // corrections are O(|K| |H~|), so their FP32 products are FP64-accurate in C
+        double* P = (double*)T1;
+        double* Q = (double*)Yr;
+        SPARC_CUDA(ctx, (gemm_f32p<false, false>(ctx, ns, ns, ns, (const double*)Kc, ns, (const double*)Hs, ns, P, ns,
+                                                 1.0, 0.0, (double*)partH, pcap, fs)));
+        SPARC_CUDA(ctx, (gemm_f32p<false, true>(ctx, ns, ns, ns, P, ns, (const double*)Kc, ns, Q, ns, 1.0, 0.0,
+                                                (double*)partH, pcap, fs)));
+        k_csum<<<ceil_div(nn, 256), 256, 0, fs>>>((const double*)Hs, P, Q, ns, (double*)A0);
+        ++ctx->launches;
+        return SPARC_OK;
+      };
+      s = replay(ctx, std::make_tuple(1 << 21, ns, (void*)A1, (void*)Vj, (void*)Qs), st, series_launches);
+      if (s != SPARC_OK) return s;
     }
   }
   if (!series) {
