@@ -1617,36 +1617,40 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
     tritz = timing_begin(ctx, st);
     // FP32 Jacobi vectors are orthonormal to about (rotations per vector) x u32; one
     // Newton-Schulz step, V <- V (3 I - V^H V) / 2, squares that error
-    if constexpr (TCP) {
-      // real data: the step on the tensor cores (3xTF32 Gram with FP64 sums, 3xTF32
-      // product): V ends orthonormal to about 1e-7, below the FP32 rounding of the
-      // orbitals it rotates
-      SPARC_CUDA(ctx, tc::gram(ctx, (const float*)SV, ns, (const float*)SV, ns, ns, ns, (double*)T1, tcs, st));
-      k_ns_coef<<<ceil_div(nn, 256), 256, 0, st>>>((double*)T1, ns);
+    // the Ritz pairs' chain of launches (FP32 data: replayed from a CUDA graph)
+    auto ritz = [&](cudaStream_t fs) -> sparc_status {
+      if constexpr (TCP) {
+        // real data: the step on the tensor cores (3xTF32 Gram with FP64 sums, 3xTF32
+        // product): V ends orthonormal to about 1e-7, below the FP32 rounding of the
+        // orbitals it rotates
+        SPARC_CUDA(ctx, tc::gram(ctx, (const float*)SV, ns, (const float*)SV, ns, ns, ns, (double*)T1, tcs, fs));
+        k_ns_coef<<<ceil_div(nn, 256), 256, 0, fs>>>((double*)T1, ns);
+        ++ctx->launches;
+        SPARC_CUDA(ctx, tc::rotate(ctx, (const float*)SV, ns, (const double*)T1, ns, ns, (float*)S1, ns, tcs, fs));
+        k_convert<TS, TW><<<ceil_div(nn, 256), 256, 0, fs>>>(S1, Vj, nn);
+        ++ctx->launches;
+        // C V with FP32-exact V: float-float products and sums at the FP32 rate
+        k_gemm_ff<<<dim3((unsigned)ceil_div(ns, 32), (unsigned)ceil_div(ns, 32)), 256, 0, fs>>>(
+            (const double*)A0, (const double*)Vj, (double*)T1, ns);
+        ++ctx->launches;
+      } else {
+        k_convert<TS, TW><<<ceil_div(nn, 256), 256, 0, fs>>>(SV, A1, nn);
+        ++ctx->launches;
+        SPARC_CUDA(ctx, (gemm64<TW, true, false>(ctx, ns, ns, ns, A1, ns, A1, ns, T1, ns, 1.0, 0.0, partH, pcap, fs)));
+        SPARC_CUDA(ctx, cudaMemcpyAsync(Vj, A1, nn * sizeof(TW), cudaMemcpyDeviceToDevice, fs));
+        SPARC_CUDA(ctx, (gemm64<TW, false, false>(ctx, ns, ns, ns, A1, ns, T1, ns, Vj, ns, -0.5, 1.5, partH, pcap, fs)));
+        SPARC_CUDA(ctx, (gemm64<TW, false, false>(ctx, ns, ns, ns, A0, ns, Vj, ns, T1, ns, 1.0, 0.0, partH, pcap, fs)));
+      }
+      k_rayleigh<TW><<<ceil_div(ns, 8), 256, 0, fs>>>(Vj, T1, ns, lam);
       ++ctx->launches;
-      SPARC_CUDA(ctx, tc::rotate(ctx, (const float*)SV, ns, (const double*)T1, ns, ns, (float*)S1, ns, tcs, st));
-      k_convert<TS, TW><<<ceil_div(nn, 256), 256, 0, st>>>(S1, Vj, nn);
-      ++ctx->launches;
-    } else {
-      k_convert<TS, TW><<<ceil_div(nn, 256), 256, 0, st>>>(SV, A1, nn);
-      ++ctx->launches;
-      SPARC_CUDA(ctx, (gemm64<TW, true, false>(ctx, ns, ns, ns, A1, ns, A1, ns, T1, ns, 1.0, 0.0, partH, pcap, st)));
-      SPARC_CUDA(ctx, cudaMemcpyAsync(Vj, A1, nn * sizeof(TW), cudaMemcpyDeviceToDevice, st));
-      SPARC_CUDA(ctx, (gemm64<TW, false, false>(ctx, ns, ns, ns, A1, ns, T1, ns, Vj, ns, -0.5, 1.5, partH, pcap, st)));
-    }
-    if constexpr (TCP) {
-      // C V with FP32-exact V: float-float products and sums at the FP32 rate
-      k_gemm_ff<<<dim3((unsigned)ceil_div(ns, 32), (unsigned)ceil_div(ns, 32)), 256, 0, st>>>(
-          (const double*)A0, (const double*)Vj, (double*)T1, ns);
-      ++ctx->launches;
-    } else {
-      SPARC_CUDA(ctx, (gemm64<TW, false, false>(ctx, ns, ns, ns, A0, ns, Vj, ns, T1, ns, 1.0, 0.0, partH, pcap, st)));
-    }
-    k_rayleigh<TW><<<ceil_div(ns, 8), 256, 0, st>>>(Vj, T1, ns, lam);
-    ++ctx->launches;
-    k_sort<TW><<<ceil_div(ns, 128), 128, 0, st>>>(nullptr, lam, ns, eig, (int*)scal);
-    k_permute_cols<TW><<<ceil_div(nn, 256), 256, 0, st>>>(Vj, (const int*)scal, ns, Qs);
-    ctx->launches += 2;
+      k_sort<TW><<<ceil_div(ns, 128), 128, 0, fs>>>(nullptr, lam, ns, eig, (int*)scal);
+      k_permute_cols<TW><<<ceil_div(nn, 256), 256, 0, fs>>>(Vj, (const int*)scal, ns, Qs);
+      ctx->launches += 2;
+      return SPARC_OK;
+    };
+    if constexpr (TCP) s = replay(ctx, std::make_tuple(1 << 22, ns, (void*)SV, (void*)eig, (void*)Qs), st, ritz);
+    else s = ritz(st);
+    if (s != SPARC_OK) return s;
   }
   timing_end(ctx, TK_RITZ, tritz, st);
   ctx->last_sweeps = sweeps;
