@@ -670,8 +670,16 @@ __global__ void __launch_bounds__(256) k_bj_apply(const float* __restrict__ A, f
 #pragma unroll
     for (int u = 0; u < CPT; ++u) An[gi + (long long)bj_index<BJ>(j0 + u, bp, bq) * n] = acc[u];
     if (ka != kb) {
+      // the transpose through shared memory, so that a warp's stores cover 32 rows of a
+      // column of A' (as the direct ones do)
+      __syncthreads();
 #pragma unroll
-      for (int u = 0; u < CPT; ++u) An[bj_index<BJ>(j0 + u, bp, bq) + (long long)gi * n] = acc[u];
+      for (int u = 0; u < CPT; ++u) Tm[i][j0 + u] = acc[u];
+      __syncthreads();
+      const int jj = t % NI, ig = (t / NI) * CPT;
+      const int gj = bj_index<BJ>(jj, bp, bq);
+#pragma unroll
+      for (int u = 0; u < CPT; ++u) An[gj + (long long)bj_index<BJ>(ig + u, ap, aq) * n] = Tm[ig + u][jj];
     }
   } else {
     const int vb = bid;
