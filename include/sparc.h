@@ -66,9 +66,9 @@ typedef enum {
 /* Rayleigh-Ritz precision modes. */
 typedef enum {
   SPARC_RR_FP64 = 0,  /* Grams, eigensolve and rotation in FP64 (input must be F64/C128)   */
-  SPARC_RR_MIXED = 1  /* F32 input: Grams and rotation on tensor cores with 3xTF32
-                         error compensation (see sparc_gram_f32); C64 input: FP32 SIMT
-                         products with FP64 accumulation; FP64 Cholesky + eigensolve */
+  SPARC_RR_MIXED = 1  /* F32 and C64 input: Grams and rotation on tensor cores with
+                         3xTF32 error compensation (see sparc_gram_f32, sparc_gram_c64);
+                         FP64 factorisations, FP32 Jacobi eigenvectors, FP64 Ritz values */
 } sparc_rr_mode;
 
 /* Finite-difference grid at one Bloch wavevector (Section 3.1). */
@@ -327,8 +327,10 @@ sparc_status sparc_rayleigh_ritz(sparc_ham* H, sparc_dtype dtype, void* U, int n
  * sparc_rayleigh_ritz computes them in MIXED mode: G = A^T B, with A, B device,
  * real FP32, column-major nd x ns (lda, ldb >= nd) and G device, FP64,
  * column-major ns x ns.  (H~ = U^T (H U) and M~ = U^T U are the two calls.)
- * Tensor-core products (tcgen05, kind::tf32) with 3xTF32 error compensation,
- * FP32 accumulation over chunks of 1024 grid points and FP64 across chunks;
+ * Tensor-core products (tcgen05, kind::tf32) of the TF32 high and low parts of
+ * both factors (four products), FP32 accumulation over chunks of 64 grid points
+ * (the tensor core's accumulation rounds toward zero: sums of squares come out
+ * about 2.5e-7 low) and FP64 across chunks;
  * the result is symmetrised (G is taken as symmetric: tiles below the diagonal
  * are the transposes of those above).  Deterministic.  1 <= ns <= 4096. */
 sparc_status sparc_gram_f32(sparc_ctx* ctx, const float* A, int64_t lda, const float* B, int64_t ldb,
@@ -340,6 +342,25 @@ sparc_status sparc_gram_f32(sparc_ctx* ctx, const float* A, int64_t lda, const f
  * overlap U.  Tensor-core products with 3xTF32 compensation.  1 <= ns <= 4096. */
 sparc_status sparc_rotate_f32(sparc_ctx* ctx, const float* U, int64_t ldu, const double* Yr, int64_t nd,
                               int ns, float* C, int64_t ldc, void* stream);
+
+/* The projections of Eq. SubspaceGeneralizedEigenproblem for complex64 data (Bloch
+ * orbitals at k != 0, Section 3.3), as sparc_rayleigh_ritz computes them in MIXED mode:
+ * G = A^H B, with A, B device, complex64 ((re, im) pairs), column-major nd x ns (lda,
+ * ldb >= nd) and G device, complex128, column-major ns x ns.  Computed on the real
+ * views of the columns (2 nd FP32 values each): Re G = r(A)^T r(B) and
+ * Im G = -r(A)^T r(i B), two calls of the sparc_gram_f32 kernels; G is taken as
+ * Hermitian (its real part symmetrised, its imaginary part antisymmetrised).  The
+ * workspace holds i B (nd x ns complex64).  Deterministic.  1 <= ns <= 4096. */
+sparc_status sparc_gram_c64(sparc_ctx* ctx, const void* A, int64_t lda, const void* B, int64_t ldb,
+                            int64_t nd, int ns, void* G, void* stream);
+
+/* The rotation of Eq. OrbitalTransformation for complex64 data: C = U Yr, with U
+ * device complex64 column-major nd x ns (ldu), Yr device complex128 column-major
+ * ns x ns (rounded to FP32), C device complex64 column-major nd x ns (ldc); C may not
+ * overlap U.  One tensor-core rotation of the real views, r(C) = r(U) Re Yr +
+ * r(i U) Im Yr, with 3xTF32 compensation.  1 <= ns <= 4096. */
+sparc_status sparc_rotate_c64(sparc_ctx* ctx, const void* U, int64_t ldu, const void* Yr, int64_t nd,
+                              int ns, void* C, int64_t ldc, void* stream);
 
 /* ---------------------------------------------------------------- SCF iteration
  * One self-consistent-field iteration around the CheFSI step (Section 3.4, Eq. EL;
@@ -436,9 +457,9 @@ sparc_status sparc_scf_forces(sparc_scf* S, sparc_dtype dtype, const void* U, in
  * their stream is being captured into a CUDA graph are not timed.
  *   which = 0: the H-apply / Chebyshev-recurrence pass of the generic kernel (k_hpass)
  *   which = 1: the nonlocal projection (k_nl_gather, k_gather_rows, k_gather_rows_f2)
- *   which = 2: the Gram products of Rayleigh-Ritz (and sparc_gram_f32)
+ *   which = 2: the Gram products of Rayleigh-Ritz (and sparc_gram_f32, sparc_gram_c64)
  *   which = 3: the Cholesky + subspace eigensolve of Rayleigh-Ritz
- *   which = 4: the subspace rotation of Rayleigh-Ritz (and sparc_rotate_f32)
+ *   which = 4: the subspace rotation of Rayleigh-Ritz (and sparc_rotate_f32, sparc_rotate_c64)
  *   which = 5: the Jacobi sweeps of the subspace eigensolve (inside which = 3)
  *   which = 6: the FP32 / complex64 filter pass (k_pass_tma, k_pass_f2, k_pass_c2)
  *   which = 7, 8, 9: parts of which = 3 in the mixed mode of FP32 data: the first

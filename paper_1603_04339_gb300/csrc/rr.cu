@@ -724,6 +724,15 @@ __global__ void k_transpose(const double* __restrict__ in, double* __restrict__ 
   out[j + (long long)i * n] = in[e];
 }
 
+// out = in^H (n x n, column-major)
+template <class TW>
+__global__ void k_adjoint(const TW* __restrict__ in, TW* __restrict__ out, int n) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  const int i = (int)(e % n), j = (int)(e / n);
+  out[j + (long long)i * n] = Tr<TW>::conj(in[e]);
+}
+
 template <class TW>
 __global__ void k_identity(TW* V, int n) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1389,15 +1398,19 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
   const int nbk = ceil_div(ns, CB);
   const size_t dinvb = align256((size_t)nbk * CB * CB * ew);
   constexpr bool TCP = std::is_same<T, float>::value;   // FP32 data: tensor-core Grams and rotation
-  const size_t tcb = TCP ? align256(std::max(tc::gram_scratch_bytes(ctx, ns, nd), tc::rot_scratch_bytes(ns))) : 0;
-  const size_t w1b = TCP ? hub : 0;   // U1, the orthonormalised basis
+  constexpr bool TCC = std::is_same<T, cf32>::value;    // complex64 data: the same, on the real views
+  const size_t tcb = TCP   ? align256(std::max(tc::gram_scratch_bytes(ctx, ns, nd), tc::rot_scratch_bytes(ns)))
+                     : TCC ? align256(std::max(tc::cgram_scratch_bytes(ctx, ns, nd), tc::rot_scratch_bytes(ns, true)))
+                           : 0;
+  const size_t w1b = (TCP || TCC) ? hub : 0;   // U1, the orthonormalised basis
+  const size_t jbb = TCC ? hub : 0;            // i B, the second operand of a complex Gram's imaginary part
   const size_t gsb = apply_scratch_bytes(H, DtypeOf<T>::v, ns);   // projection scratch of the H-apply
   // rotations of the block Jacobi rounds (FP32 subproblems of the mixed mode)
   // (block size b: ns / b / 2 pairs of 4 b^2 floats, that is 2 b ns floats, twice: the
   // rotations of two consecutive rounds)
   const size_t wjb = (bj_type<TS>() && bj_size(ns) > 0) ? align256((size_t)4 * BJ_MAX * ns * sizeof(float)) : 0;
   const size_t extra = hub + 2 * partb + 10 * sm + dinvb + align256(nn * es) + 3 * align256(nn * sizeof(TS)) +
-                       align256(ns * sizeof(double)) + tcb + w1b + gsb + wjb + 256;
+                       align256(ns * sizeof(double)) + tcb + w1b + jbb + gsb + wjb + 256;
   BlockWs w;
   char* tail = nullptr;
   sparc_status s = block_ws(H, DtypeOf<T>::v, ns, extra, &w, &tail);
@@ -1424,6 +1437,7 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
   double* lam = (double*)tail; tail += align256(ns * sizeof(double));
   void* tcs = tail; tail += tcb;
   float* Wjb = wjb ? (float*)tail : nullptr; tail += wjb;
+  T* JB = (T*)tail; tail += jbb;
   T* W1 = (T*)tail;
   const long long pcap = (long long)(partb / ew);
 
@@ -1437,7 +1451,7 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
     // M~ amplifies the Gram's rounding by kappa; in the basis U1 the pencil has M~1 ~ I.
     // Both bases span the same subspace (Eq. SubspaceGeneralizedEigenproblem).
     tg = timing_begin(ctx, st);
-    SPARC_CUDA(ctx, tc::gram(ctx, U, ld, U, ld, nd, ns, Ms, tcs, st));
+    SPARC_CUDA(ctx, tc::gram(ctx, U, ld, U, ld, nd, ns, Ms, tcs, st, false, true));
     SPARC_LAUNCH(ctx, "gram M0");
     timing_end(ctx, TK_GRAM, tg, st);
     cudaEvent_t t0 = timing_begin(ctx, st);
@@ -1489,7 +1503,36 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
     Ub = W1;
     ldb = nd;
   }
-  // 1. HU = H U (U1 for FP32 data)
+  if constexpr (TCC) {
+    // complex64 data: the same first orthonormalisation, U1 = U L^-H, with the Gram and
+    // the rotation on the tensor cores and the factorisation of M~ = L L^H in FP64
+    tg = timing_begin(ctx, st);
+    SPARC_CUDA(ctx, tc::cgram(ctx, U, ld, U, ld, nd, ns, Ms, JB, tcs, st, true));
+    SPARC_LAUNCH(ctx, "gram M0");
+    timing_end(ctx, TK_GRAM, tg, st);
+    cudaEvent_t t0 = timing_begin(ctx, st);
+    cudaEvent_t to = timing_begin(ctx, st);
+    s = chol_inverse<TW>(ctx, Ms, Li, ns, Dinv, T1, partH, pcap, st);
+    if (s != SPARC_OK) return s;
+    int w0 = 0;
+    SPARC_CUDA(ctx, cudaMemcpyAsync(&w0, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SPARC_CUDA(ctx, cudaStreamSynchronize(st));
+    if (w0 & STATUS_NOT_POSDEF) {
+      cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st);
+      return fail(ctx, SPARC_ERR_NOT_POSDEF, "M~ = U^H U is not positive definite");
+    }
+    k_adjoint<TW><<<ceil_div(nn, 256), 256, 0, st>>>(Li, T1, ns);   // L^-H, upper triangular
+    ++ctx->launches;
+    timing_end(ctx, TK_ORTHO, to, st);
+    timing_end(ctx, TK_EIG, t0, st);
+    cudaEvent_t t1 = timing_begin(ctx, st);
+    SPARC_CUDA(ctx, tc::crotate(ctx, U, ld, T1, nd, ns, W1, nd, tcs, st));
+    SPARC_LAUNCH(ctx, "orthonormalise");
+    timing_end(ctx, TK_ROT, t1, st);
+    Ub = W1;
+    ldb = nd;
+  }
+  // 1. HU = H U (U1 for FP32 and complex64 data)
   s = apply_block<T>(H, Ub, HU, ns, ldb, st, w);
   if (s != SPARC_OK) return s;
   // 2. H~ = U^H (HU), M~ = U^H U (split-K partials, then fixed-order sum + symmetrisation)
@@ -1498,6 +1541,11 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
     SPARC_CUDA(ctx, tc::gram(ctx, Ub, nd, HU, nd, nd, ns, Hs, tcs, st));
     SPARC_LAUNCH(ctx, "gram H");
     SPARC_CUDA(ctx, tc::gram(ctx, Ub, nd, Ub, nd, nd, ns, Ms, tcs, st));
+    SPARC_LAUNCH(ctx, "gram M");
+  } else if constexpr (TCC) {
+    SPARC_CUDA(ctx, tc::cgram(ctx, Ub, nd, HU, nd, nd, ns, Hs, JB, tcs, st));
+    SPARC_LAUNCH(ctx, "gram H");
+    SPARC_CUDA(ctx, tc::cgram(ctx, Ub, nd, Ub, nd, nd, ns, Ms, JB, tcs, st));
     SPARC_LAUNCH(ctx, "gram M");
   } else {
     SPARC_CUDA(ctx, (gemm<T, T, TC, TW, true, false>(ctx, ns, ns, (int)nd, U, ld, HU, nd, partH, ns, nsplit,
@@ -1628,9 +1676,9 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
     // the Ritz pairs' chain of launches (FP32 data: replayed from a CUDA graph)
     auto ritz = [&](cudaStream_t fs) -> sparc_status {
       if constexpr (TCP) {
-        // real data: the step on the tensor cores (3xTF32 Gram with FP64 sums, 3xTF32
-        // product): V ends orthonormal to about 1e-7, below the FP32 rounding of the
-        // orbitals it rotates
+        // real data: the step on the tensor cores (compensated TF32 Gram with FP64 sums,
+        // 3xTF32 product): V ends orthonormal to about 1e-7, below the FP32 rounding of
+        // the orbitals it rotates
         SPARC_CUDA(ctx, tc::gram(ctx, (const float*)SV, ns, (const float*)SV, ns, ns, ns, (double*)T1, tcs, fs));
         k_ns_coef<<<ceil_div(nn, 256), 256, 0, fs>>>((double*)T1, ns);
         ++ctx->launches;
@@ -1672,7 +1720,7 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
     SPARC_CUDA(ctx, (gemm64<TW, true, false>(ctx, ns, ns, ns, Li, ns, Qs, ns, Yr, ns, 1.0, 0.0, partH, pcap, st)));
   }
   // 7. rotation U <- U Yr (into HU, then back into U)
-  if constexpr (!TCP) {
+  if constexpr (!TCP && !TCC) {
     k_narrow<TW, T><<<ceil_div(nn, 256), 256, 0, st>>>(Yr, YrT, nn);
     ++ctx->launches;
   }
@@ -1681,6 +1729,8 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
   cudaEvent_t tr = timing_begin(ctx, st);
   if constexpr (TCP) {
     SPARC_CUDA(ctx, tc::rotate(ctx, Ub, ldb, Yr, nd, ns, U, ld, tcs, st));   // U1 -> U
+  } else if constexpr (TCC) {
+    SPARC_CUDA(ctx, tc::crotate(ctx, Ub, ldb, Yr, nd, ns, U, ld, tcs, st));  // U1 -> U
   } else {
     SPARC_CUDA(ctx, (gemm<T, T, TC, T, false, false>(ctx, (int)nd, ns, ns, U, ld, YrT, ns, HU, nd, 1, 0, 1.0, st)));
     SPARC_CUDA(ctx, cudaMemcpy2DAsync(U, ld * es, HU, nd * es, nd * es, ns, cudaMemcpyDeviceToDevice, st));

@@ -38,12 +38,23 @@ sparc_status filter_run(sparc_ham* H, sparc_dtype dtype, int m, double a, double
 namespace tc {
 // G = A^T B (ns x ns, FP64, symmetrised) for column-major nd x ns FP32 A, B.
 size_t gram_scratch_bytes(const sparc_ctx* ctx, int ns, long long nd);
+// anti: G is antisymmetric (tiles below the diagonal are minus the transposes);
+// fast: longer FP32 accumulation chunks (sums of like-signed products about 6e-7 low
+// instead of 2.5e-7), where FP32 accuracy is enough.
 cudaError_t gram(sparc_ctx* ctx, const float* A, long long lda, const float* B, long long ldb, long long nd, int ns,
-                 double* G, void* scratch, cudaStream_t st);
+                 double* G, void* scratch, cudaStream_t st, bool anti = false, bool fast = false);
+// G = A^H B (ns x ns, complex FP64, Hermitian) for column-major nd x ns complex64 A, B,
+// from two real Grams of the real views; JB: nd x ns complex64 scratch (i B).
+size_t cgram_scratch_bytes(const sparc_ctx* ctx, int ns, long long nd);
+cudaError_t cgram(sparc_ctx* ctx, const cf32* A, long long lda, const cf32* B, long long ldb, long long nd, int ns,
+                  cf64* G, cf32* JB, void* scratch, cudaStream_t st, bool fast = false);
 // C = U Yr (nd x ns, FP32) for column-major FP32 U and FP64 ns x ns Yr; C must not overlap U.
-size_t rot_scratch_bytes(int ns);
+size_t rot_scratch_bytes(int ns, bool cplx = false);
 cudaError_t rotate(sparc_ctx* ctx, const float* U, long long ldu, const double* Yr, long long nd, int ns, float* C,
                    long long ldc, void* scratch, cudaStream_t st, bool upper = false);
+// The same for complex64 U, C and complex FP64 Yr (one real rotation with 2 ns values of k).
+cudaError_t crotate(sparc_ctx* ctx, const cf32* U, long long ldu, const cf64* Yr, long long nd, int ns, cf32* C,
+                    long long ldc, void* scratch, cudaStream_t st);
 }  // namespace tc
 
 }  // namespace sparc

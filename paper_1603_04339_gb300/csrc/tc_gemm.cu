@@ -7,11 +7,13 @@
 // swizzle (rows of 32 FP32 values, 8-row groups 1024 bytes apart).  Products
 // are error-compensated ("3xTF32"):
 //   a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi,
-// where a_hi keeps the sign, exponent and top 10 stored mantissa bits of a and
-// a_lo = a - a_hi exactly; a_lo b_lo (relative size 2^-22) is dropped.
+// where a_hi is a rounded to the nearest TF32 value (10 stored mantissa bits) and
+// a_lo = a - a_hi exactly; a_lo b_lo (relative size 2^-22; over a sum of squares a
+// bias of about 4e-8) is dropped in the rotation and kept in the Grams (four
+// products), whose sums decide the Ritz values.
 //
 // Gram  G = A^T B (Ns x Ns, FP64): one CTA per (upper-triangular 128 x 128 tile
-//   pair, split of the Nd range); the CTA accumulates GCH k-tiles at a time in
+//   pair, split of the Nd range); the CTA accumulates 2^gsh k-tiles at a time in
 //   TMEM (FP32; a_hi b_hi and the cross terms in separate accumulators) and adds
 //   each chunk in FP64 to its own partial; a second kernel
 //   sums the splits in a fixed order and mirrors the tiles, so the result is
@@ -19,6 +21,15 @@
 // Rotation  C = U Yr (Nd x Ns): one CTA per (128 grid rows, 256 columns); Yr is
 //   split and swizzled once into its shared-memory images, U is split and
 //   transposed to K-major on its way into shared memory.
+// Complex64 orbitals (k-points, Section 3.3) take the same kernels on their real
+// views: a column of nd complex values is a column of 2 nd FP32 values (real and
+// imaginary parts interleaved along the grid index).  For columns u, v with real
+// views r(u), r(v), and i v = (-Im v, Re v) interleaved the same way,
+//   Re(u^H v) = r(u) . r(v),   Im(u^H v) = -r(u) . r(i v),
+// so a complex Gram is two real Grams of 2 nd rows (the second of an antisymmetric
+// matrix), and the rotation U Q = r(U) Re Q + r(i U) Im Q is one real rotation with
+// 2 Ns values of k, the i U half formed as U is loaded.  Four real products per
+// complex one, all on the tensor cores.
 #include <cuda.h>
 
 #include <algorithm>
@@ -37,7 +48,16 @@ constexpr int THREADS = 256;   // rotation CTA
 constexpr int GTHREADS = 512;  // Gram CTA: 16 warps split, swizzle and stage the operands
 constexpr int GN = 128;        // Gram tile N
 constexpr int GST = 3;         // Gram pipeline stages
-constexpr int GCH = 8;         // Gram k-tiles per FP32 accumulation chunk (256 grid points)
+// Gram k-tiles per FP32 accumulation chunk, 2^gsh: 2 (64 grid points), or 8 (256) where the Gram only has to be good to FP32 accuracy (the first
+// orthonormalisation, which the second corrects).  The tensor core's FP32
+// accumulation rounds toward zero: a sum of like-signed products (each diagonal entry
+// of M~, most of H~'s, columns close to parallel) comes out low, by 6e-7 of itself
+// over chunks of 8 k-tiles (32 MMAs, measured) against 2.5e-7 over chunks of 2.  A
+// bias the same for every entry of M~ and H~ would leave the Ritz values alone, but
+// it is not (H~'s sums are partly of mixed sign), and at 8 k-tiles it moved them by
+// up to 1.8e-7 of themselves, against 2e-8 at 2.
+constexpr int GCH_ACC_LOG = 1;    // 2 k-tiles
+constexpr int GCH_FAST_LOG = 3;   // 8 k-tiles
 constexpr int RN = 256;        // rotation tile N
 constexpr int RST = 2;         // rotation pipeline stages
 constexpr int TILE_A = BM * BK * 4;   // 16 KB: one 128-row operand image
@@ -96,6 +116,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+// two such loads (16 columns each, at taddr0 and taddr1), one wait
+__device__ __forceinline__ void tmem_ld16x2(uint32_t taddr0, uint32_t taddr1, float (&v)[16], float (&w)[16]) {
+  uint32_t r[16], u[16];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(taddr0));
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+               : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+               : "r"(taddr1));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) { v[i] = __uint_as_float(r[i]); w[i] = __uint_as_float(u[i]); }
+}
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
@@ -117,18 +150,35 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
 // byte offset of 16-byte chunk c (0..7) of row r in a swizzled operand image
 __device__ __forceinline__ uint32_t swz(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
 
+// x = hi + lo: hi is x rounded to the nearest TF32 value (10 stored mantissa bits;
+// on the magnitude bits: add half a unit of the last kept bit, clear the 13 bits
+// below; ties, one x in 2^13, go away from zero), lo = x - hi exactly (|lo| <= 2^-11
+// |x|, up to 12 significant bits, of either sign).  The tensor core reads lo to 11
+// significant bits, truncating at most one, so the product's error is about 2^-22 of
+// it and, lo being as often negative as positive, without bias.  (Truncating x to hi
+// instead leaves lo with the sign of x: the dropped parts of every square then add
+// up, about 2e-7 low over a sum of squares.)
 __device__ __forceinline__ void split(float x, float& hi, float& lo) {
-  hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-  lo = x - hi;   // exact: x and hi share the exponent
+  hi = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+  lo = x - hi;
 }
 __device__ __forceinline__ void split4(float4 x, float4& hi, float4& lo) {
   split(x.x, hi.x, lo.x); split(x.y, hi.y, lo.y); split(x.z, hi.z, lo.z); split(x.w, hi.w, lo.w);
 }
 
-// Issue the 12 MMAs of one k-tile (4 K-steps x 3 products): a_hi b_hi into d, the
-// two small cross products into ds (ds == d accumulates all three together).  The
+__device__ __forceinline__ void two_sum(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  const float ap = s - bp;
+  lo += (hi - ap) + (x - bp);
+  hi = s;
+}
+
+// Issue the MMAs of one k-tile (4 K-steps x 3 products, x 4 with LOLO): a_hi b_hi
+// into d, the small products into ds (ds == d accumulates them all together).  The
 // tensor core's FP32 accumulation rounds each addition, so keeping the small terms
 // apart from the large one, and the chunks short, bounds the accumulated rounding.
+template <bool LOLO = false>
 __device__ __forceinline__ void mma_ktile(uint32_t d, uint32_t ds, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
                                           uint32_t b_lo, uint32_t idesc, bool overwrite) {
 #pragma unroll
@@ -139,6 +189,7 @@ __device__ __forceinline__ void mma_ktile(uint32_t d, uint32_t ds, uint32_t a_hi
     mma_tf32(d, ah, bh, idesc, first ? 0u : 1u);
     mma_tf32(ds, ah, bl, idesc, (first && ds != d) ? 0u : 1u);
     mma_tf32(ds, al, bh, idesc, 1u);
+    if (LOLO) mma_tf32(ds, al, bl, idesc, 1u);
   }
 }
 
@@ -184,7 +235,7 @@ __device__ __forceinline__ void gram_store(uint8_t* hi, uint8_t* lo, const float
 template <bool VEC>
 __global__ void __launch_bounds__(GTHREADS, 1)
 k_gram_tc(const float* __restrict__ A, long long lda, const float* __restrict__ B, long long ldb, long long nd,
-          int ns, int nt, int nsplit, double* __restrict__ part, int* status) {
+          int ns, int nt, int nsplit, double* __restrict__ part, int* status, int gsh) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t bar[GST];
   __shared__ uint32_t tmem_base;
@@ -217,6 +268,7 @@ k_gram_tc(const float* __restrict__ A, long long lda, const float* __restrict__ 
   float4 ca[GQ], cb[GQ], na[GQ], nb[GQ];
   gram_load<VEC>(A, lda, i0, ns, nd, kt0 * BK, ca);
   gram_load<VEC>(B, ldb, j0, ns, nd, kt0 * BK, cb);
+  const int gm = (1 << gsh) - 1;   // a chunk is 2^gsh k-tiles
   bool first_flush = true, aborted = false;
   int last = -1;
   for (int t = 0; t < nkt; ++t) {
@@ -235,13 +287,13 @@ k_gram_tc(const float* __restrict__ A, long long lda, const float* __restrict__ 
     if (threadIdx.x == 0) {
       tc_after();
       const uint32_t b0 = saddr(st);
-      mma_ktile(tmem, tmem + GN, b0, b0 + TILE_A, b0 + 2 * TILE_A, b0 + 3 * TILE_A, IDESC, t % GCH == 0);
+      mma_ktile<true>(tmem, tmem + GN, b0, b0 + TILE_A, b0 + 2 * TILE_A, b0 + 3 * TILE_A, IDESC, (t & gm) == 0);
       mma_commit(&bar[s]);
     }
     last = t;
 #pragma unroll
     for (int q = 0; q < GQ; ++q) { ca[q] = na[q]; cb[q] = nb[q]; }
-    if (t % GCH == GCH - 1 || t == nkt - 1) {
+    if ((t & gm) == gm || t == nkt - 1) {
       // drain the FP32 chunk in TMEM into the FP64 partial
       ok = mbar_wait(&bar[s], (uint32_t)(t / GST) & 1u);
       tc_after();
@@ -284,10 +336,10 @@ k_gram_tc(const float* __restrict__ A, long long lda, const float* __restrict__ 
 //     128-byte swizzle the MMA reads, into a ring of NH slots (four k-tiles in flight);
 //   * warps 0..14 split each landed tile in place into its TF32 high part and the
 //     remainder, whose images go to a ring of NL slots (a slot is free once the MMAs of
-//     the k-tile NL before are done); all 16 warps, every GCH k-tiles, drain the finished FP32 TMEM
+//     the k-tile NL before are done); all 16 warps, every 2^gsh k-tiles, drain the finished FP32 TMEM
 //     chunk into float-float accumulators in registers (TwoSum: the GPU's FP64 rate
 //     would make FP64 adds the bottleneck);
-//   * the 12 MMAs of a k-tile (3xTF32) go into one of two TMEM accumulator pairs,
+//   * the 16 MMAs of a k-tile (four products) go into one of two TMEM accumulator pairs,
 //     alternating per chunk, so that a chunk drains while the next accumulates.
 // Lane 0 of warp 15 issues the loads and the MMAs, as non-blocking steps in a loop that
 // also drains that warp's share of each completed chunk; it splits no tiles, so an MMA
@@ -310,20 +362,13 @@ __device__ __forceinline__ void tma2(uint32_t dst, const CUtensorMap* m, int c0,
 __device__ __forceinline__ void arrive(uint64_t* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
 }
-__device__ __forceinline__ void two_sum(float& hi, float& lo, float x) {
-  const float s = hi + x;
-  const float bp = s - hi;
-  const float ap = s - bp;
-  lo += (hi - ap) + (x - bp);
-  hi = s;
-}
 
 struct GramRing {
   uint64_t full[TST], conv[TST], mmad[TST], accd[2], tfree[2];
   int abort_flag;
   // role state (one thread each): next k-tile to load (pt) and to multiply (mt)
   int pt, mt;
-  int nkt, i0, j0;
+  int nkt, i0, j0, gsh;
   long long kt0;
   uint32_t tmem, sm;
 };
@@ -349,16 +394,17 @@ __device__ __noinline__ void gram_poll(GramRing* R, const CUtensorMap* ma, const
     constexpr uint32_t IDESC = idesc_tf32(BM, GN);
     int mt = R->mt;
     while (mt < R->nkt) {
-      const int s = mt % TST, c = mt / GCH, b = c & 1;
+      const int s = mt % TST, c = mt >> R->gsh, b = c & 1;
+      const int gm = (1 << R->gsh) - 1;
       if (!ptx::mbar_test(&R->conv[s], (uint32_t)(mt / TST) & 1u)) break;
-      if (mt % GCH == 0 && c >= 2 && !ptx::mbar_test(&R->tfree[b], (uint32_t)((c / 2) - 1) & 1u)) break;
+      if ((mt & gm) == 0 && c >= 2 && !ptx::mbar_test(&R->tfree[b], (uint32_t)((c / 2) - 1) & 1u)) break;
       tc_after();
       const uint32_t h0 = R->sm + (uint32_t)(s * TSTAGE);
       const uint32_t l0 = R->sm + (uint32_t)((TST + mt % TLO) * TSTAGE);
       const uint32_t d = R->tmem + (uint32_t)(b * 2 * GN);
-      mma_ktile(d, d + GN, h0, l0, h0 + TILE_A, l0 + TILE_A, IDESC, mt % GCH == 0);
+      mma_ktile<true>(d, d + GN, h0, l0, h0 + TILE_A, l0 + TILE_A, IDESC, (mt & gm) == 0);
       mma_commit(&R->mmad[s]);
-      if (mt % GCH == GCH - 1 || mt == R->nkt - 1) mma_commit(&R->accd[b]);
+      if ((mt & gm) == gm || mt == R->nkt - 1) mma_commit(&R->accd[b]);
       ++mt;
     }
     R->mt = mt;
@@ -367,7 +413,7 @@ __device__ __noinline__ void gram_poll(GramRing* R, const CUtensorMap* ma, const
 
 __global__ void __launch_bounds__(TTHREADS, 1)
 k_gram_tma(const __grid_constant__ CUtensorMap ma, const __grid_constant__ CUtensorMap mb, long long nd, int nt,
-           int nsplit, double* __restrict__ part, int* status) {
+           int nsplit, double* __restrict__ part, int* status, int gsh) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ GramRing R;
   __shared__ uint32_t tmem_base;
@@ -400,6 +446,7 @@ k_gram_tma(const __grid_constant__ CUtensorMap ma, const __grid_constant__ CUten
     R.pt = 0;
     R.mt = 0;
     R.nkt = nkt;
+    R.gsh = gsh;
     R.i0 = ti * BM;
     R.j0 = tj * GN;
     R.kt0 = kt0;
@@ -413,7 +460,8 @@ k_gram_tma(const __grid_constant__ CUtensorMap ma, const __grid_constant__ CUten
   __syncthreads();
   tc_after();
   const uint32_t tmem = tmem_base;
-  const int nchunk = (nkt + GCH - 1) / GCH;
+  const int gm = (1 << gsh) - 1;
+  const int nchunk = (nkt + gm) >> gsh;
   volatile int* abort_flag = &R.abort_flag;
   // warp 15 is the control warp: its lane 0 issues the loads and the MMAs, and the warp
   // drains its share of TMEM; warps 0..14 split the landed tiles and drain theirs
@@ -441,11 +489,11 @@ k_gram_tma(const __grid_constant__ CUtensorMap ma, const __grid_constant__ CUten
     tc_after();
     const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(b * 2 * GN + col0);
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {   // a_hi b_hi (h = 0, 1), then the cross terms (h = 2, 3)
-      float v[16];
-      tmem_ld16(ta + (uint32_t)((h >> 1) * GN + 16 * (h & 1)), v);
+    for (int h = 0; h < 2; ++h) {   // columns 16 h .. 16 h + 15: a_hi b_hi plus the small products
+      float v[16], vs[16];
+      tmem_ld16x2(ta + (uint32_t)(16 * h), ta + (uint32_t)(GN + 16 * h), v, vs);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) two_sum(ahi[16 * (h & 1) + q], alo[16 * (h & 1) + q], v[q]);
+      for (int q = 0; q < 16; ++q) two_sum(ahi[16 * h + q], alo[16 * h + q], v[q] + vs[q]);
     }
     tc_before();
     __syncwarp();
@@ -502,7 +550,7 @@ k_gram_tma(const __grid_constant__ CUtensorMap ma, const __grid_constant__ CUten
       proxy_fence();
       __syncwarp();
       if (lane == 0) arrive(&R.conv[s]);
-      if (t % GCH == GCH / 2 && drained < t / GCH) {
+      if ((t & gm) == (gm + 1) / 2 && drained < (t >> gsh)) {
         ok = wait(&R.accd[drained & 1], (uint32_t)(drained / 2) & 1u);
         if (ok) drain_now(drained++);
       }
@@ -538,8 +586,10 @@ k_gram_tma(const __grid_constant__ CUtensorMap ma, const __grid_constant__ CUten
 }
 
 // G[i + j ns] from the partials: fixed-order sum over splits; tile pairs below the
-// diagonal are the transposes of those above; diagonal tiles are symmetrised.
-__global__ void k_gram_reduce(const double* __restrict__ part, int nt, int nsplit, int ns, double* __restrict__ G) {
+// diagonal are the transposes of those above (times sgn: 1 for a symmetric G, -1 for
+// an antisymmetric one); diagonal tiles are (anti)symmetrised.
+__global__ void k_gram_reduce(const double* __restrict__ part, int nt, int nsplit, int ns, double* __restrict__ G,
+                              double sgn) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)ns * ns) return;
   const int i = (int)(e % ns), j = (int)(e / ns);
@@ -553,19 +603,42 @@ __global__ void k_gram_reduce(const double* __restrict__ part, int nt, int nspli
     if (ti <= tj) a += Ps[(size_t)jj * BM + ii];
     if (ti >= tj) b += Ps[(size_t)ii * BM + jj];
   }
-  G[e] = ti < tj ? a : (ti > tj ? b : 0.5 * (a + b));
+  G[e] = ti < tj ? a : (ti > tj ? sgn * b : 0.5 * (a + sgn * b));
+}
+
+// JB = i B for complex B (nd x ns, ldb; JB leading dimension nd): (re, im) -> (-im, re)
+__global__ void k_times_i(const float2* __restrict__ B, long long ldb, long long nd, int ns, float2* __restrict__ JB) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nd * ns) return;
+  const long long g = e % nd, j = e / nd;
+  const float2 v = B[g + j * ldb];
+  JB[e] = make_float2(-v.y, v.x);
+}
+
+// G = Gre - i Gim (Gre = r(A)^T r(B), Gim = r(A)^T r(i B), both ns x ns)
+__global__ void k_cgram_combine(const double* __restrict__ Gre, const double* __restrict__ Gim, long long nn,
+                                double2* __restrict__ G) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < nn) G[e] = make_double2(Gre[e], -Gim[e]);
 }
 
 // ------------------------------------------------------------------ rotation
 // Shared-memory images of Yr: for column half nh (256 columns) and k-tile t,
 // hi then lo, each 256 rows (columns n of Yr) x 32 values (rows k of Yr), swizzled.
-__global__ void k_rot_pack(const double* __restrict__ Yr, int ns, int nkt, int nnh, float* __restrict__ bp) {
+// CPLX: Yr is complex (ns x ns, (re, im) pairs) and its real K = 2 ns rows are
+// Re Yr over Im Yr.
+template <bool CPLX>
+__global__ void k_rot_pack(const double* __restrict__ Yr, int ns, int nk, int nkt, int nnh, float* __restrict__ bp) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)nnh * nkt * RN * BK) return;
   const int kk = (int)(e % BK), r = (int)((e / BK) % RN);
   const int t = (int)((e / (BK * RN)) % nkt), nh = (int)(e / ((long long)BK * RN * nkt));
   const int n = nh * RN + r, k = t * BK + kk;
-  const float x = (n < ns && k < ns) ? (float)Yr[k + (size_t)n * ns] : 0.f;
+  float x = 0.f;
+  if (n < ns && k < nk) {
+    if constexpr (CPLX) x = (float)(k < ns ? Yr[2 * (k + (size_t)n * ns)] : Yr[2 * ((k - ns) + (size_t)n * ns) + 1]);
+    else x = (float)Yr[k + (size_t)n * ns];
+  }
   float hi, lo;
   split(x, hi, lo);
   const size_t img = (size_t)(nh * nkt + t) * 2 * (RN * BK);
@@ -575,10 +648,14 @@ __global__ void k_rot_pack(const double* __restrict__ Yr, int ns, int nkt, int n
 }
 
 // C[g + n ldc] = sum_k U[g + k ldu] Yr[k + n ns] for g in [128 blockIdx.y, +128),
-// n in [256 blockIdx.x, +256).
+// n in [256 blockIdx.x, +256), k < nk (= ns).  CPLX: U, C are the real views (2 nd
+// rows) of complex columns and k runs over nk = 2 ns: column k >= ns of the operand
+// is r(i U_{k - ns}), whose row g is -/+ row g ^ 1 of r(U_{k - ns}) (minus on the
+// real parts, the even rows).
+template <bool CPLX>
 __global__ void __launch_bounds__(THREADS, 1)
-k_rot_tc(const float* __restrict__ U, long long ldu, const float* __restrict__ bp, long long nd, int ns, int nkt_all,
-         float* __restrict__ C, long long ldc, int* status, int upper) {
+k_rot_tc(const float* __restrict__ U, long long ldu, const float* __restrict__ bp, long long nd, int ns, int nk,
+         int nkt_all, float* __restrict__ C, long long ldc, int* status, int upper) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t bar[RST];
   __shared__ uint32_t tmem_base;
@@ -607,7 +684,20 @@ k_rot_tc(const float* __restrict__ U, long long ldu, const float* __restrict__ b
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       const int k = t * BK + kh * 16 + j;
-      v[j] = (gok && k < ns) ? __ldg(U + g + (long long)k * ldu) : 0.f;
+      if constexpr (CPLX) {
+        float x = 0.f;
+        if (gok && k < nk) {
+          if (k < ns) {
+            x = __ldg(U + g + (long long)k * ldu);
+          } else {
+            x = __ldg(U + (g ^ 1) + (long long)(k - ns) * ldu);
+            if (!(g & 1)) x = -x;
+          }
+        }
+        v[j] = x;
+      } else {
+        v[j] = (gok && k < ns) ? __ldg(U + g + (long long)k * ldu) : 0.f;
+      }
     }
   };
   auto load_b = [&](int t, int s) {   // the hi and lo images of Yr, 64 KB
@@ -731,7 +821,8 @@ static bool map_operand(CUtensorMap* m, const float* X, long long ldx, long long
 }
 
 cudaError_t gram(sparc_ctx* ctx, const float* A, long long lda, const float* B, long long ldb, long long nd, int ns,
-                 double* G, void* scratch, cudaStream_t st) {
+                 double* G, void* scratch, cudaStream_t st, bool anti, bool fast) {
+  const int gsh = fast ? GCH_FAST_LOG : GCH_ACC_LOG;
   const int nt = ceil_div(ns, BM);
   const int pairs = nt * (nt + 1) / 2;
   const int nsplit = gram_nsplit(ctx, ns, nd);
@@ -743,26 +834,50 @@ cudaError_t gram(sparc_ctx* ctx, const float* A, long long lda, const float* B, 
     e = cudaFuncSetAttribute(k_gram_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, TSMEM);
     if (e != cudaSuccess) return e;
     k_gram_tma<<<dim3(pairs, nsplit), TTHREADS, TSMEM, st>>>(ma, mb, nd, nt, nsplit, (double*)scratch,
-                                                              ctx->d_status);
+                                                              ctx->d_status, gsh);
   } else if (vec) {
     e = cudaFuncSetAttribute(k_gram_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, GSMEM);
     if (e != cudaSuccess) return e;
     k_gram_tc<true><<<dim3(pairs, nsplit), GTHREADS, GSMEM, st>>>(A, lda, B, ldb, nd, ns, nt, nsplit,
-                                                                 (double*)scratch, ctx->d_status);
+                                                                 (double*)scratch, ctx->d_status, gsh);
   } else {
     e = cudaFuncSetAttribute(k_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, GSMEM);
     if (e != cudaSuccess) return e;
     k_gram_tc<false><<<dim3(pairs, nsplit), GTHREADS, GSMEM, st>>>(A, lda, B, ldb, nd, ns, nt, nsplit,
-                                                                  (double*)scratch, ctx->d_status);
+                                                                  (double*)scratch, ctx->d_status, gsh);
   }
   const long long nn = (long long)ns * ns;
-  k_gram_reduce<<<(unsigned)ceil_div(nn, 256), 256, 0, st>>>((const double*)scratch, nt, nsplit, ns, G);
+  k_gram_reduce<<<(unsigned)ceil_div(nn, 256), 256, 0, st>>>((const double*)scratch, nt, nsplit, ns, G,
+                                                             anti ? -1.0 : 1.0);
   ctx->launches += 2;
   return cudaGetLastError();
 }
 
-size_t rot_scratch_bytes(int ns) {
-  const int nkt = ceil_div(ns, BK), nnh = ceil_div(ns, RN);
+size_t cgram_scratch_bytes(const sparc_ctx* ctx, int ns, long long nd) {
+  const size_t g = (gram_scratch_bytes(ctx, ns, 2 * nd) + 255) & ~(size_t)255;
+  return g + 2 * (((size_t)ns * ns * sizeof(double) + 255) & ~(size_t)255);
+}
+
+cudaError_t cgram(sparc_ctx* ctx, const cf32* A, long long lda, const cf32* B, long long ldb, long long nd, int ns,
+                  cf64* G, cf32* JB, void* scratch, cudaStream_t st, bool fast) {
+  const size_t g = (gram_scratch_bytes(ctx, ns, 2 * nd) + 255) & ~(size_t)255;
+  double* Gre = (double*)((char*)scratch + g);
+  double* Gim = (double*)((char*)Gre + (((size_t)ns * ns * sizeof(double) + 255) & ~(size_t)255));
+  const long long ne = nd * ns, nn = (long long)ns * ns;
+  k_times_i<<<(unsigned)ceil_div(ne, 256), 256, 0, st>>>((const float2*)B, ldb, nd, ns, (float2*)JB);
+  ++ctx->launches;
+  cudaError_t e = gram(ctx, (const float*)A, 2 * lda, (const float*)B, 2 * ldb, 2 * nd, ns, Gre, scratch, st, false,
+                       fast);
+  if (e != cudaSuccess) return e;
+  e = gram(ctx, (const float*)A, 2 * lda, (const float*)JB, 2 * nd, 2 * nd, ns, Gim, scratch, st, true, fast);
+  if (e != cudaSuccess) return e;
+  k_cgram_combine<<<(unsigned)ceil_div(nn, 256), 256, 0, st>>>(Gre, Gim, nn, (double2*)G);
+  ++ctx->launches;
+  return cudaGetLastError();
+}
+
+size_t rot_scratch_bytes(int ns, bool cplx) {
+  const int nkt = ceil_div(cplx ? 2 * ns : ns, BK), nnh = ceil_div(ns, RN);
   return (size_t)nnh * nkt * 2 * RN * BK * sizeof(float);
 }
 
@@ -771,11 +886,27 @@ cudaError_t rotate(sparc_ctx* ctx, const float* U, long long ldu, const double* 
   const int nkt = ceil_div(ns, BK), nnh = ceil_div(ns, RN);
   if ((nd + BM - 1) / BM > 65535) return cudaErrorInvalidValue;   // grid y limit
   const long long npack = (long long)nnh * nkt * RN * BK;
-  k_rot_pack<<<(unsigned)ceil_div(npack, 256), 256, 0, st>>>(Yr, ns, nkt, nnh, (float*)scratch);
-  cudaError_t e = cudaFuncSetAttribute(k_rot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, RSMEM);
+  k_rot_pack<false><<<(unsigned)ceil_div(npack, 256), 256, 0, st>>>(Yr, ns, ns, nkt, nnh, (float*)scratch);
+  cudaError_t e = cudaFuncSetAttribute(k_rot_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, RSMEM);
   if (e != cudaSuccess) return e;
-  k_rot_tc<<<dim3(nnh, (unsigned)ceil_div(nd, BM)), THREADS, RSMEM, st>>>(U, ldu, (const float*)scratch, nd, ns, nkt,
-                                                                          C, ldc, ctx->d_status, upper ? 1 : 0);
+  k_rot_tc<false><<<dim3(nnh, (unsigned)ceil_div(nd, BM)), THREADS, RSMEM, st>>>(
+      U, ldu, (const float*)scratch, nd, ns, ns, nkt, C, ldc, ctx->d_status, upper ? 1 : 0);
+  ctx->launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t crotate(sparc_ctx* ctx, const cf32* U, long long ldu, const cf64* Yr, long long nd, int ns, cf32* C,
+                    long long ldc, void* scratch, cudaStream_t st) {
+  const int nk = 2 * ns, nkt = ceil_div(nk, BK), nnh = ceil_div(ns, RN);
+  const long long nr = 2 * nd;   // rows of the real views
+  if ((nr + BM - 1) / BM > 65535) return cudaErrorInvalidValue;   // grid y limit
+  const long long npack = (long long)nnh * nkt * RN * BK;
+  k_rot_pack<true><<<(unsigned)ceil_div(npack, 256), 256, 0, st>>>((const double*)Yr, ns, nk, nkt, nnh,
+                                                                   (float*)scratch);
+  cudaError_t e = cudaFuncSetAttribute(k_rot_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, RSMEM);
+  if (e != cudaSuccess) return e;
+  k_rot_tc<true><<<dim3(nnh, (unsigned)ceil_div(nr, BM)), THREADS, RSMEM, st>>>(
+      (const float*)U, 2 * ldu, (const float*)scratch, nr, ns, nk, nkt, (float*)C, 2 * ldc, ctx->d_status, 0);
   ctx->launches += 2;
   return cudaGetLastError();
 }
@@ -817,6 +948,43 @@ extern "C" sparc_status sparc_rotate_f32(sparc_ctx* ctx, const float* U, int64_t
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t t0 = timing_begin(ctx, st);
   SPARC_CUDA(ctx, tc::rotate(ctx, U, ldu, Yr, nd, ns, C, ldc, ctx->ws, st));
+  timing_end(ctx, TK_ROT, t0, st);
+  return SPARC_OK;
+}
+
+extern "C" sparc_status sparc_gram_c64(sparc_ctx* ctx, const void* A, int64_t lda, const void* B, int64_t ldb,
+                                       int64_t nd, int ns, void* G, void* stream) {
+  if (!ctx) return SPARC_ERR_INVALID_ARG;
+  if (!A || !B || !G || nd < 1 || ns < 1 || ns > 4096 || lda < nd || ldb < nd)
+    return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_gram_c64: need nd >= 1, 1 <= ns <= 4096, lda, ldb >= nd");
+  SPARC_CUDA(ctx, cudaSetDevice(ctx->device));
+  const size_t gb = align256(tc::cgram_scratch_bytes(ctx, ns, nd));
+  if (!ensure_ws(ctx, gb + (size_t)nd * ns * sizeof(cf32)))
+    return fail(ctx, SPARC_ERR_OOM, "sparc_gram_c64: workspace allocation failed");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t t0 = timing_begin(ctx, st);
+  SPARC_CUDA(ctx, tc::cgram(ctx, (const cf32*)A, lda, (const cf32*)B, ldb, nd, ns, (cf64*)G,
+                            (cf32*)((char*)ctx->ws + gb), ctx->ws, st));
+  timing_end(ctx, TK_GRAM, t0, st);
+  return SPARC_OK;
+}
+
+extern "C" sparc_status sparc_rotate_c64(sparc_ctx* ctx, const void* U, int64_t ldu, const void* Yr, int64_t nd,
+                                         int ns, void* C, int64_t ldc, void* stream) {
+  if (!ctx) return SPARC_ERR_INVALID_ARG;
+  if (!U || !Yr || !C || nd < 1 || ns < 1 || ns > 4096 || ldu < nd || ldc < nd)
+    return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_rotate_c64: need nd >= 1, 1 <= ns <= 4096, ldu, ldc >= nd");
+  const char* u0 = (const char*)U;
+  const char* u1 = (const char*)((const cf32*)U + (size_t)ldu * (ns - 1) + nd);
+  const char* c0 = (const char*)C;
+  const char* c1 = (const char*)((cf32*)C + (size_t)ldc * (ns - 1) + nd);
+  if (u0 < c1 && c0 < u1) return fail(ctx, SPARC_ERR_INVALID_ARG, "sparc_rotate_c64: C overlaps U");
+  SPARC_CUDA(ctx, cudaSetDevice(ctx->device));
+  if (!ensure_ws(ctx, tc::rot_scratch_bytes(ns, true)))
+    return fail(ctx, SPARC_ERR_OOM, "sparc_rotate_c64: workspace allocation failed");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t t0 = timing_begin(ctx, st);
+  SPARC_CUDA(ctx, tc::crotate(ctx, (const cf32*)U, ldu, (const cf64*)Yr, nd, ns, (cf32*)C, ldc, ctx->ws, st));
   timing_end(ctx, TK_ROT, t0, st);
   return SPARC_OK;
 }

@@ -32,7 +32,7 @@ EXPORTS = ["sparc_create", "sparc_destroy", "sparc_last_error", "sparc_sync", "s
            "sparc_filter_graph_launch", "sparc_filter_graph_destroy", "sparc_scf_set_density",
            "sparc_mlp_create", "sparc_mlp_params", "sparc_mlp_descriptors", "sparc_mlp_forward", "sparc_mlp_grad",
            "sparc_mlp_train_step", "sparc_mlp_destroy", "sparc_scf_create_k", "sparc_debug_inject",
-           "sparc_filter_kernel"]
+           "sparc_filter_kernel", "sparc_gram_c64", "sparc_rotate_c64"]
 KERNEL_GENERIC, KERNEL_TILED, KERNEL_TMA = 0, 1, 2
 TIMED = {"hpass": 0, "gather": 1, "gram": 2, "eig": 3, "rotation": 4, "jacobi": 5, "fpass": 6,
          "ortho": 7, "series": 8, "ritz": 9}
@@ -118,6 +118,10 @@ def load(path: str = LIB_PATH):
                                  c_void_p]
     L.sparc_rotate_f32.argtypes = [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int, c_void_p, c_int64,
                                    c_void_p]
+    L.sparc_gram_c64.argtypes = [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int64, c_int, c_void_p,
+                                 c_void_p]
+    L.sparc_rotate_c64.argtypes = [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_int, c_void_p, c_int64,
+                                   c_void_p]
     L.sparc_scf_create.argtypes = [c_void_p, POINTER(SparcScfDesc), POINTER(c_void_p)]
     L.sparc_scf_create_k.argtypes = [POINTER(c_void_p), c_int, POINTER(c_double), POINTER(SparcScfDesc),
                                      POINTER(c_void_p)]
@@ -159,7 +163,7 @@ def load(path: str = LIB_PATH):
     L.sparc_scf_destroy.restype = None
     for name in ("sparc_timing_enable", "sparc_timing_read", "sparc_create", "sparc_sync", "sparc_ham_create", "sparc_ham_set_veff",
                  "sparc_apply_H", "sparc_cheb_filter", "sparc_lanczos_bounds", "sparc_rayleigh_ritz",
-                 "sparc_gram_f32", "sparc_rotate_f32", "sparc_scf_create", "sparc_scf_step", "sparc_scf_read",
+                 "sparc_gram_f32", "sparc_rotate_f32", "sparc_gram_c64", "sparc_rotate_c64", "sparc_scf_create", "sparc_scf_step", "sparc_scf_read",
                  "sparc_scf_forces"):
         getattr(L, name).restype = c_int
     _lib = L
@@ -564,6 +568,24 @@ def sparc_rotate_f32(ctx: Context, U, Yr, C, nd=None, stream=None):
     ns = U.shape[0]
     nd = U.shape[-1] if nd is None else nd
     ctx.check(load().sparc_rotate_f32(ctx.handle, _ptr(U), int(U.shape[-1]), _ptr(Yr), int(nd), int(ns), _ptr(C),
+                                      int(C.shape[-1]), _stream(stream)))
+
+
+def sparc_gram_c64(ctx: Context, A, B, G, nd=None, stream=None):
+    """G = A^H B (complex128, ns x ns) for complex64 CUDA tensors A, B of shape (ns, ld)
+    (column-major nd x ns); row j of the tensor G is column j of the matrix."""
+    ns = A.shape[0]
+    nd = A.shape[-1] if nd is None else nd
+    ctx.check(load().sparc_gram_c64(ctx.handle, _ptr(A), int(A.shape[-1]), _ptr(B), int(B.shape[-1]), int(nd),
+                                    int(ns), _ptr(G), _stream(stream)))
+
+
+def sparc_rotate_c64(ctx: Context, U, Yr, C, nd=None, stream=None):
+    """C = U Yr for complex64 CUDA tensors U, C of shape (ns, ld) and a complex128 (ns, ns)
+    tensor Yr holding the column-major ns x ns matrix (row n of the tensor is column n)."""
+    ns = U.shape[0]
+    nd = U.shape[-1] if nd is None else nd
+    ctx.check(load().sparc_rotate_c64(ctx.handle, _ptr(U), int(U.shape[-1]), _ptr(Yr), int(nd), int(ns), _ptr(C),
                                       int(C.shape[-1]), _stream(stream)))
 
 

@@ -7,7 +7,8 @@
   are independent in the filter); FP64 Lanczos bounds against the oracle; the
   mixed Rayleigh-Ritz output against properties that hold at any size.
 * 40^3 Si-like cell at one Monkhorst-Pack k-point, complex64 filter on sampled
-  columns.
+  columns; the complex64 mixed Rayleigh-Ritz of the filtered Ns = 192 block against
+  the oracle's.
 """
 import numpy as np
 import pytest
@@ -223,3 +224,39 @@ def test_mixed_rayleigh_ritz_matches_oracle_at_ns256(ctx):
             assert 0.0 <= err <= 1e-3, err     # the series path ran
         U = U32.to(torch.float64)
         assert float((U @ U.T - torch.eye(ns, dtype=torch.float64, device="cuda")).abs().max()) < 5e-5
+
+
+def test_si_cell_kpoint_mixed_rayleigh_ritz_complex64_matches_oracle(ctx):
+    """The complex64 mixed Rayleigh-Ritz at the k-point workload's size (40^3 Si-like
+    cell, one Monkhorst-Pack k-point, Ns = 192, m = 20; Section 3.3): tensor-core
+    Grams and rotations on the real views of the Bloch orbitals, FP64 factorisations,
+    against the oracle's FP64 Rayleigh-Ritz (Eq. SubspaceGeneralizedEigenproblem) of
+    the same complex64 block.  Target: 1e-6 Ha on every Ritz value."""
+    from paper_1603_04339_gb300 import sparc
+    wl = synth.config3()
+    kidx = 5
+    H = sparc.Hamiltonian.from_workload(ctx, wl, kidx)
+    Hor = O.OracleH(wl, kidx)
+    ns = wl.ns
+    X = synth.random_orbitals(wl.nd, ns, 2021, complex_=True).astype(np.complex64)
+    Xd = torch.from_numpy(X).cuda()
+    Yd = torch.empty_like(Xd)
+    v0 = synth.lanczos_start(wl.nd, 2022, complex_=True)
+    a0, b = sparc.sparc_lanczos_bounds(H, 10, torch.from_numpy(v0).cuda())
+    a = a0 + (b - a0) * (ns / wl.nd) ** (2.0 / 3.0)
+    sparc.sparc_cheb_filter(H, wl.m, a, b, a0, Xd, Yd)
+    torch.cuda.synchronize()
+    Y = Yd.cpu().numpy().astype(np.complex128)       # the block both sides project
+    lam_ref, _, _, _ = O.rayleigh_ritz(Hor, Y)
+    U = Yd.clone()
+    eig = torch.zeros(ns, dtype=torch.float64, device="cuda")
+    sparc.sparc_rayleigh_ritz(H, U, eig, sparc.RR_MIXED)
+    torch.cuda.synchronize()
+    d = np.abs(eig.cpu().numpy() - lam_ref)
+    Uc = U.to(torch.complex128)
+    orth = float((Uc.conj() @ Uc.T - torch.eye(ns, dtype=torch.complex128, device="cuda")).abs().max())
+    print(f"complex64 mixed RR vs oracle at 40^3, Ns={ns}: max {d.max():.3e} Ha over "
+          f"[{lam_ref[0]:.4f}, {lam_ref[-1]:.4f}]; max |U^H U - I| = {orth:.2e}")
+    H.close()
+    assert d.max() < 1e-6, d.max()
+    assert orth < 5e-5, orth
