@@ -263,9 +263,25 @@ def kpoint_filter_throughput(sparc, synth, torch, ctx, reps=2, tune=True, nk=Non
     torch.cuda.synchronize()
     split = {k: ctx.timing_read(k)[0] for k in ("fpass", "gather")}
     ctx.timing(False)
+    # the complex64 mixed Rayleigh-Ritz of one k-point's filtered block (k != 0): Grams
+    # and rotations on the tensor cores (each timed call also copies the block in)
+    kk = 1 if nk > 1 else 0
+    U = torch.empty_like(Y[kk])
+    eig = torch.zeros(wl.ns, dtype=torch.float64, device="cuda")
+
+    def rr():
+        U.copy_(Y[kk])
+        sparc.sparc_rayleigh_ritz(Hs[kk], U, eig, sparc.RR_MIXED)
+
+    ms_rr, l_rr, _ = timed(rr)
+    ctx.timing(True)
+    rr()
+    torch.cuda.synchronize()
+    rr_split = {k: ctx.timing_read(k)[0] for k in ("gram", "rotation", "eig")}
+    ctx.timing(False)
     for H in Hs:
         H.close()
-    del X, Y
+    del X, Y, U
     torch.cuda.empty_cache()
     return {"workload": f"40^3 Si-like cell, 64 s+p atoms, 3x3x3 MP k-points ({nk} of 27), Ns=192, m=20, complex64",
             "batched": {"value": work / (ms_b * 1e-3) / 1e9, "unit": "Gpt-orb-deg/s", "ms_per_filter": ms_b,
@@ -275,7 +291,11 @@ def kpoint_filter_throughput(sparc, synth, torch, ctx, reps=2, tune=True, nk=Non
             "per_k": {"value": work / (ms_k * 1e-3) / 1e9, "unit": "Gpt-orb-deg/s", "ms_per_filter": ms_k,
                       "launches_per_filter": l_k},
             "hbm_roof": {"gpt_orb_deg_per_s": _peaks()[0] / 24.0, "bytes_per_unit": 24,
-                         "frac_batched": work / (ms_b * 1e-3) / 1e9 / (_peaks()[0] / 24.0)}}
+                         "frac_batched": work / (ms_b * 1e-3) / 1e9 / (_peaks()[0] / 24.0)},
+            "rayleigh_ritz_one_k": {"ms": ms_rr, "launches": l_rr, "gram_ms": rr_split["gram"],
+                                    "rotation_ms": rr_split["rotation"], "chol_eig_ms": rr_split["eig"],
+                                    "note": "complex64 mixed mode, Ns=192, tensor-core Grams and rotations; "
+                                            "includes a 98 MB device copy of the block"}}
 
 
 def cell_batch_throughput(sparc, synth, torch, ctx, reps=3, nbranch=8):
