@@ -277,8 +277,9 @@ def kpoint_filter_throughput(sparc, synth, torch, ctx, reps=2, tune=True, nk=Non
     ctx.timing(True)
     rr()
     torch.cuda.synchronize()
-    rr_split = {k: ctx.timing_read(k)[0] for k in ("gram", "rotation", "eig")}
+    rr_split = {k: ctx.timing_read(k)[0] for k in ("gram", "rotation", "eig", "jacobi", "ortho", "series", "ritz")}
     ctx.timing(False)
+    sweeps_rr = ctx.last_sweeps()
     for H in Hs:
         H.close()
     del X, Y, U
@@ -294,6 +295,9 @@ def kpoint_filter_throughput(sparc, synth, torch, ctx, reps=2, tune=True, nk=Non
                          "frac_batched": work / (ms_b * 1e-3) / 1e9 / (_peaks()[0] / 24.0)},
             "rayleigh_ritz_one_k": {"ms": ms_rr, "launches": l_rr, "gram_ms": rr_split["gram"],
                                     "rotation_ms": rr_split["rotation"], "chol_eig_ms": rr_split["eig"],
+                                    "jacobi_ms": rr_split["jacobi"], "jacobi_sweeps": sweeps_rr,
+                                    "first_factorisation_ms": rr_split["ortho"],
+                                    "second_factorisation_ms": rr_split["series"], "ritz_pairs_ms": rr_split["ritz"],
                                     "note": "complex64 mixed mode, Ns=192, tensor-core Grams and rotations; "
                                             "includes a 98 MB device copy of the block"}}
 
