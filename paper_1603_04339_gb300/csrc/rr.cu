@@ -273,6 +273,85 @@ __global__ void __launch_bounds__(256) k_chol_blk(TS* A, long long lda, TS* Dk, 
   }
 }
 
+// The same for complex FP64 blocks (A = L L^H, Hermitian; kb <= 64), right-looking in
+// dynamic shared memory (83,968 bytes): column j is scaled by the real 1 / L_jj, the
+// trailing lower triangle updated with S_ic -= L_ij conj(L_cj), and L^-1 formed in place
+// column by column from the last (X_jj = 1 / L_jj, X_ij = -(1 / L_jj) sum_{k=j+1..i}
+// X_ik L_kj).  One launch per diagonal block, in place of the per-column kernels.
+constexpr int CHOL_C_SMEM = (64 * 65 + 16 * 64 + 64) * (int)sizeof(cf64);
+__global__ void __launch_bounds__(256) k_chol_blk_c(cf64* A, long long lda, cf64* Dk, long long ldd, int kb,
+                                                    int* status) {
+  extern __shared__ __align__(16) cf64 csm[];
+  cf64(*S)[65] = reinterpret_cast<cf64(*)[65]>(csm);
+  cf64(*part)[64] = reinterpret_cast<cf64(*)[64]>(csm + 64 * 65);
+  cf64* x = csm + 64 * 65 + 16 * 64;
+  __shared__ double rdiag[64];
+  __shared__ double a0[64];
+  __shared__ int bad;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) bad = 0;
+  for (int e = tid; e < kb * kb; e += nt) {
+    const int i = e % kb, j = e / kb;
+    const cf64 v = i >= j ? A[i + (long long)j * lda] : cf64{0.0, 0.0};
+    S[i][j] = v;
+    if (i == j) a0[i] = v.x;
+  }
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    if (tid == 0) {
+      const double d = S[j][j].x;   // a_jj minus the updates of the columns before j
+      if (!(d > 1e-14 * a0[j]) || !isfinite(d)) {
+        bad = 1;
+        atomicOr(status, STATUS_NOT_POSDEF);
+      } else {
+        const double l = sqrt(d);
+        S[j][j] = cf64{l, 0.0};
+        rdiag[j] = 1.0 / l;
+      }
+    }
+    __syncthreads();
+    if (bad) return;
+    const double inv = rdiag[j];
+    for (int i = j + 1 + tid; i < kb; i += nt) S[i][j] = scale(inv, S[i][j]);
+    __syncthreads();
+    const int tx = tid & 15, ty = tid >> 4;
+    for (int i = j + 1 + ty; i < kb; i += 16) {
+      const cf64 lij = S[i][j];
+      for (int c = j + 1 + tx; c <= i; c += 16) S[i][c] = S[i][c] - lij * Tr<cf64>::conj(S[c][j]);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < kb * kb; e += nt) {
+    const int i = e % kb, j = e / kb;
+    A[i + (long long)j * lda] = i >= j ? S[i][j] : cf64{0.0, 0.0};
+  }
+  __syncthreads();
+  for (int j = kb - 1; j >= 0; --j) {
+    const double rj = rdiag[j];
+    const int tx = tid & 15, ty = tid >> 4;
+    for (int i = j + 1 + ty; i < kb; i += 16) {
+      cf64 sacc{0.0, 0.0};
+      for (int k = j + 1 + tx; k <= i; k += 16) sacc = sacc + S[i][k] * S[k][j];
+      part[tx][i] = sacc;
+    }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < kb; i += nt) {
+      cf64 sacc{0.0, 0.0};
+      for (int q = 0; q < 16; ++q)
+        if (j + 1 + q <= i) sacc = sacc + part[q][i];
+      x[i] = scale(-rj, sacc);
+    }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < kb; i += nt) S[i][j] = x[i];
+    if (tid == 0) S[j][j] = cf64{rj, 0.0};
+    __syncthreads();
+  }
+  for (int e = tid; e < kb * kb; e += nt) {
+    const int i = e % kb, j = e / kb;
+    Dk[i + (long long)j * ldd] = i >= j ? S[i][j] : cf64{0.0, 0.0};
+  }
+}
+
 // The same for FP32 blocks of up to 64, left-looking with one thread per row: column j
 // is L_jj = sqrt(a_jj - sum_{k<j} L_jk^2), L_ij = (a_ij - sum_{k<j} L_ik L_jk) / L_jj,
 // two barriers per column; then thread j forms column j of L^-1 by forward
@@ -1098,6 +1177,10 @@ sparc_status chol_inverse(sparc_ctx* ctx, TW* A, TW* Li, int n, TW* Dinv, TW* tm
       ctx->launches += 1;
     } else if constexpr (std::is_same<TW, double>::value) {
       k_chol_blk<TW, CB><<<1, 256, 0, st>>>(Akk, n, Dk, CB, kb, ctx->d_status);
+      ctx->launches += 1;
+    } else if constexpr (std::is_same<TW, cf64>::value) {
+      SPARC_CUDA(ctx, cudaFuncSetAttribute(k_chol_blk_c, cudaFuncAttributeMaxDynamicSharedMemorySize, CHOL_C_SMEM));
+      k_chol_blk_c<<<1, 256, CHOL_C_SMEM, st>>>(Akk, n, Dk, CB, kb, ctx->d_status);
       ctx->launches += 1;
     } else {
       TW* blk = part;                     // kb x kb, leading dimension kb
