@@ -223,7 +223,7 @@ def test_complex64_mixed_rr_simple_and_degenerate_spectra(ctx, case):
     Hor = O.OracleH(wl)
     ns = 48
     X = synth.random_orbitals(wl.nd, ns, 17, complex_=True)
-    a0, b, _ = O.lanczos_bounds(Hor, synth.lanczos_start(wl.nd, 3, complex_=True), 10)
+    a0, b, _ = O.lanczos_bounds(Hor, synth.lanczos_start(wl.nd, 3, complex_=Hor.is_complex), 10)
     Yf = O.cheb_filter(Hor, X, 8, a0 + 0.05 * (b - a0), b, a0).astype(np.complex64)
     Ud = torch.from_numpy(Yf).cuda()
     eig = torch.zeros(ns, dtype=torch.float64, device="cuda")
