@@ -1,4 +1,4 @@
-// Tensor-core products of Rayleigh-Ritz for FP32 orbitals (Section 3.4: the
+// Tensor-core products of Rayleigh-Ritz for FP32 and complex64 orbitals (Section 3.4: the
 // projections of Eq. SubspaceGeneralizedEigenproblem and the rotation of Eq.
 // OrbitalTransformation) on sm_103a.
 //
@@ -48,14 +48,15 @@ constexpr int THREADS = 256;   // rotation CTA
 constexpr int GTHREADS = 512;  // Gram CTA: 16 warps split, swizzle and stage the operands
 constexpr int GN = 128;        // Gram tile N
 constexpr int GST = 3;         // Gram pipeline stages
-// Gram k-tiles per FP32 accumulation chunk, 2^gsh: 2 (64 grid points), or 8 (256) where the Gram only has to be good to FP32 accuracy (the first
-// orthonormalisation, which the second corrects).  The tensor core's FP32
-// accumulation rounds toward zero: a sum of like-signed products (each diagonal entry
-// of M~, most of H~'s, columns close to parallel) comes out low, by 6e-7 of itself
-// over chunks of 8 k-tiles (32 MMAs, measured) against 2.5e-7 over chunks of 2.  A
-// bias the same for every entry of M~ and H~ would leave the Ritz values alone, but
-// it is not (H~'s sums are partly of mixed sign), and at 8 k-tiles it moved them by
-// up to 1.8e-7 of themselves, against 2e-8 at 2.
+// Gram k-tiles per FP32 accumulation chunk, 2^gsh: 2 (64 grid points), or 8 (256)
+// where the Gram only has to be good to FP32 accuracy (the first orthonormalisation,
+// which the second corrects).  The tensor core's FP32 accumulation rounds toward zero:
+// a sum of like-signed products (each diagonal entry of M~, most of H~'s, columns
+// close to parallel) comes out low, by 6e-7 of itself over chunks of 8 k-tiles (32
+// MMAs, measured) against 2.5e-7 over chunks of 2.  A bias the same for every entry of
+// M~ and H~ would leave the Ritz values alone, but it is not (H~'s sums are partly of
+// mixed sign): on the 64^3 cell the mixed Ritz values were 7.6e-7 Ha from the FP64
+// path's with chunks of 8 (and a truncated split), 1.7e-7 with chunks of 2.
 constexpr int GCH_ACC_LOG = 1;    // 2 k-tiles
 constexpr int GCH_FAST_LOG = 3;   // 8 k-tiles
 constexpr int RN = 256;        // rotation tile N
