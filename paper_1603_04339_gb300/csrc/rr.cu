@@ -1493,7 +1493,7 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
   // rotations of two consecutive rounds)
   const size_t wjb = (bj_type<TS>() && bj_size(ns) > 0) ? align256((size_t)4 * BJ_MAX * ns * sizeof(float)) : 0;
   const size_t extra = hub + 2 * partb + 10 * sm + dinvb + align256(nn * es) + 3 * align256(nn * sizeof(TS)) +
-                       align256(ns * sizeof(double)) + tcb + w1b + jbb + gsb + wjb + 256;
+                       2 * align256(ns * sizeof(double)) + tcb + w1b + jbb + gsb + wjb + 256;
   BlockWs w;
   char* tail = nullptr;
   sparc_status s = block_ws(H, DtypeOf<T>::v, ns, extra, &w, &tail);
@@ -1518,8 +1518,11 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
   TS* S1 = (TS*)tail; tail += align256(nn * sizeof(TS));
   TS* SV = (TS*)tail; tail += align256(nn * sizeof(TS));
   double* lam = (double*)tail; tail += align256(ns * sizeof(double));
-  void* tcs = tail; tail += tcb;
+  double* eigw = (double*)tail; tail += align256(ns * sizeof(double));   // sorted Ritz values (graph-owned)
+  // the block Jacobi's rotations ahead of the tensor-core scratch, whose size depends on
+  // Nd: every buffer a cached graph uses sits at an offset fixed by those in its key
   float* Wjb = wjb ? (float*)tail : nullptr; tail += wjb;
+  void* tcs = tail; tail += tcb;
   T* JB = (T*)tail; tail += jbb;
   T* W1 = (T*)tail;
   const long long pcap = (long long)(partb / ew);
@@ -1782,14 +1785,16 @@ sparc_status rayleigh_ritz(sparc_ham* H, T* U, int ns, long long ld, double* eig
       }
       k_rayleigh<TW><<<ceil_div(ns, 8), 256, 0, fs>>>(Vj, T1, ns, lam);
       ++ctx->launches;
-      k_sort<TW><<<ceil_div(ns, 128), 128, 0, fs>>>(nullptr, lam, ns, eig, (int*)scal);
+      k_sort<TW><<<ceil_div(ns, 128), 128, 0, fs>>>(nullptr, lam, ns, eigw, (int*)scal);
       k_permute_cols<TW><<<ceil_div(nn, 256), 256, 0, fs>>>(Vj, (const int*)scal, ns, Qs);
       ctx->launches += 2;
       return SPARC_OK;
     };
-    if constexpr (TCP) s = replay(ctx, std::make_tuple(1 << 22, ns, (void*)SV, (void*)eig, (void*)Qs), st, ritz);
+    if constexpr (TCP) s = replay(ctx, std::make_tuple(1 << 22, ns, (void*)SV, (void*)eigw, (void*)Qs), st, ritz);
     else s = ritz(st);
     if (s != SPARC_OK) return s;
+    // the caller's eig outside the graph, so that the graph's key holds no caller buffer
+    SPARC_CUDA(ctx, cudaMemcpyAsync(eig, eigw, ns * sizeof(double), cudaMemcpyDeviceToDevice, st));
   }
   timing_end(ctx, TK_RITZ, tritz, st);
   ctx->last_sweeps = sweeps;
